@@ -1,0 +1,259 @@
+"""Plain FP64 CPU oracle for the GRMHD method-of-lines hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product path (the CUDA library
+and its binding) never imports, links or runs anything here.
+
+The numerics live in ``grmhd_oracle.cpp`` (see its header for the paper
+passages each routine follows).  This module only compiles it with the host
+compiler and marshals numpy arrays through ``ctypes``.
+
+Array layout (shared with the CUDA library only as a data format): SoA
+``[var][z][y][x]`` float64, x fastest, ``N = n + 2*ng`` points per axis.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "grmhd_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+REC_MINMOD, REC_WENO5 = 0, 1
+BC_PERIODIC, BC_COPY = 0, 1
+RK2, RK3, RK4 = 2, 3, 4
+
+
+class OParams(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("recon", ctypes.c_int32),
+        ("bc", ctypes.c_int32),
+        ("rho_atm", ctypes.c_double),
+        ("p_atm", ctypes.c_double),
+        ("weno_eps", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in place (g++ -O2 -fopenmp)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        Dd = ctypes.c_double
+        pp = ctypes.POINTER(OParams)
+        lib.oracle_num_threads.restype = I
+        lib.oracle_set_threads.argtypes = [I]
+        lib.oracle_prim2con.argtypes = [P, I, P, Dd, P, P, P]
+        lib.oracle_con2prim.argtypes = [P, I, P, pp, P, P, P, P]
+        lib.oracle_con2prim.restype = I
+        lib.oracle_fill_ghosts.argtypes = [P, I, I, I, P]
+        lib.oracle_rhs.argtypes = [P, I, P, pp, P, P, P, P]
+        lib.oracle_rhs_cells.argtypes = [P, I, P, pp, P, P, P, ctypes.c_long, P, P]
+        lib.oracle_source_cells.argtypes = [P, I, P, pp, P, P, P, ctypes.c_long, P, P]
+        lib.oracle_rk_step.argtypes = [P, I, P, pp, I, Dd, P, P, P, P, P]
+        lib.oracle_rk_step.restype = I
+        lib.oracle_point.argtypes = [P, P, Dd, P, P, P, P]
+        lib.oracle_hlle.argtypes = [P, P, P, Dd, I, P, P]
+        lib.oracle_reconstruct_1d.argtypes = [I, Dd, I, P, P, P]
+        lib.oracle_con2prim_point.argtypes = [P, P, pp, P]
+        lib.oracle_con2prim_point.restype = I
+        lib.oracle_loss_jvp.argtypes = [P, I, P, pp, I, Dd, I, P, P, Dd, P, P, P, P]
+        lib.oracle_loss_jvp.restype = I
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(gamma=5.0 / 3.0, recon=REC_WENO5, bc=BC_PERIODIC, rho_atm=1e-10, p_atm=None, weno_eps=1e-6):
+    if p_atm is None:
+        p_atm = 1e-2 * rho_atm ** gamma
+    return OParams(gamma, recon, bc, rho_atm, p_atm, weno_eps)
+
+
+class Grid:
+    """Interior extent n (x, y, z), ghost width ng, spacing dx (x, y, z)."""
+
+    def __init__(self, n, ng, dx):
+        self.n = tuple(int(v) for v in n)
+        self.ng = int(ng)
+        self.dx = tuple(float(v) for v in dx)
+        self._n = (ctypes.c_int * 3)(*self.n)
+        self._dx = (ctypes.c_double * 3)(*self.dx)
+
+    @property
+    def shape(self):
+        nx, ny, nz = (v + 2 * self.ng for v in self.n)
+        return (nz, ny, nx)
+
+    def interior(self):
+        g = self.ng
+        nx, ny, nz = self.n
+        return (slice(g, g + nz), slice(g, g + ny), slice(g, g + nx))
+
+
+def threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def prim2con(grid: Grid, gamma: float, prim, metric=None):
+    prim = _f64(prim)
+    metric = _f64(metric)
+    cons = np.zeros_like(prim)
+    _load().oracle_prim2con(grid._n, grid.ng, grid._dx, gamma, _ptr(prim), _ptr(metric), _ptr(cons))
+    return cons
+
+
+def con2prim(grid: Grid, params: OParams, cons, metric=None, prim_init=None):
+    """Recover primitives on the interior; ghost entries copied from prim_init."""
+    cons = _f64(cons)
+    metric = _f64(metric)
+    prim = np.zeros_like(cons) if prim_init is None else np.array(prim_init, dtype=np.float64, copy=True)
+    status = np.zeros(grid.shape, dtype=np.int8)
+    nfail = _load().oracle_con2prim(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(cons),
+                                    _ptr(metric), _ptr(prim), _ptr(status))
+    return prim, status, nfail
+
+
+def fill_ghosts(grid: Grid, bc: int, arr):
+    arr = np.array(arr, dtype=np.float64, copy=True, order="C")
+    nvar = arr.shape[0]
+    _load().oracle_fill_ghosts(grid._n, grid.ng, bc, nvar, _ptr(arr))
+    return arr
+
+
+def rhs(grid: Grid, params: OParams, prim, metric=None, kij=None):
+    prim = _f64(prim)
+    metric = _f64(metric)
+    kij = _f64(kij)
+    out = np.zeros_like(prim)
+    _load().oracle_rhs(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(prim), _ptr(metric),
+                       _ptr(kij), _ptr(out))
+    return out
+
+
+def rhs_cells(grid: Grid, params: OParams, prim, cells, metric=None, kij=None):
+    """RHS at selected cells; ``cells`` is an (m, 3) int array of (i, j, k) full-array indices."""
+    prim = _f64(prim)
+    metric = _f64(metric)
+    kij = _f64(kij)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros((cells.shape[0], 8), dtype=np.float64)
+    _load().oracle_rhs_cells(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(prim), _ptr(metric),
+                             _ptr(kij), cells.shape[0], _ptr(cells), _ptr(out))
+    return out
+
+
+def source_cells(grid: Grid, params: OParams, prim, cells, metric=None, kij=None):
+    """Eq. 13 source vector at selected (i, j, k) cells, shape (m, 8)."""
+    prim = _f64(prim)
+    metric = _f64(metric)
+    kij = _f64(kij)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros((cells.shape[0], 8), dtype=np.float64)
+    _load().oracle_source_cells(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(prim), _ptr(metric),
+                                _ptr(kij), cells.shape[0], _ptr(cells), _ptr(out))
+    return out
+
+
+def rk_step(grid: Grid, params: OParams, scheme: int, dt: float, cons, prim, metric=None, kij=None):
+    cons = np.array(cons, dtype=np.float64, copy=True)
+    prim = np.array(prim, dtype=np.float64, copy=True)
+    metric = _f64(metric)
+    kij = _f64(kij)
+    status = np.zeros(grid.shape, dtype=np.int8)
+    nfail = _load().oracle_rk_step(grid._n, grid.ng, grid._dx, ctypes.byref(params), scheme, dt, _ptr(cons),
+                                   _ptr(prim), _ptr(metric), _ptr(kij), _ptr(status))
+    return cons, prim, nfail
+
+
+def point(prim8, gamma, adm10=None):
+    """Conserved vector, fluxes F[d][8], speeds lam[d][(minus, plus)], extras (W, b^2, b.u, u.u)."""
+    p = _f64(np.asarray(prim8).reshape(8))
+    a = None if adm10 is None else _f64(np.asarray(adm10).reshape(10))
+    U = np.zeros(8)
+    F = np.zeros((3, 8))
+    lam = np.zeros((3, 2))
+    ex = np.zeros(4)
+    _load().oracle_point(_ptr(p), _ptr(a), gamma, _ptr(U), _ptr(F), _ptr(lam), _ptr(ex))
+    return U, F, lam, ex
+
+
+def hlle(pL, pR, gamma, direction, adm10=None):
+    pL = _f64(np.asarray(pL).reshape(8))
+    pR = _f64(np.asarray(pR).reshape(8))
+    a = None if adm10 is None else _f64(np.asarray(adm10).reshape(10))
+    F = np.zeros(8)
+    sp = np.zeros(4)
+    _load().oracle_hlle(_ptr(pL), _ptr(pR), _ptr(a), gamma, int(direction), _ptr(F), _ptr(sp))
+    return F, sp
+
+
+def reconstruct_1d(recon: int, u, eps=1e-6):
+    """Face states for faces between cells c-1 and c, c = 3 .. n-3 (NaN elsewhere)."""
+    u = _f64(np.asarray(u).ravel())
+    n = u.size
+    uL = np.full(n, np.nan)
+    uR = np.full(n, np.nan)
+    _load().oracle_reconstruct_1d(recon, eps, n, _ptr(u), _ptr(uL), _ptr(uR))
+    return uL, uR
+
+
+def con2prim_point(U8, params: OParams, adm10=None):
+    U = _f64(np.asarray(U8).reshape(8))
+    a = None if adm10 is None else _f64(np.asarray(adm10).reshape(10))
+    out = np.zeros(8)
+    st = _load().oracle_con2prim_point(_ptr(U), _ptr(a), ctypes.byref(params), _ptr(out))
+    return out, st
+
+
+def loss_jvp(grid: Grid, params: OParams, scheme: int, dt: float, nsteps: int, prim0, dprim0=None, dgamma=0.0,
+             metric=None, kij=None):
+    """Value and directional derivative of L = sum rho^2 sqrt(gamma) dV after nsteps."""
+    prim0 = _f64(prim0)
+    dprim0 = _f64(dprim0)
+    metric = _f64(metric)
+    kij = _f64(kij)
+    L = ctypes.c_double()
+    dL = ctypes.c_double()
+    nfail = _load().oracle_loss_jvp(grid._n, grid.ng, grid._dx, ctypes.byref(params), scheme, dt, nsteps,
+                                    _ptr(prim0), _ptr(dprim0), float(dgamma), _ptr(metric), _ptr(kij),
+                                    ctypes.byref(L), ctypes.byref(dL))
+    return L.value, dL.value, nfail

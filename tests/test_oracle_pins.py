@@ -1,0 +1,625 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a number
+printed in the paper, the paper's explicit 3+1 equations (the oracle computes
+the covariant projections instead), a closed form, an invariant, a textbook
+special case or an independent library root finder.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(12345)
+
+
+# ----------------------------------------------------------------- helpers --
+def random_metric(rng, shift=True):
+    """A random, positive-definite ADM metric (alpha, beta^i, gamma_ij)."""
+    A = rng.normal(size=(3, 3)) * 0.15
+    gam = np.eye(3) + A @ A.T + 0.1 * np.eye(3)
+    alpha = rng.uniform(0.5, 1.5)
+    beta = rng.normal(size=3) * 0.2 if shift else np.zeros(3)
+    return np.array([alpha, *beta, gam[0, 0], gam[0, 1], gam[0, 2], gam[1, 1], gam[1, 2], gam[2, 2]])
+
+
+def gam_of(adm):
+    return np.array([[adm[4], adm[5], adm[6]], [adm[5], adm[7], adm[8]], [adm[6], adm[8], adm[9]]])
+
+
+def random_prim(rng, gam, vmax=0.9, bmax=1.0):
+    rho = rng.uniform(0.1, 2.0)
+    P = rng.uniform(0.01, 2.0)
+    v = rng.normal(size=3)
+    v = v / math.sqrt(v @ gam @ v) * rng.uniform(0.0, vmax)
+    B = rng.normal(size=3) * rng.uniform(0.0, bmax)
+    return np.array([rho, *v, P, *B])
+
+
+def valencia_3p1(prim, adm, gamma):
+    """Eqs. 6-9 and Eq. 12 exactly as printed in Sec. 2.2 (3+1 form)."""
+    alpha, beta, gam = adm[0], adm[1:4], gam_of(adm)
+    sg = math.sqrt(np.linalg.det(gam))
+    rho, v, P, B = prim[0], prim[1:4], prim[4], prim[5:8]
+    vl = gam @ v
+    W = 1.0 / math.sqrt(1.0 - v @ vl)
+    Bl = gam @ B
+    ab0 = W * (B @ vl)                      # alpha b^0
+    bl = Bl / W + ab0 * vl                  # b_i
+    b2 = (B @ Bl + ab0 ** 2) / W ** 2
+    eps = P / ((gamma - 1) * rho)
+    h = 1 + eps + P / rho
+    hs = rho * h + b2                       # rho h*
+    Ps = P + b2 / 2
+    D = sg * rho * W
+    S = sg * (hs * W ** 2 * vl - ab0 * bl)
+    tau = sg * (hs * W ** 2 - Ps - ab0 ** 2) - D
+    Bc = sg * B
+    U = np.array([D, *S, tau, *Bc])
+    vt = v - beta / alpha
+    F = np.zeros((3, 8))
+    for i in range(3):
+        F[i, 0] = D * vt[i]
+        for j in range(3):
+            F[i, 1 + j] = S[j] * vt[i] + sg * Ps * (1.0 if i == j else 0.0) - bl[j] * Bc[i] / W
+        F[i, 4] = tau * vt[i] + sg * Ps * v[i] - ab0 * Bc[i] / W
+        for k in range(3):
+            F[i, 5 + k] = Bc[k] * vt[i] - Bc[i] * vt[k]
+        F[i] *= alpha
+    return U, F, W
+
+
+# ------------------------------------------------ prim -> cons, flux, state --
+def test_prim2con_and_flux_match_printed_equations():
+    """Covariant projections == Eqs. 6-9 and Eq. 12 (curved metric with shift)."""
+    for _ in range(200):
+        adm = random_metric(RNG)
+        prim = random_prim(RNG, gam_of(adm))
+        gamma = RNG.uniform(1.2, 2.0)
+        U, F, lam, ex = O.point(prim, gamma, adm)
+        U3, F3, W3 = valencia_3p1(prim, adm, gamma)
+        scale = np.max(np.abs(U3))
+        np.testing.assert_allclose(U, U3, rtol=0, atol=1e-13 * scale)
+        np.testing.assert_allclose(F, F3, rtol=0, atol=1e-13 * np.max(np.abs(F3)))
+        assert abs(ex[0] - W3) < 1e-13 * W3
+
+
+def test_four_velocity_and_magnetic_invariants():
+    """u^mu u_mu = -1 and b^mu u_mu = 0 (b is orthogonal to u by definition)."""
+    for _ in range(200):
+        adm = random_metric(RNG)
+        prim = random_prim(RNG, gam_of(adm))
+        _, _, _, ex = O.point(prim, 5.0 / 3.0, adm)
+        assert abs(ex[3] + 1.0) < 1e-13
+        assert abs(ex[2]) < 1e-12 * (1.0 + ex[1])
+
+
+def test_balsara4_lorentz_factor_printed_in_paper():
+    g = json.load(open(os.path.join(GOLDEN, "balsara_table.json")))
+    st = g["tests"]["balsara4"]["left"]
+    prim = [st["rho"], *st["v"], 0.1, 10.0, *st["ByBz"]]
+    _, _, _, ex = O.point(prim, g["tests"]["balsara4"]["gamma"])
+    assert abs(ex[0] - g["printed_values"]["balsara4_lorentz_factor"]["value"]) < 5e-3
+
+
+# ------------------------------------------------------------ wave speeds --
+def test_speeds_hydro_velocity_addition():
+    """B = 0, flat, flow along d: lambda = (v +- cs) / (1 +- v cs) (textbook)."""
+    for _ in range(50):
+        gamma = RNG.uniform(1.2, 2.0)
+        rho, P, v = RNG.uniform(0.1, 2), RNG.uniform(0.01, 2), RNG.uniform(-0.95, 0.95)
+        h = 1 + gamma / (gamma - 1) * P / rho
+        cs = math.sqrt(gamma * P / (rho * h))
+        for d in range(3):
+            prim = np.zeros(8)
+            prim[0], prim[4], prim[1 + d] = rho, P, v
+            _, _, lam, _ = O.point(prim, gamma)
+            assert abs(lam[d, 1] - (v + cs) / (1 + v * cs)) < 1e-14
+            assert abs(lam[d, 0] - (v - cs) / (1 - v * cs)) < 1e-14
+
+
+def test_speeds_fluid_at_rest_magnetised():
+    """v = 0: lambda = +- a with a^2 = cs^2 + vA^2 - cs^2 vA^2 (fast speed bound)."""
+    for _ in range(50):
+        gamma = 5.0 / 3.0
+        rho, P = RNG.uniform(0.1, 2), RNG.uniform(0.01, 2)
+        B = RNG.normal(size=3)
+        prim = np.array([rho, 0, 0, 0, P, *B])
+        h = 1 + gamma / (gamma - 1) * P / rho
+        b2 = B @ B
+        cs2 = gamma * P / (rho * h)
+        va2 = b2 / (rho * h + b2)
+        a = math.sqrt(cs2 + va2 - cs2 * va2)
+        _, _, lam, _ = O.point(prim, gamma)
+        np.testing.assert_allclose(lam[:, 1], a, rtol=1e-14)
+        np.testing.assert_allclose(lam[:, 0], -a, rtol=1e-14)
+
+
+def test_speeds_lapse_shift_and_conformal_factor():
+    """gamma_ij = psi^4 delta: lambda = (alpha / psi^2) lambda_flat(psi^2 v) - beta^d."""
+    for _ in range(50):
+        alpha, psi = RNG.uniform(0.3, 1.5), RNG.uniform(0.8, 1.5)
+        beta = RNG.normal(size=3) * 0.3
+        adm = np.array([alpha, *beta, psi ** 4, 0, 0, psi ** 4, 0, psi ** 4])
+        prim = random_prim(RNG, np.eye(3) * psi ** 4, vmax=0.8)
+        flat = prim.copy()
+        flat[1:4] *= psi ** 2                 # orthonormal-frame velocity
+        flat[5:8] *= psi ** 2                 # orthonormal-frame field
+        _, _, lam, _ = O.point(prim, 5.0 / 3.0, adm)
+        _, _, lam0, _ = O.point(flat, 5.0 / 3.0)
+        for d in range(3):
+            np.testing.assert_allclose(lam[d], alpha / psi ** 2 * lam0[d] - beta[d], rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------------- HLLE --
+def test_hlle_equal_states_give_physical_flux():
+    for _ in range(100):
+        adm = random_metric(RNG)
+        prim = random_prim(RNG, gam_of(adm))
+        _, F, _, _ = O.point(prim, 5.0 / 3.0, adm)
+        for d in range(3):
+            Fh, _ = O.hlle(prim, prim, 5.0 / 3.0, d, adm)
+            np.testing.assert_allclose(Fh, F[d], rtol=0, atol=4e-16 * np.max(np.abs(F[d])) * 8)
+
+
+def test_hlle_supersonic_upwinding():
+    """All signal speeds of one sign: the flux is the upwind physical flux."""
+    gamma = 5.0 / 3.0
+    pL = np.array([1.0, 0.9, 0.05, 0.0, 0.05, 0.01, 0.02, 0.0])
+    pR = np.array([0.5, 0.85, -0.02, 0.01, 0.04, 0.01, -0.01, 0.01])
+    FhL, sp = O.hlle(pL, pR, gamma, 0)
+    assert min(sp) > 0
+    _, FL, _, _ = O.point(pL, gamma)
+    np.testing.assert_allclose(FhL, FL[0], rtol=4e-16, atol=0)
+    mL, mR = pL.copy(), pR.copy()
+    mL[1:4] *= -1
+    mR[1:4] *= -1
+    FhR, sp = O.hlle(mL, mR, gamma, 0)
+    assert max(sp) < 0
+    _, FR, _, _ = O.point(mR, gamma)
+    np.testing.assert_allclose(FhR, FR[0], rtol=4e-16, atol=0)
+
+
+def test_hlle_satisfies_jump_conditions_across_outer_waves():
+    """With the HLL state U* from the integral form over the fan [xi-, xi+],
+    F* - F_L = xi- (U* - U_L) and F* - F_R = xi+ (U* - U_R) (Rankine-Hugoniot)."""
+    for _ in range(100):
+        adm = random_metric(RNG)
+        gam = gam_of(adm)
+        pL = random_prim(RNG, gam, vmax=0.6)
+        pR = random_prim(RNG, gam, vmax=0.6)
+        for d in range(3):
+            Fh, sp = O.hlle(pL, pR, 5.0 / 3.0, d, adm)
+            UL, FL, _, _ = O.point(pL, 5.0 / 3.0, adm)
+            UR, FR, _, _ = O.point(pR, 5.0 / 3.0, adm)
+            xm, xp = min(0.0, sp[0], sp[2]), max(0.0, sp[1], sp[3])
+            Us = (xp * UR - xm * UL - (FR[d] - FL[d])) / (xp - xm)
+            sc = np.max(np.abs(FL[d])) + np.max(np.abs(FR[d])) + np.max(np.abs(UL)) + np.max(np.abs(UR))
+            np.testing.assert_allclose(Fh - FL[d], xm * (Us - UL), rtol=0, atol=1e-13 * sc)
+            np.testing.assert_allclose(Fh - FR[d], xp * (Us - UR), rtol=0, atol=1e-13 * sc)
+
+
+# --------------------------------------------------------- reconstruction --
+def test_minmod_reproduces_linear_data_and_flattens_extrema():
+    u = 0.3 + 0.7 * np.arange(20.0)
+    uL, uR = O.reconstruct_1d(O.REC_MINMOD, u)
+    c = np.arange(3, 18)
+    np.testing.assert_allclose(uL[c], 0.3 + 0.7 * (c - 0.5), rtol=1e-15)
+    np.testing.assert_allclose(uR[c], 0.3 + 0.7 * (c - 0.5), rtol=1e-15)
+    u = np.array([0.0, 1, 2, 3, 4, 3, 2, 1, 0, 1])       # maximum at index 4
+    uL, uR = O.reconstruct_1d(O.REC_MINMOD, u)
+    assert uL[5] == 4.0 and uR[4] == 4.0                    # zero slope at the extremum
+    # TVD: face values bounded by neighbouring cell values
+    u = RNG.normal(size=64)
+    uL, uR = O.reconstruct_1d(O.REC_MINMOD, u)
+    for c in range(3, 61):
+        assert min(u[c - 1], u[c]) - 1e-15 <= uL[c] <= max(u[c - 1], u[c]) + 1e-15
+        assert min(u[c - 1], u[c]) - 1e-15 <= uR[c] <= max(u[c - 1], u[c]) + 1e-15
+
+
+def _cell_avg(F, x0, h, n):
+    """Cell averages from an antiderivative F."""
+    e = x0 + h * np.arange(n + 1)
+    return (F(e[1:]) - F(e[:-1])) / h, e
+
+
+def test_weno5_exact_for_quadratic_averages():
+    a, b, c = 0.7, -1.3, 2.1
+    F = lambda x: a * x + b * x ** 2 / 2 + c * x ** 3 / 3
+    p = lambda x: a + b * x + c * x ** 2
+    u, e = _cell_avg(F, -0.4, 0.05, 24)
+    uL, uR = O.reconstruct_1d(O.REC_WENO5, u)
+    for k in range(3, 22):
+        assert abs(uL[k] - p(e[k])) < 1e-13
+        assert abs(uR[k] - p(e[k])) < 1e-13
+
+
+def test_weno5_linear_limit_is_the_fifth_order_upwind_formula():
+    """eps >> beta_k: the weights become (1/10, 6/10, 3/10) and the face value is
+    the textbook fifth-order upwind-biased interpolant (2, -13, 47, 27, -3) / 60."""
+    u = RNG.normal(size=30)
+    uL, uR = O.reconstruct_1d(O.REC_WENO5, u, eps=1e30)
+    for c in range(3, 27):
+        i = c - 1                       # uL at face c-1/2 comes from cell c-1
+        lin = (2 * u[i - 2] - 13 * u[i - 1] + 47 * u[i] + 27 * u[i + 1] - 3 * u[i + 2]) / 60
+        assert abs(uL[c] - lin) < 1e-13
+        i = c                           # uR comes from cell c, mirrored stencil
+        lin = (2 * u[i + 2] - 13 * u[i + 1] + 47 * u[i] + 27 * u[i - 1] - 3 * u[i - 2]) / 60
+        assert abs(uR[c] - lin) < 1e-13
+
+
+def test_weno5_picks_the_smooth_stencil_next_to_a_step():
+    """ENO property: beside a jump the face value comes from the substencil that
+    does not cross it (weights of the others are ~eps^2 / beta^2)."""
+    u = np.where(np.arange(20) >= 10, 1.0, 0.0)
+    uL, uR = O.reconstruct_1d(O.REC_WENO5, u)
+    assert abs(uL[10] - 0.0) < 1e-10       # face 9|10 from cell 9: cells 7, 8, 9 are flat
+    assert abs(uR[10] - 1.0) < 1e-10       # face 9|10 from cell 10: cells 10, 11, 12 are flat
+    assert abs(uL[9] - 0.0) < 1e-10
+    assert abs(uR[11] - 1.0) < 1e-10
+
+
+def test_weno5_fifth_order_on_smooth_monotone_data():
+    errs = []
+    for n in (16, 32, 64):
+        h = 1.0 / n
+        u, e = _cell_avg(np.exp, 0.0, h, n + 6)
+        uL, uR = O.reconstruct_1d(O.REC_WENO5, u)
+        k = np.arange(3, n + 3)
+        errs.append(max(np.max(np.abs(uL[k] - np.exp(e[k]))), np.max(np.abs(uR[k] - np.exp(e[k])))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 4.5, (errs, orders)
+
+
+# ------------------------------------------------------------- con2prim --
+def hydro_inversion_brentq(U, gamma):
+    """B = 0 Gamma-law inversion by scipy's brentq on the pressure (textbook)."""
+    from scipy.optimize import brentq
+    D, S, tau = U[0], np.linalg.norm(U[1:4]), U[4]
+
+    def f(P):
+        v = S / (tau + D + P)
+        W = 1 / math.sqrt(1 - v * v)
+        rho = D / W
+        eps = (tau + D * (1 - W) + P * (1 - W * W)) / (D * W)
+        return (gamma - 1) * rho * eps - P
+
+    lo = max(1e-16, S - tau - D + 1e-15)
+    P = brentq(f, lo, 10 * (tau + D), xtol=1e-18, rtol=1e-15, maxiter=500)
+    v = S / (tau + D + P)
+    return P, D * math.sqrt(1 - v * v), U[1:4] / (tau + D + P)
+
+
+def test_con2prim_hydro_limit_matches_brentq():
+    par = O.make_params()
+    for _ in range(100):
+        prim = random_prim(RNG, np.eye(3), vmax=0.95, bmax=0.0)
+        prim[5:] = 0
+        U, _, _, _ = O.point(prim, par.gamma)
+        out, st = O.con2prim_point(U, par)
+        assert st == 0
+        P, rho, v = hydro_inversion_brentq(U, par.gamma)
+        assert abs(out[4] - P) < 1e-12 * P
+        assert abs(out[0] - rho) < 1e-12 * rho
+        np.testing.assert_allclose(out[1:4], v, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_con2prim_round_trip_and_residual(curved):
+    par = O.make_params()
+    worst = 0.0
+    for _ in range(300):
+        adm = random_metric(RNG) if curved else None
+        gam = gam_of(adm) if curved else np.eye(3)
+        prim = random_prim(RNG, gam, vmax=0.95, bmax=1.5)
+        U, _, _, _ = O.point(prim, par.gamma, adm)
+        out, st = O.con2prim_point(U, par, adm)
+        assert st == 0
+        err = np.max(np.abs(out - prim) / np.maximum(np.abs(prim), 1e-3 * np.max(np.abs(prim))))
+        worst = max(worst, err)
+        U2, _, _, _ = O.point(out, par.gamma, adm)
+        assert np.max(np.abs(U2 - U)) <= 1e-13 * np.max(np.abs(U))
+    assert worst < 1e-11
+
+
+def test_con2prim_balsara_states():
+    """Round trip at every state of the paper's shock-tube table, incl. W ~ 22.4."""
+    g = json.load(open(os.path.join(GOLDEN, "balsara_table.json")))
+    for name, t in g["tests"].items():
+        par = O.make_params(gamma=t["gamma"])
+        for side in ("left", "right"):
+            s = t[side]
+            P = (t["gamma"] - 1) * s["rho"] * s["eps"]
+            prim = np.array([s["rho"], *s["v"], P, t["Bx"], *s["ByBz"]])
+            U, _, _, _ = O.point(prim, t["gamma"])
+            out, st = O.con2prim_point(U, par)
+            assert st == 0, name
+            np.testing.assert_allclose(out, prim, rtol=1e-9, atol=1e-10 * np.max(np.abs(prim)), err_msg=name)
+
+
+def test_con2prim_unphysical_input_sets_atmosphere():
+    par = O.make_params(rho_atm=1e-8)
+    U = np.array([1.0, 0.0, 0.0, 0.0, -2.0, 0.1, 0.0, 0.0])   # tau + D < 0
+    out, st = O.con2prim_point(U, par)
+    assert st == 1 and out[0] == 1e-8 and np.all(out[1:4] == 0) and out[5] == 0.1
+
+
+# --------------------------------------------------------------- the RHS --
+def _block(n, ng=3, L=1.0):
+    return O.Grid((n, n, n), ng, (L / n,) * 3)
+
+
+def _smooth(g, seed=0, vmax=0.5):
+    from paper_2210_17509_gb300 import inputs as I
+    blk = I.Block(g.n, g.ng, g.dx, (0.0, 0.0, 0.0))
+    return I.smooth_prims(blk, seed, vmax=vmax)
+
+
+@pytest.mark.parametrize("recon", [O.REC_MINMOD, O.REC_WENO5])
+def test_rhs_uniform_state_is_exactly_zero(recon):
+    g = _block(8)
+    prim = np.zeros((8,) + g.shape)
+    for q, v in enumerate([1.3, 0.2, -0.4, 0.1, 0.7, 0.3, -0.2, 0.5]):
+        prim[q] = v
+    r = O.rhs(g, O.make_params(recon=recon), prim)
+    assert np.all(r == 0.0)
+
+
+@pytest.mark.parametrize("recon", [O.REC_MINMOD, O.REC_WENO5])
+def test_rhs_periodic_telescoping(recon):
+    g = _block(12)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, _smooth(g))
+    r = O.rhs(g, O.make_params(recon=recon), prim)
+    inn = g.interior()
+    for q in range(8):
+        tot = r[q][inn].sum()
+        assert abs(tot) < 1e-13 * np.abs(r[q][inn]).sum(), q
+
+
+def test_rhs_axis_permutation():
+    """Runs along x, y and z give the same result (Sec. 4.1 does this check)."""
+    g = _block(10)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, _smooth(g, seed=3))
+    par = O.make_params()
+    r = O.rhs(g, par, prim)
+    # swap x <-> y: array axes (z, y, x) -> (z, x, y); components 1<->2, 5<->6
+    perm = [0, 2, 1, 3, 4, 6, 5, 7]
+    pt = np.ascontiguousarray(prim[perm].transpose(0, 1, 3, 2))
+    rt = O.rhs(g, par, pt)
+    back = rt[perm].transpose(0, 1, 3, 2)
+    for q in range(8):
+        assert np.max(np.abs(back[q] - r[q])) <= 1e-14 * np.max(np.abs(r[q])), q
+
+
+def test_rhs_scales_with_constant_lapse():
+    g = _block(8)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, _smooth(g, seed=5))
+    par = O.make_params()
+    met = np.zeros((10,) + g.shape)
+    met[0] = 1.0
+    met[4] = met[7] = met[9] = 1.0
+    r1 = O.rhs(g, par, prim, met)
+    r0 = O.rhs(g, par, prim)
+    np.testing.assert_array_equal(r1, r0)          # explicit flat metric == NULL metric
+    met[0] = 0.5
+    r2 = O.rhs(g, par, prim, met)
+    np.testing.assert_allclose(r2, 0.5 * r1, rtol=0, atol=1e-15 * np.max(np.abs(r1)))
+
+
+def _schwarzschild(g, origin):
+    from paper_2210_17509_gb300 import inputs as I
+    blk = I.Block(g.n, g.ng, g.dx, origin)
+    return I.schwarzschild_metric(blk), blk
+
+
+def _fd4(f, axis, h):
+    return (-np.roll(f, -2, axis) + 8 * np.roll(f, -1, axis) - 8 * np.roll(f, 1, axis) + np.roll(f, 2, axis)) / (12 * h)
+
+
+def test_source_fluid_at_rest_closed_form():
+    """v = B = 0, beta = 0: S_j = sqrt(gamma) (-e d_j alpha + alpha P gamma^ik d_j gamma_ik / 2), S_tau = 0."""
+    g = O.Grid((8, 8, 8), 3, (0.25, 0.25, 0.25))
+    met, _ = _schwarzschild(g, (3.0, 3.5, 4.0))
+    prim = np.zeros((8,) + g.shape)
+    rng = np.random.default_rng(7)
+    prim[0] = rng.uniform(0.5, 1.5, size=g.shape)
+    prim[4] = rng.uniform(0.1, 1.0, size=g.shape)
+    gamma = 5.0 / 3.0
+    par = O.make_params(gamma=gamma)
+    cells = np.array([(i, j, k) for i in (3, 6, 10) for j in (3, 7) for k in (4, 10)])
+    src = O.source_cells(g, par, prim, cells, met)
+    for s, (i, j, k) in enumerate(cells):
+        rho, P = prim[0, k, j, i], prim[4, k, j, i]
+        e = rho + P / (gamma - 1)
+        alpha, psi4 = met[0, k, j, i], met[4, k, j, i]
+        sg = psi4 ** 1.5
+        for d, ax in enumerate((2, 1, 0)):
+            da = _fd4(met[0], ax, g.dx[d])[k, j, i]
+            dp4 = _fd4(met[4], ax, g.dx[d])[k, j, i]
+            expect = sg * (-e * da + alpha * P * 0.5 * 3 * dp4 / psi4)
+            assert abs(src[s, 1 + d] - expect) < 1e-13 * (abs(expect) + 1e-3), (s, d)
+        assert abs(src[s, 4]) < 1e-15 and np.all(src[s, [0, 5, 6, 7]] == 0)
+
+
+def test_source_moving_fluid_matches_3p1_form():
+    """Covariant Eq. 13 == the standard 3+1 form for a static metric with beta = 0, K = 0."""
+    g = O.Grid((6, 6, 6), 3, (0.3, 0.3, 0.3))
+    met, _ = _schwarzschild(g, (3.0, 2.5, 4.0))
+    rng = np.random.default_rng(11)
+    gamma = 5.0 / 3.0
+    par = O.make_params(gamma=gamma)
+    prim = np.zeros((8,) + g.shape)
+    prim[0] = rng.uniform(0.5, 1.5, size=g.shape)
+    prim[4] = rng.uniform(0.1, 1.0, size=g.shape)
+    for q in (1, 2, 3):
+        prim[q] = rng.uniform(-0.15, 0.15, size=g.shape)
+    for q in (5, 6, 7):
+        prim[q] = rng.uniform(-0.5, 0.5, size=g.shape)
+    cells = np.array([(i, j, k) for i in (3, 5, 8) for j in (4, 7) for k in (3, 6)])
+    src = O.source_cells(g, par, prim, cells, met)
+    for s, (i, j, k) in enumerate(cells):
+        alpha, psi4 = met[0, k, j, i], met[4, k, j, i]
+        gam = np.eye(3) * psi4
+        gu = np.eye(3) / psi4
+        sg = psi4 ** 1.5
+        rho, v, P, B = prim[0, k, j, i], prim[1:4, k, j, i], prim[4, k, j, i], prim[5:8, k, j, i]
+        vl = gam @ v
+        W = 1 / math.sqrt(1 - v @ vl)
+        b0 = W * (B @ vl) / alpha
+        bu = B / W + alpha * b0 * v
+        b2 = (B @ gam @ B) / W ** 2 + (alpha * b0) ** 2 / W ** 2
+        h = 1 + gamma / (gamma - 1) * P / rho
+        hs, Ps = rho * h + b2, P + b2 / 2
+        T00 = hs * W ** 2 / alpha ** 2 - Ps / alpha ** 2 - b0 * b0
+        T0i = hs * W ** 2 * v / alpha - b0 * bu
+        Tij = hs * W ** 2 * np.outer(v, v) + Ps * gu - np.outer(bu, bu)
+        da = np.array([_fd4(met[0], ax, g.dx[d])[k, j, i] for d, ax in enumerate((2, 1, 0))])
+        dg = [np.array([[_fd4(met[c], ax, g.dx[d])[k, j, i] for c in r] for r in ((4, 5, 6), (5, 7, 8), (6, 8, 9))])
+              for d, ax in enumerate((2, 1, 0))]
+        for d in range(3):
+            expect = alpha * sg * (-T00 * alpha * da[d] + 0.5 * np.sum(Tij * dg[d]))
+            assert abs(src[s, 1 + d] - expect) < 1e-12 * (abs(expect) + 1e-2)
+        expect_tau = -alpha * sg * (T0i @ da)
+        assert abs(src[s, 4] - expect_tau) < 1e-12 * (abs(expect_tau) + 1e-2)
+
+
+def test_fd4_metric_derivative_converges_fourth_order():
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        g = O.Grid((4, 4, 4), 3, (h, h, h))
+        met, _ = _schwarzschild(g, (3.0, 3.0 - 2 * h, 3.0 + h))
+        prim = np.zeros((8,) + g.shape)
+        prim[0] = 1.0
+        prim[4] = 0.5
+        par = O.make_params()
+        src = O.source_cells(g, par, prim, np.array([[4, 4, 4]]), met)
+        x = 3.0 + (4 - 3 + 0.5) * h
+        y = 3.0 - 2 * h + 1.5 * h
+        z = 3.0 + h + 1.5 * h
+        r = math.sqrt(x * x + y * y + z * z)
+        psi = 1 + 1 / (2 * r)
+        alpha = (1 - 1 / (2 * r)) / psi
+        dpsi = -1 / (2 * r * r) * (x / r)
+        dalpha = (1 / (2 * r * r) * (x / r) * psi - (1 - 1 / (2 * r)) * dpsi) / psi ** 2
+        e = 1.0 + 0.5 / (2 / 3)
+        expect = psi ** 6 * (-e * dalpha + alpha * 0.5 * 0.5 * 3 * 4 * dpsi / psi)
+        errs.append(abs(src[0, 1] - expect))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 3.5, (errs, orders)
+
+
+# -------------------------------------------------------- time evolution --
+def _advection_1d(n, recon, scheme, tfinal, cfl_pow, eps=1e-6, amp=0.2):
+    g = O.Grid((n, 1, 1), 3, (1.0 / n, 1.0 / n, 1.0 / n))
+    par = O.make_params(recon=recon, weno_eps=eps)
+    x = (np.arange(n + 6) - 3) / n
+    v, P = 0.5, 1.0
+    F = lambda t: x_avg(t)
+
+    def x_avg(t):
+        lo, hi = x - v * t, x + 1.0 / n - v * t
+        return 1 + amp * (np.cos(2 * np.pi * lo) - np.cos(2 * np.pi * hi)) / (2 * np.pi / n)
+
+    prim = np.zeros((8,) + g.shape)
+    prim[0] = x_avg(0.0)[None, None, :]
+    prim[1] = v
+    prim[4] = P
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, prim)
+    cons = O.prim2con(g, par.gamma, prim)
+    dt0 = 0.4 * (1.0 / n) ** cfl_pow
+    nsteps = int(math.ceil(tfinal / dt0))
+    dt = tfinal / nsteps
+    for _ in range(nsteps):
+        cons, prim, nf = O.rk_step(g, par, scheme, dt, cons, prim)
+        assert nf == 0
+    exact = x_avg(tfinal)[3:n + 3]
+    return np.mean(np.abs(prim[0, 3, 3, 3:n + 3] - exact))
+
+
+def test_convergence_minmod_second_order():
+    e = [_advection_1d(n, O.REC_MINMOD, O.RK3, 0.4, 1.0) for n in (32, 64, 128)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] >= 1.8, (e, orders)
+
+
+def test_convergence_weno5_linear_weights_fifth_order():
+    """eps large => linear weights: the scheme is fifth order in space; RK3 with dt ~ dx^(5/3)."""
+    e = [_advection_1d(n, O.REC_WENO5, O.RK3, 0.2, 5.0 / 3.0, eps=1e3) for n in (16, 32, 64)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] >= 4.5, (e, orders)
+
+
+def test_convergence_weno5_nonlinear_weights():
+    e = [_advection_1d(n, O.REC_WENO5, O.RK3, 0.2, 5.0 / 3.0) for n in (32, 64, 128)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] >= 4.0, (e, orders)
+
+
+def test_rk_conserves_totals_periodic():
+    g = _block(8)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, _smooth(g, seed=9))
+    par = O.make_params()
+    cons = O.prim2con(g, par.gamma, prim)
+    inn = (slice(None),) + g.interior()
+    tot0 = cons[inn].sum(axis=(1, 2, 3))
+    for scheme in (O.RK2, O.RK3, O.RK4):
+        c2, p2, nf = O.rk_step(g, par, scheme, 0.25 / 8, cons, prim)
+        assert nf == 0
+        tot = c2[inn].sum(axis=(1, 2, 3))
+        scale = np.abs(cons[inn]).sum(axis=(1, 2, 3))
+        assert np.all(np.abs(tot - tot0) <= 1e-14 * scale), scheme
+
+
+def test_balsara1_peak_lorentz_factor_printed_in_paper():
+    """Balsara 1 with the paper's setup at 400 points: peak W ~ 1.458 at t = 0.4."""
+    gold = json.load(open(os.path.join(GOLDEN, "balsara_table.json")))
+    t = gold["tests"]["balsara1"]
+    n = 400
+    g = O.Grid((n, 1, 1), 3, (1.0 / n,) * 3)
+    par = O.make_params(gamma=t["gamma"], recon=O.REC_MINMOD, bc=O.BC_COPY)
+    x = -0.5 + (np.arange(n + 6) - 3 + 0.5) / n
+    prim = np.zeros((8,) + g.shape)
+    for q, key in ((0, "rho"),):
+        pass
+    L = x < 0
+    for side, mask in (("left", L), ("right", ~L)):
+        s = t[side]
+        prim[0][..., mask] = s["rho"]
+        prim[4][..., mask] = (t["gamma"] - 1) * s["rho"] * s["eps"]
+        prim[5][..., mask] = t["Bx"]
+        prim[6][..., mask] = s["ByBz"][0]
+        prim[7][..., mask] = s["ByBz"][1]
+    prim = O.fill_ghosts(g, O.BC_COPY, prim)
+    cons = O.prim2con(g, t["gamma"], prim)
+    dt = 0.8 / n
+    for _ in range(int(round(t["t_ref"] / dt))):
+        cons, prim, nf = O.rk_step(g, par, O.RK4, dt, cons, prim)
+        assert nf == 0
+    v2 = prim[1] ** 2 + prim[2] ** 2 + prim[3] ** 2
+    W = 1 / np.sqrt(1 - v2)
+    assert abs(W.max() - gold["printed_values"]["balsara1_peak_lorentz_factor"]["value"]) < 5e-3
+
+
+def test_dual_number_gradient_matches_central_differences():
+    """Forward-mode derivative of the end-state functional vs central differences."""
+    g = _block(6)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, _smooth(g, seed=2))
+    par = O.make_params()
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=prim.shape) * 1e-2
+    d[4] *= 0.1
+    dt = 0.25 / 6
+    L, dL, nf = O.loss_jvp(g, par, O.RK3, dt, 2, prim, d, 0.3)
+    assert nf == 0
+    h = 1e-5
+    par_p = O.make_params(gamma=par.gamma + 0.3 * h)
+    par_m = O.make_params(gamma=par.gamma - 0.3 * h)
+    Lp, _, _ = O.loss_jvp(g, par_p, O.RK3, dt, 2, prim + h * d)
+    Lm, _, _ = O.loss_jvp(g, par_m, O.RK3, dt, 2, prim - h * d)
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(fd - dL) < 1e-7 * abs(dL)
