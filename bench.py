@@ -1,0 +1,373 @@
+"""Benchmark of the GRMHD method-of-lines hot path on GB300.
+
+One step = one full SSP-RK3 step of the 128^3 + 3-ghost Schwarzschild block
+(WENO5, HLLE, copy boundaries, CFL 0.25): three stages of fused RHS +
+stage update, con2prim and ghost fill.  Metric: zone-cycles/s =
+steps * interior cells / time (the paper's definition, Sec. 5).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grmhd|reference]
+
+Under torchrun each rank runs an independent replica of the block (the
+method shards by blocks with no collective on this path); the reported value
+is the sum over ranks of the work divided by the slowest rank's time.
+`--impl reference` times the CPU oracle (the only other implementation of
+the method) on a bounded sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2210_17509_gb300 import inputs as I  # noqa: E402
+
+METRIC = "GRMHD zone-cycles/s (RHS+con2prim) FP64 vs mixed; adjoint/forward cost ratio"
+UNIT = "zone-cycles/s"
+N_CELLS_SIDE = 128
+CFL = 0.25
+PAPER_V100_SETUPA = 0.47e8   # zone-cycles/s, 240^3, RK2, one V100 (Sec. 5.1) -- context only
+
+
+def workload_config(n=N_CELLS_SIDE):
+    return {
+        "workload": f"schwarzschild-block-{n}^3+3ghost-weno5-hlle-ssprk3",
+        "block": [n, n, n], "ghosts": 3, "spacetime": "Schwarzschild isotropic M=1, block [4,12]^3",
+        "recon": "WENO5", "riemann": "HLLE", "integrator": "SSP-RK3", "cfl": CFL, "bc": "copy",
+        "gamma": I.GAMMA, "l2": "inputs larger than L2 (prim+cons+metric ~ 500 MB per block)",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.lines = []
+        self.uuid = device_uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+# --------------------------------------------------------------- reference --
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    nthreads = os.cpu_count() or 1
+    O.set_threads(nthreads)
+    blk, prim, met = I.smooth_schwarzschild(N_CELLS_SIDE, seed=1)
+    # bounded sample: a 24^3 sub-block (cells [52, 76)^3 of the full block, with ghosts)
+    sub = 24
+    lo = 52
+    sl = (slice(None),) + tuple(slice(lo, lo + sub + 6) for _ in range(3))
+    sblk = I.Block((sub,) * 3, 3, blk.dx, tuple(blk.origin[d] + (lo - 3 + 3) * blk.dx[d] for d in range(3)))
+    sprim = np.ascontiguousarray(prim[sl])
+    smet = np.ascontiguousarray(met[sl])
+    g = O.Grid(sblk.n, 3, sblk.dx)
+    par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY)
+    sprim = O.fill_ghosts(g, O.BC_COPY, sprim)
+    cons = O.prim2con(g, par.gamma, sprim, smet)
+    dt = CFL * min(sblk.dx)
+    for _ in range(max(args.warmup, 0)):
+        cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)
+    t = time.perf_counter() - t0
+    value = args.steps * sblk.ncells / t
+    sample = (f"{args.steps} SSP-RK3 steps of a {sub}^3 sub-block of the {N_CELLS_SIDE}^3 Schwarzschild "
+              f"workload (same cells, metric, WENO5/HLLE/copy BC), oracle with {nthreads} OpenMP threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(seconds_target=15.0):
+    """Oracle throughput on a bounded sample (about 10-30 s of CPU work)."""
+    import oracle as O
+    O.build()
+    nthreads = os.cpu_count() or 1
+    O.set_threads(nthreads)
+    blk, prim, met = I.smooth_schwarzschild(N_CELLS_SIDE, seed=1)
+    sub, lo = 48, 40
+    sl = (slice(None),) + tuple(slice(lo, lo + sub + 6) for _ in range(3))
+    sblk = I.Block((sub,) * 3, 3, blk.dx, blk.origin)
+    sprim = np.ascontiguousarray(prim[sl])
+    smet = np.ascontiguousarray(met[sl])
+    g = O.Grid(sblk.n, 3, sblk.dx)
+    par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY)
+    sprim = O.fill_ghosts(g, O.BC_COPY, sprim)
+    cons = O.prim2con(g, par.gamma, sprim, smet)
+    dt = CFL * min(sblk.dx)
+    cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)     # warm-up
+    steps, t = 0, 0.0
+    t0 = time.perf_counter()
+    while t < seconds_target and steps < 100:
+        cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)
+        steps += 1
+        t = time.perf_counter() - t0
+    return {
+        "value": steps * sblk.ncells / t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+        "sample": f"{steps} SSP-RK3 steps of a {sub}^3 sub-block of the same Schwarzschild workload "
+                  f"({t:.1f} s of CPU work, {nthreads} OpenMP threads)",
+    }
+
+
+# ------------------------------------------------------------------- GPU --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
+    ap.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2210_17509_gb300 import grmhd as G
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    blk, prim_h, met_h = I.smooth_schwarzschild(args.n, seed=1 + rank)
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    dt = CFL * min(blk.dx)
+    met = torch.from_numpy(met_h).cuda()
+    stream = torch.cuda.current_stream()
+
+    def setup(precision):
+        p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision)
+        prim = torch.from_numpy(prim_h).cuda()
+        G.fill_ghosts(g, G.BC_COPY, prim)
+        cons = G.prim2con(g, p, prim, met)
+        ws = G.workspace(g, G.RK3)
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        return p, prim, cons, ws, nfail
+
+    def timed(precision, steps, warmup):
+        p, prim, cons, ws, nfail = setup(precision)
+        for _ in range(warmup):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, int(nfail.item())
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    # FP64 (headline) -- clocks sampled during this timed region
+    p64, prim, cons, ws, nfail = setup(G.FP64)
+    for _ in range(args.warmup):
+        G.rk_step(g, p64, G.RK3, dt, cons, prim, met, None, ws, nfail)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        G.rk_step(g, p64, G.RK3, dt, cons, prim, met, None, ws, nfail)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms64 = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms64 = float(t.item())
+    nfail64 = int(nfail.item())
+    ncells = blk.ncells
+    value64 = world * ncells * args.steps / (ms64 * 1e-3)
+
+    # mixed precision path
+    msmx, nfailmx = timed(G.MIXED, args.steps, args.warmup)
+    value_mx = world * ncells * args.steps / (msmx * 1e-3)
+
+    # dominant kernel: the fused FP64 RHS, timed live with events on its stream
+    p, prim_k, cons_k, _, _ = setup(G.FP64)
+    rhs_out = torch.empty_like(prim_k)
+    for _ in range(3):
+        G.rhs(g, p, prim_k, met, None, rhs_out)
+    nk = max(5, args.steps)
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(nk):
+        G.rhs(g, p, prim_k, met, None, rhs_out)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    rhs_ms = k0.elapsed_time(k1) / nk
+    from paper_2210_17509_gb300 import roofline as R
+    roof = R.rhs_fp64_roofline(ncells, rhs_ms)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        p, prim_d, cons_d, ws_e, nfail_e = setup(G.FP64)
+        cons_h = cons_d.cpu().pin_memory()
+        prim_h2 = prim_d.cpu().pin_memory()
+        met_hp = met.cpu().pin_memory()
+        out_c = torch.empty_like(cons_h).pin_memory()
+        out_p = torch.empty_like(prim_h2).pin_memory()
+        met_d = torch.empty_like(met)
+        steps_e = max(3, args.steps // 2)
+
+        def e2e_step():
+            cons_d.copy_(cons_h, non_blocking=True)
+            prim_d.copy_(prim_h2, non_blocking=True)
+            met_d.copy_(met_hp, non_blocking=True)
+            G.rk_step(g, p, G.RK3, dt, cons_d, prim_d, met_d, None, ws_e, nfail_e)
+            out_c.copy_(cons_d, non_blocking=True)
+            out_p.copy_(prim_d, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(steps_e):
+            e2e_step()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = q0.elapsed_time(q1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = cons_h.numel() * 8 + prim_h2.numel() * 8 + met_hp.numel() * 8
+        d2h = out_c.numel() * 8 + out_p.numel() * 8
+        e2e = {"value": world * ncells * steps_e / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "dtype": "f64"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_sample()
+    line = {
+        "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.n),
+        "mixed": {"value": value_mx, "unit": UNIT, "ms_per_step": msmx / args.steps,
+                  "dtype": "f32 reconstruct/HLLE/divergence + f64 con2prim/metric",
+                  "speedup_vs_fp64": value_mx / value64, "failed_cells": nfailmx},
+        "failed_cells": nfail64,
+        "gpu_launches": args.steps * 9,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
+                    "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * grmhd.h -- C ABI of the GB300 GRMHD method-of-lines library (libgrmhd.so).
+ *
+ * The library evaluates the Valencia-formulation GRMHD right-hand side of
+ * GRaM-X (arXiv 2210.17509), Sec. 2.2-2.3, on one 3D Cartesian block with
+ * ghost zones, plus the pieces a method-of-lines step needs around it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array pointers are DEVICE pointers (cudaMalloc / torch CUDA memory)
+ *    unless the argument says "host".  The caller owns every buffer; the
+ *    library never allocates, frees or retains memory.
+ *  - Layout: structure of arrays, double precision, [var][z][y][x] with x
+ *    fastest.  Every field spans the full block including ghosts:
+ *    N_d = n_d + 2 ng points per axis, ncell = N_x N_y N_z, component q of a
+ *    field starts at element q * ncell.
+ *      prim   8 comps  [rho, v^x, v^y, v^z, P, B^x, B^y, B^z]
+ *             v^i is the Valencia 3-velocity (Eq. 10), B^i the Eulerian field
+ *             (undensitised).  Pressure replaces the paper's eps as the
+ *             thermal variable: eps = P / ((Gamma - 1) rho) (Gamma-law EOS).
+ *      cons   8 comps  [D, S_x, S_y, S_z, tau, B~^x, B~^y, B~^z]  (Eqs. 6-9)
+ *      metric 10 comps [alpha, beta^x, beta^y, beta^z,
+ *                       g_xx, g_xy, g_xz, g_yy, g_yz, g_zz] at cell centres,
+ *             ghosts included.  NULL means Minkowski (alpha = 1, beta = 0,
+ *             gamma_ij = delta_ij); the kernels then take a flat fast path.
+ *      kij    6 comps  [K_xx, K_xy, K_xz, K_yy, K_yz, K_zz]; NULL means 0.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  No call synchronises the device.
+ *  - Return value: GRMHD_OK, or a negative error code.  Argument errors are
+ *    detected on the host before anything is launched.  Per-cell physics
+ *    failures of the primitive recovery are NOT return codes: they go to the
+ *    optional `status` array and `nfail` counter.
+ *  - Buffers passed to one call must not overlap unless stated otherwise.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRMHD_OK 0
+#define GRMHD_ERR_ARG (-1)     /* invalid argument (NULL, extent, ghost width, alignment, size) */
+#define GRMHD_ERR_CUDA (-2)    /* a CUDA runtime call or launch failed */
+#define GRMHD_ERR_TIMEOUT (-3) /* a bounded device-side wait gave up */
+#define GRMHD_ERR_SIZE (-4)    /* workspace too small */
+
+/* reconstruction (Sec. 2.3: TVD with minmod limiter, or WENO5 after Shu 1998) */
+#define GRMHD_MINMOD 0
+#define GRMHD_WENO5 1
+/* boundary condition applied to primitive ghost zones: periodic, or a copy of
+ * the nearest interior cell (the "von Neumann" condition of Sec. 4.1) */
+#define GRMHD_BC_PERIODIC 0
+#define GRMHD_BC_COPY 1
+/* arithmetic of the RHS: all FP64, or FP32 reconstruction / Riemann flux /
+ * divergence with FP64 primitive recovery, sqrt(gamma) and metric inverse */
+#define GRMHD_FP64 0
+#define GRMHD_MIXED 1
+/* method-of-lines integrators: SSP Heun, SSP Shu-Osher RK3, classical RK4 */
+#define GRMHD_RK2 2
+#define GRMHD_RK3 3
+#define GRMHD_RK4 4
+
+/* Block geometry.  n = interior cells per axis (x, y, z); ng = ghost width
+ * (>= 3 for WENO5 and for a curved metric, >= 2 for minmod on a flat
+ * metric); dx = cell size per axis. */
+typedef struct {
+  int32_t n[3];
+  int32_t ng;
+  double dx[3];
+} grmhd_grid;
+
+/* Method parameters. */
+typedef struct {
+  double gamma;      /* Gamma-law index, P = (Gamma - 1) rho eps (Sec. 2.3); 1 < gamma <= 3 */
+  int32_t recon;     /* GRMHD_MINMOD | GRMHD_WENO5 */
+  int32_t bc;        /* GRMHD_BC_PERIODIC | GRMHD_BC_COPY */
+  int32_t precision; /* GRMHD_FP64 | GRMHD_MIXED */
+  int32_t nr_maxit;  /* Newton iteration cap of the primitive recovery (e.g. 50) */
+  double rho_atm;    /* atmosphere density (Sec. 4.4 uses an artificial atmosphere) */
+  double p_atm;      /* atmosphere pressure */
+  double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
+  double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
+} grmhd_params;
+
+/* Primitive -> conserved variables, Eqs. 6-9 (Sec. 2.2), on every cell of
+ * the block (ghosts included), with the metric of that cell.
+ *   prim   in   8 x ncell
+ *   metric in   10 x ncell or NULL
+ *   cons   out  8 x ncell */
+int grmhd_prim2con(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                   const double* metric, double* cons, void* stream);
+
+/* Conserved -> primitive recovery (Sec. 2.3, "Find the primitive variable
+ * vector"): per interior cell, a 2D Newton-Raphson in (z = rho h W^2, W)
+ * (the paper's 3D Newton with the temperature eliminated by the Gamma-law),
+ * falling back to bracketed bisection in z; cells that still fail or come out
+ * unphysical (no root, NaN, rho < rho_atm, v >= 1) get the atmosphere
+ * (rho_atm, v = 0, p_atm, B kept); a valid root with P <= 0 keeps rho and v
+ * and gets the pressure floor P = p_atm (Sec. 2.3 lists these failure modes).
+ *   cons   in      8 x ncell (interior read)
+ *   metric in      10 x ncell or NULL
+ *   prim   in/out  8 x ncell: interior holds the initial guess on entry and
+ *                  the result on exit; ghost entries are not touched
+ *   status out     int8 x ncell or NULL: 0 Newton, 1 bisection fallback,
+ *                  2 atmosphere, 3 pressure floor (interior entries only)
+ *   nfail  in/out  one device int32 or NULL: atomically incremented by the
+ *                  number of atmosphere and pressure-floor cells (caller
+ *                  zeroes it) */
+int grmhd_con2prim(const grmhd_grid* grid, const grmhd_params* params, const double* cons,
+                   const double* metric, double* prim, int8_t* status, int32_t* nfail,
+                   void* stream);
+
+/* Ghost-zone fill of an nvar-component field from its interior: periodic
+ * wrap or copy of the nearest interior cell (Sec. 4.1 boundary; Sec. 5 runs
+ * are periodic).  Edges and corners are filled consistently. */
+int grmhd_fill_ghosts(const grmhd_grid* grid, int32_t bc, int32_t nvar, double* field, void* stream);
+
+/* Method-of-lines right-hand side dU/dt = -d_i F^i + S (Eq. 11): reconstruct
+ * the primitives to faces (minmod or WENO5), metric at faces as the mean of
+ * the two adjacent cells (a face state with rho <= 0, P <= 0 or v >= 1 is
+ * replaced by its cell's state), HLLE fluxes (Eq. 12), flux divergence, source
+ * terms (Eq. 13, 3+1 form, metric derivatives by 4th-order centred
+ * differences).  Each face flux is computed once per launch tile.
+ *   prim   in   8 x ncell, ghosts filled
+ *   metric in   10 x ncell or NULL
+ *   kij    in   6 x ncell or NULL
+ *   rhs    out  8 x ncell; interior written, ghost entries not touched */
+int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+              const double* metric, const double* kij, double* rhs, void* stream);
+
+/* Bytes of device workspace grmhd_rk_step needs for `scheme`. */
+size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
+
+/* One method-of-lines step of size dt (Sec. 2.3; integrators RK2/RK4 as in
+ * Secs. 4-5, and SSP RK3).  Every stage evaluates the RHS from the current
+ * primitives and folds the stage combination into the RHS epilogue, then
+ * recovers primitives (con2prim) and fills their ghosts.
+ *   cons   in/out  8 x ncell: U^n on entry (interior), U^{n+1} on exit
+ *   prim   in/out  8 x ncell: on entry consistent with cons, ghosts filled;
+ *                  on exit the primitives of U^{n+1}, ghosts filled
+ *   metric, kij    as for grmhd_rhs
+ *   ws             device workspace of ws_bytes >= grmhd_rk_workspace_bytes()
+ *                  (256-byte aligned), contents scratch
+ *   nfail          as for grmhd_con2prim (summed over the stages) or NULL */
+int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                  double* cons, double* prim, const double* metric, const double* kij, void* ws,
+                  size_t ws_bytes, int32_t* nfail, void* stream);
+
+/* Human-readable name of a return code (static storage). */
+const char* grmhd_error_string(int code);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int grmhd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRMHD_H */

@@ -39,7 +39,13 @@
 //   R8 Gamma-law EOS P = (Gamma - 1) rho eps (Sec. 2.3);
 //   R9 boundary: periodic, or copy of the nearest interior primitive;
 //   R10 RK2 = SSP Heun, RK3 = SSP Shu-Osher, RK4 = classical; every stage is
-//      con2prim -> ghost fill -> RHS (the RHS recipe of Sec. 2.3).
+//      con2prim -> ghost fill -> RHS (the RHS recipe of Sec. 2.3);
+//   R11 a reconstructed face state with rho <= 0, P <= 0 or v^2 >= 1 (one of
+//      the unphysical outcomes Sec. 2.3 lists for the recovery) is replaced
+//      by the primitive state of the cell it was reconstructed from;
+//   R12 recovery failures (Sec. 2.3 lists them): no root, NaN, rho < rho_atm
+//      or v >= 1 -> atmosphere (rho_atm, v = 0, p_atm, B kept); a root with
+//      P <= 0 but valid rho and v -> pressure floor P = p_atm.
 
 #include <algorithm>
 #include <cmath>
@@ -419,10 +425,22 @@ void face_flux(const Grid& G, const Par<S>& p, const S* prim, const double* metr
     reconstruct_face(p.recon, p.weno_eps, u, pL[q], pR[q]);
   }
   off[d] = -1;
+  const long cm = G.at(i + off[0], j + off[1], k + off[2]), cp = G.at(i, j, k);
   S a0[10], a1[10], adm[10];
-  load_adm(G, metric, G.at(i + off[0], j + off[1], k + off[2]), a0);
-  load_adm(G, metric, G.at(i, j, k), a1);
+  load_adm(G, metric, cm, a0);
+  load_adm(G, metric, cp, a1);
   for (int q = 0; q < 10; ++q) adm[q] = 0.5 * (a0[q] + a1[q]);
+  // Reading R11: unphysical face states fall back to their cell's state.
+  auto physical = [&](const S pr[8]) {
+    double v2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) v2 += val(adm[SYM[a][b]]) * val(pr[1 + a]) * val(pr[1 + b]);
+    return val(pr[0]) > 0.0 && val(pr[4]) > 0.0 && v2 < 1.0;
+  };
+  if (!physical(pL))
+    for (int q = 0; q < 8; ++q) pL[q] = prim[q * G.ncell + cm];
+  if (!physical(pR))
+    for (int q = 0; q < 8; ++q) pR[q] = prim[q * G.ncell + cp];
   FaceOut<S> fo;
   hlle(pL, pR, adm, p.gamma, d, fo);
   for (int q = 0; q < 8; ++q) F[q] = fo.F[q];
@@ -655,7 +673,8 @@ S c2p_f(const C2P<S>& in, const S& z) {
   return in.tau + in.D - z - in.B2 + 0.5 * in.B2 * iw * iw + 0.5 * in.BS * in.BS / (z * z) + press;
 }
 
-// Returns status 0 on success, 1 if the atmosphere was imposed.
+// Returns status 0 on success, 1 if the atmosphere was imposed, 2 if the
+// pressure floor was applied.
 template <class S>
 int con2prim_cell(const S U[8], const double adm[10], const Par<S>& p, S out[8]) {
   Spacetime<double> st;
@@ -721,8 +740,10 @@ int con2prim_cell(const S U[8], const double adm[10], const Par<S>& p, S out[8])
   const S iw = sqrt(S(1.0) - v2);
   const S rho = in.D * iw;
   const S press = (in.gamma - 1.0) / in.gamma * (z * iw * iw - rho);
-  if (!(val(rho) >= p.rho_atm) || !(val(press) > 0.0) || !(val(v2) < 1.0) || !std::isfinite(val(press)))
-    return atmosphere();
+  if (!(val(rho) >= p.rho_atm) || !(val(v2) < 1.0) || !std::isfinite(val(press))) return atmosphere();
+  int status = 0;
+  S pout = press;
+  if (!(val(press) > 0.0)) { pout = S(p.p_atm); status = 2; }  // reading R12: pressure floor
   S vl[3];
   // v_i = (S_i + (B.S / z) B_i) / (z + B^2) with B_i = gamma_ij B^j
   for (int i = 0; i < 3; ++i) {
@@ -736,9 +757,9 @@ int con2prim_cell(const S U[8], const double adm[10], const Par<S>& p, S out[8])
     for (int j = 0; j < 3; ++j) t += gu3[i][j] * vl[j];
     out[1 + i] = t;
   }
-  out[4] = press;
+  out[4] = pout;
   for (int i = 0; i < 3; ++i) out[5 + i] = B[i];
-  return 0;
+  return status;
 }
 
 template <class S>
@@ -757,7 +778,7 @@ int con2prim_block(const Grid& G, const Par<S>& p, const S* cons, const double* 
         const int st = con2prim_cell(U, adm, p, P);
         for (int q = 0; q < 8; ++q) prim[q * G.ncell + c] = P[q];
         if (status) status[c] = (int8_t)st;
-        nfail += st;
+        nfail += (st != 0);
       }
   return nfail;
 }

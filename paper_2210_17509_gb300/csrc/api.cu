@@ -1,0 +1,235 @@
+// C ABI of libgrmhd: argument validation and orchestration of the kernels.
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace grmhd {
+
+DevGrid make_grid(const grmhd_grid& g) {
+  DevGrid d;
+  for (int i = 0; i < 3; ++i) {
+    d.n[i] = g.n[i];
+    d.N[i] = g.n[i] + 2 * g.ng;
+    d.dx[i] = g.dx[i];
+    d.idx[i] = 1.0 / g.dx[i];
+  }
+  d.ng = g.ng;
+  d.sy = d.N[0];
+  d.sz = (long long)d.N[0] * d.N[1];
+  d.ncell = d.sz * d.N[2];
+  return d;
+}
+
+DevParams make_params(const grmhd_params& p) {
+  DevParams d;
+  d.gamma = p.gamma;
+  d.gfac = p.gamma / (p.gamma - 1.0);
+  d.gm1g = (p.gamma - 1.0) / p.gamma;
+  d.rho_atm = p.rho_atm;
+  d.p_atm = p.p_atm;
+  d.nr_tol = p.nr_tol;
+  d.weno_eps = p.weno_eps;
+  d.nr_maxit = p.nr_maxit;
+  d.recon = p.recon;
+  d.bc = p.bc;
+  d.precision = p.precision;
+  return d;
+}
+
+}  // namespace grmhd
+
+using namespace grmhd;
+
+namespace {
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+int check_grid(const grmhd_grid* g, int min_ng) {
+  if (!g) return GRMHD_ERR_ARG;
+  if (g->ng < min_ng || g->ng > 16) return GRMHD_ERR_ARG;
+  long long cells = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 1 || g->n[d] > (1 << 20)) return GRMHD_ERR_ARG;
+    if (!(g->dx[d] > 0.0) || !std::isfinite(g->dx[d])) return GRMHD_ERR_ARG;
+    cells *= (long long)(g->n[d] + 2 * g->ng);
+    if (cells > (1LL << 40)) return GRMHD_ERR_ARG;
+  }
+  return GRMHD_OK;
+}
+
+int check_params(const grmhd_params* p) {
+  if (!p) return GRMHD_ERR_ARG;
+  if (!(p->gamma > 1.0 && p->gamma <= 3.0)) return GRMHD_ERR_ARG;
+  if (p->recon != GRMHD_MINMOD && p->recon != GRMHD_WENO5) return GRMHD_ERR_ARG;
+  if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+  if (p->precision != GRMHD_FP64 && p->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
+  if (p->nr_maxit < 1 || p->nr_maxit > 1000) return GRMHD_ERR_ARG;
+  if (!(p->nr_tol > 0.0 && p->nr_tol < 1.0)) return GRMHD_ERR_ARG;
+  if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
+  if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
+  return GRMHD_OK;
+}
+
+// Ghost width the stencils need: WENO5 reads 3 cells, minmod 2, the metric
+// derivatives 2.
+int min_ghosts(const grmhd_params* p, const double* metric) {
+  int m = (p->recon == GRMHD_WENO5) ? 3 : 2;
+  if (metric && m < 2) m = 2;
+  return m;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+cudaError_t launch_rhs(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                       const double* kij, const StageEpilogue& ep, cudaStream_t s) {
+  if (p.precision == GRMHD_MIXED) return launch_rhs_mixed(g, p, prim, metric, kij, ep, s);
+  return launch_rhs_fp64(g, p, prim, metric, kij, ep, s);
+}
+
+StageEpilogue no_epilogue() {
+  StageEpilogue e;
+  e.rhs = nullptr;
+  e.u = nullptr;
+  e.u0 = nullptr;
+  e.acc_in = nullptr;
+  e.acc_out = nullptr;
+  e.c0 = e.c1 = e.cr = e.ca = e.wa = e.wr = 0.0;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grmhd_version(void) { return 100; }
+
+const char* grmhd_error_string(int code) {
+  switch (code) {
+    case GRMHD_OK: return "ok";
+    case GRMHD_ERR_ARG: return "invalid argument";
+    case GRMHD_ERR_CUDA: return "CUDA error";
+    case GRMHD_ERR_TIMEOUT: return "device wait timed out";
+    case GRMHD_ERR_SIZE: return "workspace too small";
+    default: return "unknown error";
+  }
+}
+
+int grmhd_prim2con(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+                   double* cons, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, 0))) return e;
+  if (!prim || !cons || !aligned8(prim) || !aligned8(cons) || (metric && !aligned8(metric)))
+    return GRMHD_ERR_ARG;
+  return cuda_status(launch_prim2con(make_grid(*grid), make_params(*params), prim, metric, cons,
+                                     (cudaStream_t)stream));
+}
+
+int grmhd_con2prim(const grmhd_grid* grid, const grmhd_params* params, const double* cons, const double* metric,
+                   double* prim, int8_t* status, int32_t* nfail, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, 0))) return e;
+  if (!prim || !cons || !aligned8(prim) || !aligned8(cons) || (metric && !aligned8(metric))) return GRMHD_ERR_ARG;
+  if (nfail && (reinterpret_cast<uintptr_t>(nfail) & 3u)) return GRMHD_ERR_ARG;
+  return cuda_status(launch_con2prim(make_grid(*grid), make_params(*params), cons, metric, prim, status, nfail,
+                                     (cudaStream_t)stream));
+}
+
+int grmhd_fill_ghosts(const grmhd_grid* grid, int32_t bc, int32_t nvar, double* field, void* stream) {
+  int e = check_grid(grid, 0);
+  if (e) return e;
+  if (bc != GRMHD_BC_PERIODIC && bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+  if (nvar < 1 || nvar > 64 || !field || !aligned8(field)) return GRMHD_ERR_ARG;
+  return cuda_status(launch_fill_ghosts(make_grid(*grid), bc, nvar, field, (cudaStream_t)stream));
+}
+
+int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+              const double* kij, double* rhs, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
+  if (!prim || !rhs || !aligned8(prim) || !aligned8(rhs)) return GRMHD_ERR_ARG;
+  if ((metric && !aligned8(metric)) || (kij && !aligned8(kij))) return GRMHD_ERR_ARG;
+  if (kij && !metric) return GRMHD_ERR_ARG;
+  StageEpilogue ep = no_epilogue();
+  ep.rhs = rhs;
+  return cuda_status(launch_rhs(make_grid(*grid), make_params(*params), prim, metric, kij, ep,
+                                (cudaStream_t)stream));
+}
+
+size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
+  if (check_grid(grid, 0)) return 0;
+  if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3 && scheme != GRMHD_RK4) return 0;
+  const DevGrid g = make_grid(*grid);
+  const size_t field = round256((size_t)8 * g.ncell * sizeof(double));
+  return scheme == GRMHD_RK4 ? 2 * field : field;
+}
+
+int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
+                  double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes,
+                  int32_t* nfail, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
+  if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3 && scheme != GRMHD_RK4) return GRMHD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return GRMHD_ERR_ARG;
+  if (!cons || !prim || !ws || !aligned8(cons) || !aligned8(prim)) return GRMHD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  if ((metric && !aligned8(metric)) || (kij && !aligned8(kij)) || (kij && !metric)) return GRMHD_ERR_ARG;
+  if (nfail && (reinterpret_cast<uintptr_t>(nfail) & 3u)) return GRMHD_ERR_ARG;
+  if (ws_bytes < grmhd_rk_workspace_bytes(grid, scheme)) return GRMHD_ERR_SIZE;
+
+  const DevGrid g = make_grid(*grid);
+  const DevParams p = make_params(*params);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t field = round256((size_t)8 * g.ncell * sizeof(double));
+  double* u0 = static_cast<double*>(ws);
+  double* acc = scheme == GRMHD_RK4 ? reinterpret_cast<double*>(static_cast<char*>(ws) + field) : nullptr;
+
+  cudaError_t ce = cudaMemcpyAsync(u0, cons, (size_t)8 * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (ce != cudaSuccess) return GRMHD_ERR_CUDA;
+
+  // Stage coefficients: u <- c0 u0 + c1 u + cr L (+ ca acc); acc <- wa acc + wr L.
+  struct Stage { double c0, c1, cr, ca, wa, wr; bool acc_in, acc_out; };
+  Stage st[4];
+  int ns = 0;
+  if (scheme == GRMHD_RK2) {
+    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
+    st[1] = {0.5, 0.5, 0.5 * dt, 0, 0, 0, false, false};
+    ns = 2;
+  } else if (scheme == GRMHD_RK3) {
+    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
+    st[1] = {0.75, 0.25, 0.25 * dt, 0, 0, 0, false, false};
+    st[2] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, 0, 0, 0, false, false};
+    ns = 3;
+  } else {
+    st[0] = {1.0, 0.0, 0.5 * dt, 0, 0, 1.0, false, true};
+    st[1] = {1.0, 0.0, 0.5 * dt, 0, 1.0, 2.0, true, true};
+    st[2] = {1.0, 0.0, dt, 0, 1.0, 2.0, true, true};
+    st[3] = {1.0, 0.0, dt / 6.0, dt / 6.0, 0, 0, true, false};
+    ns = 4;
+  }
+  for (int k = 0; k < ns; ++k) {
+    StageEpilogue ep = no_epilogue();
+    ep.u = cons;
+    ep.u0 = u0;
+    ep.acc_in = st[k].acc_in ? acc : nullptr;
+    ep.acc_out = st[k].acc_out ? acc : nullptr;
+    ep.c0 = st[k].c0;
+    ep.c1 = st[k].c1;
+    ep.cr = st[k].cr;
+    ep.ca = st[k].ca;
+    ep.wa = st[k].wa;
+    ep.wr = st[k].wr;
+    if ((ce = launch_rhs(g, p, prim, metric, kij, ep, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if ((ce = launch_con2prim(g, p, cons, metric, prim, nullptr, nfail, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if ((ce = launch_fill_ghosts(g, p.bc, 8, prim, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+  }
+  return GRMHD_OK;
+}
+
+}  // extern "C"

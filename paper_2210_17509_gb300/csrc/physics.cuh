@@ -1,0 +1,237 @@
+// Device physics of the Valencia GRMHD RHS in 3+1 component form, templated
+// on the compute type T (double for the FP64 path, float for the mixed path).
+//
+// Formulas (GRaM-X, arXiv 2210.17509, Sec. 2.2):
+//   prim -> cons, Eqs. 6-9, with b^0 = W B^i v_i / alpha and
+//   b_i = B_i / W + alpha b^0 v_i (the spatial projection of b^mu = u_nu *F^{mu nu});
+//   flux F^d, Eq. 12; signal speeds of the fast-magnetosonic bound
+//   a^2 = cs^2 + vA^2 - cs^2 vA^2 (HLLE after Gammie 2003, cited in Sec. 2.3);
+//   HLLE combination (Sec. 2.3, step 3).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace grmhd {
+
+__device__ __forceinline__ double xsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double xabs(double x) { return fabs(x); }
+__device__ __forceinline__ float xabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double xmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float xmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double xmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float xmax(float a, float b) { return fmaxf(a, b); }
+
+// ------------------------------------------------------------ reconstruction
+// minmod slope limiter (TVD, Sec. 2.3): 0 across an extremum, otherwise the
+// smaller one-sided difference (first argument on a tie).
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  if (a * b <= T(0)) return T(0);
+  return (xabs(a) <= xabs(b)) ? a : b;
+}
+
+// WENO5 (Jiang-Shu indicators, linear weights 1/10, 6/10, 3/10): value at
+// the face i+1/2 from the cell values i-2 .. i+2.  The double version forms
+// the weights as d_k prod_{j != k} (eps + beta_j)^2 over their sum, which
+// needs a single division; the float version uses the textbook reciprocals
+// so that the squared products cannot overflow.
+template <class T>
+__device__ __forceinline__ T weno5(T um2, T um1, T u0, T up1, T up2, T eps);
+
+template <>
+__device__ __forceinline__ double weno5<double>(double um2, double um1, double u0, double up1, double up2,
+                                                double eps) {
+  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
+  const double q0 = (2.0 * um2 - 7.0 * um1 + 11.0 * u0) * c6;
+  const double q1 = (-um1 + 5.0 * u0 + 2.0 * up1) * c6;
+  const double q2 = (2.0 * u0 + 5.0 * up1 - up2) * c6;
+  const double t0 = um2 - 2.0 * um1 + u0, s0 = um2 - 4.0 * um1 + 3.0 * u0;
+  const double t1 = um1 - 2.0 * u0 + up1, s1 = um1 - up1;
+  const double t2 = u0 - 2.0 * up1 + up2, s2 = 3.0 * u0 - 4.0 * up1 + up2;
+  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
+  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
+  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+template <>
+__device__ __forceinline__ float weno5<float>(float um2, float um1, float u0, float up1, float up2, float eps) {
+  const float c6 = 1.0f / 6.0f, c1312 = 13.0f / 12.0f;
+  const float q0 = (2.0f * um2 - 7.0f * um1 + 11.0f * u0) * c6;
+  const float q1 = (-um1 + 5.0f * u0 + 2.0f * up1) * c6;
+  const float q2 = (2.0f * u0 + 5.0f * up1 - up2) * c6;
+  const float t0 = um2 - 2.0f * um1 + u0, s0 = um2 - 4.0f * um1 + 3.0f * u0;
+  const float t1 = um1 - 2.0f * u0 + up1, s1 = um1 - up1;
+  const float t2 = u0 - 2.0f * up1 + up2, s2 = 3.0f * u0 - 4.0f * up1 + up2;
+  const float e0 = eps + (c1312 * t0 * t0 + 0.25f * s0 * s0);
+  const float e1 = eps + (c1312 * t1 * t1 + 0.25f * s1 * s1);
+  const float e2 = eps + (c1312 * t2 * t2 + 0.25f * s2 * s2);
+  const float a0 = __fdividef(0.1f, e0 * e0), a1 = __fdividef(0.6f, e1 * e1), a2 = __fdividef(0.3f, e2 * e2);
+  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------- geometry
+// Metric at a face (or a cell) converted to the compute type.
+template <class T>
+struct Geom {
+  T alpha, beta[3];
+  T g[6];      // gamma_xx, gamma_xy, gamma_xz, gamma_yy, gamma_yz, gamma_zz
+  T sqrtg;     // sqrt(det gamma)
+  T gup_dd;    // gamma^{dd} of the face normal
+};
+
+// Face metric = mean of the two adjacent cell-centre values; sqrt(gamma) and
+// gamma^{dd} are always computed in FP64.
+template <class T, int DIR>
+__device__ __forceinline__ void face_geom(const double* __restrict__ metric, long long ncell, long long c,
+                                          long long stride, Geom<T>& m) {
+  double a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = 0.5 * (__ldg(metric + q * ncell + c - stride) + __ldg(metric + q * ncell + c));
+  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+  const double cxx = gyy * gzz - gyz * gyz;
+  const double cyy = gxx * gzz - gxz * gxz;
+  const double czz = gxx * gyy - gxy * gxy;
+  const double det = gxx * cxx - gxy * (gxy * gzz - gyz * gxz) + gxz * (gxy * gyz - gyy * gxz);
+  const double cdd = (DIR == 0) ? cxx : ((DIR == 1) ? cyy : czz);
+  m.alpha = (T)a[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.beta[i] = (T)a[1 + i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m.g[i] = (T)a[4 + i];
+  m.sqrtg = (T)sqrt(det);
+  m.gup_dd = (T)(cdd / det);
+}
+
+template <class T>
+__device__ __forceinline__ void lower(const T g[6], const T v[3], T vl[3]) {
+  vl[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+  vl[1] = g[1] * v[0] + g[3] * v[1] + g[4] * v[2];
+  vl[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
+}
+
+template <class T, bool CURVED>
+__device__ __forceinline__ bool physical_state(const T pr[8], const Geom<T>& m) {
+  const T v[3] = {pr[1], pr[2], pr[3]};
+  T v2;
+  if (CURVED) {
+    T vl[3];
+    lower(m.g, v, vl);
+    v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  } else {
+    v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  }
+  return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
+}
+
+// ------------------------------------------------- one side of a Riemann face
+template <class T>
+struct Side {
+  T U[8];
+  T F[8];
+  T lm, lp;
+};
+
+// Conserved vector (Eqs. 6-9), flux along DIR (Eq. 12) and signal speeds of
+// the primitive state pr at a face with metric m.
+template <class T, bool CURVED, int DIR>
+__device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T gamma, T gfac, Side<T>& o) {
+  const T rho = pr[0], P = pr[4];
+  const T v[3] = {pr[1], pr[2], pr[3]};
+  const T B[3] = {pr[5], pr[6], pr[7]};
+  T vl[3], Bl[3];
+  if (CURVED) {
+    lower(m.g, v, vl);
+    lower(m.g, B, Bl);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { vl[i] = v[i]; Bl[i] = B[i]; }
+  }
+  const T v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const T omv2 = T(1) - v2;
+  const T iW = xsqrt(omv2);         // 1 / W
+  const T W = T(1) / iW;
+  const T ab0 = W * Bv;             // alpha b^0
+  const T b2 = B2 * omv2 + Bv * Bv; // (B^2 + (alpha b^0)^2) / W^2
+  T bl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
+  const T rhoh = rho + gfac * P;
+  const T hs = rhoh + b2;           // rho h*
+  const T Ps = P + T(0.5) * b2;     // P*
+  const T sg = CURVED ? m.sqrtg : T(1);
+  const T hW2 = hs * W * W;
+  const T D = sg * rho * W;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) o.U[1 + i] = sg * (hW2 * vl[i] - ab0 * bl[i]);
+  const T tau = sg * (hW2 - Ps - ab0 * ab0) - D;
+  o.U[0] = D;
+  o.U[4] = tau;
+  T Bc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { Bc[i] = sg * B[i]; o.U[5 + i] = Bc[i]; }
+  // flux along DIR
+  const T alpha = CURVED ? m.alpha : T(1);
+  T vt[3];
+  if (CURVED) {
+    const T ia = T(1) / alpha;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vt[i] = v[i] - m.beta[i] * ia;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vt[i] = v[i];
+  }
+  const T vtd = vt[DIR];
+  const T sgPs = sg * Ps;
+  const T BdiW = Bc[DIR] * iW;
+  o.F[0] = alpha * (D * vtd);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) o.F[1 + j] = alpha * (o.U[1 + j] * vtd + (j == DIR ? sgPs : T(0)) - bl[j] * BdiW);
+  o.F[4] = alpha * (tau * vtd + sgPs * v[DIR] - ab0 * BdiW);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) o.F[5 + k] = (k == DIR) ? T(0) : alpha * (Bc[k] * vtd - Bc[DIR] * vt[k]);
+  // signal speeds
+  const T r = T(1) / (rhoh * hs);
+  const T cs2 = gamma * P * hs * r;
+  const T va2 = b2 * rhoh * r;
+  const T a2 = cs2 + va2 - cs2 * va2;
+  const T gdd = CURVED ? m.gup_dd : T(1);
+  const T den = T(1) - v2 * a2;
+  const T vd = v[DIR];
+  T disc = omv2 * (gdd * den - vd * vd * (T(1) - a2));
+  disc = xmax(disc, T(0));
+  const T sq = xsqrt(a2 * disc);
+  const T ide = alpha / den;
+  const T c0 = vd * (T(1) - a2);
+  const T bd = CURVED ? m.beta[DIR] : T(0);
+  o.lp = ide * (c0 + sq) - bd;
+  o.lm = ide * (c0 - sq) - bd;
+}
+
+// HLLE flux (Sec. 2.3) from the two sides; 1e-300 (double) / 1e-30 (float)
+// guards the degenerate fan xi+ = xi- = 0 with the mean physical flux.
+template <class T>
+__device__ __forceinline__ void hlle_combine(const Side<T>& L, const Side<T>& R, T F[8]) {
+  const T xm = xmin(T(0), xmin(L.lm, R.lm));
+  const T xp = xmax(T(0), xmax(L.lp, R.lp));
+  const T den = xp - xm;
+  const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
+  if (den < tiny) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) F[q] = T(0.5) * (L.F[q] + R.F[q]);
+    return;
+  }
+  const T inv = T(1) / den;
+  const T xpm = xp * xm;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) F[q] = (xp * L.F[q] - xm * R.F[q] + xpm * (R.U[q] - L.U[q])) * inv;
+}
+
+}  // namespace grmhd

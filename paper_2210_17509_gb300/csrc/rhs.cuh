@@ -1,0 +1,294 @@
+// Fused method-of-lines RHS kernel: reconstruction + face metric + HLLE +
+// flux divergence + source terms + RK stage epilogue, one launch.
+//
+// Work decomposition: a CTA owns a TX x TY x TZ tile of interior cells.  It
+// computes every face flux of the tile exactly once -- (TX+1) TY TZ x-faces,
+// TX (TY+1) TZ y-faces, TX TY (TZ+1) z-faces, one flat list spread over all
+// threads -- into shared memory (SoA [comp][face], conflict-free), then each
+// thread differences the six faces of its cell, adds the Eq. 13 source
+// (3+1 form, curved metric only) and applies the stage epilogue.
+#pragma once
+
+#include "physics.cuh"
+
+namespace grmhd {
+
+// Load the 8 primitives at the six-point stencil of the face between cell
+// c - stride and c, reconstruct both states.
+template <class T, int RECON>
+__device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim, long long ncell, long long c,
+                                                 long long stride, T eps, T pL[8], T pR[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double* a = prim + q * ncell + c;
+    if (RECON == GRMHD_WENO5) {
+      const T um3 = (T)__ldg(a - 3 * stride), um2 = (T)__ldg(a - 2 * stride), um1 = (T)__ldg(a - stride);
+      const T u0 = (T)__ldg(a), up1 = (T)__ldg(a + stride), up2 = (T)__ldg(a + 2 * stride);
+      pL[q] = weno5<T>(um3, um2, um1, u0, up1, eps);
+      pR[q] = weno5<T>(up2, up1, u0, um1, um2, eps);
+    } else {
+      const T um2 = (T)__ldg(a - 2 * stride), um1 = (T)__ldg(a - stride);
+      const T u0 = (T)__ldg(a), up1 = (T)__ldg(a + stride);
+      pL[q] = um1 + T(0.5) * minmod<T>(um1 - um2, u0 - um1);
+      pR[q] = u0 - T(0.5) * minmod<T>(u0 - um1, up1 - u0);
+    }
+  }
+}
+
+template <class T, int RECON, bool CURVED, int DIR>
+__device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
+                                          const double* __restrict__ metric, long long c, T F[8]) {
+  const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
+  T pL[8], pR[8];
+  reconstruct_face<T, RECON>(prim, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+  Geom<T> m;
+  if (CURVED) face_geom<T, DIR>(metric, g.ncell, c, stride, m);
+  // A face state with rho <= 0, P <= 0 or v^2 >= 1 falls back to the state of
+  // the cell it was reconstructed from (rare; WENO5 overshoot at sharp
+  // gradients of under-resolved data).
+  if (!physical_state<T, CURVED>(pL, m)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pL[q] = (T)__ldg(prim + q * g.ncell + c - stride);
+  }
+  if (!physical_state<T, CURVED>(pR, m)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pR[q] = (T)__ldg(prim + q * g.ncell + c);
+  }
+  Side<T> L, R;
+  side_state<T, CURVED, DIR>(pL, m, (T)p.gamma, (T)p.gfac, L);
+  side_state<T, CURVED, DIR>(pR, m, (T)p.gamma, (T)p.gfac, R);
+  hlle_combine<T>(L, R, F);
+}
+
+// Eq. 13 in 3+1 form for a static-in-time lapse and shift:
+//   S_{S_j} = alpha sqrt(gamma) [ T^00 (beta^i beta^k d_j g_ik / 2 - alpha d_j alpha)
+//             + T^0i beta^k d_j g_ik + T^0_i d_j beta^i + T^ik d_j g_ik / 2 ]
+//   S_tau   = alpha sqrt(gamma) [ T^00 (beta^i beta^j K_ij - beta^i d_i alpha)
+//             + T^0i (2 beta^j K_ij - d_i alpha) + T^ij K_ij ]
+// Metric derivatives by 4th-order centred differences of the cell-centred
+// metric; the spatial inverse and sqrt(gamma) in FP64.
+template <class T>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
+                                             const double* __restrict__ metric, const double* __restrict__ kij,
+                                             long long c, T src[8]) {
+  double a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = __ldg(metric + q * g.ncell + c);
+  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+  const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
+  const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
+  const double det = gxx * cxx + gxy * cxy + gxz * cxz;
+  const double idet = 1.0 / det;
+  const T sg = (T)sqrt(det);
+  const T gu[6] = {(T)(cxx * idet), (T)(cxy * idet), (T)(cxz * idet),
+                   (T)(cyy * idet), (T)(cyz * idet), (T)(czz * idet)};
+  const T alpha = (T)a[0];
+  const T beta[3] = {(T)a[1], (T)a[2], (T)a[3]};
+  const T gm[6] = {(T)gxx, (T)gxy, (T)gxz, (T)gyy, (T)gyz, (T)gzz};
+  // derivatives d[e][q] of the 10 metric components
+  T dA[3][10];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long s = (e == 0) ? 1 : ((e == 1) ? g.sy : g.sz);
+    const double w = g.idx[e] * (1.0 / 12.0);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const double* m = metric + q * g.ncell + c;
+      dA[e][q] = (T)((8.0 * (__ldg(m + s) - __ldg(m - s)) - (__ldg(m + 2 * s) - __ldg(m - 2 * s))) * w);
+    }
+  }
+  // fluid at the cell centre
+  const double* pc = prim + c;
+  const T rho = (T)__ldg(pc), P = (T)__ldg(pc + 4 * g.ncell);
+  const T v[3] = {(T)__ldg(pc + g.ncell), (T)__ldg(pc + 2 * g.ncell), (T)__ldg(pc + 3 * g.ncell)};
+  const T B[3] = {(T)__ldg(pc + 5 * g.ncell), (T)__ldg(pc + 6 * g.ncell), (T)__ldg(pc + 7 * g.ncell)};
+  T vl[3], Bl[3], bl_[3];
+  lower(gm, v, vl);
+  lower(gm, B, Bl);
+  (void)bl_;
+  const T v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const T omv2 = T(1) - v2;
+  const T iW = xsqrt(omv2);
+  const T W = T(1) / iW;
+  const T ab0 = W * Bv;
+  const T b2 = B2 * omv2 + Bv * Bv;
+  const T hs = rho + (T)p.gfac * P + b2;
+  const T Ps = P + T(0.5) * b2;
+  const T ia = T(1) / alpha;
+  const T ia2 = ia * ia;
+  const T b0 = ab0 * ia;
+  T vt[3], bu[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vt[i] = v[i] - beta[i] * ia;
+    bu[i] = B[i] * iW + ab0 * vt[i];
+  }
+  const T hW2 = hs * W * W;
+  const T T00 = (hW2 - Ps) * ia2 - b0 * b0;
+  T T0[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) T0[i] = hW2 * vt[i] * ia + Ps * beta[i] * ia2 - b0 * bu[i];
+  // T^{ij}, symmetric, packed like gamma
+  const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+  T Tij[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const int i = I6[s], j = J6[s];
+    Tij[s] = hW2 * vt[i] * vt[j] + Ps * (gu[s] - beta[i] * beta[j] * ia2) - bu[i] * bu[j];
+  }
+  T betal[3];
+  lower(gm, beta, betal);
+  T T0l[3];  // T^0_i = beta_i T^00 + gamma_ij T^0j
+  lower(gm, T0, T0l);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) T0l[i] += betal[i] * T00;
+  const T asg = alpha * sg;
+  // symmetric contraction weights: off-diagonal entries count twice
+  const T wsym[6] = {T(1), T(2), T(2), T(1), T(2), T(1)};
+  src[0] = T(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T bbdg = T(0), t0dg = T(0), tdg = T(0);
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      const int i = I6[s], k = J6[s];
+      const T dg = dA[j][4 + s] * wsym[s];
+      bbdg += beta[i] * beta[k] * dg;
+      // T^0i beta^k d_j g_ik summed over i, k: symmetric part
+      t0dg += T(0.5) * (T0[i] * beta[k] + T0[k] * beta[i]) * dg;
+      tdg += Tij[s] * dg;
+    }
+    const T t0db = T0l[0] * dA[j][1] + T0l[1] * dA[j][2] + T0l[2] * dA[j][3];
+    src[1 + j] = asg * (T00 * (T(0.5) * bbdg - alpha * dA[j][0]) + t0dg + t0db + T(0.5) * tdg);
+  }
+  {
+    T t = -(T0[0] * dA[0][0] + T0[1] * dA[1][0] + T0[2] * dA[2][0]);
+    t -= T00 * (beta[0] * dA[0][0] + beta[1] * dA[1][0] + beta[2] * dA[2][0]);
+    if (kij) {
+      T K[6];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) K[s] = (T)__ldg(kij + s * g.ncell + c);
+      T bK[3];
+      lower(K, beta, bK);  // K_ij beta^j
+      const T bbK = beta[0] * bK[0] + beta[1] * bK[1] + beta[2] * bK[2];
+      const T tK = T0[0] * bK[0] + T0[1] * bK[1] + T0[2] * bK[2];
+      T TK = T(0);
+#pragma unroll
+      for (int s = 0; s < 6; ++s) TK += Tij[s] * K[s] * wsym[s];
+      t += T00 * bbK + T(2) * tK + TK;
+    }
+    src[4] = asg * t;
+  }
+  src[5] = src[6] = src[7] = T(0);
+}
+
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) rhs_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                                           const double* __restrict__ metric,
+                                                           const double* __restrict__ kij, StageEpilogue ep) {
+  constexpr int NT = TX * TY * TZ;
+  constexpr int NFX = (TX + 1) * TY * TZ;
+  constexpr int NFY = TX * (TY + 1) * TZ;
+  constexpr int NFZ = TX * TY * (TZ + 1);
+  constexpr int NF = NFX + NFY + NFZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);  // [8][NF]
+
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int ng = g.ng;
+  for (int f = threadIdx.x; f < NF; f += NT) {
+    T F[8];
+    bool ok;
+    if (f < NFX) {
+      const int a = f % (TX + 1), r = f / (TX + 1), b = r % TY, cz = r / TY;
+      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      ok = (xi <= g.n[0]) && (yi < g.n[1]) && (zi < g.n[2]);
+      if (ok) {
+        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+        face_flux<T, RECON, CURVED, 0>(g, p, prim, metric, c, F);
+      }
+    } else if (f < NFX + NFY) {
+      const int ff = f - NFX;
+      const int a = ff % TX, r = ff / TX, b = r % (TY + 1), cz = r / (TY + 1);
+      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      ok = (xi < g.n[0]) && (yi <= g.n[1]) && (zi < g.n[2]);
+      if (ok) {
+        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+        face_flux<T, RECON, CURVED, 1>(g, p, prim, metric, c, F);
+      }
+    } else {
+      const int ff = f - NFX - NFY;
+      const int a = ff % TX, r = ff / TX, b = r % TY, cz = r / TY;
+      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      ok = (xi < g.n[0]) && (yi < g.n[1]) && (zi <= g.n[2]);
+      if (ok) {
+        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+        face_flux<T, RECON, CURVED, 2>(g, p, prim, metric, c, F);
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sF[q * NF + f] = F[q];
+    }
+  }
+  __syncthreads();
+
+  const int ci = threadIdx.x % TX, cj = (threadIdx.x / TX) % TY, ck = threadIdx.x / (TX * TY);
+  const int xi = x0 + ci, yi = y0 + cj, zi = z0 + ck;
+  if (xi >= g.n[0] || yi >= g.n[1] || zi >= g.n[2]) return;
+  const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+  const int fx = (ck * TY + cj) * (TX + 1) + ci;
+  const int fy = NFX + (ck * (TY + 1) + cj) * TX + ci;
+  const int fz = NFX + NFY + (ck * TY + cj) * TX + ci;
+  const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+  T r[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const T* s = sF + q * NF;
+    T acc = -(s[fx + 1] - s[fx]) * ix;
+    acc -= (s[fy + TX] - s[fy]) * iy;
+    acc -= (s[fz + TX * TY] - s[fz]) * iz;
+    r[q] = acc;
+  }
+  if (CURVED) {
+    T src[8];
+    source_terms<T>(g, p, prim, metric, kij, c, src);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] += src[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long o = q * g.ncell + c;
+    const double rq = (double)r[q];
+    if (ep.rhs) ep.rhs[o] = rq;
+    const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
+    if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+    if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
+  }
+}
+
+// Host-side launcher for one precision.
+template <class T>
+cudaError_t launch_rhs_t(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                         const double* kij, const StageEpilogue& ep, cudaStream_t s) {
+  constexpr int TX = 8, TY = 8, TZ = 4;
+  constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
+  const size_t smem = (size_t)8 * NF * sizeof(T);
+  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + TZ - 1) / TZ);
+  const dim3 block(TX * TY * TZ);
+  const bool curved = metric != nullptr;
+  const bool weno = p.recon == GRMHD_WENO5;
+  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, StageEpilogue);
+  if (weno)
+    k = curved ? rhs_kernel<T, GRMHD_WENO5, true, TX, TY, TZ> : rhs_kernel<T, GRMHD_WENO5, false, TX, TY, TZ>;
+  else
+    k = curved ? rhs_kernel<T, GRMHD_MINMOD, true, TX, TY, TZ> : rhs_kernel<T, GRMHD_MINMOD, false, TX, TY, TZ>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, block, smem, s>>>(g, p, prim, metric, kij, ep);
+  return cudaGetLastError();
+}
+
+}  // namespace grmhd

@@ -1,0 +1,11 @@
+// FP64 instantiation of the fused RHS kernel (the plain method).
+#include "rhs.cuh"
+
+namespace grmhd {
+
+cudaError_t launch_rhs_fp64(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                            const double* kij, const StageEpilogue& ep, cudaStream_t s) {
+  return launch_rhs_t<double>(g, p, prim, metric, kij, ep, s);
+}
+
+}  // namespace grmhd

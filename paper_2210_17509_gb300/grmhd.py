@@ -1,0 +1,221 @@
+"""Thin Python binding of libgrmhd.so (the C ABI declared in include/grmhd.h).
+
+Argument marshalling only: every function checks the tensors it is given
+(CUDA, float64, contiguous, expected shape), passes raw device pointers and
+the current torch stream to the C entry point of the same name, and raises
+``GrmhdError`` on a non-zero return code.  All arithmetic runs in the CUDA
+kernels of the library.  Importing this module fails loudly when the
+library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgrmhd.so")
+
+MINMOD, WENO5 = 0, 1
+BC_PERIODIC, BC_COPY = 0, 1
+FP64, MIXED = 0, 1
+RK2, RK3, RK4 = 2, 3, 4
+
+
+class GrmhdError(RuntimeError):
+    pass
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libgrmhd.so not found at {LIB_PATH}; build it with "
+        "`python -m paper_2210_17509_gb300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class CGrid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("ng", ctypes.c_int32), ("dx", ctypes.c_double * 3)]
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("recon", ctypes.c_int32),
+        ("bc", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("nr_maxit", ctypes.c_int32),
+        ("rho_atm", ctypes.c_double),
+        ("p_atm", ctypes.c_double),
+        ("nr_tol", ctypes.c_double),
+        ("weno_eps", ctypes.c_double),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I32 = ctypes.c_int32
+_pg = ctypes.POINTER(CGrid)
+_pp = ctypes.POINTER(CParams)
+
+_lib.grmhd_prim2con.argtypes = [_pg, _pp, _P, _P, _P, _P]
+_lib.grmhd_con2prim.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, _P]
+_lib.grmhd_fill_ghosts.argtypes = [_pg, _I32, _I32, _P, _P]
+_lib.grmhd_rhs.argtypes = [_pg, _pp, _P, _P, _P, _P, _P]
+_lib.grmhd_rk_workspace_bytes.argtypes = [_pg, _I32]
+_lib.grmhd_rk_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
+_lib.grmhd_error_string.argtypes = [_I]
+_lib.grmhd_error_string.restype = ctypes.c_char_p
+_lib.grmhd_version.restype = _I
+for _name in ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rhs", "grmhd_rk_step"):
+    getattr(_lib, _name).restype = _I
+
+C_SYMBOLS = ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rhs", "grmhd_rk_workspace_bytes",
+             "grmhd_rk_step", "grmhd_error_string", "grmhd_version")
+
+
+@dataclass
+class Grid:
+    """Interior cells n = (nx, ny, nz), ghost width ng, spacing dx = (dx, dy, dz)."""
+    n: tuple
+    ng: int
+    dx: tuple
+
+    def c(self) -> CGrid:
+        return CGrid((ctypes.c_int32 * 3)(*[int(v) for v in self.n]), int(self.ng),
+                     (ctypes.c_double * 3)(*[float(v) for v in self.dx]))
+
+    @property
+    def shape(self):
+        nx, ny, nz = (v + 2 * self.ng for v in self.n)
+        return (nz, ny, nx)
+
+    @property
+    def ncell(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+
+@dataclass
+class Params:
+    gamma: float = 5.0 / 3.0
+    recon: int = WENO5
+    bc: int = BC_PERIODIC
+    precision: int = FP64
+    nr_maxit: int = 50
+    rho_atm: float = 1e-10
+    p_atm: float = 1e-20
+    nr_tol: float = 1e-12
+    weno_eps: float = 1e-6
+
+    def c(self) -> CParams:
+        return CParams(self.gamma, self.recon, self.bc, self.precision, self.nr_maxit, self.rho_atm, self.p_atm,
+                       self.nr_tol, self.weno_eps)
+
+
+def version() -> int:
+    return _lib.grmhd_version()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GrmhdError(f"{what}: {_lib.grmhd_error_string(rc).decode()} ({rc})")
+
+
+def _field(t, grid: Grid, ncomp: int, name: str, optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != (ncomp,) + grid.shape:
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {(ncomp,) + grid.shape}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def prim2con(grid: Grid, params: Params, prim, metric=None, cons=None, stream=None):
+    if cons is None:
+        cons = torch.empty_like(prim)
+    rc = _lib.grmhd_prim2con(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                             _field(metric, grid, 10, "metric", True), _field(cons, grid, 8, "cons"),
+                             _stream(stream))
+    _check(rc, "grmhd_prim2con")
+    return cons
+
+
+def con2prim(grid: Grid, params: Params, cons, prim, metric=None, status=None, nfail=None, stream=None):
+    """In place on prim (guess in, result out)."""
+    st = None
+    if status is not None:
+        if status.dtype != torch.int8 or tuple(status.shape) != grid.shape or not status.is_cuda:
+            raise ValueError("status must be a CUDA int8 tensor of the block shape")
+        st = ctypes.c_void_p(status.data_ptr())
+    nf = None
+    if nfail is not None:
+        if nfail.dtype != torch.int32 or nfail.numel() < 1 or not nfail.is_cuda:
+            raise ValueError("nfail must be a CUDA int32 tensor")
+        nf = ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_con2prim(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(cons, grid, 8, "cons"),
+                             _field(metric, grid, 10, "metric", True), _field(prim, grid, 8, "prim"), st, nf,
+                             _stream(stream))
+    _check(rc, "grmhd_con2prim")
+    return prim
+
+
+def fill_ghosts(grid: Grid, bc: int, field, stream=None):
+    nvar = field.shape[0]
+    rc = _lib.grmhd_fill_ghosts(ctypes.byref(grid.c()), bc, nvar, _field(field, grid, nvar, "field"),
+                                _stream(stream))
+    _check(rc, "grmhd_fill_ghosts")
+    return field
+
+
+def rhs(grid: Grid, params: Params, prim, metric=None, kij=None, out=None, stream=None):
+    if out is None:
+        out = torch.zeros_like(prim)
+    rc = _lib.grmhd_rhs(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                        _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                        _field(out, grid, 8, "rhs"), _stream(stream))
+    _check(rc, "grmhd_rhs")
+    return out
+
+
+def rk_workspace_bytes(grid: Grid, scheme: int) -> int:
+    return int(_lib.grmhd_rk_workspace_bytes(ctypes.byref(grid.c()), scheme))
+
+
+def workspace(grid: Grid, scheme: int, device=None):
+    nbytes = rk_workspace_bytes(grid, scheme)
+    if nbytes == 0:
+        raise GrmhdError("invalid grid or scheme for the workspace")
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def rk_step(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, metric=None, kij=None, ws=None,
+            nfail=None, stream=None):
+    """One step in place on cons and prim."""
+    if ws is None:
+        ws = workspace(grid, scheme, cons.device)
+    nf = None
+    if nfail is not None:
+        nf = ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_rk_step(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
+                            _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
+                            _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel(), nf, _stream(stream))
+    _check(rc, "grmhd_rk_step")
+    return cons, prim

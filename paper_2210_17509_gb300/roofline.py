@@ -1,0 +1,59 @@
+"""Roofline bookkeeping for the benchmark: algorithmic work per cell and peaks.
+
+Algorithmic FP64 operations of the fused RHS kernel per interior cell, counted
+by hand from the 3+1 formulas the kernel evaluates (add, sub, mul = 1, fused
+multiply-add = 2, divide and square root = 1, min/max = 1), with the three
+faces per cell counted once (tile-boundary recomputation is not algorithmic):
+
+  WENO5 reconstruction of one value            69   (candidates 16, indicators 36, weights 17)
+  face metric (mean of 2 cells, sqrt(gamma), gamma^dd)   42
+  one side of a face (cons, flux, signal speeds) 160
+  HLLE combination                              65
+  per face (WENO5): 16 * 69 + 42 + 2 * 160 + 65 = 1531
+  flux divergence                               72
+  source terms (FD4 metric derivatives, T^{mu nu}, Eq. 13 in 3+1 form)  666
+  stage epilogue                                40
+  cell total (curved, WENO5): 3 * 1531 + 72 + 666 + 40 = 5371
+
+Algorithmic HBM bytes per interior cell of grmhd_rhs (FP64): prim 8 x 8 B +
+metric 10 x 8 B read, rhs 8 x 8 B written = 208 B.
+
+Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
+FP64 FMA peak was measured on this GPU model with ``python -m
+paper_2210_17509_gb300.peaks`` (1.20 TFLOP/s at a 2.0 GHz SM clock, FMA = 2
+flops), i.e. 2 FP64 FMA per SM per clock on 152 SMs.
+"""
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
+BYTES_PER_CELL_RHS_CURVED = 208
+FP64_PEAK_TFLOPS_MEASURED = 1.20
+FP32_PEAK_TFLOPS_MEASURED = 75.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def rhs_fp64_roofline(ncells: int, ms_per_launch: float, traffic=None):
+    flops = FLOPS_PER_CELL_RHS_CURVED_WENO5 * ncells
+    achieved = flops / (ms_per_launch * 1e-3) / 1e12
+    hbm, src = hbm_peak_gbs()
+    gbs = BYTES_PER_CELL_RHS_CURVED * ncells / (ms_per_launch * 1e-3) / 1e9
+    return {
+        "bound": "alu", "kernel": "rhs_kernel<double, WENO5, curved> (grmhd_rhs, FP64)",
+        "achieved": achieved, "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS_MEASURED, "traffic": traffic,
+        "peak_source": "measured FP64 FMA probe (python -m paper_2210_17509_gb300.peaks)",
+        "ms_per_launch": ms_per_launch, "flops_per_cell": FLOPS_PER_CELL_RHS_CURVED_WENO5,
+        "hbm_context": {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_source": src, "frac": gbs / hbm,
+                        "bytes_per_cell": BYTES_PER_CELL_RHS_CURVED},
+    }

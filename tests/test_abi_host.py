@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/grmhd.h declares, and rejects bad arguments before
+touching any device pointer."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "grmhd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2210_17509_gb300 import build
+    build.build()
+    from paper_2210_17509_gb300 import grmhd
+    return grmhd
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(grmhd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ("grmhd_rhs", "grmhd_con2prim", "grmhd_rk_step", "grmhd_prim2con", "grmhd_fill_ghosts"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(so, n), n
+
+
+def _grid(lib, n=(8, 8, 8), ng=3, dx=0.1):
+    return lib.Grid(n, ng, (dx, dx, dx))
+
+
+FAKE = ctypes.c_void_p(0x1000)    # never dereferenced: every case fails validation first
+
+
+def test_rejects_insufficient_ghosts(lib):
+    g = _grid(lib, ng=2).c()
+    p = lib.Params(recon=lib.WENO5).c()
+    rc = lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None)
+    assert rc == -1
+
+
+def test_rejects_bad_params(lib):
+    g = _grid(lib).c()
+    for kw in ({"gamma": 1.0}, {"recon": 7}, {"bc": 3}, {"precision": 5}, {"nr_maxit": 0}, {"nr_tol": 0.0},
+               {"weno_eps": -1.0}, {"rho_atm": 0.0}):
+        p = lib.Params(**kw).c()
+        rc = lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None)
+        assert rc == -1, kw
+
+
+def test_rejects_null_and_misaligned(lib):
+    g = _grid(lib).c()
+    p = lib.Params().c()
+    assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), None, None, None, FAKE, None) == -1
+    assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), ctypes.c_void_p(0x1003), None, None, FAKE,
+                              None) == -1
+    # K_ij without a metric is meaningless
+    assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, FAKE, FAKE, None) == -1
+    assert lib._lib.grmhd_fill_ghosts(ctypes.byref(g), 9, 8, FAKE, None) == -1
+
+
+def test_workspace_size_and_rk_validation(lib):
+    g = _grid(lib, n=(10, 12, 14))
+    N = (16 * 18 * 20)
+    for scheme, nfield in ((lib.RK2, 1), (lib.RK3, 1), (lib.RK4, 2)):
+        b = lib.rk_workspace_bytes(g, scheme)
+        assert b >= nfield * 8 * N * 8 and b % 256 == 0
+    assert lib.rk_workspace_bytes(g, 5) == 0
+    gc = g.c()
+    p = lib.Params().c()
+    ws = ctypes.c_void_p(0x100000)
+    small = lib.rk_workspace_bytes(g, lib.RK3) - 8
+    rc = lib._lib.grmhd_rk_step(ctypes.byref(gc), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, None, None, ws,
+                                small, None, None)
+    assert rc == -4
+    rc = lib._lib.grmhd_rk_step(ctypes.byref(gc), ctypes.byref(p), lib.RK3, -0.01, FAKE, FAKE, None, None, ws,
+                                10 ** 9, None, None)
+    assert rc == -1
+    rc = lib._lib.grmhd_rk_step(ctypes.byref(gc), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, None, None,
+                                ctypes.c_void_p(0x100008), 10 ** 9, None, None)
+    assert rc == -1          # workspace must be 256-byte aligned
+
+
+def test_error_strings(lib):
+    assert lib._lib.grmhd_error_string(0) == b"ok"
+    assert lib._lib.grmhd_error_string(-4) == b"workspace too small"
+    assert lib.version() >= 100

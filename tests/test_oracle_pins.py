@@ -623,3 +623,22 @@ def test_dual_number_gradient_matches_central_differences():
     Lm, _, _ = O.loss_jvp(g, par_m, O.RK3, dt, 2, prim - h * d)
     fd = (Lp - Lm) / (2 * h)
     assert abs(fd - dL) < 1e-7 * abs(dL)
+
+
+def test_unphysical_face_state_falls_back_to_cell_state():
+    """Reading of Sec. 2.3's failure list at faces: WENO5 overshoot to rho < 0
+    is replaced by the state of the cell the value was reconstructed from."""
+    rho = np.array([1, 1, 1, 1e-3, 1e-3, 1, 1, 1, 1, 1, 1, 1], float)
+    uL, uR = O.reconstruct_1d(O.REC_WENO5, rho)
+    assert uL[4] < 0 and uR[4] < 0 and uL[5] > 0 and uR[5] > 0
+    g = O.Grid((6, 1, 1), 3, (0.1, 0.1, 0.1))
+    prim = np.zeros((8,) + g.shape)
+    prim[0] = rho[None, None, :]
+    prim[4] = 1.0
+    par = O.make_params()
+    r = O.rhs(g, par, prim)
+    state = lambda d: np.array([d, 0, 0, 0, 1.0, 0, 0, 0])
+    F34, _ = O.hlle(state(rho[3]), state(rho[4]), par.gamma, 0)   # both sides fell back
+    F45, _ = O.hlle(state(uL[5]), state(uR[5]), par.gamma, 0)
+    expect = -(F45 - F34) / 0.1
+    np.testing.assert_allclose(r[:, 3, 3, 4], expect, rtol=1e-13, atol=1e-13)
