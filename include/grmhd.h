@@ -150,6 +150,28 @@ int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t sc
                   double* cons, double* prim, const double* metric, const double* kij, void* ws,
                   size_t ws_bytes, int32_t* nfail, void* stream);
 
+/* Size of the library-owned scratch of grmhd_rk_step_static: 64 MiB. */
+#define GRMHD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* grmhd_rk_step without a caller workspace.  The paper has no counterpart:
+ * this is a convenience for callers that cannot call cudaMalloc or any other
+ * allocating routine (a host code whose device memory belongs to another
+ * allocator or pool, a callback context where allocation is forbidden, a
+ * binding without a device allocator).  Same arguments and results as
+ * grmhd_rk_step minus ws/ws_bytes; the scratch is a file-scope device array
+ * of GRMHD_STATIC_SCRATCH_BYTES held by every GPU on which this function is
+ * first called, until the process exits.
+ *   Limit: grmhd_rk_workspace_bytes(grid, scheme) <= GRMHD_STATIC_SCRATCH_BYTES,
+ *   i.e. ncell <= 1,048,576 for RK2/RK3 and about half that for RK4 (e.g. a
+ *   94^3 interior with 3 ghosts); larger blocks return GRMHD_ERR_SIZE.
+ *   The first call on a device (that device current) looks up the array's
+ *   device address once; make that first call before any stream capture.
+ *   Every call shares the one array: calls that overlap on the GPU race.
+ *   Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call. */
+int grmhd_rk_step_static(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                         double* cons, double* prim, const double* metric, const double* kij,
+                         int32_t* nfail, void* stream);
+
 /* Human-readable name of a return code (static storage). */
 const char* grmhd_error_string(int code);
 

@@ -67,6 +67,8 @@ _lib.grmhd_rhs.argtypes = [_pg, _pp, _P, _P, _P, _P, _P]
 _lib.grmhd_rk_workspace_bytes.argtypes = [_pg, _I32]
 _lib.grmhd_rk_workspace_bytes.restype = ctypes.c_size_t
 _lib.grmhd_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
+_lib.grmhd_rk_step_static.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P]
+_lib.grmhd_rk_step_static.restype = _I
 _lib.grmhd_error_string.argtypes = [_I]
 _lib.grmhd_error_string.restype = ctypes.c_char_p
 _lib.grmhd_version.restype = _I
@@ -74,7 +76,8 @@ for _name in ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rh
     getattr(_lib, _name).restype = _I
 
 C_SYMBOLS = ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rhs", "grmhd_rk_workspace_bytes",
-             "grmhd_rk_step", "grmhd_error_string", "grmhd_version")
+             "grmhd_rk_step", "grmhd_rk_step_static", "grmhd_error_string", "grmhd_version")
+STATIC_SCRATCH_BYTES = 64 << 20
 
 
 @dataclass
@@ -218,4 +221,23 @@ def rk_step(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, metr
                             _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), nf, _stream(stream))
     _check(rc, "grmhd_rk_step")
+    return cons, prim
+
+
+def rk_step_static(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, metric=None, kij=None,
+                   nfail=None, stream=None):
+    """grmhd_rk_step_static: one step in place, with no workspace argument.
+
+    For callers that cannot allocate device memory; the library supplies the
+    scratch from a fixed 64 MiB device array (blocks whose workspace would
+    exceed it raise GrmhdError).  Overlapping calls on the GPU race on that
+    array; the first call on a device should precede any stream capture."""
+    nf = None
+    if nfail is not None:
+        nf = ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_rk_step_static(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
+                                   _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
+                                   _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                                   nf, _stream(stream))
+    _check(rc, "grmhd_rk_step_static")
     return cons, prim
