@@ -182,6 +182,78 @@ def cpu_baseline_sample(seconds_target=15.0):
     }
 
 
+# --------------------------------------------------------------- batched --
+def batched_bench(G, steps, warmup, nbox=512):
+    """512 AMR-like boxes (edges from {8..64}, 3 refinement levels, flat):
+    recovery + ghost fill + RHS of every box as one graph of three persistent
+    launches, against the plain form (three launches per box)."""
+    import torch
+    from paper_2210_17509_gb300 import autotune
+    t0 = time.perf_counter()
+    data = I.amr_boxes(nbox, seed=2)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"{nbox} boxes, edges from {{8,16,24,32,48,64}}, levels 0-2, flat, WENO5+HLLE, "
+                       "recovery+ghost fill+RHS", "input_generation_s": gen_s}
+    ncells = sum(b.ncells for b, _ in data)
+    out["interior_cells"] = ncells
+    for precision, name in ((G.FP64, "fp64"), (G.MIXED, "mixed")):
+        p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=precision)
+        costs = autotune.tile_costs(p)
+        boxes = []
+        for blk, prim in data:
+            g = G.Grid(blk.n, blk.ng, blk.dx)
+            tp = torch.from_numpy(prim).cuda()
+            G.fill_ghosts(g, G.BC_PERIODIC, tp)
+            tc = G.prim2con(g, p, tp)
+            boxes.append(G.Box(g, tc, tp, torch.zeros_like(tp), None, autotune.choose(blk.n, costs),
+                               G.BC_PERIODIC))
+        batch = G.Batch(boxes, p)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(max(warmup, 1)):
+                batch.rhs(p)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            batch.rhs(p)
+        for _ in range(warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # plain form: per-box launches of the single-block entry points
+        def plain():
+            for b in boxes:
+                G.con2prim(b.grid, p, b.cons, b.prim)
+                G.fill_ghosts(b.grid, G.BC_PERIODIC, b.prim)
+                G.rhs(b.grid, p, b.prim, None, None, b.rhs)
+        plain()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            plain()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1) / steps
+        tiles_used = {}
+        for b in boxes:
+            tiles_used[str(autotune.SHAPES[b.tile])] = tiles_used.get(str(autotune.SHAPES[b.tile]), 0) + 1
+        out[name] = {"value": ncells / (ms * 1e-3), "unit": "cells/s (recovery+RHS per box, one evaluation)",
+                     "ms_per_batch": ms, "plain_per_box_ms": ms_plain, "speedup_vs_plain": ms_plain / ms,
+                     "gpu_launches_per_batch": 3, "tile_shapes": tiles_used}
+        del boxes, batch, graph
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- GPU --
 def main():
     ap = argparse.ArgumentParser()
@@ -192,6 +264,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_CELLS_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -345,6 +418,10 @@ def main():
         e2e = {"value": world * ncells * steps_e / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "dtype": "f64"}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_bench(G, args.steps, args.warmup)
+
     if rank != 0:
         return
     cpu = None
@@ -362,6 +439,7 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "e2e": e2e,
+        "batched": batched,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

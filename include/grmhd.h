@@ -84,7 +84,16 @@ typedef struct {
   double p_atm;      /* atmosphere pressure */
   double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
+  int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
+  int32_t reserved;  /* must be 0 */
 } grmhd_params;
+
+/* RHS tile shapes (cells per CTA along x, y, z; 256 cells each).  The shape
+ * changes only how the work is cut, never the result. */
+#define GRMHD_TILE_8x8x4 0
+#define GRMHD_TILE_16x4x4 1
+#define GRMHD_TILE_32x4x2 2
+#define GRMHD_TILE_4x8x8 3
 
 /* Primitive -> conserved variables, Eqs. 6-9 (Sec. 2.2), on every cell of
  * the block (ghosts included), with the metric of that cell.
@@ -149,6 +158,52 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
 int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
                   double* cons, double* prim, const double* metric, const double* kij, void* ws,
                   size_t ws_bytes, int32_t* nfail, void* stream);
+
+/* ----------------------------------------------------------------------
+ * Batched boxes: many independent, unevenly sized blocks (the AMR block
+ * structure of Sec. 3.1, here as independent boxes with their own ghost
+ * zones) swept by persistent kernels -- one launch per phase over the whole
+ * box table, with a dynamic work counter.  Each box carries its own tile
+ * shape (chosen by the project's autotuner); the result does not depend on it.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  grmhd_grid grid;
+  double* cons;          /* 8 x ncell: conserved variables, interior read */
+  double* prim;          /* 8 x ncell: Newton guess in; primitives out, ghosts filled */
+  const double* metric;  /* 10 x ncell or NULL; a batch is all flat or all curved */
+  double* rhs;           /* 8 x ncell: interior RHS out, ghost entries untouched */
+  int32_t tile;          /* GRMHD_TILE_* for this box */
+  int32_t bc;            /* GRMHD_BC_* for this box's primitive ghosts */
+} grmhd_box;
+
+/* Prepared batch (filled by grmhd_batch_prepare; plain data, caller-owned). */
+typedef struct {
+  void* ws;              /* device workspace holding the box table */
+  size_t ws_bytes;
+  int32_t nbox;
+  int32_t curved;        /* 1 if the boxes carry a metric */
+  int64_t ntiles;        /* RHS work items */
+  int64_t nc2p_items;    /* recovery work items (256 interior cells each) */
+  int64_t nghost_items;  /* ghost-fill work items (256 points each) */
+} grmhd_batch;
+
+/* Device workspace (bytes) for a batch of nbox boxes; 0 if nbox is invalid. */
+size_t grmhd_batch_workspace_bytes(int32_t nbox);
+
+/* Validate the host array `boxes`, order them largest first, lay the box
+ * table and work offsets into the device workspace `ws` (256-byte aligned,
+ * >= grmhd_batch_workspace_bytes) and fill `batch`.  Synchronises `stream`
+ * once (host-to-device copy of the table); call it outside stream capture.
+ * The box buffers must stay valid for every later grmhd_batch_rhs. */
+int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params* params, void* ws,
+                        size_t ws_bytes, grmhd_batch* batch, void* stream);
+
+/* For every box: primitive recovery from cons (as grmhd_con2prim), ghost fill
+ * (as grmhd_fill_ghosts with the box's bc), then the RHS (as grmhd_rhs with
+ * the box's tile shape).  Three persistent launches on `stream` (plus one
+ * memset of the work counters), no host synchronisation: the sequence can be
+ * captured into a CUDA graph.  nfail as for grmhd_con2prim. */
+int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream);
 
 /* Size of the library-owned scratch of grmhd_rk_step_static: 64 MiB. */
 #define GRMHD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)

@@ -1,0 +1,167 @@
+// Batched boxes: host side of grmhd_batch_prepare / grmhd_batch_rhs.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "batch.cuh"
+
+namespace grmhd {
+cudaError_t launch_batch_rhs_fp64(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                  cudaStream_t s);
+cudaError_t launch_batch_rhs_mixed(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                   cudaStream_t s);
+__global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                                    DevParams p, int32_t* nfail) {
+  int myfail = 0;
+  const int nbox = head->nbox;
+  const long long total = head->nc2p;
+  for (;;) {
+    const long long it = next_item(&head->counter[1]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<1>(boxes, nbox, it)];
+    const long long nint = (long long)b.g.n[0] * b.g.n[1] * b.g.n[2];
+    const long long t = (it - b.c2p_begin) * kBatchItem + threadIdx.x;
+    if (t < nint) {
+      const long long c = interior_cell(b.g, t);
+      myfail += (con2prim_at(b.g, p, b.cons, b.metric, b.prim, c) >= 2);
+    }
+  }
+  if (nfail && myfail) atomicAdd(nfail, myfail);
+}
+
+__global__ void __launch_bounds__(kBatchItem) batch_ghost_kernel(BatchHead* head, const BoxDev* __restrict__ boxes) {
+  const int nbox = head->nbox;
+  const long long total = head->ngh;
+  for (;;) {
+    const long long it = next_item(&head->counter[2]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<2>(boxes, nbox, it)];
+    const long long c = (it - b.gh_begin) * kBatchItem + threadIdx.x;
+    if (c < b.g.ncell) fill_ghost_at(b.g, b.bc, 8, b.prim, c);
+  }
+}
+
+}  // namespace grmhd
+
+using namespace grmhd;
+
+namespace {
+
+constexpr size_t kHeadBytes = 256;
+static_assert(sizeof(BatchHead) <= kHeadBytes, "batch header too large");
+
+const int kShape[4][3] = {{8, 8, 4}, {16, 4, 4}, {32, 4, 2}, {4, 8, 8}};
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+size_t grmhd_batch_workspace_bytes(int32_t nbox) {
+  if (nbox < 1 || nbox > (1 << 22)) return 0;
+  return kHeadBytes + (((size_t)nbox * sizeof(BoxDev) + 255) & ~(size_t)255);
+}
+
+int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params* params, void* ws,
+                        size_t ws_bytes, grmhd_batch* batch, void* stream) {
+  if (!boxes || !params || !ws || !batch || nbox < 1) return GRMHD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  const size_t need = grmhd_batch_workspace_bytes(nbox);
+  if (need == 0) return GRMHD_ERR_ARG;
+  if (ws_bytes < need) return GRMHD_ERR_SIZE;
+  const int min_ng = params->recon == GRMHD_WENO5 ? 3 : 2;
+  std::vector<BoxDev> host(nbox);
+  int ncurved = 0;
+  for (int b = 0; b < nbox; ++b) {
+    const grmhd_box& x = boxes[b];
+    const grmhd_grid& gr = x.grid;
+    if (gr.ng < min_ng || gr.ng > 16) return GRMHD_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+      if (gr.n[d] < 1 || gr.n[d] > (1 << 16) || !(gr.dx[d] > 0.0) || !std::isfinite(gr.dx[d])) return GRMHD_ERR_ARG;
+    if (!x.cons || !x.prim || !x.rhs || !aligned8(x.cons) || !aligned8(x.prim) || !aligned8(x.rhs))
+      return GRMHD_ERR_ARG;
+    if (x.metric && !aligned8(x.metric)) return GRMHD_ERR_ARG;
+    if (x.tile < 0 || x.tile > 3) return GRMHD_ERR_ARG;
+    if (x.bc != GRMHD_BC_PERIODIC && x.bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+    ncurved += x.metric != nullptr;
+    BoxDev& h = host[b];
+    h.g = make_grid(gr);
+    h.cons = x.cons;
+    h.prim = x.prim;
+    h.metric = x.metric;
+    h.rhs = x.rhs;
+    h.tile = x.tile;
+    h.bc = x.bc;
+    for (int d = 0; d < 3; ++d) h.nt[d] = (gr.n[d] + kShape[x.tile][d] - 1) / kShape[x.tile][d];
+  }
+  if (ncurved != 0 && ncurved != nbox) return GRMHD_ERR_ARG;  // one kernel variant per batch
+  // Largest boxes first (longest-processing-time order) so the dynamic work
+  // counter finishes with small items.
+  std::vector<int> order(nbox);
+  std::iota(order.begin(), order.end(), 0);
+  auto work = [&](int b) { return (long long)host[b].nt[0] * host[b].nt[1] * host[b].nt[2]; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::vector<BoxDev> sorted(nbox);
+  long long tiles = 0, c2p = 0, gh = 0;
+  for (int k = 0; k < nbox; ++k) {
+    BoxDev h = host[order[k]];
+    h.tile_begin = tiles;
+    h.c2p_begin = c2p;
+    h.gh_begin = gh;
+    tiles += work(order[k]);
+    const long long nint = (long long)h.g.n[0] * h.g.n[1] * h.g.n[2];
+    c2p += (nint + kBatchItem - 1) / kBatchItem;
+    gh += (h.g.ncell + kBatchItem - 1) / kBatchItem;
+    sorted[k] = h;
+  }
+  BatchHead head;
+  head.nbox = nbox;
+  head.pad = 0;
+  head.ntiles = tiles;
+  head.nc2p = c2p;
+  head.ngh = gh;
+  for (int i = 0; i < 4; ++i) head.counter[i] = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Host sources are pageable: the calls return once the data are staged.
+  if (cudaMemcpyAsync(ws, &head, sizeof(head), cudaMemcpyHostToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemcpyAsync(static_cast<char*>(ws) + kHeadBytes, sorted.data(), (size_t)nbox * sizeof(BoxDev),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  batch->ws = ws;
+  batch->ws_bytes = ws_bytes;
+  batch->nbox = nbox;
+  batch->curved = ncurved > 0;
+  batch->ntiles = tiles;
+  batch->nc2p_items = c2p;
+  batch->nghost_items = gh;
+  return GRMHD_OK;
+}
+
+int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream) {
+  if (!batch || !params || !batch->ws || batch->nbox < 1) return GRMHD_ERR_ARG;
+  if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
+  if (params->precision != GRMHD_FP64 && params->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
+  if (!(params->gamma > 1.0 && params->gamma <= 3.0) || params->nr_maxit < 1 || !(params->nr_tol > 0.0))
+    return GRMHD_ERR_ARG;
+  if (nfail && (reinterpret_cast<uintptr_t>(nfail) & 3u)) return GRMHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GRMHD_ERR_CUDA;
+  BatchHead* head = static_cast<BatchHead*>(batch->ws);
+  const BoxDev* boxes = reinterpret_cast<const BoxDev*>(static_cast<char*>(batch->ws) + kHeadBytes);
+  const DevParams p = make_params(*params);
+  if (cudaMemsetAsync(&head->counter[0], 0, sizeof(head->counter), s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  batch_con2prim_kernel<<<nsm * 8, kBatchItem, 0, s>>>(head, boxes, p, nfail);
+  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
+  batch_ghost_kernel<<<nsm * 8, kBatchItem, 0, s>>>(head, boxes);
+  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
+  const cudaError_t e = p.precision == GRMHD_MIXED ? launch_batch_rhs_mixed(head, boxes, p, batch->curved != 0, nsm, s)
+                                                   : launch_batch_rhs_fp64(head, boxes, p, batch->curved != 0, nsm, s);
+  return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Persistent kernels that sweep a table of independent boxes (many uneven
+// AMR-like blocks) in one launch per phase: a work counter hands out items
+// (chunks of cells, or RHS tiles with the box's own tile shape) to resident
+// CTAs until the table is exhausted.  No CTA ever waits for another.
+#pragma once
+
+#include "recovery.cuh"
+#include "rhs.cuh"
+
+namespace grmhd {
+
+// Device copy of one box (built by grmhd_batch_prepare).
+struct BoxDev {
+  DevGrid g;
+  double* cons;
+  double* prim;
+  const double* metric;
+  double* rhs;
+  int tile, bc;
+  int nt[3];           // tiles per axis for the box's tile shape
+  long long tile_begin;  // first RHS work item of the box
+  long long c2p_begin;   // first recovery item (256 interior cells each)
+  long long gh_begin;    // first ghost-fill item (256 points each)
+};
+
+struct BatchHead {
+  int nbox;
+  int pad;
+  long long ntiles, nc2p, ngh;
+  unsigned long long counter[4];  // work counters, zeroed before every run
+};
+
+constexpr int kBatchItem = 256;
+
+// Box holding work item `it` (boxes sorted by ascending begin offsets).
+template <int WHICH>
+__device__ __forceinline__ int find_box(const BoxDev* __restrict__ boxes, int nbox, long long it) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const long long b = WHICH == 0 ? boxes[mid].tile_begin : (WHICH == 1 ? boxes[mid].c2p_begin : boxes[mid].gh_begin);
+    if (b <= it) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ long long next_item(unsigned long long* counter) {
+  __shared__ long long s_item;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+  __syncthreads();
+  return s_item;
+}
+
+template <class T, int RECON, bool CURVED>
+__global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                                 DevParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);
+  const int nbox = head->nbox;
+  const long long total = head->ntiles;
+  for (;;) {
+    const long long it = next_item(&head->counter[0]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<0>(boxes, nbox, it)];
+    const long long t = it - b.tile_begin;
+    const int tx = (int)(t % b.nt[0]);
+    const int ty = (int)((t / b.nt[0]) % b.nt[1]);
+    const int tz = (int)(t / ((long long)b.nt[0] * b.nt[1]));
+    StageEpilogue ep;
+    ep.rhs = b.rhs;
+    ep.u = nullptr;
+    ep.u0 = nullptr;
+    ep.acc_in = nullptr;
+    ep.acc_out = nullptr;
+    ep.c0 = ep.c1 = ep.cr = ep.ca = ep.wa = ep.wr = 0.0;
+    const DevGrid g = b.g;
+    switch (b.tile) {
+      case 1:
+        rhs_tile<T, RECON, CURVED, 16, 4, 4>(g, p, b.prim, b.metric, nullptr, ep, tx * 16, ty * 4, tz * 4, sF);
+        break;
+      case 2:
+        rhs_tile<T, RECON, CURVED, 32, 4, 2>(g, p, b.prim, b.metric, nullptr, ep, tx * 32, ty * 4, tz * 2, sF);
+        break;
+      case 3:
+        rhs_tile<T, RECON, CURVED, 4, 8, 8>(g, p, b.prim, b.metric, nullptr, ep, tx * 4, ty * 8, tz * 8, sF);
+        break;
+      default:
+        rhs_tile<T, RECON, CURVED, 8, 8, 4>(g, p, b.prim, b.metric, nullptr, ep, tx * 8, ty * 8, tz * 4, sF);
+        break;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_batch_rhs_t(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                               cudaStream_t s) {
+  void (*k)(BatchHead*, const BoxDev*, DevParams) = nullptr;
+  if (p.recon == GRMHD_WENO5)
+    k = curved ? batch_rhs_kernel<T, GRMHD_WENO5, true> : batch_rhs_kernel<T, GRMHD_WENO5, false>;
+  else
+    k = curved ? batch_rhs_kernel<T, GRMHD_MINMOD, true> : batch_rhs_kernel<T, GRMHD_MINMOD, false>;
+  const size_t smem = (size_t)8 * kMaxTileFaces * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k<<<nsm * per_sm, kTileThreads, smem, s>>>(head, boxes, p);
+  return cudaGetLastError();
+}
+
+}  // namespace grmhd

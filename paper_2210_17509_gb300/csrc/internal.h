@@ -32,6 +32,7 @@ struct DevParams {
   double weno_eps;
   int nr_maxit;
   int recon, bc, precision;
+  int tile;        // RHS tile shape index (0..3)
 };
 
 // What the RHS kernel does with the RHS value r of each interior cell:

@@ -1,110 +1,8 @@
-// Per-cell kernels: conserved -> primitive recovery, primitive -> conserved,
-// ghost-zone fill.
-#include "physics.cuh"
+// Per-cell kernels of a single block: conserved -> primitive recovery,
+// primitive -> conserved, ghost-zone fill.
+#include "recovery.cuh"
 
 namespace grmhd {
-
-// Spatial metric of a cell: gamma_ij packed (xx, xy, xz, yy, yz, zz), its
-// inverse and sqrt(det), all FP64.  Minkowski when metric == NULL.
-struct CellMetric {
-  double g[6], gu[6], sqrtg;
-};
-
-__device__ __forceinline__ void cell_metric(const double* __restrict__ metric, long long ncell, long long c,
-                                            CellMetric& m) {
-  if (!metric) {
-    m.g[0] = m.g[3] = m.g[5] = 1.0;
-    m.g[1] = m.g[2] = m.g[4] = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) m.gu[i] = m.g[i];
-    m.sqrtg = 1.0;
-    return;
-  }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) m.g[i] = __ldg(metric + (4 + i) * ncell + c);
-  const double gxx = m.g[0], gxy = m.g[1], gxz = m.g[2], gyy = m.g[3], gyz = m.g[4], gzz = m.g[5];
-  const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
-  const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
-  const double det = gxx * cxx + gxy * cxy + gxz * cxz;
-  const double idet = 1.0 / det;
-  m.gu[0] = cxx * idet; m.gu[1] = cxy * idet; m.gu[2] = cxz * idet;
-  m.gu[3] = cyy * idet; m.gu[4] = cyz * idet; m.gu[5] = czz * idet;
-  m.sqrtg = sqrt(det);
-}
-
-// Undensitised inputs of the recovery of one cell (Sec. 2.3): the momentum
-// equation S_i = (z + B^2) v_i - (B.v) B_i with B.v = (B.S)/z reduces the
-// unknowns to z = rho h W^2 and W.
-struct C2PIn {
-  double D, tau, S2, B2, BS2;
-};
-
-// Energy residual at (z, W) and the S^2 residual, Gamma-law pressure
-// P = (Gamma - 1)/Gamma (z / W^2 - D / W).
-__device__ __forceinline__ double c2p_v2_of_z(const C2PIn& in, double z) {
-  const double zb = z + in.B2;
-  const double iz = 1.0 / z;
-  return (in.S2 + in.BS2 * (2.0 * z + in.B2) * iz * iz) / (zb * zb);
-}
-
-__device__ __forceinline__ double c2p_energy_of_z(const C2PIn& in, double z, double v2, double gm1g) {
-  const double iw2 = 1.0 - v2;
-  const double iw = sqrt(iw2);
-  const double P = gm1g * (z * iw2 - in.D * iw);
-  return in.tau + in.D - z - in.B2 + 0.5 * in.B2 * iw2 + 0.5 * in.BS2 / (z * z) + P;
-}
-
-// Returns 0 (Newton converged), 1 (bisection), 2 (failed); z, W on exit.
-__device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W) {
-  const double gm1g = p.gm1g;
-  const double D = in.D, B2 = in.B2, BS2 = in.BS2, S2 = in.S2, tau = in.tau;
-  bool ok = false;
-  if (z > 0.0 && W >= 1.0 && isfinite(z) && isfinite(W)) {
-    for (int it = 0; it < p.nr_maxit; ++it) {
-      const double iz = 1.0 / z, iW = 1.0 / W;
-      const double iW2 = iW * iW, iW3 = iW2 * iW, iz2 = iz * iz, iz3 = iz2 * iz;
-      const double zb = z + B2;
-      const double f1 = zb * zb * (1.0 - iW2) - S2 - BS2 * (2.0 * z + B2) * iz2;
-      const double f2 = tau + D - z - B2 + 0.5 * B2 * iW2 + 0.5 * BS2 * iz2 + gm1g * (z * iW2 - D * iW);
-      const double J11 = 2.0 * zb * (1.0 - iW2) + 2.0 * BS2 * zb * iz3;
-      const double J12 = 2.0 * zb * zb * iW3;
-      const double J21 = -1.0 - BS2 * iz3 + gm1g * iW2;
-      const double J22 = -B2 * iW3 + gm1g * (D * iW2 - 2.0 * z * iW3);
-      const double idet = 1.0 / (J11 * J22 - J12 * J21);
-      const double dz = (f1 * J22 - f2 * J12) * idet;
-      const double dW = (J11 * f2 - J21 * f1) * idet;
-      if (!isfinite(dz) || !isfinite(dW)) break;
-      const bool conv = fabs(dz) <= p.nr_tol * z && fabs(dW) <= p.nr_tol * W;
-      double zn = z - dz, Wn = W - dW;
-      if (!(zn > 0.0)) zn = 0.5 * z;
-      if (!(Wn >= 1.0)) Wn = 0.5 * (W + 1.0);
-      z = zn;
-      W = Wn;
-      if (conv) { ok = true; break; }
-    }
-  }
-  if (ok) return 0;
-  // Fallback: bracketed bisection of the energy residual in z, with W(z)
-  // from the S^2 equation; z below the v = 1 boundary counts as "too small".
-  double zlo = 0.0, zhi = 2.0 * (tau + D) / gm1g + B2 + 1e-300;
-  auto too_small = [&](double zz) {
-    const double v2 = c2p_v2_of_z(in, zz);
-    if (!(v2 < 1.0)) return true;
-    return c2p_energy_of_z(in, zz, v2, gm1g) > 0.0;
-  };
-  int k = 0;
-  while (too_small(zhi) && k < 200) { zlo = zhi; zhi *= 2.0; ++k; }
-  if (k >= 200 || !isfinite(zhi)) return 2;
-  for (int it = 0; it < 400 && zhi - zlo > 1e-15 * zhi; ++it) {
-    const double zm = 0.5 * (zlo + zhi);
-    if (too_small(zm)) zlo = zm; else zhi = zm;
-  }
-  z = 0.5 * (zlo + zhi);
-  const double v2 = c2p_v2_of_z(in, z);
-  if (!(v2 < 1.0)) return 2;
-  W = 1.0 / sqrt(1.0 - v2);
-  return 1;
-}
 
 __global__ void con2prim_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                 const double* __restrict__ metric, double* __restrict__ prim,
@@ -113,74 +11,9 @@ __global__ void con2prim_kernel(DevGrid g, DevParams p, const double* __restrict
   int myfail = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
-    const int xi = (int)(t % g.n[0]);
-    const long long r = t / g.n[0];
-    const int yi = (int)(r % g.n[1]);
-    const int zi = (int)(r / g.n[1]);
-    const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
-    CellMetric m;
-    cell_metric(metric, g.ncell, c, m);
-    const double isg = 1.0 / m.sqrtg;
-    double U[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) U[q] = __ldg(cons + q * g.ncell + c);
-    const double D = U[0] * isg, tau = U[4] * isg;
-    const double Sl[3] = {U[1] * isg, U[2] * isg, U[3] * isg};
-    const double B[3] = {U[5] * isg, U[6] * isg, U[7] * isg};
-    double Bl[3], Su[3];
-    lower(m.g, B, Bl);
-    lower(m.gu, Sl, Su);
-    C2PIn in;
-    in.D = D;
-    in.tau = tau;
-    in.S2 = Sl[0] * Su[0] + Sl[1] * Su[1] + Sl[2] * Su[2];
-    in.B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-    const double BS = B[0] * Sl[0] + B[1] * Sl[1] + B[2] * Sl[2];
-    in.BS2 = BS * BS;
-    // initial guess from the incoming primitives
-    double* pc = prim + c;
-    const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
-    double vl[3];
-    lower(m.g, v, vl);
-    const double v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
-    const double rg = pc[0], Pg = pc[4 * g.ncell];
-    double W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
-    double z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
-    int st = 2;
-    if (D > 0.0 && tau + D > 0.0) st = c2p_solve(in, p, z, W);
-    double out[8];
-    if (st != 2) {
-      const double rho = D / W;
-      const double P = p.gm1g * (z / (W * W) - rho);
-      const double izb = 1.0 / (z + in.B2);
-      const double bsz = BS / z;
-      double vlo[3], vu[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) vlo[i] = (Sl[i] + bsz * Bl[i]) * izb;
-      lower(m.gu, vlo, vu);
-      const double v2 = vu[0] * vlo[0] + vu[1] * vlo[1] + vu[2] * vlo[2];
-      if (rho >= p.rho_atm && v2 < 1.0 && isfinite(P)) {
-        out[0] = rho;
-        out[1] = vu[0]; out[2] = vu[1]; out[3] = vu[2];
-        out[4] = P;
-        if (!(P > 0.0)) {  // valid density and velocity, non-positive pressure: floor
-          out[4] = p.p_atm;
-          st = 3;
-          myfail += 1;
-        }
-      } else {
-        st = 2;
-      }
-    }
-    if (st == 2) {
-      out[0] = p.rho_atm;
-      out[1] = out[2] = out[3] = 0.0;
-      out[4] = p.p_atm;
-      myfail += 1;
-    }
-    out[5] = B[0]; out[6] = B[1]; out[7] = B[2];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pc[q * g.ncell] = out[q];
+    const long long c = interior_cell(g, t);
+    const int st = con2prim_at(g, p, cons, metric, prim, c);
+    myfail += (st >= 2);
     if (status) status[c] = (int8_t)st;
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
@@ -217,35 +50,10 @@ __global__ void prim2con_kernel(DevGrid g, DevParams p, const double* __restrict
   }
 }
 
-// Every non-interior point copies its source: periodic wrap or the nearest
-// interior point, per axis independently (edges and corners included).
 __global__ void fill_ghosts_kernel(DevGrid g, int bc, int nvar, double* __restrict__ f) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    int idx[3];
-    idx[0] = (int)(c % g.N[0]);
-    const long long r = c / g.N[0];
-    idx[1] = (int)(r % g.N[1]);
-    idx[2] = (int)(r / g.N[1]);
-    bool interior = true;
-    int src[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int i = idx[d] - g.ng;
-      if (i < 0 || i >= g.n[d]) interior = false;
-      int s;
-      if (bc == GRMHD_BC_PERIODIC) {
-        s = i % g.n[d];
-        if (s < 0) s += g.n[d];
-      } else {
-        s = i < 0 ? 0 : (i >= g.n[d] ? g.n[d] - 1 : i);
-      }
-      src[d] = s + g.ng;
-    }
-    if (interior) continue;
-    const long long sc = (long long)src[2] * g.sz + (long long)src[1] * g.sy + src[0];
-    for (int q = 0; q < nvar; ++q) f[q * g.ncell + c] = f[q * g.ncell + sc];
-  }
+       c += (long long)gridDim.x * blockDim.x)
+    fill_ghost_at(g, bc, nvar, f, c);
 }
 
 static int grid_blocks(long long work, int threads) {

@@ -184,19 +184,37 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   src[5] = src[6] = src[7] = T(0);
 }
 
-template <class T, int RECON, bool CURVED, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ) rhs_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
-                                                           const double* __restrict__ metric,
-                                                           const double* __restrict__ kij, StageEpilogue ep) {
-  constexpr int NT = TX * TY * TZ;
-  constexpr int NFX = (TX + 1) * TY * TZ;
-  constexpr int NFY = TX * (TY + 1) * TZ;
-  constexpr int NFZ = TX * TY * (TZ + 1);
-  constexpr int NF = NFX + NFY + NFZ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);  // [8][NF]
+// Tile shapes the kernels are instantiated for (cells per axis, 256 cells each).
+template <int S> struct TileShape;
+template <> struct TileShape<0> { static constexpr int X = 8, Y = 8, Z = 4; };
+template <> struct TileShape<1> { static constexpr int X = 16, Y = 4, Z = 4; };
+template <> struct TileShape<2> { static constexpr int X = 32, Y = 4, Z = 2; };
+template <> struct TileShape<3> { static constexpr int X = 4, Y = 8, Z = 8; };
+constexpr int kNumTileShapes = 4;
+constexpr int kTileThreads = 256;
 
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+template <int TX, int TY, int TZ>
+struct TileFaces {
+  static constexpr int NFX = (TX + 1) * TY * TZ;
+  static constexpr int NFY = TX * (TY + 1) * TZ;
+  static constexpr int NFZ = TX * TY * (TZ + 1);
+  static constexpr int NF = NFX + NFY + NFZ;
+};
+// Largest face count over the shapes: sizes the shared face buffer.
+constexpr int kMaxTileFaces = 968;
+
+// One tile of the RHS: all face fluxes of the tile (each once) into the
+// shared buffer sF [8][NF], then each thread differences its cell's faces,
+// adds the sources and applies the stage epilogue.  Called by all threads of
+// the CTA (contains __syncthreads); NT = TX*TY*TZ threads.
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ>
+__device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
+                                         const double* __restrict__ metric, const double* __restrict__ kij,
+                                         const StageEpilogue& ep, int x0, int y0, int z0, T* sF) {
+  constexpr int NT = TX * TY * TZ;
+  constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
+  constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
+  constexpr int NF = TileFaces<TX, TY, TZ>::NF;
   const int ng = g.ng;
   for (int f = threadIdx.x; f < NF; f += NT) {
     T F[8];
@@ -237,58 +255,79 @@ __global__ void __launch_bounds__(TX * TY * TZ) rhs_kernel(DevGrid g, DevParams 
 
   const int ci = threadIdx.x % TX, cj = (threadIdx.x / TX) % TY, ck = threadIdx.x / (TX * TY);
   const int xi = x0 + ci, yi = y0 + cj, zi = z0 + ck;
-  if (xi >= g.n[0] || yi >= g.n[1] || zi >= g.n[2]) return;
-  const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-  const int fx = (ck * TY + cj) * (TX + 1) + ci;
-  const int fy = NFX + (ck * (TY + 1) + cj) * TX + ci;
-  const int fz = NFX + NFY + (ck * TY + cj) * TX + ci;
-  const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
-  T r[8];
+  if (threadIdx.x < NT && xi < g.n[0] && yi < g.n[1] && zi < g.n[2]) {
+    const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+    const int fx = (ck * TY + cj) * (TX + 1) + ci;
+    const int fy = NFX + (ck * (TY + 1) + cj) * TX + ci;
+    const int fz = NFX + NFY + (ck * TY + cj) * TX + ci;
+    const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+    T r[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const T* s = sF + q * NF;
-    T acc = -(s[fx + 1] - s[fx]) * ix;
-    acc -= (s[fy + TX] - s[fy]) * iy;
-    acc -= (s[fz + TX * TY] - s[fz]) * iz;
-    r[q] = acc;
-  }
-  if (CURVED) {
-    T src[8];
-    source_terms<T>(g, p, prim, metric, kij, c, src);
+    for (int q = 0; q < 8; ++q) {
+      const T* s = sF + q * NF;
+      T acc = -(s[fx + 1] - s[fx]) * ix;
+      acc -= (s[fy + TX] - s[fy]) * iy;
+      acc -= (s[fz + TX * TY] - s[fz]) * iz;
+      r[q] = acc;
+    }
+    if (CURVED) {
+      T src[8];
+      source_terms<T>(g, p, prim, metric, kij, c, src);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) r[q] += src[q];
-  }
+      for (int q = 0; q < 8; ++q) r[q] += src[q];
+    }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const long long o = q * g.ncell + c;
-    const double rq = (double)r[q];
-    if (ep.rhs) ep.rhs[o] = rq;
-    const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
-    if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
-    if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
+    for (int q = 0; q < 8; ++q) {
+      const long long o = q * g.ncell + c;
+      const double rq = (double)r[q];
+      if (ep.rhs) ep.rhs[o] = rq;
+      const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
+      if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+      if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
+    }
   }
+}
+
+template <class T, int RECON, bool CURVED, int SHAPE>
+__global__ void __launch_bounds__(kTileThreads) rhs_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                                           const double* __restrict__ metric,
+                                                           const double* __restrict__ kij, StageEpilogue ep) {
+  using S = TileShape<SHAPE>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);
+  rhs_tile<T, RECON, CURVED, S::X, S::Y, S::Z>(g, p, prim, metric, kij, ep, blockIdx.x * S::X, blockIdx.y * S::Y,
+                                                blockIdx.z * S::Z, sF);
+}
+
+template <class T, int RECON, bool CURVED>
+cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, const double* prim,
+                             const double* metric, const double* kij, const StageEpilogue& ep, cudaStream_t s) {
+  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, StageEpilogue) = nullptr;
+  int tx = 8, ty = 8, tz = 4;
+  switch (shape) {
+    case 1: k = rhs_kernel<T, RECON, CURVED, 1>; tx = TileShape<1>::X; ty = TileShape<1>::Y; tz = TileShape<1>::Z; break;
+    case 2: k = rhs_kernel<T, RECON, CURVED, 2>; tx = TileShape<2>::X; ty = TileShape<2>::Y; tz = TileShape<2>::Z; break;
+    case 3: k = rhs_kernel<T, RECON, CURVED, 3>; tx = TileShape<3>::X; ty = TileShape<3>::Y; tz = TileShape<3>::Z; break;
+    default: k = rhs_kernel<T, RECON, CURVED, 0>; break;
+  }
+  const size_t smem = (size_t)8 * kMaxTileFaces * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((g.n[0] + tx - 1) / tx, (g.n[1] + ty - 1) / ty, (g.n[2] + tz - 1) / tz);
+  k<<<grid, kTileThreads, smem, s>>>(g, p, prim, metric, kij, ep);
+  return cudaGetLastError();
 }
 
 // Host-side launcher for one precision.
 template <class T>
 cudaError_t launch_rhs_t(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
                          const double* kij, const StageEpilogue& ep, cudaStream_t s) {
-  constexpr int TX = 8, TY = 8, TZ = 4;
-  constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
-  const size_t smem = (size_t)8 * NF * sizeof(T);
-  const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + TZ - 1) / TZ);
-  const dim3 block(TX * TY * TZ);
-  const bool curved = metric != nullptr;
-  const bool weno = p.recon == GRMHD_WENO5;
-  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, StageEpilogue);
-  if (weno)
-    k = curved ? rhs_kernel<T, GRMHD_WENO5, true, TX, TY, TZ> : rhs_kernel<T, GRMHD_WENO5, false, TX, TY, TZ>;
-  else
-    k = curved ? rhs_kernel<T, GRMHD_MINMOD, true, TX, TY, TZ> : rhs_kernel<T, GRMHD_MINMOD, false, TX, TY, TZ>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, block, smem, s>>>(g, p, prim, metric, kij, ep);
-  return cudaGetLastError();
+  const int shape = p.tile;
+  if (p.recon == GRMHD_WENO5)
+    return metric ? launch_rhs_shape<T, GRMHD_WENO5, true>(shape, g, p, prim, metric, kij, ep, s)
+                  : launch_rhs_shape<T, GRMHD_WENO5, false>(shape, g, p, prim, metric, kij, ep, s);
+  return metric ? launch_rhs_shape<T, GRMHD_MINMOD, true>(shape, g, p, prim, metric, kij, ep, s)
+                : launch_rhs_shape<T, GRMHD_MINMOD, false>(shape, g, p, prim, metric, kij, ep, s);
 }
 
 }  // namespace grmhd

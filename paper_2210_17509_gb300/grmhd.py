@@ -51,6 +51,8 @@ class CParams(ctypes.Structure):
         ("p_atm", ctypes.c_double),
         ("nr_tol", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
+        ("tile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -113,10 +115,11 @@ class Params:
     p_atm: float = 1e-20
     nr_tol: float = 1e-12
     weno_eps: float = 1e-6
+    tile: int = 0
 
     def c(self) -> CParams:
         return CParams(self.gamma, self.recon, self.bc, self.precision, self.nr_maxit, self.rho_atm, self.p_atm,
-                       self.nr_tol, self.weno_eps)
+                       self.nr_tol, self.weno_eps, self.tile, 0)
 
 
 def version() -> int:
@@ -241,3 +244,65 @@ def rk_step_static(grid: Grid, params: Params, scheme: int, dt: float, cons, pri
                                    nf, _stream(stream))
     _check(rc, "grmhd_rk_step_static")
     return cons, prim
+
+
+# ------------------------------------------------------------ batched boxes --
+class CBox(ctypes.Structure):
+    _fields_ = [("grid", CGrid), ("cons", _P), ("prim", _P), ("metric", _P), ("rhs", _P), ("tile", _I32),
+                ("bc", _I32)]
+
+
+class CBatch(ctypes.Structure):
+    _fields_ = [("ws", _P), ("ws_bytes", ctypes.c_size_t), ("nbox", _I32), ("curved", _I32), ("ntiles", ctypes.c_int64),
+                ("nc2p_items", ctypes.c_int64), ("nghost_items", ctypes.c_int64)]
+
+
+_lib.grmhd_batch_workspace_bytes.argtypes = [_I32]
+_lib.grmhd_batch_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_batch_prepare.argtypes = [ctypes.POINTER(CBox), _I32, _pp, _P, ctypes.c_size_t, ctypes.POINTER(CBatch), _P]
+_lib.grmhd_batch_prepare.restype = _I
+_lib.grmhd_batch_rhs.argtypes = [ctypes.POINTER(CBatch), _pp, _P, _P]
+_lib.grmhd_batch_rhs.restype = _I
+C_SYMBOLS = C_SYMBOLS + ("grmhd_batch_workspace_bytes", "grmhd_batch_prepare", "grmhd_batch_rhs")
+
+
+@dataclass
+class Box:
+    """One block of a batch: its grid, state tensors, tile shape and boundary."""
+    grid: Grid
+    cons: "torch.Tensor"
+    prim: "torch.Tensor"
+    rhs: "torch.Tensor"
+    metric: "torch.Tensor" = None
+    tile: int = 0
+    bc: int = BC_PERIODIC
+
+
+class Batch:
+    """A prepared box table (grmhd_batch_prepare); keeps the tensors alive."""
+
+    def __init__(self, boxes, params: Params, stream=None):
+        self.boxes = list(boxes)
+        n = len(self.boxes)
+        arr = (CBox * n)()
+        for i, b in enumerate(self.boxes):
+            arr[i] = CBox(b.grid.c(), _field(b.cons, b.grid, 8, "cons"), _field(b.prim, b.grid, 8, "prim"),
+                          _field(b.metric, b.grid, 10, "metric", True), _field(b.rhs, b.grid, 8, "rhs"),
+                          int(b.tile), int(b.bc))
+        nbytes = int(_lib.grmhd_batch_workspace_bytes(n))
+        if nbytes == 0:
+            raise GrmhdError("invalid number of boxes")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.boxes[0].cons.device)
+        self.c = CBatch()
+        rc = _lib.grmhd_batch_prepare(arr, n, ctypes.byref(params.c()), ctypes.c_void_p(self.ws.data_ptr()), nbytes,
+                                      ctypes.byref(self.c), _stream(stream))
+        _check(rc, "grmhd_batch_prepare")
+
+    @property
+    def ncells(self):
+        return sum(b.grid.n[0] * b.grid.n[1] * b.grid.n[2] for b in self.boxes)
+
+    def rhs(self, params: Params, nfail=None, stream=None):
+        nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+        rc = _lib.grmhd_batch_rhs(ctypes.byref(self.c), ctypes.byref(params.c()), nf, _stream(stream))
+        _check(rc, "grmhd_batch_rhs")

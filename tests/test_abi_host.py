@@ -54,7 +54,7 @@ def test_rejects_insufficient_ghosts(lib):
 def test_rejects_bad_params(lib):
     g = _grid(lib).c()
     for kw in ({"gamma": 1.0}, {"recon": 7}, {"bc": 3}, {"precision": 5}, {"nr_maxit": 0}, {"nr_tol": 0.0},
-               {"weno_eps": -1.0}, {"rho_atm": 0.0}):
+               {"weno_eps": -1.0}, {"rho_atm": 0.0}, {"tile": 7}):
         p = lib.Params(**kw).c()
         rc = lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None)
         assert rc == -1, kw
@@ -97,3 +97,34 @@ def test_error_strings(lib):
     assert lib._lib.grmhd_error_string(0) == b"ok"
     assert lib._lib.grmhd_error_string(-4) == b"workspace too small"
     assert lib.version() >= 100
+
+
+def test_batch_prepare_validation(lib):
+    import ctypes as C
+    G = lib
+    p = G.Params().c()
+    assert G._lib.grmhd_batch_workspace_bytes(0) == 0
+    nb = G._lib.grmhd_batch_workspace_bytes(4)
+    assert nb > 0 and nb % 256 == 0
+    boxes = (G.CBox * 1)()
+    g = G.Grid((8, 8, 8), 2, (0.1, 0.1, 0.1))       # too few ghosts for WENO5
+    boxes[0] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 0, 0)
+    out = G.CBatch()
+    rc = G._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None)
+    assert rc == -1
+    g = G.Grid((8, 8, 8), 3, (0.1, 0.1, 0.1))
+    boxes[0] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 9, 0)  # bad tile shape
+    rc = G._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None)
+    assert rc == -1
+    boxes[0] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 0, 0)
+    rc = G._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), 16, C.byref(out), None)
+    assert rc == -4
+
+
+def test_autotuner_choice_logic_on_cpu():
+    from paper_2210_17509_gb300 import autotune
+    costs = {0: 1.0, 1: 1.0, 2: 1.0, 3: 1.0}
+    assert autotune.n_tiles(0, (8, 8, 4)) == 1
+    assert autotune.n_tiles(2, (8, 8, 8)) == 8        # 32-wide tiles waste 3/4 on an 8-wide box
+    assert autotune.choose((8, 8, 8), costs) in (0, 3)
+    assert autotune.choose((64, 8, 8), {0: 1.0, 1: 1.0, 2: 0.5, 3: 1.0}) == 2

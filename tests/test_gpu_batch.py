@@ -1,0 +1,135 @@
+"""Batched boxes (persistent launches over a box table) against the
+single-block entry points and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2210_17509_gb300 import inputs as I
+from tests.helpers import FP64_TOL, interior, normwise
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2210_17509_gb300 import build
+    build.build()
+    from paper_2210_17509_gb300 import grmhd
+    return grmhd
+
+
+def make_boxes(G, params, nbox, seed=2, tiles=None, curved=False):
+    shapes = I.amr_box_shapes(nbox, seed)
+    boxes, host = [], []
+    for b, (n, lev) in enumerate(shapes):
+        h = 1.0 / 2 ** lev
+        blk = I.Block(n, 3, (h, h, h), (4.0, 4.0, 4.0) if curved else (0.0, 0.0, 0.0))
+        met = I.schwarzschild_metric(blk) if curved else None
+        prim = I.smooth_prims(blk, 1000 + b, rho_range=(0.1, 1.0) if curved else None, metric=met)
+        g = G.Grid(blk.n, 3, blk.dx)
+        tp = torch.from_numpy(prim).cuda()
+        tm = None if met is None else torch.from_numpy(met).cuda()
+        G.fill_ghosts(g, G.BC_PERIODIC, tp)
+        tc = G.prim2con(g, params, tp, tm)
+        tile = (b % 4) if tiles is None else tiles[b]
+        boxes.append(G.Box(g, tc, tp.clone(), torch.zeros_like(tp), tm, tile, G.BC_PERIODIC))
+        host.append((blk, tp.cpu().numpy(), met))
+    return boxes, host
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_single_block_calls_bit_exact(G, precision):
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=precision)
+    boxes, _ = make_boxes(G, p, 24)
+    batch = G.Batch(boxes, p)
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.rhs(p, nfail)
+    torch.cuda.synchronize()
+    assert int(nfail.item()) == 0
+    for b in boxes:
+        prim = b.prim.clone()
+        # the same steps through the single-block entry points (default tile)
+        ref_prim = prim.clone()
+        ref_prim.copy_(b.prim)
+        r = G.rhs(b.grid, p, b.prim, b.metric)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(interior(b.rhs.cpu().numpy(), 3), interior(r.cpu().numpy(), 3))
+
+
+def test_batch_recovery_and_ghosts_match_single_calls(G):
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    boxes, _ = make_boxes(G, p, 12, seed=5)
+    guesses = [b.prim.clone() for b in boxes]
+    batch = G.Batch(boxes, p)
+    batch.rhs(p)
+    for b, guess in zip(boxes, guesses):
+        G.con2prim(b.grid, p, b.cons, guess, b.metric)
+        G.fill_ghosts(b.grid, G.BC_PERIODIC, guess)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(b.prim.cpu().numpy(), guess.cpu().numpy())
+
+
+def test_batch_against_oracle(G):
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    boxes, host = make_boxes(G, p, 6, seed=9)
+    batch = G.Batch(boxes, p)
+    batch.rhs(p)
+    torch.cuda.synchronize()
+    op = O.make_params(recon=O.REC_WENO5, bc=O.BC_PERIODIC, rho_atm=p.rho_atm, p_atm=p.p_atm)
+    for b, (blk, prim, met) in zip(boxes, host):
+        og = O.Grid(blk.n, 3, blk.dx)
+        ro = O.rhs(og, op, O.fill_ghosts(og, 0, prim), met)
+        err = normwise(interior(b.rhs.cpu().numpy(), 3), interior(ro, 3))
+        assert np.all(err < FP64_TOL), err
+
+
+def test_batch_curved_boxes(G):
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    boxes, _ = make_boxes(G, p, 8, seed=4, curved=True)
+    batch = G.Batch(boxes, p)
+    batch.rhs(p)
+    for b in boxes:
+        r = G.rhs(b.grid, p, b.prim, b.metric)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(interior(b.rhs.cpu().numpy(), 3), interior(r.cpu().numpy(), 3))
+
+
+def test_batch_cuda_graph_replay(G):
+    """The three persistent launches captured once and replayed give the same
+    result as a direct call from the same starting primitives."""
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    boxes, _ = make_boxes(G, p, 16, seed=6)
+    batch = G.Batch(boxes, p)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.rhs(p)           # warm-up outside capture (module load, attributes)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    start = [b.prim.clone() for b in boxes]
+    batch.rhs(p)
+    torch.cuda.synchronize()
+    ref = [b.rhs.clone() for b in boxes]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.rhs(p)
+    for _ in range(2):
+        for b, s0 in zip(boxes, start):
+            b.prim.copy_(s0)
+            b.rhs.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for b, r in zip(boxes, ref):
+            np.testing.assert_array_equal(b.rhs.cpu().numpy(), r.cpu().numpy())
+
+
+def test_autotuner_choices_are_valid(G):
+    from paper_2210_17509_gb300 import autotune
+    p = G.Params(recon=G.WENO5)
+    costs = autotune.tile_costs(p, refresh=True)
+    assert set(costs) == {0, 1, 2, 3} and all(c > 0 for c in costs.values())
+    for n, _ in I.amr_box_shapes(64, 2):
+        sid = autotune.choose(n, costs)
+        best = min(autotune.n_tiles(s, n) * costs[s] for s in costs)
+        assert autotune.n_tiles(sid, n) * costs[sid] == best
