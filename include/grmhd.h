@@ -205,6 +205,69 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
  * captured into a CUDA graph.  nfail as for grmhd_con2prim. */
 int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream);
 
+/* ----------------------------------------------------------------------
+ * Reverse mode (adjoint) of the FP64 method, hand-written.  The paper has no
+ * adjoint; these are the transposes of the forward entry points above, so
+ * that gradients of a functional of the evolved state with respect to the
+ * initial primitives and Gamma can be accumulated backwards through a
+ * checkpointed sequence of grmhd_rk_step calls.  All require
+ * params->precision == GRMHD_FP64.  "Accumulated" outputs are added to.
+ * ---------------------------------------------------------------------- */
+
+/* prim_bar += (d rhs / d prim)^T rhs_bar, gamma_bar += (d rhs / d Gamma)^T rhs_bar.
+ *   prim      in   8 x ncell, ghosts filled (the RHS input)
+ *   rhs_bar   in   8 x ncell, interior read
+ *   prim_bar  acc  8 x ncell, ghost entries included (they receive the
+ *                  adjoint of the stencil reads; see grmhd_fill_ghosts_adjoint)
+ *   gamma_bar acc  one device double
+ * Contributions are added with atomics; the summation order varies. */
+int grmhd_rhs_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                      const double* metric, const double* kij, const double* rhs_bar, double* prim_bar,
+                      double* gamma_bar, void* stream);
+
+/* Adjoint of the primitive recovery at its solution prim (interior): the
+ * recovery inverts prim -> cons (Eqs. 6-9), so cons_bar += (dU/dP)^{-T}
+ * prim_bar and gamma_bar -= cons_bar_added . dU/dGamma (implicit function
+ * theorem).  nsingular (device int32, nullable) counts cells whose Jacobian
+ * could not be inverted (their contribution is skipped). */
+int grmhd_con2prim_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                           const double* metric, const double* prim_bar, double* cons_bar,
+                           double* gamma_bar, int32_t* nsingular, void* stream);
+
+/* Adjoint of grmhd_prim2con on the interior: prim_bar += (dU/dP)^T cons_bar,
+ * gamma_bar += cons_bar . dU/dGamma. */
+int grmhd_prim2con_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                           const double* metric, const double* cons_bar, double* prim_bar,
+                           double* gamma_bar, void* stream);
+
+/* Transpose of grmhd_fill_ghosts: every ghost entry of field_bar is added to
+ * the interior entry it was copied from, then set to zero. */
+int grmhd_fill_ghosts_adjoint(const grmhd_grid* grid, int32_t bc, int32_t nvar, double* field_bar,
+                              void* stream);
+
+/* Functional L = sum over interior cells of rho^2 sqrt(gamma) dx dy dz:
+ * loss (device double, nullable) += L; prim_bar (nullable) += lbar dL/dprim. */
+int grmhd_density_l2(const grmhd_grid* grid, const double* prim, const double* metric, double lbar,
+                     double* loss, double* prim_bar, void* stream);
+
+/* Bytes of workspace for grmhd_rk_step_adjoint (RK2 / RK3; 0 otherwise). */
+size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
+
+/* Reverse of one grmhd_rk_step (SSP RK2 or RK3) taken from (cons, prim):
+ * recomputes the stages, then sweeps them backwards.
+ *   cons, prim  in      the step's inputs (prim ghosts filled), unchanged
+ *   cons_bar    in/out  adjoint of the step's output U (interior) on entry,
+ *                       adjoint of the input U on exit
+ *   prim_bar    in/out  adjoint of the step's output primitives (8 x ncell,
+ *                       ghost entries included) on entry; adjoint of the
+ *                       input primitives (ghost entries included) on exit
+ *   gamma_bar   acc     one device double
+ *   ws          >= grmhd_rk_adjoint_workspace_bytes, 256-byte aligned */
+int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                          const double* cons, const double* prim, const double* metric, const double* kij,
+                          double* cons_bar, double* prim_bar, double* gamma_bar, void* ws, size_t ws_bytes,
+                          void* stream);
+
 /* Size of the library-owned scratch of grmhd_rk_step_static: 64 MiB. */
 #define GRMHD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -1,0 +1,1093 @@
+// Hand-written reverse mode of the FP64 method-of-lines step.
+//
+// Pieces (each the transpose of a forward kernel of this library):
+//   * face adjoint: per face, recompute the reconstruction, the two face
+//     states and the HLLE flux, then propagate the flux adjoint
+//     Fbar = (Lbar_c - Lbar_{c-1}) / dx back through HLLE, the 3+1 state
+//     formulas (Eqs. 6-9, 12, signal speeds) and WENO5 / minmod into the six
+//     stencil cells (FP64 atomics) and into Gamma;
+//   * source adjoint (curved metric): per cell, forward-mode dual numbers over
+//     the 8 primitives and Gamma through the Eq. 13 source, transposed;
+//   * con2prim adjoint: the recovery is the inverse of prim -> cons, so its
+//     adjoint solves (dU/dP)^T x = Pbar (implicit function theorem) with
+//     dU/dP from dual numbers; prim -> cons adjoint multiplies by (dU/dP)^T;
+//   * ghost-fill adjoint: every ghost point's adjoint is added to its source
+//     interior point;
+//   * the RK step reverse (SSP RK2 / RK3): recompute the stages, then sweep
+//     them backwards.
+#include <cmath>
+
+#include "recovery.cuh"
+#include "rhs.cuh"
+
+namespace grmhd {
+
+// ------------------------------------------------------------ dual numbers
+// Forward-mode number with N derivative lanes (for per-cell 8x8 Jacobians).
+template <int N>
+struct Dn {
+  double v;
+  double d[N];
+  __device__ Dn() {}
+  __device__ Dn(double x) : v(x) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = 0.0;
+  }
+};
+template <int N> __device__ __forceinline__ Dn<N> operator+(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator-(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator-(const Dn<N>& a) {
+  Dn<N> r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator/(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r; r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator*(double a, const Dn<N>& b) {
+  Dn<N> r; r.v = a * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a * b.d[i];
+  return r;
+}
+template <int N> __device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, double b) { return b * a; }
+template <int N> __device__ __forceinline__ Dn<N>& operator+=(Dn<N>& a, const Dn<N>& b) { a = a + b; return a; }
+template <int N> __device__ __forceinline__ Dn<N>& operator-=(Dn<N>& a, const Dn<N>& b) { a = a - b; return a; }
+template <int N> __device__ __forceinline__ Dn<N> xsqrt(const Dn<N>& a) {
+  Dn<N> r; r.v = sqrt(a.v);
+  const double s = r.v > 0.0 ? 0.5 / r.v : 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+
+typedef Dn<9> D9;  // lanes 0..7: primitives, lane 8: Gamma
+
+// Packed index of the symmetric pair (i, j) in [xx, xy, xz, yy, yz, zz].
+__device__ __forceinline__ int sym_index(int i, int j) {
+  const int a = i < j ? i : j, b = i < j ? j : i;
+  return a == 0 ? b : (a == 1 ? 2 + b : 5);
+}
+
+// Conserved vector of one primitive state (Eqs. 6-9), generic scalar.
+template <class T>
+__device__ __forceinline__ void cons_of_prim(const T pr[8], const double g[6], double sg, T gfac, T U[8]) {
+  const T v[3] = {pr[1], pr[2], pr[3]};
+  const T B[3] = {pr[5], pr[6], pr[7]};
+  T vl[3], Bl[3];
+  vl[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+  vl[1] = g[1] * v[0] + g[3] * v[1] + g[4] * v[2];
+  vl[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
+  Bl[0] = g[0] * B[0] + g[1] * B[1] + g[2] * B[2];
+  Bl[1] = g[1] * B[0] + g[3] * B[1] + g[4] * B[2];
+  Bl[2] = g[2] * B[0] + g[4] * B[1] + g[5] * B[2];
+  const T v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const T omv2 = T(1.0) - v2;
+  const T iW = xsqrt(omv2);
+  const T W = T(1.0) / iW;
+  const T ab0 = W * Bv;
+  const T b2 = B2 * omv2 + Bv * Bv;
+  const T hs = pr[0] + gfac * pr[4] + b2;
+  const T Ps = pr[4] + T(0.5) * b2;
+  const T hW2 = hs * W * W;
+  const T D = T(sg) * pr[0] * W;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) U[1 + i] = T(sg) * (hW2 * vl[i] - ab0 * (Bl[i] * iW + ab0 * vl[i]));
+  U[0] = D;
+  U[4] = T(sg) * (hW2 - Ps - ab0 * ab0) - D;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) U[5 + i] = T(sg) * B[i];
+}
+
+// J[i][j] = dU_i / dP_j (j < 8) and dU_i / dGamma (j = 8) at the cell c.
+__device__ __forceinline__ void cons_jacobian(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
+                                              const double* __restrict__ metric, long long c, double J[8][9]) {
+  CellMetric m;
+  cell_metric(metric, g.ncell, c, m);
+  D9 pr[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    pr[q] = D9(__ldg(prim + q * g.ncell + c));
+    pr[q].d[q] = 1.0;
+  }
+  D9 gf(p.gfac);
+  gf.d[8] = -1.0 / ((p.gamma - 1.0) * (p.gamma - 1.0));  // d/dGamma of Gamma/(Gamma-1)
+  D9 U[8];
+  cons_of_prim<D9>(pr, m.g, m.sqrtg, gf, U);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) J[i][j] = U[i].d[j];
+}
+
+// Solve A^T x = b (8x8, partial pivoting) in place: b becomes x.
+__device__ __forceinline__ bool solve_transposed8(const double J[8][9], double b[8]) {
+  double a[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[r][c] = J[c][r];  // A^T
+  for (int c = 0; c < 8; ++c) {
+    int piv = c;
+    double best = fabs(a[c][c]);
+    for (int r = c + 1; r < 8; ++r)
+      if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); piv = r; }
+    if (!(best > 0.0)) return false;
+    if (piv != c) {
+      for (int k = 0; k < 8; ++k) { const double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t; }
+      const double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    const double ip = 1.0 / a[c][c];
+    for (int r = c + 1; r < 8; ++r) {
+      const double f = a[r][c] * ip;
+      if (f != 0.0) {
+        for (int k = c; k < 8; ++k) a[r][k] -= f * a[c][k];
+        b[r] -= f * b[c];
+      }
+    }
+  }
+  for (int r = 7; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < 8; ++k) s -= a[r][k] * b[k];
+    b[r] = s / a[r][r];
+  }
+  return true;
+}
+
+__device__ __forceinline__ void block_add_gamma(double v, double* gamma_bar) {
+  // warp reduction, then one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gamma_bar, v);
+}
+
+// ---------------------------------------------------- con2prim / prim2con
+// cons_bar += (dU/dP)^{-T} prim_bar;  gamma_bar -= x . dU/dGamma   (interior)
+__global__ void con2prim_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                        const double* __restrict__ metric, const double* __restrict__ prim_bar,
+                                        double* __restrict__ cons_bar, double* __restrict__ gamma_bar,
+                                        int* __restrict__ singular) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  double gb = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    double J[8][9];
+    cons_jacobian(g, p, prim, metric, c, J);
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = prim_bar[q * g.ncell + c];
+    if (!solve_transposed8(J, x)) {
+      atomicAdd(singular, 1);
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      cons_bar[q * g.ncell + c] += x[q];
+      gb -= x[q] * J[q][8];
+    }
+  }
+  block_add_gamma(gb, gamma_bar);
+}
+
+// prim_bar += (dU/dP)^T cons_bar;  gamma_bar += cons_bar . dU/dGamma   (interior)
+__global__ void prim2con_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                        const double* __restrict__ metric, const double* __restrict__ cons_bar,
+                                        double* __restrict__ prim_bar, double* __restrict__ gamma_bar) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  double gb = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    double J[8][9];
+    cons_jacobian(g, p, prim, metric, c, J);
+    double ub[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ub[q] = cons_bar[q * g.ncell + c];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s += J[i][j] * ub[i];
+      prim_bar[j * g.ncell + c] += s;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gb += ub[i] * J[i][8];
+  }
+  block_add_gamma(gb, gamma_bar);
+}
+
+// ------------------------------------------------------------ ghost fill
+// Transpose of the ghost fill: each interior point gathers the adjoints of
+// all ghost points that copy from it; ghost entries are then zero.
+__global__ void fill_ghosts_adjoint_kernel(DevGrid g, int bc, int nvar, double* __restrict__ f) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    idx[0] = (int)(t % g.n[0]);
+    idx[1] = (int)((t / g.n[0]) % g.n[1]);
+    idx[2] = (int)(t / ((long long)g.n[0] * g.n[1]));
+    // per axis, every full-array coordinate whose source is this interior coordinate
+    int pos[3][1 + 2 * 16];
+    int cnt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int i = idx[d];
+      cnt[d] = 0;
+      pos[d][cnt[d]++] = i + g.ng;
+      for (int gpos = 0; gpos < g.ng; ++gpos) {
+        const int lo = gpos - g.ng;        // interior-relative coordinate of a low ghost
+        const int hi = g.n[d] + gpos;      // ... of a high ghost
+        int slo, shi;
+        if (bc == GRMHD_BC_PERIODIC) {
+          slo = ((lo % g.n[d]) + g.n[d]) % g.n[d];
+          shi = hi % g.n[d];
+        } else {
+          slo = 0;
+          shi = g.n[d] - 1;
+        }
+        if (slo == i) pos[d][cnt[d]++] = lo + g.ng;
+        if (shi == i) pos[d][cnt[d]++] = hi + g.ng;
+      }
+    }
+    const long long self = (long long)(idx[2] + g.ng) * g.sz + (long long)(idx[1] + g.ng) * g.sy + (idx[0] + g.ng);
+    for (int q = 0; q < nvar; ++q) {
+      double s = 0.0;
+      for (int a = 0; a < cnt[2]; ++a)
+        for (int b = 0; b < cnt[1]; ++b)
+          for (int e = 0; e < cnt[0]; ++e) {
+            const long long cc = (long long)pos[2][a] * g.sz + (long long)pos[1][b] * g.sy + pos[0][e];
+            s += f[q * g.ncell + cc];
+            if (cc != self) f[q * g.ncell + cc] = 0.0;
+          }
+      f[q * g.ncell + self] = s;
+    }
+  }
+}
+
+// ----------------------------------------------------- reconstruction adjoint
+// WENO5 value v(u0..u4) at the right face of the middle cell: returns v and
+// adds dv/du_k * vbar to ub[k].
+__device__ __forceinline__ double weno5_adj(const double u[5], double eps, double vbar, double ub[5]) {
+  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
+  const double q0 = (2.0 * u[0] - 7.0 * u[1] + 11.0 * u[2]) * c6;
+  const double q1 = (-u[1] + 5.0 * u[2] + 2.0 * u[3]) * c6;
+  const double q2 = (2.0 * u[2] + 5.0 * u[3] - u[4]) * c6;
+  const double t0 = u[0] - 2.0 * u[1] + u[2], s0 = u[0] - 4.0 * u[1] + 3.0 * u[2];
+  const double t1 = u[1] - 2.0 * u[2] + u[3], s1 = u[1] - u[3];
+  const double t2 = u[2] - 2.0 * u[3] + u[4], s2 = 3.0 * u[2] - 4.0 * u[3] + u[4];
+  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
+  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
+  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
+  const double iw = 1.0 / (w0 + w1 + w2);
+  const double o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
+  const double v = o0 * q0 + o1 * q1 + o2 * q2;
+  // d v = sum_k o_k dq_k - 2 sum_k o_k (q_k - v) de_k / e_k
+  const double qb0 = o0 * vbar, qb1 = o1 * vbar, qb2 = o2 * vbar;
+  const double eb0 = -2.0 * o0 * (q0 - v) / e0 * vbar;
+  const double eb1 = -2.0 * o1 * (q1 - v) / e1 * vbar;
+  const double eb2 = -2.0 * o2 * (q2 - v) / e2 * vbar;
+  const double tb0 = 2.0 * c1312 * t0 * eb0, sb0 = 0.5 * s0 * eb0;
+  const double tb1 = 2.0 * c1312 * t1 * eb1, sb1 = 0.5 * s1 * eb1;
+  const double tb2 = 2.0 * c1312 * t2 * eb2, sb2 = 0.5 * s2 * eb2;
+  ub[0] += 2.0 * c6 * qb0 + tb0 + sb0;
+  ub[1] += -7.0 * c6 * qb0 - c6 * qb1 - 2.0 * tb0 - 4.0 * sb0 + tb1 + sb1;
+  ub[2] += 11.0 * c6 * qb0 + 5.0 * c6 * qb1 + 2.0 * c6 * qb2 + tb0 + 3.0 * sb0 - 2.0 * tb1 + tb2 + 3.0 * sb2;
+  ub[3] += 2.0 * c6 * qb1 + 5.0 * c6 * qb2 + tb1 - sb1 - 2.0 * tb2 - 4.0 * sb2;
+  ub[4] += -c6 * qb2 + tb2 + sb2;
+  return v;
+}
+
+// minmod face value um1 + minmod(um1 - um2, u0 - um1) / 2 with its adjoint.
+__device__ __forceinline__ double minmod_left_adj(double um2, double um1, double u0, double vbar, double ub[3]) {
+  const double a = um1 - um2, b = u0 - um1;
+  double v = um1;
+  ub[1] += vbar;
+  if (a * b > 0.0) {
+    if (fabs(a) <= fabs(b)) { v += 0.5 * a; ub[1] += 0.5 * vbar; ub[0] -= 0.5 * vbar; }
+    else { v += 0.5 * b; ub[2] += 0.5 * vbar; ub[1] -= 0.5 * vbar; }
+  }
+  return v;
+}
+
+// ------------------------------------------------------------- side adjoint
+// Recompute one face state (see side_state) and propagate the adjoints of
+// its outputs (U, F, lm, lp) to the primitives and Gamma.
+template <bool CURVED, int DIR>
+__device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<double>& m, double gamma, double gfac,
+                                               const double Ub[8], const double Fb[8], double lmb, double lpb,
+                                               double prb[8], double& gammab) {
+  const double rho = pr[0], P = pr[4];
+  const double v[3] = {pr[1], pr[2], pr[3]};
+  const double B[3] = {pr[5], pr[6], pr[7]};
+  double vl[3], Bl[3];
+  if (CURVED) { lower(m.g, v, vl); lower(m.g, B, Bl); }
+  else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { vl[i] = v[i]; Bl[i] = B[i]; }
+  }
+  const double v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const double omv2 = 1.0 - v2;
+  const double iW = sqrt(omv2);
+  const double W = 1.0 / iW;
+  const double ab0 = W * Bv;
+  const double b2 = B2 * omv2 + Bv * Bv;
+  double bl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
+  const double rhoh = rho + gfac * P;
+  const double hs = rhoh + b2;
+  const double Ps = P + 0.5 * b2;
+  const double sg = CURVED ? m.sqrtg : 1.0;
+  const double hW2 = hs * W * W;
+  const double D = sg * rho * W;
+  double S[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i] = sg * (hW2 * vl[i] - ab0 * bl[i]);
+  const double tau = sg * (hW2 - Ps - ab0 * ab0) - D;
+  double Bc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Bc[i] = sg * B[i];
+  const double alpha = CURVED ? m.alpha : 1.0;
+  double vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vt[i] = CURVED ? v[i] - m.beta[i] / alpha : v[i];
+  const double vtd = vt[DIR];
+  const double BdiW = Bc[DIR] * iW;
+  const double cs2 = gamma * P / rhoh;
+  const double va2 = b2 / hs;
+  const double a2 = cs2 + va2 - cs2 * va2;
+  const double gdd = CURVED ? m.gup_dd : 1.0;
+  const double den = 1.0 - v2 * a2;
+  const double vd = v[DIR];
+  const double disc0 = omv2 * (gdd * den - vd * vd * (1.0 - a2));
+  const double disc = disc0 > 0.0 ? disc0 : 0.0;
+  const double sq = sqrt(a2 * disc);
+  const double ide = alpha / den;
+  const double c0 = vd * (1.0 - a2);
+
+  // ---- reverse ----
+  double rhob = 0, Pb = 0, vb[3] = {0, 0, 0}, Bb[3] = {0, 0, 0};
+  double vlb[3] = {0, 0, 0}, Blb[3] = {0, 0, 0}, blb[3] = {0, 0, 0};
+  double v2b = 0, Bvb = 0, B2b = 0, omv2b = 0, iWb = 0, Wb = 0, ab0b = 0, b2b = 0;
+  double rhohb = 0, hsb = 0, Psb = 0, hW2b = 0, Db = 0, Sb[3], taub = 0, Bcb[3], vtb[3] = {0, 0, 0};
+  double gfacb = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { Sb[i] = Ub[1 + i]; Bcb[i] = Ub[5 + i]; }
+  Db = Ub[0];
+  taub = Ub[4];
+  // speeds
+  {
+    const double ideb = lpb * (c0 + sq) + lmb * (c0 - sq);
+    const double c0b = ide * (lpb + lmb);
+    const double sqb = ide * (lpb - lmb);
+    double denb = -ide / den * ideb;
+    double a2b = 0, vdb = 0, discb = 0;
+    vdb += (1.0 - a2) * c0b;
+    a2b -= vd * c0b;
+    if (sq > 0.0) {
+      const double tb = sqb * 0.5 / sq;
+      a2b += disc * tb;
+      discb += a2 * tb;
+    }
+    if (disc0 > 0.0) {
+      omv2b += (gdd * den - vd * vd * (1.0 - a2)) * discb;
+      denb += omv2 * gdd * discb;
+      vdb -= 2.0 * vd * (1.0 - a2) * omv2 * discb;
+      a2b += vd * vd * omv2 * discb;
+    }
+    v2b -= a2 * denb;
+    a2b -= v2 * denb;
+    const double cs2b = (1.0 - va2) * a2b;
+    const double va2b = (1.0 - cs2) * a2b;
+    gammab += P / rhoh * cs2b;
+    Pb += gamma / rhoh * cs2b;
+    rhohb -= cs2 / rhoh * cs2b;
+    b2b += va2b / hs;
+    hsb -= va2 / hs * va2b;
+    vb[DIR] += vdb;
+  }
+  // fluxes
+  {
+    double BdiWb = 0;
+    Db += alpha * vtd * Fb[0];
+    vtb[DIR] += alpha * D * Fb[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double f = alpha * Fb[1 + j];
+      Sb[j] += vtd * f;
+      vtb[DIR] += S[j] * f;
+      if (j == DIR) Psb += sg * f;
+      blb[j] -= BdiW * f;
+      BdiWb -= bl[j] * f;
+    }
+    {
+      const double f = alpha * Fb[4];
+      taub += vtd * f;
+      vtb[DIR] += tau * f;
+      Psb += sg * v[DIR] * f;
+      vb[DIR] += sg * Ps * f;
+      ab0b -= BdiW * f;
+      BdiWb -= ab0 * f;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k == DIR) continue;
+      const double f = alpha * Fb[5 + k];
+      Bcb[k] += vtd * f;
+      vtb[DIR] += Bc[k] * f;
+      Bcb[DIR] -= vt[k] * f;
+      vtb[k] -= Bc[DIR] * f;
+    }
+    Bcb[DIR] += iW * BdiWb;
+    iWb += Bc[DIR] * BdiWb;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vb[i] += vtb[i];
+  }
+  // conserved variables
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Bb[i] += sg * Bcb[i];
+  hW2b += sg * taub;
+  Psb -= sg * taub;
+  ab0b -= 2.0 * sg * ab0 * taub;
+  Db -= taub;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    hW2b += sg * vl[i] * Sb[i];
+    vlb[i] += sg * hW2 * Sb[i];
+    ab0b -= sg * bl[i] * Sb[i];
+    blb[i] -= sg * ab0 * Sb[i];
+  }
+  rhob += sg * W * Db;
+  Wb += sg * rho * Db;
+  hsb += W * W * hW2b;
+  Wb += 2.0 * hs * W * hW2b;
+  Pb += Psb;
+  b2b += 0.5 * Psb;
+  rhohb += hsb;
+  b2b += hsb;
+  rhob += rhohb;
+  Pb += gfac * rhohb;
+  gfacb += P * rhohb;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Blb[i] += iW * blb[i];
+    iWb += Bl[i] * blb[i];
+    ab0b += vl[i] * blb[i];
+    vlb[i] += ab0 * blb[i];
+  }
+  B2b += omv2 * b2b;
+  omv2b += B2 * b2b;
+  Bvb += 2.0 * Bv * b2b;
+  Wb += Bv * ab0b;
+  Bvb += W * ab0b;
+  iWb -= W * W * Wb;
+  omv2b += iWb * 0.5 / iW;
+  v2b -= omv2b;
+  // v2 = v.Gv, Bv = B.Gv, B2 = B.GB; vl = Gv, Bl = GB (G symmetric)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vb[i] += 2.0 * vl[i] * v2b + Bl[i] * Bvb;
+    Bb[i] += vl[i] * Bvb + 2.0 * Bl[i] * B2b;
+  }
+  double Gvlb[3], GBlb[3];
+  if (CURVED) { lower(m.g, vlb, Gvlb); lower(m.g, Blb, GBlb); }
+  else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { Gvlb[i] = vlb[i]; GBlb[i] = Blb[i]; }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { vb[i] += Gvlb[i]; Bb[i] += GBlb[i]; }
+  gammab += gfacb * (-1.0 / ((gamma - 1.0) * (gamma - 1.0)));
+  prb[0] += rhob;
+  prb[1] += vb[0];
+  prb[2] += vb[1];
+  prb[3] += vb[2];
+  prb[4] += Pb;
+  prb[5] += Bb[0];
+  prb[6] += Bb[1];
+  prb[7] += Bb[2];
+}
+
+// ---------------------------------------------------------------- face adjoint
+template <int RECON, bool CURVED, int DIR>
+__device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
+                                             const double* __restrict__ metric, long long c, const double Fb[8],
+                                             double* __restrict__ prim_bar, double& gammab) {
+  const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
+  // primal reconstruction (same arithmetic as the forward kernel)
+  double pL[8], pR[8];
+  const double eps = p.weno_eps;
+  reconstruct_face<double, RECON>(prim, g.ncell, c, stride, eps, pL, pR);
+  Geom<double> m;
+  if (CURVED) face_geom<double, DIR>(metric, g.ncell, c, stride, m);
+  const bool fbL = !physical_state<double, CURVED>(pL, m);
+  const bool fbR = !physical_state<double, CURVED>(pR, m);
+  if (fbL)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pL[q] = __ldg(prim + q * g.ncell + c - stride);
+  if (fbR)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pR[q] = __ldg(prim + q * g.ncell + c);
+  Side<double> L, R;
+  side_state<double, CURVED, DIR>(pL, m, p.gamma, p.gfac, L);
+  side_state<double, CURVED, DIR>(pR, m, p.gamma, p.gfac, R);
+  // HLLE reverse
+  double FLb[8], FRb[8], ULb[8], URb[8], lmLb = 0, lpLb = 0, lmRb = 0, lpRb = 0;
+  const double xm = fmin(0.0, fmin(L.lm, R.lm));
+  const double xp = fmax(0.0, fmax(L.lp, R.lp));
+  const double dd = xp - xm;
+  if (dd < 1e-300) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { FLb[q] = FRb[q] = 0.5 * Fb[q]; ULb[q] = URb[q] = 0.0; }
+  } else {
+    const double inv = 1.0 / dd;
+    double xpb = 0, xmb = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double dU = R.U[q] - L.U[q];
+      const double F = (xp * L.F[q] - xm * R.F[q] + xp * xm * dU) * inv;
+      FLb[q] = xp * inv * Fb[q];
+      FRb[q] = -xm * inv * Fb[q];
+      URb[q] = xp * xm * inv * Fb[q];
+      ULb[q] = -URb[q];
+      xpb += Fb[q] * (L.F[q] + xm * dU - F) * inv;
+      xmb += Fb[q] * (-R.F[q] + xp * dU + F) * inv;
+    }
+    // route through max / min (ties go to the first candidate in the forward order)
+    if (xp > 0.0) { if (L.lp >= R.lp) lpLb += xpb; else lpRb += xpb; }
+    if (xm < 0.0) { if (L.lm <= R.lm) lmLb += xmb; else lmRb += xmb; }
+  }
+  double pLb[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pRb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  side_state_adj<CURVED, DIR>(pL, m, p.gamma, p.gfac, ULb, FLb, lmLb, lpLb, pLb, gammab);
+  side_state_adj<CURVED, DIR>(pR, m, p.gamma, p.gfac, URb, FRb, lmRb, lpRb, pRb, gammab);
+  // reconstruction reverse (stencil values reloaded), scatter to the stencil
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    double u[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u[k] = __ldg(prim + q * g.ncell + c + (k - 3) * stride);
+    double ub[6] = {0, 0, 0, 0, 0, 0};
+    if (fbL) ub[2] += pLb[q];
+    if (fbR) ub[3] += pRb[q];
+    if (RECON == GRMHD_WENO5) {
+      if (!fbL) {
+        double t[5] = {0, 0, 0, 0, 0};
+        const double uu[5] = {u[0], u[1], u[2], u[3], u[4]};
+        weno5_adj(uu, eps, pLb[q], t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ub[k] += t[k];
+      }
+      if (!fbR) {
+        double t[5] = {0, 0, 0, 0, 0};
+        const double uu[5] = {u[5], u[4], u[3], u[2], u[1]};
+        weno5_adj(uu, eps, pRb[q], t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ub[5 - k] += t[k];
+      }
+    } else {
+      if (!fbL) {
+        double t[3] = {0, 0, 0};
+        minmod_left_adj(u[1], u[2], u[3], pLb[q], t);
+        ub[1] += t[0]; ub[2] += t[1]; ub[3] += t[2];
+      }
+      if (!fbR) {
+        // u0 - minmod(u0 - um1, up1 - u0)/2 is the mirror of the left formula
+        double t[3] = {0, 0, 0};
+        minmod_left_adj(u[4], u[3], u[2], pRb[q], t);
+        ub[4] += t[0]; ub[3] += t[1]; ub[2] += t[2];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (ub[s] != 0.0) atomicAdd(prim_bar + q * g.ncell + c + (s - 3) * stride, ub[s]);
+  }
+}
+
+// One thread per face: F_bar = scale * (Lbar_c - Lbar_{c-1}) / dx_d, with
+// Lbar = 0 outside the interior.
+template <int RECON, bool CURVED>
+__global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                                              const double* __restrict__ metric,
+                                                              const double* __restrict__ rhs_bar, double scale,
+                                                              double* __restrict__ prim_bar,
+                                                              double* __restrict__ gamma_bar) {
+  const long long nfx = (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
+  const long long nfy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
+  const long long nfz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+  const long long total = nfx + nfy + nfz;
+  double gb = 0.0;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    int dir, xi, yi, zi;
+    if (f < nfx) {
+      dir = 0;
+      xi = (int)(f % (g.n[0] + 1));
+      yi = (int)((f / (g.n[0] + 1)) % g.n[1]);
+      zi = (int)(f / ((long long)(g.n[0] + 1) * g.n[1]));
+    } else if (f < nfx + nfy) {
+      const long long ff = f - nfx;
+      dir = 1;
+      xi = (int)(ff % g.n[0]);
+      yi = (int)((ff / g.n[0]) % (g.n[1] + 1));
+      zi = (int)(ff / ((long long)g.n[0] * (g.n[1] + 1)));
+    } else {
+      const long long ff = f - nfx - nfy;
+      dir = 2;
+      xi = (int)(ff % g.n[0]);
+      yi = (int)((ff / g.n[0]) % g.n[1]);
+      zi = (int)(ff / ((long long)g.n[0] * g.n[1]));
+    }
+    const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
+    const long long stride = dir == 0 ? 1 : (dir == 1 ? g.sy : g.sz);
+    const int ic = dir == 0 ? xi : (dir == 1 ? yi : zi);
+    const bool has_hi = ic < g.n[dir];   // cell c is interior
+    const bool has_lo = ic > 0;          // cell c - stride is interior
+    double Fb[8];
+    const double w = scale * g.idx[dir];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double hi = has_hi ? rhs_bar[q * g.ncell + c] : 0.0;
+      const double lo = has_lo ? rhs_bar[q * g.ncell + c - stride] : 0.0;
+      Fb[q] = w * (hi - lo);
+    }
+    if (dir == 0) face_adjoint<RECON, CURVED, 0>(g, p, prim, metric, c, Fb, prim_bar, gb);
+    else if (dir == 1) face_adjoint<RECON, CURVED, 1>(g, p, prim, metric, c, Fb, prim_bar, gb);
+    else face_adjoint<RECON, CURVED, 2>(g, p, prim, metric, c, Fb, prim_bar, gb);
+  }
+  block_add_gamma(gb, gamma_bar);
+}
+
+// ------------------------------------------------------------- source adjoint
+// The Eq. 13 source of one cell (3+1 form as in source_terms) on dual numbers.
+__device__ __forceinline__ void source_dual(const DevGrid& g, const double* __restrict__ metric,
+                                            const double* __restrict__ kij, long long c, const D9 pr[8],
+                                            const D9& gfac, D9 src[8]) {
+  double a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = __ldg(metric + q * g.ncell + c);
+  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+  const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
+  const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
+  const double det = gxx * cxx + gxy * cxy + gxz * cxz;
+  const double idet = 1.0 / det;
+  const double sg = sqrt(det);
+  const double gu[6] = {cxx * idet, cxy * idet, cxz * idet, cyy * idet, cyz * idet, czz * idet};
+  const double alpha = a[0];
+  const double beta[3] = {a[1], a[2], a[3]};
+  const double gm[6] = {gxx, gxy, gxz, gyy, gyz, gzz};
+  double dA[3][10];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long s = (e == 0) ? 1 : ((e == 1) ? g.sy : g.sz);
+    const double w = g.idx[e] * (1.0 / 12.0);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const double* mm = metric + q * g.ncell + c;
+      dA[e][q] = (8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w;
+    }
+  }
+  const D9 rho = pr[0], P = pr[4];
+  const D9 v[3] = {pr[1], pr[2], pr[3]};
+  const D9 B[3] = {pr[5], pr[6], pr[7]};
+  D9 vl[3], Bl[3];
+  for (int i = 0; i < 3; ++i) {
+    vl[i] = D9(0.0);
+    Bl[i] = D9(0.0);
+  }
+  const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+  for (int s = 0; s < 6; ++s) {
+    const int i = I6[s], j = J6[s];
+    vl[i] += D9(gm[s]) * v[j];
+    Bl[i] += D9(gm[s]) * B[j];
+    if (i != j) {
+      vl[j] += D9(gm[s]) * v[i];
+      Bl[j] += D9(gm[s]) * B[i];
+    }
+  }
+  const D9 v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const D9 Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const D9 B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const D9 omv2 = D9(1.0) - v2;
+  const D9 iW = xsqrt(omv2);
+  const D9 W = D9(1.0) / iW;
+  const D9 ab0 = W * Bv;
+  const D9 b2 = B2 * omv2 + Bv * Bv;
+  const D9 hs = rho + gfac * P + b2;
+  const D9 Ps = P + D9(0.5) * b2;
+  const double ia = 1.0 / alpha;
+  const double ia2 = ia * ia;
+  const D9 b0 = ab0 * D9(ia);
+  D9 vt[3], bu[3];
+  for (int i = 0; i < 3; ++i) {
+    vt[i] = v[i] - D9(beta[i] * ia);
+    bu[i] = B[i] * iW + ab0 * vt[i];
+  }
+  const D9 hW2 = hs * W * W;
+  const D9 T00 = (hW2 - Ps) * D9(ia2) - b0 * b0;
+  D9 T0[3];
+  for (int i = 0; i < 3; ++i) T0[i] = hW2 * vt[i] * D9(ia) + Ps * D9(beta[i] * ia2) - b0 * bu[i];
+  D9 Tij[6];
+  for (int s = 0; s < 6; ++s) {
+    const int i = I6[s], j = J6[s];
+    Tij[s] = hW2 * vt[i] * vt[j] + Ps * D9(gu[s] - beta[i] * beta[j] * ia2) - bu[i] * bu[j];
+  }
+  double betal[3];
+  lower(gm, beta, betal);
+  D9 T0l[3];
+  for (int i = 0; i < 3; ++i) {
+    T0l[i] = T00 * D9(betal[i]);
+    for (int j = 0; j < 3; ++j) T0l[i] += D9(gm[sym_index(i, j)]) * T0[j];
+  }
+  const double asg = alpha * sg;
+  const double wsym[6] = {1, 2, 2, 1, 2, 1};
+  src[0] = D9(0.0);
+  for (int j = 0; j < 3; ++j) {
+    double bbdg = 0.0;
+    D9 t0dg(0.0), tdg(0.0);
+    for (int s = 0; s < 6; ++s) {
+      const int i = I6[s], k = J6[s];
+      const double dg = dA[j][4 + s] * wsym[s];
+      bbdg += beta[i] * beta[k] * dg;
+      t0dg += D9(0.5 * dg) * (T0[i] * D9(beta[k]) + T0[k] * D9(beta[i]));
+      tdg += Tij[s] * D9(dg);
+    }
+    const D9 t0db = T0l[0] * D9(dA[j][1]) + T0l[1] * D9(dA[j][2]) + T0l[2] * D9(dA[j][3]);
+    src[1 + j] = D9(asg) * (T00 * D9(0.5 * bbdg - alpha * dA[j][0]) + t0dg + t0db + D9(0.5) * tdg);
+  }
+  {
+    D9 t = -(T0[0] * D9(dA[0][0]) + T0[1] * D9(dA[1][0]) + T0[2] * D9(dA[2][0]));
+    t -= T00 * D9(beta[0] * dA[0][0] + beta[1] * dA[1][0] + beta[2] * dA[2][0]);
+    if (kij) {
+      double K[6];
+      for (int s = 0; s < 6; ++s) K[s] = __ldg(kij + s * g.ncell + c);
+      double bK[3];
+      lower(K, beta, bK);
+      const double bbK = beta[0] * bK[0] + beta[1] * bK[1] + beta[2] * bK[2];
+      D9 tK = T0[0] * D9(bK[0]) + T0[1] * D9(bK[1]) + T0[2] * D9(bK[2]);
+      D9 TK(0.0);
+      for (int s = 0; s < 6; ++s) TK += Tij[s] * D9(K[s] * wsym[s]);
+      t += T00 * D9(bbK) + D9(2.0) * tK + TK;
+    }
+    src[4] = D9(asg) * t;
+  }
+  src[5] = src[6] = src[7] = D9(0.0);
+}
+
+__global__ void source_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                      const double* __restrict__ metric, const double* __restrict__ kij,
+                                      const double* __restrict__ rhs_bar, double scale, double* __restrict__ prim_bar,
+                                      double* __restrict__ gamma_bar) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  double gb = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    D9 pr[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      pr[q] = D9(__ldg(prim + q * g.ncell + c));
+      pr[q].d[q] = 1.0;
+    }
+    D9 gf(p.gfac);
+    gf.d[8] = -1.0 / ((p.gamma - 1.0) * (p.gamma - 1.0));
+    D9 src[8];
+    source_dual(g, metric, kij, c, pr, gf, src);
+    double lb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) lb[q] = scale * rhs_bar[q * g.ncell + c];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s += src[i].d[j] * lb[i];
+      if (s != 0.0) atomicAdd(prim_bar + j * g.ncell + c, s);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gb += src[i].d[8] * lb[i];
+  }
+  block_add_gamma(gb, gamma_bar);
+}
+
+// --------------------------------------------------------- elementwise pieces
+// y = a * x + b * y on the interior of nvar fields (x may be NULL: y = b y).
+__global__ void axpby_interior_kernel(DevGrid g, int nvar, double a, const double* __restrict__ x, double b,
+                                      double* __restrict__ y) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint * nvar;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / nint);
+    const long long c = interior_cell(g, t % nint) + q * g.ncell;
+    y[c] = (x ? a * x[c] : 0.0) + (b != 0.0 ? b * y[c] : 0.0);
+  }
+}
+
+// L += sum_interior rho^2 sqrt(gamma) dV ;  prim_bar[rho] += 2 rho sqrt(gamma) dV * lbar
+__global__ void density_l2_kernel(DevGrid g, const double* __restrict__ prim, const double* __restrict__ metric,
+                                  double lbar, double* __restrict__ loss, double* __restrict__ prim_bar) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  const double dV = g.dx[0] * g.dx[1] * g.dx[2];
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    CellMetric m;
+    cell_metric(metric, g.ncell, c, m);
+    const double rho = prim[c];
+    acc += rho * rho * m.sqrtg * dV;
+    if (prim_bar) prim_bar[c] += 2.0 * rho * m.sqrtg * dV * lbar;
+  }
+  if (loss) block_add_gamma(acc, loss);
+}
+
+int blocks_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_rhs_adjoint(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                               const double* kij, const double* rhs_bar, double scale, double* prim_bar,
+                               double* gamma_bar, cudaStream_t s) {
+  const long long faces = (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
+                          (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+  const int nb = blocks_for(faces, 128);
+  const bool weno = p.recon == GRMHD_WENO5;
+  if (metric) {
+    if (weno) rhs_face_adjoint_kernel<GRMHD_WENO5, true><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+    else rhs_face_adjoint_kernel<GRMHD_MINMOD, true><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+  } else {
+    if (weno) rhs_face_adjoint_kernel<GRMHD_WENO5, false><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+    else rhs_face_adjoint_kernel<GRMHD_MINMOD, false><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !metric) return e;
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  source_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, s>>>(g, p, prim, metric, kij, rhs_bar, scale, prim_bar,
+                                                              gamma_bar);
+  return cudaGetLastError();
+}
+
+}  // namespace grmhd
+
+using namespace grmhd;
+
+namespace {
+
+bool al8(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; }
+size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int check_common(const grmhd_grid* grid, const grmhd_params* params, const double* metric) {
+  if (!grid || !params) return GRMHD_ERR_ARG;
+  if (params->precision != GRMHD_FP64) return GRMHD_ERR_ARG;  // the adjoint is of the FP64 method
+  if (!(params->gamma > 1.0 && params->gamma <= 3.0)) return GRMHD_ERR_ARG;
+  if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
+  if (params->bc != GRMHD_BC_PERIODIC && params->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+  if (params->nr_maxit < 1 || !(params->nr_tol > 0.0) || !(params->weno_eps > 0.0)) return GRMHD_ERR_ARG;
+  if (!(params->rho_atm > 0.0) || !(params->p_atm > 0.0) || params->tile < 0 || params->tile > 3) return GRMHD_ERR_ARG;
+  const int min_ng = params->recon == GRMHD_WENO5 ? 3 : 2;
+  if (grid->ng < min_ng || grid->ng > 16) return GRMHD_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (grid->n[d] < 1 || grid->n[d] > (1 << 20) || !(grid->dx[d] > 0.0)) return GRMHD_ERR_ARG;
+  if (metric && !al8(metric)) return GRMHD_ERR_ARG;
+  return GRMHD_OK;
+}
+
+int st(cudaError_t e) { return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
+
+cudaError_t axpby(const DevGrid& g, double a, const double* x, double b, double* y, cudaStream_t s) {
+  const long long n = (long long)g.n[0] * g.n[1] * g.n[2] * 8;
+  axpby_interior_kernel<<<blocks_for(n, 256), 256, 0, s>>>(g, 8, a, x, b, y);
+  return cudaGetLastError();
+}
+
+cudaError_t c2p_adjoint(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                        const double* prim_bar, double* cons_bar, double* gamma_bar, int32_t* nsing, cudaStream_t s) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  con2prim_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, s>>>(g, p, prim, metric, prim_bar, cons_bar, gamma_bar,
+                                                                 nsing);
+  return cudaGetLastError();
+}
+
+cudaError_t ghost_adjoint(const DevGrid& g, int bc, int nvar, double* f, cudaStream_t s) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  fill_ghosts_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, s>>>(g, bc, nvar, f);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int grmhd_rhs_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+                      const double* kij, const double* rhs_bar, double* prim_bar, double* gamma_bar, void* stream) {
+  int e = check_common(grid, params, metric);
+  if (e) return e;
+  if (!prim || !rhs_bar || !prim_bar || !gamma_bar || !al8(prim) || !al8(rhs_bar) || !al8(prim_bar) || !al8(gamma_bar))
+    return GRMHD_ERR_ARG;
+  if (kij && (!metric || !al8(kij))) return GRMHD_ERR_ARG;
+  return st(launch_rhs_adjoint(make_grid(*grid), make_params(*params), prim, metric, kij, rhs_bar, 1.0, prim_bar,
+                               gamma_bar, (cudaStream_t)stream));
+}
+
+int grmhd_con2prim_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                           const double* metric, const double* prim_bar, double* cons_bar, double* gamma_bar,
+                           int32_t* nsingular, void* stream) {
+  int e = check_common(grid, params, metric);
+  if (e) return e;
+  if (!prim || !prim_bar || !cons_bar || !gamma_bar || !al8(prim) || !al8(prim_bar) || !al8(cons_bar)) return GRMHD_ERR_ARG;
+  return st(c2p_adjoint(make_grid(*grid), make_params(*params), prim, metric, prim_bar, cons_bar, gamma_bar,
+                        nsingular, (cudaStream_t)stream));
+}
+
+int grmhd_prim2con_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                           const double* metric, const double* cons_bar, double* prim_bar, double* gamma_bar,
+                           void* stream) {
+  int e = check_common(grid, params, metric);
+  if (e) return e;
+  if (!prim || !prim_bar || !cons_bar || !gamma_bar || !al8(prim) || !al8(prim_bar) || !al8(cons_bar)) return GRMHD_ERR_ARG;
+  const DevGrid g = make_grid(*grid);
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  prim2con_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, (cudaStream_t)stream>>>(g, make_params(*params), prim, metric,
+                                                                                     cons_bar, prim_bar, gamma_bar);
+  return st(cudaGetLastError());
+}
+
+int grmhd_fill_ghosts_adjoint(const grmhd_grid* grid, int32_t bc, int32_t nvar, double* field_bar, void* stream) {
+  if (!grid || !field_bar || !al8(field_bar) || nvar < 1 || nvar > 64) return GRMHD_ERR_ARG;
+  if (bc != GRMHD_BC_PERIODIC && bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+  if (grid->ng < 0 || grid->ng > 16) return GRMHD_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (grid->n[d] < 1 || grid->n[d] > (1 << 20)) return GRMHD_ERR_ARG;
+  return st(ghost_adjoint(make_grid(*grid), bc, nvar, field_bar, (cudaStream_t)stream));
+}
+
+int grmhd_density_l2(const grmhd_grid* grid, const double* prim, const double* metric, double lbar, double* loss,
+                     double* prim_bar, void* stream) {
+  if (!grid || !prim || !al8(prim) || (metric && !al8(metric)) || (!loss && !prim_bar)) return GRMHD_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (grid->n[d] < 1 || grid->n[d] > (1 << 20) || !(grid->dx[d] > 0.0)) return GRMHD_ERR_ARG;
+  const DevGrid g = make_grid(*grid);
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  density_l2_kernel<<<blocks_for(nint, 256), 256, 0, (cudaStream_t)stream>>>(g, prim, metric, lbar, loss, prim_bar);
+  return st(cudaGetLastError());
+}
+
+size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
+  if (!grid || (scheme != GRMHD_RK2 && scheme != GRMHD_RK3)) return 0;
+  for (int d = 0; d < 3; ++d)
+    if (grid->n[d] < 1 || grid->n[d] > (1 << 20)) return 0;
+  const DevGrid g = make_grid(*grid);
+  const size_t field = r256((size_t)8 * g.ncell * sizeof(double));
+  const int stages = scheme == GRMHD_RK3 ? 3 : 2;
+  return (size_t)(1 + stages + 1 + 1 + 2) * field;
+}
+
+int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                          const double* cons, const double* prim, const double* metric, const double* kij,
+                          double* cons_bar, double* prim_bar, double* gamma_bar, void* ws, size_t ws_bytes,
+                          void* stream) {
+  int e = check_common(grid, params, metric);
+  if (e) return e;
+  if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3) return GRMHD_ERR_ARG;
+  if (!(dt > 0.0) || !cons || !prim || !cons_bar || !prim_bar || !gamma_bar || !ws) return GRMHD_ERR_ARG;
+  if (!al8(cons) || !al8(prim) || !al8(cons_bar) || !al8(prim_bar) || !al8(gamma_bar)) return GRMHD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  if (kij && (!metric || !al8(kij))) return GRMHD_ERR_ARG;
+  if (ws_bytes < grmhd_rk_adjoint_workspace_bytes(grid, scheme)) return GRMHD_ERR_SIZE;
+  const DevGrid g = make_grid(*grid);
+  const DevParams p = make_params(*params);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t field = r256((size_t)8 * g.ncell * sizeof(double));
+  const size_t nbytes = (size_t)8 * g.ncell * sizeof(double);
+  const int ns = scheme == GRMHD_RK3 ? 3 : 2;
+  char* base = static_cast<char*>(ws);
+  double* W = reinterpret_cast<double*>(base);
+  double* Pst[4];
+  Pst[0] = const_cast<double*>(prim);
+  for (int k = 1; k <= ns; ++k) Pst[k] = reinterpret_cast<double*>(base + (size_t)k * field);
+  double* A = reinterpret_cast<double*>(base + (size_t)(ns + 1) * field);
+  double* Bacc = reinterpret_cast<double*>(base + (size_t)(ns + 2) * field);
+  double* Pn = reinterpret_cast<double*>(base + (size_t)(ns + 3) * field);
+  double* Pk = reinterpret_cast<double*>(base + (size_t)(ns + 4) * field);
+  double c0[3], c1[3], cr[3];
+  if (ns == 3) {
+    c0[0] = 1.0; c1[0] = 0.0; cr[0] = 1.0;
+    c0[1] = 0.75; c1[1] = 0.25; cr[1] = 0.25;
+    c0[2] = 1.0 / 3.0; c1[2] = 2.0 / 3.0; cr[2] = 2.0 / 3.0;
+  } else {
+    c0[0] = 1.0; c1[0] = 0.0; cr[0] = 1.0;
+    c0[1] = 0.5; c1[1] = 0.5; cr[1] = 0.5;
+  }
+  // recompute the stages exactly as grmhd_rk_step does
+  if (cudaMemcpyAsync(W, cons, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  for (int k = 0; k < ns; ++k) {
+    StageEpilogue ep;
+    ep.rhs = nullptr;
+    ep.u = W;
+    ep.u0 = cons;
+    ep.acc_in = nullptr;
+    ep.acc_out = nullptr;
+    ep.c0 = c0[k];
+    ep.c1 = c1[k];
+    ep.cr = cr[k] * dt;
+    ep.ca = ep.wa = ep.wr = 0.0;
+    if (launch_rhs_fp64(g, p, Pst[k], metric, kij, ep, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (cudaMemcpyAsync(Pst[k + 1], Pst[k], nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (launch_con2prim(g, p, W, metric, Pst[k + 1], nullptr, nullptr, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (launch_fill_ghosts(g, p.bc, 8, Pst[k + 1], s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  }
+  // reverse sweep
+  if (cudaMemcpyAsync(A, cons_bar, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemsetAsync(Bacc, 0, nbytes, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemcpyAsync(Pn, prim_bar, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  for (int k = ns - 1; k >= 0; --k) {
+    if (ghost_adjoint(g, p.bc, 8, Pn, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (c2p_adjoint(g, p, Pst[k + 1], metric, Pn, A, gamma_bar, nullptr, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (axpby(g, c0[k], A, 1.0, Bacc, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (cudaMemsetAsync(Pk, 0, nbytes, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (launch_rhs_adjoint(g, p, Pst[k], metric, kij, A, cr[k] * dt, Pk, gamma_bar, s) != cudaSuccess)
+      return GRMHD_ERR_CUDA;
+    if (k >= 1) {
+      if (axpby(g, 0.0, nullptr, c1[k], A, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    } else if (c1[0] != 0.0) {
+      if (axpby(g, c1[0], A, 1.0, Bacc, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    }
+    double* t = Pn;
+    Pn = Pk;
+    Pk = t;
+  }
+  if (cudaMemcpyAsync(cons_bar, Bacc, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemcpyAsync(prim_bar, Pn, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
+}
+
+}  // extern "C"

@@ -306,3 +306,86 @@ class Batch:
         nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
         rc = _lib.grmhd_batch_rhs(ctypes.byref(self.c), ctypes.byref(params.c()), nf, _stream(stream))
         _check(rc, "grmhd_batch_rhs")
+
+
+# ------------------------------------------------------------------ adjoint --
+_lib.grmhd_rhs_adjoint.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, _P, _P]
+_lib.grmhd_con2prim_adjoint.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, _P, _P]
+_lib.grmhd_prim2con_adjoint.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, _P]
+_lib.grmhd_fill_ghosts_adjoint.argtypes = [_pg, _I32, _I32, _P, _P]
+_lib.grmhd_density_l2.argtypes = [_pg, _P, _P, ctypes.c_double, _P, _P, _P]
+_lib.grmhd_rk_adjoint_workspace_bytes.argtypes = [_pg, _I32]
+_lib.grmhd_rk_adjoint_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_rk_step_adjoint.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _P,
+                                       ctypes.c_size_t, _P]
+for _name in ("grmhd_rhs_adjoint", "grmhd_con2prim_adjoint", "grmhd_prim2con_adjoint", "grmhd_fill_ghosts_adjoint",
+              "grmhd_density_l2", "grmhd_rk_step_adjoint"):
+    getattr(_lib, _name).restype = _I
+C_SYMBOLS = C_SYMBOLS + ("grmhd_rhs_adjoint", "grmhd_con2prim_adjoint", "grmhd_prim2con_adjoint",
+                         "grmhd_fill_ghosts_adjoint", "grmhd_density_l2", "grmhd_rk_adjoint_workspace_bytes",
+                         "grmhd_rk_step_adjoint")
+
+
+def _scalar(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.numel() < 1:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def rhs_adjoint(grid: Grid, params: Params, prim, rhs_bar, prim_bar, gamma_bar, metric=None, kij=None, stream=None):
+    rc = _lib.grmhd_rhs_adjoint(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                                _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                                _field(rhs_bar, grid, 8, "rhs_bar"), _field(prim_bar, grid, 8, "prim_bar"),
+                                _scalar(gamma_bar, "gamma_bar"), _stream(stream))
+    _check(rc, "grmhd_rhs_adjoint")
+
+
+def con2prim_adjoint(grid: Grid, params: Params, prim, prim_bar, cons_bar, gamma_bar, metric=None, stream=None):
+    rc = _lib.grmhd_con2prim_adjoint(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                                     _field(metric, grid, 10, "metric", True), _field(prim_bar, grid, 8, "prim_bar"),
+                                     _field(cons_bar, grid, 8, "cons_bar"), _scalar(gamma_bar, "gamma_bar"), None,
+                                     _stream(stream))
+    _check(rc, "grmhd_con2prim_adjoint")
+
+
+def prim2con_adjoint(grid: Grid, params: Params, prim, cons_bar, prim_bar, gamma_bar, metric=None, stream=None):
+    rc = _lib.grmhd_prim2con_adjoint(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                                     _field(metric, grid, 10, "metric", True), _field(cons_bar, grid, 8, "cons_bar"),
+                                     _field(prim_bar, grid, 8, "prim_bar"), _scalar(gamma_bar, "gamma_bar"),
+                                     _stream(stream))
+    _check(rc, "grmhd_prim2con_adjoint")
+
+
+def fill_ghosts_adjoint(grid: Grid, bc: int, field_bar, stream=None):
+    nvar = field_bar.shape[0]
+    rc = _lib.grmhd_fill_ghosts_adjoint(ctypes.byref(grid.c()), bc, nvar, _field(field_bar, grid, nvar, "field_bar"),
+                                        _stream(stream))
+    _check(rc, "grmhd_fill_ghosts_adjoint")
+
+
+def density_l2(grid: Grid, prim, metric=None, lbar=0.0, loss=None, prim_bar=None, stream=None):
+    rc = _lib.grmhd_density_l2(ctypes.byref(grid.c()), _field(prim, grid, 8, "prim"),
+                               _field(metric, grid, 10, "metric", True), float(lbar),
+                               None if loss is None else _scalar(loss, "loss"),
+                               None if prim_bar is None else _field(prim_bar, grid, 8, "prim_bar"), _stream(stream))
+    _check(rc, "grmhd_density_l2")
+
+
+def adjoint_workspace(grid: Grid, scheme: int, device=None):
+    nbytes = int(_lib.grmhd_rk_adjoint_workspace_bytes(ctypes.byref(grid.c()), scheme))
+    if nbytes == 0:
+        raise GrmhdError("invalid grid or scheme for the adjoint workspace")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def rk_step_adjoint(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, cons_bar, prim_bar, gamma_bar,
+                    metric=None, kij=None, ws=None, stream=None):
+    if ws is None:
+        ws = adjoint_workspace(grid, scheme, cons.device)
+    rc = _lib.grmhd_rk_step_adjoint(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
+                                    _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
+                                    _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                                    _field(cons_bar, grid, 8, "cons_bar"), _field(prim_bar, grid, 8, "prim_bar"),
+                                    _scalar(gamma_bar, "gamma_bar"), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    _stream(stream))
+    _check(rc, "grmhd_rk_step_adjoint")
