@@ -171,7 +171,7 @@ def cpu_baseline_sample(seconds_target=15.0):
     cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)     # warm-up
     steps, t = 0, 0.0
     t0 = time.perf_counter()
-    while t < seconds_target and steps < 100:
+    while t < seconds_target and steps < 400:
         cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)
         steps += 1
         t = time.perf_counter() - t0
@@ -254,6 +254,74 @@ def batched_bench(G, steps, warmup, nbox=512):
     return out
 
 
+# --------------------------------------------------------------- adjoint --
+def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
+    """64^3 periodic flat block, WENO5, 20 SSP-RK3 steps, L = sum rho^2 dV:
+    time of the checkpointed adjoint (backward) against the forward pass, and
+    the adjoint gradient against central differences along ndir smooth random
+    directions (initial primitives and Gamma together)."""
+    import dataclasses
+    import torch
+    from paper_2210_17509_gb300 import adjoint as A
+    blk, prim_h, _ = I.smooth_flat(n, seed=3)
+    g = G.Grid(blk.n, 3, blk.dx)
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    dt = 0.25 * blk.dx[0]
+    prim0 = torch.from_numpy(prim_h[:, 3:-3, 3:-3, 3:-3].copy()).cuda()
+
+    def run(with_grad):
+        x = prim0.clone().requires_grad_(with_grad)
+        gam = torch.tensor(p.gamma, dtype=torch.float64, requires_grad=with_grad)
+        L = A.density_l2(A.evolve(x, gam, g, p, G.RK3, dt, nsteps, checkpoint_every=every), g)
+        return x, gam, L
+
+    run(True)[2].backward()          # warm-up (module load, workspaces)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    x, gam, L = run(True)
+    e1.record()
+    L.backward()
+    e2.record()
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1)
+    t_bwd = e1.elapsed_time(e2)
+    # plain forward without checkpoint copies, for context
+    e0.record()
+    with torch.no_grad():
+        run(False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1)
+    # central differences along smooth random directions
+    rng = np.random.default_rng(123)
+    h = 1e-7
+    errs = []
+    for k in range(ndir):
+        d = I.smooth_prims(blk, 5000 + k)[:, 3:-3, 3:-3, 3:-3]
+        d = d - d.mean(axis=(1, 2, 3), keepdims=True)
+        d = d / np.abs(d).max(axis=(1, 2, 3), keepdims=True)
+        dt_ = torch.from_numpy(np.ascontiguousarray(d)).cuda() * prim0.abs().amax(dim=(1, 2, 3), keepdim=True)
+        dg = float(rng.normal())
+
+        def loss(p0, gm):
+            with torch.no_grad():
+                pp = dataclasses.replace(p)
+                return float(A.density_l2(A.evolve(p0, torch.tensor(gm, dtype=torch.float64), g, pp, G.RK3, dt,
+                                                   nsteps), g))
+        fd = (loss(prim0 + h * dt_, p.gamma + h * dg) - loss(prim0 - h * dt_, p.gamma - h * dg)) / (2 * h)
+        ad = float((x.grad * dt_).sum()) + float(gam.grad) * dg
+        errs.append(abs(fd - ad) / abs(ad))
+    return {
+        "workload": f"{n}^3 periodic flat, WENO5+HLLE, {nsteps} SSP-RK3 steps, checkpoint every {every}, "
+                    "L = sum rho^2 dV, gradient w.r.t. initial primitives [8,64,64,64] and Gamma",
+        "forward_ms": t_fwd, "backward_ms": t_bwd, "forward_plain_ms": t_plain,
+        "adjoint_forward_ratio": t_bwd / t_fwd, "adjoint_plain_forward_ratio": t_bwd / t_plain,
+        "fd_check": {"directions": ndir, "h": h, "max_rel_err": max(errs), "median_rel_err": float(np.median(errs))},
+        "loss": float(L.item()),
+    }
+
+
 # ------------------------------------------------------------------- GPU --
 def main():
     ap = argparse.ArgumentParser()
@@ -265,6 +333,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -421,6 +490,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_bench(G, args.steps, args.warmup)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_bench(G)
 
     if rank != 0:
         return
@@ -440,6 +512,7 @@ def main():
         "clocks": clk,
         "e2e": e2e,
         "batched": batched,
+        "adjoint": adjoint,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

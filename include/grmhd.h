@@ -144,6 +144,14 @@ int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* 
 /* Bytes of device workspace grmhd_rk_step needs for `scheme`. */
 size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
 
+/* Bytes of workspace with which grmhd_rk_step runs the mixed-precision path
+ * from caches: an FP32 copy of the primitives and a geometry cache of the
+ * metric (sqrt(gamma), inverse metric and metric derivatives computed in FP64
+ * once per step, stored as FP32).  With less (but at least
+ * grmhd_rk_workspace_bytes) the mixed RHS reads the FP64 inputs instead;
+ * FP64 steps never use the extra space. */
+size_t grmhd_rk_workspace_bytes_mixed(const grmhd_grid* grid, int32_t scheme);
+
 /* One method-of-lines step of size dt (Sec. 2.3; integrators RK2/RK4 as in
  * Secs. 4-5, and SSP RK3).  Every stage evaluates the RHS from the current
  * primitives and folds the stage combination into the RHS epilogue, then

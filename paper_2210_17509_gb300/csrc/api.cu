@@ -171,6 +171,13 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
   return scheme == GRMHD_RK4 ? 2 * field : field;
 }
 
+size_t grmhd_rk_workspace_bytes_mixed(const grmhd_grid* grid, int32_t scheme) {
+  const size_t base = grmhd_rk_workspace_bytes(grid, scheme);
+  if (base == 0) return 0;
+  const DevGrid g = make_grid(*grid);
+  return base + round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kGeomCacheComps * g.ncell * sizeof(float));
+}
+
 int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
                   double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes,
                   int32_t* nfail, void* stream) {
@@ -194,6 +201,19 @@ int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t sc
 
   cudaError_t ce = cudaMemcpyAsync(u0, cons, (size_t)8 * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (ce != cudaSuccess) return GRMHD_ERR_CUDA;
+  // Mixed precision with room for the caches: FP32 primitive copy + geometry
+  // cache (rebuilt here, once per step) feed the RHS; otherwise the RHS reads
+  // the FP64 inputs directly.
+  const bool fast_mixed = p.precision == GRMHD_MIXED && ws_bytes >= grmhd_rk_workspace_bytes_mixed(grid, scheme);
+  float* prim32 = nullptr;
+  float* geom = nullptr;
+  if (fast_mixed) {
+    char* after = static_cast<char*>(ws) + grmhd_rk_workspace_bytes(grid, scheme);
+    prim32 = reinterpret_cast<float*>(after);
+    geom = reinterpret_cast<float*>(after + round256((size_t)8 * g.ncell * sizeof(float)));
+    if (metric && launch_geom_cache(g, metric, geom, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  }
 
   // Stage coefficients: u <- c0 u0 + c1 u + cr L (+ ca acc); acc <- wa acc + wr L.
   struct Stage { double c0, c1, cr, ca, wa, wr; bool acc_in, acc_out; };
@@ -227,6 +247,14 @@ int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t sc
     ep.ca = st[k].ca;
     ep.wa = st[k].wa;
     ep.wr = st[k].wr;
+    if (fast_mixed) {
+      if (launch_rhs_mixed_cached(g, p, prim32, geom, kij, metric != nullptr, ep, s) != cudaSuccess)
+        return GRMHD_ERR_CUDA;
+      if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, nfail, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (launch_fill_ghosts_f32(g, p.bc, 8, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (k == ns - 1 && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      continue;
+    }
     if ((ce = launch_rhs(g, p, prim, metric, kij, ep, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
     if ((ce = launch_con2prim(g, p, cons, metric, prim, nullptr, nfail, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
     if ((ce = launch_fill_ghosts(g, p.bc, 8, prim, s)) != cudaSuccess) return GRMHD_ERR_CUDA;

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* h
     const long long t = (it - b.c2p_begin) * kBatchItem + threadIdx.x;
     if (t < nint) {
       const long long c = interior_cell(b.g, t);
-      myfail += (con2prim_at(b.g, p, b.cons, b.metric, b.prim, c) >= 2);
+      myfail += (con2prim_at<false>(b.g, p, b.cons, b.metric, b.prim, c) >= 2);
     }
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);

@@ -75,18 +75,22 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
     ep.acc_out = nullptr;
     ep.c0 = ep.c1 = ep.cr = ep.ca = ep.wa = ep.wr = 0.0;
     const DevGrid g = b.g;
+    SrcF64 src;
+    src.prim = b.prim;
+    src.metric = b.metric;
+    src.kij = nullptr;
     switch (b.tile) {
       case 1:
-        rhs_tile<T, RECON, CURVED, 16, 4, 4>(g, p, b.prim, b.metric, nullptr, ep, tx * 16, ty * 4, tz * 4, sF);
+        rhs_tile<T, RECON, CURVED, 16, 4, 4, SrcF64>(g, p, src, ep, tx * 16, ty * 4, tz * 4, sF);
         break;
       case 2:
-        rhs_tile<T, RECON, CURVED, 32, 4, 2>(g, p, b.prim, b.metric, nullptr, ep, tx * 32, ty * 4, tz * 2, sF);
+        rhs_tile<T, RECON, CURVED, 32, 4, 2, SrcF64>(g, p, src, ep, tx * 32, ty * 4, tz * 2, sF);
         break;
       case 3:
-        rhs_tile<T, RECON, CURVED, 4, 8, 8>(g, p, b.prim, b.metric, nullptr, ep, tx * 4, ty * 8, tz * 8, sF);
+        rhs_tile<T, RECON, CURVED, 4, 8, 8, SrcF64>(g, p, src, ep, tx * 4, ty * 8, tz * 8, sF);
         break;
       default:
-        rhs_tile<T, RECON, CURVED, 8, 8, 4>(g, p, b.prim, b.metric, nullptr, ep, tx * 8, ty * 8, tz * 4, sF);
+        rhs_tile<T, RECON, CURVED, 8, 8, 4, SrcF64>(g, p, src, ep, tx * 8, ty * 8, tz * 4, sF);
         break;
     }
   }

@@ -12,7 +12,7 @@ __global__ void con2prim_kernel(DevGrid g, DevParams p, const double* __restrict
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    const int st = con2prim_at(g, p, cons, metric, prim, c);
+    const int st = con2prim_at<false>(g, p, cons, metric, prim, c);
     myfail += (st >= 2);
     if (status) status[c] = (int8_t)st;
   }
@@ -56,6 +56,98 @@ __global__ void fill_ghosts_kernel(DevGrid g, int bc, int nvar, double* __restri
     fill_ghost_at(g, bc, nvar, f, c);
 }
 
+// Mixed path: FP32-predicted FP64 recovery, writing FP64 and FP32 primitives.
+__global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
+                                      const double* __restrict__ metric, double* __restrict__ prim,
+                                      float* __restrict__ prim32, int32_t* __restrict__ nfail) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  int myfail = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    myfail += (con2prim_at<true>(g, p, cons, metric, prim, c, prim32) >= 2);
+  }
+  if (nfail && myfail) atomicAdd(nfail, myfail);
+}
+
+__global__ void fill_ghosts_f32_kernel(DevGrid g, int bc, int nvar, float* __restrict__ f) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (long long)gridDim.x * blockDim.x)
+    fill_ghost_at(g, bc, nvar, f, c);
+}
+
+__global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Geometry cache of a static metric (layout in rhs.cuh, kGeomComps floats per
+// point): every FP64 quantity the mixed RHS needs, computed once in FP64.
+__global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, float* __restrict__ geom) {
+  const long long n = g.ncell;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    idx[0] = (int)(c % g.N[0]);
+    idx[1] = (int)((c / g.N[0]) % g.N[1]);
+    idx[2] = (int)(c / ((long long)g.N[0] * g.N[1]));
+    double a[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      a[q] = __ldg(metric + q * n + c);
+      geom[q * n + c] = (float)a[q];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long s = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+      float sgf = 1.0f, gupf = 1.0f;
+      if (idx[d] >= 1) {
+        double m[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] = 0.5 * (__ldg(metric + (4 + i) * n + c - s) + a[4 + i]);
+        const double cxx = m[3] * m[5] - m[4] * m[4];
+        const double cyy = m[0] * m[5] - m[2] * m[2];
+        const double czz = m[0] * m[3] - m[1] * m[1];
+        const double det = m[0] * cxx - m[1] * (m[1] * m[5] - m[4] * m[2]) + m[2] * (m[1] * m[4] - m[3] * m[2]);
+        const double cdd = d == 0 ? cxx : (d == 1 ? cyy : czz);
+        sgf = (float)sqrt(det);
+        gupf = (float)(cdd / det);
+      }
+      geom[(10 + d) * n + c] = sgf;
+      geom[(13 + d) * n + c] = gupf;
+    }
+    {
+      const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+      const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
+      const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
+      const double det = gxx * cxx + gxy * cxy + gxz * cxz;
+      const double idet = 1.0 / det;
+      geom[16 * n + c] = (float)sqrt(det);
+      geom[17 * n + c] = (float)(cxx * idet);
+      geom[18 * n + c] = (float)(cxy * idet);
+      geom[19 * n + c] = (float)(cxz * idet);
+      geom[20 * n + c] = (float)(cyy * idet);
+      geom[21 * n + c] = (float)(cyz * idet);
+      geom[22 * n + c] = (float)(czz * idet);
+    }
+    const bool inner = idx[0] >= 2 && idx[0] < g.N[0] - 2 && idx[1] >= 2 && idx[1] < g.N[1] - 2 && idx[2] >= 2 &&
+                       idx[2] < g.N[2] - 2;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const long long s = e == 0 ? 1 : (e == 1 ? g.sy : g.sz);
+      const double w = g.idx[e] * (1.0 / 12.0);
+#pragma unroll
+      for (int q = 0; q < 10; ++q) {
+        float v = 0.0f;
+        if (inner) {
+          const double* mm = metric + q * n + c;
+          v = (float)((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
+        }
+        geom[(23 + 10 * e + q) * n + c] = v;
+      }
+    }
+  }
+}
+
 static int grid_blocks(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
   const long long cap = 152LL * 64;
@@ -79,6 +171,32 @@ cudaError_t launch_prim2con(const DevGrid& g, const DevParams& p, const double* 
 
 cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field, cudaStream_t s) {
   fill_ghosts_kernel<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, bc, nvar, field);
+  return cudaGetLastError();
+}
+
+}  // namespace grmhd
+
+namespace grmhd {
+
+cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
+                                  double* prim, float* prim32, int32_t* nfail, cudaStream_t s) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  con2prim_mixed_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, nfail);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s) {
+  fill_ghosts_f32_kernel<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, bc, nvar, field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s) {
+  to_f32_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, cudaStream_t s) {
+  geom_cache_kernel<<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, geom);
   return cudaGetLastError();
 }
 

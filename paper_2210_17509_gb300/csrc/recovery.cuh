@@ -108,12 +108,52 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
   return 1;
 }
 
+// FP32 Newton predictor for the mixed path: iterates the same 2D system in
+// single precision to a relative step of 1e-6 and returns the improved (z, W)
+// (unchanged if it fails); the FP64 Newton of c2p_solve then finishes to
+// nr_tol, normally in one or two steps.
+__device__ __forceinline__ void c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
+  const float gm1g = (float)p.gm1g;
+  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
+  float zf = (float)z, Wf = (float)W;
+  if (!(zf > 0.0f) || !(Wf >= 1.0f)) return;
+  for (int it = 0; it < 30; ++it) {
+    const float iz = 1.0f / zf, iW = 1.0f / Wf;
+    const float iW2 = iW * iW, iW3 = iW2 * iW, iz2 = iz * iz, iz3 = iz2 * iz;
+    const float zb = zf + B2;
+    const float f1 = zb * zb * (1.0f - iW2) - S2 - BS2 * (2.0f * zf + B2) * iz2;
+    const float f2 = tau + D - zf - B2 + 0.5f * B2 * iW2 + 0.5f * BS2 * iz2 + gm1g * (zf * iW2 - D * iW);
+    const float J11 = 2.0f * zb * (1.0f - iW2) + 2.0f * BS2 * zb * iz3;
+    const float J12 = 2.0f * zb * zb * iW3;
+    const float J21 = -1.0f - BS2 * iz3 + gm1g * iW2;
+    const float J22 = -B2 * iW3 + gm1g * (D * iW2 - 2.0f * zf * iW3);
+    const float idet = 1.0f / (J11 * J22 - J12 * J21);
+    const float dz = (f1 * J22 - f2 * J12) * idet;
+    const float dW = (J11 * f2 - J21 * f1) * idet;
+    if (!isfinite(dz) || !isfinite(dW)) return;
+    float zn = zf - dz, Wn = Wf - dW;
+    if (!(zn > 0.0f)) zn = 0.5f * zf;
+    if (!(Wn >= 1.0f)) Wn = 0.5f * (Wf + 1.0f);
+    const bool conv = fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf;
+    zf = zn;
+    Wf = Wn;
+    if (conv) break;
+  }
+  if (zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf)) {
+    z = (double)zf;
+    W = (double)Wf;
+  }
+}
+
 // Recovery of the interior cell c (Sec. 2.3).  The incoming primitives of
 // the cell are the Newton initial guess and are overwritten with the result.
 // Returns the status: 0 Newton, 1 bisection, 2 atmosphere, 3 pressure floor.
+// With PREDICT, an FP32 Newton predictor runs before the FP64 Newton and the
+// result is also stored as FP32 in prim32 (the mixed path's RHS input).
+template <bool PREDICT>
 __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p, const double* __restrict__ cons,
                                            const double* __restrict__ metric, double* __restrict__ prim,
-                                           long long c) {
+                                           long long c, float* __restrict__ prim32 = nullptr) {
   CellMetric m;
   cell_metric(metric, g.ncell, c, m);
   const double isg = 1.0 / m.sqrtg;
@@ -143,7 +183,10 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   double W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
   double z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
   int st = 2;
-  if (D > 0.0 && tau + D > 0.0) st = c2p_solve(in, p, z, W);
+  if (D > 0.0 && tau + D > 0.0) {
+    if (PREDICT) c2p_predict_fp32(in, p, z, W);
+    st = c2p_solve(in, p, z, W);
+  }
   double out[8];
   if (st != 2) {
     const double rho = D / W;
@@ -179,13 +222,17 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   out[7] = B[2];
 #pragma unroll
   for (int q = 0; q < 8; ++q) pc[q * g.ncell] = out[q];
+  if (PREDICT) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = (float)out[q];
+  }
   return st;
 }
 
 // Ghost point c copies its source: periodic wrap or the nearest interior
 // point, per axis (edges and corners included).  Interior points: no-op.
-__device__ __forceinline__ void fill_ghost_at(const DevGrid& g, int bc, int nvar, double* __restrict__ f,
-                                              long long c) {
+template <class F>
+__device__ __forceinline__ void fill_ghost_at(const DevGrid& g, int bc, int nvar, F* __restrict__ f, long long c) {
   int idx[3];
   idx[0] = (int)(c % g.N[0]);
   const long long r = c / g.N[0];

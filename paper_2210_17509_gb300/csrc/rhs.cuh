@@ -13,46 +13,113 @@
 
 namespace grmhd {
 
+// Where the kernels read their inputs from.
+//  SrcF64:   primitives and metric as stored (FP64); the FP64 path, and the
+//            mixed path when no workspace for the caches is available.
+//  SrcCache: FP32 copy of the primitives plus the FP32 geometry cache (metric
+//            values, face and cell sqrt(gamma) and inverse-metric entries and
+//            metric derivatives, all computed in FP64 once per step); the fast
+//            mixed path.
+struct SrcF64 {
+  const double* __restrict__ prim;
+  const double* __restrict__ metric;
+  const double* __restrict__ kij;
+};
+struct SrcCache {
+  const float* __restrict__ prim;
+  const float* __restrict__ geom;
+  const double* __restrict__ kij;
+};
+
+// Geometry cache layout ([comp][ncell] floats, every point of the block):
+//   0..9    metric (alpha, beta^i, gamma_ij)
+//   10..12  sqrt(gamma) on the lower x / y / z face of the point
+//   13..15  gamma^{dd} on the lower x / y / z face
+//   16      sqrt(gamma) at the point;  17..22 gamma^{ij} at the point
+//   23..52  4th-order derivatives d_e of the 10 metric entries (index 23 + 10 e + q)
+constexpr int kGeomComps = 53;
+
+template <class T>
+__device__ __forceinline__ T ld_prim(const SrcF64& s, long long i) { return (T)__ldg(s.prim + i); }
+template <class T>
+__device__ __forceinline__ T ld_prim(const SrcCache& s, long long i) { return (T)__ldg(s.prim + i); }
+
 // Load the 8 primitives at the six-point stencil of the face between cell
 // c - stride and c, reconstruct both states.
-template <class T, int RECON>
-__device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim, long long ncell, long long c,
-                                                 long long stride, T eps, T pL[8], T pR[8]) {
+template <class T, int RECON, class S>
+__device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, long long c, long long stride, T eps,
+                                                 T pL[8], T pR[8]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double* a = prim + q * ncell + c;
+    const long long a = q * ncell + c;
     if (RECON == GRMHD_WENO5) {
-      const T um3 = (T)__ldg(a - 3 * stride), um2 = (T)__ldg(a - 2 * stride), um1 = (T)__ldg(a - stride);
-      const T u0 = (T)__ldg(a), up1 = (T)__ldg(a + stride), up2 = (T)__ldg(a + 2 * stride);
+      const T um3 = ld_prim<T>(src, a - 3 * stride), um2 = ld_prim<T>(src, a - 2 * stride);
+      const T um1 = ld_prim<T>(src, a - stride), u0 = ld_prim<T>(src, a);
+      const T up1 = ld_prim<T>(src, a + stride), up2 = ld_prim<T>(src, a + 2 * stride);
       pL[q] = weno5<T>(um3, um2, um1, u0, up1, eps);
       pR[q] = weno5<T>(up2, up1, u0, um1, um2, eps);
     } else {
-      const T um2 = (T)__ldg(a - 2 * stride), um1 = (T)__ldg(a - stride);
-      const T u0 = (T)__ldg(a), up1 = (T)__ldg(a + stride);
+      const T um2 = ld_prim<T>(src, a - 2 * stride), um1 = ld_prim<T>(src, a - stride);
+      const T u0 = ld_prim<T>(src, a), up1 = ld_prim<T>(src, a + stride);
       pL[q] = um1 + T(0.5) * minmod<T>(um1 - um2, u0 - um1);
       pR[q] = u0 - T(0.5) * minmod<T>(u0 - um1, up1 - u0);
     }
   }
 }
 
-template <class T, int RECON, bool CURVED, int DIR>
-__device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
-                                          const double* __restrict__ metric, long long c, T F[8]) {
+// Legacy form used by the adjoint (FP64 primitives).
+template <class T, int RECON>
+__device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim, long long ncell, long long c,
+                                                 long long stride, T eps, T pL[8], T pR[8]) {
+  SrcF64 s;
+  s.prim = prim;
+  s.metric = nullptr;
+  s.kij = nullptr;
+  reconstruct_face<T, RECON, SrcF64>(s, ncell, c, stride, eps, pL, pR);
+}
+
+// Face metric from the inputs (FP64 mean, FP64 sqrt(gamma) and gamma^dd).
+template <class T, int DIR>
+__device__ __forceinline__ void face_geometry(const SrcF64& s, long long ncell, long long c, long long stride,
+                                              Geom<T>& m) {
+  face_geom<T, DIR>(s.metric, ncell, c, stride, m);
+}
+
+// Face metric from the cache: FP32 mean of the two cells, cached sqrt(gamma)
+// and gamma^dd of the face.
+template <class T, int DIR>
+__device__ __forceinline__ void face_geometry(const SrcCache& s, long long ncell, long long c, long long stride,
+                                              Geom<T>& m) {
+  const float* gm = s.geom;
+  T a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = T(0.5) * ((T)__ldg(gm + q * ncell + c - stride) + (T)__ldg(gm + q * ncell + c));
+  m.alpha = a[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.beta[i] = a[1 + i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m.g[i] = a[4 + i];
+  m.sqrtg = (T)__ldg(gm + (10 + DIR) * ncell + c);
+  m.gup_dd = (T)__ldg(gm + (13 + DIR) * ncell + c);
+}
+
+template <class T, int RECON, bool CURVED, int DIR, class S>
+__device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, const S& src, long long c, T F[8]) {
   const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
   T pL[8], pR[8];
-  reconstruct_face<T, RECON>(prim, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+  reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
   Geom<T> m;
-  if (CURVED) face_geom<T, DIR>(metric, g.ncell, c, stride, m);
+  if (CURVED) face_geometry<T, DIR>(src, g.ncell, c, stride, m);
   // A face state with rho <= 0, P <= 0 or v^2 >= 1 falls back to the state of
   // the cell it was reconstructed from (rare; WENO5 overshoot at sharp
   // gradients of under-resolved data).
   if (!physical_state<T, CURVED>(pL, m)) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) pL[q] = (T)__ldg(prim + q * g.ncell + c - stride);
+    for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
   }
   if (!physical_state<T, CURVED>(pR, m)) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) pR[q] = (T)__ldg(prim + q * g.ncell + c);
+    for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
   }
   Side<T> L, R;
   side_state<T, CURVED, DIR>(pL, m, (T)p.gamma, (T)p.gfac, L);
@@ -67,41 +134,22 @@ __device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, 
 //             + T^0i (2 beta^j K_ij - d_i alpha) + T^ij K_ij ]
 // Metric derivatives by 4th-order centred differences of the cell-centred
 // metric; the spatial inverse and sqrt(gamma) in FP64.
-template <class T>
-__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
-                                             const double* __restrict__ metric, const double* __restrict__ kij,
-                                             long long c, T src[8]) {
-  double a[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) a[q] = __ldg(metric + q * g.ncell + c);
-  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
-  const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
-  const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
-  const double det = gxx * cxx + gxy * cxy + gxz * cxz;
-  const double idet = 1.0 / det;
-  const T sg = (T)sqrt(det);
-  const T gu[6] = {(T)(cxx * idet), (T)(cxy * idet), (T)(cxz * idet),
-                   (T)(cyy * idet), (T)(cyz * idet), (T)(czz * idet)};
-  const T alpha = (T)a[0];
-  const T beta[3] = {(T)a[1], (T)a[2], (T)a[3]};
-  const T gm[6] = {(T)gxx, (T)gxy, (T)gxz, (T)gyy, (T)gyz, (T)gzz};
-  // derivatives d[e][q] of the 10 metric components
-  T dA[3][10];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const long long s = (e == 0) ? 1 : ((e == 1) ? g.sy : g.sz);
-    const double w = g.idx[e] * (1.0 / 12.0);
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      const double* m = metric + q * g.ncell + c;
-      dA[e][q] = (T)((8.0 * (__ldg(m + s) - __ldg(m - s)) - (__ldg(m + 2 * s) - __ldg(m - 2 * s))) * w);
-    }
-  }
+// Eq. 13 in 3+1 form for a static-in-time lapse and shift:
+//   S_{S_j} = alpha sqrt(gamma) [ T^00 (beta^i beta^k d_j g_ik / 2 - alpha d_j alpha)
+//             + T^0i beta^k d_j g_ik + T^0_i d_j beta^i + T^ik d_j g_ik / 2 ]
+//   S_tau   = alpha sqrt(gamma) [ T^00 (beta^i beta^j K_ij - beta^i d_i alpha)
+//             + T^0i (2 beta^j K_ij - d_i alpha) + T^ij K_ij ]
+// from the cell's metric (alpha, beta, gamma_ij, sqrt(gamma), gamma^ij) and
+// the metric derivatives dA[e][q].
+template <class T, class S>
+__device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p, const S& src, long long c,
+                                            const T alpha, const T beta[3], const T gm[6], const T sg, const T gu[6],
+                                            const T dA[3][10], T out[8]) {
   // fluid at the cell centre
-  const double* pc = prim + c;
-  const T rho = (T)__ldg(pc), P = (T)__ldg(pc + 4 * g.ncell);
-  const T v[3] = {(T)__ldg(pc + g.ncell), (T)__ldg(pc + 2 * g.ncell), (T)__ldg(pc + 3 * g.ncell)};
-  const T B[3] = {(T)__ldg(pc + 5 * g.ncell), (T)__ldg(pc + 6 * g.ncell), (T)__ldg(pc + 7 * g.ncell)};
+  const T rho = ld_prim<T>(src, c), P = ld_prim<T>(src, c + 4 * g.ncell);
+  const T v[3] = {ld_prim<T>(src, c + g.ncell), ld_prim<T>(src, c + 2 * g.ncell), ld_prim<T>(src, c + 3 * g.ncell)};
+  const T B[3] = {ld_prim<T>(src, c + 5 * g.ncell), ld_prim<T>(src, c + 6 * g.ncell),
+                  ld_prim<T>(src, c + 7 * g.ncell)};
   T vl[3], Bl[3], bl_[3];
   lower(gm, v, vl);
   lower(gm, B, Bl);
@@ -147,7 +195,7 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   const T asg = alpha * sg;
   // symmetric contraction weights: off-diagonal entries count twice
   const T wsym[6] = {T(1), T(2), T(2), T(1), T(2), T(1)};
-  src[0] = T(0);
+  out[0] = T(0);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     T bbdg = T(0), t0dg = T(0), tdg = T(0);
@@ -161,15 +209,15 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
       tdg += Tij[s] * dg;
     }
     const T t0db = T0l[0] * dA[j][1] + T0l[1] * dA[j][2] + T0l[2] * dA[j][3];
-    src[1 + j] = asg * (T00 * (T(0.5) * bbdg - alpha * dA[j][0]) + t0dg + t0db + T(0.5) * tdg);
+    out[1 + j] = asg * (T00 * (T(0.5) * bbdg - alpha * dA[j][0]) + t0dg + t0db + T(0.5) * tdg);
   }
   {
     T t = -(T0[0] * dA[0][0] + T0[1] * dA[1][0] + T0[2] * dA[2][0]);
     t -= T00 * (beta[0] * dA[0][0] + beta[1] * dA[1][0] + beta[2] * dA[2][0]);
-    if (kij) {
+    if (src.kij) {
       T K[6];
 #pragma unroll
-      for (int s = 0; s < 6; ++s) K[s] = (T)__ldg(kij + s * g.ncell + c);
+      for (int s = 0; s < 6; ++s) K[s] = (T)__ldg(src.kij + s * g.ncell + c);
       T bK[3];
       lower(K, beta, bK);  // K_ij beta^j
       const T bbK = beta[0] * bK[0] + beta[1] * bK[1] + beta[2] * bK[2];
@@ -179,9 +227,67 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
       for (int s = 0; s < 6; ++s) TK += Tij[s] * K[s] * wsym[s];
       t += T00 * bbK + T(2) * tK + TK;
     }
-    src[4] = asg * t;
+    out[4] = asg * t;
   }
-  src[5] = src[6] = src[7] = T(0);
+  out[5] = out[6] = out[7] = T(0);
+}
+
+// Metric quantities from the FP64 inputs: inverse and sqrt(gamma) in FP64,
+// 4th-order centred differences of the cell-centred metric.
+template <class T>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcF64& src, long long c,
+                                             T out[8]) {
+  const double* __restrict__ metric = src.metric;
+  double a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = __ldg(metric + q * g.ncell + c);
+  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+  const double cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
+  const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
+  const double det = gxx * cxx + gxy * cxy + gxz * cxz;
+  const double idet = 1.0 / det;
+  const T sg = (T)sqrt(det);
+  const T gu[6] = {(T)(cxx * idet), (T)(cxy * idet), (T)(cxz * idet),
+                   (T)(cyy * idet), (T)(cyz * idet), (T)(czz * idet)};
+  const T alpha = (T)a[0];
+  const T beta[3] = {(T)a[1], (T)a[2], (T)a[3]};
+  const T gm[6] = {(T)gxx, (T)gxy, (T)gxz, (T)gyy, (T)gyz, (T)gzz};
+  // derivatives d[e][q] of the 10 metric components
+  T dA[3][10];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long s = (e == 0) ? 1 : ((e == 1) ? g.sy : g.sz);
+    const double w = g.idx[e] * (1.0 / 12.0);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const double* m = metric + q * g.ncell + c;
+      dA[e][q] = (T)((8.0 * (__ldg(m + s) - __ldg(m - s)) - (__ldg(m + 2 * s) - __ldg(m - 2 * s))) * w);
+    }
+  }
+  source_core<T, SrcF64>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+}
+
+// Metric quantities from the geometry cache.
+template <class T>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcCache& src, long long c,
+                                             T out[8]) {
+  const float* gc = src.geom;
+  const long long n = g.ncell;
+  const T alpha = (T)__ldg(gc + c);
+  const T beta[3] = {(T)__ldg(gc + n + c), (T)__ldg(gc + 2 * n + c), (T)__ldg(gc + 3 * n + c)};
+  T gm[6], gu[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    gm[i] = (T)__ldg(gc + (4 + i) * n + c);
+    gu[i] = (T)__ldg(gc + (17 + i) * n + c);
+  }
+  const T sg = (T)__ldg(gc + 16 * n + c);
+  T dA[3][10];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+#pragma unroll
+    for (int q = 0; q < 10; ++q) dA[e][q] = (T)__ldg(gc + (23 + 10 * e + q) * n + c);
+  source_core<T, SrcCache>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
 }
 
 // Tile shapes the kernels are instantiated for (cells per axis, 256 cells each).
@@ -207,10 +313,9 @@ constexpr int kMaxTileFaces = 968;
 // shared buffer sF [8][NF], then each thread differences its cell's faces,
 // adds the sources and applies the stage epilogue.  Called by all threads of
 // the CTA (contains __syncthreads); NT = TX*TY*TZ threads.
-template <class T, int RECON, bool CURVED, int TX, int TY, int TZ>
-__device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
-                                         const double* __restrict__ metric, const double* __restrict__ kij,
-                                         const StageEpilogue& ep, int x0, int y0, int z0, T* sF) {
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
+__device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
+                                         int x0, int y0, int z0, T* sF) {
   constexpr int NT = TX * TY * TZ;
   constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
   constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
@@ -225,7 +330,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       ok = (xi <= g.n[0]) && (yi < g.n[1]) && (zi < g.n[2]);
       if (ok) {
         const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 0>(g, p, prim, metric, c, F);
+        face_flux<T, RECON, CURVED, 0, S>(g, p, src, c, F);
       }
     } else if (f < NFX + NFY) {
       const int ff = f - NFX;
@@ -234,7 +339,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       ok = (xi < g.n[0]) && (yi <= g.n[1]) && (zi < g.n[2]);
       if (ok) {
         const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 1>(g, p, prim, metric, c, F);
+        face_flux<T, RECON, CURVED, 1, S>(g, p, src, c, F);
       }
     } else {
       const int ff = f - NFX - NFY;
@@ -243,7 +348,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       ok = (xi < g.n[0]) && (yi < g.n[1]) && (zi <= g.n[2]);
       if (ok) {
         const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 2>(g, p, prim, metric, c, F);
+        face_flux<T, RECON, CURVED, 2, S>(g, p, src, c, F);
       }
     }
     if (ok) {
@@ -271,10 +376,10 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       r[q] = acc;
     }
     if (CURVED) {
-      T src[8];
-      source_terms<T>(g, p, prim, metric, kij, c, src);
+      T sv[8];
+      source_terms<T>(g, p, src, c, sv);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) r[q] += src[q];
+      for (int q = 0; q < 8; ++q) r[q] += sv[q];
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -288,46 +393,54 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   }
 }
 
-template <class T, int RECON, bool CURVED, int SHAPE>
-__global__ void __launch_bounds__(kTileThreads) rhs_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
-                                                           const double* __restrict__ metric,
-                                                           const double* __restrict__ kij, StageEpilogue ep) {
-  using S = TileShape<SHAPE>;
+template <class T, int RECON, bool CURVED, int SHAPE, class S>
+__global__ void __launch_bounds__(kTileThreads) rhs_kernel(DevGrid g, DevParams p, S src, StageEpilogue ep) {
+  using TS = TileShape<SHAPE>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);
-  rhs_tile<T, RECON, CURVED, S::X, S::Y, S::Z>(g, p, prim, metric, kij, ep, blockIdx.x * S::X, blockIdx.y * S::Y,
-                                                blockIdx.z * S::Z, sF);
+  rhs_tile<T, RECON, CURVED, TS::X, TS::Y, TS::Z, S>(g, p, src, ep, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                      blockIdx.z * TS::Z, sF);
 }
 
-template <class T, int RECON, bool CURVED>
-cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, const double* prim,
-                             const double* metric, const double* kij, const StageEpilogue& ep, cudaStream_t s) {
-  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, StageEpilogue) = nullptr;
+template <class T, int RECON, bool CURVED, class S>
+cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
+                             cudaStream_t s) {
+  void (*k)(DevGrid, DevParams, S, StageEpilogue) = nullptr;
   int tx = 8, ty = 8, tz = 4;
   switch (shape) {
-    case 1: k = rhs_kernel<T, RECON, CURVED, 1>; tx = TileShape<1>::X; ty = TileShape<1>::Y; tz = TileShape<1>::Z; break;
-    case 2: k = rhs_kernel<T, RECON, CURVED, 2>; tx = TileShape<2>::X; ty = TileShape<2>::Y; tz = TileShape<2>::Z; break;
-    case 3: k = rhs_kernel<T, RECON, CURVED, 3>; tx = TileShape<3>::X; ty = TileShape<3>::Y; tz = TileShape<3>::Z; break;
-    default: k = rhs_kernel<T, RECON, CURVED, 0>; break;
+    case 1: k = rhs_kernel<T, RECON, CURVED, 1, S>; tx = TileShape<1>::X; ty = TileShape<1>::Y; tz = TileShape<1>::Z; break;
+    case 2: k = rhs_kernel<T, RECON, CURVED, 2, S>; tx = TileShape<2>::X; ty = TileShape<2>::Y; tz = TileShape<2>::Z; break;
+    case 3: k = rhs_kernel<T, RECON, CURVED, 3, S>; tx = TileShape<3>::X; ty = TileShape<3>::Y; tz = TileShape<3>::Z; break;
+    default: k = rhs_kernel<T, RECON, CURVED, 0, S>; break;
   }
   const size_t smem = (size_t)8 * kMaxTileFaces * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((g.n[0] + tx - 1) / tx, (g.n[1] + ty - 1) / ty, (g.n[2] + tz - 1) / tz);
-  k<<<grid, kTileThreads, smem, s>>>(g, p, prim, metric, kij, ep);
+  k<<<grid, kTileThreads, smem, s>>>(g, p, src, ep);
   return cudaGetLastError();
 }
 
-// Host-side launcher for one precision.
+// Host-side launcher for one precision and input source.
+template <class T, class S>
+cudaError_t launch_rhs_src(const DevGrid& g, const DevParams& p, const S& src, bool curved, const StageEpilogue& ep,
+                           cudaStream_t s) {
+  const int shape = p.tile;
+  if (p.recon == GRMHD_WENO5)
+    return curved ? launch_rhs_shape<T, GRMHD_WENO5, true, S>(shape, g, p, src, ep, s)
+                  : launch_rhs_shape<T, GRMHD_WENO5, false, S>(shape, g, p, src, ep, s);
+  return curved ? launch_rhs_shape<T, GRMHD_MINMOD, true, S>(shape, g, p, src, ep, s)
+                : launch_rhs_shape<T, GRMHD_MINMOD, false, S>(shape, g, p, src, ep, s);
+}
+
 template <class T>
 cudaError_t launch_rhs_t(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
                          const double* kij, const StageEpilogue& ep, cudaStream_t s) {
-  const int shape = p.tile;
-  if (p.recon == GRMHD_WENO5)
-    return metric ? launch_rhs_shape<T, GRMHD_WENO5, true>(shape, g, p, prim, metric, kij, ep, s)
-                  : launch_rhs_shape<T, GRMHD_WENO5, false>(shape, g, p, prim, metric, kij, ep, s);
-  return metric ? launch_rhs_shape<T, GRMHD_MINMOD, true>(shape, g, p, prim, metric, kij, ep, s)
-                : launch_rhs_shape<T, GRMHD_MINMOD, false>(shape, g, p, prim, metric, kij, ep, s);
+  SrcF64 src;
+  src.prim = prim;
+  src.metric = metric;
+  src.kij = kij;
+  return launch_rhs_src<T, SrcF64>(g, p, src, metric != nullptr, ep, s);
 }
 
 }  // namespace grmhd

@@ -11,4 +11,13 @@ cudaError_t launch_rhs_mixed(const DevGrid& g, const DevParams& p, const double*
   return launch_rhs_t<float>(g, p, prim, metric, kij, ep, s);
 }
 
+cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const float* prim32, const float* geom,
+                                    const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s) {
+  SrcCache src;
+  src.prim = prim32;
+  src.geom = geom;
+  src.kij = kij;
+  return launch_rhs_src<float, SrcCache>(g, p, src, curved, ep, s);
+}
+
 }  // namespace grmhd

@@ -68,6 +68,8 @@ _lib.grmhd_fill_ghosts.argtypes = [_pg, _I32, _I32, _P, _P]
 _lib.grmhd_rhs.argtypes = [_pg, _pp, _P, _P, _P, _P, _P]
 _lib.grmhd_rk_workspace_bytes.argtypes = [_pg, _I32]
 _lib.grmhd_rk_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_rk_workspace_bytes_mixed.argtypes = [_pg, _I32]
+_lib.grmhd_rk_workspace_bytes_mixed.restype = ctypes.c_size_t
 _lib.grmhd_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
 _lib.grmhd_rk_step_static.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P]
 _lib.grmhd_rk_step_static.restype = _I
@@ -78,7 +80,7 @@ for _name in ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rh
     getattr(_lib, _name).restype = _I
 
 C_SYMBOLS = ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rhs", "grmhd_rk_workspace_bytes",
-             "grmhd_rk_step", "grmhd_rk_step_static", "grmhd_error_string", "grmhd_version")
+             "grmhd_rk_workspace_bytes_mixed", "grmhd_rk_step", "grmhd_rk_step_static", "grmhd_error_string", "grmhd_version")
 STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -203,8 +205,14 @@ def rk_workspace_bytes(grid: Grid, scheme: int) -> int:
     return int(_lib.grmhd_rk_workspace_bytes(ctypes.byref(grid.c()), scheme))
 
 
-def workspace(grid: Grid, scheme: int, device=None):
-    nbytes = rk_workspace_bytes(grid, scheme)
+def rk_workspace_bytes_mixed(grid: Grid, scheme: int) -> int:
+    return int(_lib.grmhd_rk_workspace_bytes_mixed(ctypes.byref(grid.c()), scheme))
+
+
+def workspace(grid: Grid, scheme: int, device=None, mixed: bool = True):
+    """Device workspace for rk_step; by default large enough for the cached
+    mixed-precision path (FP64 steps use only the first part)."""
+    nbytes = rk_workspace_bytes_mixed(grid, scheme) if mixed else rk_workspace_bytes(grid, scheme)
     if nbytes == 0:
         raise GrmhdError("invalid grid or scheme for the workspace")
     # torch's caching allocator returns 512-byte aligned blocks

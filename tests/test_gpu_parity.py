@@ -307,3 +307,24 @@ def test_rk3_periodic_conserves_totals(G):
     c = interior(host(tc), 3)
     scale = np.abs(c).sum(axis=(1, 2, 3))
     assert np.all(np.abs(c.sum(axis=(1, 2, 3)) - tot0) <= 1e-13 * scale)
+
+
+def test_rk3_mixed_without_cache_workspace(G):
+    """With only the minimum workspace the mixed path reads the FP64 inputs
+    (no FP32 caches); it must meet the same 1e-5 bound."""
+    blk, prim, met = block_curved(16, seed=1, rho_range=(0.1, 1.0))
+    g, og = grids(G, blk)
+    gp, op = params(G, 1, bc=1, precision=1)
+    prim = O.fill_ghosts(og, 1, prim)
+    cons = O.prim2con(og, op.gamma, prim, met)
+    dt = 0.25 * blk.dx[0]
+    tc, tp, tm = cuda(cons), cuda(prim), cuda(met)
+    ws = G.workspace(g, G.RK3, mixed=False)
+    assert ws.numel() < G.rk_workspace_bytes_mixed(g, G.RK3)
+    for _ in range(3):
+        G.rk_step(g, gp, G.RK3, dt, tc, tp, tm, None, ws)
+    co, po = cons, prim
+    for _ in range(3):
+        co, po, _ = O.rk_step(og, op, O.RK3, dt, co, po, met)
+    err = normwise(interior(host(tc), 3), interior(co, 3))
+    assert np.all(err < MIXED_TOL), err
