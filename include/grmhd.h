@@ -85,8 +85,15 @@ typedef struct {
   double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
   int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
-  int32_t reserved;  /* must be 0 */
+  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY */
 } grmhd_params;
+
+/* flags: the metric and the grid are unchanged since the previous
+ * grmhd_rk_step with this same workspace, so the geometry cache of the
+ * mixed path (built from the metric, see grmhd_rk_workspace_bytes_mixed)
+ * is reused instead of rebuilt.  A static spacetime sets it after its first
+ * step.  Ignored by every other call. */
+#define GRMHD_REUSE_GEOMETRY 1
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 cells each).  The shape
  * changes only how the work is cut, never the result. */
@@ -261,9 +268,19 @@ int grmhd_density_l2(const grmhd_grid* grid, const double* prim, const double* m
 /* Bytes of workspace for grmhd_rk_step_adjoint (RK2 / RK3; 0 otherwise). */
 size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
 
+/* grmhd_rk_step that also records the primitives after each stage (ghosts
+ * filled) into stage_prims: stages x 8 x ncell doubles, stage k at offset
+ * k * 8 * ncell; the last one equals the step's output primitives.  Feeds
+ * grmhd_rk_step_adjoint without a second recomputation. */
+int grmhd_rk_step_record(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                         double* cons, double* prim, const double* metric, const double* kij, void* ws,
+                         size_t ws_bytes, double* stage_prims, int32_t* nfail, void* stream);
+
 /* Reverse of one grmhd_rk_step (SSP RK2 or RK3) taken from (cons, prim):
- * recomputes the stages, then sweeps them backwards.
+ * recomputes the stages (or takes them from stage_prims, as recorded by
+ * grmhd_rk_step_record for this step), then sweeps them backwards.
  *   cons, prim  in      the step's inputs (prim ghosts filled), unchanged
+ *   stage_prims in      NULL, or the recorded stage primitives of the step
  *   cons_bar    in/out  adjoint of the step's output U (interior) on entry,
  *                       adjoint of the input U on exit
  *   prim_bar    in/out  adjoint of the step's output primitives (8 x ncell,
@@ -273,8 +290,8 @@ size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
  *   ws          >= grmhd_rk_adjoint_workspace_bytes, 256-byte aligned */
 int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
                           const double* cons, const double* prim, const double* metric, const double* kij,
-                          double* cons_bar, double* prim_bar, double* gamma_bar, void* ws, size_t ws_bytes,
-                          void* stream);
+                          const double* stage_prims, double* cons_bar, double* prim_bar, double* gamma_bar,
+                          void* ws, size_t ws_bytes, void* stream);
 
 /* Size of the library-owned scratch of grmhd_rk_step_static: 64 MiB. */
 #define GRMHD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)

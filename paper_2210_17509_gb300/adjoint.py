@@ -66,12 +66,14 @@ class _Evolve(torch.autograd.Function):
             s1 = starts[k + 1] if k + 1 < len(starts) else ctx.nsteps
             cons, prim = (t.clone() for t in ctx.ckpt[s0])
             states = []
+            ns = G.stage_count(scheme)
             for s in range(s0, s1):
-                states.append((cons.clone(), prim.clone()))
-                if s + 1 < s1:
-                    G.rk_step(grid, p, scheme, dt, cons, prim, metric, None, ws)
-            for cons_s, prim_s in reversed(states):
-                G.rk_step_adjoint(grid, p, scheme, dt, cons_s, prim_s, ubar, pbar, gbar, metric, None, wsa)
+                stages = torch.empty((ns, 8) + grid.shape, dtype=torch.float64, device=dev)
+                states.append((cons.clone(), prim.clone(), stages))
+                G.rk_step_record(grid, p, scheme, dt, cons, prim, stages, metric, None, ws)
+            for cons_s, prim_s, stages in reversed(states):
+                G.rk_step_adjoint(grid, p, scheme, dt, cons_s, prim_s, ubar, pbar, gbar, metric, None, wsa,
+                                  stage_prims=stages)
         # initial data: P_full = ghost_fill(P0), U0 = prim2con(P_full)
         _, prim_init = ctx.ckpt[0]
         G.fill_ghosts_adjoint(grid, p.bc, pbar)

@@ -1013,8 +1013,8 @@ size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme) 
 
 int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
                           const double* cons, const double* prim, const double* metric, const double* kij,
-                          double* cons_bar, double* prim_bar, double* gamma_bar, void* ws, size_t ws_bytes,
-                          void* stream) {
+                          const double* stage_prims, double* cons_bar, double* prim_bar, double* gamma_bar,
+                          void* ws, size_t ws_bytes, void* stream) {
   int e = check_common(grid, params, metric);
   if (e) return e;
   if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3) return GRMHD_ERR_ARG;
@@ -1047,9 +1047,14 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
     c0[0] = 1.0; c1[0] = 0.0; cr[0] = 1.0;
     c0[1] = 0.5; c1[1] = 0.5; cr[1] = 0.5;
   }
-  // recompute the stages exactly as grmhd_rk_step does
-  if (cudaMemcpyAsync(W, cons, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-  for (int k = 0; k < ns; ++k) {
+  if (stage_prims) {
+    if (!al8(stage_prims)) return GRMHD_ERR_ARG;
+    for (int k = 1; k <= ns; ++k) Pst[k] = const_cast<double*>(stage_prims) + (size_t)(k - 1) * 8 * g.ncell;
+  }
+  // recompute the stages exactly as grmhd_rk_step does (unless recorded)
+  if (!stage_prims && cudaMemcpyAsync(W, cons, nbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  for (int k = 0; k < ns && !stage_prims; ++k) {
     StageEpilogue ep;
     ep.rhs = nullptr;
     ep.u = W;

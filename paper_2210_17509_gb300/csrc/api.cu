@@ -35,6 +35,7 @@ DevParams make_params(const grmhd_params& p) {
   d.bc = p.bc;
   d.precision = p.precision;
   d.tile = p.tile;
+  d.flags = p.flags;
   return d;
 }
 
@@ -70,6 +71,7 @@ int check_params(const grmhd_params* p) {
   if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
   if (p->tile < 0 || p->tile > 3) return GRMHD_ERR_ARG;
+  if ((p->flags & ~GRMHD_REUSE_GEOMETRY) != 0) return GRMHD_ERR_ARG;
   return GRMHD_OK;
 }
 
@@ -175,12 +177,19 @@ size_t grmhd_rk_workspace_bytes_mixed(const grmhd_grid* grid, int32_t scheme) {
   const size_t base = grmhd_rk_workspace_bytes(grid, scheme);
   if (base == 0) return 0;
   const DevGrid g = make_grid(*grid);
-  return base + round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kGeomCacheComps * g.ncell * sizeof(float));
+  return base + round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kGeomCacheComps * g.ncell * sizeof(float)) +
+         round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
 }
 
-int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
-                  double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes,
-                  int32_t* nfail, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// One step; with record != NULL the FP64 primitives after every stage are
+// also copied to record + k * 8 * ncell (k = 0 .. stages-1).
+int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
+                 double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes, int32_t* nfail,
+                 void* stream, double* record) {
   int e = check_params(params);
   if (e) return e;
   if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
@@ -207,11 +216,16 @@ int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t sc
   const bool fast_mixed = p.precision == GRMHD_MIXED && ws_bytes >= grmhd_rk_workspace_bytes_mixed(grid, scheme);
   float* prim32 = nullptr;
   float* geom = nullptr;
+  double* mcache = nullptr;
   if (fast_mixed) {
     char* after = static_cast<char*>(ws) + grmhd_rk_workspace_bytes(grid, scheme);
     prim32 = reinterpret_cast<float*>(after);
-    geom = reinterpret_cast<float*>(after + round256((size_t)8 * g.ncell * sizeof(float)));
-    if (metric && launch_geom_cache(g, metric, geom, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    after += round256((size_t)8 * g.ncell * sizeof(float));
+    geom = reinterpret_cast<float*>(after);
+    after += round256((size_t)kGeomCacheComps * g.ncell * sizeof(float));
+    mcache = reinterpret_cast<double*>(after);
+    const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
+    if (metric && !reuse && launch_geom_cache(g, metric, geom, mcache, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     if (launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
   }
 
@@ -250,16 +264,37 @@ int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t sc
     if (fast_mixed) {
       if (launch_rhs_mixed_cached(g, p, prim32, geom, kij, metric != nullptr, ep, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;
-      if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, nfail, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, metric ? mcache : nullptr, nfail, s) != cudaSuccess)
+        return GRMHD_ERR_CUDA;
       if (launch_fill_ghosts_f32(g, p.bc, 8, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-      if (k == ns - 1 && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-      continue;
+      if ((k == ns - 1 || record) && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    } else {
+      if ((ce = launch_rhs(g, p, prim, metric, kij, ep, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if ((ce = launch_con2prim(g, p, cons, metric, prim, nullptr, nfail, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if ((ce = launch_fill_ghosts(g, p.bc, 8, prim, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
     }
-    if ((ce = launch_rhs(g, p, prim, metric, kij, ep, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
-    if ((ce = launch_con2prim(g, p, cons, metric, prim, nullptr, nfail, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
-    if ((ce = launch_fill_ghosts(g, p.bc, 8, prim, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (record && cudaMemcpyAsync(record + (size_t)k * 8 * g.ncell, prim, (size_t)8 * g.ncell * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return GRMHD_ERR_CUDA;
   }
   return GRMHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grmhd_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
+                  double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes,
+                  int32_t* nfail, void* stream) {
+  return rk_step_impl(grid, params, scheme, dt, cons, prim, metric, kij, ws, ws_bytes, nfail, stream, nullptr);
+}
+
+int grmhd_rk_step_record(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
+                         double* cons, double* prim, const double* metric, const double* kij, void* ws,
+                         size_t ws_bytes, double* stage_prims, int32_t* nfail, void* stream) {
+  if (!stage_prims || !aligned8(stage_prims)) return GRMHD_ERR_ARG;
+  return rk_step_impl(grid, params, scheme, dt, cons, prim, metric, kij, ws, ws_bytes, nfail, stream, stage_prims);
 }
 
 }  // extern "C"

@@ -33,6 +33,7 @@ struct DevParams {
   int nr_maxit;
   int recon, bc, precision;
   int tile;        // RHS tile shape index (0..3)
+  int flags;       // GRMHD_REUSE_GEOMETRY, ...
 };
 
 // What the RHS kernel does with the RHS value r of each interior cell:
@@ -65,12 +66,13 @@ cudaError_t launch_prim2con(const DevGrid& g, const DevParams& p, const double* 
 cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field, cudaStream_t s);
 // Fast mixed path: FP32 primitive copy and the FP64-computed geometry cache.
 cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
-                                  double* prim, float* prim32, int32_t* nfail, cudaStream_t s);
+                                  double* prim, float* prim32, const double* mcache, int32_t* nfail, cudaStream_t s);
 cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s);
-cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, cudaStream_t s);
+cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, double* mcache, cudaStream_t s);
 cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const float* prim32, const float* geom,
                                     const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s);
 constexpr int kGeomCacheComps = 53;
+constexpr int kMetricCacheComps = 7;
 
 }  // namespace grmhd

@@ -59,13 +59,14 @@ __global__ void fill_ghosts_kernel(DevGrid g, int bc, int nvar, double* __restri
 // Mixed path: FP32-predicted FP64 recovery, writing FP64 and FP32 primitives.
 __global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                       const double* __restrict__ metric, double* __restrict__ prim,
-                                      float* __restrict__ prim32, int32_t* __restrict__ nfail) {
+                                      float* __restrict__ prim32, const double* __restrict__ mcache,
+                                      int32_t* __restrict__ nfail) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   int myfail = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    myfail += (con2prim_at<true>(g, p, cons, metric, prim, c, prim32) >= 2);
+    myfail += (con2prim_at<true>(g, p, cons, metric, prim, c, prim32, mcache) >= 2);
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }
@@ -83,7 +84,10 @@ __global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* 
 
 // Geometry cache of a static metric (layout in rhs.cuh, kGeomComps floats per
 // point): every FP64 quantity the mixed RHS needs, computed once in FP64.
-__global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, float* __restrict__ geom) {
+// mcache (FP64, 7 components per point): 1/sqrt(gamma) and gamma^ij for the
+// primitive recovery.
+__global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, float* __restrict__ geom,
+                                  double* __restrict__ mcache) {
   const long long n = g.ncell;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     int idx[3];
@@ -121,7 +125,15 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       const double cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
       const double det = gxx * cxx + gxy * cxy + gxz * cxz;
       const double idet = 1.0 / det;
-      geom[16 * n + c] = (float)sqrt(det);
+      const double sgd = sqrt(det);
+      geom[16 * n + c] = (float)sgd;
+      mcache[c] = 1.0 / sgd;
+      mcache[1 * n + c] = cxx * idet;
+      mcache[2 * n + c] = cxy * idet;
+      mcache[3 * n + c] = cxz * idet;
+      mcache[4 * n + c] = cyy * idet;
+      mcache[5 * n + c] = cyz * idet;
+      mcache[6 * n + c] = czz * idet;
       geom[17 * n + c] = (float)(cxx * idet);
       geom[18 * n + c] = (float)(cxy * idet);
       geom[19 * n + c] = (float)(cxz * idet);
@@ -179,9 +191,9 @@ cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field
 namespace grmhd {
 
 cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
-                                  double* prim, float* prim32, int32_t* nfail, cudaStream_t s) {
+                                  double* prim, float* prim32, const double* mcache, int32_t* nfail, cudaStream_t s) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  con2prim_mixed_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, nfail);
+  con2prim_mixed_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache, nfail);
   return cudaGetLastError();
 }
 
@@ -195,8 +207,8 @@ cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, cudaStream_t s) {
-  geom_cache_kernel<<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, geom);
+cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, double* mcache, cudaStream_t s) {
+  geom_cache_kernel<<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, geom, mcache);
   return cudaGetLastError();
 }
 

@@ -57,7 +57,11 @@ __device__ __forceinline__ double c2p_energy_of_z(const C2PIn& in, double z, dou
 }
 
 // Returns 0 (Newton converged), 1 (bisection), 2 (failed); z, W on exit.
-static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W) {
+// tol_first applies to the first Newton step only: after an FP32 predictor
+// that converged to 1e-6, one FP64 step leaves an error of order 1e-12 times
+// the problem's curvature scale (quadratic convergence), so a first step
+// below tol_first ends the solve; every later step must be below nr_tol.
+static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W, double tol_first) {
   const double gm1g = p.gm1g;
   const double D = in.D, B2 = in.B2, BS2 = in.BS2, S2 = in.S2, tau = in.tau;
   bool ok = false;
@@ -76,7 +80,8 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
       const double dz = (f1 * J22 - f2 * J12) * idet;
       const double dW = (J11 * f2 - J21 * f1) * idet;
       if (!isfinite(dz) || !isfinite(dW)) break;
-      const bool conv = fabs(dz) <= p.nr_tol * z && fabs(dW) <= p.nr_tol * W;
+      const double tol = it == 0 ? tol_first : p.nr_tol;
+      const bool conv = fabs(dz) <= tol * z && fabs(dW) <= tol * W;
       double zn = z - dz, Wn = W - dW;
       if (!(zn > 0.0)) zn = 0.5 * z;
       if (!(Wn >= 1.0)) Wn = 0.5 * (W + 1.0);
@@ -112,11 +117,12 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
 // single precision to a relative step of 1e-6 and returns the improved (z, W)
 // (unchanged if it fails); the FP64 Newton of c2p_solve then finishes to
 // nr_tol, normally in one or two steps.
-__device__ __forceinline__ void c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
+__device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
   const float gm1g = (float)p.gm1g;
   const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
   float zf = (float)z, Wf = (float)W;
-  if (!(zf > 0.0f) || !(Wf >= 1.0f)) return;
+  if (!(zf > 0.0f) || !(Wf >= 1.0f)) return false;
+  bool converged = false;
   for (int it = 0; it < 30; ++it) {
     const float iz = 1.0f / zf, iW = 1.0f / Wf;
     const float iW2 = iW * iW, iW3 = iW2 * iW, iz2 = iz * iz, iz3 = iz2 * iz;
@@ -130,33 +136,48 @@ __device__ __forceinline__ void c2p_predict_fp32(const C2PIn& in, const DevParam
     const float idet = 1.0f / (J11 * J22 - J12 * J21);
     const float dz = (f1 * J22 - f2 * J12) * idet;
     const float dW = (J11 * f2 - J21 * f1) * idet;
-    if (!isfinite(dz) || !isfinite(dW)) return;
+    if (!isfinite(dz) || !isfinite(dW)) return false;
     float zn = zf - dz, Wn = Wf - dW;
     if (!(zn > 0.0f)) zn = 0.5f * zf;
     if (!(Wn >= 1.0f)) Wn = 0.5f * (Wf + 1.0f);
     const bool conv = fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf;
     zf = zn;
     Wf = Wn;
-    if (conv) break;
+    if (conv) { converged = true; break; }
   }
   if (zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf)) {
     z = (double)zf;
     W = (double)Wf;
+    return converged;
   }
+  return false;
 }
 
 // Recovery of the interior cell c (Sec. 2.3).  The incoming primitives of
 // the cell are the Newton initial guess and are overwritten with the result.
 // Returns the status: 0 Newton, 1 bisection, 2 atmosphere, 3 pressure floor.
-// With PREDICT, an FP32 Newton predictor runs before the FP64 Newton and the
-// result is also stored as FP32 in prim32 (the mixed path's RHS input).
+// With PREDICT (mixed path) the guess comes from the FP32 primitives prim32,
+// an FP32 Newton predictor runs before the FP64 Newton, and the result is
+// also stored in prim32.  mcache (nullable) holds, per point, 1/sqrt(gamma)
+// and gamma^ij in FP64 (7 components), saving the per-call inverse.
 template <bool PREDICT>
 __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p, const double* __restrict__ cons,
                                            const double* __restrict__ metric, double* __restrict__ prim,
-                                           long long c, float* __restrict__ prim32 = nullptr) {
+                                           long long c, float* __restrict__ prim32 = nullptr,
+                                           const double* __restrict__ mcache = nullptr) {
   CellMetric m;
-  cell_metric(metric, g.ncell, c, m);
-  const double isg = 1.0 / m.sqrtg;
+  double isg;
+  if (mcache && metric) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      m.g[i] = __ldg(metric + (4 + i) * g.ncell + c);
+      m.gu[i] = __ldg(mcache + (1 + i) * g.ncell + c);
+    }
+    isg = __ldg(mcache + c);
+  } else {
+    cell_metric(metric, g.ncell, c, m);
+    isg = 1.0 / m.sqrtg;
+  }
   double U[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) U[q] = __ldg(cons + q * g.ncell + c);
@@ -175,17 +196,32 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   in.BS2 = BS * BS;
   // initial guess from the incoming primitives
   double* pc = prim + c;
-  const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
-  double vl[3];
-  lower(m.g, v, vl);
-  const double v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
-  const double rg = pc[0], Pg = pc[4 * g.ncell];
-  double W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
-  double z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
+  double W, z;
+  if (PREDICT) {
+    const float* pf = prim32 + c;
+    const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
+    const float gf[6] = {(float)m.g[0], (float)m.g[1], (float)m.g[2], (float)m.g[3], (float)m.g[4], (float)m.g[5]};
+    float vl[3];
+    lower(gf, v, vl);
+    const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+    const float rg = pf[0], Pg = pf[4 * g.ncell];
+    const float Wf = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
+    W = (double)Wf;
+    z = (rg > 0.0f && Pg > 0.0f) ? (double)((rg + (float)p.gfac * Pg) * Wf * Wf) : (tau + D + in.B2);
+  } else {
+    const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
+    double vl[3];
+    lower(m.g, v, vl);
+    const double v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+    const double rg = pc[0], Pg = pc[4 * g.ncell];
+    W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
+    z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
+  }
   int st = 2;
   if (D > 0.0 && tau + D > 0.0) {
-    if (PREDICT) c2p_predict_fp32(in, p, z, W);
-    st = c2p_solve(in, p, z, W);
+    double tol_first = p.nr_tol;
+    if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
+    st = c2p_solve(in, p, z, W, tol_first);
   }
   double out[8];
   if (st != 2) {

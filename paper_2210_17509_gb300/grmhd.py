@@ -22,6 +22,7 @@ MINMOD, WENO5 = 0, 1
 BC_PERIODIC, BC_COPY = 0, 1
 FP64, MIXED = 0, 1
 RK2, RK3, RK4 = 2, 3, 4
+REUSE_GEOMETRY = 1
 
 
 class GrmhdError(RuntimeError):
@@ -52,7 +53,7 @@ class CParams(ctypes.Structure):
         ("nr_tol", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
         ("tile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -118,10 +119,11 @@ class Params:
     nr_tol: float = 1e-12
     weno_eps: float = 1e-6
     tile: int = 0
+    flags: int = 0
 
     def c(self) -> CParams:
         return CParams(self.gamma, self.recon, self.bc, self.precision, self.nr_maxit, self.rho_atm, self.p_atm,
-                       self.nr_tol, self.weno_eps, self.tile, 0)
+                       self.nr_tol, self.weno_eps, self.tile, self.flags)
 
 
 def version() -> int:
@@ -324,14 +326,17 @@ _lib.grmhd_fill_ghosts_adjoint.argtypes = [_pg, _I32, _I32, _P, _P]
 _lib.grmhd_density_l2.argtypes = [_pg, _P, _P, ctypes.c_double, _P, _P, _P]
 _lib.grmhd_rk_adjoint_workspace_bytes.argtypes = [_pg, _I32]
 _lib.grmhd_rk_adjoint_workspace_bytes.restype = ctypes.c_size_t
-_lib.grmhd_rk_step_adjoint.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _P,
+_lib.grmhd_rk_step_adjoint.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                        ctypes.c_size_t, _P]
+_lib.grmhd_rk_step_record.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P,
+                                      _P]
+_lib.grmhd_rk_step_record.restype = _I
 for _name in ("grmhd_rhs_adjoint", "grmhd_con2prim_adjoint", "grmhd_prim2con_adjoint", "grmhd_fill_ghosts_adjoint",
               "grmhd_density_l2", "grmhd_rk_step_adjoint"):
     getattr(_lib, _name).restype = _I
 C_SYMBOLS = C_SYMBOLS + ("grmhd_rhs_adjoint", "grmhd_con2prim_adjoint", "grmhd_prim2con_adjoint",
                          "grmhd_fill_ghosts_adjoint", "grmhd_density_l2", "grmhd_rk_adjoint_workspace_bytes",
-                         "grmhd_rk_step_adjoint")
+                         "grmhd_rk_step_adjoint", "grmhd_rk_step_record")
 
 
 def _scalar(t, name):
@@ -386,13 +391,41 @@ def adjoint_workspace(grid: Grid, scheme: int, device=None):
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
+def stage_count(scheme: int) -> int:
+    return {RK2: 2, RK3: 3, RK4: 4}[scheme]
+
+
+def rk_step_record(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, stage_prims, metric=None,
+                   kij=None, ws=None, nfail=None, stream=None):
+    """rk_step that also stores the per-stage primitives in stage_prims [stages, 8, *shape]."""
+    if ws is None:
+        ws = workspace(grid, scheme, cons.device)
+    ns = stage_count(scheme)
+    if (stage_prims.dtype != torch.float64 or not stage_prims.is_cuda or not stage_prims.is_contiguous()
+            or tuple(stage_prims.shape) != (ns, 8) + grid.shape):
+        raise ValueError("stage_prims must be a contiguous CUDA float64 tensor [stages, 8, *shape]")
+    nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_rk_step_record(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
+                                   _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
+                                   _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(stage_prims.data_ptr()),
+                                   nf, _stream(stream))
+    _check(rc, "grmhd_rk_step_record")
+    return cons, prim
+
+
 def rk_step_adjoint(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, cons_bar, prim_bar, gamma_bar,
-                    metric=None, kij=None, ws=None, stream=None):
+                    metric=None, kij=None, ws=None, stream=None, stage_prims=None):
     if ws is None:
         ws = adjoint_workspace(grid, scheme, cons.device)
+    sp = None
+    if stage_prims is not None:
+        if tuple(stage_prims.shape) != (stage_count(scheme), 8) + grid.shape or not stage_prims.is_contiguous():
+            raise ValueError("stage_prims has the wrong shape")
+        sp = ctypes.c_void_p(stage_prims.data_ptr())
     rc = _lib.grmhd_rk_step_adjoint(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
                                     _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
-                                    _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                                    _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True), sp,
                                     _field(cons_bar, grid, 8, "cons_bar"), _field(prim_bar, grid, 8, "prim_bar"),
                                     _scalar(gamma_bar, "gamma_bar"), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                     _stream(stream))

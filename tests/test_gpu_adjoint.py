@@ -228,3 +228,29 @@ def test_config3_gradient_matches_central_differences(G, A):
         fd = (loss(prim0 + h * d, p.gamma + h * dg) - loss(prim0 - h * d, p.gamma - h * dg)) / (2 * h)
         ad = dot(x.grad, d) + float(gam.grad.item()) * dg
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_rk_step_adjoint_with_recorded_stages_is_identical(G):
+    g, p, prim, met, blk, _ = state(G, 8, True)
+    cons = G.prim2con(g, p, prim, met)
+    dt = 0.25 * blk.dx[0]
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    ub0 = torch.randn(prim.shape, dtype=torch.float64, device="cuda", generator=gen) * interior_mask(g)
+    pb0 = torch.randn(prim.shape, dtype=torch.float64, device="cuda", generator=gen)
+    stages = torch.empty((3, 8) + g.shape, dtype=torch.float64, device="cuda")
+    c1, p1 = cons.clone(), prim.clone()
+    G.rk_step_record(g, p, G.RK3, dt, c1, p1, stages, met)
+    c2, p2 = cons.clone(), prim.clone()
+    G.rk_step(g, p, G.RK3, dt, c2, p2, met)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2) and torch.equal(p1, p2) and torch.equal(stages[2], p1)
+    outs = []
+    for sp in (None, stages):
+        ub, pb = ub0.clone(), pb0.clone()
+        gb = torch.zeros(1, dtype=torch.float64, device="cuda")
+        G.rk_step_adjoint(g, p, G.RK3, dt, cons, prim, ub, pb, gb, met, stage_prims=sp)
+        torch.cuda.synchronize()
+        outs.append((ub, pb, gb))
+    # atomics make the summation order vary: compare to round-off
+    for a, b in zip(outs[0], outs[1]):
+        assert float((a - b).abs().max()) <= 1e-12 * float(a.abs().max())

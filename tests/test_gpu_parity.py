@@ -328,3 +328,25 @@ def test_rk3_mixed_without_cache_workspace(G):
         co, po, _ = O.rk_step(og, op, O.RK3, dt, co, po, met)
     err = normwise(interior(host(tc), 3), interior(co, 3))
     assert np.all(err < MIXED_TOL), err
+
+
+def test_mixed_geometry_reuse_flag(G):
+    """Reusing the geometry cache of a static metric gives the same steps."""
+    import dataclasses
+    blk, prim, met = block_curved(12, seed=2, rho_range=(0.1, 1.0))
+    g, og = grids(G, blk)
+    gp, op = params(G, 1, bc=1, precision=1)
+    prim = O.fill_ghosts(og, 1, prim)
+    cons = O.prim2con(og, op.gamma, prim, met)
+    dt = 0.25 * blk.dx[0]
+    res = []
+    for reuse in (False, True):
+        tc, tp, tm = cuda(cons), cuda(prim), cuda(met)
+        ws = G.workspace(g, G.RK3)
+        p = gp
+        for _ in range(3):
+            G.rk_step(g, p, G.RK3, dt, tc, tp, tm, None, ws)
+            if reuse:
+                p = dataclasses.replace(gp, flags=G.REUSE_GEOMETRY)
+        res.append(host(tc))
+    np.testing.assert_array_equal(res[0], res[1])
