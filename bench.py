@@ -319,9 +319,72 @@ def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
                     "L = sum rho^2 dV, gradient w.r.t. initial primitives [8,64,64,64] and Gamma",
         "forward_ms": t_fwd, "backward_ms": t_bwd, "forward_plain_ms": t_plain,
         "adjoint_forward_ratio": t_bwd / t_fwd, "adjoint_plain_forward_ratio": t_bwd / t_plain,
-        "fd_check": {"directions": ndir, "h": h, "max_rel_err": max(errs), "median_rel_err": float(np.median(errs))},
+        "fd_check": ({"directions": ndir, "h": h, "max_rel_err": max(errs), "median_rel_err": float(np.median(errs))}
+                     if errs else None),
         "loss": float(L.item()),
     }
+
+
+# ------------------------------------------------------------ 256^3 block --
+def large_block_bench(G, steps=3, warmup=1, n=256):
+    """256^3 + 3 ghosts on the Schwarzschild background, planar Riemann jump
+    along x with 1% perturbation, WENO5+HLLE, SSP-RK3: FP64, mixed and the
+    adjoint step, each with its HBM fraction against the per-kernel
+    algorithmic byte floor (512 B per cell per stage)."""
+    import torch
+    blk, prim_h, met_h = I.riemann_schwarzschild(n, seed=4)
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    dt = CFL * min(blk.dx)
+    met = torch.from_numpy(met_h).cuda()
+    from paper_2210_17509_gb300 import roofline as R
+    hbm, _ = R.hbm_peak_gbs()
+    out = {"workload": f"Riemann jump on Schwarzschild, {n}^3+3 ghosts, WENO5+HLLE, SSP-RK3, copy BC"}
+    ncells = blk.ncells
+    for precision, name in ((G.FP64, "fp64"), (G.MIXED, "mixed")):
+        p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision)
+        prim = torch.from_numpy(prim_h).cuda()
+        G.fill_ghosts(g, G.BC_COPY, prim)
+        cons = G.prim2con(g, p, prim, met)
+        ws = G.workspace(g, G.RK3)
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+            p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        zc = ncells / (ms * 1e-3)
+        out[name] = {"value": zc, "unit": UNIT, "ms_per_step": ms, "failed_cells": int(nfail.item()),
+                     "hbm_frac_512B_floor": 512.0 * 3 * zc / (hbm * 1e9)}
+        if precision == G.FP64:
+            # adjoint of one step from recorded stages (the checkpointed backward's unit of work)
+            stages = torch.empty((3, 8) + g.shape, dtype=torch.float64, device="cuda")
+            c0, p0 = cons.clone(), prim.clone()
+            G.rk_step_record(g, p, G.RK3, dt, cons, prim, stages, met, None, ws)
+            wsa = G.adjoint_workspace(g, G.RK3)
+            ub = torch.zeros_like(cons)
+            pb = torch.zeros_like(prim)
+            pb[0] = 1.0
+            gb = torch.zeros(1, dtype=torch.float64, device="cuda")
+            G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
+            torch.cuda.synchronize()
+            e0.record()
+            G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
+            e1.record()
+            torch.cuda.synchronize()
+            ams = e0.elapsed_time(e1)
+            out["adjoint_step"] = {"ms": ams, "ratio_to_fp64_step": ams / ms, "value": ncells / (ams * 1e-3),
+                                   "unit": "zone-cycles/s (reverse step, recorded stages)"}
+            del stages, wsa, ub, pb, c0, p0
+        del prim, cons, ws
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------- GPU --
@@ -336,6 +399,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=64)
+    ap.add_argument("--adjoint-dirs", type=int, default=50)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -496,7 +562,10 @@ def main():
         batched = batched_bench(G, args.steps, args.warmup)
     adjoint = None
     if not args.no_adjoint:
-        adjoint = adjoint_bench(G)
+        adjoint = adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs)
+    large = None
+    if not args.no_large:
+        large = large_block_bench(G)
 
     if rank != 0:
         return
@@ -517,6 +586,7 @@ def main():
         "e2e": e2e,
         "batched": batched,
         "adjoint": adjoint,
+        "block_256": large,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

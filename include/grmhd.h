@@ -95,12 +95,15 @@ typedef struct {
  * step.  Ignored by every other call. */
 #define GRMHD_REUSE_GEOMETRY 1
 
-/* RHS tile shapes (cells per CTA along x, y, z; 256 cells each).  The shape
- * changes only how the work is cut, never the result. */
+/* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
+ * shape changes only how the work is cut, never the result.  8x8x8 (two
+ * cells per thread, fewer recomputed tile-boundary faces) is for single
+ * blocks; batched boxes use 0..3. */
 #define GRMHD_TILE_8x8x4 0
 #define GRMHD_TILE_16x4x4 1
 #define GRMHD_TILE_32x4x2 2
 #define GRMHD_TILE_4x8x8 3
+#define GRMHD_TILE_8x8x8 4
 
 /* Primitive -> conserved variables, Eqs. 6-9 (Sec. 2.2), on every cell of
  * the block (ghosts included), with the metric of that cell.

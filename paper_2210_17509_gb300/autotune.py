@@ -17,12 +17,13 @@ import torch
 
 from . import grmhd as G
 
-SHAPES = {0: (8, 8, 4), 1: (16, 4, 4), 2: (32, 4, 2), 3: (4, 8, 8)}
+SHAPES = {0: (8, 8, 4), 1: (16, 4, 4), 2: (32, 4, 2), 3: (4, 8, 8)}   # batched boxes
+BLOCK_SHAPES = {**SHAPES, 4: (8, 8, 8)}                               # single blocks
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".autotune_cache.json")
 
 
 def n_tiles(shape_id: int, n) -> int:
-    s = SHAPES[shape_id]
+    s = BLOCK_SHAPES[shape_id]
     return math.prod((n[d] + s[d] - 1) // s[d] for d in range(3))
 
 
@@ -31,8 +32,9 @@ def _key(params: G.Params, curved: bool) -> str:
     return f"{name}|prec{params.precision}|recon{params.recon}|curved{int(curved)}"
 
 
-def measure_tile_costs(params: G.Params, curved: bool = False, n: int = 64, reps: int = 5) -> dict:
+def measure_tile_costs(params: G.Params, curved: bool = False, n: int = 64, reps: int = 5, shapes=None) -> dict:
     """Seconds per tile for each shape, timed with CUDA events on the current stream."""
+    shapes = SHAPES if shapes is None else shapes
     from . import inputs as I
     blk = I.Block((n, n, n), 3, (1.0 / n,) * 3, (4.0, 4.0, 4.0))
     met = I.schwarzschild_metric(blk) if curved else None
@@ -42,7 +44,7 @@ def measure_tile_costs(params: G.Params, curved: bool = False, n: int = 64, reps
     metric = None if met is None else torch.from_numpy(met).cuda()
     out = torch.empty_like(prim)
     costs = {}
-    for sid in SHAPES:
+    for sid in shapes:
         p = G.Params(**{**params.__dict__, "tile": sid})
         for _ in range(2):
             G.rhs(g, p, prim, metric, None, out)
@@ -80,3 +82,9 @@ def tile_costs(params: G.Params, curved: bool = False, refresh: bool = False) ->
 def choose(n, costs: dict) -> int:
     """Best tile shape for a box of interior extent n = (nx, ny, nz)."""
     return min(costs, key=lambda sid: (n_tiles(sid, n) * costs[sid], sid))
+
+
+def best_block_shape(params: G.Params, n, curved: bool = False) -> int:
+    """Tile shape for one large block of extent n (all five shapes timed)."""
+    costs = measure_tile_costs(params, curved, shapes=BLOCK_SHAPES)
+    return choose(n, costs)

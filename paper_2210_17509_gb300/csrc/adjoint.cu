@@ -912,7 +912,7 @@ int check_common(const grmhd_grid* grid, const grmhd_params* params, const doubl
   if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
   if (params->bc != GRMHD_BC_PERIODIC && params->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
   if (params->nr_maxit < 1 || !(params->nr_tol > 0.0) || !(params->weno_eps > 0.0)) return GRMHD_ERR_ARG;
-  if (!(params->rho_atm > 0.0) || !(params->p_atm > 0.0) || params->tile < 0 || params->tile > 3) return GRMHD_ERR_ARG;
+  if (!(params->rho_atm > 0.0) || !(params->p_atm > 0.0) || params->tile < 0 || params->tile > 4) return GRMHD_ERR_ARG;
   const int min_ng = params->recon == GRMHD_WENO5 ? 3 : 2;
   if (grid->ng < min_ng || grid->ng > 16) return GRMHD_ERR_ARG;
   for (int d = 0; d < 3; ++d)

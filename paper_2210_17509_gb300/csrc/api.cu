@@ -70,7 +70,7 @@ int check_params(const grmhd_params* p) {
   if (!(p->nr_tol > 0.0 && p->nr_tol < 1.0)) return GRMHD_ERR_ARG;
   if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
-  if (p->tile < 0 || p->tile > 3) return GRMHD_ERR_ARG;
+  if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
   if ((p->flags & ~GRMHD_REUSE_GEOMETRY) != 0) return GRMHD_ERR_ARG;
   return GRMHD_OK;
 }

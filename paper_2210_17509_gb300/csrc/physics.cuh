@@ -17,6 +17,8 @@ namespace grmhd {
 
 __device__ __forceinline__ double xsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double xrsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float xrsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double xabs(double x) { return fabs(x); }
 __device__ __forceinline__ float xabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double xmin(double a, double b) { return fmin(a, b); }
@@ -156,8 +158,8 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
   const T omv2 = T(1) - v2;
-  const T iW = xsqrt(omv2);         // 1 / W
-  const T W = T(1) / iW;
+  const T W = xrsqrt(omv2);         // Lorentz factor
+  const T iW = omv2 * W;            // 1 / W
   const T ab0 = W * Bv;             // alpha b^0
   const T b2 = B2 * omv2 + Bv * Bv; // (B^2 + (alpha b^0)^2) / W^2
   T bl[3];

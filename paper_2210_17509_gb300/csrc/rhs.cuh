@@ -158,8 +158,8 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
   const T omv2 = T(1) - v2;
-  const T iW = xsqrt(omv2);
-  const T W = T(1) / iW;
+  const T W = xrsqrt(omv2);
+  const T iW = omv2 * W;
   const T ab0 = W * Bv;
   const T b2 = B2 * omv2 + Bv * Bv;
   const T hs = rho + (T)p.gfac * P + b2;
@@ -296,7 +296,8 @@ template <> struct TileShape<0> { static constexpr int X = 8, Y = 8, Z = 4; };
 template <> struct TileShape<1> { static constexpr int X = 16, Y = 4, Z = 4; };
 template <> struct TileShape<2> { static constexpr int X = 32, Y = 4, Z = 2; };
 template <> struct TileShape<3> { static constexpr int X = 4, Y = 8, Z = 8; };
-constexpr int kNumTileShapes = 4;
+template <> struct TileShape<4> { static constexpr int X = 8, Y = 8, Z = 8; };  // 2 cells per thread
+constexpr int kNumTileShapes = 5;
 constexpr int kTileThreads = 256;
 
 template <int TX, int TY, int TZ>
@@ -306,17 +307,20 @@ struct TileFaces {
   static constexpr int NFZ = TX * TY * (TZ + 1);
   static constexpr int NF = NFX + NFY + NFZ;
 };
-// Largest face count over the shapes: sizes the shared face buffer.
+// Largest face count over the 256-cell shapes 0..3 (the batched kernel's
+// shared face buffer); single-block launches size it per shape.
 constexpr int kMaxTileFaces = 968;
 
 // One tile of the RHS: all face fluxes of the tile (each once) into the
 // shared buffer sF [8][NF], then each thread differences its cell's faces,
 // adds the sources and applies the stage epilogue.  Called by all threads of
-// the CTA (contains __syncthreads); NT = TX*TY*TZ threads.
+// the CTA (contains __syncthreads); kTileThreads threads, each handling one
+// or more cells of the TX*TY*TZ tile.
 template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
 __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
                                          int x0, int y0, int z0, T* sF) {
-  constexpr int NT = TX * TY * TZ;
+  constexpr int NT = kTileThreads;
+  constexpr int NC = TX * TY * TZ;
   constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
   constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
   constexpr int NF = TileFaces<TX, TY, TZ>::NF;
@@ -358,9 +362,11 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   }
   __syncthreads();
 
-  const int ci = threadIdx.x % TX, cj = (threadIdx.x / TX) % TY, ck = threadIdx.x / (TX * TY);
+#pragma unroll 1
+  for (int cl = threadIdx.x; cl < NC; cl += NT) {
+  const int ci = cl % TX, cj = (cl / TX) % TY, ck = cl / (TX * TY);
   const int xi = x0 + ci, yi = y0 + cj, zi = z0 + ck;
-  if (threadIdx.x < NT && xi < g.n[0] && yi < g.n[1] && zi < g.n[2]) {
+  if (xi < g.n[0] && yi < g.n[1] && zi < g.n[2]) {
     const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
     const int fx = (ck * TY + cj) * (TX + 1) + ci;
     const int fy = NFX + (ck * (TY + 1) + cj) * TX + ci;
@@ -391,6 +397,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
     }
   }
+  }
 }
 
 template <class T, int RECON, bool CURVED, int SHAPE, class S>
@@ -407,13 +414,17 @@ cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, co
                              cudaStream_t s) {
   void (*k)(DevGrid, DevParams, S, StageEpilogue) = nullptr;
   int tx = 8, ty = 8, tz = 4;
+  int nf = TileFaces<8, 8, 4>::NF;
   switch (shape) {
+    case 4: k = rhs_kernel<T, RECON, CURVED, 4, S>; tx = TileShape<4>::X; ty = TileShape<4>::Y; tz = TileShape<4>::Z;
+            nf = TileFaces<8, 8, 8>::NF; break;
     case 1: k = rhs_kernel<T, RECON, CURVED, 1, S>; tx = TileShape<1>::X; ty = TileShape<1>::Y; tz = TileShape<1>::Z; break;
     case 2: k = rhs_kernel<T, RECON, CURVED, 2, S>; tx = TileShape<2>::X; ty = TileShape<2>::Y; tz = TileShape<2>::Z; break;
     case 3: k = rhs_kernel<T, RECON, CURVED, 3, S>; tx = TileShape<3>::X; ty = TileShape<3>::Y; tz = TileShape<3>::Z; break;
     default: k = rhs_kernel<T, RECON, CURVED, 0, S>; break;
   }
-  const size_t smem = (size_t)8 * kMaxTileFaces * sizeof(T);
+  if (shape >= 1 && shape <= 3) nf = kMaxTileFaces;
+  const size_t smem = (size_t)8 * nf * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((g.n[0] + tx - 1) / tx, (g.n[1] + ty - 1) / ty, (g.n[2] + tz - 1) / tz);

@@ -350,3 +350,18 @@ def test_mixed_geometry_reuse_flag(G):
                 p = dataclasses.replace(gp, flags=G.REUSE_GEOMETRY)
         res.append(host(tc))
     np.testing.assert_array_equal(res[0], res[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rhs_independent_of_tile_shape(G, precision):
+    """Every tile shape cuts the same face fluxes: bit-identical RHS."""
+    import dataclasses
+    blk, prim, met = block_curved((19, 13, 10), seed=6, rho_range=(0.1, 1.0))
+    g, og = grids(G, blk)
+    gp, _ = params(G, 1, bc=1, precision=precision)
+    prim = O.fill_ghosts(og, 1, prim)
+    tp, tm = cuda(prim), cuda(met)
+    ref = host(G.rhs(g, gp, tp, tm))
+    for shape in (1, 2, 3, 4):
+        r = host(G.rhs(g, dataclasses.replace(gp, tile=shape), tp, tm))
+        np.testing.assert_array_equal(interior(r, 3), interior(ref, 3))
