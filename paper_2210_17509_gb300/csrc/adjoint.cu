@@ -324,6 +324,40 @@ __device__ __forceinline__ double weno5_adj(const double u[5], double eps, doubl
   return v;
 }
 
+// WENO5 value v(u0..u4) and its five partial derivatives dv/du_k in one
+// pass (same formulas as weno5_adj with vbar = 1; the three 1/e_k share one
+// division through the products e_i e_j already formed for the weights).
+__device__ __forceinline__ double weno5_value_grad(const double u[5], double eps, double gr[5]) {
+  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
+  const double q0 = (2.0 * u[0] - 7.0 * u[1] + 11.0 * u[2]) * c6;
+  const double q1 = (-u[1] + 5.0 * u[2] + 2.0 * u[3]) * c6;
+  const double q2 = (2.0 * u[2] + 5.0 * u[3] - u[4]) * c6;
+  const double t0 = u[0] - 2.0 * u[1] + u[2], s0 = u[0] - 4.0 * u[1] + 3.0 * u[2];
+  const double t1 = u[1] - 2.0 * u[2] + u[3], s1 = u[1] - u[3];
+  const double t2 = u[2] - 2.0 * u[3] + u[4], s2 = 3.0 * u[2] - 4.0 * u[3] + u[4];
+  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
+  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
+  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
+  const double iw = 1.0 / (w0 + w1 + w2);
+  const double o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
+  const double v = o0 * q0 + o1 * q1 + o2 * q2;
+  const double ie = 1.0 / (e0 * p12);  // 1 / (e0 e1 e2)
+  const double eb0 = -2.0 * o0 * (q0 - v) * (p12 * ie);
+  const double eb1 = -2.0 * o1 * (q1 - v) * (p02 * ie);
+  const double eb2 = -2.0 * o2 * (q2 - v) * (p01 * ie);
+  const double tb0 = 2.0 * c1312 * t0 * eb0, sb0 = 0.5 * s0 * eb0;
+  const double tb1 = 2.0 * c1312 * t1 * eb1, sb1 = 0.5 * s1 * eb1;
+  const double tb2 = 2.0 * c1312 * t2 * eb2, sb2 = 0.5 * s2 * eb2;
+  gr[0] = 2.0 * c6 * o0 + tb0 + sb0;
+  gr[1] = -7.0 * c6 * o0 - c6 * o1 - 2.0 * tb0 - 4.0 * sb0 + tb1 + sb1;
+  gr[2] = 11.0 * c6 * o0 + 5.0 * c6 * o1 + 2.0 * c6 * o2 + tb0 + 3.0 * sb0 - 2.0 * tb1 + tb2 + 3.0 * sb2;
+  gr[3] = 2.0 * c6 * o1 + 5.0 * c6 * o2 + tb1 - sb1 - 2.0 * tb2 - 4.0 * sb2;
+  gr[4] = -c6 * o2 + tb2 + sb2;
+  return v;
+}
+
 // minmod face value um1 + minmod(um1 - um2, u0 - um1) / 2 with its adjoint.
 __device__ __forceinline__ double minmod_left_adj(double um2, double um1, double u0, double vbar, double ub[3]) {
   const double a = um1 - um2, b = u0 - um1;
@@ -541,12 +575,32 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
 template <int RECON, bool CURVED, int DIR>
 __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
                                              const double* __restrict__ metric, long long c, const double Fb[8],
-                                             double* __restrict__ prim_bar, double& gammab) {
+                                             double* __restrict__ prim_bar, double& gammab, double* gsm) {
   const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
-  // primal reconstruction (same arithmetic as the forward kernel)
+  // primal reconstruction; for WENO5 the five partial derivatives of every
+  // face value are kept in shared memory (gsm[j * blockDim.x + tid],
+  // j = (2 q + side) * 5 + k) for the reverse sweep below
   double pL[8], pR[8];
   const double eps = p.weno_eps;
-  reconstruct_face<double, RECON>(prim, g.ncell, c, stride, eps, pL, pR);
+  if (RECON == GRMHD_WENO5) {
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      double u[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) u[k] = __ldg(prim + q * g.ncell + c + (k - 3) * stride);
+      double gr[5];
+      const double uL[5] = {u[0], u[1], u[2], u[3], u[4]};
+      pL[q] = weno5_value_grad(uL, eps, gr);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gsm[((2 * q) * 5 + k) * blockDim.x + threadIdx.x] = gr[k];
+      const double uR[5] = {u[5], u[4], u[3], u[2], u[1]};
+      pR[q] = weno5_value_grad(uR, eps, gr);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gsm[((2 * q + 1) * 5 + k) * blockDim.x + threadIdx.x] = gr[k];
+    }
+  } else {
+    reconstruct_face<double, RECON>(prim, g.ncell, c, stride, eps, pL, pR);
+  }
   Geom<double> m;
   if (CURVED) face_geom<double, DIR>(metric, g.ncell, c, stride, m);
   const bool fbL = !physical_state<double, CURVED>(pL, m);
@@ -592,28 +646,22 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
   // reconstruction reverse (stencil values reloaded), scatter to the stencil
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {
-    double u[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) u[k] = __ldg(prim + q * g.ncell + c + (k - 3) * stride);
     double ub[6] = {0, 0, 0, 0, 0, 0};
     if (fbL) ub[2] += pLb[q];
     if (fbR) ub[3] += pRb[q];
     if (RECON == GRMHD_WENO5) {
       if (!fbL) {
-        double t[5] = {0, 0, 0, 0, 0};
-        const double uu[5] = {u[0], u[1], u[2], u[3], u[4]};
-        weno5_adj(uu, eps, pLb[q], t);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) ub[k] += t[k];
+        for (int k = 0; k < 5; ++k) ub[k] += gsm[((2 * q) * 5 + k) * blockDim.x + threadIdx.x] * pLb[q];
       }
       if (!fbR) {
-        double t[5] = {0, 0, 0, 0, 0};
-        const double uu[5] = {u[5], u[4], u[3], u[2], u[1]};
-        weno5_adj(uu, eps, pRb[q], t);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) ub[5 - k] += t[k];
+        for (int k = 0; k < 5; ++k) ub[5 - k] += gsm[((2 * q + 1) * 5 + k) * blockDim.x + threadIdx.x] * pRb[q];
       }
     } else {
+      double u[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) u[k] = __ldg(prim + q * g.ncell + c + (k - 3) * stride);
       if (!fbL) {
         double t[3] = {0, 0, 0};
         minmod_left_adj(u[1], u[2], u[3], pLb[q], t);
@@ -644,6 +692,8 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
   const long long nfy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
   const long long nfz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
   const long long total = nfx + nfy + nfz;
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  double* gsm = reinterpret_cast<double*>(adj_smem);  // WENO5 partials, 80 per thread
   double gb = 0.0;
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
        f += (long long)gridDim.x * blockDim.x) {
@@ -679,9 +729,9 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
       const double lo = has_lo ? rhs_bar[q * g.ncell + c - stride] : 0.0;
       Fb[q] = w * (hi - lo);
     }
-    if (dir == 0) face_adjoint<RECON, CURVED, 0>(g, p, prim, metric, c, Fb, prim_bar, gb);
-    else if (dir == 1) face_adjoint<RECON, CURVED, 1>(g, p, prim, metric, c, Fb, prim_bar, gb);
-    else face_adjoint<RECON, CURVED, 2>(g, p, prim, metric, c, Fb, prim_bar, gb);
+    if (dir == 0) face_adjoint<RECON, CURVED, 0>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
+    else if (dir == 1) face_adjoint<RECON, CURVED, 1>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
+    else face_adjoint<RECON, CURVED, 2>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
   }
   block_add_gamma(gb, gamma_bar);
 }
@@ -881,14 +931,14 @@ cudaError_t launch_rhs_adjoint(const DevGrid& g, const DevParams& p, const doubl
                           (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
   const int nb = blocks_for(faces, 128);
   const bool weno = p.recon == GRMHD_WENO5;
-  if (metric) {
-    if (weno) rhs_face_adjoint_kernel<GRMHD_WENO5, true><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
-    else rhs_face_adjoint_kernel<GRMHD_MINMOD, true><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
-  } else {
-    if (weno) rhs_face_adjoint_kernel<GRMHD_WENO5, false><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
-    else rhs_face_adjoint_kernel<GRMHD_MINMOD, false><<<nb, 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
-  }
-  cudaError_t e = cudaGetLastError();
+  const size_t smem = weno ? (size_t)80 * 128 * sizeof(double) : 0;
+  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, double, double*, double*);
+  if (metric) k = weno ? rhs_face_adjoint_kernel<GRMHD_WENO5, true> : rhs_face_adjoint_kernel<GRMHD_MINMOD, true>;
+  else k = weno ? rhs_face_adjoint_kernel<GRMHD_WENO5, false> : rhs_face_adjoint_kernel<GRMHD_MINMOD, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<nb, 128, smem, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+  e = cudaGetLastError();
   if (e != cudaSuccess || !metric) return e;
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   source_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, s>>>(g, p, prim, metric, kij, rhs_bar, scale, prim_bar,
