@@ -408,20 +408,16 @@ def main():
         return
 
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    from paper_2210_17509_gb300.replicas import Replicas
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    R = Replicas("nccl", torch.device("cuda", local))
+    world, rank = R.world, R.rank
 
     from paper_2210_17509_gb300 import grmhd as G
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        R.barrier()
 
     blk, prim_h, met_h = I.smooth_schwarzschild(args.n, seed=1 + rank)
     g = G.Grid(blk.n, blk.ng, blk.dx)
@@ -454,11 +450,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = R.max_over_ranks(e0.elapsed_time(e1))
         return ms, int(nfail.item())
 
     uuid = None
@@ -486,18 +478,14 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms64 = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms64 = float(t.item())
+    ms64 = R.max_over_ranks(e0.elapsed_time(e1))
     nfail64 = int(nfail.item())
     ncells = blk.ncells
-    value64 = world * ncells * args.steps / (ms64 * 1e-3)
+    value64 = R.job_rate(ncells * args.steps, ms64)
 
     # mixed precision path
     msmx, nfailmx = timed(G.MIXED, args.steps, args.warmup)
-    value_mx = world * ncells * args.steps / (msmx * 1e-3)
+    value_mx = R.job_rate(ncells * args.steps, msmx)
 
     # dominant kernel: the fused FP64 RHS, timed live with events on its stream
     p, prim_k, cons_k, _, _ = setup(G.FP64)
@@ -547,14 +535,10 @@ def main():
         q1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = q0.elapsed_time(q1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = R.max_over_ranks(q0.elapsed_time(q1))
         h2d = cons_h.numel() * 8 + prim_h2.numel() * 8 + met_hp.numel() * 8
         d2h = out_c.numel() * 8 + out_p.numel() * 8
-        e2e = {"value": world * ncells * steps_e / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": R.job_rate(ncells * steps_e, ems), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "dtype": "f64"}
 
     batched = None

@@ -24,7 +24,10 @@ __global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* h
     const long long t = (it - b.c2p_begin) * kBatchItem + threadIdx.x;
     if (t < nint) {
       const long long c = interior_cell(b.g, t);
-      myfail += (con2prim_at<false>(b.g, p, b.cons, b.metric, b.prim, c) >= 2);
+      // mixed precision: FP32 Newton predictor, then the FP64 Newton
+      const int st = p.precision == GRMHD_MIXED ? con2prim_at<true, false>(b.g, p, b.cons, b.metric, b.prim, c)
+                                                : con2prim_at<false>(b.g, p, b.cons, b.metric, b.prim, c);
+      myfail += (st >= 2);
     }
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);

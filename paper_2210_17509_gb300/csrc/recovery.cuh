@@ -160,7 +160,9 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 // an FP32 Newton predictor runs before the FP64 Newton, and the result is
 // also stored in prim32.  mcache (nullable) holds, per point, 1/sqrt(gamma)
 // and gamma^ij in FP64 (7 components), saving the per-call inverse.
-template <bool PREDICT>
+// F32IO (with PREDICT) takes the guess from and writes the result to prim32;
+// without it the guess is read from the FP64 primitives.
+template <bool PREDICT, bool F32IO = PREDICT>
 __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p, const double* __restrict__ cons,
                                            const double* __restrict__ metric, double* __restrict__ prim,
                                            long long c, float* __restrict__ prim32 = nullptr,
@@ -197,7 +199,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   // initial guess from the incoming primitives
   double* pc = prim + c;
   double W, z;
-  if (PREDICT) {
+  if (F32IO) {
     const float* pf = prim32 + c;
     const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
     const float gf[6] = {(float)m.g[0], (float)m.g[1], (float)m.g[2], (float)m.g[3], (float)m.g[4], (float)m.g[5]};
@@ -258,7 +260,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   out[7] = B[2];
 #pragma unroll
   for (int q = 0; q < 8; ++q) pc[q * g.ncell] = out[q];
-  if (PREDICT) {
+  if (F32IO) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = (float)out[q];
   }

@@ -133,3 +133,22 @@ def test_autotuner_choices_are_valid(G):
         sid = autotune.choose(n, costs)
         best = min(autotune.n_tiles(s, n) * costs[s] for s in costs)
         assert autotune.n_tiles(sid, n) * costs[sid] == best
+
+
+def test_batch_mixed_against_fp64_oracle(G):
+    """Mixed-precision batch (FP32-predicted recovery, FP32 fluxes): RHS of
+    every box within 1e-4 of the FP64 oracle, recovery exact to round-off."""
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=G.MIXED)
+    boxes, host = make_boxes(G, p, 6, seed=11)
+    batch = G.Batch(boxes, p)
+    batch.rhs(p)
+    torch.cuda.synchronize()
+    op = O.make_params(recon=O.REC_WENO5, bc=O.BC_PERIODIC, rho_atm=p.rho_atm, p_atm=p.p_atm)
+    for b, (blk, prim, met) in zip(boxes, host):
+        og = O.Grid(blk.n, 3, blk.dx)
+        pf = O.fill_ghosts(og, 0, prim)
+        ro = O.rhs(og, op, pf, met)
+        err = normwise(interior(b.rhs.cpu().numpy(), 3), interior(ro, 3))
+        assert np.all(err < 1e-4), err
+        perr = normwise(interior(b.prim.cpu().numpy(), 3), interior(pf, 3))
+        assert np.all(perr < 1e-12), perr
