@@ -88,11 +88,11 @@ typedef struct {
   int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY */
 } grmhd_params;
 
-/* flags: the metric and the grid are unchanged since the previous
- * grmhd_rk_step with this same workspace, so the geometry cache of the
- * mixed path (built from the metric, see grmhd_rk_workspace_bytes_mixed)
- * is reused instead of rebuilt.  A static spacetime sets it after its first
- * step.  Ignored by every other call. */
+/* flags: the metric, the grid and the precision are unchanged since the
+ * previous grmhd_rk_step with this same workspace, so the geometry caches
+ * (built from the metric, see grmhd_rk_workspace_bytes_cached) are reused
+ * instead of rebuilt.  A static spacetime sets it after its first step.
+ * Ignored by every other call. */
 #define GRMHD_REUSE_GEOMETRY 1
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
@@ -151,16 +151,29 @@ int grmhd_fill_ghosts(const grmhd_grid* grid, int32_t bc, int32_t nvar, double* 
 int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
               const double* metric, const double* kij, double* rhs, void* stream);
 
+/* grmhd_rhs computed from the geometry caches of grmhd_rk_workspace_bytes_cached
+ * (and, for GRMHD_MIXED, an FP32 copy of prim) held in ws: the same RHS,
+ * with the per-face and per-cell metric algebra done once per static metric.
+ * ws >= grmhd_rhs_workspace_bytes(grid), 256-byte aligned; the caches are
+ * rebuilt unless params->flags has GRMHD_REUSE_GEOMETRY (same grid, metric and
+ * precision as the previous call with this ws). */
+size_t grmhd_rhs_workspace_bytes(const grmhd_grid* grid);
+int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
+                     const double* metric, const double* kij, double* rhs, void* ws, size_t ws_bytes,
+                     void* stream);
+
 /* Bytes of device workspace grmhd_rk_step needs for `scheme`. */
 size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
 
-/* Bytes of workspace with which grmhd_rk_step runs the mixed-precision path
- * from caches: an FP32 copy of the primitives and a geometry cache of the
- * metric (sqrt(gamma), inverse metric and metric derivatives computed in FP64
- * once per step, stored as FP32).  With less (but at least
- * grmhd_rk_workspace_bytes) the mixed RHS reads the FP64 inputs instead;
- * FP64 steps never use the extra space. */
-size_t grmhd_rk_workspace_bytes_mixed(const grmhd_grid* grid, int32_t scheme);
+/* Bytes of workspace with which grmhd_rk_step runs from caches: a geometry
+ * cache of the metric (face and cell sqrt(gamma), inverse metric and 4th-order
+ * metric derivatives, computed in FP64 once per step -- or once per static
+ * spacetime with GRMHD_REUSE_GEOMETRY -- stored as FP64 for the FP64 path and
+ * as FP32 for the mixed path), an FP64 inverse-metric cache for the recovery,
+ * and for the mixed path an FP32 copy of the primitives.  With less (but at
+ * least grmhd_rk_workspace_bytes) the kernels read the FP64 inputs directly;
+ * results agree to round-off. */
+size_t grmhd_rk_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme);
 
 /* One method-of-lines step of size dt (Sec. 2.3; integrators RK2/RK4 as in
  * Secs. 4-5, and SSP RK3).  Every stage evaluates the RHS from the current

@@ -80,11 +80,11 @@ def tile_costs(params: G.Params, curved: bool = False, refresh: bool = False) ->
 
 
 def choose(n, costs: dict) -> int:
-    """Best tile shape for a box of interior extent n = (nx, ny, nz)."""
-    return min(costs, key=lambda sid: (n_tiles(sid, n) * costs[sid], sid))
+    """Best tile shape (0..3) for a box of interior extent n = (nx, ny, nz)."""
+    return min((sid for sid in costs if sid in SHAPES), key=lambda sid: (n_tiles(sid, n) * costs[sid], sid))
 
 
 def best_block_shape(params: G.Params, n, curved: bool = False) -> int:
     """Tile shape for one large block of extent n (all five shapes timed)."""
     costs = measure_tile_costs(params, curved, shapes=BLOCK_SHAPES)
-    return choose(n, costs)
+    return min(costs, key=lambda sid: (n_tiles(sid, n) * costs[sid], sid))

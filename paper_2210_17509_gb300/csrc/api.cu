@@ -165,6 +165,44 @@ int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* 
                                 (cudaStream_t)stream));
 }
 
+size_t grmhd_rhs_workspace_bytes(const grmhd_grid* grid) {
+  if (check_grid(grid, 0)) return 0;
+  const DevGrid g = make_grid(*grid);
+  return round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) + round256((size_t)8 * g.ncell * sizeof(float)) +
+         round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
+}
+
+int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+                     const double* kij, double* rhs, void* ws, size_t ws_bytes, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
+  if (!prim || !rhs || !ws || !aligned8(prim) || !aligned8(rhs)) return GRMHD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  if ((metric && !aligned8(metric)) || (kij && !aligned8(kij)) || (kij && !metric)) return GRMHD_ERR_ARG;
+  if (ws_bytes < grmhd_rhs_workspace_bytes(grid)) return GRMHD_ERR_SIZE;
+  const DevGrid g = make_grid(*grid);
+  const DevParams p = make_params(*params);
+  cudaStream_t s = (cudaStream_t)stream;
+  StageEpilogue ep = no_epilogue();
+  ep.rhs = rhs;
+  char* base = static_cast<char*>(ws);
+  void* geom = base;
+  float* prim32 = reinterpret_cast<float*>(base + round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)));
+  double* mcache = reinterpret_cast<double*>(reinterpret_cast<char*>(prim32) +
+                                             round256((size_t)8 * g.ncell * sizeof(float)));
+  const bool mixed = p.precision == GRMHD_MIXED;
+  const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
+  if (metric && !reuse && launch_geom_cache(g, metric, geom, !mixed, mcache, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (mixed) {
+    if (launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    return cuda_status(launch_rhs_mixed_cached(g, p, prim32, static_cast<const float*>(geom), kij, metric != nullptr,
+                                               ep, s));
+  }
+  if (!metric) return cuda_status(launch_rhs(g, p, prim, metric, kij, ep, s));
+  return cuda_status(launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s));
+}
+
 size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
   if (check_grid(grid, 0)) return 0;
   if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3 && scheme != GRMHD_RK4) return 0;
@@ -173,12 +211,12 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
   return scheme == GRMHD_RK4 ? 2 * field : field;
 }
 
-size_t grmhd_rk_workspace_bytes_mixed(const grmhd_grid* grid, int32_t scheme) {
+size_t grmhd_rk_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme) {
   const size_t base = grmhd_rk_workspace_bytes(grid, scheme);
   if (base == 0) return 0;
   const DevGrid g = make_grid(*grid);
-  return base + round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kGeomCacheComps * g.ncell * sizeof(float)) +
-         round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
+  return base + round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) +
+         round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
 }
 
 }  // extern "C"
@@ -213,20 +251,27 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
   // Mixed precision with room for the caches: FP32 primitive copy + geometry
   // cache (rebuilt here, once per step) feed the RHS; otherwise the RHS reads
   // the FP64 inputs directly.
-  const bool fast_mixed = p.precision == GRMHD_MIXED && ws_bytes >= grmhd_rk_workspace_bytes_mixed(grid, scheme);
+  // Cached paths (workspace >= grmhd_rk_workspace_bytes_cached):
+  //  mixed: FP32 primitive copy + FP32 geometry cache + FP64 inverse-metric cache;
+  //  FP64 on a metric: FP64 geometry cache + FP64 inverse-metric cache.
+  // The caches are rebuilt once per call unless GRMHD_REUSE_GEOMETRY is set.
+  const bool cached = ws_bytes >= grmhd_rk_workspace_bytes_cached(grid, scheme);
+  const bool fast_mixed = p.precision == GRMHD_MIXED && cached;
+  const bool fast_fp64 = p.precision == GRMHD_FP64 && cached && metric != nullptr;
   float* prim32 = nullptr;
-  float* geom = nullptr;
+  void* geom = nullptr;
   double* mcache = nullptr;
-  if (fast_mixed) {
+  if (fast_mixed || fast_fp64) {
     char* after = static_cast<char*>(ws) + grmhd_rk_workspace_bytes(grid, scheme);
+    geom = after;
+    after += round256((size_t)kGeomCacheComps * g.ncell * sizeof(double));
     prim32 = reinterpret_cast<float*>(after);
     after += round256((size_t)8 * g.ncell * sizeof(float));
-    geom = reinterpret_cast<float*>(after);
-    after += round256((size_t)kGeomCacheComps * g.ncell * sizeof(float));
     mcache = reinterpret_cast<double*>(after);
     const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
-    if (metric && !reuse && launch_geom_cache(g, metric, geom, mcache, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-    if (launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (metric && !reuse && launch_geom_cache(g, metric, geom, fast_fp64, mcache, s) != cudaSuccess)
+      return GRMHD_ERR_CUDA;
+    if (fast_mixed && launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
   }
 
   // Stage coefficients: u <- c0 u0 + c1 u + cr L (+ ca acc); acc <- wa acc + wr L.
@@ -261,8 +306,14 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     ep.ca = st[k].ca;
     ep.wa = st[k].wa;
     ep.wr = st[k].wr;
-    if (fast_mixed) {
-      if (launch_rhs_mixed_cached(g, p, prim32, geom, kij, metric != nullptr, ep, s) != cudaSuccess)
+    if (fast_fp64) {
+      if (launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s) != cudaSuccess)
+        return GRMHD_ERR_CUDA;
+      if (launch_con2prim_cached(g, p, cons, metric, mcache, prim, nfail, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    } else if (fast_mixed) {
+      if (launch_rhs_mixed_cached(g, p, prim32, static_cast<const float*>(geom), kij, metric != nullptr, ep, s) !=
+          cudaSuccess)
         return GRMHD_ERR_CUDA;
       if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, metric ? mcache : nullptr, nfail, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;

@@ -69,7 +69,12 @@ cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const do
                                   double* prim, float* prim32, const double* mcache, int32_t* nfail, cudaStream_t s);
 cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s);
-cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, double* mcache, cudaStream_t s);
+cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, void* geom, bool fp64, double* mcache,
+                              cudaStream_t s);
+cudaError_t launch_con2prim_cached(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
+                                   const double* mcache, double* prim, int32_t* nfail, cudaStream_t s);
+cudaError_t launch_rhs_fp64_cached(const DevGrid& g, const DevParams& p, const double* prim, const double* geom64,
+                                   const double* kij, const StageEpilogue& ep, cudaStream_t s);
 cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const float* prim32, const float* geom,
                                     const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s);
 constexpr int kGeomCacheComps = 53;

@@ -77,6 +77,45 @@ __device__ __forceinline__ float weno5<float>(float um2, float um1, float u0, fl
   return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
+// Both WENO5 states of the face between cells c-1 and c from the six values
+// u[c-3 .. c+2]: the left state from cell c-1, the right state (mirrored
+// stencil) from cell c.  In FP64 the two normalisations share one division:
+// 1/a and 1/b come from 1/(a b).
+template <class T>
+__device__ __forceinline__ void weno5_pair(T um3, T um2, T um1, T u0, T up1, T up2, T eps, T& vL, T& vR) {
+  vL = weno5<T>(um3, um2, um1, u0, up1, eps);
+  vR = weno5<T>(up2, up1, u0, um1, um2, eps);
+}
+
+__device__ __forceinline__ void weno5_parts(double um2, double um1, double u0, double up1, double up2, double eps,
+                                            double& num, double& den) {
+  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
+  const double q0 = (2.0 * um2 - 7.0 * um1 + 11.0 * u0) * c6;
+  const double q1 = (-um1 + 5.0 * u0 + 2.0 * up1) * c6;
+  const double q2 = (2.0 * u0 + 5.0 * up1 - up2) * c6;
+  const double t0 = um2 - 2.0 * um1 + u0, s0 = um2 - 4.0 * um1 + 3.0 * u0;
+  const double t1 = um1 - 2.0 * u0 + up1, s1 = um1 - up1;
+  const double t2 = u0 - 2.0 * up1 + up2, s2 = 3.0 * u0 - 4.0 * up1 + up2;
+  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
+  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
+  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
+  num = w0 * q0 + w1 * q1 + w2 * q2;
+  den = w0 + w1 + w2;
+}
+
+template <>
+__device__ __forceinline__ void weno5_pair<double>(double um3, double um2, double um1, double u0, double up1,
+                                                   double up2, double eps, double& vL, double& vR) {
+  double nL, dL, nR, dR;
+  weno5_parts(um3, um2, um1, u0, up1, eps, nL, dL);
+  weno5_parts(up2, up1, u0, um1, um2, eps, nR, dR);
+  const double r = 1.0 / (dL * dR);
+  vL = nL * (dR * r);
+  vR = nR * (dL * r);
+}
+
 // ---------------------------------------------------------------- geometry
 // Metric at a face (or a cell) converted to the compute type.
 template <class T>

@@ -86,7 +86,8 @@ __global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* 
 // point): every FP64 quantity the mixed RHS needs, computed once in FP64.
 // mcache (FP64, 7 components per point): 1/sqrt(gamma) and gamma^ij for the
 // primitive recovery.
-__global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, float* __restrict__ geom,
+template <class GT>
+__global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, GT* __restrict__ geom,
                                   double* __restrict__ mcache) {
   const long long n = g.ncell;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -98,12 +99,12 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
       a[q] = __ldg(metric + q * n + c);
-      geom[q * n + c] = (float)a[q];
+      geom[q * n + c] = (GT)a[q];
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long s = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
-      float sgf = 1.0f, gupf = 1.0f;
+      GT sgf = GT(1), gupf = GT(1);
       if (idx[d] >= 1) {
         double m[6];
 #pragma unroll
@@ -113,8 +114,8 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
         const double czz = m[0] * m[3] - m[1] * m[1];
         const double det = m[0] * cxx - m[1] * (m[1] * m[5] - m[4] * m[2]) + m[2] * (m[1] * m[4] - m[3] * m[2]);
         const double cdd = d == 0 ? cxx : (d == 1 ? cyy : czz);
-        sgf = (float)sqrt(det);
-        gupf = (float)(cdd / det);
+        sgf = (GT)sqrt(det);
+        gupf = (GT)(cdd / det);
       }
       geom[(10 + d) * n + c] = sgf;
       geom[(13 + d) * n + c] = gupf;
@@ -126,7 +127,7 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       const double det = gxx * cxx + gxy * cxy + gxz * cxz;
       const double idet = 1.0 / det;
       const double sgd = sqrt(det);
-      geom[16 * n + c] = (float)sgd;
+      geom[16 * n + c] = (GT)sgd;
       mcache[c] = 1.0 / sgd;
       mcache[1 * n + c] = cxx * idet;
       mcache[2 * n + c] = cxy * idet;
@@ -134,12 +135,12 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       mcache[4 * n + c] = cyy * idet;
       mcache[5 * n + c] = cyz * idet;
       mcache[6 * n + c] = czz * idet;
-      geom[17 * n + c] = (float)(cxx * idet);
-      geom[18 * n + c] = (float)(cxy * idet);
-      geom[19 * n + c] = (float)(cxz * idet);
-      geom[20 * n + c] = (float)(cyy * idet);
-      geom[21 * n + c] = (float)(cyz * idet);
-      geom[22 * n + c] = (float)(czz * idet);
+      geom[17 * n + c] = (GT)(cxx * idet);
+      geom[18 * n + c] = (GT)(cxy * idet);
+      geom[19 * n + c] = (GT)(cxz * idet);
+      geom[20 * n + c] = (GT)(cyy * idet);
+      geom[21 * n + c] = (GT)(cyz * idet);
+      geom[22 * n + c] = (GT)(czz * idet);
     }
     const bool inner = idx[0] >= 2 && idx[0] < g.N[0] - 2 && idx[1] >= 2 && idx[1] < g.N[1] - 2 && idx[2] >= 2 &&
                        idx[2] < g.N[2] - 2;
@@ -149,10 +150,10 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       const double w = g.idx[e] * (1.0 / 12.0);
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
-        float v = 0.0f;
+        GT v = GT(0);
         if (inner) {
           const double* mm = metric + q * n + c;
-          v = (float)((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
+          v = (GT)((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
         }
         geom[(23 + 10 * e + q) * n + c] = v;
       }
@@ -207,8 +208,32 @@ cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, float* geom, double* mcache, cudaStream_t s) {
-  geom_cache_kernel<<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, geom, mcache);
+cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, void* geom, bool fp64, double* mcache,
+                              cudaStream_t s) {
+  if (fp64)
+    geom_cache_kernel<double><<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, static_cast<double*>(geom), mcache);
+  else
+    geom_cache_kernel<float><<<grid_blocks(g.ncell, 128), 128, 0, s>>>(g, metric, static_cast<float*>(geom), mcache);
+  return cudaGetLastError();
+}
+
+__global__ void con2prim_cached_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
+                                       const double* __restrict__ metric, const double* __restrict__ mcache,
+                                       double* __restrict__ prim, int32_t* __restrict__ nfail) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  int myfail = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, t);
+    myfail += (con2prim_at<false>(g, p, cons, metric, prim, c, nullptr, mcache) >= 2);
+  }
+  if (nfail && myfail) atomicAdd(nfail, myfail);
+}
+
+cudaError_t launch_con2prim_cached(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
+                                   const double* mcache, double* prim, int32_t* nfail, cudaStream_t s) {
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  con2prim_cached_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, mcache, prim, nfail);
   return cudaGetLastError();
 }
 

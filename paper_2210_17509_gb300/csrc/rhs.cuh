@@ -25,11 +25,14 @@ struct SrcF64 {
   const double* __restrict__ metric;
   const double* __restrict__ kij;
 };
-struct SrcCache {
-  const float* __restrict__ prim;
-  const float* __restrict__ geom;
+template <class PT, class GT>
+struct SrcCacheT {
+  const PT* __restrict__ prim;
+  const GT* __restrict__ geom;
   const double* __restrict__ kij;
 };
+typedef SrcCacheT<float, float> SrcCache;      // mixed: FP32 primitives + FP32 geometry cache
+typedef SrcCacheT<double, double> SrcCache64;  // FP64: FP64 primitives + FP64 geometry cache
 
 // Geometry cache layout ([comp][ncell] floats, every point of the block):
 //   0..9    metric (alpha, beta^i, gamma_ij)
@@ -41,8 +44,8 @@ constexpr int kGeomComps = 53;
 
 template <class T>
 __device__ __forceinline__ T ld_prim(const SrcF64& s, long long i) { return (T)__ldg(s.prim + i); }
-template <class T>
-__device__ __forceinline__ T ld_prim(const SrcCache& s, long long i) { return (T)__ldg(s.prim + i); }
+template <class T, class PT, class GT>
+__device__ __forceinline__ T ld_prim(const SrcCacheT<PT, GT>& s, long long i) { return (T)__ldg(s.prim + i); }
 
 // Load the 8 primitives at the six-point stencil of the face between cell
 // c - stride and c, reconstruct both states.
@@ -56,8 +59,7 @@ __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, 
       const T um3 = ld_prim<T>(src, a - 3 * stride), um2 = ld_prim<T>(src, a - 2 * stride);
       const T um1 = ld_prim<T>(src, a - stride), u0 = ld_prim<T>(src, a);
       const T up1 = ld_prim<T>(src, a + stride), up2 = ld_prim<T>(src, a + 2 * stride);
-      pL[q] = weno5<T>(um3, um2, um1, u0, up1, eps);
-      pR[q] = weno5<T>(up2, up1, u0, um1, um2, eps);
+      weno5_pair<T>(um3, um2, um1, u0, up1, up2, eps, pL[q], pR[q]);
     } else {
       const T um2 = ld_prim<T>(src, a - 2 * stride), um1 = ld_prim<T>(src, a - stride);
       const T u0 = ld_prim<T>(src, a), up1 = ld_prim<T>(src, a + stride);
@@ -85,12 +87,12 @@ __device__ __forceinline__ void face_geometry(const SrcF64& s, long long ncell, 
   face_geom<T, DIR>(s.metric, ncell, c, stride, m);
 }
 
-// Face metric from the cache: FP32 mean of the two cells, cached sqrt(gamma)
-// and gamma^dd of the face.
-template <class T, int DIR>
-__device__ __forceinline__ void face_geometry(const SrcCache& s, long long ncell, long long c, long long stride,
-                                              Geom<T>& m) {
-  const float* gm = s.geom;
+// Face metric from the cache: mean of the two cells (in the compute type),
+// cached sqrt(gamma) and gamma^dd of the face.
+template <class T, int DIR, class PT, class GT>
+__device__ __forceinline__ void face_geometry(const SrcCacheT<PT, GT>& s, long long ncell, long long c,
+                                              long long stride, Geom<T>& m) {
+  const GT* gm = s.geom;
   T a[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) a[q] = T(0.5) * ((T)__ldg(gm + q * ncell + c - stride) + (T)__ldg(gm + q * ncell + c));
@@ -268,10 +270,10 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
 }
 
 // Metric quantities from the geometry cache.
-template <class T>
-__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcCache& src, long long c,
-                                             T out[8]) {
-  const float* gc = src.geom;
+template <class T, class PT, class GT>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcCacheT<PT, GT>& src,
+                                             long long c, T out[8]) {
+  const GT* gc = src.geom;
   const long long n = g.ncell;
   const T alpha = (T)__ldg(gc + c);
   const T beta[3] = {(T)__ldg(gc + n + c), (T)__ldg(gc + 2 * n + c), (T)__ldg(gc + 3 * n + c)};
@@ -287,7 +289,7 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   for (int e = 0; e < 3; ++e)
 #pragma unroll
     for (int q = 0; q < 10; ++q) dA[e][q] = (T)__ldg(gc + (23 + 10 * e + q) * n + c);
-  source_core<T, SrcCache>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+  source_core<T, SrcCacheT<PT, GT>>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
 }
 
 // Tile shapes the kernels are instantiated for (cells per axis, 256 cells each).

@@ -69,8 +69,8 @@ _lib.grmhd_fill_ghosts.argtypes = [_pg, _I32, _I32, _P, _P]
 _lib.grmhd_rhs.argtypes = [_pg, _pp, _P, _P, _P, _P, _P]
 _lib.grmhd_rk_workspace_bytes.argtypes = [_pg, _I32]
 _lib.grmhd_rk_workspace_bytes.restype = ctypes.c_size_t
-_lib.grmhd_rk_workspace_bytes_mixed.argtypes = [_pg, _I32]
-_lib.grmhd_rk_workspace_bytes_mixed.restype = ctypes.c_size_t
+_lib.grmhd_rk_workspace_bytes_cached.argtypes = [_pg, _I32]
+_lib.grmhd_rk_workspace_bytes_cached.restype = ctypes.c_size_t
 _lib.grmhd_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
 _lib.grmhd_rk_step_static.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P]
 _lib.grmhd_rk_step_static.restype = _I
@@ -81,7 +81,7 @@ for _name in ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rh
     getattr(_lib, _name).restype = _I
 
 C_SYMBOLS = ("grmhd_prim2con", "grmhd_con2prim", "grmhd_fill_ghosts", "grmhd_rhs", "grmhd_rk_workspace_bytes",
-             "grmhd_rk_workspace_bytes_mixed", "grmhd_rk_step", "grmhd_rk_step_static", "grmhd_error_string", "grmhd_version")
+             "grmhd_rk_workspace_bytes_cached", "grmhd_rk_step", "grmhd_rk_step_static", "grmhd_error_string", "grmhd_version")
 STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -203,18 +203,46 @@ def rhs(grid: Grid, params: Params, prim, metric=None, kij=None, out=None, strea
     return out
 
 
+_lib.grmhd_rhs_workspace_bytes.argtypes = [_pg]
+_lib.grmhd_rhs_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_rhs_cached.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
+_lib.grmhd_rhs_cached.restype = _I
+C_SYMBOLS = C_SYMBOLS + ("grmhd_rhs_workspace_bytes", "grmhd_rhs_cached")
+
+
+def rhs_workspace(grid: Grid, device=None):
+    nbytes = int(_lib.grmhd_rhs_workspace_bytes(ctypes.byref(grid.c())))
+    if nbytes == 0:
+        raise GrmhdError("invalid grid for the RHS workspace")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def rhs_cached(grid: Grid, params: Params, prim, metric=None, kij=None, out=None, ws=None, stream=None):
+    """grmhd_rhs_cached: the RHS from geometry caches kept in ws."""
+    if out is None:
+        out = torch.zeros_like(prim)
+    if ws is None:
+        ws = rhs_workspace(grid, prim.device)
+    rc = _lib.grmhd_rhs_cached(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                               _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                               _field(out, grid, 8, "rhs"), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                               _stream(stream))
+    _check(rc, "grmhd_rhs_cached")
+    return out
+
+
 def rk_workspace_bytes(grid: Grid, scheme: int) -> int:
     return int(_lib.grmhd_rk_workspace_bytes(ctypes.byref(grid.c()), scheme))
 
 
-def rk_workspace_bytes_mixed(grid: Grid, scheme: int) -> int:
-    return int(_lib.grmhd_rk_workspace_bytes_mixed(ctypes.byref(grid.c()), scheme))
+def rk_workspace_bytes_cached(grid: Grid, scheme: int) -> int:
+    return int(_lib.grmhd_rk_workspace_bytes_cached(ctypes.byref(grid.c()), scheme))
 
 
-def workspace(grid: Grid, scheme: int, device=None, mixed: bool = True):
+def workspace(grid: Grid, scheme: int, device=None, cached: bool = True):
     """Device workspace for rk_step; by default large enough for the cached
-    mixed-precision path (FP64 steps use only the first part)."""
-    nbytes = rk_workspace_bytes_mixed(grid, scheme) if mixed else rk_workspace_bytes(grid, scheme)
+    paths (geometry caches, FP32 primitive copy)."""
+    nbytes = rk_workspace_bytes_cached(grid, scheme) if cached else rk_workspace_bytes(grid, scheme)
     if nbytes == 0:
         raise GrmhdError("invalid grid or scheme for the workspace")
     # torch's caching allocator returns 512-byte aligned blocks

@@ -319,8 +319,8 @@ def test_rk3_mixed_without_cache_workspace(G):
     cons = O.prim2con(og, op.gamma, prim, met)
     dt = 0.25 * blk.dx[0]
     tc, tp, tm = cuda(cons), cuda(prim), cuda(met)
-    ws = G.workspace(g, G.RK3, mixed=False)
-    assert ws.numel() < G.rk_workspace_bytes_mixed(g, G.RK3)
+    ws = G.workspace(g, G.RK3, cached=False)
+    assert ws.numel() < G.rk_workspace_bytes_cached(g, G.RK3)
     for _ in range(3):
         G.rk_step(g, gp, G.RK3, dt, tc, tp, tm, None, ws)
     co, po = cons, prim
@@ -365,3 +365,46 @@ def test_rhs_independent_of_tile_shape(G, precision):
     for shape in (1, 2, 3, 4):
         r = host(G.rhs(g, dataclasses.replace(gp, tile=shape), tp, tm))
         np.testing.assert_array_equal(interior(r, 3), interior(ref, 3))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cached_and_direct_paths_agree(G, precision):
+    """The workspace size selects geometry caches (cached) or direct FP64 reads;
+    both are the same method and agree with each other and the oracle."""
+    blk, prim, met = block_curved(14, seed=3, rho_range=(0.1, 1.0))
+    g, og = grids(G, blk)
+    gp, op = params(G, 1, bc=1, precision=precision)
+    prim = O.fill_ghosts(og, 1, prim)
+    cons = O.prim2con(og, op.gamma, prim, met)
+    dt = 0.25 * blk.dx[0]
+    outs = []
+    for cached in (True, False):
+        tc, tp, tm = cuda(cons), cuda(prim), cuda(met)
+        ws = G.workspace(g, G.RK3, cached=cached)
+        for _ in range(2):
+            G.rk_step(g, gp, G.RK3, dt, tc, tp, tm, None, ws)
+        outs.append(host(tc))
+    co, po = cons, prim
+    for _ in range(2):
+        co, po, _ = O.rk_step(og, op, O.RK3, dt, co, po, met)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    for o in outs:
+        assert np.all(normwise(interior(o, 3), interior(co, 3)) < tol)
+    assert np.all(normwise(interior(outs[0], 3), interior(outs[1], 3)) < (1e-14 if precision == 0 else MIXED_TOL))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rhs_cached_matches_rhs(G, precision):
+    import dataclasses
+    blk, prim, met = block_curved((13, 11, 9), seed=4, rho_range=(0.1, 1.0))
+    g, og = grids(G, blk)
+    gp, op = params(G, 1, bc=1, precision=precision)
+    prim = O.fill_ghosts(og, 1, prim)
+    tp, tm = cuda(prim), cuda(met)
+    ws = G.rhs_workspace(g)
+    r1 = host(G.rhs_cached(g, gp, tp, tm, None, None, ws))
+    r2 = host(G.rhs_cached(g, dataclasses.replace(gp, flags=G.REUSE_GEOMETRY), tp, tm, None, None, ws))
+    np.testing.assert_array_equal(r1, r2)
+    ro = O.rhs(og, op, prim, met)
+    tol = FP64_TOL if precision == 0 else 1e-4
+    assert np.all(normwise(interior(r1, 3), interior(ro, 3)) < tol)
