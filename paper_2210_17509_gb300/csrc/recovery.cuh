@@ -67,7 +67,8 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
   bool ok = false;
   if (z > 0.0 && W >= 1.0 && isfinite(z) && isfinite(W)) {
     for (int it = 0; it < p.nr_maxit; ++it) {
-      const double iz = 1.0 / z, iW = 1.0 / W;
+      const double izW = 1.0 / (z * W);  // 1/z and 1/W from one division
+      const double iz = W * izW, iW = z * izW;
       const double iW2 = iW * iW, iW3 = iW2 * iW, iz2 = iz * iz, iz3 = iz2 * iz;
       const double zb = z + B2;
       const double f1 = zb * zb * (1.0 - iW2) - S2 - BS2 * (2.0 * z + B2) * iz2;
@@ -227,10 +228,13 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   }
   double out[8];
   if (st != 2) {
-    const double rho = D / W;
-    const double P = p.gm1g * (z / (W * W) - rho);
-    const double izb = 1.0 / (z + in.B2);
-    const double bsz = BS / z;
+    // 1/W, 1/z and 1/(z + B^2) from one division
+    const double zb = z + in.B2;
+    const double X = 1.0 / (W * z * zb);
+    const double iW = z * zb * X, iz = W * zb * X, izb = W * z * X;
+    const double rho = D * iW;
+    const double P = p.gm1g * (z * iW * iW - rho);
+    const double bsz = BS * iz;
     double vlo[3], vu[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) vlo[i] = (Sl[i] + bsz * Bl[i]) * izb;

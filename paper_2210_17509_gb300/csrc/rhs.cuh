@@ -52,6 +52,30 @@ __device__ __forceinline__ T ld_prim(const SrcCacheT<PT, GT>& s, long long i) { 
 template <class T, int RECON, class S>
 __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, long long c, long long stride, T eps,
                                                  T pL[8], T pR[8]) {
+  if (RECON == GRMHD_WENO5 && sizeof(T) == 8) {
+    // FP64: the four normalisations of two variables share one division
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      double n[4], d[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long a = (q + h) * ncell + c;
+        const double um3 = ld_prim<double>(src, a - 3 * stride), um2 = ld_prim<double>(src, a - 2 * stride);
+        const double um1 = ld_prim<double>(src, a - stride), u0 = ld_prim<double>(src, a);
+        const double up1 = ld_prim<double>(src, a + stride), up2 = ld_prim<double>(src, a + 2 * stride);
+        weno5_parts(um3, um2, um1, u0, up1, (double)eps, n[2 * h], d[2 * h]);
+        weno5_parts(up2, up1, u0, um1, um2, (double)eps, n[2 * h + 1], d[2 * h + 1]);
+      }
+      const double d01 = d[0] * d[1], d23 = d[2] * d[3];
+      const double X = 1.0 / (d01 * d23);
+      const double x01 = d23 * X, x23 = d01 * X;
+      pL[q] = (T)(n[0] * (d[1] * x01));
+      pR[q] = (T)(n[1] * (d[0] * x01));
+      pL[q + 1] = (T)(n[2] * (d[3] * x23));
+      pR[q + 1] = (T)(n[3] * (d[2] * x23));
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const long long a = q * ncell + c;
