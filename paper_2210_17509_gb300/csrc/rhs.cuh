@@ -426,8 +426,14 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   }
 }
 
+// Resident CTAs per SM the register budget is fitted to: 3 for the FP32
+// (mixed) kernels, which are latency bound, 1 for FP64 (pipe bound).
+template <class T>
+struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+
 template <class T, int RECON, bool CURVED, int SHAPE, class S>
-__global__ void __launch_bounds__(kTileThreads) rhs_kernel(DevGrid g, DevParams p, S src, StageEpilogue ep) {
+__global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(DevGrid g, DevParams p, S src,
+                                                                             StageEpilogue ep) {
   using TS = TileShape<SHAPE>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);
