@@ -149,6 +149,75 @@ __device__ __forceinline__ void face_geom(const double* __restrict__ metric, lon
   m.gup_dd = (T)(cdd / det);
 }
 
+// Face metric with the face normal given at run time (dir = 0, 1, 2).
+template <class T>
+__device__ __forceinline__ void face_geom_rt(const double* __restrict__ metric, long long ncell, long long c,
+                                             long long stride, int dir, Geom<T>& m) {
+  double a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = 0.5 * (__ldg(metric + q * ncell + c - stride) + __ldg(metric + q * ncell + c));
+  const double gxx = a[4], gxy = a[5], gxz = a[6], gyy = a[7], gyz = a[8], gzz = a[9];
+  const double cxx = gyy * gzz - gyz * gyz;
+  const double cyy = gxx * gzz - gxz * gxz;
+  const double czz = gxx * gyy - gxy * gxy;
+  const double det = gxx * cxx - gxy * (gxy * gzz - gyz * gxz) + gxz * (gxy * gyz - gyy * gxz);
+  const double cdd = (dir == 0) ? cxx : ((dir == 1) ? cyy : czz);
+  m.alpha = (T)a[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.beta[i] = (T)a[1 + i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m.g[i] = (T)a[4 + i];
+  m.sqrtg = (T)sqrt(det);
+  m.gup_dd = (T)(cdd / det);
+}
+
+template <class T>
+__device__ __forceinline__ T sel3(int k, T a, T b, T c) { return k == 0 ? a : (k == 1 ? b : c); }
+
+// Cyclic relabelling of the axes that makes the face normal dir the first
+// axis: new axis k is old axis (dir + k) mod 3.  Applied to a primitive
+// state and to the face metric, so that one face-state routine (normal = x)
+// serves all three directions; unrotate_flux maps the result back.
+template <class T>
+__device__ __forceinline__ void rotate_state(int dir, const T in[8], T out[8]) {
+  out[0] = in[0];
+  out[4] = in[4];
+  out[1] = sel3(dir, in[1], in[2], in[3]);
+  out[2] = sel3(dir, in[2], in[3], in[1]);
+  out[3] = sel3(dir, in[3], in[1], in[2]);
+  out[5] = sel3(dir, in[5], in[6], in[7]);
+  out[6] = sel3(dir, in[6], in[7], in[5]);
+  out[7] = sel3(dir, in[7], in[5], in[6]);
+}
+
+template <class T>
+__device__ __forceinline__ void unrotate_flux(int dir, const T in[8], T out[8]) {
+  out[0] = in[0];
+  out[4] = in[4];
+  out[1] = sel3(dir, in[1], in[3], in[2]);
+  out[2] = sel3(dir, in[2], in[1], in[3]);
+  out[3] = sel3(dir, in[3], in[2], in[1]);
+  out[5] = sel3(dir, in[5], in[7], in[6]);
+  out[6] = sel3(dir, in[6], in[5], in[7]);
+  out[7] = sel3(dir, in[7], in[6], in[5]);
+}
+
+// Packed symmetric metric [xx, xy, xz, yy, yz, zz] and shift in rotated axes.
+template <class T>
+__device__ __forceinline__ void rotate_metric(int dir, Geom<T>& m) {
+  const T gxx = m.g[0], gxy = m.g[1], gxz = m.g[2], gyy = m.g[3], gyz = m.g[4], gzz = m.g[5];
+  m.g[0] = sel3(dir, gxx, gyy, gzz);
+  m.g[1] = sel3(dir, gxy, gyz, gxz);
+  m.g[2] = sel3(dir, gxz, gxy, gyz);
+  m.g[3] = sel3(dir, gyy, gzz, gxx);
+  m.g[4] = sel3(dir, gyz, gxz, gxy);
+  m.g[5] = sel3(dir, gzz, gxx, gyy);
+  const T bx = m.beta[0], by = m.beta[1], bz = m.beta[2];
+  m.beta[0] = sel3(dir, bx, by, bz);
+  m.beta[1] = sel3(dir, by, bz, bx);
+  m.beta[2] = sel3(dir, bz, bx, by);
+}
+
 template <class T>
 __device__ __forceinline__ void lower(const T g[6], const T v[3], T vl[3]) {
   vl[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];

@@ -129,6 +129,59 @@ __device__ __forceinline__ void face_geometry(const SrcCacheT<PT, GT>& s, long l
   m.gup_dd = (T)__ldg(gm + (13 + DIR) * ncell + c);
 }
 
+// Face metric with a run-time face normal.
+template <class T>
+__device__ __forceinline__ void face_geometry_rt(const SrcF64& s, long long ncell, long long c, long long stride,
+                                                 int dir, Geom<T>& m) {
+  face_geom_rt<T>(s.metric, ncell, c, stride, dir, m);
+}
+template <class T, class PT, class GT>
+__device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, long long ncell, long long c,
+                                                 long long stride, int dir, Geom<T>& m) {
+  const GT* gm = s.geom;
+  T a[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = T(0.5) * ((T)__ldg(gm + q * ncell + c - stride) + (T)__ldg(gm + q * ncell + c));
+  m.alpha = a[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.beta[i] = a[1 + i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m.g[i] = a[4 + i];
+  m.sqrtg = (T)__ldg(gm + (10 + dir) * ncell + c);
+  m.gup_dd = (T)__ldg(gm + (13 + dir) * ncell + c);
+}
+
+// Flux through a face whose normal dir is known only at run time: the
+// states and the metric are relabelled so the normal is the first axis,
+// one x-face computation runs, and the flux is relabelled back (one copy of
+// the face code instead of three keeps the kernel small).
+template <class T, int RECON, bool CURVED, class S>
+__device__ __forceinline__ void face_flux_rt(const DevGrid& g, const DevParams& p, const S& src, long long c, int dir,
+                                             T F[8]) {
+  const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
+  T pL[8], pR[8];
+  reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+  Geom<T> m;
+  if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
+  if (!physical_state<T, CURVED>(pL, m)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+  }
+  if (!physical_state<T, CURVED>(pR, m)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+  }
+  T rL[8], rR[8], Fr[8];
+  rotate_state(dir, pL, rL);
+  rotate_state(dir, pR, rR);
+  if (CURVED) rotate_metric(dir, m);
+  Side<T> L, R;
+  side_state<T, CURVED, 0>(rL, m, (T)p.gamma, (T)p.gfac, L);
+  side_state<T, CURVED, 0>(rR, m, (T)p.gamma, (T)p.gfac, R);
+  hlle_combine<T>(L, R, Fr);
+  unrotate_flux(dir, Fr, F);
+}
+
 template <class T, int RECON, bool CURVED, int DIR, class S>
 __device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, const S& src, long long c, T F[8]) {
   const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
@@ -353,33 +406,29 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   const int ng = g.ng;
   for (int f = threadIdx.x; f < NF; f += NT) {
     T F[8];
+    int dir, xi, yi, zi;
     bool ok;
     if (f < NFX) {
-      const int a = f % (TX + 1), r = f / (TX + 1), b = r % TY, cz = r / TY;
-      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      const int a = f % (TX + 1), r = f / (TX + 1);
+      dir = 0;
+      xi = x0 + a; yi = y0 + r % TY; zi = z0 + r / TY;
       ok = (xi <= g.n[0]) && (yi < g.n[1]) && (zi < g.n[2]);
-      if (ok) {
-        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 0, S>(g, p, src, c, F);
-      }
     } else if (f < NFX + NFY) {
       const int ff = f - NFX;
-      const int a = ff % TX, r = ff / TX, b = r % (TY + 1), cz = r / (TY + 1);
-      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      const int r = ff / TX;
+      dir = 1;
+      xi = x0 + ff % TX; yi = y0 + r % (TY + 1); zi = z0 + r / (TY + 1);
       ok = (xi < g.n[0]) && (yi <= g.n[1]) && (zi < g.n[2]);
-      if (ok) {
-        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 1, S>(g, p, src, c, F);
-      }
     } else {
       const int ff = f - NFX - NFY;
-      const int a = ff % TX, r = ff / TX, b = r % TY, cz = r / TY;
-      const int xi = x0 + a, yi = y0 + b, zi = z0 + cz;
+      const int r = ff / TX;
+      dir = 2;
+      xi = x0 + ff % TX; yi = y0 + r % TY; zi = z0 + r / TY;
       ok = (xi < g.n[0]) && (yi < g.n[1]) && (zi <= g.n[2]);
-      if (ok) {
-        const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-        face_flux<T, RECON, CURVED, 2, S>(g, p, src, c, F);
-      }
+    }
+    if (ok) {
+      const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+      face_flux_rt<T, RECON, CURVED, S>(g, p, src, c, dir, F);
     }
     if (ok) {
 #pragma unroll
