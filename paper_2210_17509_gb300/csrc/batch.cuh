@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
                                                                  DevParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);
+  T* sR = sF + 8 * kMaxTileFaces;
   const int nbox = head->nbox;
   const long long total = head->ntiles;
   for (;;) {
@@ -81,16 +82,16 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
     src.kij = nullptr;
     switch (b.tile) {
       case 1:
-        rhs_tile<T, RECON, CURVED, 16, 4, 4, SrcF64>(g, p, src, ep, tx * 16, ty * 4, tz * 4, sF);
+        rhs_tile<T, RECON, CURVED, 16, 4, 4, SrcF64>(g, p, src, ep, tx * 16, ty * 4, tz * 4, sF, sR);
         break;
       case 2:
-        rhs_tile<T, RECON, CURVED, 32, 4, 2, SrcF64>(g, p, src, ep, tx * 32, ty * 4, tz * 2, sF);
+        rhs_tile<T, RECON, CURVED, 32, 4, 2, SrcF64>(g, p, src, ep, tx * 32, ty * 4, tz * 2, sF, sR);
         break;
       case 3:
-        rhs_tile<T, RECON, CURVED, 4, 8, 8, SrcF64>(g, p, src, ep, tx * 4, ty * 8, tz * 8, sF);
+        rhs_tile<T, RECON, CURVED, 4, 8, 8, SrcF64>(g, p, src, ep, tx * 4, ty * 8, tz * 8, sF, sR);
         break;
       default:
-        rhs_tile<T, RECON, CURVED, 8, 8, 4, SrcF64>(g, p, src, ep, tx * 8, ty * 8, tz * 4, sF);
+        rhs_tile<T, RECON, CURVED, 8, 8, 4, SrcF64>(g, p, src, ep, tx * 8, ty * 8, tz * 4, sF, sR);
         break;
     }
   }
@@ -104,7 +105,7 @@ cudaError_t launch_batch_rhs_t(BatchHead* head, const BoxDev* boxes, const DevPa
     k = curved ? batch_rhs_kernel<T, GRMHD_WENO5, true> : batch_rhs_kernel<T, GRMHD_WENO5, false>;
   else
     k = curved ? batch_rhs_kernel<T, GRMHD_MINMOD, true> : batch_rhs_kernel<T, GRMHD_MINMOD, false>;
-  const size_t smem = (size_t)8 * kMaxTileFaces * sizeof(T);
+  const size_t smem = p.recon == GRMHD_WENO5 ? batch_smem_bytes<T, GRMHD_WENO5>() : batch_smem_bytes<T, GRMHD_MINMOD>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -116,6 +116,77 @@ __device__ __forceinline__ void weno5_pair<double>(double um3, double um2, doubl
   vR = nR * (dL * r);
 }
 
+// Both WENO5 states of one cell i from u[i-2 .. i+2]: "plus" is the value at
+// the upper face i+1/2 (the left state of that face), "minus" the value at
+// the lower face i-1/2 (the right state, mirrored stencil).  The mirrored
+// stencil has the same three smoothness indicators in reverse order, so
+// they are formed once.  Two rescalings leave the nonlinear weights
+// unchanged: every (eps + beta_k) is multiplied by 12/13, which makes it
+// t_k^2 + (3/13) s_k^2 + (12/13) eps (eps13 is that last term), and the
+// candidate values are kept as 6 q_k, the factor 6 moving into the
+// denominator.
+//
+// FP64: product form.  The weights d_k / e_k^2 times (e_0 e_1 e_2)^2 are
+// plus (P12, 6 P02, 3 P01) and minus (P01, 6 P02, 3 P12) up to a common
+// factor, with Pjk = (e_j e_k)^2; the caller divides num / (6 den).
+__device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double u0, double up1, double up2,
+                                                 double eps13, double& nm, double& dm, double& np, double& dp) {
+  const double k313 = 3.0 / 13.0;
+  const double t0 = fma(-2.0, um1, um2 + u0), s0 = fma(3.0, u0, fma(-4.0, um1, um2));
+  const double t1 = fma(-2.0, u0, um1 + up1), s1 = um1 - up1;
+  const double t2 = fma(-2.0, up1, u0 + up2), s2 = fma(3.0, u0, fma(-4.0, up1, up2));
+  const double e0 = fma(t0, t0, fma(k313 * s0, s0, eps13));
+  const double e1 = fma(t1, t1, fma(k313 * s1, s1, eps13));
+  const double e2 = fma(t2, t2, fma(k313 * s2, s2, eps13));
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double P01 = p01 * p01, P12 = p12 * p12;
+  const double A = 6.0 * (p02 * p02), B = 3.0 * P01, C = 3.0 * P12;
+  const double u11 = 11.0 * u0;
+  const double qp0 = fma(2.0, um2, fma(-7.0, um1, u11));
+  const double qp1 = fma(2.0, up1, fma(5.0, u0, -um1));
+  const double qp2 = fma(5.0, up1, fma(2.0, u0, -up2));
+  const double qm0 = fma(2.0, up2, fma(-7.0, up1, u11));
+  const double qm1 = fma(2.0, um1, fma(5.0, u0, -up1));
+  const double qm2 = fma(5.0, um1, fma(2.0, u0, -um2));
+  np = fma(P12, qp0, fma(A, qp1, B * qp2));
+  dp = P12 + A + B;
+  nm = fma(P01, qm0, fma(A, qm1, C * qm2));
+  dm = P01 + A + C;
+}
+
+// FP32: reciprocal form (the squared products could overflow in single
+// precision): weights r_k = 1 / e_k^2, plus (r0, 6 r1, 3 r2), minus
+// (r2, 6 r1, 3 r0).
+__device__ __forceinline__ void weno5_cell(float um2, float um1, float u0, float up1, float up2, float eps13,
+                                           float& vm, float& vp) {
+  const float k313 = 3.0f / 13.0f;
+  const float t0 = fmaf(-2.0f, um1, um2 + u0), s0 = fmaf(3.0f, u0, fmaf(-4.0f, um1, um2));
+  const float t1 = fmaf(-2.0f, u0, um1 + up1), s1 = um1 - up1;
+  const float t2 = fmaf(-2.0f, up1, u0 + up2), s2 = fmaf(3.0f, u0, fmaf(-4.0f, up1, up2));
+  const float e0 = fmaf(t0, t0, fmaf(k313 * s0, s0, eps13));
+  const float e1 = fmaf(t1, t1, fmaf(k313 * s1, s1, eps13));
+  const float e2 = fmaf(t2, t2, fmaf(k313 * s2, s2, eps13));
+  const float r0 = __fdividef(1.0f, e0 * e0), r1 = 6.0f * __fdividef(1.0f, e1 * e1), r2 = __fdividef(1.0f, e2 * e2);
+  const float u11 = 11.0f * u0;
+  const float qp0 = fmaf(2.0f, um2, fmaf(-7.0f, um1, u11));
+  const float qp1 = fmaf(2.0f, up1, fmaf(5.0f, u0, -um1));
+  const float qp2 = fmaf(5.0f, up1, fmaf(2.0f, u0, -up2));
+  const float qm0 = fmaf(2.0f, up2, fmaf(-7.0f, up1, u11));
+  const float qm1 = fmaf(2.0f, um1, fmaf(5.0f, u0, -up1));
+  const float qm2 = fmaf(5.0f, um1, fmaf(2.0f, u0, -um2));
+  const float R0 = 3.0f * r0, R2 = 3.0f * r2;
+  vp = __fdividef(fmaf(r0, qp0, fmaf(r1, qp1, R2 * qp2)), 6.0f * (r0 + r1 + R2));
+  vm = __fdividef(fmaf(r2, qm0, fmaf(r1, qm1, R0 * qm2)), 6.0f * (r2 + r1 + R0));
+}
+
+// Both minmod states of one cell from u[i-1 .. i+1].
+template <class T>
+__device__ __forceinline__ void minmod_cell(T um1, T u0, T up1, T& vm, T& vp) {
+  const T h = T(0.5) * minmod<T>(u0 - um1, up1 - u0);
+  vp = u0 + h;
+  vm = u0 - h;
+}
+
 // ---------------------------------------------------------------- geometry
 // Metric at a face (or a cell) converted to the compute type.
 template <class T>
@@ -245,12 +316,25 @@ struct Side {
   T U[8];
   T F[8];
   T lm, lp;
+  T sden;  // speed denominator (SHARED side states only)
 };
 
 // Conserved vector (Eqs. 6-9), flux along DIR (Eq. 12) and signal speeds of
 // the primitive state pr at a face with metric m.
-template <class T, bool CURVED, int DIR>
-__device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T gamma, T gfac, Side<T>& o) {
+//
+// Signal speeds: with the fast-magnetosonic bound
+// a^2 = cs^2 + vA^2 - cs^2 vA^2, cs^2 = Gamma P / (rho h), vA^2 = b^2 / hs,
+// hs = rho h + b^2, the bound simplifies to a^2 = Na / hs, Na = Gamma P + b^2,
+// and the two roots become
+//   lambda_pm = alpha [v^d (hs - Na) pm sqrt(Na (1 - v^2) Q)] / (hs - v^2 Na) - beta^d,
+//   Q = gamma^{dd} (hs - v^2 Na) - (v^d)^2 (hs - Na)   (clamped at 0),
+// one division per side.  SHARED: the caller passes 1/alpha (ia) and
+// finishes the speeds itself -- lm / lp then hold the bracketed numerators
+// and sden the denominator -- so that the two sides of a face share one
+// division (finish_speeds).
+template <class T, bool CURVED, int DIR, bool SHARED = false>
+__device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T gamma, T gfac, Side<T>& o,
+                                           T ia_in = T(0)) {
   const T rho = pr[0], P = pr[4];
   const T v[3] = {pr[1], pr[2], pr[3]};
   const T B[3] = {pr[5], pr[6], pr[7]};
@@ -291,7 +375,7 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   const T alpha = CURVED ? m.alpha : T(1);
   T vt[3];
   if (CURVED) {
-    const T ia = T(1) / alpha;
+    const T ia = SHARED ? ia_in : T(1) / alpha;
 #pragma unroll
     for (int i = 0; i < 3; ++i) vt[i] = v[i] - m.beta[i] * ia;
   } else {
@@ -308,21 +392,38 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
 #pragma unroll
   for (int k = 0; k < 3; ++k) o.F[5 + k] = (k == DIR) ? T(0) : alpha * (Bc[k] * vtd - Bc[DIR] * vt[k]);
   // signal speeds
-  const T r = T(1) / (rhoh * hs);
-  const T cs2 = gamma * P * hs * r;
-  const T va2 = b2 * rhoh * r;
-  const T a2 = cs2 + va2 - cs2 * va2;
+  const T Na = gamma * P + b2;
+  const T dsp = hs - v2 * Na;  // (1 - v^2 a^2) hs
+  const T hmn = hs - Na;       // (1 - a^2) hs
   const T gdd = CURVED ? m.gup_dd : T(1);
-  const T den = T(1) - v2 * a2;
   const T vd = v[DIR];
-  T disc = omv2 * (gdd * den - vd * vd * (T(1) - a2));
-  disc = xmax(disc, T(0));
-  const T sq = xsqrt(a2 * disc);
-  const T ide = alpha / den;
-  const T c0 = vd * (T(1) - a2);
+  const T Q = xmax(gdd * dsp - vd * vd * hmn, T(0));
+  const T sq = xsqrt(Na * omv2 * Q);
+  const T c0 = vd * hmn;
+  if (SHARED) {
+    o.lp = c0 + sq;
+    o.lm = c0 - sq;
+    o.sden = dsp;
+  } else {
+    const T ide = alpha / dsp;
+    const T bd = CURVED ? m.beta[DIR] : T(0);
+    o.lp = ide * (c0 + sq) - bd;
+    o.lm = ide * (c0 - sq) - bd;
+  }
+}
+
+// Speeds of the two sides of a face from their SHARED side states: one
+// division for both denominators.
+template <class T, bool CURVED, int DIR>
+__device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side<T>& R) {
+  const T alpha = CURVED ? m.alpha : T(1);
   const T bd = CURVED ? m.beta[DIR] : T(0);
-  o.lp = ide * (c0 + sq) - bd;
-  o.lm = ide * (c0 - sq) - bd;
+  const T X = alpha / (L.sden * R.sden);
+  const T iL = R.sden * X, iR = L.sden * X;
+  L.lp = iL * L.lp - bd;
+  L.lm = iL * L.lm - bd;
+  R.lp = iR * R.lp - bd;
+  R.lm = iR * R.lm - bd;
 }
 
 // HLLE flux (Sec. 2.3) from the two sides; 1e-300 (double) / 1e-30 (float)

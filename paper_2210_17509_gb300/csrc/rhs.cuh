@@ -104,29 +104,45 @@ __device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim
   reconstruct_face<T, RECON, SrcF64>(s, ncell, c, stride, eps, pL, pR);
 }
 
-// Face metric from the inputs (FP64 mean, FP64 sqrt(gamma) and gamma^dd).
-template <class T, int DIR>
-__device__ __forceinline__ void face_geometry(const SrcF64& s, long long ncell, long long c, long long stride,
-                                              Geom<T>& m) {
-  face_geom<T, DIR>(s.metric, ncell, c, stride, m);
-}
-
-// Face metric from the cache: mean of the two cells (in the compute type),
-// cached sqrt(gamma) and gamma^dd of the face.
-template <class T, int DIR, class PT, class GT>
-__device__ __forceinline__ void face_geometry(const SrcCacheT<PT, GT>& s, long long ncell, long long c,
-                                              long long stride, Geom<T>& m) {
-  const GT* gm = s.geom;
-  T a[10];
+// Both reconstructed states of cell c (value at its lower face, "minus", and
+// at its upper face, "plus") for the primitives 2h and 2h+1, written to the
+// stage buffer sR at [2q][e] (minus) and [2q+1][e] (plus), ne entries per
+// component.  eps13 = (12/13) weno_eps (see weno5_cell_parts).
+template <class T, int RECON, class S>
+__device__ __forceinline__ void reconstruct_cell_pair(const S& src, long long ncell, long long c, long long stride,
+                                                      int h, T eps13, T* __restrict__ sR, int ne, int e) {
+  if constexpr (RECON == GRMHD_WENO5 && sizeof(T) == 8) {
+    // FP64: the four values of the two variables share one division
+    double nm[2], dm[2], np[2], dp[2];
 #pragma unroll
-  for (int q = 0; q < 10; ++q) a[q] = T(0.5) * ((T)__ldg(gm + q * ncell + c - stride) + (T)__ldg(gm + q * ncell + c));
-  m.alpha = a[0];
+    for (int k = 0; k < 2; ++k) {
+      const long long a = (2 * h + k) * ncell + c;
+      weno5_cell_parts(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride),
+                       ld_prim<double>(src, a), ld_prim<double>(src, a + stride),
+                       ld_prim<double>(src, a + 2 * stride), (double)eps13, nm[k], dm[k], np[k], dp[k]);
+    }
+    const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
+    const double X = 1.0 / (6.0 * a0 * a1);
+    const double x0 = a1 * X, x1 = a0 * X;
+    sR[(4 * h + 0) * ne + e] = (T)(nm[0] * (dp[0] * x0));
+    sR[(4 * h + 1) * ne + e] = (T)(np[0] * (dm[0] * x0));
+    sR[(4 * h + 2) * ne + e] = (T)(nm[1] * (dp[1] * x1));
+    sR[(4 * h + 3) * ne + e] = (T)(np[1] * (dm[1] * x1));
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) m.beta[i] = a[1 + i];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) m.g[i] = a[4 + i];
-  m.sqrtg = (T)__ldg(gm + (10 + DIR) * ncell + c);
-  m.gup_dd = (T)__ldg(gm + (13 + DIR) * ncell + c);
+    for (int k = 0; k < 2; ++k) {
+      const long long a = (2 * h + k) * ncell + c;
+      T vm, vp;
+      if constexpr (RECON == GRMHD_WENO5) {
+        weno5_cell((float)ld_prim<T>(src, a - 2 * stride), (float)ld_prim<T>(src, a - stride), (float)ld_prim<T>(src, a),
+                   (float)ld_prim<T>(src, a + stride), (float)ld_prim<T>(src, a + 2 * stride), (float)eps13, vm, vp);
+      } else {
+        minmod_cell<T>(ld_prim<T>(src, a - stride), ld_prim<T>(src, a), ld_prim<T>(src, a + stride), vm, vp);
+      }
+      sR[(4 * h + 2 * k) * ne + e] = vm;
+      sR[(4 * h + 2 * k + 1) * ne + e] = vp;
+    }
+  }
 }
 
 // Face metric with a run-time face normal.
@@ -151,16 +167,14 @@ __device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, lon
   m.gup_dd = (T)__ldg(gm + (13 + dir) * ncell + c);
 }
 
-// Flux through a face whose normal dir is known only at run time: the
-// states and the metric are relabelled so the normal is the first axis,
-// one x-face computation runs, and the flux is relabelled back (one copy of
-// the face code instead of three keeps the kernel small).
-template <class T, int RECON, bool CURVED, class S>
-__device__ __forceinline__ void face_flux_rt(const DevGrid& g, const DevParams& p, const S& src, long long c, int dir,
-                                             T F[8]) {
-  const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
-  T pL[8], pR[8];
-  reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+// Flux through a face whose normal dir is known only at run time, from its
+// reconstructed left / right states: the states and the metric are
+// relabelled so the normal is the first axis, one x-face computation runs,
+// and the flux is relabelled back (one copy of the face code instead of
+// three keeps the kernel small).  c is the cell above the face.
+template <class T, bool CURVED, class S>
+__device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevParams& p, const S& src, long long c,
+                                                 int dir, long long stride, T pL[8], T pR[8], T F[8]) {
   Geom<T> m;
   if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
   if (!physical_state<T, CURVED>(pL, m)) {
@@ -176,35 +190,14 @@ __device__ __forceinline__ void face_flux_rt(const DevGrid& g, const DevParams& 
   rotate_state(dir, pR, rR);
   if (CURVED) rotate_metric(dir, m);
   Side<T> L, R;
-  side_state<T, CURVED, 0>(rL, m, (T)p.gamma, (T)p.gfac, L);
-  side_state<T, CURVED, 0>(rR, m, (T)p.gamma, (T)p.gfac, R);
+  const T ia = CURVED ? T(1) / m.alpha : T(1);  // shared by both sides
+  side_state<T, CURVED, 0, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia);
+  side_state<T, CURVED, 0, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia);
+  finish_speeds<T, CURVED, 0>(m, L, R);
   hlle_combine<T>(L, R, Fr);
   unrotate_flux(dir, Fr, F);
 }
 
-template <class T, int RECON, bool CURVED, int DIR, class S>
-__device__ __forceinline__ void face_flux(const DevGrid& g, const DevParams& p, const S& src, long long c, T F[8]) {
-  const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
-  T pL[8], pR[8];
-  reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
-  Geom<T> m;
-  if (CURVED) face_geometry<T, DIR>(src, g.ncell, c, stride, m);
-  // A face state with rho <= 0, P <= 0 or v^2 >= 1 falls back to the state of
-  // the cell it was reconstructed from (rare; WENO5 overshoot at sharp
-  // gradients of under-resolved data).
-  if (!physical_state<T, CURVED>(pL, m)) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
-  }
-  if (!physical_state<T, CURVED>(pR, m)) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
-  }
-  Side<T> L, R;
-  side_state<T, CURVED, DIR>(pL, m, (T)p.gamma, (T)p.gfac, L);
-  side_state<T, CURVED, DIR>(pR, m, (T)p.gamma, (T)p.gfac, R);
-  hlle_combine<T>(L, R, F);
-}
 
 // Eq. 13 in 3+1 form for a static-in-time lapse and shift:
 //   S_{S_j} = alpha sqrt(gamma) [ T^00 (beta^i beta^k d_j g_ik / 2 - alpha d_j alpha)
@@ -386,56 +379,188 @@ struct TileFaces {
   static constexpr int NFZ = TX * TY * (TZ + 1);
   static constexpr int NF = NFX + NFY + NFZ;
 };
-// Largest face count over the 256-cell shapes 0..3 (the batched kernel's
-// shared face buffer); single-block launches size it per shape.
-constexpr int kMaxTileFaces = 968;
+// Reconstruction stage: per direction, the tile extended by one cell on
+// both sides along that direction (EXX, EYY, EZZ cells); NE is the largest
+// of the three, NEA their sum.
+template <int TX, int TY, int TZ>
+struct TileStage {
+  static constexpr int EXX = (TX + 2) * TY * TZ, EYY = TX * (TY + 2) * TZ, EZZ = TX * TY * (TZ + 2);
+  static constexpr int NE = EXX > EYY ? (EXX > EZZ ? EXX : EZZ) : (EYY > EZZ ? EYY : EZZ);
+  static constexpr int NEA = EXX + EYY + EZZ;
+};
 
-// One tile of the RHS: all face fluxes of the tile (each once) into the
-// shared buffer sF [8][NF], then each thread differences its cell's faces,
-// adds the sources and applies the stage epilogue.  Called by all threads of
-// the CTA (contains __syncthreads); kTileThreads threads, each handling one
-// or more cells of the TX*TY*TZ tile.
+// Reconstruction per cell (both face states of a cell from one stencil,
+// staged in shared memory) pays off where the reconstruction dominates:
+// FP64 WENO5.  FP32 and minmod reconstruct per face, inline.
+template <class T, int RECON>
+struct CellRecon { static constexpr bool value = RECON == GRMHD_WENO5 && sizeof(T) == 8; };
+
+constexpr size_t kMaxTileSmem = 227 * 1024;
+
+// Stage layout of a tile: all three directions at once (one face pass over
+// every face of the tile) when the shared memory allows, else one direction
+// at a time (three face passes).
+template <class T, int RECON, int TX, int TY, int TZ>
+struct TileSmem {
+  static constexpr size_t faces = (size_t)8 * TileFaces<TX, TY, TZ>::NF * sizeof(T);
+  static constexpr size_t all = faces + (size_t)16 * TileStage<TX, TY, TZ>::NEA * sizeof(T);
+  static constexpr bool stage_all = CellRecon<T, RECON>::value && all <= kMaxTileSmem;
+  static constexpr size_t bytes = !CellRecon<T, RECON>::value
+                                      ? faces
+                                      : (stage_all ? all : faces + (size_t)16 * TileStage<TX, TY, TZ>::NE * sizeof(T));
+  // stage entries per component
+  static constexpr int ns = stage_all ? TileStage<TX, TY, TZ>::NEA : TileStage<TX, TY, TZ>::NE;
+};
+
+template <class T, int RECON, int TX, int TY, int TZ>
+constexpr size_t tile_smem_bytes() { return TileSmem<T, RECON, TX, TY, TZ>::bytes; }
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// Batched kernel (one buffer for the shapes 0..3): face buffer
+// [8][kMaxTileFaces], then the stage [16][batch_stage_entries].
+constexpr int kMaxTileFaces = 968;  // largest NF over the shapes 0..3
+template <class T, int RECON>
+constexpr int batch_stage_entries() {
+  return !CellRecon<T, RECON>::value
+             ? 0
+             : (int)cmax(cmax(TileSmem<T, RECON, 8, 8, 4>::ns, TileSmem<T, RECON, 16, 4, 4>::ns),
+                         cmax(TileSmem<T, RECON, 32, 4, 2>::ns, TileSmem<T, RECON, 4, 8, 8>::ns));
+}
+template <class T, int RECON>
+constexpr size_t batch_smem_bytes() {
+  return (size_t)(8 * kMaxTileFaces + 16 * batch_stage_entries<T, RECON>()) * sizeof(T);
+}
+
+// Face flux of face f (flat index over the NFX x-, NFY y- and NFZ z-faces of
+// the tile) into sF [8][NF].  With a stage, the face states come from sR
+// (stage index of the cell below the face: eoff[dir] + its index in that
+// direction's extended box); otherwise they are reconstructed here.
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
+__device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, const S& src, int x0, int y0, int z0,
+                                          int f, T* __restrict__ sF, const T* __restrict__ sR, int ns, int eoff_y,
+                                          int eoff_z) {
+  constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
+  constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
+  constexpr int NF = TileFaces<TX, TY, TZ>::NF;
+  // face coordinates in the tile (compile-time divisors per direction)
+  int dir, fx, fy, fz;
+  if (f < NFX) {
+    dir = 0;
+    fx = f % (TX + 1); fy = (f / (TX + 1)) % TY; fz = f / ((TX + 1) * TY);
+  } else if (f < NFX + NFY) {
+    const int fl = f - NFX;
+    dir = 1;
+    fx = fl % TX; fy = (fl / TX) % (TY + 1); fz = fl / (TX * (TY + 1));
+  } else {
+    const int fl = f - NFX - NFY;
+    dir = 2;
+    fx = fl % TX; fy = (fl / TX) % TY; fz = fl / (TX * TY);
+  }
+  const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
+  const int xi = x0 + fx, yi = y0 + fy, zi = z0 + fz;
+  if (!(xi < g.n[0] + ux && yi < g.n[1] + uy && zi < g.n[2] + uz)) return;
+  const int ng = g.ng;
+  const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+  const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
+  T pL[8], pR[8], F[8];
+  if constexpr (CellRecon<T, RECON>::value) {
+    // extended box of this direction: one more cell on each side along dir
+    const int ex_n = TX + 2 * ux, ey_n = TY + 2 * uy;
+    const int eL = (dir == 0 ? 0 : (dir == 1 ? eoff_y : eoff_z)) + (fz * ey_n + fy) * ex_n + fx;
+    const int eR = eL + (dir == 0 ? 1 : (dir == 1 ? ex_n : ex_n * ey_n));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      pL[q] = sR[(2 * q + 1) * ns + eL];
+      pR[q] = sR[(2 * q) * ns + eR];
+    }
+  } else {
+    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+  }
+  face_flux_states<T, CURVED, S>(g, p, src, c, dir, stride, pL, pR, F);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sF[q * NF + f] = F[q];
+}
+
+// Stage item it of the directions [d0, d1]: cell e of the extended box of
+// its direction, variable pair h; written at stage index eoff + e.
+template <class T, int RECON, int TX, int TY, int TZ, class S>
+__device__ __forceinline__ void tile_stage_item(const DevGrid& g, const S& src, int x0, int y0, int z0, int dir, int e,
+                                                int h, int eoff, T eps13, T* __restrict__ sR, int ns) {
+  const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
+  int ex, ey, ez;  // compile-time divisors per direction
+  if (dir == 0) {
+    ex = e % (TX + 2); ey = (e / (TX + 2)) % TY; ez = e / ((TX + 2) * TY);
+  } else if (dir == 1) {
+    ex = e % TX; ey = (e / TX) % (TY + 2); ez = e / (TX * (TY + 2));
+  } else {
+    ex = e % TX; ey = (e / TX) % TY; ez = e / (TX * TY);
+  }
+  const int xi = x0 + ex - ux, yi = y0 + ey - uy, zi = z0 + ez - uz;
+  // cells -1 .. n along dir (ghosts have >= 3 layers), interior across
+  if (xi < g.n[0] + ux && yi < g.n[1] + uy && zi < g.n[2] + uz) {
+    const int ng = g.ng;
+    const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+    const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
+    reconstruct_cell_pair<T, RECON, S>(src, g.ncell, c, stride, h, eps13, sR, ns, eoff + e);
+  }
+}
+
+// One tile of the RHS.  Every face flux of the tile is computed once into
+// the face buffer sF [8][NF].  For FP64 WENO5 the reconstruction runs per
+// cell first: every cell of the tile extended by one along a direction
+// reconstructs both of its face states in that direction into the stage
+// buffer sR [16][ns] (all three directions at once, or one at a time when
+// the shared memory is short), and each face takes its left state (plus
+// state of the cell below) and right state (minus state of the cell above)
+// from there.  Then each thread differences its cell's six faces, adds the
+// sources and applies the stage epilogue.  Called by all threads of the CTA
+// (contains __syncthreads); kTileThreads threads, each handling one or more
+// cells of the TX*TY*TZ tile.
 template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
 __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
-                                         int x0, int y0, int z0, T* sF) {
+                                         int x0, int y0, int z0, T* sF, T* sR) {
   constexpr int NT = kTileThreads;
   constexpr int NC = TX * TY * TZ;
   constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
   constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
+  constexpr int NFZ = TileFaces<TX, TY, TZ>::NFZ;
   constexpr int NF = TileFaces<TX, TY, TZ>::NF;
+  using ST = TileStage<TX, TY, TZ>;
+  using SM = TileSmem<T, RECON, TX, TY, TZ>;
   const int ng = g.ng;
-  for (int f = threadIdx.x; f < NF; f += NT) {
-    T F[8];
-    int dir, xi, yi, zi;
-    bool ok;
-    if (f < NFX) {
-      const int a = f % (TX + 1), r = f / (TX + 1);
-      dir = 0;
-      xi = x0 + a; yi = y0 + r % TY; zi = z0 + r / TY;
-      ok = (xi <= g.n[0]) && (yi < g.n[1]) && (zi < g.n[2]);
-    } else if (f < NFX + NFY) {
-      const int ff = f - NFX;
-      const int r = ff / TX;
-      dir = 1;
-      xi = x0 + ff % TX; yi = y0 + r % (TY + 1); zi = z0 + r / (TY + 1);
-      ok = (xi < g.n[0]) && (yi <= g.n[1]) && (zi < g.n[2]);
-    } else {
-      const int ff = f - NFX - NFY;
-      const int r = ff / TX;
-      dir = 2;
-      xi = x0 + ff % TX; yi = y0 + r % TY; zi = z0 + r / TY;
-      ok = (xi < g.n[0]) && (yi < g.n[1]) && (zi <= g.n[2]);
+  if constexpr (!CellRecon<T, RECON>::value) {
+    for (int f = threadIdx.x; f < NF; f += NT)
+      tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f, sF, sR, 0, 0, 0);
+    __syncthreads();
+  } else if constexpr (SM::stage_all) {
+    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+    for (int it = threadIdx.x; it < 4 * ST::NEA; it += NT) {
+      const int ea = it % ST::NEA, h = it / ST::NEA;
+      const int dir = ea < ST::EXX ? 0 : (ea < ST::EXX + ST::EYY ? 1 : 2);
+      const int eoff = dir == 0 ? 0 : (dir == 1 ? ST::EXX : ST::EXX + ST::EYY);
+      tile_stage_item<T, RECON, TX, TY, TZ, S>(g, src, x0, y0, z0, dir, ea - eoff, h, eoff, eps13, sR, ST::NEA);
     }
-    if (ok) {
-      const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-      face_flux_rt<T, RECON, CURVED, S>(g, p, src, c, dir, F);
-    }
-    if (ok) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sF[q * NF + f] = F[q];
+    __syncthreads();
+    for (int f = threadIdx.x; f < NF; f += NT)
+      tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f, sF, sR, ST::NEA, ST::EXX,
+                                                  ST::EXX + ST::EYY);
+    __syncthreads();
+  } else {
+    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int ne = dir == 0 ? ST::EXX : (dir == 1 ? ST::EYY : ST::EZZ);
+      for (int it = threadIdx.x; it < 4 * ne; it += NT)
+        tile_stage_item<T, RECON, TX, TY, TZ, S>(g, src, x0, y0, z0, dir, it % ne, it / ne, 0, eps13, sR, ST::NE);
+      __syncthreads();
+      const int f0 = dir == 0 ? 0 : (dir == 1 ? NFX : NFX + NFY);
+      const int nfd = dir == 0 ? NFX : (dir == 1 ? NFY : NFZ);
+      for (int f = threadIdx.x; f < nfd; f += NT)
+        tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f0 + f, sF, sR, ST::NE, 0, 0);
+      __syncthreads();
     }
   }
-  __syncthreads();
 
 #pragma unroll 1
   for (int cl = threadIdx.x; cl < NC; cl += NT) {
@@ -486,26 +611,32 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(De
   using TS = TileShape<SHAPE>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);
+  T* sR = sF + 8 * TileFaces<TS::X, TS::Y, TS::Z>::NF;  // stage (FP64 WENO5 only)
   rhs_tile<T, RECON, CURVED, TS::X, TS::Y, TS::Z, S>(g, p, src, ep, blockIdx.x * TS::X, blockIdx.y * TS::Y,
-                                                      blockIdx.z * TS::Z, sF);
+                                                      blockIdx.z * TS::Z, sF, sR);
 }
 
 template <class T, int RECON, bool CURVED, class S>
 cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
                              cudaStream_t s) {
   void (*k)(DevGrid, DevParams, S, StageEpilogue) = nullptr;
-  int tx = 8, ty = 8, tz = 4;
-  int nf = TileFaces<8, 8, 4>::NF;
+  int tx, ty, tz;
+  size_t smem;
   switch (shape) {
-    case 4: k = rhs_kernel<T, RECON, CURVED, 4, S>; tx = TileShape<4>::X; ty = TileShape<4>::Y; tz = TileShape<4>::Z;
-            nf = TileFaces<8, 8, 8>::NF; break;
-    case 1: k = rhs_kernel<T, RECON, CURVED, 1, S>; tx = TileShape<1>::X; ty = TileShape<1>::Y; tz = TileShape<1>::Z; break;
-    case 2: k = rhs_kernel<T, RECON, CURVED, 2, S>; tx = TileShape<2>::X; ty = TileShape<2>::Y; tz = TileShape<2>::Z; break;
-    case 3: k = rhs_kernel<T, RECON, CURVED, 3, S>; tx = TileShape<3>::X; ty = TileShape<3>::Y; tz = TileShape<3>::Z; break;
-    default: k = rhs_kernel<T, RECON, CURVED, 0, S>; break;
+#define GRMHD_SHAPE_CASE(SH)                                                          \
+  case SH:                                                                            \
+    k = rhs_kernel<T, RECON, CURVED, SH, S>;                                          \
+    tx = TileShape<SH>::X; ty = TileShape<SH>::Y; tz = TileShape<SH>::Z;              \
+    smem = tile_smem_bytes<T, RECON, TileShape<SH>::X, TileShape<SH>::Y, TileShape<SH>::Z>(); \
+    break;
+    GRMHD_SHAPE_CASE(1)
+    GRMHD_SHAPE_CASE(2)
+    GRMHD_SHAPE_CASE(3)
+    GRMHD_SHAPE_CASE(4)
+    default:
+    GRMHD_SHAPE_CASE(0)
+#undef GRMHD_SHAPE_CASE
   }
-  if (shape >= 1 && shape <= 3) nf = kMaxTileFaces;
-  const size_t smem = (size_t)8 * nf * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((g.n[0] + tx - 1) / tx, (g.n[1] + ty - 1) / ty, (g.n[2] + tz - 1) / tz);
