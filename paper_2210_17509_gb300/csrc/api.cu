@@ -315,7 +315,10 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
       if (launch_rhs_mixed_cached(g, p, prim32, static_cast<const float*>(geom), kij, metric != nullptr, ep, s) !=
           cudaSuccess)
         return GRMHD_ERR_CUDA;
-      if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, metric ? mcache : nullptr, nfail, s) != cudaSuccess)
+      // the FP64 primitives are needed after the last stage (and when recording)
+      const bool result64 = k == ns - 1 || record;
+      if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, metric ? mcache : nullptr,
+                                metric ? static_cast<const float*>(geom) : nullptr, result64, nfail, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;
       if (launch_fill_ghosts_f32(g, p.bc, 8, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
       if ((k == ns - 1 || record) && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;

@@ -64,9 +64,11 @@ cudaError_t launch_con2prim(const DevGrid& g, const DevParams& p, const double* 
 cudaError_t launch_prim2con(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
                             double* cons, cudaStream_t s);
 cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field, cudaStream_t s);
-// Fast mixed path: FP32 primitive copy and the FP64-computed geometry cache.
+// Fast mixed path: FP32 primitive copy and the FP64-computed geometry cache
+// (geom32 nullable); result64 = false writes the FP32 primitives only.
 cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
-                                  double* prim, float* prim32, const double* mcache, int32_t* nfail, cudaStream_t s);
+                                  double* prim, float* prim32, const double* mcache, const float* geom32,
+                                  bool result64, int32_t* nfail, cudaStream_t s);
 cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s);
 cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, void* geom, bool fp64, double* mcache,

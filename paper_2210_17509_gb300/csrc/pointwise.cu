@@ -57,16 +57,17 @@ __global__ void fill_ghosts_kernel(DevGrid g, int bc, int nvar, double* __restri
 }
 
 // Mixed path: FP32-predicted FP64 recovery, writing FP64 and FP32 primitives.
+template <bool RESULT64>
 __global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                       const double* __restrict__ metric, double* __restrict__ prim,
                                       float* __restrict__ prim32, const double* __restrict__ mcache,
-                                      int32_t* __restrict__ nfail) {
+                                      const float* __restrict__ geom32, int32_t* __restrict__ nfail) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   int myfail = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    myfail += (con2prim_at<true>(g, p, cons, metric, prim, c, prim32, mcache) >= 2);
+    myfail += (con2prim_at<true, true, RESULT64>(g, p, cons, metric, prim, c, prim32, mcache, geom32) >= 2);
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }
@@ -192,9 +193,15 @@ cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field
 namespace grmhd {
 
 cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
-                                  double* prim, float* prim32, const double* mcache, int32_t* nfail, cudaStream_t s) {
+                                  double* prim, float* prim32, const double* mcache, const float* geom32,
+                                  bool result64, int32_t* nfail, cudaStream_t s) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  con2prim_mixed_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache, nfail);
+  if (result64)
+    con2prim_mixed_kernel<true><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache,
+                                                                      geom32, nfail);
+  else
+    con2prim_mixed_kernel<false><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache,
+                                                                       geom32, nfail);
   return cudaGetLastError();
 }
 

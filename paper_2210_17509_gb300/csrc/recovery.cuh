@@ -162,12 +162,19 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 // also stored in prim32.  mcache (nullable) holds, per point, 1/sqrt(gamma)
 // and gamma^ij in FP64 (7 components), saving the per-call inverse.
 // F32IO (with PREDICT) takes the guess from and writes the result to prim32;
-// without it the guess is read from the FP64 primitives.
-template <bool PREDICT, bool F32IO = PREDICT>
+// without it the guess is read from the FP64 primitives.  geom32 (nullable,
+// F32IO only) is the FP32 geometry cache, whose gamma_ij and gamma^ij then
+// serve the single-precision parts.  Without RESULT64 (F32IO only) the
+// primitives are formed in FP32 from the FP64 root (z, W) and only prim32 is
+// written: for the intermediate stages of a mixed step, whose primitives
+// feed only the FP32 RHS and the next recovery's guess.
+template <bool PREDICT, bool F32IO = PREDICT, bool RESULT64 = true>
 __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p, const double* __restrict__ cons,
                                            const double* __restrict__ metric, double* __restrict__ prim,
                                            long long c, float* __restrict__ prim32 = nullptr,
-                                           const double* __restrict__ mcache = nullptr) {
+                                           const double* __restrict__ mcache = nullptr,
+                                           const float* __restrict__ geom32 = nullptr) {
+  static_assert(RESULT64 || F32IO, "an FP32-only result needs the FP32 primitives");
   CellMetric m;
   double isg;
   if (mcache && metric) {
@@ -203,7 +210,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   if (F32IO) {
     const float* pf = prim32 + c;
     const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
-    const float gf[6] = {(float)m.g[0], (float)m.g[1], (float)m.g[2], (float)m.g[3], (float)m.g[4], (float)m.g[5]};
+    float gf[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : (float)m.g[i];
     float vl[3];
     lower(gf, v, vl);
     const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
@@ -225,6 +234,55 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     double tol_first = p.nr_tol;
     if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
     st = c2p_solve(in, p, z, W, tol_first);
+  }
+  if constexpr (!RESULT64) {
+    // FP32 primitives from the FP64 root: 1/W, 1/z, 1/(z + B^2) from one division
+    float outf[8];
+    const float Bf[3] = {(float)B[0], (float)B[1], (float)B[2]};
+    if (st != 2) {
+      const float zf = (float)z, Wf = (float)W, zbf = (float)(z + in.B2);
+      const float X = 1.0f / (Wf * zf * zbf);
+      const float iW = zf * zbf * X, iz = Wf * zbf * X, izb = Wf * zf * X;
+      const float rho = (float)D * iW;
+      const float P = (float)p.gm1g * (zf * iW * iW - rho);
+      const float bsz = (float)BS * iz;
+      float gf[6], guf[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : (float)m.g[i];
+        guf[i] = geom32 ? __ldg(geom32 + (17 + i) * g.ncell + c) : (float)m.gu[i];
+      }
+      float Blf[3], vlo[3], vu[3];
+      lower(gf, Bf, Blf);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) vlo[i] = ((float)Sl[i] + bsz * Blf[i]) * izb;
+      lower(guf, vlo, vu);
+      const float v2 = vu[0] * vlo[0] + vu[1] * vlo[1] + vu[2] * vlo[2];
+      if (rho >= (float)p.rho_atm && v2 < 1.0f && isfinite(P)) {
+        outf[0] = rho;
+        outf[1] = vu[0];
+        outf[2] = vu[1];
+        outf[3] = vu[2];
+        outf[4] = P;
+        if (!(P > 0.0f)) {
+          outf[4] = (float)p.p_atm;
+          st = 3;
+        }
+      } else {
+        st = 2;
+      }
+    }
+    if (st == 2) {
+      outf[0] = (float)p.rho_atm;
+      outf[1] = outf[2] = outf[3] = 0.0f;
+      outf[4] = (float)p.p_atm;
+    }
+    outf[5] = Bf[0];
+    outf[6] = Bf[1];
+    outf[7] = Bf[2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = outf[q];
+    return st;
   }
   double out[8];
   if (st != 2) {
