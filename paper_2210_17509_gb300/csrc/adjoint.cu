@@ -290,72 +290,75 @@ __global__ void fill_ghosts_adjoint_kernel(DevGrid g, int bc, int nvar, double* 
 }
 
 // ----------------------------------------------------- reconstruction adjoint
-// WENO5 value v(u0..u4) at the right face of the middle cell: returns v and
-// adds dv/du_k * vbar to ub[k].
-__device__ __forceinline__ double weno5_adj(const double u[5], double eps, double vbar, double ub[5]) {
-  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
-  const double q0 = (2.0 * u[0] - 7.0 * u[1] + 11.0 * u[2]) * c6;
-  const double q1 = (-u[1] + 5.0 * u[2] + 2.0 * u[3]) * c6;
-  const double q2 = (2.0 * u[2] + 5.0 * u[3] - u[4]) * c6;
-  const double t0 = u[0] - 2.0 * u[1] + u[2], s0 = u[0] - 4.0 * u[1] + 3.0 * u[2];
-  const double t1 = u[1] - 2.0 * u[2] + u[3], s1 = u[1] - u[3];
-  const double t2 = u[2] - 2.0 * u[3] + u[4], s2 = 3.0 * u[2] - 4.0 * u[3] + u[4];
-  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
-  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
-  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
-  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
-  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
-  const double iw = 1.0 / (w0 + w1 + w2);
-  const double o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
-  const double v = o0 * q0 + o1 * q1 + o2 * q2;
-  // d v = sum_k o_k dq_k - 2 sum_k o_k (q_k - v) de_k / e_k
-  const double qb0 = o0 * vbar, qb1 = o1 * vbar, qb2 = o2 * vbar;
-  const double eb0 = -2.0 * o0 * (q0 - v) / e0 * vbar;
-  const double eb1 = -2.0 * o1 * (q1 - v) / e1 * vbar;
-  const double eb2 = -2.0 * o2 * (q2 - v) / e2 * vbar;
-  const double tb0 = 2.0 * c1312 * t0 * eb0, sb0 = 0.5 * s0 * eb0;
-  const double tb1 = 2.0 * c1312 * t1 * eb1, sb1 = 0.5 * s1 * eb1;
-  const double tb2 = 2.0 * c1312 * t2 * eb2, sb2 = 0.5 * s2 * eb2;
-  ub[0] += 2.0 * c6 * qb0 + tb0 + sb0;
-  ub[1] += -7.0 * c6 * qb0 - c6 * qb1 - 2.0 * tb0 - 4.0 * sb0 + tb1 + sb1;
-  ub[2] += 11.0 * c6 * qb0 + 5.0 * c6 * qb1 + 2.0 * c6 * qb2 + tb0 + 3.0 * sb0 - 2.0 * tb1 + tb2 + 3.0 * sb2;
-  ub[3] += 2.0 * c6 * qb1 + 5.0 * c6 * qb2 + tb1 - sb1 - 2.0 * tb2 - 4.0 * sb2;
-  ub[4] += -c6 * qb2 + tb2 + sb2;
-  return v;
+// WENO5 value v(u0..u4) at the right face of the middle cell and its five
+// partial derivatives dv/du_k, with the weights of the forward (indicators
+// scaled by 12/13, product form; see weno5_cell_parts):
+//   dv = sum_k o_k dq_k - 2 sum_k o_k (q_k - v) de_k / e_k.
+// Everything before the two reciprocals 1/sum(w) and 1/(e0 e1 e2):
+struct Weno5VG {
+  double q[3];  // 6 q_k
+  double t[3], s[3], e[3], p[3];  // p = (e1 e2, e0 e2, e0 e1)
+  double w[3], ws, ee;            // weights, their sum, e0 e1 e2
+};
+
+__device__ __forceinline__ void weno5_vg_parts(const double u[5], double eps13, Weno5VG& a) {
+  const double k313 = 3.0 / 13.0;
+  a.q[0] = fma(2.0, u[0], fma(-7.0, u[1], 11.0 * u[2]));
+  a.q[1] = fma(2.0, u[3], fma(5.0, u[2], -u[1]));
+  a.q[2] = fma(5.0, u[3], fma(2.0, u[2], -u[4]));
+  a.t[0] = fma(-2.0, u[1], u[0] + u[2]);
+  a.s[0] = fma(3.0, u[2], fma(-4.0, u[1], u[0]));
+  a.t[1] = fma(-2.0, u[2], u[1] + u[3]);
+  a.s[1] = u[1] - u[3];
+  a.t[2] = fma(-2.0, u[3], u[2] + u[4]);
+  a.s[2] = fma(3.0, u[2], fma(-4.0, u[3], u[4]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) a.e[k] = fma(a.t[k], a.t[k], fma(k313 * a.s[k], a.s[k], eps13));
+  a.p[0] = a.e[1] * a.e[2];
+  a.p[1] = a.e[0] * a.e[2];
+  a.p[2] = a.e[0] * a.e[1];
+  a.w[0] = a.p[0] * a.p[0];
+  a.w[1] = 6.0 * (a.p[1] * a.p[1]);
+  a.w[2] = 3.0 * (a.p[2] * a.p[2]);
+  a.ws = a.w[0] + a.w[1] + a.w[2];
+  a.ee = a.e[0] * a.p[0];
 }
 
-// WENO5 value v(u0..u4) and its five partial derivatives dv/du_k in one
-// pass (same formulas as weno5_adj with vbar = 1; the three 1/e_k share one
-// division through the products e_i e_j already formed for the weights).
-__device__ __forceinline__ double weno5_value_grad(const double u[5], double eps, double gr[5]) {
-  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
-  const double q0 = (2.0 * u[0] - 7.0 * u[1] + 11.0 * u[2]) * c6;
-  const double q1 = (-u[1] + 5.0 * u[2] + 2.0 * u[3]) * c6;
-  const double q2 = (2.0 * u[2] + 5.0 * u[3] - u[4]) * c6;
-  const double t0 = u[0] - 2.0 * u[1] + u[2], s0 = u[0] - 4.0 * u[1] + 3.0 * u[2];
-  const double t1 = u[1] - 2.0 * u[2] + u[3], s1 = u[1] - u[3];
-  const double t2 = u[2] - 2.0 * u[3] + u[4], s2 = 3.0 * u[2] - 4.0 * u[3] + u[4];
-  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
-  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
-  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
-  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
-  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
-  const double iw = 1.0 / (w0 + w1 + w2);
-  const double o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
-  const double v = o0 * q0 + o1 * q1 + o2 * q2;
-  const double ie = 1.0 / (e0 * p12);  // 1 / (e0 e1 e2)
-  const double eb0 = -2.0 * o0 * (q0 - v) * (p12 * ie);
-  const double eb1 = -2.0 * o1 * (q1 - v) * (p02 * ie);
-  const double eb2 = -2.0 * o2 * (q2 - v) * (p01 * ie);
-  const double tb0 = 2.0 * c1312 * t0 * eb0, sb0 = 0.5 * s0 * eb0;
-  const double tb1 = 2.0 * c1312 * t1 * eb1, sb1 = 0.5 * s1 * eb1;
-  const double tb2 = 2.0 * c1312 * t2 * eb2, sb2 = 0.5 * s2 * eb2;
-  gr[0] = 2.0 * c6 * o0 + tb0 + sb0;
-  gr[1] = -7.0 * c6 * o0 - c6 * o1 - 2.0 * tb0 - 4.0 * sb0 + tb1 + sb1;
-  gr[2] = 11.0 * c6 * o0 + 5.0 * c6 * o1 + 2.0 * c6 * o2 + tb0 + 3.0 * sb0 - 2.0 * tb1 + tb2 + 3.0 * sb2;
-  gr[3] = 2.0 * c6 * o1 + 5.0 * c6 * o2 + tb1 - sb1 - 2.0 * tb2 - 4.0 * sb2;
-  gr[4] = -c6 * o2 + tb2 + sb2;
-  return v;
+// Value and gradient from the parts and the reciprocals iws = 1/ws, iee = 1/ee.
+__device__ __forceinline__ double weno5_vg_finish(const Weno5VG& a, double iws, double iee, double gr[5]) {
+  const double c6 = 1.0 / 6.0, k313 = 3.0 / 13.0;
+  double o[3], tb[3], sb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) o[k] = a.w[k] * iws;
+  const double v6 = fma(o[0], a.q[0], fma(o[1], a.q[1], o[2] * a.q[2]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // -2 o_k (q_k - v) / e_k, with q_k - v = (6 q_k - 6 v) / 6 and 1/e_k = p_k / ee
+    const double eb = (-2.0 * c6) * o[k] * (a.q[k] - v6) * (a.p[k] * iee);
+    tb[k] = 2.0 * a.t[k] * eb;
+    sb[k] = (2.0 * k313) * a.s[k] * eb;
+    o[k] *= c6;
+  }
+  gr[0] = 2.0 * o[0] + tb[0] + sb[0];
+  gr[1] = -7.0 * o[0] - o[1] - 2.0 * tb[0] - 4.0 * sb[0] + tb[1] + sb[1];
+  gr[2] = 11.0 * o[0] + 5.0 * o[1] + 2.0 * o[2] + tb[0] + 3.0 * sb[0] - 2.0 * tb[1] + tb[2] + 3.0 * sb[2];
+  gr[3] = 2.0 * o[1] + 5.0 * o[2] + tb[1] - sb[1] - 2.0 * tb[2] - 4.0 * sb[2];
+  gr[4] = -o[2] + tb[2] + sb[2];
+  return v6 * c6;
+}
+
+// Values and gradients of two stencils (the two states of a face); the four
+// reciprocals come from one division.
+__device__ __forceinline__ void weno5_value_grad2(const double uA[5], const double uB[5], double eps13, double& vA,
+                                                  double grA[5], double& vB, double grB[5]) {
+  Weno5VG A, B;
+  weno5_vg_parts(uA, eps13, A);
+  weno5_vg_parts(uB, eps13, B);
+  const double xa = A.ws * A.ee, xb = B.ws * B.ee;
+  const double Z = 1.0 / (xa * xb);
+  const double ra = xb * Z, rb = xa * Z;
+  vA = weno5_vg_finish(A, A.ee * ra, A.ws * ra, grA);
+  vB = weno5_vg_finish(B, B.ee * rb, B.ws * rb, grB);
 }
 
 // minmod face value um1 + minmod(um1 - um2, u0 - um1) / 2 with its adjoint.
@@ -373,10 +376,14 @@ __device__ __forceinline__ double minmod_left_adj(double um2, double um1, double
 // ------------------------------------------------------------- side adjoint
 // Recompute one face state (see side_state) and propagate the adjoints of
 // its outputs (U, F, lm, lp) to the primitives and Gamma.
+// ia = 1 / alpha of the face.  The speeds are those of side_state:
+// lambda_pm = alpha (c0 pm sq) / dsp - beta^d with Na = Gamma P + b^2,
+// dsp = hs - v^2 Na, hmn = hs - Na, Q = max(gamma^dd dsp - vd^2 hmn, 0),
+// sq = sqrt(Na (1 - v^2) Q), c0 = vd hmn.
 template <bool CURVED, int DIR>
 __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<double>& m, double gamma, double gfac,
-                                               const double Ub[8], const double Fb[8], double lmb, double lpb,
-                                               double prb[8], double& gammab) {
+                                               double ia, const double Ub[8], const double Fb[8], double lmb,
+                                               double lpb, double prb[8], double& gammab) {
   const double rho = pr[0], P = pr[4];
   const double v[3] = {pr[1], pr[2], pr[3]};
   const double B[3] = {pr[5], pr[6], pr[7]};
@@ -390,8 +397,8 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
   const double omv2 = 1.0 - v2;
-  const double iW = sqrt(omv2);
-  const double W = 1.0 / iW;
+  const double W = rsqrt(omv2);
+  const double iW = omv2 * W;
   const double ab0 = W * Bv;
   const double b2 = B2 * omv2 + Bv * Bv;
   double bl[3];
@@ -413,20 +420,23 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   const double alpha = CURVED ? m.alpha : 1.0;
   double vt[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) vt[i] = CURVED ? v[i] - m.beta[i] / alpha : v[i];
+  for (int i = 0; i < 3; ++i) vt[i] = CURVED ? v[i] - m.beta[i] * ia : v[i];
   const double vtd = vt[DIR];
   const double BdiW = Bc[DIR] * iW;
-  const double cs2 = gamma * P / rhoh;
-  const double va2 = b2 / hs;
-  const double a2 = cs2 + va2 - cs2 * va2;
   const double gdd = CURVED ? m.gup_dd : 1.0;
-  const double den = 1.0 - v2 * a2;
+  const double Na = gamma * P + b2;
+  const double dsp = hs - v2 * Na;
+  const double hmn = hs - Na;
   const double vd = v[DIR];
-  const double disc0 = omv2 * (gdd * den - vd * vd * (1.0 - a2));
-  const double disc = disc0 > 0.0 ? disc0 : 0.0;
-  const double sq = sqrt(a2 * disc);
-  const double ide = alpha / den;
-  const double c0 = vd * (1.0 - a2);
+  const double Q0 = gdd * dsp - vd * vd * hmn;
+  const double Q = Q0 > 0.0 ? Q0 : 0.0;
+  const double sq = sqrt(Na * omv2 * Q);
+  const double c0 = vd * hmn;
+  // 1/dsp and 1/sq from one division
+  const double sqs = sq > 0.0 ? sq : 1.0;
+  const double Y = 1.0 / (dsp * sqs);
+  const double idsp = sqs * Y, isq = dsp * Y;
+  const double id = alpha * idsp;
 
   // ---- reverse ----
   double rhob = 0, Pb = 0, vb[3] = {0, 0, 0}, Bb[3] = {0, 0, 0};
@@ -440,33 +450,30 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   taub = Ub[4];
   // speeds
   {
-    const double ideb = lpb * (c0 + sq) + lmb * (c0 - sq);
-    const double c0b = ide * (lpb + lmb);
-    const double sqb = ide * (lpb - lmb);
-    double denb = -ide / den * ideb;
-    double a2b = 0, vdb = 0, discb = 0;
-    vdb += (1.0 - a2) * c0b;
-    a2b -= vd * c0b;
+    const double idb = lpb * (c0 + sq) + lmb * (c0 - sq);
+    const double c0b = id * (lpb + lmb);
+    const double sqb = id * (lpb - lmb);
+    double dspb = -id * idsp * idb;
+    double Nab = 0, hmnb = 0, vdb = 0;
     if (sq > 0.0) {
-      const double tb = sqb * 0.5 / sq;
-      a2b += disc * tb;
-      discb += a2 * tb;
+      const double Xb = 0.5 * sqb * isq;
+      Nab += omv2 * Q * Xb;
+      omv2b += Na * Q * Xb;
+      const double Qb = Na * omv2 * Xb;
+      if (Q0 > 0.0) {
+        dspb += gdd * Qb;
+        vdb -= 2.0 * vd * hmn * Qb;
+        hmnb -= vd * vd * Qb;
+      }
     }
-    if (disc0 > 0.0) {
-      omv2b += (gdd * den - vd * vd * (1.0 - a2)) * discb;
-      denb += omv2 * gdd * discb;
-      vdb -= 2.0 * vd * (1.0 - a2) * omv2 * discb;
-      a2b += vd * vd * omv2 * discb;
-    }
-    v2b -= a2 * denb;
-    a2b -= v2 * denb;
-    const double cs2b = (1.0 - va2) * a2b;
-    const double va2b = (1.0 - cs2) * a2b;
-    gammab += P / rhoh * cs2b;
-    Pb += gamma / rhoh * cs2b;
-    rhohb -= cs2 / rhoh * cs2b;
-    b2b += va2b / hs;
-    hsb -= va2 / hs * va2b;
+    vdb += hmn * c0b;
+    hmnb += vd * c0b;
+    hsb += hmnb + dspb;
+    Nab -= hmnb + v2 * dspb;
+    v2b -= Na * dspb;
+    gammab += P * Nab;
+    Pb += gamma * Nab;
+    b2b += Nab;
     vb[DIR] += vdb;
   }
   // fluxes
@@ -544,7 +551,7 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   Wb += Bv * ab0b;
   Bvb += W * ab0b;
   iWb -= W * W * Wb;
-  omv2b += iWb * 0.5 / iW;
+  omv2b += iWb * 0.5 * W;
   v2b -= omv2b;
   // v2 = v.Gv, Bv = B.Gv, B2 = B.GB; vl = Gv, Bl = GB (G symmetric)
 #pragma unroll
@@ -583,20 +590,21 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
   double pL[8], pR[8];
   const double eps = p.weno_eps;
   if (RECON == GRMHD_WENO5) {
+    const double eps13 = eps * (12.0 / 13.0);
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
       double u[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) u[k] = __ldg(prim + q * g.ncell + c + (k - 3) * stride);
-      double gr[5];
+      double grL[5], grR[5];
       const double uL[5] = {u[0], u[1], u[2], u[3], u[4]};
-      pL[q] = weno5_value_grad(uL, eps, gr);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) gsm[((2 * q) * 5 + k) * blockDim.x + threadIdx.x] = gr[k];
       const double uR[5] = {u[5], u[4], u[3], u[2], u[1]};
-      pR[q] = weno5_value_grad(uR, eps, gr);
+      weno5_value_grad2(uL, uR, eps13, pL[q], grL, pR[q], grR);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) gsm[((2 * q + 1) * 5 + k) * blockDim.x + threadIdx.x] = gr[k];
+      for (int k = 0; k < 5; ++k) {
+        gsm[((2 * q) * 5 + k) * blockDim.x + threadIdx.x] = grL[k];
+        gsm[((2 * q + 1) * 5 + k) * blockDim.x + threadIdx.x] = grR[k];
+      }
     }
   } else {
     reconstruct_face<double, RECON>(prim, g.ncell, c, stride, eps, pL, pR);
@@ -612,8 +620,10 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
 #pragma unroll
     for (int q = 0; q < 8; ++q) pR[q] = __ldg(prim + q * g.ncell + c);
   Side<double> L, R;
-  side_state<double, CURVED, DIR>(pL, m, p.gamma, p.gfac, L);
-  side_state<double, CURVED, DIR>(pR, m, p.gamma, p.gfac, R);
+  const double ia = CURVED ? 1.0 / m.alpha : 1.0;
+  side_state<double, CURVED, DIR, true>(pL, m, p.gamma, p.gfac, L, ia);
+  side_state<double, CURVED, DIR, true>(pR, m, p.gamma, p.gfac, R, ia);
+  finish_speeds<double, CURVED, DIR>(m, L, R);
   // HLLE reverse
   double FLb[8], FRb[8], ULb[8], URb[8], lmLb = 0, lpLb = 0, lmRb = 0, lpRb = 0;
   const double xm = fmin(0.0, fmin(L.lm, R.lm));
@@ -641,8 +651,8 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
     if (xm < 0.0) { if (L.lm <= R.lm) lmLb += xmb; else lmRb += xmb; }
   }
   double pLb[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pRb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  side_state_adj<CURVED, DIR>(pL, m, p.gamma, p.gfac, ULb, FLb, lmLb, lpLb, pLb, gammab);
-  side_state_adj<CURVED, DIR>(pR, m, p.gamma, p.gfac, URb, FRb, lmRb, lpRb, pRb, gammab);
+  side_state_adj<CURVED, DIR>(pL, m, p.gamma, p.gfac, ia, ULb, FLb, lmLb, lpLb, pLb, gammab);
+  side_state_adj<CURVED, DIR>(pR, m, p.gamma, p.gfac, ia, URb, FRb, lmRb, lpRb, pRb, gammab);
   // reconstruction reverse (stencil values reloaded), scatter to the stencil
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {

@@ -52,7 +52,7 @@ __device__ __forceinline__ T ld_prim(const SrcCacheT<PT, GT>& s, long long i) { 
 template <class T, int RECON, class S>
 __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, long long c, long long stride, T eps,
                                                  T pL[8], T pR[8]) {
-  if (RECON == GRMHD_WENO5 && sizeof(T) == 8) {
+  if constexpr (RECON == GRMHD_WENO5 && sizeof(T) == 8) {
     // FP64: the four normalisations of two variables share one division
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
@@ -74,21 +74,21 @@ __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, 
       pL[q + 1] = (T)(n[2] * (d[3] * x23));
       pR[q + 1] = (T)(n[3] * (d[2] * x23));
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const long long a = q * ncell + c;
-    if (RECON == GRMHD_WENO5) {
-      const T um3 = ld_prim<T>(src, a - 3 * stride), um2 = ld_prim<T>(src, a - 2 * stride);
-      const T um1 = ld_prim<T>(src, a - stride), u0 = ld_prim<T>(src, a);
-      const T up1 = ld_prim<T>(src, a + stride), up2 = ld_prim<T>(src, a + 2 * stride);
-      weno5_pair<T>(um3, um2, um1, u0, up1, up2, eps, pL[q], pR[q]);
-    } else {
-      const T um2 = ld_prim<T>(src, a - 2 * stride), um1 = ld_prim<T>(src, a - stride);
-      const T u0 = ld_prim<T>(src, a), up1 = ld_prim<T>(src, a + stride);
-      pL[q] = um1 + T(0.5) * minmod<T>(um1 - um2, u0 - um1);
-      pR[q] = u0 - T(0.5) * minmod<T>(u0 - um1, up1 - u0);
+    for (int q = 0; q < 8; ++q) {
+      const long long a = q * ncell + c;
+      if constexpr (RECON == GRMHD_WENO5) {
+        const T um3 = ld_prim<T>(src, a - 3 * stride), um2 = ld_prim<T>(src, a - 2 * stride);
+        const T um1 = ld_prim<T>(src, a - stride), u0 = ld_prim<T>(src, a);
+        const T up1 = ld_prim<T>(src, a + stride), up2 = ld_prim<T>(src, a + 2 * stride);
+        weno5_pair<T>(um3, um2, um1, u0, up1, up2, eps, pL[q], pR[q]);
+      } else {
+        const T um2 = ld_prim<T>(src, a - 2 * stride), um1 = ld_prim<T>(src, a - stride);
+        const T u0 = ld_prim<T>(src, a), up1 = ld_prim<T>(src, a + stride);
+        pL[q] = um1 + T(0.5) * minmod<T>(um1 - um2, u0 - um1);
+        pR[q] = u0 - T(0.5) * minmod<T>(u0 - um1, up1 - u0);
+      }
     }
   }
 }
