@@ -45,7 +45,10 @@
 //      by the primitive state of the cell it was reconstructed from;
 //   R12 recovery failures (Sec. 2.3 lists them): no root, NaN, rho < rho_atm
 //      or v >= 1 -> atmosphere (rho_atm, v = 0, p_atm, B kept); a root with
-//      P <= 0 but valid rho and v -> pressure floor P = p_atm.
+//      P <= 0 but valid rho and v -> pressure floor P = p_atm.  "No root"
+//      includes the case where the energy residual has no sign change
+//      inside v < 1: a bracket that closes only against the v = 1 boundary
+//      is not a root (its side of the boundary is decided by round-off).
 
 #include <algorithm>
 #include <cmath>
@@ -704,25 +707,36 @@ int con2prim_cell(const S U[8], const double adm[10], const Par<S>& p, S out[8])
     return 1;
   };
   if (!(val(in.D) > 0.0) || !(val(in.tau) + val(in.D) > 0.0)) return atmosphere();
-  // Value-level bisection bracket: sign(z) = +1 where v^2 >= 1 or f > 0.
+  // Value-level bisection bracket: sign(z) = +1 where v^2 >= 1 or f > 0;
+  // lo_energy records whether the current lower end is positive through the
+  // energy residual itself (v^2 < 1, f > 0) rather than through v^2 >= 1.
   C2P<double> iv;
   iv.D = val(in.D); iv.tau = val(in.tau); iv.S2 = val(in.S2); iv.B2 = val(in.B2);
   iv.BS = val(in.BS); iv.gamma = val(in.gamma);
-  auto positive = [&](double z) {
+  auto sign_class = [&](double z) {  // 0: f <= 0 inside v < 1; 1: f > 0 inside; 2: v^2 >= 1
     const double v2 = c2p_v2(iv, z);
-    if (!(v2 < 1.0)) return true;
-    return c2p_f(iv, z) > 0.0;
+    if (!(v2 < 1.0)) return 2;
+    return c2p_f(iv, z) > 0.0 ? 1 : 0;
   };
   double zlo = 0.0;
+  bool lo_energy = false;
   double zhi = 2.0 * iv.gamma * (iv.tau + iv.D) + iv.B2 + 1e-300;
   int guard = 0;
-  while (positive(zhi) && guard < 200) { zlo = zhi; zhi *= 2.0; ++guard; }
+  for (int c = sign_class(zhi); c != 0 && guard < 200; c = sign_class(zhi)) {
+    zlo = zhi;
+    lo_energy = c == 1;
+    zhi *= 2.0;
+    ++guard;
+  }
   if (guard >= 200) return atmosphere();
   for (int it = 0; it < 400; ++it) {
     const double zm = 0.5 * (zlo + zhi);
-    if (positive(zm)) zlo = zm; else zhi = zm;
+    const int c = sign_class(zm);
+    if (c != 0) { zlo = zm; lo_energy = c == 1; } else { zhi = zm; }
     if (zhi - zlo <= 1e-15 * zhi) break;
   }
+  // reading R12: no sign change of f inside v < 1 means no root
+  if (!lo_energy) return atmosphere();
   const double zv = 0.5 * (zlo + zhi);
   // One Newton polish, carrying the derivative of the root with respect to
   // the inputs (implicit function theorem) when S is a dual number.

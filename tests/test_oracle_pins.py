@@ -349,6 +349,30 @@ def test_con2prim_unphysical_input_sets_atmosphere():
     assert st == 1 and out[0] == 1e-8 and np.all(out[1:4] == 0) and out[5] == 0.1
 
 
+def test_con2prim_no_sign_change_inside_v_below_one_is_no_root():
+    """A conserved state (met at a colliding-stream front of Balsara 4) whose energy residual is
+    negative wherever v < 1: a brute-force scan of z finds no sign change, so there is no root and
+    the recovery must impose the atmosphere, not a floor at W ~ 1e7 on the v = 1 boundary."""
+    gamma = 5.0 / 3.0
+    gm1g = (gamma - 1.0) / gamma
+    U = np.array([25.343577, -723.422237, -54.294802, -54.294802, 749.075107, 10.0, -8.205542, -8.205542])
+    D, tau, S, B = U[0], U[4], U[1:4], U[5:8]
+    S2, B2, BS = S @ S, B @ B, B @ S
+    z = np.geomspace(1e-3, 1e6, 200001)
+    zb = z + B2
+    v2 = (S2 + BS * BS * (2 * z + B2) / z ** 2) / zb ** 2
+    inside = v2 < 1.0
+    iw2 = 1.0 - v2[inside]
+    zi = z[inside]
+    f = tau + D - zi - B2 + 0.5 * B2 * iw2 + 0.5 * BS * BS / zi ** 2 + gm1g * (zi * iw2 - D * np.sqrt(iw2))
+    assert inside.any() and np.all(f < 0.0)
+    out, st = O.con2prim_point(U, O.make_params(gamma=gamma))
+    assert st == 1 and np.all(out[1:4] == 0.0)
+    # the mirrored state (S_x -> -S_x, B_y, B_z -> -B_y, -B_z) is classified the same way
+    Um = U * np.array([1, -1, 1, 1, 1, 1, -1, -1])
+    assert O.con2prim_point(Um, O.make_params(gamma=gamma))[1] == 1
+
+
 # --------------------------------------------------------------- the RHS --
 def _block(n, ng=3, L=1.0):
     return O.Grid((n, n, n), ng, (L / n,) * 3)
@@ -584,8 +608,6 @@ def test_balsara1_peak_lorentz_factor_printed_in_paper():
     par = O.make_params(gamma=t["gamma"], recon=O.REC_MINMOD, bc=O.BC_COPY)
     x = -0.5 + (np.arange(n + 6) - 3 + 0.5) / n
     prim = np.zeros((8,) + g.shape)
-    for q, key in ((0, "rho"),):
-        pass
     L = x < 0
     for side, mask in (("left", L), ("right", ~L)):
         s = t[side]
