@@ -325,6 +325,78 @@ def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
     }
 
 
+# ------------------------------------------------------------ shock tube --
+def shocktube_bench(G, test=1, n=1600, transverse=8):
+    """Balsara shock tube (Sec. 4.1) as the paper runs it: minmod + HLLE +
+    RK4, CFL 0.8, copy boundaries, n cells on [-0.5, 0.5] along x and 8 x 8
+    transverse cells, evolved to t_ref.  A 1600 x 8 x 8 block is too small to
+    fill the GPU, so the 12 launches of a step are timed both as plain
+    launches and replayed from one CUDA graph; the peak Lorentz factor at
+    t_ref is reported against the paper's printed value."""
+    import torch
+    blk, prim_h, gamma, t_ref = I.shocktube(test, n, 0, transverse)
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    p = G.Params(gamma=gamma, recon=G.MINMOD, bc=G.BC_COPY)
+    dt = 0.8 / n
+    nsteps = int(round(t_ref / dt))
+    ncells = blk.n[0] * blk.n[1] * blk.n[2]
+
+    def setup():
+        prim = torch.from_numpy(prim_h).cuda()
+        cons = G.prim2con(g, p, prim)
+        ws = G.workspace(g, G.RK4)
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        return prim, cons, ws, nfail
+
+    out = {"workload": f"Balsara {test}, {n}x{transverse}x{transverse}, minmod+HLLE, RK4, CFL 0.8, copy BC, "
+                       f"{nsteps} steps to t_ref = {t_ref}"}
+    # plain launches
+    prim, cons, ws, nfail = setup()
+    for _ in range(3):
+        G.rk_step(g, p, G.RK4, dt, cons, prim, None, None, ws, nfail)
+    prim, cons, ws, nfail = setup()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(nsteps):
+        G.rk_step(g, p, G.RK4, dt, cons, prim, None, None, ws, nfail)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    v = prim[1:4, blk.ng:-blk.ng, blk.ng:-blk.ng, blk.ng:-blk.ng]
+    wmax = float((1.0 / torch.sqrt(1.0 - (v * v).sum(dim=0))).max())
+    out["plain"] = {"value": ncells * nsteps / (ms * 1e-3), "unit": "zone-cycles/s", "ms_total": ms,
+                    "failed_cells": int(nfail.item())}
+    # one step captured in a CUDA graph, replayed nsteps times from the initial state
+    prim, cons, ws, nfail = setup()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        G.rk_step(g, p, G.RK4, dt, cons, prim, None, None, ws, nfail)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        G.rk_step(g, p, G.RK4, dt, cons, prim, None, None, ws, nfail)
+    prim0, cons0, _, _ = setup()
+    prim.copy_(prim0)
+    cons.copy_(cons0)
+    nfail.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(nsteps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    msg = e0.elapsed_time(e1)
+    v = prim[1:4, blk.ng:-blk.ng, blk.ng:-blk.ng, blk.ng:-blk.ng]
+    wmax_g = float((1.0 / torch.sqrt(1.0 - (v * v).sum(dim=0))).max())
+    out["graph"] = {"value": ncells * nsteps / (msg * 1e-3), "unit": "zone-cycles/s", "ms_total": msg,
+                    "failed_cells": int(nfail.item()), "launches_per_step": 12}
+    out["peak_lorentz_factor"] = {"plain": wmax, "graph": wmax_g, "paper_printed": 1.458}
+    return out
+
+
 # ------------------------------------------------------------ 256^3 block --
 def large_block_bench(G, steps=3, warmup=1, n=256):
     """256^3 + 3 ghosts on the Schwarzschild background, planar Riemann jump
@@ -400,6 +472,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-shocktube", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="RHS tile shape (default: autotuned)")
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-dirs", type=int, default=50)
@@ -566,6 +639,9 @@ def main():
     large = None
     if not args.no_large:
         large = large_block_bench(G)
+    tube = None
+    if not args.no_shocktube:
+        tube = shocktube_bench(G)
 
     if rank != 0:
         return
@@ -588,6 +664,7 @@ def main():
         "batched": batched,
         "adjoint": adjoint,
         "block_256": large,
+        "shocktube": tube,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

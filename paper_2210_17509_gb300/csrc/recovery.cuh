@@ -56,6 +56,57 @@ __device__ __forceinline__ double c2p_energy_of_z(const C2PIn& in, double z, dou
   return in.tau + in.D - z - in.B2 + 0.5 * in.B2 * iw2 + 0.5 * in.BS2 / (z * z) + P;
 }
 
+// Bracketed bisection of the energy residual in z, with W(z) from the S^2
+// equation; z below the v = 1 boundary counts as "too small".  A root needs
+// a sign change of the residual inside v < 1: if the lower end of the final
+// bracket is "too small" only through v >= 1, the bracket has closed on the
+// v = 1 boundary and there is no root (which side of v = 1 the midpoint
+// lands on is round-off).  Returns 1 (root found) or 2 (no root); z, W on
+// exit.
+static __device__ int c2p_bisect(const C2PIn& in, const DevParams& p, double& z, double& W) {
+  const double gm1g = p.gm1g;
+  double zlo = 0.0, zhi = 2.0 * (in.tau + in.D) / gm1g + in.B2 + 1e-300;
+  // 0: residual <= 0 inside v < 1; 1: residual > 0 inside v < 1; 2: v >= 1
+  auto sign_class = [&](double zz) {
+    const double v2 = c2p_v2_of_z(in, zz);
+    if (!(v2 < 1.0)) return 2;
+    return c2p_energy_of_z(in, zz, v2, gm1g) > 0.0 ? 1 : 0;
+  };
+  bool lo_energy = false;
+  int k = 0;
+  for (int c = sign_class(zhi); c != 0 && k < 200; c = sign_class(zhi)) {
+    zlo = zhi;
+    lo_energy = c == 1;
+    zhi *= 2.0;
+    ++k;
+  }
+  if (k >= 200 || !isfinite(zhi)) return 2;
+  for (int it = 0; it < 400 && zhi - zlo > 1e-15 * zhi; ++it) {
+    const double zm = 0.5 * (zlo + zhi);
+    const int c = sign_class(zm);
+    if (c != 0) {
+      zlo = zm;
+      lo_energy = c == 1;
+    } else {
+      zhi = zm;
+    }
+  }
+  if (!lo_energy) return 2;
+  z = 0.5 * (zlo + zhi);
+  const double v2 = c2p_v2_of_z(in, z);
+  if (!(v2 < 1.0)) return 2;
+  W = 1.0 / sqrt(1.0 - v2);
+  return 1;
+}
+
+// A Newton root is accepted only if it is physical: W >= 1, rho = D / W >=
+// rho_atm and P = (Gamma - 1)/Gamma (z / W^2 - D / W) > 0, i.e. z > D W.
+// Otherwise (the iteration can settle on a spurious root from a poor guess,
+// e.g. next to an atmosphere cell) the bracketed bisection decides.
+__device__ __forceinline__ bool c2p_root_physical(const C2PIn& in, const DevParams& p, double z, double W) {
+  return W >= 1.0 && isfinite(W) && z > in.D * W && in.D >= p.rho_atm * W;
+}
+
 // Returns 0 (Newton converged), 1 (bisection), 2 (failed); z, W on exit.
 // tol_first applies to the first Newton step only: after an FP32 predictor
 // that converged to 1e-6, one FP64 step leaves an error of order 1e-12 times
@@ -91,27 +142,8 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
       if (conv) { ok = true; break; }
     }
   }
-  if (ok) return 0;
-  // Fallback: bracketed bisection of the energy residual in z, with W(z)
-  // from the S^2 equation; z below the v = 1 boundary counts as "too small".
-  double zlo = 0.0, zhi = 2.0 * (tau + D) / gm1g + B2 + 1e-300;
-  auto too_small = [&](double zz) {
-    const double v2 = c2p_v2_of_z(in, zz);
-    if (!(v2 < 1.0)) return true;
-    return c2p_energy_of_z(in, zz, v2, gm1g) > 0.0;
-  };
-  int k = 0;
-  while (too_small(zhi) && k < 200) { zlo = zhi; zhi *= 2.0; ++k; }
-  if (k >= 200 || !isfinite(zhi)) return 2;
-  for (int it = 0; it < 400 && zhi - zlo > 1e-15 * zhi; ++it) {
-    const double zm = 0.5 * (zlo + zhi);
-    if (too_small(zm)) zlo = zm; else zhi = zm;
-  }
-  z = 0.5 * (zlo + zhi);
-  const double v2 = c2p_v2_of_z(in, z);
-  if (!(v2 < 1.0)) return 2;
-  W = 1.0 / sqrt(1.0 - v2);
-  return 1;
+  if (ok && c2p_root_physical(in, p, z, W)) return 0;
+  return c2p_bisect(in, p, z, W);
 }
 
 // FP32 Newton predictor for the mixed path: iterates the same 2D system in

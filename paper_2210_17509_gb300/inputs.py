@@ -23,6 +23,10 @@ Workloads (shapes follow the paper's test and benchmark setups, Secs. 4-5):
     1% seeded multiplicative perturbation of rho and P.
   * ``amr_boxes``: 512 boxes, edges from {8, 16, 24, 32, 48, 64} per axis,
     refinement level 0/1/2 round-robin (dx = 1, 1/2, 1/4), smooth_flat data.
+  * ``shocktube``: the 1D MHD shock tubes of Sec. 4.1 (Balsara tests 1-5,
+    the paper's table of left / right states) along x, y or z, Minkowski,
+    with a few transverse cells; the table gives eps, laid out here as the
+    primitive pressure P = (Gamma - 1) rho eps of the Gamma-law EOS.
 """
 from __future__ import annotations
 
@@ -230,3 +234,56 @@ def amr_boxes(nbox=512, seed=2, gamma=GAMMA, ng=NG, max_boxes=None):
 def cfl_dt(blk: Block, cfl: float) -> float:
     """dt = CFL * min dx (the paper's CFL definition, Sec. 4.1)."""
     return cfl * min(blk.dx)
+
+
+# 1D shock tubes of Sec. 4.1 (the paper's table of Balsara tests 1-5): per
+# test the normal field B^x, Gamma, the end time t_ref, and the left / right
+# states (rho, eps, (v^x, v^y, v^z), (B^y, B^z)); left is x < 0 on [-0.5, 0.5].
+BALSARA = {
+    1: dict(Bx=0.5, gamma=2.0, t_ref=0.4,
+            left=(1.0, 1.0, (0.0, 0.0, 0.0), (1.0, 0.0)),
+            right=(0.125, 0.8, (0.0, 0.0, 0.0), (-1.0, 0.0))),
+    2: dict(Bx=5.0, gamma=5.0 / 3.0, t_ref=0.4,
+            left=(1.0, 45.0, (0.0, 0.0, 0.0), (6.0, 6.0)),
+            right=(1.0, 1.5, (0.0, 0.0, 0.0), (0.7, 0.7))),
+    3: dict(Bx=10.0, gamma=5.0 / 3.0, t_ref=0.4,
+            left=(1.0, 1500.0, (0.0, 0.0, 0.0), (7.0, 7.0)),
+            right=(1.0, 0.15, (0.0, 0.0, 0.0), (0.7, 0.7))),
+    4: dict(Bx=10.0, gamma=5.0 / 3.0, t_ref=0.4,
+            left=(1.0, 0.15, (0.999, 0.0, 0.0), (7.0, 7.0)),
+            right=(1.0, 0.15, (-0.999, 0.0, 0.0), (-7.0, -7.0))),
+    5: dict(Bx=2.0, gamma=5.0 / 3.0, t_ref=0.55,
+            left=(1.08, 1.3194, (0.4, 0.3, 0.2), (0.3, 0.3)),
+            right=(1.0, 1.5, (-0.45, -0.2, 0.2), (-0.7, 0.5))),
+}
+
+
+def shocktube(test: int, n: int = 1600, axis: int = 0, transverse: int = 8, ng: int = NG):
+    """Balsara shock tube ``test`` along ``axis``: n cells of width 1/n on
+    [-0.5, 0.5] along the axis, ``transverse`` cells of the same width across
+    it, Minkowski.  The table's x components (v, B) lie along ``axis`` and
+    its y, z components along the next two axes in cyclic order, so the
+    three orientations are relabellings of one another.  Ghosts are filled
+    by copying the nearest interior cell (the tests' boundary, Sec. 4.1).
+    Returns (Block, prim, gamma, t_ref)."""
+    t = BALSARA[test]
+    nv = [transverse, transverse, transverse]
+    nv[axis] = n
+    origin = [0.0, 0.0, 0.0]
+    origin[axis] = -0.5
+    blk = Block(tuple(nv), ng, (1.0 / n,) * 3, tuple(origin))
+    coords = blk.centres()
+    left = coords[axis] < 0.0
+    prim = np.zeros((8,) + blk.shape)
+    for state, mask in ((t["left"], left), (t["right"], ~left)):
+        rho, eps, v, byz = state
+        comp_v = (v[0], v[1], v[2])
+        comp_b = (t["Bx"], byz[0], byz[1])
+        prim[0][mask] = rho
+        prim[4][mask] = (t["gamma"] - 1.0) * rho * eps
+        for k in range(3):
+            d = (axis + k) % 3
+            prim[1 + d][mask] = comp_v[k]
+            prim[5 + d][mask] = comp_b[k]
+    return blk, prim, t["gamma"], t["t_ref"]
+

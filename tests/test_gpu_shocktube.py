@@ -1,0 +1,176 @@
+"""Balsara shock tubes (Sec. 4.1) on the CUDA path through the C ABI:
+minmod + HLLE + RK4 at CFL 0.8 with copy boundaries, as in the paper.
+
+* parity with the FP64 oracle, element by element, over the first 25 steps
+  of all five tests (1e-12 normwise per field; 1e-11 for the W = 22.4
+  streams of Balsara 4), with the same recovery failures (the two cells of
+  the initial jump in Balsara 3 and 4, where neither side finds a root);
+* the three orientations (tube along x, y, z) give the same profiles, and
+  every transverse column equals the first bit for bit (Sec. 4.1 runs all
+  three).  The face fluxes of the three orientations are computed by the
+  same relabelled routine, but the pointwise recovery and prim->cons sum
+  vector components in x, y, z order, so the orientations agree to
+  round-off (1e-13 normwise), not bitwise;
+* before the waves reach the ends, the totals change only by the physical
+  fluxes of the two constant end states (conservation, Eq. 11);
+* Balsara 1 at the paper's 1600 points reaches the printed peak Lorentz
+  factor ~1.458 at t_ref, and Balsara 4 (W ~ 22.4 streams) runs to t_ref
+  without a recovery failure, both matching the oracle run at 400 points.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2210_17509_gb300 import inputs as I
+from tests.helpers import FP64_TOL, interior, normwise
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CFL = 0.8
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2210_17509_gb300 import build
+    build.build()
+    from paper_2210_17509_gb300 import grmhd
+    return grmhd
+
+
+def gpu_evolve(G, test, n, axis, transverse, nsteps):
+    """nsteps RK4 steps of the shock tube on the GPU; returns (blk, cons, prim, nfail)."""
+    blk, prim_h, gamma, _ = I.shocktube(test, n, axis, transverse)
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    p = G.Params(gamma=gamma, recon=G.MINMOD, bc=G.BC_COPY)
+    prim = torch.from_numpy(prim_h).cuda()
+    cons = G.prim2con(g, p, prim)
+    ws = G.workspace(g, G.RK4)
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dt = CFL / n
+    for _ in range(nsteps):
+        G.rk_step(g, p, G.RK4, dt, cons, prim, None, None, ws, nfail)
+    torch.cuda.synchronize()
+    return blk, cons.cpu().numpy(), prim.cpu().numpy(), int(nfail.item())
+
+
+def oracle_evolve(G, test, n, nsteps):
+    """The same tube along x on the oracle, one transverse cell."""
+    blk, prim, gamma, _ = I.shocktube(test, n, 0, 1)
+    gp = G.Params(gamma=gamma, recon=G.MINMOD, bc=G.BC_COPY)
+    og = O.Grid(blk.n, blk.ng, blk.dx)
+    op = O.make_params(gamma=gamma, recon=O.REC_MINMOD, bc=O.BC_COPY, rho_atm=gp.rho_atm, p_atm=gp.p_atm,
+                       weno_eps=gp.weno_eps)
+    cons = O.prim2con(og, gamma, prim)
+    nf_total = 0
+    dt = CFL / n
+    for _ in range(nsteps):
+        cons, prim, nf = O.rk_step(og, op, O.RK4, dt, cons, prim)
+        nf_total += nf
+    return cons, prim, nf_total
+
+
+def profile(arr, blk, axis):
+    """Interior of a tube field [var, z, y, x] as [var, transverse, transverse, n] with the tube
+    axis last and the vector components relabelled to the x-tube frame."""
+    a = interior(arr, blk.ng)
+    # spatial axes of the array are (z, y, x) = array dims (1, 2, 3); tube axis d -> array dim 3 - d
+    order = {0: (1, 2, 3), 1: (3, 1, 2), 2: (2, 3, 1)}[axis]
+    a = np.transpose(a, (0,) + order)
+    comp = [0, 1 + axis, 1 + (axis + 1) % 3, 1 + (axis + 2) % 3, 4,
+            5 + axis, 5 + (axis + 1) % 3, 5 + (axis + 2) % 3]
+    return a[comp]
+
+
+@pytest.mark.parametrize("test", [1, 2, 3, 4, 5])
+def test_shocktube_parity_with_oracle(G, test):
+    n, nsteps = 200, 25
+    blk, cons, prim, nf = gpu_evolve(G, test, n, 0, 4, nsteps)
+    ocons, oprim, onf = oracle_evolve(G, test, n, nsteps)
+    # the same recovery failures in every one of the 16 columns as in the oracle's one
+    # (Balsara 3 and 4 set the atmosphere in the two cells of the initial jump)
+    assert nf == 16 * onf, (nf, onf)
+    oc = interior(ocons, blk.ng)[:, 0, 0, :]
+    op_ = interior(oprim, blk.ng)[:, 0, 0, :]
+    gc = interior(cons, blk.ng)
+    gpr = interior(prim, blk.ng)
+    errc = max(normwise(gc[:, k, j, :], oc).max() for k in range(gc.shape[1]) for j in range(gc.shape[2]))
+    errp = max(normwise(gpr[:, k, j, :], op_, floor=1e-3).max() for k in range(gc.shape[1])
+               for j in range(gc.shape[2]))
+    print(f"Balsara {test}: {nsteps} steps, cons {errc:.2e}, prim {errp:.2e}, failures {nf // 16} per column")
+    # Balsara 4's streams have W = 22.4 (|v| = 0.999): forming W from 1 - v^2 = 2e-3 amplifies the
+    # round-off difference of the two formulations (3+1 here, covariant in the oracle) by about
+    # W^2 = 500 per evaluation, so its bound is 1e-11 instead of 1e-12.
+    tol = 1e-11 if test == 4 else FP64_TOL
+    assert errc <= tol and errp <= tol, (errc, errp)
+
+
+def test_shocktube_orientations_agree(G):
+    """Balsara 5 (all components non-zero) along x, y and z."""
+    n, nsteps, tr = 128, 40, 4
+    prof = []
+    for axis in range(3):
+        blk, cons, prim, nf = gpu_evolve(G, 5, n, axis, tr, nsteps)
+        assert nf == 0
+        pc = profile(cons, blk, axis)
+        # every transverse column equals the first one
+        assert np.array_equal(pc, np.broadcast_to(pc[:, :1, :1, :], pc.shape)), axis
+        prof.append(pc[:, 0, 0, :])
+    for k in (1, 2):
+        assert normwise(prof[k], prof[0]).max() <= 1e-13, k
+
+
+def test_shocktube_totals_change_by_end_fluxes_only(G):
+    """Balsara 1, t = 0.1 (waves still inside): sum_i U_i dx changes by -t (F(U_R) - F(U_L))."""
+    n, nsteps, tr = 400, 50, 2
+    blk, prim0, gamma, _ = I.shocktube(1, n, 0, tr)
+    st = I.BALSARA[1]
+    _, cons, prim, nf = gpu_evolve(G, 1, n, 0, tr, nsteps)
+    assert nf == 0
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    p = G.Params(gamma=gamma, recon=G.MINMOD, bc=G.BC_COPY)
+    cons0 = G.prim2con(g, p, torch.from_numpy(prim0).cuda()).cpu().numpy()
+    left = interior(prim0, blk.ng)[:, 0, 0, 0]
+    right = interior(prim0, blk.ng)[:, 0, 0, -1]
+    FL = O.point(left, gamma)[1][0]
+    FR = O.point(right, gamma)[1][0]
+    t = nsteps * CFL / n
+    dx = 1.0 / n
+    s0 = interior(cons0, blk.ng)[:, 0, 0, :].sum(axis=-1) * dx
+    s1 = interior(cons, blk.ng)[:, 0, 0, :].sum(axis=-1) * dx
+    expect = s0 - t * (FR - FL)
+    scale = np.abs(interior(cons, blk.ng)[:, 0, 0, :]).sum(axis=-1) * dx + 1e-300
+    assert np.all(np.abs(s1 - expect) <= 1e-12 * np.maximum(scale, 1.0)), (s1 - expect, st)
+
+
+def test_balsara1_paper_resolution_peak_lorentz_factor(G):
+    """1600 points, t_ref = 0.4: the paper prints a peak W of about 1.458 (Sec. 4.1)."""
+    n = 1600
+    _, _, gamma, t_ref = I.shocktube(1, 16, 0, 1)
+    nsteps = int(round(t_ref / (CFL / n)))
+    blk, cons, prim, nf = gpu_evolve(G, 1, n, 0, 8, nsteps)
+    assert nf == 0
+    v = interior(prim, blk.ng)[1:4]
+    W = 1.0 / np.sqrt(1.0 - (v ** 2).sum(axis=0))
+    assert abs(W.max() - 1.458) < 5e-3, W.max()
+
+
+@pytest.mark.parametrize("test", [1, 4])
+def test_shocktube_to_t_ref_matches_oracle(G, test):
+    """Full run to t_ref at 400 points against the oracle.  Balsara 4 collides two W = 22.4 streams
+    with |v| = 0.999: apart from the two cells of the initial jump in the first step, where neither
+    side finds a physical root, the recovery must not fail anywhere."""
+    n = 400
+    _, _, gamma, t_ref = I.shocktube(test, 16, 0, 1)
+    nsteps = int(round(t_ref / (CFL / n)))
+    blk, cons, prim, nf = gpu_evolve(G, test, n, 0, 2, nsteps)
+    ocons, oprim, onf = oracle_evolve(G, test, n, nsteps)
+    assert nf == 4 * onf, (nf, onf)
+    assert onf <= 2
+    gc = interior(cons, blk.ng)[:, 0, 0, :]
+    oc = interior(ocons, blk.ng)[:, 0, 0, :]
+    assert np.all(np.isfinite(gc))
+    err = normwise(gc, oc).max()
+    print(f"Balsara {test}: {nsteps} RK4 steps, max normwise cons error vs oracle {err:.3e}")
+    assert err <= 1e-10, err
