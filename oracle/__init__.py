@@ -81,6 +81,11 @@ def _load():
         lib.oracle_con2prim_point.restype = I
         lib.oracle_loss_jvp.argtypes = [P, I, P, pp, I, Dd, I, P, P, Dd, P, P, P, P]
         lib.oracle_loss_jvp.restype = I
+        lib.oracle_restrict.argtypes = [P, I, P, P, P, I, P, P, P, I]
+        lib.oracle_prolongate.argtypes = [P, I, P, P, P, I, P, P, P, I, I]
+        lib.oracle_reflux.argtypes = [P, I, P, pp, P, P, P, I, P, P, P, P, Dd, P]
+        lib.oracle_amr2_step.argtypes = [P, I, P, pp, I, Dd, P, P, P, I, P, P, P, P, P, P]
+        lib.oracle_amr2_step.restype = I
         _lib = lib
     return _lib
 
@@ -257,3 +262,64 @@ def loss_jvp(grid: Grid, params: OParams, scheme: int, dt: float, nsteps: int, p
                                     _ptr(prim0), _ptr(dprim0), float(dgamma), _ptr(metric), _ptr(kij),
                                     ctypes.byref(L), ctypes.byref(dL))
     return L.value, dL.value, nfail
+
+
+# ------------------------------------------- two-level AMR transfer (R14-R17) --
+def _lo(lo):
+    return (ctypes.c_int * 3)(*[int(v) for v in lo])
+
+
+def restrict(coarse_grid: Grid, coarse, fine_grid: Grid, fine, lo):
+    """Covered coarse cells := mean of their 8 fine children (R14); returns a new coarse array."""
+    coarse = np.array(coarse, dtype=np.float64, copy=True)
+    fine = _f64(fine)
+    _load().oracle_restrict(coarse_grid._n, coarse_grid.ng, coarse_grid._dx, _ptr(coarse), fine_grid._n,
+                            fine_grid.ng, fine_grid._dx, _ptr(fine), _lo(lo), coarse.shape[0])
+    return coarse
+
+
+def prolongate(coarse_grid: Grid, coarse, fine_grid: Grid, fine, lo, ghosts_only=True):
+    """Fine points (ghosts only, or all) from the coarse parents, limited-linear (R15)."""
+    coarse = _f64(coarse)
+    fine = np.array(fine, dtype=np.float64, copy=True)
+    _load().oracle_prolongate(coarse_grid._n, coarse_grid.ng, coarse_grid._dx, _ptr(coarse), fine_grid._n,
+                              fine_grid.ng, fine_grid._dx, _ptr(fine), _lo(lo), fine.shape[0], int(ghosts_only))
+    return fine
+
+
+def reflux(coarse_grid: Grid, params: OParams, coarse_prim, fine_grid: Grid, fine_prim, lo, scale=1.0, out=None,
+           coarse_metric=None, fine_metric=None):
+    """Adds scale * (coarse RHS change from flux restriction, R16) to out (zeros if None)."""
+    cp = _f64(coarse_prim)
+    fp = _f64(fine_prim)
+    out = np.zeros_like(cp) if out is None else np.array(out, dtype=np.float64, copy=True)
+    _load().oracle_reflux(coarse_grid._n, coarse_grid.ng, coarse_grid._dx, ctypes.byref(params), _ptr(cp),
+                          _ptr(_f64(coarse_metric)), fine_grid._n, fine_grid.ng, fine_grid._dx, _ptr(fp),
+                          _ptr(_f64(fine_metric)), _lo(lo), float(scale), _ptr(out))
+    return out
+
+
+def amr2_step(coarse_grid: Grid, params: OParams, scheme: int, dt: float, ccons, cprim, fine_grids, fcons, fprim,
+              los, coarse_metric=None, fine_metrics=None):
+    """One composite step (R17) of a coarse block and its fine blocks; returns
+    (ccons, cprim, [fcons], [fprim], nfail)."""
+    nf = len(fine_grids)
+    ccons = np.array(ccons, dtype=np.float64, copy=True)
+    cprim = np.array(cprim, dtype=np.float64, copy=True)
+    fcons = [np.array(a, dtype=np.float64, copy=True) for a in fcons]
+    fprim = [np.array(a, dtype=np.float64, copy=True) for a in fprim]
+    fmet = [None] * nf if fine_metrics is None else [_f64(m) for m in fine_metrics]
+    fn = (ctypes.c_int * (3 * nf))(*[v for g in fine_grids for v in g.n])
+    fdx = (ctypes.c_double * (3 * nf))(*[v for g in fine_grids for v in g.dx])
+    lo = (ctypes.c_int * (3 * nf))(*[int(v) for l in los for v in l])
+    P = ctypes.c_void_p
+    pc = (P * nf)(*[a.ctypes.data for a in fcons])
+    pp_ = (P * nf)(*[a.ctypes.data for a in fprim])
+    pm = (P * nf)(*[None if m is None else m.ctypes.data for m in fmet])
+    for g in fine_grids:
+        assert g.ng == coarse_grid.ng
+    nfail = _load().oracle_amr2_step(coarse_grid._n, coarse_grid.ng, coarse_grid._dx, ctypes.byref(params),
+                                     int(scheme), float(dt), _ptr(ccons), _ptr(cprim), _ptr(_f64(coarse_metric)),
+                                     nf, fn, fdx, pc, pp_, pm, lo)
+    return ccons, cprim, fcons, fprim, nfail
+

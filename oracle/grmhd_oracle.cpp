@@ -49,6 +49,27 @@
 //      includes the case where the energy residual has no sign change
 //      inside v < 1: a bracket that closes only against the v = 1 boundary
 //      is not a root (its side of the boundary is decided by round-off).
+//   Two-level block AMR without subcycling (Sec. 3: refined grids halve the
+//   spacing, are properly nested, share one global time step; ghost zones
+//   of a refined grid are filled by prolongation from the next coarser
+//   level, covered coarse cells are reset by restriction, fine fluxes are
+//   restricted onto the coarse grid):
+//   R14 restriction acts on the conserved variables: a covered coarse cell
+//      becomes the mean of its 8 children (equal coordinate volumes, so the
+//      mean conserves the integral).
+//   R15 prolongation acts on the primitives (the ghost zones hold
+//      primitives, R9): a fine point takes its coarse parent's value plus,
+//      per axis, the parent's minmod-limited slope (R2) times the child's
+//      offset of -1/4 or +1/4 coarse cell; the 8 children average to the
+//      parent.  The paper names high-order operators without an order.
+//   R16 flux restriction: on every coarse face of the coarse-fine
+//      interface, the uncovered coarse cell's RHS uses the mean of the 4
+//      fine face fluxes instead of the coarse face flux (one global dt, so no
+//      time integration of fluxes, "refluxing", is needed).
+//   R17 composite stage: RHS of every block -> flux restriction onto the
+//      coarse RHS -> stage update -> restriction of the fine U -> recovery on
+//      every block -> coarse ghosts by its boundary condition, fine ghosts by
+//      prolongation from the coarse primitives.
 
 #include <algorithm>
 #include <cmath>
@@ -879,6 +900,158 @@ int rk_step_block(const Grid& G, const Par<S>& p, int scheme, double dt, S* cons
   return nfail;
 }
 
+// --------------------------------------------- two-level AMR (R14-R17) --
+// A fine block at placement lo: its interior cell i (0-based, ghosts i < 0
+// or i >= n) lies in the coarse interior cell lo + floor(i / 2) along each
+// axis, and its spacing is half the coarse one.
+inline int floor_half(int i) { return i >= 0 ? i / 2 : -((1 - i) / 2); }
+
+// R14: covered coarse cells of `coarse` := mean of their 8 fine children.
+template <class S>
+void restrict_block(const Grid& C, S* coarse, const Grid& F, const S* fine, const int lo[3], int nvar) {
+  for (int K = 0; K < F.n[2] / 2; ++K)
+    for (int J = 0; J < F.n[1] / 2; ++J)
+      for (int I = 0; I < F.n[0] / 2; ++I)
+        for (int q = 0; q < nvar; ++q) {
+          S sum = S(0.0);
+          for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+              for (int a = 0; a < 2; ++a)
+                sum = sum + fine[q * F.ncell + F.at(F.ng + 2 * I + a, F.ng + 2 * J + b, F.ng + 2 * K + c)];
+          coarse[q * C.ncell + C.at(C.ng + lo[0] + I, C.ng + lo[1] + J, C.ng + lo[2] + K)] = sum / 8.0;
+        }
+}
+
+// R15: fine points (all, or the ghosts only) from the coarse parents.
+template <class S>
+void prolongate_block(const Grid& C, const S* coarse, const Grid& F, S* fine, const int lo[3], int nvar,
+                      bool ghosts_only) {
+  for (int k = -F.ng; k < F.n[2] + F.ng; ++k)
+    for (int j = -F.ng; j < F.n[1] + F.ng; ++j)
+      for (int i = -F.ng; i < F.n[0] + F.ng; ++i) {
+        const bool inside = i >= 0 && i < F.n[0] && j >= 0 && j < F.n[1] && k >= 0 && k < F.n[2];
+        if (ghosts_only && inside) continue;
+        const int fi[3] = {i, j, k};
+        int P[3];
+        double off[3];
+        for (int d = 0; d < 3; ++d) {
+          P[d] = C.ng + lo[d] + floor_half(fi[d]);
+          off[d] = (fi[d] - 2 * floor_half(fi[d]) == 0) ? -0.25 : 0.25;
+        }
+        for (int q = 0; q < nvar; ++q) {
+          const S* u = coarse + q * C.ncell;
+          const S u0 = u[C.at(P[0], P[1], P[2])];
+          S val = u0;
+          for (int d = 0; d < 3; ++d) {
+            int m[3] = {P[0], P[1], P[2]}, pl[3] = {P[0], P[1], P[2]};
+            m[d] -= 1;
+            pl[d] += 1;
+            const S slope = minmod(u0 - u[C.at(m[0], m[1], m[2])], u[C.at(pl[0], pl[1], pl[2])] - u0);
+            val = val + off[d] * slope;
+          }
+          fine[q * F.ncell + F.at(F.ng + i, F.ng + j, F.ng + k)] = val;
+        }
+      }
+}
+
+// R16: adds scale * (change of the coarse RHS) to `out` for the uncovered
+// coarse cells next to the fine block, the coarse interface flux being
+// replaced by the mean of its 4 fine face fluxes.
+template <class S>
+void reflux_block(const Grid& C, const Par<S>& p, const S* cprim, const double* cmetric, const Grid& F,
+                  const S* fprim, const double* fmetric, const int lo[3], double scale, S* out) {
+  const int nc[3] = {F.n[0] / 2, F.n[1] / 2, F.n[2] / 2};
+  for (int d = 0; d < 3; ++d) {
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    for (int side = 0; side < 2; ++side)
+      for (int B = 0; B < nc[b]; ++B)
+        for (int A = 0; A < nc[a]; ++A) {
+          int Ic[3];
+          Ic[d] = lo[d] + (side ? nc[d] : 0);
+          Ic[a] = lo[a] + A;
+          Ic[b] = lo[b] + B;
+          S Fc[8];
+          face_flux(C, p, cprim, cmetric, d, C.ng + Ic[0], C.ng + Ic[1], C.ng + Ic[2], Fc);
+          S Ff[8];
+          for (int q = 0; q < 8; ++q) Ff[q] = S(0.0);
+          for (int ib = 0; ib < 2; ++ib)
+            for (int ia = 0; ia < 2; ++ia) {
+              int If[3];
+              If[d] = side ? F.n[d] : 0;
+              If[a] = 2 * A + ia;
+              If[b] = 2 * B + ib;
+              S Fx[8];
+              face_flux(F, p, fprim, fmetric, d, F.ng + If[0], F.ng + If[1], F.ng + If[2], Fx);
+              for (int q = 0; q < 8; ++q) Ff[q] = Ff[q] + Fx[q];
+            }
+          int Icell[3] = {Ic[0], Ic[1], Ic[2]};
+          if (!side) Icell[d] -= 1;                  // the face is this cell's upper face
+          const double sign = side ? 1.0 : -1.0;     // ... or its lower face
+          const long cc = C.at(C.ng + Icell[0], C.ng + Icell[1], C.ng + Icell[2]);
+          for (int q = 0; q < 8; ++q) out[q * C.ncell + cc] = out[q * C.ncell + cc] + scale * sign * (0.25 * Ff[q] - Fc[q]) / C.dx[d];
+        }
+  }
+}
+
+// R17: one composite SSP-RK2 / SSP-RK3 / RK4 step of a coarse block and nf
+// fine blocks.  Returns the number of failed recoveries.
+template <class S>
+int amr2_step(const Grid& C, const Par<S>& p, int scheme, double dt, S* ccons, S* cprim, const double* cmetric,
+              int nf, const Grid* Fg, S* const* fcons, S* const* fprim, const double* const* fmetric,
+              const int* lo) {
+  const int nb = nf + 1;
+  std::vector<const Grid*> G(nb);
+  std::vector<S*> U(nb), P(nb);
+  std::vector<const double*> M(nb);
+  G[0] = &C; U[0] = ccons; P[0] = cprim; M[0] = cmetric;
+  for (int f = 0; f < nf; ++f) { G[f + 1] = &Fg[f]; U[f + 1] = fcons[f]; P[f + 1] = fprim[f]; M[f + 1] = fmetric[f]; }
+  std::vector<std::vector<S>> U0(nb), L(nb), acc(nb);
+  for (int b = 0; b < nb; ++b) {
+    const long n8 = 8 * G[b]->ncell;
+    U0[b].assign(U[b], U[b] + n8);
+    L[b].assign(n8, S(0.0));
+    acc[b].assign(n8, S(0.0));
+  }
+  int nfail = 0;
+  const int nstage = scheme == RK2 ? 2 : (scheme == RK3 ? 3 : 4);
+  for (int s = 0; s < nstage; ++s) {
+    for (int b = 0; b < nb; ++b) rhs_block(*G[b], p, P[b], M[b], nullptr, L[b].data());
+    for (int f = 0; f < nf; ++f) reflux_block(C, p, cprim, cmetric, Fg[f], P[f + 1], M[f + 1], lo + 3 * f, 1.0, L[0].data());
+    for (int b = 0; b < nb; ++b) {
+      const Grid& g = *G[b];
+      for (int k = g.ng; k < g.ng + g.n[2]; ++k)
+        for (int j = g.ng; j < g.ng + g.n[1]; ++j)
+          for (int i = g.ng; i < g.ng + g.n[0]; ++i)
+            for (int q = 0; q < 8; ++q) {
+              const long x = q * g.ncell + g.at(i, j, k);
+              S* u = U[b];
+              const S* u0 = U0[b].data();
+              const S l = L[b][x];
+              if (scheme == RK2) {
+                u[x] = s == 0 ? u0[x] + dt * l : 0.5 * u0[x] + 0.5 * (u[x] + dt * l);
+              } else if (scheme == RK3) {
+                if (s == 0) u[x] = u0[x] + dt * l;
+                else if (s == 1) u[x] = 0.75 * u0[x] + 0.25 * (u[x] + dt * l);
+                else u[x] = (1.0 / 3.0) * u0[x] + (2.0 / 3.0) * (u[x] + dt * l);
+              } else {
+                const double cst[3] = {0.5, 0.5, 1.0}, wst[3] = {1.0, 2.0, 2.0};
+                if (s < 3) {
+                  acc[b][x] = acc[b][x] + wst[s] * l;
+                  u[x] = u0[x] + (cst[s] * dt) * l;
+                } else {
+                  u[x] = u0[x] + (dt / 6.0) * (acc[b][x] + l);
+                }
+              }
+            }
+    }
+    for (int f = 0; f < nf; ++f) restrict_block(C, ccons, Fg[f], fcons[f], lo + 3 * f, 8);
+    for (int b = 0; b < nb; ++b) nfail += con2prim_block(*G[b], p, U[b], M[b], P[b], (int8_t*)nullptr);
+    fill_ghosts_block(C, p.bc, 8, cprim);
+    for (int f = 0; f < nf; ++f) prolongate_block(C, (const S*)cprim, Fg[f], fprim[f], lo + 3 * f, 8, true);
+  }
+  return nfail;
+}
+
 }  // namespace orc
 
 // ======================================================================
@@ -1058,6 +1231,40 @@ int oracle_loss_jvp(const int* n3, int ng, const double* dx3, const OParams* q, 
   *L = acc.v;
   *dL = acc.d[0];
   return nfail;
+}
+
+// Two-level AMR transfer (R14-R17).  Fine grids carry placements lo[3].
+void oracle_restrict(const int* cn, int cng, const double* cdx, double* coarse, const int* fn, int fng,
+                     const double* fdx, const double* fine, const int* lo, int nvar) {
+  Grid C; C.init(cn, cng, cdx);
+  Grid F; F.init(fn, fng, fdx);
+  restrict_block<double>(C, coarse, F, fine, lo, nvar);
+}
+
+void oracle_prolongate(const int* cn, int cng, const double* cdx, const double* coarse, const int* fn, int fng,
+                       const double* fdx, double* fine, const int* lo, int nvar, int ghosts_only) {
+  Grid C; C.init(cn, cng, cdx);
+  Grid F; F.init(fn, fng, fdx);
+  prolongate_block<double>(C, coarse, F, fine, lo, nvar, ghosts_only != 0);
+}
+
+void oracle_reflux(const int* cn, int cng, const double* cdx, const OParams* q, const double* cprim,
+                   const double* cmetric, const int* fn, int fng, const double* fdx, const double* fprim,
+                   const double* fmetric, const int* lo, double scale, double* out) {
+  Grid C; C.init(cn, cng, cdx);
+  Grid F; F.init(fn, fng, fdx);
+  reflux_block<double>(C, to_par(q), cprim, cmetric, F, fprim, fmetric, lo, scale, out);
+}
+
+// fine blocks: nf of them; fn, fdx, lo are 3 * nf arrays; fcons, fprim,
+// fmetric arrays of nf pointers (fmetric entries may be NULL).
+int oracle_amr2_step(const int* cn, int ng, const double* cdx, const OParams* q, int scheme, double dt,
+                     double* ccons, double* cprim, const double* cmetric, int nf, const int* fn, const double* fdx,
+                     double* const* fcons, double* const* fprim, const double* const* fmetric, const int* lo) {
+  Grid C; C.init(cn, ng, cdx);
+  std::vector<Grid> F(nf);
+  for (int f = 0; f < nf; ++f) F[f].init(fn + 3 * f, ng, fdx + 3 * f);
+  return amr2_step<double>(C, to_par(q), scheme, dt, ccons, cprim, cmetric, nf, F.data(), fcons, fprim, fmetric, lo);
 }
 
 }  // extern "C"
