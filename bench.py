@@ -397,6 +397,89 @@ def shocktube_bench(G, test=1, n=1600, transverse=8):
     return out
 
 
+# ------------------------------------------------------------- two-level AMR --
+def amr_bench(G, steps=5, warmup=2, nc=96, nfine=48):
+    """Two-level block AMR without subcycling (Sec. 3): a 96^3 periodic flat
+    coarse block with four 48^3 fine blocks (each covering 24^3 coarse cells,
+    apart from one another), WENO5+HLLE, SSP-RK3 at CFL 0.25 of the fine
+    spacing.  The composite step (fused RHS+update per block, flux
+    restriction, restriction, recovery, ghost fill, prolongation) is timed
+    against plain steps of the same five blocks, and the three transfer
+    kernels are timed on their own."""
+    import torch
+    ng = 3
+    cb = I.Block((nc,) * 3, ng, (1.0 / nc,) * 3, (0.0,) * 3)
+    pc_h = I.smooth_prims(cb, 31)
+    half = nfine // 2
+    los = [(8, 8, 8), (8 + half + 24, 8, 8), (8, 8 + half + 24, 8 + half + 24), (8 + half + 24, 8 + half + 24, 8)]
+    C = G.Grid(cb.n, ng, cb.dx)
+    Fs = [G.Grid((nfine,) * 3, ng, (0.5 / nc,) * 3) for _ in los]
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
+    pc = torch.from_numpy(pc_h).cuda()
+    G.fill_ghosts(C, G.BC_PERIODIC, pc)
+    pfs = []
+    for F, lo in zip(Fs, los):
+        pf = torch.zeros((8,) + F.shape, dtype=torch.float64, device="cuda")
+        G.prolongate(C, pc, F, pf, lo, ghosts_only=False)
+        pfs.append(pf)
+    uc = G.prim2con(C, p, pc)
+    ufs = [G.prim2con(F, p, pf) for F, pf in zip(Fs, pfs)]
+    for F, uf, lo in zip(Fs, ufs, los):
+        G.restrict(C, uc, F, uf, lo)
+    ws = G.amr2_workspace(C, Fs, G.RK3)
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dt = 0.25 * Fs[0].dx[0]
+    ncells = nc ** 3 + len(Fs) * nfine ** 3
+
+    def timed(fn, n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def composite():
+        G.amr2_step(C, p, G.RK3, dt, uc, pc, Fs, ufs, pfs, los, ws=ws, nfail=nfail)
+
+    for _ in range(warmup):
+        composite()
+    ms = timed(composite, steps)
+    # the same five blocks stepped independently (no transfer)
+    wsc = G.workspace(C, G.RK3, cached=False)
+    wsf = [G.workspace(F, G.RK3, cached=False) for F in Fs]
+
+    def plain():
+        G.rk_step(C, p, G.RK3, dt, uc, pc, None, None, wsc, nfail)
+        for F, uf, pf, w in zip(Fs, ufs, pfs, wsf):
+            G.rk_step(F, p, G.RK3, dt, uf, pf, None, None, w, nfail)
+
+    ms_plain = timed(plain, steps)
+    out = torch.zeros_like(uc)
+    t_restrict = timed(lambda: [G.restrict(C, uc, F, uf, lo) for F, uf, lo in zip(Fs, ufs, los)], 20)
+    t_prolong = timed(lambda: [G.prolongate(C, pc, F, pf, lo) for F, pf, lo in zip(Fs, pfs, los)], 20)
+    t_reflux = timed(lambda: [G.reflux(C, p, pc, F, pf, lo, out) for F, pf, lo in zip(Fs, pfs, los)], 20)
+    # algorithmic bytes of one restriction pass: 8 fields x (8 fine reads + 1 coarse write) per covered cell
+    cov = len(Fs) * half ** 3
+    restrict_bytes = 8 * cov * 9 * 8
+    hbm, _ = __import__("paper_2210_17509_gb300.roofline", fromlist=["hbm_peak_gbs"]).hbm_peak_gbs()
+    return {
+        "workload": f"{nc}^3 periodic flat coarse block + {len(Fs)} fine blocks of {nfine}^3 (each over {half}^3 "
+                    f"coarse cells), WENO5+HLLE, SSP-RK3, dt = 0.25 dx_fine",
+        "cells": ncells,
+        "composite": {"value": ncells / (ms * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms,
+                      "failed_cells": int(nfail.item())},
+        "plain_blocks_ms_per_step": ms_plain,
+        "transfer_overhead": ms / ms_plain - 1.0,
+        "transfer_ms_per_pass": {"restrict": t_restrict, "prolongate_ghosts": t_prolong, "reflux": t_reflux},
+        "restrict_gbs": restrict_bytes / (t_restrict * 1e-3) / 1e9,
+        "restrict_hbm_frac": restrict_bytes / (t_restrict * 1e-3) / 1e9 / hbm,
+    }
+
+
 # ------------------------------------------------------------ 256^3 block --
 def large_block_bench(G, steps=3, warmup=1, n=256):
     """256^3 + 3 ghosts on the Schwarzschild background, planar Riemann jump
@@ -473,6 +556,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-shocktube", action="store_true")
+    ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="RHS tile shape (default: autotuned)")
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-dirs", type=int, default=50)
@@ -642,6 +726,9 @@ def main():
     tube = None
     if not args.no_shocktube:
         tube = shocktube_bench(G)
+    amr = None
+    if not args.no_amr:
+        amr = amr_bench(G)
 
     if rank != 0:
         return
@@ -665,6 +752,7 @@ def main():
         "adjoint": adjoint,
         "block_256": large,
         "shocktube": tube,
+        "amr2": amr,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

@@ -331,6 +331,73 @@ int grmhd_rk_step_static(const grmhd_grid* grid, const grmhd_params* params, int
                          double* cons, double* prim, const double* metric, const double* kij,
                          int32_t* nfail, void* stream);
 
+/* ----------------------------------------------------------------------
+ * Two-level block AMR without subcycling (Sec. 3: each refined grid halves
+ * the spacing of the next coarser one and is properly nested in it; ghost
+ * zones of a refined grid are filled by prolongation from the coarser level;
+ * coarse cells overlaid by a refined grid are reset by restriction; fine
+ * fluxes are restricted onto the coarse grid; one global time step, so no
+ * refluxing in time).
+ *
+ * Placement: a fine grid at lo[3] (coarse interior cell indices) has
+ * fine.n even per axis, fine.ng == coarse.ng >= 2 and fine.dx = coarse.dx/2
+ * (relative 1e-12); its interior cell i lies in the coarse interior cell
+ * lo + floor(i/2) per axis, and it covers coarse cells lo .. lo + fine.n/2 - 1,
+ * which must lie inside the coarse interior (lo >= 0, lo + fine.n/2 <= coarse.n).
+ * All fields are SoA [var][z][y][x] with ghosts, as everywhere else.
+ * ---------------------------------------------------------------------- */
+
+/* Restriction of conserved variables: every covered coarse interior cell of
+ * coarse_field := mean of its 8 fine children in fine_field (the volume
+ * mean, which conserves the integral).  nvar fields; nothing else changes. */
+int grmhd_restrict(const grmhd_grid* coarse, double* coarse_field, const grmhd_grid* fine,
+                   const double* fine_field, const int32_t lo[3], int32_t nvar, void* stream);
+
+/* Prolongation of primitives: every fine point (ghosts_only != 0: the ghost
+ * points only) := its coarse parent's value plus, per axis, the parent's
+ * minmod-limited slope times the child's offset (-1/4 or +1/4 coarse cell);
+ * the 8 children of a parent average to the parent.  coarse_field must have
+ * its ghosts filled (the stencil of a fine ghost reaches coarse ghosts). */
+int grmhd_prolongate(const grmhd_grid* coarse, const double* coarse_field, const grmhd_grid* fine,
+                     double* fine_field, const int32_t lo[3], int32_t nvar, int32_t ghosts_only,
+                     void* stream);
+
+/* Flux restriction at the coarse-fine interface: for every coarse face on
+ * the fine grid's boundary, the uncovered coarse cell beside it should see
+ * the mean of the 4 fine face fluxes instead of the coarse face flux.  Adds
+ * scale * (that change of its RHS) to coarse_out (8 fields), and, if acc is
+ * not NULL, acc_scale * (the same change) to acc.  Face fluxes are those of
+ * grmhd_rhs (params.recon, HLLE), computed from coarse_prim / fine_prim
+ * (ghosts filled) and the metrics (NULL: Minkowski; both or neither). */
+int grmhd_reflux(const grmhd_grid* coarse, const grmhd_params* params, const double* coarse_prim,
+                 const double* coarse_metric, const grmhd_grid* fine, const double* fine_prim,
+                 const double* fine_metric, const int32_t lo[3], double scale, double* coarse_out,
+                 double acc_scale, double* acc, void* stream);
+
+/* Device workspace (bytes) of grmhd_amr2_step; 0 if a grid is invalid. */
+size_t grmhd_amr2_workspace_bytes(const grmhd_grid* coarse, int32_t nfine, const grmhd_grid* fine,
+                                  int32_t scheme);
+
+/* One composite step (FP64) of a coarse block and nfine fine blocks at the
+ * next level: per RK stage, the fused RHS and stage update of every block,
+ * flux restriction onto the coarse update, restriction of each fine U onto
+ * its covered coarse cells, recovery on every block, then the coarse ghosts
+ * by params.bc and every fine block's ghosts by prolongation.
+ *   fine[nfine], fine_cons/fine_prim/fine_metric[nfine] (host arrays of
+ *   device pointers; fine_metric entries NULL when coarse_metric is NULL),
+ *   lo[3 * nfine] placements.  Fine grids must lie inside the coarse
+ *   interior with a gap of at least one coarse cell to its boundary and to
+ *   each other (the fine ghosts then come from the coarse level only).
+ *   On entry the primitives of every block are consistent with its U and
+ *   their ghosts filled (fine ghosts by grmhd_prolongate).
+ *   ws: ws_bytes >= grmhd_amr2_workspace_bytes, 256-byte aligned; nfail as
+ *   for grmhd_rk_step. */
+int grmhd_amr2_step(const grmhd_grid* coarse, const grmhd_params* params, int32_t scheme, double dt,
+                    double* coarse_cons, double* coarse_prim, const double* coarse_metric, int32_t nfine,
+                    const grmhd_grid* fine, double* const* fine_cons, double* const* fine_prim,
+                    const double* const* fine_metric, const int32_t* lo, void* ws, size_t ws_bytes,
+                    int32_t* nfail, void* stream);
+
 /* Human-readable name of a return code (static storage). */
 const char* grmhd_error_string(int code);
 

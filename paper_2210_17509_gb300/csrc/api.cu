@@ -45,63 +45,10 @@ using namespace grmhd;
 
 namespace {
 
-bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
-
-int check_grid(const grmhd_grid* g, int min_ng) {
-  if (!g) return GRMHD_ERR_ARG;
-  if (g->ng < min_ng || g->ng > 16) return GRMHD_ERR_ARG;
-  long long cells = 1;
-  for (int d = 0; d < 3; ++d) {
-    if (g->n[d] < 1 || g->n[d] > (1 << 20)) return GRMHD_ERR_ARG;
-    if (!(g->dx[d] > 0.0) || !std::isfinite(g->dx[d])) return GRMHD_ERR_ARG;
-    cells *= (long long)(g->n[d] + 2 * g->ng);
-    if (cells > (1LL << 40)) return GRMHD_ERR_ARG;
-  }
-  return GRMHD_OK;
-}
-
-int check_params(const grmhd_params* p) {
-  if (!p) return GRMHD_ERR_ARG;
-  if (!(p->gamma > 1.0 && p->gamma <= 3.0)) return GRMHD_ERR_ARG;
-  if (p->recon != GRMHD_MINMOD && p->recon != GRMHD_WENO5) return GRMHD_ERR_ARG;
-  if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
-  if (p->precision != GRMHD_FP64 && p->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
-  if (p->nr_maxit < 1 || p->nr_maxit > 1000) return GRMHD_ERR_ARG;
-  if (!(p->nr_tol > 0.0 && p->nr_tol < 1.0)) return GRMHD_ERR_ARG;
-  if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
-  if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
-  if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
-  if ((p->flags & ~GRMHD_REUSE_GEOMETRY) != 0) return GRMHD_ERR_ARG;
-  return GRMHD_OK;
-}
-
-// Ghost width the stencils need: WENO5 reads 3 cells, minmod 2, the metric
-// derivatives 2.
-int min_ghosts(const grmhd_params* p, const double* metric) {
-  int m = (p->recon == GRMHD_WENO5) ? 3 : 2;
-  if (metric && m < 2) m = 2;
-  return m;
-}
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
-
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 cudaError_t launch_rhs(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
                        const double* kij, const StageEpilogue& ep, cudaStream_t s) {
   if (p.precision == GRMHD_MIXED) return launch_rhs_mixed(g, p, prim, metric, kij, ep, s);
   return launch_rhs_fp64(g, p, prim, metric, kij, ep, s);
-}
-
-StageEpilogue no_epilogue() {
-  StageEpilogue e;
-  e.rhs = nullptr;
-  e.u = nullptr;
-  e.u0 = nullptr;
-  e.acc_in = nullptr;
-  e.acc_out = nullptr;
-  e.c0 = e.c1 = e.cr = e.ca = e.wa = e.wr = 0.0;
-  return e;
 }
 
 }  // namespace
@@ -274,26 +221,8 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     if (fast_mixed && launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
   }
 
-  // Stage coefficients: u <- c0 u0 + c1 u + cr L (+ ca acc); acc <- wa acc + wr L.
-  struct Stage { double c0, c1, cr, ca, wa, wr; bool acc_in, acc_out; };
-  Stage st[4];
-  int ns = 0;
-  if (scheme == GRMHD_RK2) {
-    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
-    st[1] = {0.5, 0.5, 0.5 * dt, 0, 0, 0, false, false};
-    ns = 2;
-  } else if (scheme == GRMHD_RK3) {
-    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
-    st[1] = {0.75, 0.25, 0.25 * dt, 0, 0, 0, false, false};
-    st[2] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, 0, 0, 0, false, false};
-    ns = 3;
-  } else {
-    st[0] = {1.0, 0.0, 0.5 * dt, 0, 0, 1.0, false, true};
-    st[1] = {1.0, 0.0, 0.5 * dt, 0, 1.0, 2.0, true, true};
-    st[2] = {1.0, 0.0, dt, 0, 1.0, 2.0, true, true};
-    st[3] = {1.0, 0.0, dt / 6.0, dt / 6.0, 0, 0, true, false};
-    ns = 4;
-  }
+  RkStage st[4];
+  const int ns = rk_stages(scheme, dt, st);
   for (int k = 0; k < ns; ++k) {
     StageEpilogue ep = no_epilogue();
     ep.u = cons;

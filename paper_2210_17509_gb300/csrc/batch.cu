@@ -56,7 +56,6 @@ static_assert(sizeof(BatchHead) <= kHeadBytes, "batch header too large");
 
 const int kShape[4][3] = {{8, 8, 4}, {16, 4, 4}, {32, 4, 2}, {4, 8, 8}};
 
-bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 }  // namespace
 

@@ -1,6 +1,7 @@
 // Internal host/device declarations of libgrmhd (not part of the C ABI).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -81,5 +82,95 @@ cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const 
                                     const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s);
 constexpr int kGeomCacheComps = 53;
 constexpr int kMetricCacheComps = 7;
+
+// ---------------------------------------------------------- host helpers
+inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+inline int check_grid(const grmhd_grid* g, int min_ng) {
+  if (!g) return GRMHD_ERR_ARG;
+  if (g->ng < min_ng || g->ng > 16) return GRMHD_ERR_ARG;
+  long long cells = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 1 || g->n[d] > (1 << 20)) return GRMHD_ERR_ARG;
+    if (!(g->dx[d] > 0.0) || !std::isfinite(g->dx[d])) return GRMHD_ERR_ARG;
+    cells *= (long long)(g->n[d] + 2 * g->ng);
+    if (cells > (1LL << 40)) return GRMHD_ERR_ARG;
+  }
+  return GRMHD_OK;
+}
+
+inline int check_params(const grmhd_params* p) {
+  if (!p) return GRMHD_ERR_ARG;
+  if (!(p->gamma > 1.0 && p->gamma <= 3.0)) return GRMHD_ERR_ARG;
+  if (p->recon != GRMHD_MINMOD && p->recon != GRMHD_WENO5) return GRMHD_ERR_ARG;
+  if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
+  if (p->precision != GRMHD_FP64 && p->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
+  if (p->nr_maxit < 1 || p->nr_maxit > 1000) return GRMHD_ERR_ARG;
+  if (!(p->nr_tol > 0.0 && p->nr_tol < 1.0)) return GRMHD_ERR_ARG;
+  if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
+  if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
+  if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
+  if ((p->flags & ~GRMHD_REUSE_GEOMETRY) != 0) return GRMHD_ERR_ARG;
+  return GRMHD_OK;
+}
+
+// Ghost width the stencils need: WENO5 reads 3 cells, minmod 2, the metric
+// derivatives 2.
+inline int min_ghosts(const grmhd_params* p, const double* metric) {
+  int m = (p->recon == GRMHD_WENO5) ? 3 : 2;
+  if (metric && m < 2) m = 2;
+  return m;
+}
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+inline StageEpilogue no_epilogue() {
+  StageEpilogue e;
+  e.rhs = nullptr;
+  e.u = nullptr;
+  e.u0 = nullptr;
+  e.acc_in = nullptr;
+  e.acc_out = nullptr;
+  e.c0 = e.c1 = e.cr = e.ca = e.wa = e.wr = 0.0;
+  return e;
+}
+
+// Stage coefficients of the integrators (reading R10): stage k sets
+// u <- c0 u0 + c1 u + cr L (+ ca acc) and acc <- wa acc + wr L; RK2 = SSP
+// Heun, RK3 = SSP Shu-Osher, RK4 = classical.  Returns the stage count.
+struct RkStage {
+  double c0, c1, cr, ca, wa, wr;
+  bool acc_in, acc_out;
+};
+
+inline int rk_stages(int scheme, double dt, RkStage st[4]) {
+  if (scheme == GRMHD_RK2) {
+    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
+    st[1] = {0.5, 0.5, 0.5 * dt, 0, 0, 0, false, false};
+    return 2;
+  }
+  if (scheme == GRMHD_RK3) {
+    st[0] = {1.0, 0.0, dt, 0, 0, 0, false, false};
+    st[1] = {0.75, 0.25, 0.25 * dt, 0, 0, 0, false, false};
+    st[2] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, 0, 0, 0, false, false};
+    return 3;
+  }
+  st[0] = {1.0, 0.0, 0.5 * dt, 0, 0, 1.0, false, true};
+  st[1] = {1.0, 0.0, 0.5 * dt, 0, 1.0, 2.0, true, true};
+  st[2] = {1.0, 0.0, dt, 0, 1.0, 2.0, true, true};
+  st[3] = {1.0, 0.0, dt / 6.0, dt / 6.0, 0, 0, true, false};
+  return 4;
+}
+
+// Two-level AMR transfer (amr.cu).
+cudaError_t launch_restrict(const DevGrid& c, double* coarse, const DevGrid& f, const double* fine, const int lo[3],
+                            int nvar, cudaStream_t s);
+cudaError_t launch_prolongate(const DevGrid& c, const double* coarse, const DevGrid& f, double* fine,
+                              const int lo[3], int nvar, bool ghosts_only, cudaStream_t s);
+cudaError_t launch_reflux(const DevGrid& c, const DevParams& p, const double* cprim, const double* cmetric,
+                          const DevGrid& f, const double* fprim, const double* fmetric, const int lo[3],
+                          double scale, double* out, double acc_scale, double* acc, cudaStream_t s);
 
 }  // namespace grmhd

@@ -458,3 +458,90 @@ def rk_step_adjoint(grid: Grid, params: Params, scheme: int, dt: float, cons, pr
                                     _scalar(gamma_bar, "gamma_bar"), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                     _stream(stream))
     _check(rc, "grmhd_rk_step_adjoint")
+
+
+# ----------------------------------------------- two-level AMR transfer --
+_lib.grmhd_restrict.argtypes = [_pg, _P, _pg, _P, _P, _I32, _P]
+_lib.grmhd_prolongate.argtypes = [_pg, _P, _pg, _P, _P, _I32, _I32, _P]
+_lib.grmhd_reflux.argtypes = [_pg, _pp, _P, _P, _pg, _P, _P, _P, ctypes.c_double, _P, ctypes.c_double, _P, _P]
+_lib.grmhd_amr2_workspace_bytes.argtypes = [_pg, _I32, _P, _I32]
+_lib.grmhd_amr2_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_amr2_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P,
+                                 ctypes.c_size_t, _P, _P]
+for _name in ("grmhd_restrict", "grmhd_prolongate", "grmhd_reflux", "grmhd_amr2_step"):
+    getattr(_lib, _name).restype = _I
+C_SYMBOLS = C_SYMBOLS + ("grmhd_restrict", "grmhd_prolongate", "grmhd_reflux", "grmhd_amr2_workspace_bytes",
+                         "grmhd_amr2_step")
+
+
+def _lo3(lo):
+    return (ctypes.c_int32 * 3)(*[int(v) for v in lo])
+
+
+def restrict(coarse: Grid, coarse_field, fine: Grid, fine_field, lo, stream=None):
+    """grmhd_restrict: covered coarse cells of coarse_field (in place) := mean of their 8 children."""
+    nvar = coarse_field.shape[0]
+    rc = _lib.grmhd_restrict(ctypes.byref(coarse.c()), _field(coarse_field, coarse, nvar, "coarse_field"),
+                             ctypes.byref(fine.c()), _field(fine_field, fine, nvar, "fine_field"), _lo3(lo), nvar,
+                             _stream(stream))
+    _check(rc, "grmhd_restrict")
+    return coarse_field
+
+
+def prolongate(coarse: Grid, coarse_field, fine: Grid, fine_field, lo, ghosts_only=True, stream=None):
+    """grmhd_prolongate: fine points (ghosts only, or all) of fine_field (in place) from the coarse parents."""
+    nvar = fine_field.shape[0]
+    rc = _lib.grmhd_prolongate(ctypes.byref(coarse.c()), _field(coarse_field, coarse, nvar, "coarse_field"),
+                               ctypes.byref(fine.c()), _field(fine_field, fine, nvar, "fine_field"), _lo3(lo), nvar,
+                               int(bool(ghosts_only)), _stream(stream))
+    _check(rc, "grmhd_prolongate")
+    return fine_field
+
+
+def reflux(coarse: Grid, params: Params, coarse_prim, fine: Grid, fine_prim, lo, out, scale=1.0, coarse_metric=None,
+           fine_metric=None, acc=None, acc_scale=0.0, stream=None):
+    """grmhd_reflux: out += scale * (coarse RHS change from flux restriction at the interface)."""
+    rc = _lib.grmhd_reflux(ctypes.byref(coarse.c()), ctypes.byref(params.c()), _field(coarse_prim, coarse, 8, "coarse_prim"),
+                           _field(coarse_metric, coarse, 10, "coarse_metric", True), ctypes.byref(fine.c()),
+                           _field(fine_prim, fine, 8, "fine_prim"), _field(fine_metric, fine, 10, "fine_metric", True),
+                           _lo3(lo), float(scale), _field(out, coarse, 8, "out"), float(acc_scale),
+                           _field(acc, coarse, 8, "acc", True), _stream(stream))
+    _check(rc, "grmhd_reflux")
+    return out
+
+
+def _grid_array(grids):
+    arr = (CGrid * max(1, len(grids)))()
+    for i, g in enumerate(grids):
+        arr[i] = g.c()
+    return arr
+
+
+def amr2_workspace(coarse: Grid, fine, scheme: int, device=None):
+    ga = _grid_array(fine)
+    nbytes = int(_lib.grmhd_amr2_workspace_bytes(ctypes.byref(coarse.c()), len(fine), ctypes.cast(ga, _P), scheme))
+    if nbytes == 0:
+        raise GrmhdError("invalid grids for the AMR workspace")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def amr2_step(coarse: Grid, params: Params, scheme: int, dt: float, coarse_cons, coarse_prim, fine, fine_cons,
+              fine_prim, los, coarse_metric=None, fine_metrics=None, ws=None, nfail=None, stream=None):
+    """grmhd_amr2_step: one composite step of a coarse block and its fine blocks (in place)."""
+    nf = len(fine)
+    if ws is None:
+        ws = amr2_workspace(coarse, fine, scheme, coarse_cons.device)
+    ga = _grid_array(fine)
+    pc = (_P * max(1, nf))(*[_field(fine_cons[i], fine[i], 8, "fine_cons").value for i in range(nf)])
+    pp_ = (_P * max(1, nf))(*[_field(fine_prim[i], fine[i], 8, "fine_prim").value for i in range(nf)])
+    pm = None
+    if fine_metrics is not None:
+        pm = (_P * max(1, nf))(*[_field(fine_metrics[i], fine[i], 10, "fine_metric").value for i in range(nf)])
+    lo = (ctypes.c_int32 * max(3, 3 * nf))(*[int(v) for l in los for v in l])
+    nf_ptr = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_amr2_step(ctypes.byref(coarse.c()), ctypes.byref(params.c()), scheme, float(dt),
+                              _field(coarse_cons, coarse, 8, "coarse_cons"), _field(coarse_prim, coarse, 8, "coarse_prim"),
+                              _field(coarse_metric, coarse, 10, "coarse_metric", True), nf, ctypes.cast(ga, _P),
+                              ctypes.cast(pc, _P), ctypes.cast(pp_, _P), None if pm is None else ctypes.cast(pm, _P),
+                              ctypes.cast(lo, _P), ctypes.c_void_p(ws.data_ptr()), ws.numel(), nf_ptr, _stream(stream))
+    _check(rc, "grmhd_amr2_step")

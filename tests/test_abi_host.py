@@ -128,3 +128,50 @@ def test_autotuner_choice_logic_on_cpu():
     assert autotune.n_tiles(2, (8, 8, 8)) == 8        # 32-wide tiles waste 3/4 on an 8-wide box
     assert autotune.choose((8, 8, 8), costs) in (0, 3)
     assert autotune.choose((64, 8, 8), {0: 1.0, 1: 1.0, 2: 0.5, 3: 1.0}) == 2
+
+
+def test_amr_placement_validation(lib):
+    """Fine grids must halve the spacing, have even extents and lie inside the coarse interior."""
+    c = lib.Grid((16, 16, 16), 3, (0.1, 0.1, 0.1))
+    ok = lib.Grid((8, 8, 8), 3, (0.05, 0.05, 0.05))
+    lo = (ctypes.c_int32 * 3)(4, 4, 4)
+    cases = [
+        (lib.Grid((7, 8, 8), 3, (0.05, 0.05, 0.05)), lo),                 # odd extent
+        (lib.Grid((8, 8, 8), 3, (0.1, 0.05, 0.05)), lo),                  # not half the spacing
+        (lib.Grid((8, 8, 8), 2, (0.05, 0.05, 0.05)), lo),                 # ghost widths differ
+        (ok, (ctypes.c_int32 * 3)(13, 4, 4)),                             # sticks out of the coarse interior
+        (ok, (ctypes.c_int32 * 3)(-1, 4, 4)),
+    ]
+    for fine, l in cases:
+        rc = lib._lib.grmhd_restrict(ctypes.byref(c.c()), FAKE, ctypes.byref(fine.c()), FAKE, l, 8, None)
+        assert rc == -1
+        rc = lib._lib.grmhd_prolongate(ctypes.byref(c.c()), FAKE, ctypes.byref(fine.c()), FAKE, l, 8, 1, None)
+        assert rc == -1
+    # a valid placement still needs real pointers
+    assert lib._lib.grmhd_restrict(ctypes.byref(c.c()), None, ctypes.byref(ok.c()), FAKE, lo, 8, None) == -1
+
+
+def test_amr2_step_validation_and_workspace(lib):
+    c = lib.Grid((16, 16, 16), 3, (0.1, 0.1, 0.1))
+    f = [lib.Grid((8, 8, 8), 3, (0.05, 0.05, 0.05)), lib.Grid((6, 6, 6), 3, (0.05, 0.05, 0.05))]
+    ga = (lib.CGrid * 2)(f[0].c(), f[1].c())
+    b = lib._lib.grmhd_amr2_workspace_bytes(ctypes.byref(c.c()), 2, ctypes.cast(ga, ctypes.c_void_p), lib.RK3)
+    assert b == sum(((8 * n.ncell * 8 + 255) // 256) * 256 for n in [c] + f)
+    b4 = lib._lib.grmhd_amr2_workspace_bytes(ctypes.byref(c.c()), 2, ctypes.cast(ga, ctypes.c_void_p), lib.RK4)
+    assert b4 == 2 * b
+    p = lib.Params().c()
+    ptrs = (ctypes.c_void_p * 2)(0x1000, 0x2000)
+    ws = ctypes.c_void_p(0x100000)
+
+    def step(lo, ws_bytes=10 ** 10, params=p):
+        loa = (ctypes.c_int32 * 6)(*lo)
+        return lib._lib.grmhd_amr2_step(ctypes.byref(c.c()), ctypes.byref(params), lib.RK3, 0.01, FAKE, FAKE, None, 2,
+                                        ctypes.cast(ga, ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p),
+                                        ctypes.cast(ptrs, ctypes.c_void_p), None, ctypes.cast(loa, ctypes.c_void_p),
+                                        ws, ws_bytes, None, None)
+
+    assert step((0, 4, 4, 10, 10, 10)) == -1          # no gap to the coarse boundary
+    assert step((2, 2, 2, 6, 6, 6)) == -1             # fine grids touch: [2, 6) and [6, 9)
+    assert step((2, 2, 2, 9, 9, 9), ws_bytes=b - 8) == -4
+    mixed = lib.Params(precision=lib.MIXED).c()
+    assert step((2, 2, 2, 9, 9, 9), params=mixed) == -1   # the composite step is FP64 only
