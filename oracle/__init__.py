@@ -81,6 +81,8 @@ def _load():
         lib.oracle_con2prim_point.restype = I
         lib.oracle_loss_jvp.argtypes = [P, I, P, pp, I, Dd, I, P, P, Dd, P, P, P, P]
         lib.oracle_loss_jvp.restype = I
+        lib.oracle_con2prim_nh_point.argtypes = [P, pp, Dd, P]
+        lib.oracle_con2prim_nh_point.restype = I
         lib.oracle_restrict.argtypes = [P, I, P, P, P, I, P, P, P, I]
         lib.oracle_prolongate.argtypes = [P, I, P, P, P, I, P, P, P, I, I]
         lib.oracle_reflux.argtypes = [P, I, P, pp, P, P, P, I, P, P, P, P, Dd, P]
@@ -246,6 +248,14 @@ def con2prim_point(U8, params: OParams, adm10=None):
     a = None if adm10 is None else _f64(np.asarray(adm10).reshape(10))
     out = np.zeros(8)
     st = _load().oracle_con2prim_point(_ptr(U), _ptr(a), ctypes.byref(params), _ptr(out))
+    return out, st
+
+
+def con2prim_nh_point(U8, params: OParams, P0):
+    """Newman-Hamlin recovery of one flat-space state (reading R18); (prim, status 0 ok / 1 failed)."""
+    U = _f64(np.asarray(U8).reshape(8))
+    out = np.zeros(8)
+    st = _load().oracle_con2prim_nh_point(_ptr(U), ctypes.byref(params), float(P0), _ptr(out))
     return out, st
 
 

@@ -49,6 +49,15 @@
 //      includes the case where the energy residual has no sign change
 //      inside v < 1: a bracket that closes only against the v = 1 boundary
 //      is not a root (its side of the boundary is decided by round-off).
+//   R18 Newman-Hamlin recovery (Sec. 2.3: an effective 1D iteration over the
+//      pressure; each step solves a cubic in eps = B^2 + z): from the energy
+//      and momentum equations, eps^3 - a eps^2 + d = 0 with a = tau + D + P
+//      + B^2 / 2 and d = (B^2 S^2 - (B.S)^2) / 2; the physical root is the
+//      largest, eps = a/3 + (2a/3) cos(acos(1 - 27 d / (2 a^3)) / 3); then
+//      z = eps - B^2, v^2(z) from the momentum equation, and the Gamma-law
+//      pressure of (z, W) is the next iterate.  Plain fixed point here; the
+//      GPU path accelerates it (Aitken) and uses it as the fallback of its
+//      Newton iteration.
 //   Two-level block AMR without subcycling (Sec. 3: refined grids halve the
 //   spacing, are properly nested, share one global time step; ghost zones
 //   of a refined grid are filled by prolongation from the next coarser
@@ -697,6 +706,36 @@ S c2p_f(const C2P<S>& in, const S& z) {
   return in.tau + in.D - z - in.B2 + 0.5 * in.B2 * iw * iw + 0.5 * in.BS * in.BS / (z * z) + press;
 }
 
+// Reading R18: Newman-Hamlin fixed point over P from P0.  Returns true and
+// (z, W) when |P_{k+1} - P_k| <= tol |P_{k+1}| within maxit iterations.
+inline bool c2p_newman_hamlin(const C2P<double>& in, double P0, int maxit, double tol, double& z, double& W) {
+  const double E = in.tau + in.D;
+  double d = 0.5 * (in.B2 * in.S2 - in.BS * in.BS);
+  if (d < 0.0) d = 0.0;  // Cauchy-Schwarz: negative only by round-off
+  double P = P0;
+  for (int it = 0; it < maxit; ++it) {
+    const double a = E + P + 0.5 * in.B2;
+    if (!(a > 0.0)) return false;
+    const double r = 1.0 - 27.0 * d / (2.0 * a * a * a);
+    if (!(r >= -1.0)) return false;  // d > 4 a^3 / 27: no root above 2a/3
+    const double eps = a / 3.0 + (2.0 * a / 3.0) * std::cos(std::acos(std::min(r, 1.0)) / 3.0);
+    const double zz = eps - in.B2;
+    if (!(zz > 0.0)) return false;
+    const double v2 = c2p_v2(in, zz);
+    if (!(v2 < 1.0)) return false;
+    const double iw = std::sqrt(1.0 - v2);
+    const double Pn = (in.gamma - 1.0) / in.gamma * (zz * iw * iw - in.D * iw);
+    const bool done = std::fabs(Pn - P) <= tol * std::fabs(Pn);
+    P = Pn;
+    if (done) {
+      z = zz;
+      W = 1.0 / iw;
+      return std::isfinite(z) && std::isfinite(W);
+    }
+  }
+  return false;
+}
+
 // Returns status 0 on success, 1 if the atmosphere was imposed, 2 if the
 // pressure floor was applied.
 template <class S>
@@ -1185,6 +1224,26 @@ void oracle_reconstruct_1d(int recon, double eps, int n, const double* u, double
 }
 
 // Con2prim of one cell; returns the status.
+// Newman-Hamlin recovery of one flat-space state from the pressure guess P0
+// (reading R18): returns 0 and prim8 on convergence, 1 otherwise.
+int oracle_con2prim_nh_point(const double* U8, const OParams* q, double P0, double* prim8) {
+  C2P<double> in;
+  in.D = U8[0];
+  in.tau = U8[4];
+  in.S2 = U8[1] * U8[1] + U8[2] * U8[2] + U8[3] * U8[3];
+  in.B2 = U8[5] * U8[5] + U8[6] * U8[6] + U8[7] * U8[7];
+  in.BS = U8[5] * U8[1] + U8[6] * U8[2] + U8[7] * U8[3];
+  in.gamma = q->gamma;
+  double z = 0.0, W = 1.0;
+  if (!c2p_newman_hamlin(in, P0, 10000, 1e-15, z, W)) return 1;
+  const double rho = in.D / W;
+  prim8[0] = rho;
+  for (int i = 0; i < 3; ++i) prim8[1 + i] = (U8[1 + i] + in.BS / z * U8[5 + i]) / (z + in.B2);
+  prim8[4] = (in.gamma - 1.0) / in.gamma * (z / (W * W) - rho);
+  for (int i = 0; i < 3; ++i) prim8[5 + i] = U8[5 + i];
+  return 0;
+}
+
 int oracle_con2prim_point(const double* U8, const double* adm10, const OParams* q, double* prim8) {
   double adm[10];
   if (adm10) for (int k = 0; k < 10; ++k) adm[k] = adm10[k]; else flat_adm(adm);

@@ -309,6 +309,38 @@ def test_con2prim_hydro_limit_matches_brentq():
         np.testing.assert_allclose(out[1:4], v, rtol=0, atol=1e-12)
 
 
+def test_newman_hamlin_hydro_limit_matches_brentq():
+    """B = 0: d = 0 and the cubic's largest root is eps = a, the textbook pressure iteration."""
+    par = O.make_params()
+    for _ in range(60):
+        prim = random_prim(RNG, np.eye(3), vmax=0.95, bmax=0.0)
+        prim[5:] = 0
+        U, _, _, _ = O.point(prim, par.gamma)
+        out, st = O.con2prim_nh_point(U, par, 0.7 * prim[4])
+        assert st == 0
+        P, rho, v = hydro_inversion_brentq(U, par.gamma)
+        assert abs(out[4] - P) < 1e-12 * P
+        assert abs(out[0] - rho) < 1e-12 * rho
+        np.testing.assert_allclose(out[1:4], v, rtol=0, atol=1e-12)
+
+
+def test_newman_hamlin_root_solves_the_conserved_equations():
+    """Magnetised states: the Newman-Hamlin root maps back onto U (Eqs. 6-9) and, for
+    well-conditioned states, onto the primitives it came from."""
+    par = O.make_params()
+    worst = 0.0
+    for k in range(200):
+        prim = random_prim(RNG, np.eye(3), vmax=0.9, bmax=1.5)
+        U, _, _, _ = O.point(prim, par.gamma)
+        out, st = O.con2prim_nh_point(U, par, prim[4] * (0.5 + k % 3))
+        assert st == 0
+        U2, _, _, _ = O.point(out, par.gamma)
+        assert np.max(np.abs(U2 - U)) <= 1e-13 * np.max(np.abs(U))
+        err = np.max(np.abs(out - prim) / np.maximum(np.abs(prim), 1e-3 * np.max(np.abs(prim))))
+        worst = max(worst, err)
+    assert worst < 1e-9
+
+
 @pytest.mark.parametrize("curved", [False, True])
 def test_con2prim_round_trip_and_residual(curved):
     par = O.make_params()
