@@ -85,7 +85,7 @@ typedef struct {
   double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
   int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
-  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY */
+  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN */
 } grmhd_params;
 
 /* flags: the metric, the grid and the precision are unchanged since the
@@ -94,6 +94,9 @@ typedef struct {
  * instead of rebuilt.  A static spacetime sets it after its first step.
  * Ignored by every other call. */
 #define GRMHD_REUSE_GEOMETRY 1
+/* flags: the primitive recovery starts with the Newman-Hamlin iteration
+ * instead of the Newton iteration (see grmhd_con2prim). */
+#define GRMHD_NEWMAN_HAMLIN 2
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
  * shape changes only how the work is cut, never the result.  8x8x8 (two
@@ -115,17 +118,24 @@ int grmhd_prim2con(const grmhd_grid* grid, const grmhd_params* params, const dou
 
 /* Conserved -> primitive recovery (Sec. 2.3, "Find the primitive variable
  * vector"): per interior cell, a 2D Newton-Raphson in (z = rho h W^2, W)
- * (the paper's 3D Newton with the temperature eliminated by the Gamma-law),
- * falling back to bracketed bisection in z; cells that still fail or come out
- * unphysical (no root, NaN, rho < rho_atm, v >= 1) get the atmosphere
- * (rho_atm, v = 0, p_atm, B kept); a valid root with P <= 0 keeps rho and v
- * and gets the pressure floor P = p_atm (Sec. 2.3 lists these failure modes).
+ * (the paper's 3D Newton with the temperature eliminated by the Gamma-law);
+ * if it does not converge or converges to an unphysical root, the
+ * Newman-Hamlin iteration over P (an Aitken-accelerated fixed point, each
+ * step a closed-form cubic root in eps = B^2 + z), as in the paper; if that
+ * fails too, bracketed bisection in z.  With GRMHD_NEWMAN_HAMLIN in
+ * params.flags the Newman-Hamlin iteration comes first.  Cells that still
+ * fail or come out unphysical (no root, NaN, rho < rho_atm, v >= 1) get the
+ * atmosphere (rho_atm, v = 0, p_atm, B kept); a valid root with P <= 0 keeps
+ * rho and v and gets the pressure floor P = p_atm (Sec. 2.3 lists these
+ * failure modes).  The initial pressure of the Newman-Hamlin iteration is
+ * the incoming primitive pressure.
  *   cons   in      8 x ncell (interior read)
  *   metric in      10 x ncell or NULL
  *   prim   in/out  8 x ncell: interior holds the initial guess on entry and
  *                  the result on exit; ghost entries are not touched
- *   status out     int8 x ncell or NULL: 0 Newton, 1 bisection fallback,
- *                  2 atmosphere, 3 pressure floor (interior entries only)
+ *   status out     int8 x ncell or NULL: 0 Newton or Newman-Hamlin,
+ *                  1 bisection fallback, 2 atmosphere, 3 pressure floor
+ *                  (interior entries only)
  *   nfail  in/out  one device int32 or NULL: atomically incremented by the
  *                  number of atmosphere and pressure-floor cells (caller
  *                  zeroes it) */

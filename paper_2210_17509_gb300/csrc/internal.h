@@ -110,7 +110,7 @@ inline int check_params(const grmhd_params* p) {
   if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
   if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
-  if ((p->flags & ~GRMHD_REUSE_GEOMETRY) != 0) return GRMHD_ERR_ARG;
+  if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN)) != 0) return GRMHD_ERR_ARG;
   return GRMHD_OK;
 }
 

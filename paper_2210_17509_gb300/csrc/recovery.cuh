@@ -107,16 +107,65 @@ __device__ __forceinline__ bool c2p_root_physical(const C2PIn& in, const DevPara
   return W >= 1.0 && isfinite(W) && z > in.D * W && in.D >= p.rho_atm * W;
 }
 
+// Newman-Hamlin iteration over the pressure (Sec. 2.3, the paper's fallback
+// "Newman's method"): with E = tau + D, a = E + P + B^2/2 and
+// d = (B^2 S^2 - (B.S)^2)/2, the energy and momentum equations give
+// eps^3 - a eps^2 + d = 0 for eps = B^2 + z, whose physical root is the
+// largest, eps = a/3 + (2a/3) cos(acos(1 - 27 d / (2 a^3)) / 3); then
+// v^2(z) from the momentum equation and the Gamma-law pressure of (z, W)
+// give the next P.  The fixed point is accelerated by Aitken's delta-squared
+// extrapolation every third iterate.  Returns true with (z, W) when the
+// pressure changes by at most nr_tol (relative) within 3 * nr_maxit steps.
+static __device__ bool c2p_newman_hamlin(const C2PIn& in, const DevParams& p, double P, double& z, double& W) {
+  const double E = in.tau + in.D;
+  const double d = fmax(0.5 * (in.B2 * in.S2 - in.BS2), 0.0);  // >= 0 (Cauchy-Schwarz) up to round-off
+  double Pm1 = 0.0;
+  const int maxit = 3 * p.nr_maxit;
+  for (int it = 0; it < maxit; ++it) {
+    const double a = E + P + 0.5 * in.B2;
+    if (!(a > 0.0)) return false;
+    const double ia3 = 1.0 / (a * a * a);
+    const double r = 1.0 - 13.5 * d * ia3;
+    if (!(r >= -1.0)) return false;  // d > 4 a^3 / 27: no root above 2a/3
+    const double eps = a * (1.0 / 3.0) + (a * (2.0 / 3.0)) * cos(acos(fmin(r, 1.0)) * (1.0 / 3.0));
+    const double zz = eps - in.B2;
+    if (!(zz > 0.0)) return false;
+    const double v2 = c2p_v2_of_z(in, zz);
+    if (!(v2 < 1.0)) return false;
+    const double iw = sqrt(1.0 - v2);
+    double Pn = p.gm1g * (zz * (1.0 - v2) - in.D * iw);
+    if (fabs(Pn - P) <= p.nr_tol * fabs(Pn)) {
+      z = zz;
+      W = 1.0 / iw;
+      return isfinite(z) && isfinite(W);
+    }
+    // Aitken extrapolation from the last three iterates (P_{k-1}, P_k, P_{k+1})
+    if (it % 3 == 2) {
+      const double den = Pn - 2.0 * P + Pm1;
+      const double Pa = Pn - (Pn - P) * (Pn - P) / den;
+      if (den != 0.0 && Pa > 0.0 && isfinite(Pa)) Pn = Pa;
+    }
+    Pm1 = P;
+    P = Pn;
+  }
+  return false;
+}
+
 // Returns 0 (Newton converged), 1 (bisection), 2 (failed); z, W on exit.
 // tol_first applies to the first Newton step only: after an FP32 predictor
 // that converged to 1e-6, one FP64 step leaves an error of order 1e-12 times
 // the problem's curvature scale (quadratic convergence), so a first step
 // below tol_first ends the solve; every later step must be below nr_tol.
-static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W, double tol_first) {
+// P0 (> 0) starts the Newman-Hamlin iteration, which follows a failed
+// Newton iteration or, with GRMHD_NEWMAN_HAMLIN, replaces it; status 0
+// covers both.
+static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W, double tol_first,
+                                double P0) {
   const double gm1g = p.gm1g;
   const double D = in.D, B2 = in.B2, BS2 = in.BS2, S2 = in.S2, tau = in.tau;
   bool ok = false;
-  if (z > 0.0 && W >= 1.0 && isfinite(z) && isfinite(W)) {
+  const bool newman_first = (p.flags & GRMHD_NEWMAN_HAMLIN) != 0;
+  if (!newman_first && z > 0.0 && W >= 1.0 && isfinite(z) && isfinite(W)) {
     for (int it = 0; it < p.nr_maxit; ++it) {
       const double izW = 1.0 / (z * W);  // 1/z and 1/W from one division
       const double iz = W * izW, iW = z * izW;
@@ -143,6 +192,7 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
     }
   }
   if (ok && c2p_root_physical(in, p, z, W)) return 0;
+  if (c2p_newman_hamlin(in, p, P0, z, W) && c2p_root_physical(in, p, z, W)) return 0;
   return c2p_bisect(in, p, z, W);
 }
 
@@ -238,7 +288,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   in.BS2 = BS * BS;
   // initial guess from the incoming primitives
   double* pc = prim + c;
-  double W, z;
+  double W, z, P0;
   if (F32IO) {
     const float* pf = prim32 + c;
     const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
@@ -252,6 +302,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const float Wf = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
     W = (double)Wf;
     z = (rg > 0.0f && Pg > 0.0f) ? (double)((rg + (float)p.gfac * Pg) * Wf * Wf) : (tau + D + in.B2);
+    P0 = (double)Pg;
   } else {
     const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
     double vl[3];
@@ -260,12 +311,14 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const double rg = pc[0], Pg = pc[4 * g.ncell];
     W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
     z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
+    P0 = Pg;
   }
+  if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
   int st = 2;
   if (D > 0.0 && tau + D > 0.0) {
     double tol_first = p.nr_tol;
     if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
-    st = c2p_solve(in, p, z, W, tol_first);
+    st = c2p_solve(in, p, z, W, tol_first, P0);
   }
   if constexpr (!RESULT64) {
     // FP32 primitives from the FP64 root: 1/W, 1/z, 1/(z + B^2) from one division

@@ -23,6 +23,7 @@ BC_PERIODIC, BC_COPY = 0, 1
 FP64, MIXED = 0, 1
 RK2, RK3, RK4 = 2, 3, 4
 REUSE_GEOMETRY = 1
+NEWMAN_HAMLIN = 2
 
 
 class GrmhdError(RuntimeError):

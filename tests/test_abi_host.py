@@ -93,6 +93,21 @@ def test_workspace_size_and_rk_validation(lib):
     assert rc == -1          # workspace must be 256-byte aligned
 
 
+def test_recovery_flag_validation(lib):
+    """Unknown flag bits are rejected; every call here fails validation before any launch."""
+    g = _grid(lib).c()
+    ws = ctypes.c_void_p(0x100000)
+    for flags in (4, 8, lib.NEWMAN_HAMLIN | 16):
+        p = lib.Params(flags=flags).c()
+        assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1
+    # the known flags pass the parameter check and stop at the workspace size
+    for flags in (lib.NEWMAN_HAMLIN, lib.NEWMAN_HAMLIN | lib.REUSE_GEOMETRY):
+        p = lib.Params(flags=flags).c()
+        rc = lib._lib.grmhd_rk_step(ctypes.byref(g), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, None, None, ws, 8,
+                                    None, None)
+        assert rc == -4
+
+
 def test_error_strings(lib):
     assert lib._lib.grmhd_error_string(0) == b"ok"
     assert lib._lib.grmhd_error_string(-4) == b"workspace too small"

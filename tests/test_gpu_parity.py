@@ -108,6 +108,28 @@ def test_con2prim_parity_and_round_trip(G, curved):
     np.testing.assert_array_equal(P[:, gmask], guess[:, gmask])
 
 
+@pytest.mark.parametrize("curved", [False, True])
+def test_con2prim_newman_hamlin_first(G, curved):
+    """GRMHD_NEWMAN_HAMLIN: the Newman-Hamlin iteration (Sec. 2.3) as the primary recovery, from
+    a pressure guess 30% off, against the oracle's bracketed recovery."""
+    blk, prim, met = (block_curved if curved else block_flat)(16, seed=6)
+    g, og = grids(G, blk)
+    gp, op = params(G, 1)
+    gp.flags = G.NEWMAN_HAMLIN
+    Uo = O.prim2con(og, op.gamma, prim, met)
+    guess = prim.copy()
+    guess[4] *= 1.3
+    tp = cuda(guess)
+    status = torch.zeros(g.shape, dtype=torch.int8, device="cuda")
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    G.con2prim(g, gp, cuda(Uo), tp, None if met is None else cuda(met), status, nfail)
+    P = host(tp)
+    Po, st, nf = O.con2prim(og, op, Uo, met, guess)
+    assert nf == 0 and int(nfail.item()) == 0
+    assert np.all(interior(host(status)[None], 3) == 0)
+    assert np.all(normwise(interior(P, 3), interior(Po, 3)) < FP64_TOL)
+
+
 def test_con2prim_failures_set_atmosphere(G):
     """Host-injected faults: tau + D < 0, NaN, and an impossible momentum."""
     blk, prim, _ = block_flat(8, seed=2)
