@@ -261,6 +261,14 @@ __device__ __forceinline__ void rotate_state(int dir, const T in[8], T out[8]) {
   out[7] = sel3(dir, in[7], in[5], in[6]);
 }
 
+// A vector in rotated axes (new axis k = old axis (dir + k) mod 3).
+template <class T>
+__device__ __forceinline__ void rotate_vec(int dir, const T in[3], T out[3]) {
+  out[0] = sel3(dir, in[0], in[1], in[2]);
+  out[1] = sel3(dir, in[1], in[2], in[0]);
+  out[2] = sel3(dir, in[2], in[0], in[1]);
+}
+
 template <class T>
 __device__ __forceinline__ void unrotate_flux(int dir, const T in[8], T out[8]) {
   out[0] = in[0];
@@ -294,6 +302,20 @@ __device__ __forceinline__ void lower(const T g[6], const T v[3], T vl[3]) {
   vl[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
   vl[1] = g[1] * v[0] + g[3] * v[1] + g[4] * v[2];
   vl[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
+}
+
+// As physical_state, also returning the lowered velocity and v^2.
+template <class T, bool CURVED>
+__device__ __forceinline__ bool physical_state_v(const T pr[8], const Geom<T>& m, T vl[3], T& v2) {
+  const T v[3] = {pr[1], pr[2], pr[3]};
+  if (CURVED) {
+    lower(m.g, v, vl);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vl[i] = v[i];
+  }
+  v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
 }
 
 template <class T, bool CURVED>
@@ -332,21 +354,32 @@ struct Side {
 // finishes the speeds itself -- lm / lp then hold the bracketed numerators
 // and sden the denominator -- so that the two sides of a face share one
 // division (finish_speeds).
-template <class T, bool CURVED, int DIR, bool SHARED = false>
+//
+// SCALED (with SHARED): U and F come without their common factors sqrt(gamma)
+// and alpha (alpha sqrt(gamma) for F), which the two sides of a face share;
+// hlle_combine_scaled applies them once.  vl_in / v2_in (nullable): the
+// lowered velocity and v^2, when the caller has them already.
+template <class T, bool CURVED, int DIR, bool SHARED = false, bool SCALED = false>
 __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T gamma, T gfac, Side<T>& o,
-                                           T ia_in = T(0)) {
+                                           T ia_in = T(0), const T* vl_in = nullptr, T v2_in = T(0)) {
+  static_assert(!SCALED || SHARED, "scaled side states finish their speeds with the face");
   const T rho = pr[0], P = pr[4];
   const T v[3] = {pr[1], pr[2], pr[3]};
   const T B[3] = {pr[5], pr[6], pr[7]};
   T vl[3], Bl[3];
   if (CURVED) {
-    lower(m.g, v, vl);
+    if (vl_in) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) vl[i] = vl_in[i];
+    } else {
+      lower(m.g, v, vl);
+    }
     lower(m.g, B, Bl);
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) { vl[i] = v[i]; Bl[i] = B[i]; }
   }
-  const T v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const T v2 = vl_in ? v2_in : v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
   const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
   const T omv2 = T(1) - v2;
@@ -360,7 +393,7 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   const T rhoh = rho + gfac * P;
   const T hs = rhoh + b2;           // rho h*
   const T Ps = P + T(0.5) * b2;     // P*
-  const T sg = CURVED ? m.sqrtg : T(1);
+  const T sg = (CURVED && !SCALED) ? m.sqrtg : T(1);
   const T hW2 = hs * W * W;
   const T D = sg * rho * W;
 #pragma unroll
@@ -373,6 +406,7 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   for (int i = 0; i < 3; ++i) { Bc[i] = sg * B[i]; o.U[5 + i] = Bc[i]; }
   // flux along DIR
   const T alpha = CURVED ? m.alpha : T(1);
+  const T af = SCALED ? T(1) : alpha;  // lapse factor of the fluxes
   T vt[3];
   if (CURVED) {
     const T ia = SHARED ? ia_in : T(1) / alpha;
@@ -385,12 +419,12 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   const T vtd = vt[DIR];
   const T sgPs = sg * Ps;
   const T BdiW = Bc[DIR] * iW;
-  o.F[0] = alpha * (D * vtd);
+  o.F[0] = af * (D * vtd);
 #pragma unroll
-  for (int j = 0; j < 3; ++j) o.F[1 + j] = alpha * (o.U[1 + j] * vtd + (j == DIR ? sgPs : T(0)) - bl[j] * BdiW);
-  o.F[4] = alpha * (tau * vtd + sgPs * v[DIR] - ab0 * BdiW);
+  for (int j = 0; j < 3; ++j) o.F[1 + j] = af * (o.U[1 + j] * vtd + (j == DIR ? sgPs : T(0)) - bl[j] * BdiW);
+  o.F[4] = af * (tau * vtd + sgPs * v[DIR] - ab0 * BdiW);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) o.F[5 + k] = (k == DIR) ? T(0) : alpha * (Bc[k] * vtd - Bc[DIR] * vt[k]);
+  for (int k = 0; k < 3; ++k) o.F[5 + k] = (k == DIR) ? T(0) : af * (Bc[k] * vtd - Bc[DIR] * vt[k]);
   // signal speeds
   const T Na = gamma * P + b2;
   const T dsp = hs - v2 * Na;  // (1 - v^2 a^2) hs
@@ -424,6 +458,26 @@ __device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side
   L.lm = iL * L.lm - bd;
   R.lp = iR * R.lp - bd;
   R.lm = iR * R.lm - bd;
+}
+
+// HLLE flux from SCALED side states: F = sqrt(gamma) [alpha (xp F~L - xm F~R)
+// + xp xm (U~R - U~L)] / (xp - xm), the common factors applied once.
+template <class T>
+__device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side<T>& R, T alpha, T sg, T F[8]) {
+  const T xm = xmin(T(0), xmin(L.lm, R.lm));
+  const T xp = xmax(T(0), xmax(L.lp, R.lp));
+  const T den = xp - xm;
+  const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
+  if (den < tiny) {
+    const T h = T(0.5) * alpha * sg;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) F[q] = h * (L.F[q] + R.F[q]);
+    return;
+  }
+  const T s = sg / den;
+  const T axp = alpha * xp, axm = alpha * xm, xpm = xp * xm;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) F[q] = (axp * L.F[q] - axm * R.F[q] + xpm * (R.U[q] - L.U[q])) * s;
 }
 
 // HLLE flux (Sec. 2.3) from the two sides; 1e-300 (double) / 1e-30 (float)

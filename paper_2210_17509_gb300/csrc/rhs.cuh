@@ -177,24 +177,30 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
                                                  int dir, long long stride, T pL[8], T pR[8], T F[8]) {
   Geom<T> m;
   if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
-  if (!physical_state<T, CURVED>(pL, m)) {
+  // the check's lowered velocity and v^2 feed the side states
+  T vlL[3], vlR[3], v2L, v2R;
+  if (!physical_state_v<T, CURVED>(pL, m, vlL, v2L)) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+    physical_state_v<T, CURVED>(pL, m, vlL, v2L);
   }
-  if (!physical_state<T, CURVED>(pR, m)) {
+  if (!physical_state_v<T, CURVED>(pR, m, vlR, v2R)) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+    physical_state_v<T, CURVED>(pR, m, vlR, v2R);
   }
-  T rL[8], rR[8], Fr[8];
+  T rL[8], rR[8], Fr[8], rvL[3], rvR[3];
   rotate_state(dir, pL, rL);
   rotate_state(dir, pR, rR);
+  rotate_vec(dir, vlL, rvL);
+  rotate_vec(dir, vlR, rvR);
   if (CURVED) rotate_metric(dir, m);
   Side<T> L, R;
   const T ia = CURVED ? T(1) / m.alpha : T(1);  // shared by both sides
-  side_state<T, CURVED, 0, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia);
-  side_state<T, CURVED, 0, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia);
+  side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia, rvL, v2L);
+  side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia, rvR, v2R);
   finish_speeds<T, CURVED, 0>(m, L, R);
-  hlle_combine<T>(L, R, Fr);
+  hlle_combine_scaled<T>(L, R, CURVED ? m.alpha : T(1), CURVED ? m.sqrtg : T(1), Fr);
   unrotate_flux(dir, Fr, F);
 }
 
@@ -268,20 +274,23 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   // symmetric contraction weights: off-diagonal entries count twice
   const T wsym[6] = {T(1), T(2), T(2), T(1), T(2), T(1)};
   out[0] = T(0);
+  // The momentum source is sum_{ik} d_j gamma_ik [T00 beta^i beta^k / 2 +
+  // T^0i beta^k + T^ik / 2] - T00 alpha d_j alpha + T^0_i d_j beta^i; the
+  // bracket does not depend on j, so it is formed once per packed (i, k),
+  // with the symmetric weight and the factor 1/2 folded in.
+  T Wg[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const int i = I6[s], k = J6[s];
+    Wg[s] = (T(0.5) * wsym[s]) * (T00 * (beta[i] * beta[k]) + (T0[i] * beta[k] + T0[k] * beta[i]) + Tij[s]);
+  }
+  const T T00a = T00 * alpha;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    T bbdg = T(0), t0dg = T(0), tdg = T(0);
+    T acc = T0l[0] * dA[j][1] + T0l[1] * dA[j][2] + T0l[2] * dA[j][3] - T00a * dA[j][0];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-      const int i = I6[s], k = J6[s];
-      const T dg = dA[j][4 + s] * wsym[s];
-      bbdg += beta[i] * beta[k] * dg;
-      // T^0i beta^k d_j g_ik summed over i, k: symmetric part
-      t0dg += T(0.5) * (T0[i] * beta[k] + T0[k] * beta[i]) * dg;
-      tdg += Tij[s] * dg;
-    }
-    const T t0db = T0l[0] * dA[j][1] + T0l[1] * dA[j][2] + T0l[2] * dA[j][3];
-    out[1 + j] = asg * (T00 * (T(0.5) * bbdg - alpha * dA[j][0]) + t0dg + t0db + T(0.5) * tdg);
+    for (int s = 0; s < 6; ++s) acc += Wg[s] * dA[j][4 + s];
+    out[1 + j] = asg * acc;
   }
   {
     T t = -(T0[0] * dA[0][0] + T0[1] * dA[1][0] + T0[2] * dA[2][0]);
