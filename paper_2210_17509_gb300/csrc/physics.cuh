@@ -154,6 +154,38 @@ __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double 
   dm = P01 + A + C;
 }
 
+// The numerator of one of the two states of weno5_cell_parts (plus: the
+// value at the upper face, else at the lower face) and both denominators,
+// with the same arithmetic (so that the shared division rounds the same).
+__device__ __forceinline__ void weno5_cell_parts_one(double um2, double um1, double u0, double up1, double up2,
+                                                     double eps13, bool plus, double& num, double& dm,
+                                                     double& dp) {
+  const double k313 = 3.0 / 13.0;
+  const double t0 = fma(-2.0, um1, um2 + u0), s0 = fma(3.0, u0, fma(-4.0, um1, um2));
+  const double t1 = fma(-2.0, u0, um1 + up1), s1 = um1 - up1;
+  const double t2 = fma(-2.0, up1, u0 + up2), s2 = fma(3.0, u0, fma(-4.0, up1, up2));
+  const double e0 = fma(t0, t0, fma(k313 * s0, s0, eps13));
+  const double e1 = fma(t1, t1, fma(k313 * s1, s1, eps13));
+  const double e2 = fma(t2, t2, fma(k313 * s2, s2, eps13));
+  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
+  const double P01 = p01 * p01, P12 = p12 * p12;
+  const double A = 6.0 * (p02 * p02), B = 3.0 * P01, C = 3.0 * P12;
+  const double u11 = 11.0 * u0;
+  dp = P12 + A + B;
+  dm = P01 + A + C;
+  if (plus) {
+    const double qp0 = fma(2.0, um2, fma(-7.0, um1, u11));
+    const double qp1 = fma(2.0, up1, fma(5.0, u0, -um1));
+    const double qp2 = fma(5.0, up1, fma(2.0, u0, -up2));
+    num = fma(P12, qp0, fma(A, qp1, B * qp2));
+  } else {
+    const double qm0 = fma(2.0, up2, fma(-7.0, up1, u11));
+    const double qm1 = fma(2.0, um1, fma(5.0, u0, -up1));
+    const double qm2 = fma(5.0, um1, fma(2.0, u0, -um2));
+    num = fma(P01, qm0, fma(A, qm1, C * qm2));
+  }
+}
+
 // FP32: reciprocal form (the squared products could overflow in single
 // precision): weights r_k = 1 / e_k^2, plus (r0, 6 r1, 3 r2), minus
 // (r2, 6 r1, 3 r0).

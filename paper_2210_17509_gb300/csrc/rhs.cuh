@@ -108,10 +108,36 @@ __device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim
 // at its upper face, "plus") for the primitives 2h and 2h+1, written to the
 // stage buffer sR at [2q][e] (minus) and [2q+1][e] (plus), ne entries per
 // component.  eps13 = (12/13) weno_eps (see weno5_cell_parts).
+// which: 0 both states, 1 the minus state only, 2 the plus state only (the
+// cells at the ends of an extended box need one of the two).
 template <class T, int RECON, class S>
 __device__ __forceinline__ void reconstruct_cell_pair(const S& src, long long ncell, long long c, long long stride,
-                                                      int h, T eps13, T* __restrict__ sR, int ne, int e) {
+                                                      int h, T eps13, T* __restrict__ sR, int ne, int e,
+                                                      int which = 0) {
   if constexpr (RECON == GRMHD_WENO5 && sizeof(T) == 8) {
+    if (which != 0) {
+      // one state of each of the two variables; the division as below, so
+      // the value is the same to the bit as when both states are formed
+      double n[2], dm[2], dp[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const long long a = (2 * h + k) * ncell + c;
+        weno5_cell_parts_one(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride),
+                             ld_prim<double>(src, a), ld_prim<double>(src, a + stride),
+                             ld_prim<double>(src, a + 2 * stride), (double)eps13, which == 2, n[k], dm[k], dp[k]);
+      }
+      const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
+      const double X = 1.0 / (6.0 * a0 * a1);
+      const double x0 = a1 * X, x1 = a0 * X;
+      if (which == 2) {
+        sR[(4 * h + 1) * ne + e] = (T)(n[0] * (dm[0] * x0));
+        sR[(4 * h + 3) * ne + e] = (T)(n[1] * (dm[1] * x1));
+      } else {
+        sR[(4 * h + 0) * ne + e] = (T)(n[0] * (dp[0] * x0));
+        sR[(4 * h + 2) * ne + e] = (T)(n[1] * (dp[1] * x1));
+      }
+      return;
+    }
     // FP64: the four values of the two variables share one division
     double nm[2], dm[2], np[2], dp[2];
 #pragma unroll
@@ -495,7 +521,7 @@ __device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, 
 // its direction, variable pair h; written at stage index eoff + e.
 template <class T, int RECON, int TX, int TY, int TZ, class S>
 __device__ __forceinline__ void tile_stage_item(const DevGrid& g, const S& src, int x0, int y0, int z0, int dir, int e,
-                                                int h, int eoff, T eps13, T* __restrict__ sR, int ns) {
+                                                int h, int eoff, T eps13, T* __restrict__ sR, int ns, int which = 0) {
   const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
   int ex, ey, ez;  // compile-time divisors per direction
   if (dir == 0) {
@@ -511,7 +537,7 @@ __device__ __forceinline__ void tile_stage_item(const DevGrid& g, const S& src, 
     const int ng = g.ng;
     const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
     const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
-    reconstruct_cell_pair<T, RECON, S>(src, g.ncell, c, stride, h, eps13, sR, ns, eoff + e);
+    reconstruct_cell_pair<T, RECON, S>(src, g.ncell, c, stride, h, eps13, sR, ns, eoff + e, which);
   }
 }
 
@@ -544,11 +570,37 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
     __syncthreads();
   } else if constexpr (SM::stage_all) {
     const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
-    for (int it = threadIdx.x; it < 4 * ST::NEA; it += NT) {
-      const int ea = it % ST::NEA, h = it / ST::NEA;
-      const int dir = ea < ST::EXX ? 0 : (ea < ST::EXX + ST::EYY ? 1 : 2);
+    // (a) the tile's own cells, both states, per direction; (b) the two end
+    // cells of every line of the extended box, one state each (the plus
+    // state below the tile, the minus state above it).  The two groups are
+    // separate ranges of the item index, so warps stay uniform.
+    constexpr int NBX = 2 * TY * TZ, NBY = 2 * TX * TZ, NBZ = 2 * TX * TY;
+    for (int it = threadIdx.x; it < 12 * NC + 4 * (NBX + NBY + NBZ); it += NT) {
+      int dir, e, h, which = 0;
+      if (it < 12 * NC) {
+        dir = it / (4 * NC);
+        const int r = it - dir * 4 * NC;
+        h = r / NC;
+        const int l = r - h * NC;
+        const int cx = l % TX, cy = (l / TX) % TY, cz = l / (TX * TY);
+        if (dir == 0) e = (cz * TY + cy) * (TX + 2) + cx + 1;
+        else if (dir == 1) e = (cz * (TY + 2) + cy + 1) * TX + cx;
+        else e = ((cz + 1) * TY + cy) * TX + cx;
+      } else {
+        int r = it - 12 * NC;
+        const int nb = r < 4 * NBX ? NBX : (r < 4 * (NBX + NBY) ? NBY : NBZ);
+        dir = r < 4 * NBX ? 0 : (r < 4 * (NBX + NBY) ? 1 : 2);
+        r -= dir == 0 ? 0 : (dir == 1 ? 4 * NBX : 4 * (NBX + NBY));
+        h = r / nb;
+        const int b = r - h * nb;
+        const int side = b / (nb / 2), t = b - side * (nb / 2);
+        which = side ? 1 : 2;
+        if (dir == 0) e = (t / TY * TY + t % TY) * (TX + 2) + (side ? TX + 1 : 0);
+        else if (dir == 1) e = ((t / TX) * (TY + 2) + (side ? TY + 1 : 0)) * TX + t % TX;
+        else e = ((side ? TZ + 1 : 0) * TY + t / TX) * TX + t % TX;
+      }
       const int eoff = dir == 0 ? 0 : (dir == 1 ? ST::EXX : ST::EXX + ST::EYY);
-      tile_stage_item<T, RECON, TX, TY, TZ, S>(g, src, x0, y0, z0, dir, ea - eoff, h, eoff, eps13, sR, ST::NEA);
+      tile_stage_item<T, RECON, TX, TY, TZ, S>(g, src, x0, y0, z0, dir, e, h, eoff, eps13, sR, ST::NEA, which);
     }
     __syncthreads();
     for (int f = threadIdx.x; f < NF; f += NT)
