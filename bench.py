@@ -153,8 +153,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(seconds_target=15.0):
-    """Oracle throughput on a bounded sample (about 10-30 s of CPU work)."""
+def cpu_baseline_sample(G, seconds_target=15.0):
+    """Oracle throughput on a bounded sample (about 10-30 s of CPU work).
+    Its first step also gives the accuracy report: the max relative error of
+    every conserved field of the FP64 and the mixed GPU paths against the
+    FP64 oracle after one SSP-RK3 step of the same sample."""
+    import torch
     import oracle as O
     O.build()
     nthreads = os.cpu_count() or 1
@@ -166,11 +170,26 @@ def cpu_baseline_sample(seconds_target=15.0):
     sprim = np.ascontiguousarray(prim[sl])
     smet = np.ascontiguousarray(met[sl])
     g = O.Grid(sblk.n, 3, sblk.dx)
-    par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY)
+    gp = G.Params(recon=G.WENO5, bc=G.BC_COPY)
+    par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY, rho_atm=gp.rho_atm, p_atm=gp.p_atm, weno_eps=gp.weno_eps)
     sprim = O.fill_ghosts(g, O.BC_COPY, sprim)
     cons = O.prim2con(g, par.gamma, sprim, smet)
     dt = CFL * min(sblk.dx)
-    cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)     # warm-up
+    cons0, prim0 = cons, sprim
+    cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)     # warm-up, and the reference step
+    gg = G.Grid(sblk.n, 3, sblk.dx)
+    inner = (slice(None),) + tuple(slice(3, -3) for _ in range(3))
+    accuracy = {"sample": f"one SSP-RK3 step of the {sub}^3 sub-block",
+                "fields": ["D", "S_x", "S_y", "S_z", "tau", "B^x", "B^y", "B^z"]}
+    for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
+        tc = torch.from_numpy(cons0).cuda()
+        tp = torch.from_numpy(prim0).cuda()
+        G.rk_step(gg, dataclasses.replace(gp, precision=prec), G.RK3, dt, tc, tp, torch.from_numpy(smet).cuda(),
+                  None, G.workspace(gg, G.RK3))
+        c = tc.cpu().numpy()[inner]
+        ref = cons[inner]
+        err = [float(np.abs(c[q] - ref[q]).max() / np.abs(ref[q]).max()) for q in range(8)]
+        accuracy[name] = {"max_rel_err_per_field": err, "max": max(err)}
     steps, t = 0, 0.0
     t0 = time.perf_counter()
     while t < seconds_target and steps < 400:
@@ -181,6 +200,7 @@ def cpu_baseline_sample(seconds_target=15.0):
         "value": steps * sblk.ncells / t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
         "sample": f"{steps} SSP-RK3 steps of a {sub}^3 sub-block of the same Schwarzschild workload "
                   f"({t:.1f} s of CPU work, {nthreads} OpenMP threads)",
+        "accuracy_vs_oracle": accuracy,
     }
 
 
@@ -734,7 +754,7 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_sample()
+        cpu = cpu_baseline_sample(G)
     line = {
         "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -110,12 +110,14 @@ __device__ __forceinline__ bool c2p_root_physical(const C2PIn& in, const DevPara
 // Newman-Hamlin iteration over the pressure (Sec. 2.3, the paper's fallback
 // "Newman's method"): with E = tau + D, a = E + P + B^2/2 and
 // d = (B^2 S^2 - (B.S)^2)/2, the energy and momentum equations give
-// eps^3 - a eps^2 + d = 0 for eps = B^2 + z, whose physical root is the
-// largest, eps = a/3 + (2a/3) cos(acos(1 - 27 d / (2 a^3)) / 3); then
-// v^2(z) from the momentum equation and the Gamma-law pressure of (z, W)
-// give the next P.  The fixed point is accelerated by Aitken's delta-squared
-// extrapolation every third iterate.  Returns true with (z, W) when the
-// pressure changes by at most nr_tol (relative) within 3 * nr_maxit steps.
+// f(eps) = eps^3 - a eps^2 + d = 0 for eps = B^2 + z, whose physical root is
+// the largest.  f(a) = d >= 0 and f is increasing and convex above 2a/3, so
+// Newton's iteration on f from eps = a descends monotonically onto it (no
+// trigonometric closed form needed); then v^2(z) from the momentum equation
+// and the Gamma-law pressure of (z, W) give the next P.  The fixed point is
+// accelerated by Aitken's delta-squared extrapolation every third iterate.
+// Returns true with (z, W) when the pressure changes by at most nr_tol
+// (relative) within 3 * nr_maxit steps.
 static __device__ bool c2p_newman_hamlin(const C2PIn& in, const DevParams& p, double P, double& z, double& W) {
   const double E = in.tau + in.D;
   const double d = fmax(0.5 * (in.B2 * in.S2 - in.BS2), 0.0);  // >= 0 (Cauchy-Schwarz) up to round-off
@@ -123,11 +125,15 @@ static __device__ bool c2p_newman_hamlin(const C2PIn& in, const DevParams& p, do
   const int maxit = 3 * p.nr_maxit;
   for (int it = 0; it < maxit; ++it) {
     const double a = E + P + 0.5 * in.B2;
-    if (!(a > 0.0)) return false;
-    const double ia3 = 1.0 / (a * a * a);
-    const double r = 1.0 - 13.5 * d * ia3;
-    if (!(r >= -1.0)) return false;  // d > 4 a^3 / 27: no root above 2a/3
-    const double eps = a * (1.0 / 3.0) + (a * (2.0 / 3.0)) * cos(acos(fmin(r, 1.0)) * (1.0 / 3.0));
+    if (!(a > 0.0) || !(27.0 * d <= 4.0 * a * a * a)) return false;  // no root above 2a/3
+    double eps = a;
+    for (int k = 0; k < 60; ++k) {
+      const double fe = eps * eps * (eps - a) + d;
+      const double de = eps * fma(3.0, eps, -2.0 * a);
+      const double step = fe / de;
+      eps -= step;
+      if (!(fabs(step) > 1e-16 * eps)) break;
+    }
     const double zz = eps - in.B2;
     if (!(zz > 0.0)) return false;
     const double v2 = c2p_v2_of_z(in, zz);

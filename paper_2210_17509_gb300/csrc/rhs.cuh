@@ -203,28 +203,45 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
                                                  int dir, long long stride, T pL[8], T pR[8], T F[8]) {
   Geom<T> m;
   if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
-  // the check's lowered velocity and v^2 feed the side states
-  T vlL[3], vlR[3], v2L, v2R;
-  if (!physical_state_v<T, CURVED>(pL, m, vlL, v2L)) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
-    physical_state_v<T, CURVED>(pL, m, vlL, v2L);
-  }
-  if (!physical_state_v<T, CURVED>(pR, m, vlR, v2R)) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
-    physical_state_v<T, CURVED>(pR, m, vlR, v2R);
-  }
-  T rL[8], rR[8], Fr[8], rvL[3], rvR[3];
-  rotate_state(dir, pL, rL);
-  rotate_state(dir, pR, rR);
-  rotate_vec(dir, vlL, rvL);
-  rotate_vec(dir, vlR, rvR);
-  if (CURVED) rotate_metric(dir, m);
+  T rL[8], rR[8], Fr[8];
   Side<T> L, R;
   const T ia = CURVED ? T(1) / m.alpha : T(1);  // shared by both sides
-  side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia, rvL, v2L);
-  side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia, rvR, v2R);
+  if constexpr (sizeof(T) == 8) {
+    // FP64 (pipe bound): the check's lowered velocity and v^2 feed the side states
+    T vlL[3], vlR[3], v2L, v2R, rvL[3], rvR[3];
+    if (!physical_state_v<T, CURVED>(pL, m, vlL, v2L)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+      physical_state_v<T, CURVED>(pL, m, vlL, v2L);
+    }
+    if (!physical_state_v<T, CURVED>(pR, m, vlR, v2R)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+      physical_state_v<T, CURVED>(pR, m, vlR, v2R);
+    }
+    rotate_state(dir, pL, rL);
+    rotate_state(dir, pR, rR);
+    rotate_vec(dir, vlL, rvL);
+    rotate_vec(dir, vlR, rvR);
+    if (CURVED) rotate_metric(dir, m);
+    side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia, rvL, v2L);
+    side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia, rvR, v2R);
+  } else {
+    // FP32 (latency bound, 80 registers): fewer values live across the rotation
+    if (!physical_state<T, CURVED>(pL, m)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+    }
+    if (!physical_state<T, CURVED>(pR, m)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+    }
+    rotate_state(dir, pL, rL);
+    rotate_state(dir, pR, rR);
+    if (CURVED) rotate_metric(dir, m);
+    side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia);
+    side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia);
+  }
   finish_speeds<T, CURVED, 0>(m, L, R);
   hlle_combine_scaled<T>(L, R, CURVED ? m.alpha : T(1), CURVED ? m.sqrtg : T(1), Fr);
   unrotate_flux(dir, Fr, F);
