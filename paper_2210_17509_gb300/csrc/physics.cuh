@@ -36,30 +36,12 @@ __device__ __forceinline__ T minmod(T a, T b) {
 }
 
 // WENO5 (Jiang-Shu indicators, linear weights 1/10, 6/10, 3/10): value at
-// the face i+1/2 from the cell values i-2 .. i+2.  The double version forms
-// the weights as d_k prod_{j != k} (eps + beta_j)^2 over their sum, which
-// needs a single division; the float version uses the textbook reciprocals
-// so that the squared products cannot overflow.
+// the face i+1/2 from the cell values i-2 .. i+2 (FP32, per face; the FP64
+// paths use weno5_parts and weno5_cell_parts).  The weights use the textbook
+// reciprocals so that the squared products cannot overflow in single
+// precision.
 template <class T>
 __device__ __forceinline__ T weno5(T um2, T um1, T u0, T up1, T up2, T eps);
-
-template <>
-__device__ __forceinline__ double weno5<double>(double um2, double um1, double u0, double up1, double up2,
-                                                double eps) {
-  const double c6 = 1.0 / 6.0, c1312 = 13.0 / 12.0;
-  const double q0 = (2.0 * um2 - 7.0 * um1 + 11.0 * u0) * c6;
-  const double q1 = (-um1 + 5.0 * u0 + 2.0 * up1) * c6;
-  const double q2 = (2.0 * u0 + 5.0 * up1 - up2) * c6;
-  const double t0 = um2 - 2.0 * um1 + u0, s0 = um2 - 4.0 * um1 + 3.0 * u0;
-  const double t1 = um1 - 2.0 * u0 + up1, s1 = um1 - up1;
-  const double t2 = u0 - 2.0 * up1 + up2, s2 = 3.0 * u0 - 4.0 * up1 + up2;
-  const double e0 = eps + (c1312 * t0 * t0 + 0.25 * s0 * s0);
-  const double e1 = eps + (c1312 * t1 * t1 + 0.25 * s1 * s1);
-  const double e2 = eps + (c1312 * t2 * t2 + 0.25 * s2 * s2);
-  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
-  const double w0 = 0.1 * p12 * p12, w1 = 0.6 * p02 * p02, w2 = 0.3 * p01 * p01;
-  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
-}
 
 template <>
 __device__ __forceinline__ float weno5<float>(float um2, float um1, float u0, float up1, float up2, float eps) {
@@ -492,8 +474,10 @@ __device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side
   R.lm = iR * R.lm - bd;
 }
 
-// HLLE flux from SCALED side states: F = sqrt(gamma) [alpha (xp F~L - xm F~R)
-// + xp xm (U~R - U~L)] / (xp - xm), the common factors applied once.
+// HLLE flux (Sec. 2.3) from SCALED side states: F = sqrt(gamma) [alpha (xp F~L
+// - xm F~R) + xp xm (U~R - U~L)] / (xp - xm), the common factors applied once;
+// 1e-300 (double) / 1e-30 (float) guards the degenerate fan xi+ = xi- = 0
+// with the mean physical flux.
 template <class T>
 __device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side<T>& R, T alpha, T sg, T F[8]) {
   const T xm = xmin(T(0), xmin(L.lm, R.lm));
@@ -512,23 +496,5 @@ __device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side
   for (int q = 0; q < 8; ++q) F[q] = (axp * L.F[q] - axm * R.F[q] + xpm * (R.U[q] - L.U[q])) * s;
 }
 
-// HLLE flux (Sec. 2.3) from the two sides; 1e-300 (double) / 1e-30 (float)
-// guards the degenerate fan xi+ = xi- = 0 with the mean physical flux.
-template <class T>
-__device__ __forceinline__ void hlle_combine(const Side<T>& L, const Side<T>& R, T F[8]) {
-  const T xm = xmin(T(0), xmin(L.lm, R.lm));
-  const T xp = xmax(T(0), xmax(L.lp, R.lp));
-  const T den = xp - xm;
-  const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
-  if (den < tiny) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) F[q] = T(0.5) * (L.F[q] + R.F[q]);
-    return;
-  }
-  const T inv = T(1) / den;
-  const T xpm = xp * xm;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) F[q] = (xp * L.F[q] - xm * R.F[q] + xpm * (R.U[q] - L.U[q])) * inv;
-}
 
 }  // namespace grmhd

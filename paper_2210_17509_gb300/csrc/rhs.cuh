@@ -6,7 +6,12 @@
 // TX (TY+1) TZ y-faces, TX TY (TZ+1) z-faces, one flat list spread over all
 // threads -- into shared memory (SoA [comp][face], conflict-free), then each
 // thread differences the six faces of its cell, adds the Eq. 13 source
-// (3+1 form, curved metric only) and applies the stage epilogue.
+// (3+1 form, curved metric only) and applies the stage epilogue.  For FP64
+// WENO5 the reconstruction runs per cell before the face pass: every cell of
+// the tile extended by one along each direction forms its face states from
+// one stencil into a shared-memory stage, which the faces then read.  One
+// face routine serves all three directions, the states, metric and flux
+// being relabelled so that the face normal is the first axis.
 #pragma once
 
 #include "physics.cuh"
