@@ -190,3 +190,16 @@ def test_amr2_step_validation_and_workspace(lib):
     assert step((2, 2, 2, 9, 9, 9), ws_bytes=b - 8) == -4
     mixed = lib.Params(precision=lib.MIXED).c()
     assert step((2, 2, 2, 9, 9, 9), params=mixed) == -1   # the composite step is FP64 only
+
+
+def test_rejects_empty_and_oversized_grids(lib):
+    """Empty, negative, too-large and too-many-ghost grids fail validation before any launch."""
+    p = lib.Params(recon=lib.MINMOD).c()
+    for n, ng in (((0, 8, 8), 3), ((8, -1, 8), 3), ((8, 8, (1 << 20) + 1), 3), ((1 << 14, 1 << 14, 1 << 14), 3),
+                  ((8, 8, 8), 17)):
+        g = lib.Grid(n, ng, (0.1, 0.1, 0.1)).c()
+        assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1, n
+        assert lib._lib.grmhd_fill_ghosts(ctypes.byref(g), 0, 8, FAKE, None) == -1, n
+        assert lib._lib.grmhd_rk_workspace_bytes(ctypes.byref(g), lib.RK3) == 0, n
+    g = lib.Grid((8, 8, 8), 3, (0.1, 0.0, 0.1)).c()     # zero spacing
+    assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1
