@@ -83,6 +83,10 @@ def _load():
         lib.oracle_loss_jvp.restype = I
         lib.oracle_con2prim_nh_point.argtypes = [P, pp, Dd, P]
         lib.oracle_con2prim_nh_point.restype = I
+        lib.oracle_ct_rate.argtypes = [P, I, P, pp, P, P, P]
+        lib.oracle_ct_divergence.argtypes = [P, I, P, P, P]
+        lib.oracle_ct_rk_step.argtypes = [P, I, P, pp, I, Dd, P, P, P, P]
+        lib.oracle_ct_rk_step.restype = I
         lib.oracle_restrict.argtypes = [P, I, P, P, P, I, P, P, P, I]
         lib.oracle_prolongate.argtypes = [P, I, P, P, P, I, P, P, P, I, I]
         lib.oracle_reflux.argtypes = [P, I, P, pp, P, P, P, I, P, P, P, P, Dd, P]
@@ -332,4 +336,31 @@ def amr2_step(coarse_grid: Grid, params: OParams, scheme: int, dt: float, ccons,
                                      int(scheme), float(dt), _ptr(ccons), _ptr(cprim), _ptr(_f64(coarse_metric)),
                                      nf, fn, fdx, pc, pp_, pm, lo)
     return ccons, cprim, fcons, fprim, nfail
+
+
+# ------------------------------------------ constrained transport (R19) --
+def ct_rate(grid: Grid, params: OParams, prim, metric=None):
+    """Rate of change of the face field (3 x ncell): minus the discrete curl of the edge field."""
+    prim = _f64(prim)
+    out = np.zeros((3,) + grid.shape)
+    _load().oracle_ct_rate(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(prim), _ptr(_f64(metric)),
+                           _ptr(out))
+    return out
+
+
+def ct_divergence(grid: Grid, bface):
+    bface = _f64(bface)
+    out = np.zeros(grid.shape)
+    _load().oracle_ct_divergence(grid._n, grid.ng, grid._dx, _ptr(bface), _ptr(out))
+    return out
+
+
+def ct_rk_step(grid: Grid, params: OParams, scheme: int, dt: float, cons, prim, bface, metric=None):
+    """One step with constrained transport (R19); returns (cons, prim, bface, nfail)."""
+    cons = np.array(cons, dtype=np.float64, copy=True)
+    prim = np.array(prim, dtype=np.float64, copy=True)
+    bface = np.array(bface, dtype=np.float64, copy=True)
+    nfail = _load().oracle_ct_rk_step(grid._n, grid.ng, grid._dx, ctypes.byref(params), int(scheme), float(dt),
+                                      _ptr(cons), _ptr(prim), _ptr(bface), _ptr(_f64(metric)))
+    return cons, prim, bface, nfail
 

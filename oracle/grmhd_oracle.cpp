@@ -58,6 +58,16 @@
 //      pressure of (z, W) is the next iterate.  Plain fixed point here; the
 //      GPU path accelerates it (Aitken) and uses it as the fallback of its
 //      Newton iteration.
+//   R19 constrained transport (Sec. 3, staggered grids: the vector potential
+//      on cell edges keeps div B zero to round-off; used by the rotor and
+//      explosion tests and the TOV star): the densitised field lives on cell
+//      faces (component a on the a-faces) and is the discrete curl of an
+//      edge potential at the start; every stage changes it by minus the
+//      discrete curl of the edge electric field E, each E_c the mean of the
+//      four face fluxes of the field around its edge (E_c = -F_a(B^b) =
+//      F_b(B^a) for (c, a, b) cyclic; Balsara & Spicer's averaging).  The
+//      cell-centred field that the rest of the scheme sees is the mean of
+//      the two faces along its direction.
 //   Two-level block AMR without subcycling (Sec. 3: refined grids halve the
 //   spacing, are properly nested, share one global time step; ghost zones
 //   of a refined grid are filled by prolongation from the next coarser
@@ -939,6 +949,142 @@ int rk_step_block(const Grid& G, const Par<S>& p, int scheme, double dt, S* cons
   return nfail;
 }
 
+// ---------------------------------------- constrained transport (R19) --
+// Face field bface[a * ncell + idx]: component a on the lower a-face of
+// cell idx (array indices, ghosts included); the interior faces have
+// a-index ng .. ng + n_a and interior transverse indices.
+
+// Rate of change of the face field: -curl E on every interior face.
+template <class S>
+void ct_rate(const Grid& G, const Par<S>& p, const S* prim, const double* metric, S* dbdt) {
+  const int g = G.ng;
+  const long st[3] = {1, G.N[0], (long)G.N[0] * G.N[1]};
+  // face fluxes of the field components: Fb[(3 d + comp) * ncell + idx] = F_d(B^comp) on the lower
+  // d-face of cell idx, for d-index g .. g + n_d and transverse indices g - 1 .. g + n
+  std::vector<S> Fb((size_t)9 * G.ncell, S(0.0));
+  for (int d = 0; d < 3; ++d) {
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+      lo[e] = e == d ? g : g - 1;
+      hi[e] = g + G.n[e];
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          S F[8];
+          face_flux(G, p, prim, metric, d, i, j, k, F);
+          for (int c = 0; c < 3; ++c) Fb[(3 * d + c) * G.ncell + G.at(i, j, k)] = F[5 + c];
+        }
+  }
+  // edge fields: E[c * ncell + idx] on the c-edge at the corner of cell idx that is lower in a and b,
+  // (c, a, b) cyclic: E_c = (-F_a(B^b)[idx - e_b] - F_a(B^b)[idx] + F_b(B^a)[idx - e_a] + F_b(B^a)[idx]) / 4
+  std::vector<S> E((size_t)3 * G.ncell, S(0.0));
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    for (int k = g; k <= g + G.n[2]; ++k)
+      for (int j = g; j <= g + G.n[1]; ++j)
+        for (int i = g; i <= g + G.n[0]; ++i) {
+          const long x = G.at(i, j, k);
+          const S* Fab = Fb.data() + (3 * a + b) * G.ncell;
+          const S* Fba = Fb.data() + (3 * b + a) * G.ncell;
+          E[c * G.ncell + x] = 0.25 * (-Fab[x - st[b]] - Fab[x] + Fba[x - st[a]] + Fba[x]);
+        }
+  }
+  // d B^a / dt = -(E_c[idx + e_b] - E_c[idx]) / dx_b + (E_b[idx + e_c] - E_b[idx]) / dx_c, (a, b, c) cyclic
+  for (long x = 0; x < 3 * G.ncell; ++x) dbdt[x] = S(0.0);
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    int hi[3] = {g + G.n[0] - 1, g + G.n[1] - 1, g + G.n[2] - 1};
+    hi[a] = g + G.n[a];
+    for (int k = g; k <= hi[2]; ++k)
+      for (int j = g; j <= hi[1]; ++j)
+        for (int i = g; i <= hi[0]; ++i) {
+          const long x = G.at(i, j, k);
+          const S* Ec = E.data() + c * G.ncell;
+          const S* Eb = E.data() + b * G.ncell;
+          dbdt[a * G.ncell + x] = -(Ec[x + st[b]] - Ec[x]) / G.dx[b] + (Eb[x + st[c]] - Eb[x]) / G.dx[c];
+        }
+  }
+}
+
+// Cell-centred densitised field of the interior cells := mean of the two faces.
+template <class S>
+void ct_face_to_cell(const Grid& G, const S* bface, S* cons) {
+  const long st[3] = {1, G.N[0], (long)G.N[0] * G.N[1]};
+  for (int k = G.ng; k < G.ng + G.n[2]; ++k)
+    for (int j = G.ng; j < G.ng + G.n[1]; ++j)
+      for (int i = G.ng; i < G.ng + G.n[0]; ++i) {
+        const long x = G.at(i, j, k);
+        for (int a = 0; a < 3; ++a)
+          cons[(5 + a) * G.ncell + x] = 0.5 * (bface[a * G.ncell + x] + bface[a * G.ncell + x + st[a]]);
+      }
+}
+
+// Discrete divergence of the face field on the interior cells.
+template <class S>
+void ct_divergence(const Grid& G, const S* bface, S* div) {
+  const long st[3] = {1, G.N[0], (long)G.N[0] * G.N[1]};
+  for (long x = 0; x < G.ncell; ++x) div[x] = S(0.0);
+  for (int k = G.ng; k < G.ng + G.n[2]; ++k)
+    for (int j = G.ng; j < G.ng + G.n[1]; ++j)
+      for (int i = G.ng; i < G.ng + G.n[0]; ++i) {
+        const long x = G.at(i, j, k);
+        S dv = S(0.0);
+        for (int a = 0; a < 3; ++a) dv = dv + (bface[a * G.ncell + x + st[a]] - bface[a * G.ncell + x]) / G.dx[a];
+        div[x] = dv;
+      }
+}
+
+// One SSP-RK2 / SSP-RK3 / RK4 step with constrained transport: the fluid
+// variables as in rk_step_block, the face field by the same stage formulas
+// with ct_rate, the cell field taken from the faces before every recovery.
+template <class S>
+int ct_rk_step_block(const Grid& G, const Par<S>& p, int scheme, double dt, S* cons, S* prim, S* bface,
+                     const double* metric) {
+  const long n8 = 8 * G.ncell, n3 = 3 * G.ncell;
+  std::vector<S> U0(cons, cons + n8), L(n8), acc(n8, S(0.0));
+  std::vector<S> B0(bface, bface + n3), dB(n3), accB(n3, S(0.0));
+  int nfail = 0;
+  const int nstage = scheme == RK2 ? 2 : (scheme == RK3 ? 3 : 4);
+  auto update = [&](S* u, const S* u0, const S* l, S* ac, long x, int s) {
+    if (scheme == RK2) {
+      u[x] = s == 0 ? u0[x] + dt * l[x] : 0.5 * u0[x] + 0.5 * (u[x] + dt * l[x]);
+    } else if (scheme == RK3) {
+      if (s == 0) u[x] = u0[x] + dt * l[x];
+      else if (s == 1) u[x] = 0.75 * u0[x] + 0.25 * (u[x] + dt * l[x]);
+      else u[x] = (1.0 / 3.0) * u0[x] + (2.0 / 3.0) * (u[x] + dt * l[x]);
+    } else {
+      const double cst[3] = {0.5, 0.5, 1.0}, wst[3] = {1.0, 2.0, 2.0};
+      if (s < 3) {
+        ac[x] = ac[x] + wst[s] * l[x];
+        u[x] = u0[x] + (cst[s] * dt) * l[x];
+      } else {
+        u[x] = u0[x] + (dt / 6.0) * (ac[x] + l[x]);
+      }
+    }
+  };
+  for (int s = 0; s < nstage; ++s) {
+    rhs_block(G, p, prim, metric, nullptr, L.data());
+    ct_rate(G, p, prim, metric, dB.data());
+    for (int k = G.ng; k < G.ng + G.n[2]; ++k)
+      for (int j = G.ng; j < G.ng + G.n[1]; ++j)
+        for (int i = G.ng; i < G.ng + G.n[0]; ++i)
+          for (int q = 0; q < 5; ++q) update(cons, U0.data(), L.data(), acc.data(), q * G.ncell + G.at(i, j, k), s);
+    for (int a = 0; a < 3; ++a) {
+      int hi[3] = {G.ng + G.n[0] - 1, G.ng + G.n[1] - 1, G.ng + G.n[2] - 1};
+      hi[a] = G.ng + G.n[a];
+      for (int k = G.ng; k <= hi[2]; ++k)
+        for (int j = G.ng; j <= hi[1]; ++j)
+          for (int i = G.ng; i <= hi[0]; ++i) update(bface, B0.data(), dB.data(), accB.data(), a * G.ncell + G.at(i, j, k), s);
+    }
+    ct_face_to_cell(G, (const S*)bface, cons);
+    nfail += con2prim_block(G, p, cons, metric, prim, (int8_t*)nullptr);
+    fill_ghosts_block(G, p.bc, 8, prim);
+  }
+  return nfail;
+}
+
 // --------------------------------------------- two-level AMR (R14-R17) --
 // A fine block at placement lo: its interior cell i (0-based, ghosts i < 0
 // or i >= n) lies in the coarse interior cell lo + floor(i / 2) along each
@@ -1290,6 +1436,24 @@ int oracle_loss_jvp(const int* n3, int ng, const double* dx3, const OParams* q, 
   *L = acc.v;
   *dL = acc.d[0];
   return nfail;
+}
+
+// Constrained transport (R19).  bface: 3 x ncell face field (see ct_rate).
+void oracle_ct_rate(const int* n3, int ng, const double* dx3, const OParams* q, const double* prim,
+                    const double* metric, double* dbdt) {
+  Grid G; G.init(n3, ng, dx3);
+  ct_rate<double>(G, to_par(q), prim, metric, dbdt);
+}
+
+void oracle_ct_divergence(const int* n3, int ng, const double* dx3, const double* bface, double* div) {
+  Grid G; G.init(n3, ng, dx3);
+  ct_divergence<double>(G, bface, div);
+}
+
+int oracle_ct_rk_step(const int* n3, int ng, const double* dx3, const OParams* q, int scheme, double dt,
+                      double* cons, double* prim, double* bface, const double* metric) {
+  Grid G; G.init(n3, ng, dx3);
+  return ct_rk_step_block<double>(G, to_par(q), scheme, dt, cons, prim, bface, metric);
 }
 
 // Two-level AMR transfer (R14-R17).  Fine grids carry placements lo[3].

@@ -287,3 +287,70 @@ def shocktube(test: int, n: int = 1600, axis: int = 0, transverse: int = 8, ng: 
             prim[5 + d][mask] = comp_b[k]
     return blk, prim, t["gamma"], t["t_ref"]
 
+
+
+def edge_potential(blk: Block, seed: int, shift=(0.0, 0.0, 0.0), nmodes=4):
+    """Random-mode vector potential sampled on cell edges: component c at
+    the c-edge through the corner of each cell that is lower in the other
+    two axes, shape [3][z][y][x].  `shift` displaces the pattern (the
+    potential at x is the pattern at x - shift), for advected references."""
+    rng = np.random.default_rng(np.random.Philox(seed))
+    modes = [_modes(rng, nmodes) for _ in range(3)]
+    xc, yc, zc = blk.centres()
+    A = np.zeros((3,) + blk.shape)
+    for c in range(3):
+        pos = [xc, yc, zc]
+        for e in range(3):
+            if e != c:
+                pos[e] = pos[e] - 0.5 * blk.dx[e]
+        ks, ph, amp = modes[c]
+        A[c] = _mode_field(blk, pos[0] - shift[0], pos[1] - shift[1], pos[2] - shift[2], ks, ph, amp)
+    return A
+
+
+def face_curl(blk: Block, A):
+    """Densitised face field as the discrete curl of an edge potential:
+    component a on the lower a-face of each cell,
+    B^a = (A_c[+e_b] - A_c) / dx_b - (A_b[+e_c] - A_b) / dx_c, (a, b, c)
+    cyclic (entries whose stencil leaves the array are 0).  Its discrete
+    divergence vanishes identically."""
+    B = np.zeros_like(A)
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        # array axes are (z, y, x): coordinate axis e is array axis 3 - e of A[.] (axis 2 - e of a field)
+        Ac, Ab = A[c], A[b]
+        dAc = np.zeros_like(Ac)
+        dAb = np.zeros_like(Ab)
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[2 - b] = slice(0, -1)
+        sl_hi[2 - b] = slice(1, None)
+        dAc[tuple(sl_lo)] = (Ac[tuple(sl_hi)] - Ac[tuple(sl_lo)]) / blk.dx[b]
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[2 - c] = slice(0, -1)
+        sl_hi[2 - c] = slice(1, None)
+        dAb[tuple(sl_lo)] = (Ab[tuple(sl_hi)] - Ab[tuple(sl_lo)]) / blk.dx[c]
+        B[a] = dAc - dAb
+    return B
+
+
+def ct_state(blk: Block, prim, bface, metric=None):
+    """Primitives whose field is the cell mean of the face field (divided by
+    sqrt(gamma) of the cell), for the interior and ghost cells that have both
+    faces; the other entries keep `prim`."""
+    prim = prim.copy()
+    sg = np.ones(blk.shape)
+    if metric is not None:
+        g = metric
+        det = (g[4] * (g[7] * g[9] - g[8] * g[8]) - g[5] * (g[5] * g[9] - g[8] * g[6])
+               + g[6] * (g[5] * g[8] - g[7] * g[6]))
+        sg = np.sqrt(det)
+    for a in range(3):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[2 - a] = slice(0, -1)
+        hi[2 - a] = slice(1, None)
+        cell = 0.5 * (bface[a][tuple(lo)] + bface[a][tuple(hi)])
+        prim[5 + a][tuple(lo)] = cell / sg[tuple(lo)]
+    return prim
