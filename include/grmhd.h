@@ -408,6 +408,62 @@ int grmhd_amr2_step(const grmhd_grid* coarse, const grmhd_params* params, int32_
                     const double* const* fine_metric, const int32_t* lo, void* ws, size_t ws_bytes,
                     int32_t* nfail, void* stream);
 
+/* ----------------------------------------------------------------------
+ * Constrained transport (Sec. 3: the magnetic field is evolved on staggered
+ * grids so that its divergence stays zero).
+ *
+ * Face field bface [3][z][y][x] (ghosts included): component a holds the
+ * densitised field sqrt(gamma) B^a on the lower a-face of each cell.  The
+ * interior a-faces have a-index ng .. ng + n_a and interior transverse
+ * indices; the step advances exactly those and reads no other entry.
+ * Edge field: E_c at the c-edge through the corner of a cell that is lower
+ * in a and b ((c, a, b) cyclic) is the mean of the four field fluxes of the
+ * faces meeting there, E_c = (-F_a(B^b)[-e_b] - F_a(B^b) + F_b(B^a)[-e_a]
+ * + F_b(B^a)) / 4, where F_d(B^a) is the B^a component of the HLLE flux of
+ * grmhd_rhs on a lower d-face.  Face rate: dB^a/dt = -(E_c[+e_b] - E_c)/dx_b
+ * + (E_b[+e_c] - E_b)/dx_c, (a, b, c) cyclic, which leaves the discrete
+ * divergence sum_a (B^a[+e_a] - B^a)/dx_a of every cell unchanged.
+ * The cell-centred field (conserved variables 5..7) is the mean of a cell's
+ * two faces.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of the field-flux register and the edge fields (9 + 3 ncell
+ * doubles, each part rounded up to 256 bytes); 0 if the grid is invalid. */
+size_t grmhd_ct_flux_bytes(const grmhd_grid* grid);
+
+/* Device workspace (bytes) of grmhd_ct_rk_step: the field-flux register and
+ * edge fields (grmhd_ct_flux_bytes), the step-start face field, (RK4) a face-rate accumulator, then the
+ * grmhd_rk_step workspace; the _cached size adds the geometry and primitive
+ * caches that grmhd_rk_workspace_bytes_cached adds.  0 if invalid. */
+size_t grmhd_ct_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
+size_t grmhd_ct_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme);
+
+/* Face rate dB^a/dt of every interior face (the formula above) into rate
+ * [3][ncell]; every other entry is set to 0.  prim has its ghosts filled;
+ * metric/kij as for grmhd_rhs.  ws: device scratch of at least
+ * grmhd_ct_flux_bytes, 256-byte aligned. */
+int grmhd_ct_rate(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+                  const double* kij, double* rate, void* ws, size_t ws_bytes, void* stream);
+
+/* One RK step (params precision) with constrained transport: the fluid
+ * variables exactly as grmhd_rk_step, the interior faces of bface by the
+ * same stage formulas with the face rate, and the field of cons (5..7) of
+ * every interior cell replaced by the mean of its faces before each
+ * recovery.  On entry prim is consistent with cons and has its ghosts
+ * filled (its field normally the face mean).  ws >= grmhd_ct_workspace_bytes
+ * (256-byte aligned; >= the _cached size takes the cached RHS paths as
+ * grmhd_rk_step does).  Returns GRMHD_ERR_SIZE for a short workspace and
+ * GRMHD_ERR_ARG for invalid arguments, before any launch. */
+int grmhd_ct_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
+                     double* prim, double* bface, const double* metric, const double* kij, void* ws,
+                     size_t ws_bytes, int32_t* nfail, void* stream);
+
+/* Discrete divergence of the face field: div [ncell] (nullable) gets
+ * sum_a (B^a[+e_a] - B^a)/dx_a on the interior cells and 0 elsewhere;
+ * maxabs (nullable, one device double) the largest |div| (a NaN shows as
+ * NaN).  At least one of div, maxabs. */
+int grmhd_ct_divergence(const grmhd_grid* grid, const double* bface, double* div, double* maxabs, void* stream);
+
 /* Human-readable name of a return code (static storage). */
 const char* grmhd_error_string(int code);
 

@@ -1116,6 +1116,7 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
     return GRMHD_ERR_CUDA;
   for (int k = 0; k < ns && !stage_prims; ++k) {
     StageEpilogue ep;
+    ep.fb = nullptr;
     ep.rhs = nullptr;
     ep.u = W;
     ep.u0 = cons;

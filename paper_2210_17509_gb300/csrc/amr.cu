@@ -129,21 +129,6 @@ __global__ void prolongate_kernel(DevGrid c, const double* __restrict__ coarse, 
   }
 }
 
-// Flux of the face between cell c - stride and cell c along dir, as the
-// RHS kernels compute it (per-face reconstruction).
-template <int RECON, bool CURVED>
-__device__ __forceinline__ void face_flux_one(const DevGrid& g, const DevParams& p, const double* prim,
-                                              const double* metric, long long c, int dir, double F[8]) {
-  SrcF64 src;
-  src.prim = prim;
-  src.metric = metric;
-  src.kij = nullptr;
-  const long long stride = dir == 0 ? 1 : (dir == 1 ? g.sy : g.sz);
-  double pL[8], pR[8];
-  reconstruct_face<double, RECON, SrcF64>(src, g.ncell, c, stride, p.weno_eps, pL, pR);
-  face_flux_states<double, CURVED, SrcF64>(g, p, src, c, dir, stride, pL, pR, F);
-}
-
 // Interface faces: kFacesPerBlock coarse faces per CTA, five flux
 // evaluations each (the coarse face, then its four fine faces) on five
 // threads; the fluxes meet in shared memory and are combined in a fixed

@@ -174,7 +174,7 @@ namespace {
 // also copied to record + k * 8 * ncell (k = 0 .. stages-1).
 int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
                  double* prim, const double* metric, const double* kij, void* ws, size_t ws_bytes, int32_t* nfail,
-                 void* stream, double* record) {
+                 void* stream, double* record, const CtStep* ct = nullptr) {
   int e = check_params(params);
   if (e) return e;
   if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
@@ -235,24 +235,39 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     ep.ca = st[k].ca;
     ep.wa = st[k].wa;
     ep.wr = st[k].wr;
+    ep.fb = ct ? ct->fb : nullptr;
     if (fast_fp64) {
       if (launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;
-      if (launch_con2prim_cached(g, p, cons, metric, mcache, prim, nfail, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-      if (launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     } else if (fast_mixed) {
       if (launch_rhs_mixed_cached(g, p, prim32, static_cast<const float*>(geom), kij, metric != nullptr, ep, s) !=
           cudaSuccess)
         return GRMHD_ERR_CUDA;
+    } else if (launch_rhs(g, p, prim, metric, kij, ep, s) != cudaSuccess) {
+      return GRMHD_ERR_CUDA;
+    }
+    // constrained transport: the face update by the curl of the edge field,
+    // and the cell field as the mean of the faces (replacing the cell-centred
+    // field update of the epilogue) before the recovery
+    if (ct) {
+      if (launch_ct_faces(g, ct->fb, ct->E, nullptr, ct->b, ct->b0, st[k].acc_in ? ct->acc : nullptr,
+                          st[k].acc_out ? ct->acc : nullptr, st[k].c0, st[k].c1, st[k].cr, st[k].ca, st[k].wa,
+                          st[k].wr, s) != cudaSuccess)
+        return GRMHD_ERR_CUDA;
+      if (launch_ct_face_to_cell(g, ct->b, cons, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    }
+    if (fast_fp64) {
+      if (launch_con2prim_cached(g, p, cons, metric, mcache, prim, nfail, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    } else if (fast_mixed) {
       // the FP64 primitives are needed after the last stage (and when recording)
       const bool result64 = k == ns - 1 || record;
       if (launch_con2prim_mixed(g, p, cons, metric, prim, prim32, metric ? mcache : nullptr,
                                 metric ? static_cast<const float*>(geom) : nullptr, result64, nfail, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;
       if (launch_fill_ghosts_f32(g, p.bc, 8, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-      if ((k == ns - 1 || record) && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+      if (result64 && launch_fill_ghosts(g, p.bc, 8, prim, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     } else {
-      if ((ce = launch_rhs(g, p, prim, metric, kij, ep, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
       if ((ce = launch_con2prim(g, p, cons, metric, prim, nullptr, nfail, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
       if ((ce = launch_fill_ghosts(g, p.bc, 8, prim, s)) != cudaSuccess) return GRMHD_ERR_CUDA;
     }
@@ -278,6 +293,108 @@ int grmhd_rk_step_record(const grmhd_grid* grid, const grmhd_params* params, int
                          size_t ws_bytes, double* stage_prims, int32_t* nfail, void* stream) {
   if (!stage_prims || !aligned8(stage_prims)) return GRMHD_ERR_ARG;
   return rk_step_impl(grid, params, scheme, dt, cons, prim, metric, kij, ws, ws_bytes, nfail, stream, stage_prims);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ constrained transport --
+
+namespace {
+
+// Field-flux register plus the edge fields.
+size_t ct_flux_bytes(const DevGrid& g) {
+  return round256((size_t)9 * g.ncell * sizeof(double)) + round256((size_t)3 * g.ncell * sizeof(double));
+}
+
+// Bytes of the CT part of the step workspace: field fluxes, edge fields, the
+// step-start face field and (RK4) the face-rate accumulator.
+size_t ct_part_bytes(const DevGrid& g, int32_t scheme) {
+  const size_t face = round256((size_t)3 * g.ncell * sizeof(double));
+  return ct_flux_bytes(g) + face + (scheme == GRMHD_RK4 ? face : 0);
+}
+
+double* ct_edges_of(const DevGrid& g, void* ws) {
+  return reinterpret_cast<double*>(static_cast<char*>(ws) + round256((size_t)9 * g.ncell * sizeof(double)));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t grmhd_ct_flux_bytes(const grmhd_grid* grid) {
+  if (check_grid(grid, 0)) return 0;
+  return ct_flux_bytes(make_grid(*grid));
+}
+
+size_t grmhd_ct_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
+  const size_t rk = grmhd_rk_workspace_bytes(grid, scheme);
+  return rk ? ct_part_bytes(make_grid(*grid), scheme) + rk : 0;
+}
+
+size_t grmhd_ct_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme) {
+  const size_t rk = grmhd_rk_workspace_bytes_cached(grid, scheme);
+  return rk ? ct_part_bytes(make_grid(*grid), scheme) + rk : 0;
+}
+
+int grmhd_ct_rate(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
+                  const double* kij, double* rate, void* ws, size_t ws_bytes, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
+  if (!prim || !rate || !ws || !aligned8(prim) || !aligned8(rate)) return GRMHD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  if ((metric && !aligned8(metric)) || (kij && !aligned8(kij)) || (kij && !metric)) return GRMHD_ERR_ARG;
+  if (ws_bytes < grmhd_ct_flux_bytes(grid)) return GRMHD_ERR_SIZE;
+  const DevGrid g = make_grid(*grid);
+  const DevParams p = make_params(*params);
+  cudaStream_t s = (cudaStream_t)stream;
+  double* fb = static_cast<double*>(ws);
+  StageEpilogue ep = no_epilogue();
+  ep.fb = fb;
+  if (launch_rhs(g, p, prim, metric, kij, ep, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemsetAsync(rate, 0, (size_t)3 * g.ncell * sizeof(double), s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  return cuda_status(
+      launch_ct_faces(g, fb, ct_edges_of(g, ws), rate, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0, 0, 0, s));
+}
+
+int grmhd_ct_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt, double* cons,
+                     double* prim, double* bface, const double* metric, const double* kij, void* ws,
+                     size_t ws_bytes, int32_t* nfail, void* stream) {
+  int e = check_params(params);
+  if (e) return e;
+  if ((e = check_grid(grid, min_ghosts(params, metric)))) return e;
+  if (scheme != GRMHD_RK2 && scheme != GRMHD_RK3 && scheme != GRMHD_RK4) return GRMHD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return GRMHD_ERR_ARG;
+  if (!cons || !prim || !bface || !aligned8(cons) || !aligned8(prim) || !aligned8(bface)) return GRMHD_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
+  if ((metric && !aligned8(metric)) || (kij && !aligned8(kij)) || (kij && !metric)) return GRMHD_ERR_ARG;
+  if (nfail && (reinterpret_cast<uintptr_t>(nfail) & 3u)) return GRMHD_ERR_ARG;
+  if (ws_bytes < grmhd_ct_workspace_bytes(grid, scheme)) return GRMHD_ERR_SIZE;
+  const DevGrid g = make_grid(*grid);
+  const size_t part = ct_part_bytes(g, scheme);
+  char* base = static_cast<char*>(ws);
+  CtStep ct;
+  ct.fb = reinterpret_cast<double*>(base);
+  ct.E = ct_edges_of(g, ws);
+  ct.b = bface;
+  double* b0 = reinterpret_cast<double*>(base + ct_flux_bytes(g));
+  ct.b0 = b0;
+  ct.acc = scheme == GRMHD_RK4 ? reinterpret_cast<double*>(base + ct_flux_bytes(g) +
+                                                           round256((size_t)3 * g.ncell * sizeof(double)))
+                               : nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(b0, bface, (size_t)3 * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return rk_step_impl(grid, params, scheme, dt, cons, prim, metric, kij, base + part, ws_bytes - part, nfail, stream,
+                      nullptr, &ct);
+}
+
+int grmhd_ct_divergence(const grmhd_grid* grid, const double* bface, double* div, double* maxabs, void* stream) {
+  const int e = check_grid(grid, 1);
+  if (e) return e;
+  if (!bface || !aligned8(bface) || (div && !aligned8(div)) || (maxabs && !aligned8(maxabs)) || (!div && !maxabs))
+    return GRMHD_ERR_ARG;
+  return cuda_status(launch_ct_divergence(make_grid(*grid), bface, div, maxabs, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -42,9 +42,14 @@ struct DevParams {
 //   u       != NULL: u[cell] = c0 * u0[cell] + c1 * u[cell] + cr * r
 //                              (+ ca * acc_in[cell] if acc_in != NULL)
 //   acc_out != NULL: acc_out[cell] = wr * r (+ wa * acc_in[cell] if acc_in != NULL)
+//   fb      != NULL: fb[(3 d + a) * ncell + cell] = the flux of the field
+//                    component B^a through the lower d-face of the cell, for
+//                    the d-faces 0 .. n_d with transverse indices -1 .. n
+//                    (the tiles, then a ring kernel; constrained transport)
 // u0 must be valid whenever u is set.
 struct StageEpilogue {
   double* rhs;
+  double* fb;
   double* u;
   const double* u0;
   const double* acc_in;
@@ -129,6 +134,7 @@ inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 inline StageEpilogue no_epilogue() {
   StageEpilogue e;
   e.rhs = nullptr;
+  e.fb = nullptr;
   e.u = nullptr;
   e.u0 = nullptr;
   e.acc_in = nullptr;
@@ -163,6 +169,22 @@ inline int rk_stages(int scheme, double dt, RkStage st[4]) {
   st[3] = {1.0, 0.0, dt / 6.0, dt / 6.0, 0, 0, true, false};
   return 4;
 }
+
+// Constrained transport (ct.cu); layouts of the face field b [3][ncell] and
+// of the field face fluxes fb [9][ncell] as in grmhd.h.
+struct CtStep {
+  double* fb;        // field face fluxes (filled by the RHS launch)
+  double* E;         // edge fields [3][ncell]
+  double* b;         // face field, advanced in place
+  const double* b0;  // face field at the start of the step
+  double* acc;       // RK4 accumulator of the face rates (NULL otherwise)
+};
+// Edge fields from fb into E [3][ncell], then the face rates / stage update.
+cudaError_t launch_ct_faces(const DevGrid& g, const double* fb, double* E, double* rate, double* b, const double* b0,
+                            const double* acc_in, double* acc_out, double c0, double c1, double cr, double ca,
+                            double wa, double wr, cudaStream_t s);
+cudaError_t launch_ct_face_to_cell(const DevGrid& g, const double* b, double* cons, cudaStream_t s);
+cudaError_t launch_ct_divergence(const DevGrid& g, const double* b, double* div, double* maxabs, cudaStream_t s);
 
 // Two-level AMR transfer (amr.cu).
 cudaError_t launch_restrict(const DevGrid& c, double* coarse, const DevGrid& f, const double* fine, const int lo[3],

@@ -489,6 +489,22 @@ constexpr size_t batch_smem_bytes() {
   return (size_t)(8 * kMaxTileFaces + 16 * batch_stage_entries<T, RECON>()) * sizeof(T);
 }
 
+// Flux of the face between cell c - stride and cell c along dir, as the
+// RHS kernels compute it with per-face reconstruction (used outside the
+// tiles: AMR interface faces, constrained-transport ring faces).
+template <int RECON, bool CURVED>
+__device__ __forceinline__ void face_flux_one(const DevGrid& g, const DevParams& p, const double* prim,
+                                              const double* metric, long long c, int dir, double F[8]) {
+  SrcF64 src;
+  src.prim = prim;
+  src.metric = metric;
+  src.kij = nullptr;
+  const long long stride = dir == 0 ? 1 : (dir == 1 ? g.sy : g.sz);
+  double pL[8], pR[8];
+  reconstruct_face<double, RECON, SrcF64>(src, g.ncell, c, stride, p.weno_eps, pL, pR);
+  face_flux_states<double, CURVED, SrcF64>(g, p, src, c, dir, stride, pL, pR, F);
+}
+
 // Face flux of face f (flat index over the NFX x-, NFY y- and NFZ z-faces of
 // the tile) into sF [8][NF].  With a stage, the face states come from sR
 // (stage index of the cell below the face: eoff[dir] + its index in that
@@ -560,6 +576,43 @@ __device__ __forceinline__ void tile_stage_item(const DevGrid& g, const S& src, 
     const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
     const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
     reconstruct_cell_pair<T, RECON, S>(src, g.ncell, c, stride, h, eps13, sR, ns, eoff + e, which);
+  }
+}
+
+// Constrained transport: the field components (5..7) of the tile's face
+// fluxes into fb [(3 d + a) * ncell + cell below-or-at the face], each face
+// written by one tile only (its lower faces, and the upper faces on the
+// block's upper boundaries).
+template <class T, int TX, int TY, int TZ>
+__device__ __noinline__ void tile_export_field_fluxes(const DevGrid& g, int x0, int y0, int z0,
+                                                      const T* __restrict__ sF, double* __restrict__ fb) {
+  constexpr int NFX = TileFaces<TX, TY, TZ>::NFX;
+  constexpr int NFY = TileFaces<TX, TY, TZ>::NFY;
+  constexpr int NF = TileFaces<TX, TY, TZ>::NF;
+  for (int f = threadIdx.x; f < NF; f += kTileThreads) {
+    int dir, fx, fy, fz;
+    if (f < NFX) {
+      dir = 0;
+      fx = f % (TX + 1); fy = (f / (TX + 1)) % TY; fz = f / ((TX + 1) * TY);
+    } else if (f < NFX + NFY) {
+      const int fl = f - NFX;
+      dir = 1;
+      fx = fl % TX; fy = (fl / TX) % (TY + 1); fz = fl / (TX * (TY + 1));
+    } else {
+      const int fl = f - NFX - NFY;
+      dir = 2;
+      fx = fl % TX; fy = (fl / TX) % TY; fz = fl / (TX * TY);
+    }
+    const int xi = x0 + fx, yi = y0 + fy, zi = z0 + fz;
+    const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
+    if (!(xi < g.n[0] + ux && yi < g.n[1] + uy && zi < g.n[2] + uz)) continue;
+    // the tile's upper face along dir belongs to the next tile unless it is the block's
+    const int fl = dir == 0 ? fx : (dir == 1 ? fy : fz);
+    const int tl = dir == 0 ? TX : (dir == 1 ? TY : TZ);
+    if (fl == tl && (dir == 0 ? xi : (dir == 1 ? yi : zi)) != g.n[dir]) continue;
+    const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fb[(3 * dir + a) * g.ncell + c] = (double)sF[(5 + a) * NF + f];
   }
 }
 
@@ -645,6 +698,8 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
     }
   }
 
+  if (ep.fb) tile_export_field_fluxes<T, TX, TY, TZ>(g, x0, y0, z0, sF, ep.fb);
+
 #pragma unroll 1
   for (int cl = threadIdx.x; cl < NC; cl += NT) {
   const int ci = cl % TX, cj = (cl / TX) % TY, ck = cl / (TX * TY);
@@ -680,6 +735,53 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
     }
   }
+  }
+}
+
+// Constrained transport: the field fluxes of the faces outside the tiles,
+// i.e. the d-faces (d-index 0 .. n_d) on the ring of ghost rows around the
+// block (transverse (A, B) on the border of -1 .. n_a by -1 .. n_b, a = d + 1,
+// b = d + 2 cyclic: the rows B = -1 and B = n_b, then the columns A = -1 and
+// A = n_a), from the same inputs as the tiles, into fb as the tiles write it.
+__host__ __device__ __forceinline__ long long ct_ring_faces(const DevGrid& g, int d) {
+  const int na = g.n[(d + 1) % 3], nb = g.n[(d + 2) % 3];
+  return (long long)(g.n[d] + 1) * (2LL * (na + 2) + 2LL * nb);
+}
+
+constexpr int kRingThreads = 128;
+
+template <class T, int RECON, bool CURVED, class S>
+__global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevParams p, S src,
+                                                               double* __restrict__ fb) {
+  const long long r0 = ct_ring_faces(g, 0), r1 = ct_ring_faces(g, 1), total = r0 + r1 + ct_ring_faces(g, 2);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int d = t < r0 ? 0 : (t < r0 + r1 ? 1 : 2);
+    const long long r = t - (d == 0 ? 0 : (d == 1 ? r0 : r0 + r1));
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    const int na = g.n[a], nb = g.n[b];
+    const long long per = 2LL * (na + 2) + 2LL * nb;
+    const int id = (int)(r / per);
+    const int m = (int)(r - id * per);
+    int A, B;
+    if (m < na + 2) {
+      A = m - 1; B = -1;
+    } else if (m < 2 * (na + 2)) {
+      A = m - (na + 2) - 1; B = nb;
+    } else if (m < 2 * (na + 2) + nb) {
+      A = -1; B = m - 2 * (na + 2);
+    } else {
+      A = na; B = m - 2 * (na + 2) - nb;
+    }
+    int I[3];
+    I[d] = id; I[a] = A; I[b] = B;
+    const long long c = (long long)(I[2] + g.ng) * g.sz + (long long)(I[1] + g.ng) * g.sy + (I[0] + g.ng);
+    const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+    T pL[8], pR[8], F[8];
+    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+    face_flux_states<T, CURVED, S>(g, p, src, c, d, stride, pL, pR, F);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) fb[(3 * d + q) * g.ncell + c] = (double)F[5 + q];
   }
 }
 
@@ -724,6 +826,13 @@ cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, co
   if (e != cudaSuccess) return e;
   const dim3 grid((g.n[0] + tx - 1) / tx, (g.n[1] + ty - 1) / ty, (g.n[2] + tz - 1) / tz);
   k<<<grid, kTileThreads, smem, s>>>(g, p, src, ep);
+  if (ep.fb) {
+    // the rest of the field-flux register: the ring faces
+    const long long nring = ct_ring_faces(g, 0) + ct_ring_faces(g, 1) + ct_ring_faces(g, 2);
+    long long blocks = (nring + kRingThreads - 1) / kRingThreads;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    ct_ring_kernel<T, RECON, CURVED, S><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
+  }
   return cudaGetLastError();
 }
 

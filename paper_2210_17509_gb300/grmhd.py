@@ -546,3 +546,74 @@ def amr2_step(coarse: Grid, params: Params, scheme: int, dt: float, coarse_cons,
                               ctypes.cast(pc, _P), ctypes.cast(pp_, _P), None if pm is None else ctypes.cast(pm, _P),
                               ctypes.cast(lo, _P), ctypes.c_void_p(ws.data_ptr()), ws.numel(), nf_ptr, _stream(stream))
     _check(rc, "grmhd_amr2_step")
+
+
+# ------------------------------------------------ constrained transport --
+_lib.grmhd_ct_flux_bytes.argtypes = [_pg]
+_lib.grmhd_ct_flux_bytes.restype = ctypes.c_size_t
+_lib.grmhd_ct_workspace_bytes.argtypes = [_pg, _I32]
+_lib.grmhd_ct_workspace_bytes.restype = ctypes.c_size_t
+_lib.grmhd_ct_workspace_bytes_cached.argtypes = [_pg, _I32]
+_lib.grmhd_ct_workspace_bytes_cached.restype = ctypes.c_size_t
+_lib.grmhd_ct_rate.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
+_lib.grmhd_ct_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
+_lib.grmhd_ct_divergence.argtypes = [_pg, _P, _P, _P, _P]
+C_SYMBOLS = C_SYMBOLS + ("grmhd_ct_flux_bytes", "grmhd_ct_workspace_bytes", "grmhd_ct_workspace_bytes_cached",
+                         "grmhd_ct_rate", "grmhd_ct_rk_step", "grmhd_ct_divergence")
+
+
+def ct_workspace(grid: Grid, scheme: int, device=None, cached: bool = True):
+    """Device workspace for ct_rk_step (by default large enough for the cached paths)."""
+    fn = _lib.grmhd_ct_workspace_bytes_cached if cached else _lib.grmhd_ct_workspace_bytes
+    nbytes = int(fn(ctypes.byref(grid.c()), scheme))
+    if nbytes == 0:
+        raise GrmhdError("invalid grid or scheme for the workspace")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def ct_rate(grid: Grid, params: Params, prim, metric=None, kij=None, out=None, ws=None, stream=None):
+    """grmhd_ct_rate: d(face field)/dt of the interior faces, [3][z][y][x]."""
+    if out is None:
+        out = torch.empty((3,) + grid.shape, dtype=torch.float64, device=prim.device)
+    if ws is None:
+        nbytes = int(_lib.grmhd_ct_flux_bytes(ctypes.byref(grid.c())))
+        if nbytes == 0:
+            raise GrmhdError("invalid grid for the workspace")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=prim.device)
+    rc = _lib.grmhd_ct_rate(ctypes.byref(grid.c()), ctypes.byref(params.c()), _field(prim, grid, 8, "prim"),
+                            _field(metric, grid, 10, "metric", True), _field(kij, grid, 6, "kij", True),
+                            _field(out, grid, 3, "rate"), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(rc, "grmhd_ct_rate")
+    return out
+
+
+def ct_rk_step(grid: Grid, params: Params, scheme: int, dt: float, cons, prim, bface, metric=None, kij=None,
+               ws=None, nfail=None, stream=None):
+    """grmhd_ct_rk_step: one step with constrained transport, in place on cons, prim and bface."""
+    if ws is None:
+        ws = ct_workspace(grid, scheme, cons.device)
+    nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+    rc = _lib.grmhd_ct_rk_step(ctypes.byref(grid.c()), ctypes.byref(params.c()), scheme, float(dt),
+                               _field(cons, grid, 8, "cons"), _field(prim, grid, 8, "prim"),
+                               _field(bface, grid, 3, "bface"), _field(metric, grid, 10, "metric", True),
+                               _field(kij, grid, 6, "kij", True), ctypes.c_void_p(ws.data_ptr()), ws.numel(), nf,
+                               _stream(stream))
+    _check(rc, "grmhd_ct_rk_step")
+    return cons, prim, bface
+
+
+def ct_divergence(grid: Grid, bface, div=None, maxabs=None, stream=None):
+    """grmhd_ct_divergence: the discrete divergence [z][y][x] (interior; 0 elsewhere) and/or
+    its largest magnitude (a one-element device tensor).  Returns (div, maxabs)."""
+    if div is None and maxabs is None:
+        div = torch.empty(grid.shape, dtype=torch.float64, device=bface.device)
+    if div is not None and (div.dtype != torch.float64 or not div.is_cuda or not div.is_contiguous()
+                            or tuple(div.shape) != grid.shape):
+        raise ValueError("div must be a contiguous CUDA float64 tensor of the grid's shape")
+    if maxabs is not None and (maxabs.dtype != torch.float64 or not maxabs.is_cuda or maxabs.numel() < 1):
+        raise ValueError("maxabs must be a CUDA float64 tensor")
+    rc = _lib.grmhd_ct_divergence(ctypes.byref(grid.c()), _field(bface, grid, 3, "bface"),
+                                  None if div is None else ctypes.c_void_p(div.data_ptr()),
+                                  None if maxabs is None else ctypes.c_void_p(maxabs.data_ptr()), _stream(stream))
+    _check(rc, "grmhd_ct_divergence")
+    return div, maxabs

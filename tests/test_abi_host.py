@@ -203,3 +203,40 @@ def test_rejects_empty_and_oversized_grids(lib):
         assert lib._lib.grmhd_rk_workspace_bytes(ctypes.byref(g), lib.RK3) == 0, n
     g = lib.Grid((8, 8, 8), 3, (0.1, 0.0, 0.1)).c()     # zero spacing
     assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1
+
+
+def test_ct_workspace_and_validation(lib):
+    """Constrained transport: workspace sizes, and short workspaces or bad
+    arguments rejected before any launch."""
+    g = _grid(lib, n=(10, 12, 14))
+    gc = g.c()
+    N = 16 * 18 * 20
+    r256 = lambda b: (b + 255) // 256 * 256
+    assert lib._lib.grmhd_ct_flux_bytes(ctypes.byref(gc)) == r256(9 * N * 8) + r256(3 * N * 8)
+    for scheme in (lib.RK2, lib.RK3, lib.RK4):
+        part = r256(9 * N * 8) + r256(3 * N * 8) * (3 if scheme == lib.RK4 else 2)
+        assert lib._lib.grmhd_ct_workspace_bytes(ctypes.byref(gc), scheme) == part + lib.rk_workspace_bytes(g, scheme)
+        assert (lib._lib.grmhd_ct_workspace_bytes_cached(ctypes.byref(gc), scheme)
+                == part + lib.rk_workspace_bytes_cached(g, scheme))
+    assert lib._lib.grmhd_ct_workspace_bytes(ctypes.byref(gc), 7) == 0
+    p = lib.Params().c()
+    ws = ctypes.c_void_p(0x100000)
+    need = lib._lib.grmhd_ct_workspace_bytes(ctypes.byref(gc), lib.RK3)
+
+    def step(ws_bytes=10 ** 9, dt=0.01, bface=FAKE, wsp=ws, params=p):
+        return lib._lib.grmhd_ct_rk_step(ctypes.byref(gc), ctypes.byref(params), lib.RK3, dt, FAKE, FAKE, bface,
+                                         None, None, wsp, ws_bytes, None, None)
+
+    assert step(ws_bytes=need - 8) == -4
+    assert step(dt=0.0) == -1
+    assert step(bface=None) == -1
+    assert step(bface=ctypes.c_void_p(0x1004)) == -1
+    assert step(wsp=ctypes.c_void_p(0x100008)) == -1
+    rc = lib._lib.grmhd_ct_rate(ctypes.byref(gc), ctypes.byref(p), FAKE, None, None, FAKE, ws,
+                                lib._lib.grmhd_ct_flux_bytes(ctypes.byref(gc)) - 8, None)
+    assert rc == -4
+    assert lib._lib.grmhd_ct_divergence(ctypes.byref(gc), FAKE, None, None, None) == -1
+    thin = lib.Grid((8, 8, 8), 2, (0.1, 0.1, 0.1)).c()     # WENO5 needs three ghost layers
+    rc = lib._lib.grmhd_ct_rk_step(ctypes.byref(thin), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, FAKE, None, None,
+                                   ws, 10 ** 9, None, None)
+    assert rc == -1
