@@ -642,6 +642,8 @@ def main():
     ap.add_argument("--no-shocktube", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-ct", action="store_true")
+    ap.add_argument("--section", default=None, choices=["ct", "amr", "shocktube", "batched", "adjoint", "large"],
+                    help="run only this section and print its JSON (profiling runs)")
     ap.add_argument("--tile", type=int, default=-1, help="RHS tile shape (default: autotuned)")
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-dirs", type=int, default=50)
@@ -658,6 +660,16 @@ def main():
     world, rank = REP.world, REP.rank
 
     from paper_2210_17509_gb300 import grmhd as G
+
+    if args.section:
+        fns = {"ct": lambda: ct_bench(G, n=args.n), "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
+               "batched": lambda: batched_bench(G, args.steps, args.warmup),
+               "adjoint": lambda: adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs),
+               "large": lambda: large_block_bench(G)}
+        out = fns[args.section]()
+        if rank == 0:
+            print(json.dumps({"section": args.section, args.section: out}), flush=True)
+        return
 
     def barrier():
         REP.barrier()

@@ -7,7 +7,8 @@
 //
 // Layouts (array indices, ghosts included, x fastest):
 //   b [a * ncell + cell]        field component a on the lower a-face
-//   fb[(3 d + a) * ncell + cell] flux of B^a through the lower d-face
+//   fb[(3 d + a) * ncell + cell] flux of B^a through the lower d-face (a != d;
+//                               the entries a == d are not used)
 //   E [c * ncell + cell]        edge field on the c-edge through the cell's
 //                               corner lower in the other two axes
 // Face ranges (interior coordinates): the a-faces have a-index 0 .. n_a and

@@ -43,7 +43,7 @@ struct DevParams {
 //                              (+ ca * acc_in[cell] if acc_in != NULL)
 //   acc_out != NULL: acc_out[cell] = wr * r (+ wa * acc_in[cell] if acc_in != NULL)
 //   fb      != NULL: fb[(3 d + a) * ncell + cell] = the flux of the field
-//                    component B^a through the lower d-face of the cell, for
+//                    component B^a (a != d) through the lower d-face of the cell, for
 //                    the d-faces 0 .. n_d with transverse indices -1 .. n
 //                    (the tiles, then a ring kernel; constrained transport)
 // u0 must be valid whenever u is set.

@@ -579,10 +579,10 @@ __device__ __forceinline__ void tile_stage_item(const DevGrid& g, const S& src, 
   }
 }
 
-// Constrained transport: the field components (5..7) of the tile's face
-// fluxes into fb [(3 d + a) * ncell + cell below-or-at the face], each face
-// written by one tile only (its lower faces, and the upper faces on the
-// block's upper boundaries).
+// Constrained transport: the transverse field components of the tile's face
+// fluxes (B^a through a d-face, a != d) into fb [(3 d + a) * ncell + cell
+// above the face], each face written by one tile only (its lower faces, and
+// the upper faces on the block's upper boundaries).
 template <class T, int TX, int TY, int TZ>
 __device__ __noinline__ void tile_export_field_fluxes(const DevGrid& g, int x0, int y0, int z0,
                                                       const T* __restrict__ sF, double* __restrict__ fb) {
@@ -611,8 +611,10 @@ __device__ __noinline__ void tile_export_field_fluxes(const DevGrid& g, int x0, 
     const int tl = dir == 0 ? TX : (dir == 1 ? TY : TZ);
     if (fl == tl && (dir == 0 ? xi : (dir == 1 ? yi : zi)) != g.n[dir]) continue;
     const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
+    // F_d(B^d) is read by no edge field
 #pragma unroll
-    for (int a = 0; a < 3; ++a) fb[(3 * dir + a) * g.ncell + c] = (double)sF[(5 + a) * NF + f];
+    for (int a = 0; a < 3; ++a)
+      if (a != dir) fb[(3 * dir + a) * g.ncell + c] = (double)sF[(5 + a) * NF + f];
   }
 }
 
@@ -781,7 +783,8 @@ __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevPar
     reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
     face_flux_states<T, CURVED, S>(g, p, src, c, d, stride, pL, pR, F);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) fb[(3 * d + q) * g.ncell + c] = (double)F[5 + q];
+    for (int q = 0; q < 3; ++q)
+      if (q != d) fb[(3 * d + q) * g.ncell + c] = (double)F[5 + q];
   }
 }
 
