@@ -28,6 +28,7 @@ _lib = None
 
 REC_MINMOD, REC_WENO5 = 0, 1
 BC_PERIODIC, BC_COPY = 0, 1
+EOS_IDEAL, EOS_POLYTROPE = 0, 1
 RK2, RK3, RK4 = 2, 3, 4
 
 
@@ -39,6 +40,8 @@ class OParams(ctypes.Structure):
         ("rho_atm", ctypes.c_double),
         ("p_atm", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
+        ("eos", ctypes.c_int32),
+        ("poly_K", ctypes.c_double),
     ]
 
 
@@ -66,6 +69,7 @@ def _load():
         lib.oracle_num_threads.restype = I
         lib.oracle_set_threads.argtypes = [I]
         lib.oracle_prim2con.argtypes = [P, I, P, Dd, P, P, P]
+        lib.oracle_prim2con_eos.argtypes = [P, I, P, pp, P, P, P]
         lib.oracle_con2prim.argtypes = [P, I, P, pp, P, P, P, P]
         lib.oracle_con2prim.restype = I
         lib.oracle_fill_ghosts.argtypes = [P, I, I, I, P]
@@ -109,10 +113,12 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_params(gamma=5.0 / 3.0, recon=REC_WENO5, bc=BC_PERIODIC, rho_atm=1e-10, p_atm=None, weno_eps=1e-6):
+def make_params(gamma=5.0 / 3.0, recon=REC_WENO5, bc=BC_PERIODIC, rho_atm=1e-10, p_atm=None, weno_eps=1e-6,
+                eos=None, poly_K=0.0):
+    """eos: EOS_IDEAL (Gamma-law, default) or EOS_POLYTROPE with P = poly_K rho^gamma (reading R20)."""
     if p_atm is None:
         p_atm = 1e-2 * rho_atm ** gamma
-    return OParams(gamma, recon, bc, rho_atm, p_atm, weno_eps)
+    return OParams(gamma, recon, bc, rho_atm, p_atm, weno_eps, EOS_IDEAL if eos is None else eos, poly_K)
 
 
 class Grid:
@@ -144,11 +150,16 @@ def set_threads(n: int) -> None:
     _load().oracle_set_threads(int(n))
 
 
-def prim2con(grid: Grid, gamma: float, prim, metric=None):
+def prim2con(grid: Grid, gamma: float, prim, metric=None, params: OParams = None):
+    """prim -> cons; with params, under its EOS (the polytrope takes P = K rho^Gamma)."""
     prim = _f64(prim)
     metric = _f64(metric)
     cons = np.zeros_like(prim)
-    _load().oracle_prim2con(grid._n, grid.ng, grid._dx, gamma, _ptr(prim), _ptr(metric), _ptr(cons))
+    if params is not None:
+        _load().oracle_prim2con_eos(grid._n, grid.ng, grid._dx, ctypes.byref(params), _ptr(prim), _ptr(metric),
+                                    _ptr(cons))
+    else:
+        _load().oracle_prim2con(grid._n, grid.ng, grid._dx, gamma, _ptr(prim), _ptr(metric), _ptr(cons))
     return cons
 
 

@@ -68,6 +68,17 @@
 //      F_b(B^a) for (c, a, b) cyclic; Balsara & Spicer's averaging).  The
 //      cell-centred field that the rest of the scheme sees is the mean of
 //      the two faces along its direction.
+//   R20 polytropic EOS (Sec. 2.3, EOS paragraph: P = K rho^Gamma, with the
+//      atmosphere pressure from the same polytrope as in Sec. 4.4): the
+//      pressure is a function of the density everywhere it is used (cell
+//      states, the reconstructed face states, prim -> cons), eps = P /
+//      ((Gamma - 1) rho) as for the Gamma-law, and the recovery uses D, S_i
+//      and B^i only (tau is evolved but not read): with rho = D / W, z =
+//      rho h W^2 is a function of W, and the momentum equation
+//      (z + B^2)^2 (1 - 1/W^2) - (B.S)^2 (2z + B^2) / z^2 = S^2 is solved
+//      for W >= 1 by bisection (its left side is 0 - (B.S)^2 (...) <= S^2
+//      at W = 1 and grows without bound).  The atmosphere is rho_atm, v = 0,
+//      P = K rho_atm^Gamma.
 //   Two-level block AMR without subcycling (Sec. 3: refined grids halve the
 //   spacing, are properly nested, share one global time step; ghost zones
 //   of a refined grid are filled by prolongation from the next coarser
@@ -194,20 +205,34 @@ enum { RK2 = 2, RK3 = 3, RK4 = 4 };
 
 // Oracle-side parameter block (plain C layout, mirrored by the Python wrapper).
 struct OParams {
-  double gamma;     // Gamma-law adiabatic index (Sec. 2.3, EOS paragraph)
+  double gamma;     // adiabatic index (Sec. 2.3, EOS paragraph)
   int32_t recon;    // REC_MINMOD | REC_WENO5
   int32_t bc;       // BC_PERIODIC | BC_COPY
   double rho_atm;   // atmosphere density floor (Sec. 4.4 uses an atmosphere)
-  double p_atm;     // atmosphere pressure
+  double p_atm;     // atmosphere pressure (Gamma-law)
   double weno_eps;  // WENO5 epsilon (reading R3)
+  int32_t eos;      // EOS_IDEAL (Gamma-law) | EOS_POLYTROPE (reading R20)
+  double poly_K;    // polytropic constant K of P = K rho^Gamma
 };
+
+enum { EOS_IDEAL = 0, EOS_POLYTROPE = 1 };
 
 template <class S>
 struct Par {
   S gamma;
   int recon, bc;
   double rho_atm, p_atm, weno_eps;
+  int eos = EOS_IDEAL;
+  double poly_K = 0.0;
 };
+
+// Reading R20: under the polytrope the pressure entry of a primitive state
+// is K rho^Gamma (states with rho <= 0 are left for the caller's checks).
+template <class S>
+void apply_eos(const Par<S>& p, S pr[8]) {
+  using std::pow;
+  if (p.eos == EOS_POLYTROPE && val(pr[0]) > 0.0) pr[4] = p.poly_K * pow(pr[0], val(p.gamma));
+}
 
 // --------------------------------------------------- 4-metric (Sec. 2.1) --
 // ADM component order in every metric array: alpha, beta^x, beta^y, beta^z,
@@ -480,10 +505,17 @@ void face_flux(const Grid& G, const Par<S>& p, const S* prim, const double* metr
       for (int b = 0; b < 3; ++b) v2 += val(adm[SYM[a][b]]) * val(pr[1 + a]) * val(pr[1 + b]);
     return val(pr[0]) > 0.0 && val(pr[4]) > 0.0 && v2 < 1.0;
   };
-  if (!physical(pL))
+  // Reading R20: a polytrope's face pressure follows from the face density.
+  apply_eos(p, pL);
+  apply_eos(p, pR);
+  if (!physical(pL)) {
     for (int q = 0; q < 8; ++q) pL[q] = prim[q * G.ncell + cm];
-  if (!physical(pR))
+    apply_eos(p, pL);
+  }
+  if (!physical(pR)) {
     for (int q = 0; q < 8; ++q) pR[q] = prim[q * G.ncell + cp];
+    apply_eos(p, pR);
+  }
   FaceOut<S> fo;
   hlle(pL, pR, adm, p.gamma, d, fo);
   for (int q = 0; q < 8; ++q) F[q] = fo.F[q];
@@ -578,6 +610,7 @@ void source_cell(const Grid& G, const Par<S>& p, const S* prim, const double* me
       }
   S pc[8];
   for (int q = 0; q < 8; ++q) pc[q] = prim[q * G.ncell + c];
+  apply_eos(p, pc);
   Spacetime<S> sts;
   S admS[10];
   for (int q = 0; q < 10; ++q) admS[q] = S(adm[q]);
@@ -677,7 +710,12 @@ void rhs_one_cell(const Grid& G, const Par<S>& p, const S* prim, const double* m
 
 // -------------------------------------------------- prim -> cons (Eq. 6-9) --
 template <class S>
-void prim2con_block(const Grid& G, const S& gamma, const S* prim, const double* metric, S* cons) {
+void prim2con_block(const Grid& G, const S& gamma, const S* prim, const double* metric, S* cons,
+                    int eos = EOS_IDEAL, double poly_K = 0.0) {
+  Par<S> pe;
+  pe.gamma = gamma;
+  pe.eos = eos;
+  pe.poly_K = poly_K;
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < G.ncell; ++c) {
     S adm[10], p[8], U[8];
@@ -685,6 +723,7 @@ void prim2con_block(const Grid& G, const S& gamma, const S* prim, const double* 
     Spacetime<S> st;
     spacetime_from_adm(adm, st);
     for (int q = 0; q < 8; ++q) p[q] = prim[q * G.ncell + c];
+    apply_eos(pe, p);
     Fluid<S> f;
     fluid_from_prim(p, st, gamma, f);
     conserved(f, st, U);
@@ -746,6 +785,61 @@ inline bool c2p_newman_hamlin(const C2P<double>& in, double P0, int maxit, doubl
   return false;
 }
 
+// Reading R20: recovery under the polytrope P = K rho^Gamma.  With
+// rho = D / W, h = 1 + Gamma/(Gamma-1) K rho^(Gamma-1) and z = rho h W^2,
+// the momentum equation g(W) = (z + B^2)^2 (1 - 1/W^2)
+// - (B.S)^2 (2z + B^2) / z^2 - S^2 is <= 0 at W = 1 and grows without
+// bound; its root W >= 1 is found by bisection (the upper end doubled until
+// g > 0), to a relative width of 1e-15.  tau is not used.
+template <class S, class Atm>
+int con2prim_polytrope(const C2P<S>& in, const Spacetime<double>& st, const double gu3[3][3], const S Sl[3],
+                       const S B[3], const Par<S>& p, S out[8], Atm atmosphere) {
+  const double D = val(in.D), S2 = val(in.S2), B2 = val(in.B2), BS = val(in.BS);
+  const double G = val(p.gamma), K = p.poly_K;
+  if (!(D > 0.0)) return atmosphere();
+  auto z_of = [&](double W) {
+    const double rho = D / W;
+    const double h = 1.0 + G / (G - 1.0) * K * std::pow(rho, G - 1.0);
+    return rho * h * W * W;
+  };
+  auto g_of = [&](double W) {
+    const double z = z_of(W);
+    return (z + B2) * (z + B2) * (1.0 - 1.0 / (W * W)) - BS * BS * (2.0 * z + B2) / (z * z) - S2;
+  };
+  double lo = 1.0, hi = 2.0;
+  int guard = 0;
+  while (!(g_of(hi) > 0.0) && guard < 200) {
+    lo = hi;
+    hi *= 2.0;
+    ++guard;
+  }
+  if (guard >= 200) return atmosphere();
+  for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+    const double m = 0.5 * (lo + hi);
+    if (g_of(m) > 0.0) hi = m; else lo = m;
+  }
+  const double W = 0.5 * (lo + hi);
+  const double z = z_of(W);
+  const double rho = D / W;
+  if (!(rho >= p.rho_atm) || !std::isfinite(z)) return atmosphere();
+  // v_i = (S_i + (B.S / z) B_i) / (z + B^2), B_i = gamma_ij B^j
+  double vl[3];
+  for (int i = 0; i < 3; ++i) {
+    double Bl = 0.0;
+    for (int j = 0; j < 3; ++j) Bl += st.gam[i][j] * val(B[j]);
+    vl[i] = (val(Sl[i]) + BS / z * Bl) / (z + B2);
+  }
+  out[0] = S(rho);
+  for (int i = 0; i < 3; ++i) {
+    double t = 0.0;
+    for (int j = 0; j < 3; ++j) t += gu3[i][j] * vl[j];
+    out[1 + i] = S(t);
+  }
+  out[4] = S(K * std::pow(rho, G));
+  for (int i = 0; i < 3; ++i) out[5 + i] = B[i];
+  return 0;
+}
+
 // Returns status 0 on success, 1 if the atmosphere was imposed, 2 if the
 // pressure floor was applied.
 template <class S>
@@ -776,6 +870,7 @@ int con2prim_cell(const S U[8], const double adm[10], const Par<S>& p, S out[8])
     for (int i = 0; i < 3; ++i) out[5 + i] = B[i];
     return 1;
   };
+  if (p.eos == EOS_POLYTROPE) return con2prim_polytrope(in, st, gu3, Sl, B, p, out, atmosphere);
   if (!(val(in.D) > 0.0) || !(val(in.tau) + val(in.D) > 0.0)) return atmosphere();
   // Value-level bisection bracket: sign(z) = +1 where v^2 >= 1 or f > 0;
   // lo_energy records whether the current lower end is positive through the
@@ -1249,6 +1344,9 @@ static Par<double> to_par(const OParams* q) {
   Par<double> p;
   p.gamma = q->gamma; p.recon = q->recon; p.bc = q->bc;
   p.rho_atm = q->rho_atm; p.p_atm = q->p_atm; p.weno_eps = q->weno_eps;
+  p.eos = q->eos; p.poly_K = q->poly_K;
+  // reading R20: the polytrope's atmosphere pressure
+  if (p.eos == EOS_POLYTROPE) p.p_atm = q->poly_K * std::pow(q->rho_atm, q->gamma);
   return p;
 }
 
@@ -1274,6 +1372,13 @@ void oracle_prim2con(const int* n3, int ng, const double* dx3, double gamma,
                      const double* prim, const double* metric, double* cons) {
   Grid G; G.init(n3, ng, dx3);
   prim2con_block<double>(G, gamma, prim, metric, cons);
+}
+
+// prim -> cons under the EOS of q (reading R20 for the polytrope).
+void oracle_prim2con_eos(const int* n3, int ng, const double* dx3, const OParams* q, const double* prim,
+                         const double* metric, double* cons) {
+  Grid G; G.init(n3, ng, dx3);
+  prim2con_block<double>(G, q->gamma, prim, metric, cons, q->eos, q->poly_K);
 }
 
 int oracle_con2prim(const int* n3, int ng, const double* dx3, const OParams* q,
