@@ -86,7 +86,22 @@ typedef struct {
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
   int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
   int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN */
+  int32_t eos;       /* GRMHD_EOS_IDEAL (Gamma-law, P = (Gamma - 1) rho eps) | GRMHD_EOS_POLYTROPE */
+  double poly_K;     /* polytropic constant K of P = K rho^gamma (GRMHD_EOS_POLYTROPE; > 0) */
 } grmhd_params;
+
+/* Equations of state (Sec. 2.3, EOS paragraph).  Under GRMHD_EOS_POLYTROPE
+ * the pressure is K rho^gamma wherever it is used: the face states take it
+ * from the reconstructed density, prim -> cons ignores the pressure entry
+ * of its input, the recovery solves for W from D, S_i and B^i only (tau is
+ * evolved but not read) and writes P = K rho^gamma, and the atmosphere
+ * pressure is K rho_atm^gamma (p_atm is not used).  Cell primitives passed
+ * to the RHS must carry P = K rho^gamma, as the recovery writes them.
+ * eps = P / ((gamma - 1) rho) under both.  The polytrope's RHS runs on
+ * the default tile shape whatever params.tile says.  The adjoint and the
+ * batched-box entry points accept GRMHD_EOS_IDEAL only. */
+#define GRMHD_EOS_IDEAL 0
+#define GRMHD_EOS_POLYTROPE 1
 
 /* flags: the metric, the grid and the precision are unchanged since the
  * previous grmhd_rk_step with this same workspace, so the geometry caches

@@ -968,6 +968,7 @@ size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
 int check_common(const grmhd_grid* grid, const grmhd_params* params, const double* metric) {
   if (!grid || !params) return GRMHD_ERR_ARG;
   if (params->precision != GRMHD_FP64) return GRMHD_ERR_ARG;  // the adjoint is of the FP64 method
+  if (params->eos != GRMHD_EOS_IDEAL) return GRMHD_ERR_ARG;    // ... with the Gamma-law
   if (!(params->gamma > 1.0 && params->gamma <= 3.0)) return GRMHD_ERR_ARG;
   if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
   if (params->bc != GRMHD_BC_PERIODIC && params->bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;

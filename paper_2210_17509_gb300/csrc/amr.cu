@@ -136,7 +136,7 @@ __global__ void prolongate_kernel(DevGrid c, const double* __restrict__ coarse, 
 constexpr int kFacesPerBlock = 32;
 constexpr int kRefluxThreads = 5 * kFacesPerBlock;
 
-template <int RECON, bool CURVED>
+template <int RECON, bool CURVED, bool POLY>
 __global__ void __launch_bounds__(kRefluxThreads) reflux_kernel(
     DevGrid c, DevParams p, const double* __restrict__ cprim, const double* __restrict__ cmetric, DevGrid f,
     const double* __restrict__ fprim, const double* __restrict__ fmetric, int lox, int loy, int loz, double scale,
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kRefluxThreads) reflux_kernel(
         Ic[b] = lo[b] + B;
         const long long cface =
             (long long)(c.ng + Ic[2]) * c.sz + (long long)(c.ng + Ic[1]) * c.sy + (c.ng + Ic[0]);
-        face_flux_one<RECON, CURVED>(c, p, cprim, cmetric, cface, d, F);
+        face_flux_one<RECON, CURVED, POLY>(c, p, cprim, cmetric, cface, d, F);
         // the uncovered cell: below the face on the low side (the face is its
         // upper face), above it on the high side (its lower face)
         const long long st = d == 0 ? 1 : (d == 1 ? c.sy : c.sz);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kRefluxThreads) reflux_kernel(
         If[b] = 2 * B + ((role - 1) >> 1);
         const long long fface =
             (long long)(f.ng + If[2]) * f.sz + (long long)(f.ng + If[1]) * f.sy + (f.ng + If[0]);
-        face_flux_one<RECON, CURVED>(f, p, fprim, fmetric, fface, d, F);
+        face_flux_one<RECON, CURVED, POLY>(f, p, fprim, fmetric, fface, d, F);
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) sF[fl][role][q] = F[q];
@@ -224,22 +224,17 @@ cudaError_t launch_reflux(const DevGrid& c, const DevParams& p, const double* cp
   const long long nf = 2LL * ((long long)(f.n[1] / 2) * (f.n[2] / 2) + (long long)(f.n[2] / 2) * (f.n[0] / 2) +
                               (long long)(f.n[0] / 2) * (f.n[1] / 2));
   const int blocks = blocks_for(nf, kFacesPerBlock);
-  const bool curved = cmetric != nullptr;
-  if (p.recon == GRMHD_WENO5) {
-    if (curved)
-      reflux_kernel<GRMHD_WENO5, true><<<blocks, kRefluxThreads, 0, s>>>(c, p, cprim, cmetric, f, fprim, fmetric, lo[0], lo[1],
-                                                            lo[2], scale, out, acc_scale, acc);
-    else
-      reflux_kernel<GRMHD_WENO5, false><<<blocks, kRefluxThreads, 0, s>>>(c, p, cprim, cmetric, f, fprim, fmetric, lo[0], lo[1],
-                                                             lo[2], scale, out, acc_scale, acc);
-  } else {
-    if (curved)
-      reflux_kernel<GRMHD_MINMOD, true><<<blocks, kRefluxThreads, 0, s>>>(c, p, cprim, cmetric, f, fprim, fmetric, lo[0], lo[1],
-                                                             lo[2], scale, out, acc_scale, acc);
-    else
-      reflux_kernel<GRMHD_MINMOD, false><<<blocks, kRefluxThreads, 0, s>>>(c, p, cprim, cmetric, f, fprim, fmetric, lo[0],
-                                                              lo[1], lo[2], scale, out, acc_scale, acc);
-  }
+  using K = void (*)(DevGrid, DevParams, const double*, const double*, DevGrid, const double*, const double*, int,
+                     int, int, double, double*, double, double*);
+  // [polytrope][WENO5][curved]
+  static const K table[2][2][2] = {
+      {{reflux_kernel<GRMHD_MINMOD, false, false>, reflux_kernel<GRMHD_MINMOD, true, false>},
+       {reflux_kernel<GRMHD_WENO5, false, false>, reflux_kernel<GRMHD_WENO5, true, false>}},
+      {{reflux_kernel<GRMHD_MINMOD, false, true>, reflux_kernel<GRMHD_MINMOD, true, true>},
+       {reflux_kernel<GRMHD_WENO5, false, true>, reflux_kernel<GRMHD_WENO5, true, true>}}};
+  const K k = table[p.eos == GRMHD_EOS_POLYTROPE][p.recon == GRMHD_WENO5][cmetric != nullptr];
+  k<<<blocks, kRefluxThreads, 0, s>>>(c, p, cprim, cmetric, f, fprim, fmetric, lo[0], lo[1], lo[2], scale, out,
+                                      acc_scale, acc);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,10 @@ DevParams make_params(const grmhd_params& p) {
   d.precision = p.precision;
   d.tile = p.tile;
   d.flags = p.flags;
+  d.eos = p.eos;
+  d.poly_K = p.poly_K;
+  // the polytrope's atmosphere pressure
+  if (p.eos == GRMHD_EOS_POLYTROPE) d.p_atm = p.poly_K * std::pow(p.rho_atm, p.gamma);
   return d;
 }
 

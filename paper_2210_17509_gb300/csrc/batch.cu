@@ -69,6 +69,7 @@ size_t grmhd_batch_workspace_bytes(int32_t nbox) {
 int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params* params, void* ws,
                         size_t ws_bytes, grmhd_batch* batch, void* stream) {
   if (!boxes || !params || !ws || !batch || nbox < 1) return GRMHD_ERR_ARG;
+  if (params->eos != GRMHD_EOS_IDEAL) return GRMHD_ERR_ARG;  // batched boxes: Gamma-law only
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GRMHD_ERR_ARG;
   const size_t need = grmhd_batch_workspace_bytes(nbox);
   if (need == 0) return GRMHD_ERR_ARG;
@@ -144,6 +145,7 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
 
 int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream) {
   if (!batch || !params || !batch->ws || batch->nbox < 1) return GRMHD_ERR_ARG;
+  if (params->eos != GRMHD_EOS_IDEAL) return GRMHD_ERR_ARG;  // batched boxes: Gamma-law only
   if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
   if (params->precision != GRMHD_FP64 && params->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
   if (!(params->gamma > 1.0 && params->gamma <= 3.0) || params->nr_maxit < 1 || !(params->nr_tol > 0.0))

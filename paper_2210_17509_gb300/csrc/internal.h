@@ -35,6 +35,8 @@ struct DevParams {
   int recon, bc, precision;
   int tile;        // RHS tile shape index (0..3)
   int flags;       // GRMHD_REUSE_GEOMETRY, ...
+  int eos;         // GRMHD_EOS_IDEAL | GRMHD_EOS_POLYTROPE
+  double poly_K;   // K of P = K rho^gamma (polytrope)
 };
 
 // What the RHS kernel does with the RHS value r of each interior cell:
@@ -116,6 +118,8 @@ inline int check_params(const grmhd_params* p) {
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
   if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
   if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN)) != 0) return GRMHD_ERR_ARG;
+  if (p->eos != GRMHD_EOS_IDEAL && p->eos != GRMHD_EOS_POLYTROPE) return GRMHD_ERR_ARG;
+  if (p->eos == GRMHD_EOS_POLYTROPE && !(p->poly_K > 0.0 && std::isfinite(p->poly_K))) return GRMHD_ERR_ARG;
   return GRMHD_OK;
 }
 

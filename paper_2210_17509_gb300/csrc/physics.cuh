@@ -318,6 +318,19 @@ __device__ __forceinline__ void lower(const T g[6], const T v[3], T vl[3]) {
   vl[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
 }
 
+// Polytropic EOS (Sec. 2.3): the pressure entry of a state is K rho^gamma
+// (states with rho <= 0 are left to the physical-state checks).
+template <class T>
+__device__ __forceinline__ void apply_polytrope_pair(const DevParams& p, T pL[8], T pR[8]) {
+  if constexpr (sizeof(T) == 4) {
+    if (pL[0] > 0.0f) pL[4] = (float)p.poly_K * powf(pL[0], (float)p.gamma);
+    if (pR[0] > 0.0f) pR[4] = (float)p.poly_K * powf(pR[0], (float)p.gamma);
+  } else {
+    if (pL[0] > 0.0) pL[4] = p.poly_K * pow(pL[0], p.gamma);
+    if (pR[0] > 0.0) pR[4] = p.poly_K * pow(pR[0], p.gamma);
+  }
+}
+
 // As physical_state, also returning the lowered velocity and v^2.
 template <class T, bool CURVED>
 __device__ __forceinline__ bool physical_state_v(const T pr[8], const Geom<T>& m, T vl[3], T& v2) {

@@ -4,6 +4,7 @@
 
 namespace grmhd {
 
+template <bool POLY>
 __global__ void con2prim_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                 const double* __restrict__ metric, double* __restrict__ prim,
                                 int8_t* __restrict__ status, int32_t* __restrict__ nfail) {
@@ -12,7 +13,7 @@ __global__ void con2prim_kernel(DevGrid g, DevParams p, const double* __restrict
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    const int st = con2prim_at<false>(g, p, cons, metric, prim, c);
+    const int st = con2prim_at<false, false, true, POLY>(g, p, cons, metric, prim, c);
     myfail += (st >= 2);
     if (status) status[c] = (int8_t)st;
   }
@@ -26,6 +27,7 @@ __global__ void prim2con_kernel(DevGrid g, DevParams p, const double* __restrict
     double pr[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) pr[q] = __ldg(prim + q * g.ncell + c);
+    if (p.eos == GRMHD_EOS_POLYTROPE && pr[0] > 0.0) pr[4] = p.poly_K * pow(pr[0], p.gamma);
     Geom<double> m;
     if (metric) {
       CellMetric cm;
@@ -57,7 +59,7 @@ __global__ void fill_ghosts_kernel(DevGrid g, int bc, int nvar, double* __restri
 }
 
 // Mixed path: FP32-predicted FP64 recovery, writing FP64 and FP32 primitives.
-template <bool RESULT64>
+template <bool RESULT64, bool POLY>
 __global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                       const double* __restrict__ metric, double* __restrict__ prim,
                                       float* __restrict__ prim32, const double* __restrict__ mcache,
@@ -67,7 +69,7 @@ __global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __re
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    myfail += (con2prim_at<true, true, RESULT64>(g, p, cons, metric, prim, c, prim32, mcache, geom32) >= 2);
+    myfail += (con2prim_at<true, true, RESULT64, POLY>(g, p, cons, metric, prim, c, prim32, mcache, geom32) >= 2);
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }
@@ -173,7 +175,10 @@ static int grid_blocks(long long work, int threads) {
 cudaError_t launch_con2prim(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
                             double* prim, int8_t* status, int32_t* nfail, cudaStream_t s) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  con2prim_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, status, nfail);
+  if (p.eos == GRMHD_EOS_POLYTROPE)
+    con2prim_kernel<true><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, status, nfail);
+  else
+    con2prim_kernel<false><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, status, nfail);
   return cudaGetLastError();
 }
 
@@ -196,12 +201,13 @@ cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const do
                                   double* prim, float* prim32, const double* mcache, const float* geom32,
                                   bool result64, int32_t* nfail, cudaStream_t s) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  if (result64)
-    con2prim_mixed_kernel<true><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache,
-                                                                      geom32, nfail);
+  void (*k)(DevGrid, DevParams, const double*, const double*, double*, float*, const double*, const float*,
+            int32_t*);
+  if (p.eos == GRMHD_EOS_POLYTROPE)
+    k = result64 ? con2prim_mixed_kernel<true, true> : con2prim_mixed_kernel<false, true>;
   else
-    con2prim_mixed_kernel<false><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache,
-                                                                       geom32, nfail);
+    k = result64 ? con2prim_mixed_kernel<true, false> : con2prim_mixed_kernel<false, false>;
+  k<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, prim, prim32, mcache, geom32, nfail);
   return cudaGetLastError();
 }
 
@@ -224,6 +230,7 @@ cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, void* geom
   return cudaGetLastError();
 }
 
+template <bool POLY>
 __global__ void con2prim_cached_kernel(DevGrid g, DevParams p, const double* __restrict__ cons,
                                        const double* __restrict__ metric, const double* __restrict__ mcache,
                                        double* __restrict__ prim, int32_t* __restrict__ nfail) {
@@ -232,7 +239,7 @@ __global__ void con2prim_cached_kernel(DevGrid g, DevParams p, const double* __r
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    myfail += (con2prim_at<false>(g, p, cons, metric, prim, c, nullptr, mcache) >= 2);
+    myfail += (con2prim_at<false, false, true, POLY>(g, p, cons, metric, prim, c, nullptr, mcache) >= 2);
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }
@@ -240,7 +247,10 @@ __global__ void con2prim_cached_kernel(DevGrid g, DevParams p, const double* __r
 cudaError_t launch_con2prim_cached(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
                                    const double* mcache, double* prim, int32_t* nfail, cudaStream_t s) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  con2prim_cached_kernel<<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, mcache, prim, nfail);
+  if (p.eos == GRMHD_EOS_POLYTROPE)
+    con2prim_cached_kernel<true><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, mcache, prim, nfail);
+  else
+    con2prim_cached_kernel<false><<<grid_blocks(nint, 128), 128, 0, s>>>(g, p, cons, metric, mcache, prim, nfail);
   return cudaGetLastError();
 }
 

@@ -242,6 +242,44 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
   return false;
 }
 
+// Polytropic EOS (Sec. 2.3, P = K rho^gamma): with rho = D / W,
+// h = 1 + gamma/(gamma-1) K rho^(gamma-1) and z = rho h W^2 = D W h, the
+// momentum equation f(W) = (z + B^2)^2 (1 - 1/W^2) - (B.S)^2 (2z + B^2)/z^2
+// - S^2 is <= 0 at W = 1 and grows without bound (monotonically for
+// gamma <= 2).  Newton from the guess W, on a bracket [lo, hi] kept from the
+// signs of f; a step that leaves the bracket bisects it (or doubles W while
+// no upper end is known).  tau is not used.  Returns 0 (Newton), 1 (a
+// bisection step was needed) or 2 (no root: atmosphere); z and W on success.
+__device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p, double& z, double& W) {
+  const double D = in.D, gm1 = p.gamma - 1.0;
+  const double dzk = (2.0 - p.gamma) * p.gfac;
+  double lo = 1.0, hi = INFINITY, w = W >= 1.0 ? W : 1.0;
+  bool bis = false;
+  for (int it = 0; it < p.nr_maxit + 200; ++it) {
+    const double kr = p.poly_K * pow(D / w, gm1);  // K rho^(gamma-1)
+    const double zz = D * w * (1.0 + p.gfac * kr);
+    const double dz = D * (1.0 + dzk * kr);         // dz/dW
+    const double zb = zz + in.B2, iw = 1.0 / w, iz = 1.0 / zz;
+    const double v2 = 1.0 - iw * iw;
+    const double f = zb * zb * v2 - in.BS2 * (2.0 * zz + in.B2) * iz * iz - in.S2;
+    const double df = 2.0 * zb * (dz * v2 + zb * iw * iw * iw) + 2.0 * in.BS2 * dz * zb * iz * iz * iz;
+    if (!isfinite(f) || !isfinite(df)) return 2;
+    if (f > 0.0) hi = w; else lo = w;
+    double wn = w - f / df;
+    if (!(wn >= lo && wn <= hi) || !isfinite(wn)) {
+      wn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * lo;
+      bis = true;
+    }
+    if (fabs(wn - w) <= p.nr_tol * wn || (isfinite(hi) && hi - lo <= 1e-15 * hi)) {
+      W = wn;
+      z = D * wn * (1.0 + p.gfac * p.poly_K * pow(D / wn, gm1));
+      return bis ? 1 : 0;
+    }
+    w = wn;
+  }
+  return 2;
+}
+
 // Recovery of the interior cell c (Sec. 2.3).  The incoming primitives of
 // the cell are the Newton initial guess and are overwritten with the result.
 // Returns the status: 0 Newton, 1 bisection, 2 atmosphere, 3 pressure floor.
@@ -255,8 +293,9 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 // serve the single-precision parts.  Without RESULT64 (F32IO only) the
 // primitives are formed in FP32 from the FP64 root (z, W) and only prim32 is
 // written: for the intermediate stages of a mixed step, whose primitives
-// feed only the FP32 RHS and the next recovery's guess.
-template <bool PREDICT, bool F32IO = PREDICT, bool RESULT64 = true>
+// feed only the FP32 RHS and the next recovery's guess.  POLY: the
+// polytropic EOS (p.eos == GRMHD_EOS_POLYTROPE; the launchers dispatch on it).
+template <bool PREDICT, bool F32IO = PREDICT, bool RESULT64 = true, bool POLY = false>
 __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p, const double* __restrict__ cons,
                                            const double* __restrict__ metric, double* __restrict__ prim,
                                            long long c, float* __restrict__ prim32 = nullptr,
@@ -321,7 +360,10 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   }
   if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
   int st = 2;
-  if (D > 0.0 && tau + D > 0.0) {
+  constexpr bool poly = POLY;
+  if constexpr (POLY) {
+    if (D > 0.0) st = c2p_polytrope(in, p, z, W);
+  } else if (D > 0.0 && tau + D > 0.0) {
     double tol_first = p.nr_tol;
     if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
     st = c2p_solve(in, p, z, W, tol_first, P0);
@@ -335,7 +377,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
       const float X = 1.0f / (Wf * zf * zbf);
       const float iW = zf * zbf * X, iz = Wf * zbf * X, izb = Wf * zf * X;
       const float rho = (float)D * iW;
-      const float P = (float)p.gm1g * (zf * iW * iW - rho);
+      const float P = poly ? (float)p.poly_K * powf(rho, (float)p.gamma) : (float)p.gm1g * (zf * iW * iW - rho);
       const float bsz = (float)BS * iz;
       float gf[6], guf[6];
 #pragma unroll
@@ -382,7 +424,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const double X = 1.0 / (W * z * zb);
     const double iW = z * zb * X, iz = W * zb * X, izb = W * z * X;
     const double rho = D * iW;
-    const double P = p.gm1g * (z * iW * iW - rho);
+    const double P = poly ? p.poly_K * pow(rho, p.gamma) : p.gm1g * (z * iW * iW - rho);
     const double bsz = BS * iz;
     double vlo[3], vu[3];
 #pragma unroll

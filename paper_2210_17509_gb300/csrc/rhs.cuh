@@ -203,9 +203,12 @@ __device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, lon
 // relabelled so the normal is the first axis, one x-face computation runs,
 // and the flux is relabelled back (one copy of the face code instead of
 // three keeps the kernel small).  c is the cell above the face.
-template <class T, bool CURVED, class S>
+template <class T, bool CURVED, class S, bool POLY = false>
 __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevParams& p, const S& src, long long c,
                                                  int dir, long long stride, T pL[8], T pR[8], T F[8]) {
+  // polytrope (a separate instantiation, so that the Gamma-law kernels carry
+  // none of it): the face pressure follows from the face density
+  if constexpr (POLY) apply_polytrope_pair<T>(p, pL, pR);
   Geom<T> m;
   if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
   T rL[8], rR[8], Fr[8];
@@ -252,14 +255,6 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
   unrotate_flux(dir, Fr, F);
 }
 
-
-// Eq. 13 in 3+1 form for a static-in-time lapse and shift:
-//   S_{S_j} = alpha sqrt(gamma) [ T^00 (beta^i beta^k d_j g_ik / 2 - alpha d_j alpha)
-//             + T^0i beta^k d_j g_ik + T^0_i d_j beta^i + T^ik d_j g_ik / 2 ]
-//   S_tau   = alpha sqrt(gamma) [ T^00 (beta^i beta^j K_ij - beta^i d_i alpha)
-//             + T^0i (2 beta^j K_ij - d_i alpha) + T^ij K_ij ]
-// Metric derivatives by 4th-order centred differences of the cell-centred
-// metric; the spatial inverse and sqrt(gamma) in FP64.
 // Eq. 13 in 3+1 form for a static-in-time lapse and shift:
 //   S_{S_j} = alpha sqrt(gamma) [ T^00 (beta^i beta^k d_j g_ik / 2 - alpha d_j alpha)
 //             + T^0i beta^k d_j g_ik + T^0_i d_j beta^i + T^ik d_j g_ik / 2 ]
@@ -492,7 +487,7 @@ constexpr size_t batch_smem_bytes() {
 // Flux of the face between cell c - stride and cell c along dir, as the
 // RHS kernels compute it with per-face reconstruction (used outside the
 // tiles: AMR interface faces, constrained-transport ring faces).
-template <int RECON, bool CURVED>
+template <int RECON, bool CURVED, bool POLY = false>
 __device__ __forceinline__ void face_flux_one(const DevGrid& g, const DevParams& p, const double* prim,
                                               const double* metric, long long c, int dir, double F[8]) {
   SrcF64 src;
@@ -502,14 +497,14 @@ __device__ __forceinline__ void face_flux_one(const DevGrid& g, const DevParams&
   const long long stride = dir == 0 ? 1 : (dir == 1 ? g.sy : g.sz);
   double pL[8], pR[8];
   reconstruct_face<double, RECON, SrcF64>(src, g.ncell, c, stride, p.weno_eps, pL, pR);
-  face_flux_states<double, CURVED, SrcF64>(g, p, src, c, dir, stride, pL, pR, F);
+  face_flux_states<double, CURVED, SrcF64, POLY>(g, p, src, c, dir, stride, pL, pR, F);
 }
 
 // Face flux of face f (flat index over the NFX x-, NFY y- and NFZ z-faces of
 // the tile) into sF [8][NF].  With a stage, the face states come from sR
 // (stage index of the cell below the face: eoff[dir] + its index in that
 // direction's extended box); otherwise they are reconstructed here.
-template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S, bool POLY = false>
 __device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, const S& src, int x0, int y0, int z0,
                                           int f, T* __restrict__ sF, const T* __restrict__ sR, int ns, int eoff_y,
                                           int eoff_z) {
@@ -550,7 +545,7 @@ __device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, 
   } else {
     reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
   }
-  face_flux_states<T, CURVED, S>(g, p, src, c, dir, stride, pL, pR, F);
+  face_flux_states<T, CURVED, S, POLY>(g, p, src, c, dir, stride, pL, pR, F);
 #pragma unroll
   for (int q = 0; q < 8; ++q) sF[q * NF + f] = F[q];
 }
@@ -629,7 +624,7 @@ __device__ __noinline__ void tile_export_field_fluxes(const DevGrid& g, int x0, 
 // sources and applies the stage epilogue.  Called by all threads of the CTA
 // (contains __syncthreads); kTileThreads threads, each handling one or more
 // cells of the TX*TY*TZ tile.
-template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S>
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S, bool POLY = false>
 __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
                                          int x0, int y0, int z0, T* sF, T* sR) {
   constexpr int NT = kTileThreads;
@@ -643,7 +638,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   const int ng = g.ng;
   if constexpr (!CellRecon<T, RECON>::value) {
     for (int f = threadIdx.x; f < NF; f += NT)
-      tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f, sF, sR, 0, 0, 0);
+      tile_face<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, f, sF, sR, 0, 0, 0);
     __syncthreads();
   } else if constexpr (SM::stage_all) {
     const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
@@ -681,7 +676,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
     }
     __syncthreads();
     for (int f = threadIdx.x; f < NF; f += NT)
-      tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f, sF, sR, ST::NEA, ST::EXX,
+      tile_face<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, f, sF, sR, ST::NEA, ST::EXX,
                                                   ST::EXX + ST::EYY);
     __syncthreads();
   } else {
@@ -695,7 +690,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       const int f0 = dir == 0 ? 0 : (dir == 1 ? NFX : NFX + NFY);
       const int nfd = dir == 0 ? NFX : (dir == 1 ? NFY : NFZ);
       for (int f = threadIdx.x; f < nfd; f += NT)
-        tile_face<T, RECON, CURVED, TX, TY, TZ, S>(g, p, src, x0, y0, z0, f0 + f, sF, sR, ST::NE, 0, 0);
+        tile_face<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, f0 + f, sF, sR, ST::NE, 0, 0);
       __syncthreads();
     }
   }
@@ -752,7 +747,7 @@ __host__ __device__ __forceinline__ long long ct_ring_faces(const DevGrid& g, in
 
 constexpr int kRingThreads = 128;
 
-template <class T, int RECON, bool CURVED, class S>
+template <class T, int RECON, bool CURVED, class S, bool POLY = false>
 __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevParams p, S src,
                                                                double* __restrict__ fb) {
   const long long r0 = ct_ring_faces(g, 0), r1 = ct_ring_faces(g, 1), total = r0 + r1 + ct_ring_faces(g, 2);
@@ -781,7 +776,7 @@ __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevPar
     const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
     T pL[8], pR[8], F[8];
     reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
-    face_flux_states<T, CURVED, S>(g, p, src, c, d, stride, pL, pR, F);
+    face_flux_states<T, CURVED, S, POLY>(g, p, src, c, d, stride, pL, pR, F);
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       if (q != d) fb[(3 * d + q) * g.ncell + c] = (double)F[5 + q];
@@ -793,14 +788,14 @@ __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevPar
 template <class T>
 struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
 
-template <class T, int RECON, bool CURVED, int SHAPE, class S>
+template <class T, int RECON, bool CURVED, int SHAPE, class S, bool POLY = false>
 __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(DevGrid g, DevParams p, S src,
                                                                              StageEpilogue ep) {
   using TS = TileShape<SHAPE>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);
   T* sR = sF + 8 * TileFaces<TS::X, TS::Y, TS::Z>::NF;  // stage (FP64 WENO5 only)
-  rhs_tile<T, RECON, CURVED, TS::X, TS::Y, TS::Z, S>(g, p, src, ep, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+  rhs_tile<T, RECON, CURVED, TS::X, TS::Y, TS::Z, S, POLY>(g, p, src, ep, blockIdx.x * TS::X, blockIdx.y * TS::Y,
                                                       blockIdx.z * TS::Z, sF, sR);
 }
 
@@ -810,6 +805,9 @@ cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, co
   void (*k)(DevGrid, DevParams, S, StageEpilogue) = nullptr;
   int tx, ty, tz;
   size_t smem;
+  const bool poly = p.eos == GRMHD_EOS_POLYTROPE;
+  // the polytrope runs on the default tile shape only
+  if (poly) shape = -1;
   switch (shape) {
 #define GRMHD_SHAPE_CASE(SH)                                                          \
   case SH:                                                                            \
@@ -821,6 +819,11 @@ cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, co
     GRMHD_SHAPE_CASE(2)
     GRMHD_SHAPE_CASE(3)
     GRMHD_SHAPE_CASE(4)
+    case -1:
+      k = rhs_kernel<T, RECON, CURVED, 0, S, true>;
+      tx = TileShape<0>::X; ty = TileShape<0>::Y; tz = TileShape<0>::Z;
+      smem = tile_smem_bytes<T, RECON, TileShape<0>::X, TileShape<0>::Y, TileShape<0>::Z>();
+      break;
     default:
     GRMHD_SHAPE_CASE(0)
 #undef GRMHD_SHAPE_CASE
@@ -834,7 +837,10 @@ cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, co
     const long long nring = ct_ring_faces(g, 0) + ct_ring_faces(g, 1) + ct_ring_faces(g, 2);
     long long blocks = (nring + kRingThreads - 1) / kRingThreads;
     if (blocks > 152LL * 64) blocks = 152LL * 64;
-    ct_ring_kernel<T, RECON, CURVED, S><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
+    if (poly)
+      ct_ring_kernel<T, RECON, CURVED, S, true><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
+    else
+      ct_ring_kernel<T, RECON, CURVED, S><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
   }
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ FP64, MIXED = 0, 1
 RK2, RK3, RK4 = 2, 3, 4
 REUSE_GEOMETRY = 1
 NEWMAN_HAMLIN = 2
+EOS_IDEAL, EOS_POLYTROPE = 0, 1
 
 
 class GrmhdError(RuntimeError):
@@ -55,6 +56,8 @@ class CParams(ctypes.Structure):
         ("weno_eps", ctypes.c_double),
         ("tile", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("eos", ctypes.c_int32),
+        ("poly_K", ctypes.c_double),
     ]
 
 
@@ -121,10 +124,12 @@ class Params:
     weno_eps: float = 1e-6
     tile: int = 0
     flags: int = 0
+    eos: int = 0         # EOS_IDEAL | EOS_POLYTROPE
+    poly_K: float = 0.0  # K of P = K rho^gamma (EOS_POLYTROPE)
 
     def c(self) -> CParams:
         return CParams(self.gamma, self.recon, self.bc, self.precision, self.nr_maxit, self.rho_atm, self.p_atm,
-                       self.nr_tol, self.weno_eps, self.tile, self.flags)
+                       self.nr_tol, self.weno_eps, self.tile, self.flags, self.eos, self.poly_K)
 
 
 def version() -> int:

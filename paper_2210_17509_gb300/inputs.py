@@ -354,3 +354,22 @@ def ct_state(blk: Block, prim, bface, metric=None):
         cell = 0.5 * (bface[a][tuple(lo)] + bface[a][tuple(hi)])
         prim[5 + a][tuple(lo)] = cell / sg[tuple(lo)]
     return prim
+
+
+def polytrope_prims(blk: Block, seed: int, K: float, gamma: float, metric=None, vmax=0.9, log_rho=(-4.0, -2.5),
+                    b_scale=1.0):
+    """Random magnetised states on the polytrope P = K rho^gamma: log10 rho
+    uniform in log_rho, |v| uniform in [0, vmax) (lengths taken in the metric
+    when given, for isotropic metrics), B normal with scale b_scale sqrt(rho)
+    (so b^2/rho of order b_scale^2)."""
+    rng = np.random.default_rng(np.random.Philox(seed))
+    shp = blk.shape
+    prim = np.zeros((8,) + shp)
+    prim[0] = 10 ** rng.uniform(log_rho[0], log_rho[1], shp)
+    v = rng.normal(size=(3,) + shp)
+    vmag = rng.uniform(0, vmax, shp)
+    psi4 = metric[4] if metric is not None else 1.0
+    prim[1:4] = v / np.sqrt((v ** 2).sum(0)) * vmag / np.sqrt(psi4)
+    prim[4] = K * prim[0] ** gamma
+    prim[5:] = b_scale * rng.normal(size=(3,) + shp) * np.sqrt(prim[0])
+    return prim

@@ -240,3 +240,25 @@ def test_ct_workspace_and_validation(lib):
     rc = lib._lib.grmhd_ct_rk_step(ctypes.byref(thin), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, FAKE, None, None,
                                    ws, 10 ** 9, None, None)
     assert rc == -1
+
+
+def test_eos_validation(lib):
+    """An unknown EOS, a polytrope without a positive K, and the adjoint under the polytrope are refused
+    before any launch."""
+    g = _grid(lib).c()
+    for eos, K in ((2, 1.0), (lib.EOS_POLYTROPE, 0.0), (lib.EOS_POLYTROPE, float("nan"))):
+        p = lib.Params(eos=eos, poly_K=K).c()
+        assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1
+        assert lib._lib.grmhd_con2prim(ctypes.byref(g), ctypes.byref(p), FAKE, None, FAKE, None, None, None) == -1
+    p = lib.Params(eos=lib.EOS_POLYTROPE, poly_K=100.0).c()
+    assert lib._lib.grmhd_rhs_adjoint(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, FAKE, FAKE,
+                                      None) == -1
+
+
+def test_batch_rejects_the_polytrope(lib):
+    import ctypes as C
+    p = lib.Params(eos=lib.EOS_POLYTROPE, poly_K=100.0).c()
+    boxes = (lib.CBox * 1)()
+    out = lib.CBatch()
+    nb = lib._lib.grmhd_batch_workspace_bytes(1)
+    assert lib._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None) == -1

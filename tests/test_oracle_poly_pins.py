@@ -28,17 +28,7 @@ def random_states(n, seed, metric=False, K=K, gamma=GAM):
     blk = I.Block((n, n, n), 3, (8.0 / n,) * 3, (4.0,) * 3) if metric else I.Block((n, n, n), 3, (1.0 / n,) * 3,
                                                                                      (0.0,) * 3)
     m = I.schwarzschild_metric(blk) if metric else None
-    rng = np.random.default_rng(seed)
-    shp = blk.shape
-    prim = np.zeros((8,) + shp)
-    prim[0] = 10 ** rng.uniform(-4, -2.5, shp)          # K rho^(Gamma-1) from 0.01 to 0.3
-    v = rng.normal(size=(3,) + shp)
-    vmag = rng.uniform(0, 0.9, shp)
-    psi4 = m[4] if metric else 1.0
-    prim[1:4] = v / np.sqrt((v ** 2).sum(0)) * vmag / np.sqrt(psi4)
-    prim[4] = K * prim[0] ** gamma
-    prim[5:] = rng.normal(size=(3,) + shp) * np.sqrt(prim[0])   # b^2 / rho up to ~10
-    return blk, m, prim
+    return blk, m, I.polytrope_prims(blk, seed, K, gamma, m)
 
 
 def test_recovery_inverts_prim2con():
