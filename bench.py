@@ -564,6 +564,47 @@ def ct_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE):
     return out
 
 
+# ------------------------------------------------------ polytropic EOS --
+def poly_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE, K=100.0, gamma=2.0):
+    """Polytropic EOS (Sec. 2.3; K = 100, Gamma = 2 as the paper's TOV star,
+    Sec. 4.4): the headline 128^3 Schwarzschild block with a smooth state of
+    density 1e-4 .. 1.28e-3 (the TOV central density), P = K rho^Gamma,
+    |v| <= 0.5 and a weak field (|B| <= 1e-3), WENO5+HLLE, SSP-RK3 at the
+    headline dt, copy boundaries; FP64 and mixed."""
+    import torch
+    blk = I.Block((n,) * 3, 3, (8.0 / n,) * 3, (4.0,) * 3)
+    met_h = I.schwarzschild_metric(blk)
+    prim_h = I.smooth_prims(blk, 1, gamma, rho_range=(1e-4, 1.28e-3), metric=met_h, b_amp=1e-3)
+    prim_h[4] = K * prim_h[0] ** gamma
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    met = torch.from_numpy(met_h).cuda()
+    dt = CFL * min(blk.dx)
+    out = {"workload": f"{n}^3 Schwarzschild block, polytrope K = {K}, Gamma = {gamma}, rho 1e-4..1.28e-3, "
+                       f"|v| <= 0.5, |B| <= 1e-3, WENO5+HLLE, SSP-RK3, dt = {CFL} dx, copy boundaries"}
+    for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
+        p = G.Params(gamma=gamma, recon=G.WENO5, bc=G.BC_COPY, precision=prec, eos=G.EOS_POLYTROPE, poly_K=K)
+        prim = torch.from_numpy(prim_h).cuda()
+        G.fill_ghosts(g, G.BC_COPY, prim)
+        cons = G.prim2con(g, p, prim, met)
+        ws = G.workspace(g, G.RK3)
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+            p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": blk.ncells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "steps": warmup + steps, "failed_cells": int(nfail.item())}
+    return out
+
+
 # ------------------------------------------------------------ 256^3 block --
 def large_block_bench(G, steps=3, warmup=1, n=256):
     """256^3 + 3 ghosts on the Schwarzschild background, planar Riemann jump
@@ -642,7 +683,8 @@ def main():
     ap.add_argument("--no-shocktube", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-ct", action="store_true")
-    ap.add_argument("--section", default=None, choices=["ct", "amr", "shocktube", "batched", "adjoint", "large"],
+    ap.add_argument("--no-poly", action="store_true")
+    ap.add_argument("--section", default=None, choices=["ct", "poly", "amr", "shocktube", "batched", "adjoint", "large"],
                     help="run only this section and print its JSON (profiling runs)")
     ap.add_argument("--tile", type=int, default=-1, help="RHS tile shape (default: autotuned)")
     ap.add_argument("--adjoint-n", type=int, default=64)
@@ -662,7 +704,7 @@ def main():
     from paper_2210_17509_gb300 import grmhd as G
 
     if args.section:
-        fns = {"ct": lambda: ct_bench(G, n=args.n), "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
+        fns = {"ct": lambda: ct_bench(G, n=args.n), "poly": lambda: poly_bench(G, n=args.n), "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
                "batched": lambda: batched_bench(G, args.steps, args.warmup),
                "adjoint": lambda: adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs),
                "large": lambda: large_block_bench(G)}
@@ -829,6 +871,9 @@ def main():
     ct = None
     if not args.no_ct:
         ct = ct_bench(G, n=args.n)
+    poly = None
+    if not args.no_poly:
+        poly = poly_bench(G, n=args.n)
 
     if rank != 0:
         return
@@ -854,6 +899,7 @@ def main():
         "shocktube": tube,
         "amr2": amr,
         "ct": ct,
+        "polytrope": poly,
         "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},

@@ -38,6 +38,7 @@ DevParams make_params(const grmhd_params& p) {
   d.flags = p.flags;
   d.eos = p.eos;
   d.poly_K = p.poly_K;
+  d.poly_g2 = p.gamma == 2.0;
   // the polytrope's atmosphere pressure
   if (p.eos == GRMHD_EOS_POLYTROPE) d.p_atm = p.poly_K * std::pow(p.rho_atm, p.gamma);
   return d;

@@ -37,6 +37,7 @@ struct DevParams {
   int flags;       // GRMHD_REUSE_GEOMETRY, ...
   int eos;         // GRMHD_EOS_IDEAL | GRMHD_EOS_POLYTROPE
   double poly_K;   // K of P = K rho^gamma (polytrope)
+  int poly_g2;     // polytrope with gamma == 2: K rho^(gamma - 1) = K rho, no pow
 };
 
 // What the RHS kernel does with the RHS value r of each interior cell:

@@ -320,15 +320,19 @@ __device__ __forceinline__ void lower(const T g[6], const T v[3], T vl[3]) {
 
 // Polytropic EOS (Sec. 2.3): the pressure entry of a state is K rho^gamma
 // (states with rho <= 0 are left to the physical-state checks).
+// K rho^(gamma - 1) of the polytrope: a plain product for gamma = 2 (the
+// paper's TOV polytrope, Sec. 4.4), pow otherwise.
+template <class T>
+__device__ __forceinline__ T poly_k_rho_gm1(const DevParams& p, T rho) {
+  if (p.poly_g2) return (T)p.poly_K * rho;
+  if constexpr (sizeof(T) == 4) return (float)p.poly_K * powf(rho, (float)(p.gamma - 1.0));
+  else return p.poly_K * pow(rho, p.gamma - 1.0);
+}
+
 template <class T>
 __device__ __forceinline__ void apply_polytrope_pair(const DevParams& p, T pL[8], T pR[8]) {
-  if constexpr (sizeof(T) == 4) {
-    if (pL[0] > 0.0f) pL[4] = (float)p.poly_K * powf(pL[0], (float)p.gamma);
-    if (pR[0] > 0.0f) pR[4] = (float)p.poly_K * powf(pR[0], (float)p.gamma);
-  } else {
-    if (pL[0] > 0.0) pL[4] = p.poly_K * pow(pL[0], p.gamma);
-    if (pR[0] > 0.0) pR[4] = p.poly_K * pow(pR[0], p.gamma);
-  }
+  if (pL[0] > T(0)) pL[4] = pL[0] * poly_k_rho_gm1<T>(p, pL[0]);
+  if (pR[0] > T(0)) pR[4] = pR[0] * poly_k_rho_gm1<T>(p, pR[0]);
 }
 
 // As physical_state, also returning the lowered velocity and v^2.

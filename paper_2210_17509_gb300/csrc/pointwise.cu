@@ -27,7 +27,7 @@ __global__ void prim2con_kernel(DevGrid g, DevParams p, const double* __restrict
     double pr[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) pr[q] = __ldg(prim + q * g.ncell + c);
-    if (p.eos == GRMHD_EOS_POLYTROPE && pr[0] > 0.0) pr[4] = p.poly_K * pow(pr[0], p.gamma);
+    if (p.eos == GRMHD_EOS_POLYTROPE && pr[0] > 0.0) pr[4] = pr[0] * poly_k_rho_gm1<double>(p, pr[0]);
     Geom<double> m;
     if (metric) {
       CellMetric cm;

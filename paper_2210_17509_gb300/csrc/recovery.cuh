@@ -248,18 +248,22 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 // - S^2 is <= 0 at W = 1 and grows without bound (monotonically for
 // gamma <= 2).  Newton from the guess W, on a bracket [lo, hi] kept from the
 // signs of f; a step that leaves the bracket bisects it (or doubles W while
-// no upper end is known).  tau is not used.  Returns 0 (Newton), 1 (a
-// bisection step was needed) or 2 (no root: atmosphere); z and W on success.
-__device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p, double& z, double& W) {
-  const double D = in.D, gm1 = p.gamma - 1.0;
+// no upper end is known).  The first step is accepted below tol_first (a
+// guess already good to 1e-6 leaves 1e-12 after one quadratic step), later
+// ones below nr_tol.  tau is not used.  Returns 0 (Newton), 1 (a bisection
+// step was needed) or 2 (no root: atmosphere); z and W on success.
+__device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p, double& z, double& W,
+                                             double tol_first) {
+  const double D = in.D;
   const double dzk = (2.0 - p.gamma) * p.gfac;
   double lo = 1.0, hi = INFINITY, w = W >= 1.0 ? W : 1.0;
   bool bis = false;
   for (int it = 0; it < p.nr_maxit + 200; ++it) {
-    const double kr = p.poly_K * pow(D / w, gm1);  // K rho^(gamma-1)
+    const double iw = 1.0 / w;
+    const double kr = poly_k_rho_gm1<double>(p, D * iw);  // K rho^(gamma-1)
     const double zz = D * w * (1.0 + p.gfac * kr);
-    const double dz = D * (1.0 + dzk * kr);         // dz/dW
-    const double zb = zz + in.B2, iw = 1.0 / w, iz = 1.0 / zz;
+    const double dz = D * (1.0 + dzk * kr);               // dz/dW
+    const double zb = zz + in.B2, iz = 1.0 / zz;
     const double v2 = 1.0 - iw * iw;
     const double f = zb * zb * v2 - in.BS2 * (2.0 * zz + in.B2) * iz * iz - in.S2;
     const double df = 2.0 * zb * (dz * v2 + zb * iw * iw * iw) + 2.0 * in.BS2 * dz * zb * iz * iz * iz;
@@ -270,14 +274,43 @@ __device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p
       wn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * lo;
       bis = true;
     }
-    if (fabs(wn - w) <= p.nr_tol * wn || (isfinite(hi) && hi - lo <= 1e-15 * hi)) {
+    const double tol = it == 0 ? tol_first : p.nr_tol;
+    if (fabs(wn - w) <= tol * wn || (isfinite(hi) && hi - lo <= 1e-15 * hi)) {
       W = wn;
-      z = D * wn * (1.0 + p.gfac * p.poly_K * pow(D / wn, gm1));
+      z = D * wn * (1.0 + p.gfac * poly_k_rho_gm1<double>(p, D / wn));
       return bis ? 1 : 0;
     }
     w = wn;
   }
   return 2;
+}
+
+// FP32 Newton predictor of the polytropic recovery (mixed path): W to
+// about 1e-6 from the guess, for the one FP64 step that follows.  Returns
+// false (W unchanged) if it does not get there in 8 steps.
+__device__ __forceinline__ bool c2p_polytrope_predict(const C2PIn& in, const DevParams& p, double& W) {
+  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2;
+  const float gfac = (float)p.gfac, dzk = (float)((2.0 - p.gamma) * p.gfac);
+  float w = fmaxf((float)W, 1.0f);
+#pragma unroll 1
+  for (int it = 0; it < 8; ++it) {
+    const float iw = 1.0f / w;
+    const float kr = poly_k_rho_gm1<float>(p, D * iw);
+    const float zz = D * w * (1.0f + gfac * kr);
+    const float dz = D * (1.0f + dzk * kr);
+    const float zb = zz + B2, iz = 1.0f / zz;
+    const float v2 = 1.0f - iw * iw;
+    const float f = zb * zb * v2 - BS2 * (2.0f * zz + B2) * iz * iz - S2;
+    const float df = 2.0f * zb * (dz * v2 + zb * iw * iw * iw) + 2.0f * BS2 * dz * zb * iz * iz * iz;
+    const float wn = fmaxf(w - f / df, 1.0f);
+    if (!isfinite(wn)) return false;
+    if (fabsf(wn - w) <= 1e-6f * wn) {
+      W = (double)wn;
+      return true;
+    }
+    w = wn;
+  }
+  return false;
 }
 
 // Recovery of the interior cell c (Sec. 2.3).  The incoming primitives of
@@ -362,7 +395,11 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   int st = 2;
   constexpr bool poly = POLY;
   if constexpr (POLY) {
-    if (D > 0.0) st = c2p_polytrope(in, p, z, W);
+    if (D > 0.0) {
+      double tol_first = p.nr_tol;
+      if (PREDICT && c2p_polytrope_predict(in, p, W)) tol_first = 1e-6;
+      st = c2p_polytrope(in, p, z, W, tol_first);
+    }
   } else if (D > 0.0 && tau + D > 0.0) {
     double tol_first = p.nr_tol;
     if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
@@ -377,7 +414,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
       const float X = 1.0f / (Wf * zf * zbf);
       const float iW = zf * zbf * X, iz = Wf * zbf * X, izb = Wf * zf * X;
       const float rho = (float)D * iW;
-      const float P = poly ? (float)p.poly_K * powf(rho, (float)p.gamma) : (float)p.gm1g * (zf * iW * iW - rho);
+      const float P = poly ? rho * poly_k_rho_gm1<float>(p, rho) : (float)p.gm1g * (zf * iW * iW - rho);
       const float bsz = (float)BS * iz;
       float gf[6], guf[6];
 #pragma unroll
@@ -424,7 +461,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const double X = 1.0 / (W * z * zb);
     const double iW = z * zb * X, iz = W * zb * X, izb = W * z * X;
     const double rho = D * iW;
-    const double P = poly ? p.poly_K * pow(rho, p.gamma) : p.gm1g * (z * iW * iW - rho);
+    const double P = poly ? rho * poly_k_rho_gm1<double>(p, rho) : p.gm1g * (z * iW * iW - rho);
     const double bsz = BS * iz;
     double vlo[3], vu[3];
 #pragma unroll

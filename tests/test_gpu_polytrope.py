@@ -45,7 +45,7 @@ def interior(a, ng=3):
     return a[(slice(None),) + tuple(slice(ng, s - ng) for s in a.shape[1:])]
 
 
-def case(n, seed, curved, vmax=0.9, b_scale=1.0, log_rho=(-4.0, -2.5)):
+def case(n, seed, curved, vmax=0.9, b_scale=1.0, log_rho=(-4.0, -2.5), K=K, GAM=GAM):
     n = tuple(n)
     if curved:
         h = 8.0 / max(n)
@@ -58,7 +58,7 @@ def case(n, seed, curved, vmax=0.9, b_scale=1.0, log_rho=(-4.0, -2.5)):
     return blk, m, prim
 
 
-def params(G, recon=None, bc=None, precision=None):
+def params(G, recon=None, bc=None, precision=None, K=K, GAM=GAM):
     p = G.Params(gamma=GAM, eos=G.EOS_POLYTROPE, poly_K=K)
     if recon is not None:
         p.recon = recon
@@ -69,36 +69,44 @@ def params(G, recon=None, bc=None, precision=None):
     return p
 
 
-def oparams(recon=O.REC_WENO5, bc=O.BC_PERIODIC):
+def oparams(recon=O.REC_WENO5, bc=O.BC_PERIODIC, K=K, GAM=GAM):
     return O.make_params(gamma=GAM, recon=recon, bc=bc, eos=O.EOS_POLYTROPE, poly_K=K)
 
 
+# gamma = 2 takes the product form of K rho^(gamma - 1) on the GPU, other gammas pow
+EOS_CASES = [(100.0, 2.0), (10.0, 5.0 / 3.0)]
+
+
 @pytest.mark.parametrize("curved", [False, True])
-def test_prim2con_and_recovery(G, curved):
-    blk, m, prim = case((12, 10, 9), 3, curved)
+@pytest.mark.parametrize("eos", EOS_CASES)
+def test_prim2con_and_recovery(G, curved, eos):
+    Kc, Gc = eos
+    blk, m, prim = case((12, 10, 9), 3, curved, K=Kc, GAM=Gc)
     og = O.Grid(blk.n, 3, blk.dx)
     gg = G.Grid(blk.n, 3, blk.dx)
     junk = prim.copy()
     junk[4] *= np.random.default_rng(2).uniform(0.2, 5.0, junk[4].shape)
-    ref_cons = O.prim2con(og, GAM, prim, m, params=oparams())
+    op = oparams(K=Kc, GAM=Gc)
+    gpp = params(G, K=Kc, GAM=Gc)
+    ref_cons = O.prim2con(og, Gc, prim, m, params=op)
     gm = None if m is None else cuda(m)
-    gcons = host(G.prim2con(gg, params(G), cuda(junk), gm))
+    gcons = host(G.prim2con(gg, gpp, cuda(junk), gm))
     assert np.all(normwise(gcons, ref_cons) <= FP64_TOL)
-    ref, st, nf = O.con2prim(og, oparams(), ref_cons, m, prim)
+    ref, st, nf = O.con2prim(og, op, ref_cons, m, prim)
     assert nf == 0
     guess = prim.copy()
     guess[1:4] *= 0.8
     gp = cuda(guess)
     status = torch.zeros(gg.shape, dtype=torch.int8, device="cuda")
     nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
-    G.con2prim(gg, params(G), cuda(ref_cons), gp, gm, status=status, nfail=nfail)
+    G.con2prim(gg, gpp, cuda(ref_cons), gp, gm, status=status, nfail=nfail)
     assert int(host(nfail)[0]) == 0
     assert np.all(normwise(interior(host(gp)), interior(ref)) <= FP64_TOL)
     # tau is not read
     c2 = ref_cons.copy()
     c2[4] *= 3.0
     gp2 = cuda(guess)
-    G.con2prim(gg, params(G), cuda(c2), gp2, gm)
+    G.con2prim(gg, gpp, cuda(c2), gp2, gm)
     assert np.array_equal(host(gp2), host(gp))
 
 
@@ -120,19 +128,21 @@ def test_rhs(G, curved, recon, mixed):
 
 
 @pytest.mark.parametrize("mode", ["fp64_cached", "fp64_uncached", "mixed"])
-def test_rk3_steps(G, mode):
-    blk, m, prim = case((18, 12, 10), 7, True, vmax=0.5, b_scale=0.3, log_rho=(-3.5, -3.0))
+@pytest.mark.parametrize("eos", EOS_CASES)
+def test_rk3_steps(G, mode, eos):
+    Kc, Gc = eos
+    blk, m, prim = case((18, 12, 10), 7, True, vmax=0.5, b_scale=0.3, log_rho=(-3.5, -3.0), K=Kc, GAM=Gc)
     og = O.Grid(blk.n, 3, blk.dx)
     prim = O.fill_ghosts(og, O.BC_COPY, prim)
-    op = oparams(O.REC_WENO5, O.BC_COPY)
-    cons = O.prim2con(og, GAM, prim, m, params=op)
+    op = oparams(O.REC_WENO5, O.BC_COPY, K=Kc, GAM=Gc)
+    cons = O.prim2con(og, Gc, prim, m, params=op)
     dt = 0.25 * blk.dx[0]
     c, pr = cons, prim
     for _ in range(2):
         c, pr, nf = O.rk_step(og, op, O.RK3, dt, c, pr, m)
         assert nf == 0
     gg = G.Grid(blk.n, 3, blk.dx)
-    p = params(G, G.WENO5, G.BC_COPY, G.MIXED if mode == "mixed" else None)
+    p = params(G, G.WENO5, G.BC_COPY, G.MIXED if mode == "mixed" else None, K=Kc, GAM=Gc)
     gc, gp, gm = cuda(cons), cuda(prim), cuda(m)
     ws = G.workspace(gg, G.RK3, cached=(mode != "fp64_uncached"))
     nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
