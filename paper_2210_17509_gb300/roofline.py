@@ -21,9 +21,9 @@ metric, geometry cache): prim 8 x 8 B + geometry cache 53 x 8 B read, rhs
 instead of the cache: 208 B).
 
 Measured DRAM traffic of that launch (ncu, dram__bytes_read.sum +
-dram__bytes_write.sum): 645.3 MB for the 96^3 block (884,736 cells, capture
-in profiles/rhs_kernel_fp64_cached_weno5_curved_96cube.md), 729.4 B per cell;
-traffic grows with the cell count, so a launch on n^3 cells is 729.4 n^3 B.
+dram__bytes_write.sum): 648.4 MB for the 96^3 block (884,736 cells, capture
+in profiles/rhs_kernel_fp64_cached_weno5_curved_96cube.md), 732.9 B per cell;
+traffic grows with the cell count, so a launch on n^3 cells is 732.9 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
 BYTES_PER_CELL_RHS_CURVED = 552
-TRAFFIC_PER_CELL_MEASURED = 645.3e6 / 884736
+TRAFFIC_PER_CELL_MEASURED = 648.4e6 / 884736
 FP64_PEAK_TFLOPS_MEASURED = 1.20
 FP32_PEAK_TFLOPS_MEASURED = 75.0
 HBM_FALLBACK_GBS = 6800.0
