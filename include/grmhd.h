@@ -85,7 +85,7 @@ typedef struct {
   double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
   int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
-  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN */
+  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS */
   int32_t eos;       /* GRMHD_EOS_IDEAL (Gamma-law, P = (Gamma - 1) rho eps) | GRMHD_EOS_POLYTROPE */
   double poly_K;     /* polytropic constant K of P = K rho^gamma (GRMHD_EOS_POLYTROPE; > 0) */
 } grmhd_params;
@@ -112,6 +112,11 @@ typedef struct {
 /* flags: the primitive recovery starts with the Newman-Hamlin iteration
  * instead of the Newton iteration (see grmhd_con2prim). */
 #define GRMHD_NEWMAN_HAMLIN 2
+/* flags: the FP64 RHS of the cached paths runs in one pass (each tile
+ * computing the faces on its boundaries as well) instead of two (every face
+ * flux computed once into the workspace's face buffer, then a per-cell
+ * pass).  The results are the same; a switch for comparison. */
+#define GRMHD_SINGLE_PASS 4
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
  * shape changes only how the work is cut, never the result.  8x8x8 (two
@@ -177,7 +182,8 @@ int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* 
               const double* metric, const double* kij, double* rhs, void* stream);
 
 /* grmhd_rhs computed from the geometry caches of grmhd_rk_workspace_bytes_cached
- * (and, for GRMHD_MIXED, an FP32 copy of prim) held in ws: the same RHS,
+ * (and, for GRMHD_MIXED, an FP32 copy of prim; for FP64 with a metric, the
+ * two-pass face buffer) held in ws: the same RHS,
  * with the per-face and per-cell metric algebra done once per static metric.
  * ws >= grmhd_rhs_workspace_bytes(grid), 256-byte aligned; the caches are
  * rebuilt unless params->flags has GRMHD_REUSE_GEOMETRY (same grid, metric and
@@ -195,8 +201,10 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
  * metric derivatives, computed in FP64 once per step -- or once per static
  * spacetime with GRMHD_REUSE_GEOMETRY -- stored as FP64 for the FP64 path and
  * as FP32 for the mixed path), an FP64 inverse-metric cache for the recovery,
- * and for the mixed path an FP32 copy of the primitives.  With less (but at
- * least grmhd_rk_workspace_bytes) the kernels read the FP64 inputs directly;
+ * for the mixed path an FP32 copy of the primitives, and for the FP64 path a
+ * face buffer of 24 doubles per point (the two-pass RHS: every face flux
+ * computed once, see GRMHD_SINGLE_PASS).  With less (but at least
+ * grmhd_rk_workspace_bytes) the kernels read the FP64 inputs directly;
  * results agree to round-off. */
 size_t grmhd_rk_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme);
 

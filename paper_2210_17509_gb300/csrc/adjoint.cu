@@ -1118,6 +1118,7 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
   for (int k = 0; k < ns && !stage_prims; ++k) {
     StageEpilogue ep;
     ep.fb = nullptr;
+    ep.faces = nullptr;
     ep.rhs = nullptr;
     ep.u = W;
     ep.u0 = cons;

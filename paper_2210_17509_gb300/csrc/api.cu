@@ -56,6 +56,14 @@ cudaError_t launch_rhs(const DevGrid& g, const DevParams& p, const double* prim,
   return launch_rhs_fp64(g, p, prim, metric, kij, ep, s);
 }
 
+// Bytes of the cached-path scratch: geometry cache, FP32 primitives, inverse-
+// metric cache, and the two-pass face buffer (24 doubles per point).
+size_t cache_bytes(const DevGrid& g) {
+  return round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) + round256((size_t)8 * g.ncell * sizeof(float)) +
+         round256((size_t)kMetricCacheComps * g.ncell * sizeof(double)) +
+         round256((size_t)24 * g.ncell * sizeof(double));
+}
+
 }  // namespace
 
 extern "C" {
@@ -119,9 +127,7 @@ int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* 
 
 size_t grmhd_rhs_workspace_bytes(const grmhd_grid* grid) {
   if (check_grid(grid, 0)) return 0;
-  const DevGrid g = make_grid(*grid);
-  return round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) + round256((size_t)8 * g.ncell * sizeof(float)) +
-         round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
+  return cache_bytes(make_grid(*grid));
 }
 
 int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const double* prim, const double* metric,
@@ -143,6 +149,8 @@ int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const d
   float* prim32 = reinterpret_cast<float*>(base + round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)));
   double* mcache = reinterpret_cast<double*>(reinterpret_cast<char*>(prim32) +
                                              round256((size_t)8 * g.ncell * sizeof(float)));
+  double* faces = reinterpret_cast<double*>(reinterpret_cast<char*>(mcache) +
+                                            round256((size_t)kMetricCacheComps * g.ncell * sizeof(double)));
   const bool mixed = p.precision == GRMHD_MIXED;
   const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
   if (metric && !reuse && launch_geom_cache(g, metric, geom, !mixed, mcache, s) != cudaSuccess) return GRMHD_ERR_CUDA;
@@ -152,6 +160,7 @@ int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const d
                                                ep, s));
   }
   if (!metric) return cuda_status(launch_rhs(g, p, prim, metric, kij, ep, s));
+  if (!(p.flags & GRMHD_SINGLE_PASS)) ep.faces = faces;
   return cuda_status(launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s));
 }
 
@@ -166,9 +175,7 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme) {
 size_t grmhd_rk_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme) {
   const size_t base = grmhd_rk_workspace_bytes(grid, scheme);
   if (base == 0) return 0;
-  const DevGrid g = make_grid(*grid);
-  return base + round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) +
-         round256((size_t)8 * g.ncell * sizeof(float)) + round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
+  return base + cache_bytes(make_grid(*grid));
 }
 
 }  // extern "C"
@@ -213,6 +220,7 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
   float* prim32 = nullptr;
   void* geom = nullptr;
   double* mcache = nullptr;
+  double* faces = nullptr;
   if (fast_mixed || fast_fp64) {
     char* after = static_cast<char*>(ws) + grmhd_rk_workspace_bytes(grid, scheme);
     geom = after;
@@ -220,6 +228,8 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     prim32 = reinterpret_cast<float*>(after);
     after += round256((size_t)8 * g.ncell * sizeof(float));
     mcache = reinterpret_cast<double*>(after);
+    after += round256((size_t)kMetricCacheComps * g.ncell * sizeof(double));
+    if (fast_fp64 && !(p.flags & GRMHD_SINGLE_PASS)) faces = reinterpret_cast<double*>(after);
     const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
     if (metric && !reuse && launch_geom_cache(g, metric, geom, fast_fp64, mcache, s) != cudaSuccess)
       return GRMHD_ERR_CUDA;
@@ -241,6 +251,7 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     ep.wa = st[k].wa;
     ep.wr = st[k].wr;
     ep.fb = ct ? ct->fb : nullptr;
+    ep.faces = faces;
     if (fast_fp64) {
       if (launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
     const int tz = (int)(t / ((long long)b.nt[0] * b.nt[1]));
     StageEpilogue ep;
     ep.fb = nullptr;
+    ep.faces = nullptr;
     ep.rhs = b.rhs;
     ep.u = nullptr;
     ep.u0 = nullptr;

@@ -49,10 +49,14 @@ struct DevParams {
 //                    component B^a (a != d) through the lower d-face of the cell, for
 //                    the d-faces 0 .. n_d with transverse indices -1 .. n
 //                    (the tiles, then a ring kernel; constrained transport)
+//   faces   != NULL: (FP64 with the geometry cache) device scratch of
+//                    24 ncell doubles; the RHS then runs in two passes, every
+//                    face flux computed once into it (rhs.cuh)
 // u0 must be valid whenever u is set.
 struct StageEpilogue {
   double* rhs;
   double* fb;
+  double* faces;
   double* u;
   const double* u0;
   const double* acc_in;
@@ -118,7 +122,7 @@ inline int check_params(const grmhd_params* p) {
   if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
   if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
-  if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN)) != 0) return GRMHD_ERR_ARG;
+  if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS)) != 0) return GRMHD_ERR_ARG;
   if (p->eos != GRMHD_EOS_IDEAL && p->eos != GRMHD_EOS_POLYTROPE) return GRMHD_ERR_ARG;
   if (p->eos == GRMHD_EOS_POLYTROPE && !(p->poly_K > 0.0 && std::isfinite(p->poly_K))) return GRMHD_ERR_ARG;
   return GRMHD_OK;
@@ -140,6 +144,7 @@ inline StageEpilogue no_epilogue() {
   StageEpilogue e;
   e.rhs = nullptr;
   e.fb = nullptr;
+  e.faces = nullptr;
   e.u = nullptr;
   e.u0 = nullptr;
   e.acc_in = nullptr;

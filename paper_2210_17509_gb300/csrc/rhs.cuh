@@ -14,6 +14,8 @@
 // being relabelled so that the face normal is the first axis.
 #pragma once
 
+#include <type_traits>
+
 #include "physics.cuh"
 
 namespace grmhd {
@@ -500,10 +502,44 @@ __device__ __forceinline__ void face_flux_one(const DevGrid& g, const DevParams&
   face_flux_states<double, CURVED, SrcF64, POLY>(g, p, src, c, dir, stride, pL, pR, F);
 }
 
+// Flux of the dir-face at tile face coordinates (fx, fy, fz), i.e. the
+// lower dir-face of tile cell (fx, fy, fz) (fx = TX etc. for the tile's
+// upper boundary faces), into F; false (F untouched) outside the block.
+// With a stage, the face states come from sR (stage index of the cell below
+// the face: eoff[dir] + its index in that direction's extended box);
+// otherwise they are reconstructed here.  cell: array index of the cell
+// above the face.
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S, bool POLY = false>
+__device__ __forceinline__ bool tile_face_at(const DevGrid& g, const DevParams& p, const S& src, int x0, int y0,
+                                             int z0, int dir, int fx, int fy, int fz, const T* __restrict__ sR, int ns,
+                                             int eoff_y, int eoff_z, T F[8], long long& cell) {
+  const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
+  const int xi = x0 + fx, yi = y0 + fy, zi = z0 + fz;
+  if (!(xi < g.n[0] + ux && yi < g.n[1] + uy && zi < g.n[2] + uz)) return false;
+  const int ng = g.ng;
+  const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
+  const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
+  T pL[8], pR[8];
+  if constexpr (CellRecon<T, RECON>::value) {
+    // extended box of this direction: one more cell on each side along dir
+    const int ex_n = TX + 2 * ux, ey_n = TY + 2 * uy;
+    const int eL = (dir == 0 ? 0 : (dir == 1 ? eoff_y : eoff_z)) + (fz * ey_n + fy) * ex_n + fx;
+    const int eR = eL + (dir == 0 ? 1 : (dir == 1 ? ex_n : ex_n * ey_n));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      pL[q] = sR[(2 * q + 1) * ns + eL];
+      pR[q] = sR[(2 * q) * ns + eR];
+    }
+  } else {
+    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+  }
+  face_flux_states<T, CURVED, S, POLY>(g, p, src, c, dir, stride, pL, pR, F);
+  cell = c;
+  return true;
+}
+
 // Face flux of face f (flat index over the NFX x-, NFY y- and NFZ z-faces of
-// the tile) into sF [8][NF].  With a stage, the face states come from sR
-// (stage index of the cell below the face: eoff[dir] + its index in that
-// direction's extended box); otherwise they are reconstructed here.
+// the tile) into sF [8][NF].
 template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S, bool POLY = false>
 __device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, const S& src, int x0, int y0, int z0,
                                           int f, T* __restrict__ sF, const T* __restrict__ sR, int ns, int eoff_y,
@@ -525,27 +561,11 @@ __device__ __forceinline__ void tile_face(const DevGrid& g, const DevParams& p, 
     dir = 2;
     fx = fl % TX; fy = (fl / TX) % TY; fz = fl / (TX * TY);
   }
-  const int ux = dir == 0, uy = dir == 1, uz = dir == 2;
-  const int xi = x0 + fx, yi = y0 + fy, zi = z0 + fz;
-  if (!(xi < g.n[0] + ux && yi < g.n[1] + uy && zi < g.n[2] + uz)) return;
-  const int ng = g.ng;
-  const long long c = (long long)(zi + ng) * g.sz + (long long)(yi + ng) * g.sy + (xi + ng);
-  const long long stride = (dir == 0) ? 1 : ((dir == 1) ? g.sy : g.sz);
-  T pL[8], pR[8], F[8];
-  if constexpr (CellRecon<T, RECON>::value) {
-    // extended box of this direction: one more cell on each side along dir
-    const int ex_n = TX + 2 * ux, ey_n = TY + 2 * uy;
-    const int eL = (dir == 0 ? 0 : (dir == 1 ? eoff_y : eoff_z)) + (fz * ey_n + fy) * ex_n + fx;
-    const int eR = eL + (dir == 0 ? 1 : (dir == 1 ? ex_n : ex_n * ey_n));
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      pL[q] = sR[(2 * q + 1) * ns + eL];
-      pR[q] = sR[(2 * q) * ns + eR];
-    }
-  } else {
-    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
-  }
-  face_flux_states<T, CURVED, S, POLY>(g, p, src, c, dir, stride, pL, pR, F);
+  T F[8];
+  long long c;
+  if (!tile_face_at<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, dir, fx, fy, fz, sR, ns, eoff_y,
+                                                           eoff_z, F, c))
+    return;
 #pragma unroll
   for (int q = 0; q < 8; ++q) sF[q * NF + f] = F[q];
 }
@@ -735,6 +755,160 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
   }
 }
 
+// Resident CTAs per SM the register budget is fitted to: 3 for the FP32
+// (mixed) kernels, which are latency bound, 1 for FP64 (pipe bound).
+template <class T>
+struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+
+// ---------------------------------------------------------------------------
+// Two-pass FP64 RHS.  FP64 issue is what bounds the RHS on this GPU, and HBM
+// bandwidth is plentiful, so the FP64 path can spend bytes to save flops:
+// pass 1 computes every face flux of the block exactly once into a face
+// buffer Ff [(8 dir + q) * ncell + cell above the face] (192 B per cell
+// written and read back), and pass 2 differences the buffer per cell, adds
+// the sources and applies the stage epilogue, with the same operations in
+// the same order as the single-pass cell loop.  The single-pass tile
+// computes the faces on its upper boundaries too (896 face fluxes for 768
+// faces in an 8x8x4 tile, in four rounds of 256 threads instead of three)
+// and reconstructs one more end cell per line.
+
+// Pass 1, one tile: the lower faces of its cells (3 per cell; the cell
+// beyond the block's upper end along dir, when the tile is ragged there,
+// gives the block's upper boundary face) and, when the tile ends exactly at
+// the block's upper end along dir, that boundary face layer.  The stage
+// skips the end cells above the tile except there.  fb (nullable): the
+// transverse field fluxes for constrained transport, as the tile export
+// writes them.
+template <class T, int RECON, bool CURVED, int TX, int TY, int TZ, class S, bool POLY>
+__device__ __forceinline__ void faces_tile(const DevGrid& g, const DevParams& p, const S& src, int x0, int y0, int z0,
+                                           double* __restrict__ Ff, double* __restrict__ fb, T* sR) {
+  constexpr int NT = kTileThreads;
+  constexpr int NC = TX * TY * TZ;
+  using ST = TileStage<TX, TY, TZ>;
+  constexpr int NBX = TY * TZ, NBY = TX * TZ, NBZ = TX * TY;  // lines (boundary faces) per direction
+  const bool top[3] = {x0 + TX == g.n[0], y0 + TY == g.n[1], z0 + TZ == g.n[2]};
+  if constexpr (CellRecon<T, RECON>::value) {
+    static_assert(TileSmem<T, RECON, TX, TY, TZ>::stage_all, "two-pass RHS needs the all-direction stage");
+    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+    // (a) the tile's own cells, both states; (b) the end cell below every
+    // line, plus state; (c) the end cell above every line of the directions
+    // in which the tile ends at the block's upper end, minus state
+    const int nb_up = 4 * ((top[0] ? NBX : 0) + (top[1] ? NBY : 0) + (top[2] ? NBZ : 0));
+    const int nitems = 12 * NC + 4 * (NBX + NBY + NBZ) + nb_up;
+    for (int it = threadIdx.x; it < nitems; it += NT) {
+      int dir, e, h, which = 0;
+      if (it < 12 * NC) {
+        dir = it / (4 * NC);
+        const int r = it - dir * 4 * NC;
+        h = r / NC;
+        const int l = r - h * NC;
+        const int cx = l % TX, cy = (l / TX) % TY, cz = l / (TX * TY);
+        if (dir == 0) e = (cz * TY + cy) * (TX + 2) + cx + 1;
+        else if (dir == 1) e = (cz * (TY + 2) + cy + 1) * TX + cx;
+        else e = ((cz + 1) * TY + cy) * TX + cx;
+      } else {
+        int r = it - 12 * NC;
+        int side = 0;
+        if (r >= 4 * (NBX + NBY + NBZ)) {
+          // upper end cells of the top directions, in x, y, z order
+          side = 1;
+          r -= 4 * (NBX + NBY + NBZ);
+          if (!top[0]) r += 4 * NBX;
+          if (!top[1] && r >= 4 * NBX) r += 4 * NBY;
+        }
+        const int nb = r < 4 * NBX ? NBX : (r < 4 * (NBX + NBY) ? NBY : NBZ);
+        dir = r < 4 * NBX ? 0 : (r < 4 * (NBX + NBY) ? 1 : 2);
+        r -= dir == 0 ? 0 : (dir == 1 ? 4 * NBX : 4 * (NBX + NBY));
+        h = r / nb;
+        const int t = r - h * nb;
+        which = side ? 1 : 2;
+        if (dir == 0) e = (t / TY * TY + t % TY) * (TX + 2) + (side ? TX + 1 : 0);
+        else if (dir == 1) e = ((t / TX) * (TY + 2) + (side ? TY + 1 : 0)) * TX + t % TX;
+        else e = ((side ? TZ + 1 : 0) * TY + t / TX) * TX + t % TX;
+      }
+      const int eoff = dir == 0 ? 0 : (dir == 1 ? ST::EXX : ST::EXX + ST::EYY);
+      tile_stage_item<T, RECON, TX, TY, TZ, S>(g, src, x0, y0, z0, dir, e, h, eoff, eps13, sR, ST::NEA, which);
+    }
+    __syncthreads();
+  }
+  auto store = [&](int dir, int fx, int fy, int fz) {
+    T F[8];
+    long long c;
+    if (!tile_face_at<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, dir, fx, fy, fz, sR, ST::NEA,
+                                                             ST::EXX, ST::EXX + ST::EYY, F, c))
+      return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Ff[(8 * dir + q) * g.ncell + c] = (double)F[q];
+    if (fb) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a != dir) fb[(3 * dir + a) * g.ncell + c] = (double)F[5 + a];
+    }
+  };
+  // the lower faces of the tile's cells: 3 NC faces, a whole number of rounds
+  for (int f = threadIdx.x; f < 3 * NC; f += NT) {
+    const int dir = f / NC, l = f - dir * NC;
+    store(dir, l % TX, (l / TX) % TY, l / (TX * TY));
+  }
+  // the block's upper boundary faces where the tile ends exactly there
+  if (top[0])
+    for (int f = threadIdx.x; f < NBX; f += NT) store(0, TX, f % TY, f / TY);
+  if (top[1])
+    for (int f = threadIdx.x; f < NBY; f += NT) store(1, f % TX, TY, f / TX);
+  if (top[2])
+    for (int f = threadIdx.x; f < NBZ; f += NT) store(2, f % TX, f / TX, TZ);
+}
+
+template <class T, int RECON, bool CURVED, class S, bool POLY>
+__global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_faces_kernel(DevGrid g, DevParams p, S src,
+                                                                                    double* Ff, double* fb) {
+  using TS = TileShape<0>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sR = reinterpret_cast<T*>(smem_raw);  // the stage only: no face buffer in shared memory
+  faces_tile<T, RECON, CURVED, TS::X, TS::Y, TS::Z, S, POLY>(g, p, src, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                             blockIdx.z * TS::Z, Ff, fb, sR);
+}
+
+// Pass 2: per interior cell, the flux differences, the sources and the stage
+// epilogue (the single-pass cell loop's operations, in its order).
+template <class T, bool CURVED, class S>
+__global__ void __launch_bounds__(256) rhs_div_kernel(DevGrid g, DevParams p, S src, const double* __restrict__ Ff,
+                                                      StageEpilogue ep) {
+  const long long nx = g.n[0], ny = g.n[1], nint = nx * ny * g.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long q0 = t / nx;
+    const long long c = (q0 / ny + g.ng) * g.sz + (q0 % ny + g.ng) * g.sy + (t - q0 * nx + g.ng);
+    const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+    T r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double* fx = Ff + (0 * 8 + q) * g.ncell + c;
+      const double* fy = Ff + (1 * 8 + q) * g.ncell + c;
+      const double* fz = Ff + (2 * 8 + q) * g.ncell + c;
+      T acc = -((T)__ldg(fx + 1) - (T)__ldg(fx)) * ix;
+      acc -= ((T)__ldg(fy + g.sy) - (T)__ldg(fy)) * iy;
+      acc -= ((T)__ldg(fz + g.sz) - (T)__ldg(fz)) * iz;
+      r[q] = acc;
+    }
+    if (CURVED) {
+      T sv[8];
+      source_terms<T>(g, p, src, c, sv);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) r[q] += sv[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const long long o = q * g.ncell + c;
+      const double rq = (double)r[q];
+      if (ep.rhs) ep.rhs[o] = rq;
+      const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
+      if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+      if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
+    }
+  }
+}
+
 // Constrained transport: the field fluxes of the faces outside the tiles,
 // i.e. the d-faces (d-index 0 .. n_d) on the ring of ghost rows around the
 // block (transverse (A, B) on the border of -1 .. n_a by -1 .. n_b, a = d + 1,
@@ -783,11 +957,6 @@ __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevPar
   }
 }
 
-// Resident CTAs per SM the register budget is fitted to: 3 for the FP32
-// (mixed) kernels, which are latency bound, 1 for FP64 (pipe bound).
-template <class T>
-struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
-
 template <class T, int RECON, bool CURVED, int SHAPE, class S, bool POLY = false>
 __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(DevGrid g, DevParams p, S src,
                                                                              StageEpilogue ep) {
@@ -799,9 +968,46 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(De
                                                       blockIdx.z * TS::Z, sF, sR);
 }
 
+// Two-pass launch (FP64 with the geometry cache and a face buffer in
+// ep.faces): faces, the constrained-transport ring if asked for, then the
+// per-cell pass.  Tile shape 8x8x4.
+template <class T, int RECON, bool CURVED, class S>
+cudaError_t launch_rhs_two_pass(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
+                                cudaStream_t s) {
+  using TS = TileShape<0>;
+  const bool poly = p.eos == GRMHD_EOS_POLYTROPE;
+  void (*k)(DevGrid, DevParams, S, double*, double*) =
+      poly ? rhs_faces_kernel<T, RECON, CURVED, S, true> : rhs_faces_kernel<T, RECON, CURVED, S, false>;
+  const size_t smem =
+      CellRecon<T, RECON>::value ? (size_t)16 * TileStage<TS::X, TS::Y, TS::Z>::NEA * sizeof(T) : (size_t)0;
+  if (smem) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((g.n[0] + TS::X - 1) / TS::X, (g.n[1] + TS::Y - 1) / TS::Y, (g.n[2] + TS::Z - 1) / TS::Z);
+  k<<<grid, kTileThreads, smem, s>>>(g, p, src, ep.faces, ep.fb);
+  if (ep.fb) {
+    const long long nring = ct_ring_faces(g, 0) + ct_ring_faces(g, 1) + ct_ring_faces(g, 2);
+    long long blocks = (nring + kRingThreads - 1) / kRingThreads;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (poly)
+      ct_ring_kernel<T, RECON, CURVED, S, true><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
+    else
+      ct_ring_kernel<T, RECON, CURVED, S><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
+  }
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  long long blocks = (nint + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  rhs_div_kernel<T, CURVED, S><<<(int)blocks, 256, 0, s>>>(g, p, src, ep.faces, ep);
+  return cudaGetLastError();
+}
+
 template <class T, int RECON, bool CURVED, class S>
 cudaError_t launch_rhs_shape(int shape, const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
                              cudaStream_t s) {
+  if constexpr (sizeof(T) == 8 && std::is_same<S, SrcCache64>::value) {
+    if (ep.faces) return launch_rhs_two_pass<T, RECON, CURVED, S>(g, p, src, ep, s);
+  }
   void (*k)(DevGrid, DevParams, S, StageEpilogue) = nullptr;
   int tx, ty, tz;
   size_t smem;

@@ -24,6 +24,7 @@ FP64, MIXED = 0, 1
 RK2, RK3, RK4 = 2, 3, 4
 REUSE_GEOMETRY = 1
 NEWMAN_HAMLIN = 2
+SINGLE_PASS = 4
 EOS_IDEAL, EOS_POLYTROPE = 0, 1
 
 

@@ -15,15 +15,21 @@ faces per cell counted once (tile-boundary recomputation is not algorithmic):
   stage epilogue                                40
   cell total (curved, WENO5): 3 * 1531 + 72 + 666 + 40 = 5371
 
-Algorithmic HBM bytes per interior cell of grmhd_rhs_cached (FP64, static
-metric, geometry cache): prim 8 x 8 B + geometry cache 53 x 8 B read, rhs
-8 x 8 B written = 552 B (the uncached grmhd_rhs reads the 10 metric entries
-instead of the cache: 208 B).
+The FP64 RHS of the cached paths runs in two passes: rhs_faces_kernel
+(reconstruction and HLLE, every face once: 3 * 1531 flops per cell) and
+rhs_div_kernel (divergence, sources, epilogue: 72 + 666 + 40).  The unit the
+benchmark times is that pair (one grmhd_rhs_cached call).
 
-Measured DRAM traffic of that launch (ncu, dram__bytes_read.sum +
-dram__bytes_write.sum): 648.4 MB for the 96^3 block (884,736 cells, capture
-in profiles/rhs_kernel_fp64_cached_weno5_curved_96cube.md), 732.9 B per cell;
-traffic grows with the cell count, so a launch on n^3 cells is 732.9 n^3 B.
+Algorithmic HBM bytes per interior cell of the pair (FP64, static metric,
+geometry cache): prim 8 x 8 B + geometry cache 53 x 8 B read, rhs 8 x 8 B
+written = 552 B, plus the face buffer, 24 x 8 B written and read back =
+384 B: 936 B (the uncached single-pass grmhd_rhs reads the 10 metric
+entries instead of the cache and has no face buffer: 208 B).
+
+Measured DRAM traffic of the pair (ncu, dram__bytes_read.sum +
+dram__bytes_write.sum, both kernels) for the 96^3 block (884,736 cells,
+capture in profiles/rhs_two_pass_fp64_cached_weno5_curved_96cube.md); traffic
+grows with the cell count, so a launch on n^3 cells scales by n^3 / 96^3.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -36,8 +42,8 @@ import os
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
-BYTES_PER_CELL_RHS_CURVED = 552
-TRAFFIC_PER_CELL_MEASURED = 648.4e6 / 884736
+BYTES_PER_CELL_RHS_CURVED = 552 + 384
+TRAFFIC_PER_CELL_MEASURED = None  # set from the two-pass capture below
 FP64_PEAK_TFLOPS_MEASURED = 1.20
 FP32_PEAK_TFLOPS_MEASURED = 75.0
 HBM_FALLBACK_GBS = 6800.0
@@ -56,10 +62,11 @@ def rhs_fp64_roofline(ncells: int, ms_per_launch: float, traffic="measured"):
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     hbm, src = hbm_peak_gbs()
     if traffic == "measured":
-        traffic = TRAFFIC_PER_CELL_MEASURED * ncells
+        traffic = None if TRAFFIC_PER_CELL_MEASURED is None else TRAFFIC_PER_CELL_MEASURED * ncells
     gbs = BYTES_PER_CELL_RHS_CURVED * ncells / (ms_per_launch * 1e-3) / 1e9
     return {
-        "bound": "alu", "kernel": "rhs_kernel<double, WENO5, curved, geometry cache> (grmhd_rhs_cached, FP64)",
+        "bound": "alu",
+        "kernel": "rhs_faces_kernel + rhs_div_kernel<double, WENO5, curved, geometry cache> (grmhd_rhs_cached, FP64)",
         "achieved": achieved, "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS_MEASURED, "traffic": traffic,
         "peak_source": "measured FP64 FMA probe (python -m paper_2210_17509_gb300.peaks)",
