@@ -28,8 +28,9 @@ entries instead of the cache and has no face buffer: 208 B).
 
 Measured DRAM traffic of the pair (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, both kernels) for the 96^3 block (884,736 cells,
-capture in profiles/rhs_two_pass_fp64_cached_weno5_curved_96cube.md); traffic
-grows with the cell count, so a launch on n^3 cells scales by n^3 / 96^3.
+capture in profiles/rhs_two_pass_fp64_cached_weno5_curved_96cube.md):
+345.7 MB + 771.0 MB = 1116.7 MB, 1262 B per cell; traffic grows with the
+cell count, so a launch on n^3 cells is 1262 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -43,7 +44,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
 BYTES_PER_CELL_RHS_CURVED = 552 + 384
-TRAFFIC_PER_CELL_MEASURED = None  # set from the two-pass capture below
+TRAFFIC_PER_CELL_MEASURED = (345.7e6 + 771.0e6) / 884736  # 1262 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.20
 FP32_PEAK_TFLOPS_MEASURED = 75.0
 HBM_FALLBACK_GBS = 6800.0
