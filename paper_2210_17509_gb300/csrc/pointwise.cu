@@ -239,7 +239,8 @@ __global__ void con2prim_cached_kernel(DevGrid g, DevParams p, const double* __r
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    myfail += (con2prim_at<false, false, true, POLY>(g, p, cons, metric, prim, c, nullptr, mcache) >= 2);
+    // FP64 recovery from the FP32 predictor's guess (Gamma-law; the polytrope has its own)
+    myfail += (con2prim_at<!POLY, false, true, POLY>(g, p, cons, metric, prim, c, nullptr, mcache) >= 2);
   }
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }

@@ -402,7 +402,12 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     }
   } else if (D > 0.0 && tau + D > 0.0) {
     double tol_first = p.nr_tol;
-    if (PREDICT && c2p_predict_fp32(in, p, z, W)) tol_first = 1e-6;
+    // mixed: after the FP32 predictor (about 1e-7 relative) one quadratic FP64
+    // step leaves about the square of its size, so steps up to 1e-6 end the
+    // solve (about 1e-12); FP64: the predictor only supplies the starting
+    // point, and the FP64 Newton still converges to nr_tol, so the root (and
+    // the floor decision of a cell whose pressure is round-off) is unchanged
+    if (PREDICT && c2p_predict_fp32(in, p, z, W) && p.precision == GRMHD_MIXED) tol_first = 1e-6;
     st = c2p_solve(in, p, z, W, tol_first, P0);
   }
   if constexpr (!RESULT64) {
