@@ -724,12 +724,14 @@ def main():
 
     # tile shape of the single block from the project's autotuner (per precision)
     from paper_2210_17509_gb300 import autotune
+    # (the FP64 RHS of the cached step runs in two passes on the 8x8x4 tile,
+    # whatever the tile parameter says; the mixed RHS takes the tuned shape)
     if args.tile >= 0:
         tiles = {G.FP64: args.tile, G.MIXED: args.tile}
     else:
-        tiles = {prec: autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=prec), blk.n,
-                                                 curved=True)
-                 for prec in (G.FP64, G.MIXED)}
+        tiles = {G.FP64: 0,
+                 G.MIXED: autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n,
+                                                    curved=True)}
 
     def setup(precision):
         p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision, tile=tiles[precision])
@@ -888,8 +890,10 @@ def main():
                   "dtype": "f32 reconstruct/HLLE/divergence + f64 con2prim/metric",
                   "speedup_vs_fp64": value_mx / value64, "failed_cells": nfailmx},
         "failed_cells": nfail64,
-        "tile_shapes": {"fp64": autotune.BLOCK_SHAPES[tiles[G.FP64]], "mixed": autotune.BLOCK_SHAPES[tiles[G.MIXED]]},
-        "gpu_launches": args.steps * 9,
+        "tile_shapes": {"fp64": str(autotune.BLOCK_SHAPES[0]) + " (two-pass RHS)",
+                        "mixed": autotune.BLOCK_SHAPES[tiles[G.MIXED]]},
+        # per SSP-RK3 stage: the two RHS passes, the recovery and the ghost fill
+        "gpu_launches": args.steps * 12,
         "roofline": roof,
         "clocks": clk,
         "e2e": e2e,

@@ -220,16 +220,21 @@ def test_rhs_periodic_telescoping(G):
         assert abs(r[q].sum()) < 1e-13 * np.abs(r[q]).sum()
 
 
-def test_rhs_full_size_schwarzschild_sampled(G):
-    """128^3 WENO5 on the Schwarzschild block, the benchmark's launch: sampled
-    cells (random, faces, edges, corners) against the oracle one by one."""
+@pytest.mark.parametrize("path", ["rhs", "rhs_cached"])
+def test_rhs_full_size_schwarzschild_sampled(G, path):
+    """128^3 WENO5 on the Schwarzschild block, the benchmark's launch (the
+    cached path is the two-pass RHS the benchmark times): sampled cells
+    (random, faces, edges, corners) against the oracle one by one."""
     blk, prim, met = I.smooth_schwarzschild(128, seed=1)
     g, og = grids(G, blk)
     gp, op = params(G, 1, bc=1)
     tp = cuda(prim)
     G.fill_ghosts(g, 1, tp)
     prim = host(tp)
-    r = host(G.rhs(g, gp, tp, cuda(met)))
+    if path == "rhs":
+        r = host(G.rhs(g, gp, tp, cuda(met)))
+    else:
+        r = host(G.rhs_cached(g, gp, tp, cuda(met)))
     rng = np.random.default_rng(5)
     n = 128
     pick = [rng.integers(0, n, size=3) for _ in range(400)]
