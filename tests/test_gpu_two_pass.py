@@ -4,7 +4,7 @@ kernel (GRMHD_SINGLE_PASS): the same face routine on the same stage, and the
 same per-cell operations in the same order, so the results are bit-identical.
 Blocks that end inside a tile (ragged) and exactly at a tile boundary (the
 boundary face layers of the last tiles) are both covered, with and without
-constrained transport.
+constrained transport, and blocks one cell thick along each axis.
 """
 import dataclasses
 
@@ -45,7 +45,7 @@ def state(n):
     return blk, m, prim
 
 
-@pytest.mark.parametrize("n", [(19, 13, 11), (16, 16, 8), (8, 24, 12)])
+@pytest.mark.parametrize("n", [(19, 13, 11), (16, 16, 8), (8, 24, 12), (9, 7, 1), (1, 10, 6), (8, 1, 5)])
 @pytest.mark.parametrize("recon", ["weno5", "minmod"])
 def test_rk_steps_bit_identical(G, n, recon):
     blk, m, prim = state(n)
