@@ -238,6 +238,8 @@ typedef struct {
   double* rhs;           /* 8 x ncell: interior RHS out, ghost entries untouched */
   int32_t tile;          /* GRMHD_TILE_* for this box */
   int32_t bc;            /* GRMHD_BC_* for this box's primitive ghosts */
+  double* faces;         /* nullable: 24 x ncell doubles of face buffer; when every box has one, the
+                            FP64 RHS runs in two passes (every face flux once), else in one */
 } grmhd_box;
 
 /* Prepared batch (filled by grmhd_batch_prepare; plain data, caller-owned). */
@@ -249,6 +251,8 @@ typedef struct {
   int64_t ntiles;        /* RHS work items */
   int64_t nc2p_items;    /* recovery work items (256 interior cells each) */
   int64_t nghost_items;  /* ghost-fill work items (256 points each) */
+  int32_t two_pass;      /* 1 if every box carries a face buffer */
+  int32_t reserved;
 } grmhd_batch;
 
 /* Device workspace (bytes) for a batch of nbox boxes; 0 if nbox is invalid. */
@@ -264,9 +268,11 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
 
 /* For every box: primitive recovery from cons (as grmhd_con2prim), ghost fill
  * (as grmhd_fill_ghosts with the box's bc), then the RHS (as grmhd_rhs with
- * the box's tile shape).  Three persistent launches on `stream` (plus one
- * memset of the work counters), no host synchronisation: the sequence can be
- * captured into a CUDA graph.  nfail as for grmhd_con2prim. */
+ * the box's tile shape; the same bits in two passes when batch->two_pass and
+ * params->precision is GRMHD_FP64).  Three persistent launches on `stream`
+ * (four with two passes; plus one memset of the work counters), no host
+ * synchronisation: the sequence can be captured into a CUDA graph.  nfail as
+ * for grmhd_con2prim.  Boxes' face buffers must not overlap. */
 int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream);
 
 /* ----------------------------------------------------------------------

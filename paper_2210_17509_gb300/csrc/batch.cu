@@ -11,6 +11,8 @@ cudaError_t launch_batch_rhs_fp64(BatchHead* head, const BoxDev* boxes, const De
                                   cudaStream_t s);
 cudaError_t launch_batch_rhs_mixed(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
                                    cudaStream_t s);
+cudaError_t launch_batch_rhs_two_pass(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                      cudaStream_t s);
 __global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
                                                                     DevParams p, int32_t* nfail) {
   int myfail = 0;
@@ -76,7 +78,7 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   if (ws_bytes < need) return GRMHD_ERR_SIZE;
   const int min_ng = params->recon == GRMHD_WENO5 ? 3 : 2;
   std::vector<BoxDev> host(nbox);
-  int ncurved = 0;
+  int ncurved = 0, nfaces = 0;
   for (int b = 0; b < nbox; ++b) {
     const grmhd_box& x = boxes[b];
     const grmhd_grid& gr = x.grid;
@@ -86,6 +88,8 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
     if (!x.cons || !x.prim || !x.rhs || !aligned8(x.cons) || !aligned8(x.prim) || !aligned8(x.rhs))
       return GRMHD_ERR_ARG;
     if (x.metric && !aligned8(x.metric)) return GRMHD_ERR_ARG;
+    if (x.faces && !aligned8(x.faces)) return GRMHD_ERR_ARG;
+    nfaces += x.faces != nullptr;
     if (x.tile < 0 || x.tile > 3) return GRMHD_ERR_ARG;
     if (x.bc != GRMHD_BC_PERIODIC && x.bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
     ncurved += x.metric != nullptr;
@@ -95,11 +99,13 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
     h.prim = x.prim;
     h.metric = x.metric;
     h.rhs = x.rhs;
+    h.faces = x.faces;
     h.tile = x.tile;
     h.bc = x.bc;
     for (int d = 0; d < 3; ++d) h.nt[d] = (gr.n[d] + kShape[x.tile][d] - 1) / kShape[x.tile][d];
   }
   if (ncurved != 0 && ncurved != nbox) return GRMHD_ERR_ARG;  // one kernel variant per batch
+  if (nfaces != 0 && nfaces != nbox) return GRMHD_ERR_ARG;    // two passes for all boxes or none
   // Largest boxes first (longest-processing-time order) so the dynamic work
   // counter finishes with small items.
   std::vector<int> order(nbox);
@@ -140,6 +146,8 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   batch->ntiles = tiles;
   batch->nc2p_items = c2p;
   batch->nghost_items = gh;
+  batch->two_pass = nfaces == nbox;
+  batch->reserved = 0;
   return GRMHD_OK;
 }
 
@@ -163,8 +171,11 @@ int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_
   if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
   batch_ghost_kernel<<<nsm * 8, kBatchItem, 0, s>>>(head, boxes);
   if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
-  const cudaError_t e = p.precision == GRMHD_MIXED ? launch_batch_rhs_mixed(head, boxes, p, batch->curved != 0, nsm, s)
-                                                   : launch_batch_rhs_fp64(head, boxes, p, batch->curved != 0, nsm, s);
+  const bool curved = batch->curved != 0;
+  cudaError_t e;
+  if (p.precision == GRMHD_MIXED) e = launch_batch_rhs_mixed(head, boxes, p, curved, nsm, s);
+  else if (batch->two_pass) e = launch_batch_rhs_two_pass(head, boxes, p, curved, nsm, s);
+  else e = launch_batch_rhs_fp64(head, boxes, p, curved, nsm, s);
   return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }
 

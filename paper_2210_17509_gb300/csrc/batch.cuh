@@ -16,6 +16,7 @@ struct BoxDev {
   double* prim;
   const double* metric;
   double* rhs;
+  double* faces;       // two-pass face buffer (24 ncell doubles) or NULL
   int tile, bc;
   int nt[3];           // tiles per axis for the box's tile shape
   long long tile_begin;  // first RHS work item of the box
@@ -95,6 +96,82 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
       default:
         rhs_tile<T, RECON, CURVED, 8, 8, 4, SrcF64>(g, p, src, ep, tx * 8, ty * 8, tz * 4, sF, sR);
         break;
+    }
+  }
+}
+
+// Two-pass FP64 RHS over the table.  Pass 1: every face flux of every box
+// once, into the box's face buffer, tiles in the box's own shape.
+template <int RECON, bool CURVED>
+__global__ void __launch_bounds__(kTileThreads) batch_faces_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                                   DevParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sR = reinterpret_cast<double*>(smem_raw);  // the stage only
+  const int nbox = head->nbox;
+  const long long total = head->ntiles;
+  for (;;) {
+    const long long it = next_item(&head->counter[0]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<0>(boxes, nbox, it)];
+    const long long t = it - b.tile_begin;
+    const int tx = (int)(t % b.nt[0]);
+    const int ty = (int)((t / b.nt[0]) % b.nt[1]);
+    const int tz = (int)(t / ((long long)b.nt[0] * b.nt[1]));
+    const DevGrid g = b.g;
+    SrcF64 src;
+    src.prim = b.prim;
+    src.metric = b.metric;
+    src.kij = nullptr;
+    switch (b.tile) {
+      case 1:
+        faces_tile<double, RECON, CURVED, 16, 4, 4, SrcF64, false>(g, p, src, tx * 16, ty * 4, tz * 4, b.faces, nullptr,
+                                                                   sR);
+        break;
+      case 2:
+        faces_tile<double, RECON, CURVED, 32, 4, 2, SrcF64, false>(g, p, src, tx * 32, ty * 4, tz * 2, b.faces, nullptr,
+                                                                   sR);
+        break;
+      case 3:
+        faces_tile<double, RECON, CURVED, 4, 8, 8, SrcF64, false>(g, p, src, tx * 4, ty * 8, tz * 8, b.faces, nullptr,
+                                                                  sR);
+        break;
+      default:
+        faces_tile<double, RECON, CURVED, 8, 8, 4, SrcF64, false>(g, p, src, tx * 8, ty * 8, tz * 4, b.faces, nullptr,
+                                                                  sR);
+        break;
+    }
+    __syncthreads();  // the stage is reused by the next item
+  }
+}
+
+// Pass 2: the per-cell pass of every box into its rhs, in the recovery's
+// items of kBatchItem interior cells.
+template <bool CURVED>
+__global__ void __launch_bounds__(kBatchItem) batch_div_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                               DevParams p) {
+  const int nbox = head->nbox;
+  const long long total = head->nc2p;
+  for (;;) {
+    const long long it = next_item(&head->counter[3]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<1>(boxes, nbox, it)];
+    const long long nint = (long long)b.g.n[0] * b.g.n[1] * b.g.n[2];
+    const long long t = (it - b.c2p_begin) * kBatchItem + threadIdx.x;
+    if (t < nint) {
+      StageEpilogue ep;
+      ep.fb = nullptr;
+      ep.faces = nullptr;
+      ep.rhs = b.rhs;
+      ep.u = nullptr;
+      ep.u0 = nullptr;
+      ep.acc_in = nullptr;
+      ep.acc_out = nullptr;
+      ep.c0 = ep.c1 = ep.cr = ep.ca = ep.wa = ep.wr = 0.0;
+      SrcF64 src;
+      src.prim = b.prim;
+      src.metric = b.metric;
+      src.kij = nullptr;
+      div_cell<double, CURVED, SrcF64>(b.g, p, src, b.faces, interior_cell(b.g, t), ep);
     }
   }
 }

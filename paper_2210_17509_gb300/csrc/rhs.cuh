@@ -869,8 +869,42 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_faces_ker
                                                              blockIdx.z * TS::Z, Ff, fb, sR);
 }
 
-// Pass 2: per interior cell, the flux differences, the sources and the stage
-// epilogue (the single-pass cell loop's operations, in its order).
+// Pass 2 at interior cell c (array index): the flux differences, the
+// sources and the stage epilogue (the single-pass cell loop's operations, in
+// its order).
+template <class T, bool CURVED, class S>
+__device__ __forceinline__ void div_cell(const DevGrid& g, const DevParams& p, const S& src,
+                                         const double* __restrict__ Ff, long long c, const StageEpilogue& ep) {
+  const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+  T r[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double* fx = Ff + (0 * 8 + q) * g.ncell + c;
+    const double* fy = Ff + (1 * 8 + q) * g.ncell + c;
+    const double* fz = Ff + (2 * 8 + q) * g.ncell + c;
+    T acc = -((T)__ldg(fx + 1) - (T)__ldg(fx)) * ix;
+    acc -= ((T)__ldg(fy + g.sy) - (T)__ldg(fy)) * iy;
+    acc -= ((T)__ldg(fz + g.sz) - (T)__ldg(fz)) * iz;
+    r[q] = acc;
+  }
+  if (CURVED) {
+    T sv[8];
+    source_terms<T>(g, p, src, c, sv);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] += sv[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long o = q * g.ncell + c;
+    const double rq = (double)r[q];
+    if (ep.rhs) ep.rhs[o] = rq;
+    const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
+    if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+    if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
+  }
+}
+
+// Pass 2 over the interior cells of one block.
 template <class T, bool CURVED, class S>
 __global__ void __launch_bounds__(256) rhs_div_kernel(DevGrid g, DevParams p, S src, const double* __restrict__ Ff,
                                                       StageEpilogue ep) {
@@ -879,33 +913,7 @@ __global__ void __launch_bounds__(256) rhs_div_kernel(DevGrid g, DevParams p, S 
        t += (long long)gridDim.x * blockDim.x) {
     const long long q0 = t / nx;
     const long long c = (q0 / ny + g.ng) * g.sz + (q0 % ny + g.ng) * g.sy + (t - q0 * nx + g.ng);
-    const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
-    T r[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double* fx = Ff + (0 * 8 + q) * g.ncell + c;
-      const double* fy = Ff + (1 * 8 + q) * g.ncell + c;
-      const double* fz = Ff + (2 * 8 + q) * g.ncell + c;
-      T acc = -((T)__ldg(fx + 1) - (T)__ldg(fx)) * ix;
-      acc -= ((T)__ldg(fy + g.sy) - (T)__ldg(fy)) * iy;
-      acc -= ((T)__ldg(fz + g.sz) - (T)__ldg(fz)) * iz;
-      r[q] = acc;
-    }
-    if (CURVED) {
-      T sv[8];
-      source_terms<T>(g, p, src, c, sv);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) r[q] += sv[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const long long o = q * g.ncell + c;
-      const double rq = (double)r[q];
-      if (ep.rhs) ep.rhs[o] = rq;
-      const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
-      if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
-      if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
-    }
+    div_cell<T, CURVED, S>(g, p, src, Ff, c, ep);
   }
 }
 
