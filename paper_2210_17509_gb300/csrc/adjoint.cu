@@ -6,8 +6,9 @@
 //     Fbar = (Lbar_c - Lbar_{c-1}) / dx back through HLLE, the 3+1 state
 //     formulas (Eqs. 6-9, 12, signal speeds) and WENO5 / minmod into the six
 //     stencil cells (FP64 atomics) and into Gamma;
-//   * source adjoint (curved metric): per cell, forward-mode dual numbers over
-//     the 8 primitives and Gamma through the Eq. 13 source, transposed;
+//   * source adjoint (curved metric): per cell, the hand-written reverse of
+//     the Eq. 13 source (the source is linear in T^{mu nu}; the reverse runs
+//     through b^mu, W, h* and P* to the primitives and Gamma);
 //   * con2prim adjoint: the recovery is the inverse of prim -> cons, so its
 //     adjoint solves (dU/dP)^T x = Pbar (implicit function theorem) with
 //     dU/dP from dual numbers; prim -> cons adjoint multiplies by (dU/dP)^T;
@@ -747,10 +748,14 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
 }
 
 // ------------------------------------------------------------- source adjoint
-// The Eq. 13 source of one cell (3+1 form as in source_terms) on dual numbers.
-__device__ __forceinline__ void source_dual(const DevGrid& g, const double* __restrict__ metric,
-                                            const double* __restrict__ kij, long long c, const D9 pr[8],
-                                            const D9& gfac, D9 src[8]) {
+// Reverse of the Eq. 13 source of one cell (3+1 form as in source_terms):
+// given sbar = d(loss)/d(source), add d(loss)/d(primitives) to pbar[8] and
+// d(loss)/d(gfac) to gfbar.  Every source component is linear in T^00, T^0i
+// and T^ij with coefficients of the metric alone, so their adjoints come
+// first; the reverse then runs through b^mu, W, h* and P* to the primitives.
+__device__ __forceinline__ void source_reverse(const DevGrid& g, const double* __restrict__ metric,
+                                               const double* __restrict__ kij, long long c, const double pr[8],
+                                               double gfac, const double sbar[8], double pbar[8], double& gfbar) {
   double a[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) a[q] = __ldg(metric + q * g.ncell + c);
@@ -764,102 +769,156 @@ __device__ __forceinline__ void source_dual(const DevGrid& g, const double* __re
   const double alpha = a[0];
   const double beta[3] = {a[1], a[2], a[3]};
   const double gm[6] = {gxx, gxy, gxz, gyy, gyz, gzz};
-  double dA[3][10];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const long long s = (e == 0) ? 1 : ((e == 1) ? g.sy : g.sz);
-    const double w = g.idx[e] * (1.0 / 12.0);
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      const double* mm = metric + q * g.ncell + c;
-      dA[e][q] = (8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w;
-    }
-  }
-  const D9 rho = pr[0], P = pr[4];
-  const D9 v[3] = {pr[1], pr[2], pr[3]};
-  const D9 B[3] = {pr[5], pr[6], pr[7]};
-  D9 vl[3], Bl[3];
-  for (int i = 0; i < 3; ++i) {
-    vl[i] = D9(0.0);
-    Bl[i] = D9(0.0);
-  }
   const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
-  for (int s = 0; s < 6; ++s) {
-    const int i = I6[s], j = J6[s];
-    vl[i] += D9(gm[s]) * v[j];
-    Bl[i] += D9(gm[s]) * B[j];
-    if (i != j) {
-      vl[j] += D9(gm[s]) * v[i];
-      Bl[j] += D9(gm[s]) * B[i];
-    }
-  }
-  const D9 v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
-  const D9 Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
-  const D9 B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-  const D9 omv2 = D9(1.0) - v2;
-  const D9 iW = xsqrt(omv2);
-  const D9 W = D9(1.0) / iW;
-  const D9 ab0 = W * Bv;
-  const D9 b2 = B2 * omv2 + Bv * Bv;
-  const D9 hs = rho + gfac * P + b2;
-  const D9 Ps = P + D9(0.5) * b2;
-  const double ia = 1.0 / alpha;
-  const double ia2 = ia * ia;
-  const D9 b0 = ab0 * D9(ia);
-  D9 vt[3], bu[3];
-  for (int i = 0; i < 3; ++i) {
-    vt[i] = v[i] - D9(beta[i] * ia);
-    bu[i] = B[i] * iW + ab0 * vt[i];
-  }
-  const D9 hW2 = hs * W * W;
-  const D9 T00 = (hW2 - Ps) * D9(ia2) - b0 * b0;
-  D9 T0[3];
-  for (int i = 0; i < 3; ++i) T0[i] = hW2 * vt[i] * D9(ia) + Ps * D9(beta[i] * ia2) - b0 * bu[i];
-  D9 Tij[6];
-  for (int s = 0; s < 6; ++s) {
-    const int i = I6[s], j = J6[s];
-    Tij[s] = hW2 * vt[i] * vt[j] + Ps * D9(gu[s] - beta[i] * beta[j] * ia2) - bu[i] * bu[j];
-  }
+  const double wsym[6] = {1, 2, 2, 1, 2, 1};
+  const double asg = alpha * sg;
+  const double ia = 1.0 / alpha, ia2 = ia * ia;
   double betal[3];
   lower(gm, beta, betal);
-  D9 T0l[3];
-  for (int i = 0; i < 3; ++i) {
-    T0l[i] = T00 * D9(betal[i]);
-    for (int j = 0; j < 3; ++j) T0l[i] += D9(gm[sym_index(i, j)]) * T0[j];
-  }
-  const double asg = alpha * sg;
-  const double wsym[6] = {1, 2, 2, 1, 2, 1};
-  src[0] = D9(0.0);
-  for (int j = 0; j < 3; ++j) {
-    double bbdg = 0.0;
-    D9 t0dg(0.0), tdg(0.0);
-    for (int s = 0; s < 6; ++s) {
-      const int i = I6[s], k = J6[s];
-      const double dg = dA[j][4 + s] * wsym[s];
-      bbdg += beta[i] * beta[k] * dg;
-      t0dg += D9(0.5 * dg) * (T0[i] * D9(beta[k]) + T0[k] * D9(beta[i]));
-      tdg += Tij[s] * D9(dg);
-    }
-    const D9 t0db = T0l[0] * D9(dA[j][1]) + T0l[1] * D9(dA[j][2]) + T0l[2] * D9(dA[j][3]);
-    src[1 + j] = D9(asg) * (T00 * D9(0.5 * bbdg - alpha * dA[j][0]) + t0dg + t0db + D9(0.5) * tdg);
-  }
+  // adjoints of T^00, T^0i, T^ij (packed like gamma) from the linear source map
+  double T00b = 0.0, T0b[3] = {0.0, 0.0, 0.0}, Tijb[6] = {0, 0, 0, 0, 0, 0};
   {
-    D9 t = -(T0[0] * D9(dA[0][0]) + T0[1] * D9(dA[1][0]) + T0[2] * D9(dA[2][0]));
-    t -= T00 * D9(beta[0] * dA[0][0] + beta[1] * dA[1][0] + beta[2] * dA[2][0]);
-    if (kij) {
-      double K[6];
-      for (int s = 0; s < 6; ++s) K[s] = __ldg(kij + s * g.ncell + c);
-      double bK[3];
-      lower(K, beta, bK);
-      const double bbK = beta[0] * bK[0] + beta[1] * bK[1] + beta[2] * bK[2];
-      D9 tK = T0[0] * D9(bK[0]) + T0[1] * D9(bK[1]) + T0[2] * D9(bK[2]);
-      D9 TK(0.0);
-      for (int s = 0; s < 6; ++s) TK += Tij[s] * D9(K[s] * wsym[s]);
-      t += T00 * D9(bbK) + D9(2.0) * tK + TK;
+    double dA0[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const long long st = (j == 0) ? 1 : ((j == 1) ? g.sy : g.sz);
+      const double w = g.idx[j] * (1.0 / 12.0);
+      double d[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) {
+        const double* mm = metric + q * g.ncell + c;
+        d[q] = (8.0 * (__ldg(mm + st) - __ldg(mm - st)) - (__ldg(mm + 2 * st) - __ldg(mm - 2 * st))) * w;
+      }
+      dA0[j] = d[0];
+      const double wj = sbar[1 + j] * asg;  // momentum j
+      if (wj != 0.0) {
+        double bbdg = 0.0;
+#pragma unroll
+        for (int s2 = 0; s2 < 6; ++s2) {
+          const int i = I6[s2], k = J6[s2];
+          const double dg = d[4 + s2] * wsym[s2];
+          bbdg += beta[i] * beta[k] * dg;
+          // 0.5 dg (T0_i beta_k + T0_k beta_i) and 0.5 Tij dg
+          T0b[i] += wj * 0.5 * dg * beta[k];
+          T0b[k] += wj * 0.5 * dg * beta[i];
+          Tijb[s2] += wj * 0.5 * dg;
+        }
+        T00b += wj * (0.5 * bbdg - alpha * d[0]);
+        // T0l_i = T00 betal_i + gamma_im T0_m, weighted by d[1 + i]
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          T00b += wj * d[1 + i] * betal[i];
+#pragma unroll
+          for (int m2 = 0; m2 < 3; ++m2) T0b[m2] += wj * d[1 + i] * gm[sym_index(i, m2)];
+        }
+      }
     }
-    src[4] = D9(asg) * t;
+    const double we = sbar[4] * asg;  // energy
+    if (we != 0.0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) T0b[i] -= we * dA0[i];
+      T00b -= we * (beta[0] * dA0[0] + beta[1] * dA0[1] + beta[2] * dA0[2]);
+      if (kij) {
+        double K[6];
+#pragma unroll
+        for (int s2 = 0; s2 < 6; ++s2) K[s2] = __ldg(kij + s2 * g.ncell + c);
+        double bK[3];
+        lower(K, beta, bK);
+        T00b += we * (beta[0] * bK[0] + beta[1] * bK[1] + beta[2] * bK[2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) T0b[i] += we * 2.0 * bK[i];
+#pragma unroll
+        for (int s2 = 0; s2 < 6; ++s2) Tijb[s2] += we * K[s2] * wsym[s2];
+      }
+    }
   }
-  src[5] = src[6] = src[7] = D9(0.0);
+  // forward values of the fluid part
+  const double rho = pr[0], P = pr[4];
+  const double v[3] = {pr[1], pr[2], pr[3]};
+  const double B[3] = {pr[5], pr[6], pr[7]};
+  double vl[3], Bl[3];
+  lower(gm, v, vl);
+  lower(gm, B, Bl);
+  const double v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const double omv2 = 1.0 - v2;
+  const double iW = sqrt(omv2);
+  const double W = 1.0 / iW;
+  const double ab0 = W * Bv;
+  const double b2 = B2 * omv2 + Bv * Bv;
+  const double hs = rho + gfac * P + b2;
+  const double Ps = P + 0.5 * b2;
+  const double b0 = ab0 * ia;
+  double vt[3], bu[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vt[i] = v[i] - beta[i] * ia;
+    bu[i] = B[i] * iW + ab0 * vt[i];
+  }
+  const double hW2 = hs * W * W;
+  // reverse through T^00, T^0i, T^ij
+  double hW2b = T00b * ia2, Psb = -T00b * ia2, b0b = -2.0 * b0 * T00b;
+  double vtb[3] = {0.0, 0.0, 0.0}, bub[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    hW2b += T0b[i] * vt[i] * ia;
+    vtb[i] += T0b[i] * hW2 * ia;
+    Psb += T0b[i] * beta[i] * ia2;
+    b0b -= T0b[i] * bu[i];
+    bub[i] -= T0b[i] * b0;
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < 6; ++s2) {
+    const int i = I6[s2], j = J6[s2];
+    const double t = Tijb[s2];
+    hW2b += t * vt[i] * vt[j];
+    vtb[i] += t * hW2 * vt[j];
+    vtb[j] += t * hW2 * vt[i];
+    Psb += t * (gu[s2] - beta[i] * beta[j] * ia2);
+    bub[i] -= t * bu[j];
+    bub[j] -= t * bu[i];
+  }
+  // hW2 = hs W^2
+  double hsb = hW2b * W * W;
+  double Wb = hW2b * 2.0 * hs * W;
+  // bu_i = B_i iW + ab0 vt_i ;  b0 = ab0 ia
+  double Bb[3], iWb = 0.0, ab0b = b0b * ia;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Bb[i] = bub[i] * iW;
+    iWb += bub[i] * B[i];
+    ab0b += bub[i] * vt[i];
+    vtb[i] += bub[i] * ab0;
+  }
+  // hs = rho + gfac P + b2 ;  Ps = P + b2 / 2
+  const double rhob = hsb;
+  double Pb = hsb * gfac + Psb;
+  gfbar += hsb * P;
+  const double b2b = hsb + 0.5 * Psb;
+  // ab0 = W Bv ;  b2 = B2 omv2 + Bv^2
+  Wb += ab0b * Bv;
+  const double Bvb = ab0b * W + 2.0 * Bv * b2b;
+  const double B2b = b2b * omv2;
+  double omv2b = b2b * B2;
+  // W = 1 / iW ;  iW = sqrt(omv2) ;  omv2 = 1 - v2
+  iWb -= Wb * W * W;
+  omv2b += iWb * 0.5 * W;
+  const double v2b = -omv2b;
+  // vt_i = v_i - beta_i / alpha ;  v2 = v.Gv ;  Bv = B.Gv ;  B2 = B.GB
+  double vb[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vb[i] = vtb[i] + 2.0 * v2b * vl[i] + Bvb * Bl[i];
+    Bb[i] += Bvb * vl[i] + 2.0 * B2b * Bl[i];
+  }
+  pbar[0] += rhob;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    pbar[1 + i] += vb[i];
+    pbar[5 + i] += Bb[i];
+  }
+  pbar[4] += Pb;
 }
 
 __global__ void source_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
@@ -868,31 +927,23 @@ __global__ void source_adjoint_kernel(DevGrid g, DevParams p, const double* __re
                                       double* __restrict__ gamma_bar) {
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   double gb = 0.0;
+  // d gfac / d Gamma for gfac = Gamma / (Gamma - 1)
+  const double dgfac = -1.0 / ((p.gamma - 1.0) * (p.gamma - 1.0));
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
        t += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, t);
-    D9 pr[8];
+    double pr[8], sbar[8], pb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      pr[q] = D9(__ldg(prim + q * g.ncell + c));
-      pr[q].d[q] = 1.0;
+      pr[q] = __ldg(prim + q * g.ncell + c);
+      sbar[q] = scale * rhs_bar[q * g.ncell + c];
     }
-    D9 gf(p.gfac);
-    gf.d[8] = -1.0 / ((p.gamma - 1.0) * (p.gamma - 1.0));
-    D9 src[8];
-    source_dual(g, metric, kij, c, pr, gf, src);
-    double lb[8];
+    double gfb = 0.0;
+    source_reverse(g, metric, kij, c, pr, p.gfac, sbar, pb, gfb);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) lb[q] = scale * rhs_bar[q * g.ncell + c];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      double s = 0.0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) s += src[i].d[j] * lb[i];
-      if (s != 0.0) atomicAdd(prim_bar + j * g.ncell + c, s);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) gb += src[i].d[8] * lb[i];
+    for (int q = 0; q < 8; ++q)
+      if (pb[q] != 0.0) atomicAdd(prim_bar + q * g.ncell + c, pb[q]);
+    gb += gfb * dgfac;
   }
   block_add_gamma(gb, gamma_bar);
 }
