@@ -848,7 +848,6 @@ __device__ __forceinline__ void source_reverse(const DevGrid& g, const double* _
   const double ab0 = W * Bv;
   const double b2 = B2 * omv2 + Bv * Bv;
   const double hs = rho + gfac * P + b2;
-  const double Ps = P + 0.5 * b2;
   const double b0 = ab0 * ia;
   double vt[3], bu[3];
 #pragma unroll
