@@ -158,15 +158,10 @@ static __device__ bool c2p_newman_hamlin(const C2PIn& in, const DevParams& p, do
 }
 
 // Returns 0 (Newton converged), 1 (bisection), 2 (failed); z, W on exit.
-// tol_first applies to the first Newton step only: after an FP32 predictor
-// that converged to 1e-6, one FP64 step leaves an error of order 1e-12 times
-// the problem's curvature scale (quadratic convergence), so a first step
-// below tol_first ends the solve; every later step must be below nr_tol.
-// P0 (> 0) starts the Newman-Hamlin iteration, which follows a failed
-// Newton iteration or, with GRMHD_NEWMAN_HAMLIN, replaces it; status 0
-// covers both.
-static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W, double tol_first,
-                                double P0) {
+// The Newton steps must fall below nr_tol (relative).  P0 (> 0) starts the
+// Newman-Hamlin iteration, which follows a failed Newton iteration or, with
+// GRMHD_NEWMAN_HAMLIN, replaces it; status 0 covers both.
+static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, double& W, double P0) {
   const double gm1g = p.gm1g;
   const double D = in.D, B2 = in.B2, BS2 = in.BS2, S2 = in.S2, tau = in.tau;
   bool ok = false;
@@ -187,8 +182,7 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
       const double dz = (f1 * J22 - f2 * J12) * idet;
       const double dW = (J11 * f2 - J21 * f1) * idet;
       if (!isfinite(dz) || !isfinite(dW)) break;
-      const double tol = it == 0 ? tol_first : p.nr_tol;
-      const bool conv = fabs(dz) <= tol * z && fabs(dW) <= tol * W;
+      const bool conv = fabs(dz) <= p.nr_tol * z && fabs(dW) <= p.nr_tol * W;
       double zn = z - dz, Wn = W - dW;
       if (!(zn > 0.0)) zn = 0.5 * z;
       if (!(Wn >= 1.0)) Wn = 0.5 * (W + 1.0);
@@ -202,10 +196,10 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
   return c2p_bisect(in, p, z, W);
 }
 
-// FP32 Newton predictor for the mixed path: iterates the same 2D system in
-// single precision to a relative step of 1e-6 and returns the improved (z, W)
-// (unchanged if it fails); the FP64 Newton of c2p_solve then finishes to
-// nr_tol, normally in one or two steps.
+// FP32 Newton starting point of the FP64 recovery: iterates the same 2D
+// system in single precision to a relative step of 1e-6 and returns the
+// improved (z, W) (unchanged if it fails); the FP64 Newton of c2p_solve then
+// finishes to nr_tol, normally in one or two steps.
 __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
   const float gm1g = (float)p.gm1g;
   const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
@@ -240,6 +234,106 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
     return converged;
   }
   return false;
+}
+
+// Mixed-path recovery of the Gamma-law system (Sec. 2.3), from the FP32
+// guess (zf, Wf).
+//
+// (1) FP32 Newton predictor on the same 2D system, to a relative step of
+// 1e-6.  The loop is warp-uniform: a vote keeps every lane of the warp
+// iterating until all have converged (a converged lane holds its values), so
+// the FP64 code that follows runs once per warp with all lanes rather than
+// once per exit iteration.  1/z and 1/W come from one fast reciprocal; the
+// predictor's accuracy does not depend on them, only its convergence rate.
+//
+// (2) One step of mixed-precision iterative refinement (Wilkinson): the
+// residual of the 2D system at the predicted (z, W) in FP64 and the
+// correction from the FP32 Jacobian at that point.  Both equations
+// multiplied by W^2 z^2 need no division in FP64; the factor is divided out
+// in FP32, where only the correction's relative accuracy matters.  The
+// Jacobian's v^2 = (W^2 - 1)/W^2 comes from the FP64 W^2 - 1 (exact: W is an
+// FP32 value), so slow flows lose no digits to the cancellation in 1 - 1/W^2
+// and the Jacobian carries only FP32 rounding.  The error after the step is
+// the predictor's times that rounding plus its square, i.e. of order 1e-13
+// relative, as after a full FP64 Newton step.  A correction above 1e-6
+// (relative), a failed predictor or an unphysical root hands the solve to
+// the FP64 Newton of c2p_solve, from the best point.  Pg: the guess's
+// pressure, which starts the Newman-Hamlin fallback.
+__device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams& p, float zf, float Wf, float Pg,
+                                               double& z, double& W) {
+  const float gm1g = (float)p.gm1g;
+  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
+  bool active = zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf);
+  bool converged = false;
+  const unsigned mask = __activemask();
+  for (int it = 0; it < 30 && __any_sync(mask, active); ++it) {
+    if (active) {
+      const float r = __fdividef(1.0f, zf * Wf);
+      const float iz = Wf * r, iW = zf * r;
+      const float iW2 = iW * iW, iW3 = iW2 * iW, iz2 = iz * iz, iz3 = iz2 * iz;
+      const float zb = zf + B2;
+      const float f1 = zb * zb * (1.0f - iW2) - S2 - BS2 * (2.0f * zf + B2) * iz2;
+      const float f2 = tau + D - zf - B2 + 0.5f * B2 * iW2 + 0.5f * BS2 * iz2 + gm1g * (zf * iW2 - D * iW);
+      const float J11 = 2.0f * zb * (1.0f - iW2) + 2.0f * BS2 * zb * iz3;
+      const float J12 = 2.0f * zb * zb * iW3;
+      const float J21 = -1.0f - BS2 * iz3 + gm1g * iW2;
+      const float J22 = -B2 * iW3 + gm1g * (D * iW2 - 2.0f * zf * iW3);
+      const float idet = __fdividef(1.0f, J11 * J22 - J12 * J21);
+      const float dz = (f1 * J22 - f2 * J12) * idet;
+      const float dW = (J11 * f2 - J21 * f1) * idet;
+      if (!isfinite(dz) || !isfinite(dW)) {
+        active = false;
+      } else {
+        float zn = zf - dz, Wn = Wf - dW;
+        if (!(zn > 0.0f)) zn = 0.5f * zf;
+        if (!(Wn >= 1.0f)) Wn = 0.5f * (Wf + 1.0f);
+        const bool conv = fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf;
+        zf = zn;
+        Wf = Wn;
+        if (conv) {
+          active = false;
+          converged = true;
+        }
+      }
+    }
+  }
+  z = (double)zf;
+  W = (double)Wf;
+  if (converged) {
+    // z and W are FP32 values: z^2, W^2 and W^2 - 1 are exact in FP64
+    const double W2 = W * W, z2 = z * z, W2z2 = W2 * z2, u2 = W2 - 1.0;
+    const double zb = z + in.B2;
+    const double F1 = zb * zb * u2 * z2 - in.S2 * W2z2 - in.BS2 * fma(2.0, z, in.B2) * W2;
+    const double F2 = (in.tau + in.D - z - in.B2) * W2z2 + 0.5 * in.B2 * z2 + 0.5 * in.BS2 * W2 +
+                      p.gm1g * z2 * (z - in.D * W);
+    const float r = __fdividef(1.0f, zf * Wf);
+    const float iz = Wf * r, iW = zf * r;
+    const float iW2 = iW * iW, iW3 = iW2 * iW, iz3 = iz * iz * iz;
+    const float v2 = (float)u2 * iW2;
+    const float zb32 = zf + B2;
+    const float J11 = 2.0f * zb32 * v2 + 2.0f * BS2 * zb32 * iz3;
+    const float J12 = 2.0f * zb32 * zb32 * iW3;
+    const float J21 = -1.0f - BS2 * iz3 + gm1g * iW2;
+    const float J22 = -B2 * iW3 + gm1g * (D * iW2 - 2.0f * zf * iW3);
+    const float idet = 1.0f / (J11 * J22 - J12 * J21);
+    const float s = iz * iz * iW2;  // 1 / (W^2 z^2)
+    const float f1 = (float)F1 * s, f2 = (float)F2 * s;
+    const float dz = (f1 * J22 - f2 * J12) * idet;
+    const float dW = (J11 * f2 - J21 * f1) * idet;
+    if (fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf) {
+      const double zn = z - (double)dz, Wn = W - (double)dW;
+      if (zn > 0.0 && c2p_root_physical(in, p, zn, Wn)) {
+        z = zn;
+        W = Wn;
+        return 0;
+      }
+    }
+  }
+  // from the predictor's last point (an unusable guess fails the FP64
+  // Newton's own checks and goes on to Newman-Hamlin and bisection)
+  double P0 = (double)Pg;
+  if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (in.tau + in.D);
+  return c2p_solve(in, p, z, W, P0);
 }
 
 // Polytropic EOS (Sec. 2.3, P = K rho^gamma): with rho = D / W,
@@ -366,7 +460,8 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   in.BS2 = BS * BS;
   // initial guess from the incoming primitives
   double* pc = prim + c;
-  double W, z, P0;
+  double W = 1.0, z = 0.0, P0 = 0.0;
+  float Wg = 1.0f, zg = 0.0f, Pgf = 0.0f;  // the FP32 guess (F32IO)
   if (F32IO) {
     const float* pf = prim32 + c;
     const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
@@ -377,10 +472,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     lower(gf, v, vl);
     const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
     const float rg = pf[0], Pg = pf[4 * g.ncell];
-    const float Wf = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
-    W = (double)Wf;
-    z = (rg > 0.0f && Pg > 0.0f) ? (double)((rg + (float)p.gfac * Pg) * Wf * Wf) : (tau + D + in.B2);
-    P0 = (double)Pg;
+    Wg = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
+    zg = (rg > 0.0f && Pg > 0.0f) ? (rg + (float)p.gfac * Pg) * Wg * Wg : (float)(tau + D + in.B2);
+    Pgf = Pg;
   } else {
     const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
     double vl[3];
@@ -391,24 +485,37 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
     P0 = Pg;
   }
-  if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
   int st = 2;
   constexpr bool poly = POLY;
   if constexpr (POLY) {
     if (D > 0.0) {
+      if (F32IO) W = (double)Wg;
       double tol_first = p.nr_tol;
       if (PREDICT && c2p_polytrope_predict(in, p, W)) tol_first = 1e-6;
       st = c2p_polytrope(in, p, z, W, tol_first);
     }
   } else if (D > 0.0 && tau + D > 0.0) {
-    double tol_first = p.nr_tol;
-    // mixed: after the FP32 predictor (about 1e-7 relative) one quadratic FP64
-    // step leaves about the square of its size, so steps up to 1e-6 end the
-    // solve (about 1e-12); FP64: the predictor only supplies the starting
-    // point, and the FP64 Newton still converges to nr_tol, so the root (and
-    // the floor decision of a cell whose pressure is round-off) is unchanged
-    if (PREDICT && c2p_predict_fp32(in, p, z, W) && p.precision == GRMHD_MIXED) tol_first = 1e-6;
-    st = c2p_solve(in, p, z, W, tol_first, P0);
+    // mixed: the FP32 predictor and one refinement step (c2p_solve_mixed);
+    // FP64: the predictor only supplies the starting point, and the FP64
+    // Newton still converges to nr_tol, so the root (and the floor decision
+    // of a cell whose pressure is round-off) is unchanged
+    if (PREDICT && p.precision == GRMHD_MIXED && !(p.flags & GRMHD_NEWMAN_HAMLIN)) {
+      if (!F32IO) {
+        zg = (float)z;
+        Wg = (float)W;
+        Pgf = (float)P0;
+      }
+      st = c2p_solve_mixed(in, p, zg, Wg, Pgf, z, W);
+    } else {
+      if (F32IO) {
+        z = (double)zg;
+        W = (double)Wg;
+        P0 = (double)Pgf;
+      }
+      if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
+      if (PREDICT) c2p_predict_fp32(in, p, z, W);
+      st = c2p_solve(in, p, z, W, P0);
+    }
   }
   if constexpr (!RESULT64) {
     // FP32 primitives from the FP64 root: 1/W, 1/z, 1/(z + B^2) from one division

@@ -311,6 +311,18 @@ def test_rk3_mixed_conserved_error(G):
     assert np.all(err < MIXED_TOL), err
 
 
+@pytest.mark.parametrize("seed,rho_range", [(1, (0.1, 1.0)), (4, (1e-3, 1.0))])
+def test_mixed_recovery_is_an_fp64_solve(G, seed, rho_range):
+    """Mixed path with dt = 1e-9 dx: the FP32 right-hand side changes U by
+    round-off only, so the step's FP64 primitives are the recovery's root
+    from the FP32 guess.  The FP32 predictor alone would leave about 1e-7;
+    its FP64-residual refinement must reach the FP64 oracle's root."""
+    blk, prim, met = block_curved(16, seed=seed, rho_range=rho_range)
+    c, p, co, po = _evolve_both(G, blk, prim, met, 1, 1, 3, 1, 1e-9, precision=1)
+    err = normwise(interior(p, 3), interior(po, 3))
+    assert np.all(err < 1e-10), err
+
+
 @pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
 def test_rk3_full_size_schwarzschild_step(G, precision, tol):
     '''The benchmark's workload and launch (128^3 Schwarzschild, WENO5, SSP-RK3,
