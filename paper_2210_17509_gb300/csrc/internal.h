@@ -92,7 +92,8 @@ cudaError_t launch_rhs_fp64_cached(const DevGrid& g, const DevParams& p, const d
                                    const double* kij, const StageEpilogue& ep, cudaStream_t s);
 cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const float* prim32, const float* geom,
                                     const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s);
-constexpr int kGeomCacheComps = 53;
+constexpr int kGeomCacheComps = 63;  // geometry cache components (layout in rhs.cuh)
+constexpr int kGeomCacheHalf = 53;   // first of the ten half-metric components
 constexpr int kMetricCacheComps = 7;
 
 // ---------------------------------------------------------- host helpers

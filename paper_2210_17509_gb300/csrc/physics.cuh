@@ -39,24 +39,28 @@ __device__ __forceinline__ T minmod(T a, T b) {
 // the face i+1/2 from the cell values i-2 .. i+2 (FP32, per face; the FP64
 // paths use weno5_parts and weno5_cell_parts).  The weights use the textbook
 // reciprocals so that the squared products cannot overflow in single
-// precision.
+// precision.  Every operation is explicit (fused multiply-adds and
+// round-to-nearest products and sums), so that the kernels that inline this
+// function, which read their stencils from different memories, compute the
+// same bits.
 template <class T>
 __device__ __forceinline__ T weno5(T um2, T um1, T u0, T up1, T up2, T eps);
 
 template <>
 __device__ __forceinline__ float weno5<float>(float um2, float um1, float u0, float up1, float up2, float eps) {
   const float c6 = 1.0f / 6.0f, c1312 = 13.0f / 12.0f;
-  const float q0 = (2.0f * um2 - 7.0f * um1 + 11.0f * u0) * c6;
-  const float q1 = (-um1 + 5.0f * u0 + 2.0f * up1) * c6;
-  const float q2 = (2.0f * u0 + 5.0f * up1 - up2) * c6;
-  const float t0 = um2 - 2.0f * um1 + u0, s0 = um2 - 4.0f * um1 + 3.0f * u0;
-  const float t1 = um1 - 2.0f * u0 + up1, s1 = um1 - up1;
-  const float t2 = u0 - 2.0f * up1 + up2, s2 = 3.0f * u0 - 4.0f * up1 + up2;
-  const float e0 = eps + (c1312 * t0 * t0 + 0.25f * s0 * s0);
-  const float e1 = eps + (c1312 * t1 * t1 + 0.25f * s1 * s1);
-  const float e2 = eps + (c1312 * t2 * t2 + 0.25f * s2 * s2);
-  const float a0 = __fdividef(0.1f, e0 * e0), a1 = __fdividef(0.6f, e1 * e1), a2 = __fdividef(0.3f, e2 * e2);
-  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+  const float q0 = __fmul_rn(fmaf(2.0f, um2, fmaf(-7.0f, um1, __fmul_rn(11.0f, u0))), c6);
+  const float q1 = __fmul_rn(fmaf(2.0f, up1, fmaf(5.0f, u0, -um1)), c6);
+  const float q2 = __fmul_rn(fmaf(5.0f, up1, fmaf(2.0f, u0, -up2)), c6);
+  const float t0 = fmaf(-2.0f, um1, __fadd_rn(um2, u0)), s0 = fmaf(3.0f, u0, fmaf(-4.0f, um1, um2));
+  const float t1 = fmaf(-2.0f, u0, __fadd_rn(um1, up1)), s1 = __fsub_rn(um1, up1);
+  const float t2 = fmaf(-2.0f, up1, __fadd_rn(u0, up2)), s2 = fmaf(3.0f, u0, fmaf(-4.0f, up1, up2));
+  const float e0 = __fadd_rn(eps, fmaf(__fmul_rn(c1312, t0), t0, __fmul_rn(__fmul_rn(0.25f, s0), s0)));
+  const float e1 = __fadd_rn(eps, fmaf(__fmul_rn(c1312, t1), t1, __fmul_rn(__fmul_rn(0.25f, s1), s1)));
+  const float e2 = __fadd_rn(eps, fmaf(__fmul_rn(c1312, t2), t2, __fmul_rn(__fmul_rn(0.25f, s2), s2)));
+  const float a0 = __fdividef(0.1f, __fmul_rn(e0, e0)), a1 = __fdividef(0.6f, __fmul_rn(e1, e1)),
+              a2 = __fdividef(0.3f, __fmul_rn(e2, e2));
+  return __fdividef(fmaf(a0, q0, fmaf(a1, q1, __fmul_rn(a2, q2))), __fadd_rn(__fadd_rn(a0, a1), a2));
 }
 
 // Both WENO5 states of the face between cells c-1 and c from the six values

@@ -85,7 +85,7 @@ __global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* 
     b[i] = (float)a[i];
 }
 
-// Geometry cache of a static metric (layout in rhs.cuh, kGeomComps floats per
+// Geometry cache of a static metric (layout in rhs.cuh, kGeomCacheComps values per
 // point): every FP64 quantity the mixed RHS needs, computed once in FP64.
 // mcache (FP64, 7 components per point): 1/sqrt(gamma) and gamma^ij for the
 // primitive recovery.
@@ -103,6 +103,7 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
     for (int q = 0; q < 10; ++q) {
       a[q] = __ldg(metric + q * n + c);
       geom[q * n + c] = (GT)a[q];
+      geom[(kGeomCacheHalf + q) * n + c] = (GT)(0.5 * a[q]);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -47,7 +47,10 @@ typedef SrcCacheT<double, double> SrcCache64;  // FP64: FP64 primitives + FP64 g
 //   13..15  gamma^{dd} on the lower x / y / z face
 //   16      sqrt(gamma) at the point;  17..22 gamma^{ij} at the point
 //   23..52  4th-order derivatives d_e of the 10 metric entries (index 23 + 10 e + q)
-constexpr int kGeomComps = 53;
+//   53..62  half the metric values, 0.5 (alpha, beta^i, gamma_ij): a face's
+//           metric is then the sum of its two cells' entries (scaling by 0.5
+//           is exact, so the sum has the bits of 0.5 (a + b))
+static_assert(kGeomCacheComps == 63 && kGeomCacheHalf == 53, "geometry cache layout");
 
 template <class T>
 __device__ __forceinline__ T ld_prim(const SrcF64& s, long long i) { return (T)__ldg(s.prim + i); }
@@ -190,7 +193,10 @@ __device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, lon
   const GT* gm = s.geom;
   T a[10];
 #pragma unroll
-  for (int q = 0; q < 10; ++q) a[q] = T(0.5) * ((T)__ldg(gm + q * ncell + c - stride) + (T)__ldg(gm + q * ncell + c));
+  for (int q = 0; q < 10; ++q) {
+    const GT* h = gm + (kGeomCacheHalf + q) * ncell + c;
+    a[q] = (T)__ldg(h - stride) + (T)__ldg(h);
+  }
   m.alpha = a[0];
 #pragma unroll
   for (int i = 0; i < 3; ++i) m.beta[i] = a[1 + i];

@@ -1,7 +1,9 @@
 // Arithmetic-peak probe for the roofline denominators of the FP64 and FP32
 // pipes: independent FMA chains (8 per thread, 8 CTAs of 256 threads per SM),
-// plus FP64 divide / square-root and FP32 divide throughput.  Every thread
-// writes one value to its own slot of an output buffer sized grid x block.
+// plus FP64 divide / square-root and FP32 divide throughput, and the rate of
+// two instruction kinds that share the FP64 pipe with the arithmetic: FP64
+// <-> FP32 conversions and FP64 compares.  Every thread writes one value to
+// its own slot of an output buffer sized grid x block.
 #include <cstdio>
 #include <cuda_runtime.h>
 template<class T, int CH>
@@ -29,6 +31,46 @@ __global__ void sqrt_loop(T* out, int iters, T a) {
   T x = (T)(threadIdx.x + 1), y = (T)(threadIdx.x + 2), z = (T)3, w = (T)5;
   for (int i = 0; i < iters; ++i) { x = sqrt(x) + a; y = sqrt(y) + a; z = sqrt(z) + a; w = sqrt(w) + a; }
   out[blockIdx.x * blockDim.x + threadIdx.x] = x + y + z + w;
+}
+// FP64 -> FP32 and FP32 -> FP64 conversions, 8 chains per thread; each chain
+// returns to its type through integer operations only.
+__global__ void cvt_loop(double* out, int iters, double a) {
+  double x[8];
+  float f[8];
+  #pragma unroll
+  for (int c = 0; c < 8; ++c) { x[c] = a + threadIdx.x * 1e-3 + c; f[c] = (float)c + 0.5f; }
+  for (int i = 0; i < iters; ++i) {
+    #pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float g = (float)x[c];
+      x[c] = __hiloint2double(__float_as_int(g) ^ 0x40000000, i);
+      const double y = (double)f[c];
+      f[c] = __int_as_float((__double2hiint(y) ^ i) & 0x3fffffff);
+    }
+  }
+  double s = 0;
+  #pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c] + f[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+// FP64 compares feeding integer counters, 8 chains per thread; the compared
+// values change through integer operations only.
+__global__ void cmp_loop(double* out, int iters, double b) {
+  double x[8];
+  int n[8];
+  #pragma unroll
+  for (int c = 0; c < 8; ++c) { x[c] = threadIdx.x * 1e-3 + c; n[c] = 0; }
+  for (int i = 0; i < iters; ++i) {
+    #pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      n[c] += x[c] > b ? 1 : 0;
+      x[c] = __hiloint2double(__double2hiint(x[c]) ^ (n[c] & 1), i);
+    }
+  }
+  int s = 0;
+  #pragma unroll
+  for (int c = 0; c < 8; ++c) s += n[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 int main() {
   int dev = 0; cudaDeviceProp p; cudaGetDeviceProperties(&p, dev);
@@ -71,6 +113,22 @@ int main() {
     cudaEventRecord(e1); cudaEventSynchronize(e1);
     cudaEventElapsedTime(&ms, e0, e1);
     printf("fp32 div: %.3f G div/s\n", 4.0 * itd * 16 * blocks * threads / ms / 1e6);
+    const int itc = 1024;
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    const double per_sm_clk = (double)p.multiProcessorCount * clk_khz * 1e3;  // at the maximum SM clock
+    cudaEventRecord(e0);
+    cvt_loop<<<blocks, threads>>>(d, itc, 0.25);
+    cudaEventRecord(e1); cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    double ops = 16.0 * itc * blocks * threads;
+    printf("fp64<->fp32 convert: %.3f G/s  %.2f per SM per clock\n", ops / ms / 1e6, ops / (ms * 1e-3) / per_sm_clk);
+    cudaEventRecord(e0);
+    cmp_loop<<<blocks, threads>>>(d, itc, 1e-3);
+    cudaEventRecord(e1); cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    ops = 8.0 * itc * blocks * threads;
+    printf("fp64 compare: %.3f G/s  %.2f per SM per clock\n", ops / ms / 1e6, ops / (ms * 1e-3) / per_sm_clk);
   }
   cudaError_t err = cudaDeviceSynchronize();
   printf("status: %s\n", cudaGetErrorString(err));

@@ -21,16 +21,17 @@ rhs_div_kernel (divergence, sources, epilogue: 72 + 666 + 40).  The unit the
 benchmark times is that pair (one grmhd_rhs_cached call).
 
 Algorithmic HBM bytes per interior cell of the pair (FP64, static metric,
-geometry cache): prim 8 x 8 B + geometry cache 53 x 8 B read, rhs 8 x 8 B
-written = 552 B, plus the face buffer, 24 x 8 B written and read back =
-384 B: 936 B (the uncached single-pass grmhd_rhs reads the 10 metric
+geometry cache): prim 8 x 8 B + geometry cache 63 x 8 B read (the faces
+kernel reads the half-metric and face entries, the per-cell pass the rest),
+rhs 8 x 8 B written = 632 B, plus the face buffer, 24 x 8 B written and read
+back = 384 B: 1016 B (the uncached single-pass grmhd_rhs reads the 10 metric
 entries instead of the cache and has no face buffer: 208 B).
 
 Measured DRAM traffic of the pair (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, both kernels) for the 96^3 block (884,736 cells,
 capture in profiles/rhs_two_pass_fp64_cached_weno5_curved_96cube.md):
-345.7 MB + 771.0 MB = 1116.7 MB, 1262 B per cell; traffic grows with the
-cell count, so a launch on n^3 cells is 1262 n^3 B.
+348.4 MB + 770.7 MB = 1119.1 MB, 1265 B per cell; traffic grows with the
+cell count, so a launch on n^3 cells is 1265 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -43,8 +44,8 @@ import os
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
-BYTES_PER_CELL_RHS_CURVED = 552 + 384
-TRAFFIC_PER_CELL_MEASURED = (345.7e6 + 771.0e6) / 884736  # 1262 B per cell
+BYTES_PER_CELL_RHS_CURVED = 632 + 384
+TRAFFIC_PER_CELL_MEASURED = (348.4e6 + 770.7e6) / 884736  # 1265 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.20
 FP32_PEAK_TFLOPS_MEASURED = 75.0
 HBM_FALLBACK_GBS = 6800.0
