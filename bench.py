@@ -933,10 +933,10 @@ def main():
                   "dtype": "f32 reconstruct/HLLE/divergence + f64 con2prim/metric",
                   "speedup_vs_fp64": value_mx / value64, "failed_cells": nfailmx},
         "failed_cells": nfail64,
-        "tile_shapes": {"fp64": str(autotune.BLOCK_SHAPES[0]) + " (two-pass RHS)",
+        "tile_shapes": {"fp64": "none (three-pass RHS: states, faces, cells)",
                         "mixed": autotune.BLOCK_SHAPES[tiles[G.MIXED]]},
-        # per SSP-RK3 stage: the two RHS passes, the recovery and the ghost fill
-        "gpu_launches": args.steps * 12,
+        # per SSP-RK3 stage: the three RHS passes, the recovery and the ghost fill
+        "gpu_launches": args.steps * 15,
         "roofline": roof,
         "clocks": clk,
         "e2e": e2e,

@@ -1169,6 +1169,7 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
     StageEpilogue ep;
     ep.fb = nullptr;
     ep.faces = nullptr;
+    ep.states = nullptr;
     ep.rhs = nullptr;
     ep.u = W;
     ep.u0 = cons;

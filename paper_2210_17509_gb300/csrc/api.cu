@@ -57,11 +57,13 @@ cudaError_t launch_rhs(const DevGrid& g, const DevParams& p, const double* prim,
 }
 
 // Bytes of the cached-path scratch: geometry cache, FP32 primitives, inverse-
-// metric cache, and the two-pass face buffer (24 doubles per point).
+// metric cache, and the multi-pass FP64 RHS buffers: face fluxes (24 doubles
+// per point) followed by the WENO5 face states (48 doubles per point).
+constexpr int kFaceBufComps = 24, kStateBufComps = 48;
 size_t cache_bytes(const DevGrid& g) {
   return round256((size_t)kGeomCacheComps * g.ncell * sizeof(double)) + round256((size_t)8 * g.ncell * sizeof(float)) +
          round256((size_t)kMetricCacheComps * g.ncell * sizeof(double)) +
-         round256((size_t)24 * g.ncell * sizeof(double));
+         round256((size_t)(kFaceBufComps + kStateBufComps) * g.ncell * sizeof(double));
 }
 
 }  // namespace
@@ -160,7 +162,10 @@ int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const d
                                                ep, s));
   }
   if (!metric) return cuda_status(launch_rhs(g, p, prim, metric, kij, ep, s));
-  if (!(p.flags & GRMHD_SINGLE_PASS)) ep.faces = faces;
+  if (!(p.flags & GRMHD_SINGLE_PASS)) {
+    ep.faces = faces;
+    ep.states = faces + (size_t)kFaceBufComps * g.ncell;
+  }
   return cuda_status(launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s));
 }
 
@@ -252,6 +257,7 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     ep.wr = st[k].wr;
     ep.fb = ct ? ct->fb : nullptr;
     ep.faces = faces;
+    ep.states = faces ? faces + (size_t)kFaceBufComps * g.ncell : nullptr;
     if (fast_fp64) {
       if (launch_rhs_fp64_cached(g, p, prim, static_cast<const double*>(geom), kij, ep, s) != cudaSuccess)
         return GRMHD_ERR_CUDA;

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kTileThreads) batch_rhs_kernel(BatchHead* head
     StageEpilogue ep;
     ep.fb = nullptr;
     ep.faces = nullptr;
+    ep.states = nullptr;
     ep.rhs = b.rhs;
     ep.u = nullptr;
     ep.u0 = nullptr;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kBatchItem) batch_div_kernel(BatchHead* head, 
       StageEpilogue ep;
       ep.fb = nullptr;
       ep.faces = nullptr;
+    ep.states = nullptr;
       ep.rhs = b.rhs;
       ep.u = nullptr;
       ep.u0 = nullptr;

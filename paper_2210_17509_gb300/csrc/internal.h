@@ -57,6 +57,7 @@ struct StageEpilogue {
   double* rhs;
   double* fb;
   double* faces;
+  double* states;  // FP64 WENO5 face states, [3 dir][16][ncell] (nullable; with faces)
   double* u;
   const double* u0;
   const double* acc_in;
@@ -146,6 +147,7 @@ inline StageEpilogue no_epilogue() {
   e.rhs = nullptr;
   e.fb = nullptr;
   e.faces = nullptr;
+  e.states = nullptr;
   e.u = nullptr;
   e.u0 = nullptr;
   e.acc_in = nullptr;

@@ -114,7 +114,9 @@ __device__ __forceinline__ void weno5_pair<double>(double um3, double um2, doubl
 //
 // FP64: product form.  The weights d_k / e_k^2 times (e_0 e_1 e_2)^2 are
 // plus (P12, 6 P02, 3 P01) and minus (P01, 6 P02, 3 P12) up to a common
-// factor, with Pjk = (e_j e_k)^2; the caller divides num / (6 den).
+// factor, with Pjk = (e_j e_k)^2; the caller divides num / (6 den).  The
+// denominators' sums are written as rounded adds, so that no kernel that
+// inlines this fuses them differently: every FP64 path forms the same bits.
 __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double u0, double up1, double up2,
                                                  double eps13, double& nm, double& dm, double& np, double& dp) {
   const double k313 = 3.0 / 13.0;
@@ -135,9 +137,9 @@ __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double 
   const double qm1 = fma(2.0, um1, fma(5.0, u0, -up1));
   const double qm2 = fma(5.0, um1, fma(2.0, u0, -um2));
   np = fma(P12, qp0, fma(A, qp1, B * qp2));
-  dp = P12 + A + B;
+  dp = __dadd_rn(__dadd_rn(P12, A), B);
   nm = fma(P01, qm0, fma(A, qm1, C * qm2));
-  dm = P01 + A + C;
+  dm = __dadd_rn(__dadd_rn(P01, A), C);
 }
 
 // The numerator of one of the two states of weno5_cell_parts (plus: the
@@ -157,8 +159,8 @@ __device__ __forceinline__ void weno5_cell_parts_one(double um2, double um1, dou
   const double P01 = p01 * p01, P12 = p12 * p12;
   const double A = 6.0 * (p02 * p02), B = 3.0 * P01, C = 3.0 * P12;
   const double u11 = 11.0 * u0;
-  dp = P12 + A + B;
-  dm = P01 + A + C;
+  dp = __dadd_rn(__dadd_rn(P12, A), B);
+  dm = __dadd_rn(__dadd_rn(P01, A), C);
   if (plus) {
     const double qp0 = fma(2.0, um2, fma(-7.0, um1, u11));
     const double qp1 = fma(2.0, up1, fma(5.0, u0, -um1));

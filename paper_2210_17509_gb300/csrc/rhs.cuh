@@ -114,6 +114,28 @@ __device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim
   reconstruct_face<T, RECON, SrcF64>(s, ncell, c, stride, eps, pL, pR);
 }
 
+// FP64 WENO5: both states of cell c for the primitives 2h and 2h+1 into v
+// (minus and plus of 2h, then of 2h+1); the four values share one division.
+template <class S>
+__device__ __forceinline__ void weno5_cell_pair_states(const S& src, long long ncell, long long c, long long stride,
+                                                       int h, double eps13, double v[4]) {
+  double nm[2], dm[2], np[2], dp[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long a = (2 * h + k) * ncell + c;
+    weno5_cell_parts(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride), ld_prim<double>(src, a),
+                     ld_prim<double>(src, a + stride), ld_prim<double>(src, a + 2 * stride), eps13, nm[k], dm[k],
+                     np[k], dp[k]);
+  }
+  const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
+  const double X = 1.0 / (6.0 * a0 * a1);
+  const double x0 = a1 * X, x1 = a0 * X;
+  v[0] = nm[0] * (dp[0] * x0);
+  v[1] = np[0] * (dm[0] * x0);
+  v[2] = nm[1] * (dp[1] * x1);
+  v[3] = np[1] * (dm[1] * x1);
+}
+
 // Both reconstructed states of cell c (value at its lower face, "minus", and
 // at its upper face, "plus") for the primitives 2h and 2h+1, written to the
 // stage buffer sR at [2q][e] (minus) and [2q+1][e] (plus), ne entries per
@@ -148,22 +170,10 @@ __device__ __forceinline__ void reconstruct_cell_pair(const S& src, long long nc
       }
       return;
     }
-    // FP64: the four values of the two variables share one division
-    double nm[2], dm[2], np[2], dp[2];
+    double v[4];
+    weno5_cell_pair_states<S>(src, ncell, c, stride, h, (double)eps13, v);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const long long a = (2 * h + k) * ncell + c;
-      weno5_cell_parts(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride),
-                       ld_prim<double>(src, a), ld_prim<double>(src, a + stride),
-                       ld_prim<double>(src, a + 2 * stride), (double)eps13, nm[k], dm[k], np[k], dp[k]);
-    }
-    const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
-    const double X = 1.0 / (6.0 * a0 * a1);
-    const double x0 = a1 * X, x1 = a0 * X;
-    sR[(4 * h + 0) * ne + e] = (T)(nm[0] * (dp[0] * x0));
-    sR[(4 * h + 1) * ne + e] = (T)(np[0] * (dm[0] * x0));
-    sR[(4 * h + 2) * ne + e] = (T)(nm[1] * (dp[1] * x1));
-    sR[(4 * h + 3) * ne + e] = (T)(np[1] * (dm[1] * x1));
+    for (int k = 0; k < 4; ++k) sR[(4 * h + k) * ne + e] = (T)v[k];
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -982,24 +992,138 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(De
                                                       blockIdx.z * TS::Z, sF, sR);
 }
 
-// Two-pass launch (FP64 with the geometry cache and a face buffer in
-// ep.faces): faces, the constrained-transport ring if asked for, then the
-// per-cell pass.  Tile shape 8x8x4.
+// ---------------------------------------------------------------------------
+// Three-pass FP64 WENO5 RHS (the cached paths, with a state buffer in
+// ep.states).  The tile stage of the faces kernel reconstructs, besides its
+// own cells, the end cell below every line of the tile (about 8% of the
+// kernel's FP64 work); without tiles no cell is reconstructed twice:
+//   pass 1, rhs_states_kernel: per direction d, both face states of every
+//     cell on the lines of cells -1 .. n_d along d (interior across), into
+//     St [(16 d + 2 q + s) ncell + cell], s = 0 for the value at the cell's
+//     lower face (minus), 1 at its upper face (plus);
+//   pass 2, rhs_face_kernel: the flux of every d-face 0 .. n_d from the
+//     plus state of the cell below and the minus state of the cell above,
+//     into the face buffer (and the field fluxes for constrained transport)
+//     as faces_tile writes them;
+//   pass 3, rhs_div_kernel.
+// The operations and their inputs are those of the tiles, so the results
+// have the same bits.  The buffer costs 768 B of traffic per cell (written
+// once, read once), against an FP64-pipe-bound pass.
+constexpr int kStatesThreads = 256, kFaceThreads = 128;
+
+// Cells of direction d's state box: n_d + 2 along d, interior across.
+__host__ __device__ __forceinline__ long long state_cells(const DevGrid& g, int d) {
+  return (long long)(g.n[0] + 2 * (d == 0)) * (g.n[1] + 2 * (d == 1)) * (g.n[2] + 2 * (d == 2));
+}
+// Faces of direction d: n_d + 1 along d, interior across.
+__host__ __device__ __forceinline__ long long face_count(const DevGrid& g, int d) {
+  return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+}
+
+template <class S>
+__global__ void __launch_bounds__(kStatesThreads) rhs_states_kernel(DevGrid g, DevParams p, S src,
+                                                                    double* __restrict__ St) {
+  const long long m0 = state_cells(g, 0), m1 = state_cells(g, 1), m2 = state_cells(g, 2);
+  const long long total = 4 * (m0 + m1 + m2);
+  const double eps13 = p.weno_eps * (12.0 / 13.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    // direction, then variable pair, then the cells of the direction's box (x fastest)
+    int d = 0;
+    long long r = t;
+    if (r >= 4 * m0) {
+      r -= 4 * m0;
+      d = 1;
+      if (r >= 4 * m1) {
+        r -= 4 * m1;
+        d = 2;
+      }
+    }
+    const long long m = d == 0 ? m0 : (d == 1 ? m1 : m2);
+    const int h = (int)(r / m);
+    const long long l = r - h * m;
+    const int ex = g.n[0] + 2 * (d == 0), ey = g.n[1] + 2 * (d == 1);
+    const long long lxy = l / ex;
+    const int i = (int)(l - lxy * ex) - (d == 0);
+    const int j = (int)(lxy % ey) - (d == 1);
+    const int k = (int)(lxy / ey) - (d == 2);
+    const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
+    const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+    double v[4];
+    weno5_cell_pair_states<S>(src, g.ncell, c, stride, h, eps13, v);
+    double* o = St + (16LL * d + 4 * h) * g.ncell + c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q * g.ncell] = v[q];
+  }
+}
+
+template <bool CURVED, class S, bool POLY>
+__global__ void __launch_bounds__(kFaceThreads) rhs_face_kernel(DevGrid g, DevParams p, S src,
+                                                                const double* __restrict__ St,
+                                                                double* __restrict__ Ff, double* __restrict__ fb) {
+  const long long f0 = face_count(g, 0), f1 = face_count(g, 1), total = f0 + f1 + face_count(g, 2);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int d = t < f0 ? 0 : (t < f0 + f1 ? 1 : 2);
+    const long long l = t - (d == 0 ? 0 : (d == 1 ? f0 : f0 + f1));
+    const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+    const long long lxy = l / ex;
+    const int i = (int)(l - lxy * ex), j = (int)(lxy % ey), k = (int)(lxy / ey);
+    // c: the cell above the face
+    const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
+    const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+    const double* Sd = St + 16LL * d * g.ncell;
+    double pL[8], pR[8], F[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      pL[q] = __ldg(Sd + (2 * q + 1) * g.ncell + c - stride);
+      pR[q] = __ldg(Sd + (2 * q) * g.ncell + c);
+    }
+    face_flux_states<double, CURVED, S, POLY>(g, p, src, c, d, stride, pL, pR, F);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Ff[(8 * d + q) * g.ncell + c] = F[q];
+    if (fb) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a != d) fb[(3 * d + a) * g.ncell + c] = F[5 + a];
+    }
+  }
+}
+
+// Multi-pass launch (FP64 with the geometry cache and a face buffer in
+// ep.faces): the face fluxes (for WENO5 with a state buffer in ep.states the
+// state and face kernels, otherwise the 8x8x4 tile kernel), the
+// constrained-transport ring if asked for, then the per-cell pass.
 template <class T, int RECON, bool CURVED, class S>
 cudaError_t launch_rhs_two_pass(const DevGrid& g, const DevParams& p, const S& src, const StageEpilogue& ep,
                                 cudaStream_t s) {
   using TS = TileShape<0>;
   const bool poly = p.eos == GRMHD_EOS_POLYTROPE;
-  void (*k)(DevGrid, DevParams, S, double*, double*) =
-      poly ? rhs_faces_kernel<T, RECON, CURVED, S, true> : rhs_faces_kernel<T, RECON, CURVED, S, false>;
-  const size_t smem =
-      CellRecon<T, RECON>::value ? (size_t)16 * TileStage<TS::X, TS::Y, TS::Z>::NEA * sizeof(T) : (size_t)0;
-  if (smem) {
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  if (CellRecon<T, RECON>::value && ep.states) {
+    // three passes: states, faces (then the ring and the per-cell pass below)
+    const long long ns = 4 * (state_cells(g, 0) + state_cells(g, 1) + state_cells(g, 2));
+    long long bs = (ns + kStatesThreads - 1) / kStatesThreads;
+    if (bs > 152LL * 32) bs = 152LL * 32;
+    rhs_states_kernel<S><<<(int)bs, kStatesThreads, 0, s>>>(g, p, src, ep.states);
+    const long long nf = face_count(g, 0) + face_count(g, 1) + face_count(g, 2);
+    long long bf = (nf + kFaceThreads - 1) / kFaceThreads;
+    if (bf > 152LL * 32) bf = 152LL * 32;
+    if (poly)
+      rhs_face_kernel<CURVED, S, true><<<(int)bf, kFaceThreads, 0, s>>>(g, p, src, ep.states, ep.faces, ep.fb);
+    else
+      rhs_face_kernel<CURVED, S, false><<<(int)bf, kFaceThreads, 0, s>>>(g, p, src, ep.states, ep.faces, ep.fb);
+  } else {
+    void (*k)(DevGrid, DevParams, S, double*, double*) =
+        poly ? rhs_faces_kernel<T, RECON, CURVED, S, true> : rhs_faces_kernel<T, RECON, CURVED, S, false>;
+    const size_t smem =
+        CellRecon<T, RECON>::value ? (size_t)16 * TileStage<TS::X, TS::Y, TS::Z>::NEA * sizeof(T) : (size_t)0;
+    if (smem) {
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const dim3 grid((g.n[0] + TS::X - 1) / TS::X, (g.n[1] + TS::Y - 1) / TS::Y, (g.n[2] + TS::Z - 1) / TS::Z);
+    k<<<grid, kTileThreads, smem, s>>>(g, p, src, ep.faces, ep.fb);
   }
-  const dim3 grid((g.n[0] + TS::X - 1) / TS::X, (g.n[1] + TS::Y - 1) / TS::Y, (g.n[2] + TS::Z - 1) / TS::Z);
-  k<<<grid, kTileThreads, smem, s>>>(g, p, src, ep.faces, ep.fb);
   if (ep.fb) {
     const long long nring = ct_ring_faces(g, 0) + ct_ring_faces(g, 1) + ct_ring_faces(g, 2);
     long long blocks = (nring + kRingThreads - 1) / kRingThreads;

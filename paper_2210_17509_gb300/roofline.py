@@ -15,23 +15,27 @@ faces per cell counted once (tile-boundary recomputation is not algorithmic):
   stage epilogue                                40
   cell total (curved, WENO5): 3 * 1531 + 72 + 666 + 40 = 5371
 
-The FP64 RHS of the cached paths runs in two passes: rhs_faces_kernel
-(reconstruction and HLLE, every face once: 3 * 1531 flops per cell) and
-rhs_div_kernel (divergence, sources, epilogue: 72 + 666 + 40).  The unit the
-benchmark times is that pair (one grmhd_rhs_cached call).
+The FP64 RHS of the cached paths runs in three passes: rhs_states_kernel
+(WENO5 reconstruction, both states of every cell per direction: 3 * 16 * 69
+flops per cell counted per face as below), rhs_face_kernel (face metric,
+side states and HLLE of every face once) and rhs_div_kernel (divergence,
+sources, epilogue: 72 + 666 + 40).  The unit the benchmark times is that
+triple (one grmhd_rhs_cached call); the two first passes together do the
+3 * 1531 flops of the faces.
 
-Algorithmic HBM bytes per interior cell of the pair (FP64, static metric,
-geometry cache): prim 8 x 8 B + geometry cache 63 x 8 B read (the faces
-kernel reads the half-metric and face entries, the per-cell pass the rest),
-rhs 8 x 8 B written = 632 B, plus the face buffer, 24 x 8 B written and read
-back = 384 B: 1016 B (the uncached single-pass grmhd_rhs reads the 10 metric
-entries instead of the cache and has no face buffer: 208 B).
+Algorithmic HBM bytes per interior cell of the triple (FP64, static metric,
+geometry cache): prim 8 x 8 B + geometry cache 63 x 8 B read (the face pass
+reads the half-metric and face entries, the per-cell pass the rest), rhs
+8 x 8 B written = 632 B, plus the face buffer, 24 x 8 B written and read
+back = 384 B, and the state buffer, 48 x 8 B written and read back = 768 B:
+1784 B (the uncached single-pass grmhd_rhs reads the 10 metric entries
+instead of the cache and has no buffers: 208 B).
 
-Measured DRAM traffic of the pair (ncu, dram__bytes_read.sum +
-dram__bytes_write.sum, both kernels) for the 96^3 block (884,736 cells,
-capture in profiles/rhs_two_pass_fp64_cached_weno5_curved_96cube.md):
-348.4 MB + 770.7 MB = 1119.1 MB, 1265 B per cell; traffic grows with the
-cell count, so a launch on n^3 cells is 1265 n^3 B.
+Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
+dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
+cells, capture in profiles/rhs_three_pass_fp64_cached_weno5_curved_96cube.md):
+406.1 + 754.4 + 770.5 MB = 1931.0 MB, 2183 B per cell; traffic grows with
+the cell count, so a launch on n^3 cells is 2183 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -44,8 +48,8 @@ import os
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
-BYTES_PER_CELL_RHS_CURVED = 632 + 384
-TRAFFIC_PER_CELL_MEASURED = (348.4e6 + 770.7e6) / 884736  # 1265 B per cell
+BYTES_PER_CELL_RHS_CURVED = 632 + 384 + 768
+TRAFFIC_PER_CELL_MEASURED = (406.1e6 + 754.4e6 + 770.5e6) / 884736  # 2183 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.20
 FP32_PEAK_TFLOPS_MEASURED = 75.0
 HBM_FALLBACK_GBS = 6800.0
@@ -68,7 +72,8 @@ def rhs_fp64_roofline(ncells: int, ms_per_launch: float, traffic="measured"):
     gbs = BYTES_PER_CELL_RHS_CURVED * ncells / (ms_per_launch * 1e-3) / 1e9
     return {
         "bound": "alu",
-        "kernel": "rhs_faces_kernel + rhs_div_kernel<double, WENO5, curved, geometry cache> (grmhd_rhs_cached, FP64)",
+        "kernel": "rhs_states_kernel + rhs_face_kernel + rhs_div_kernel<double, WENO5, curved, geometry cache> "
+                  "(grmhd_rhs_cached, FP64)",
         "achieved": achieved, "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS_MEASURED, "traffic": traffic,
         "peak_source": "measured FP64 FMA probe (python -m paper_2210_17509_gb300.peaks)",
