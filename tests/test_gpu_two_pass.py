@@ -1,10 +1,11 @@
-"""The FP64 RHS of the cached paths in two passes (every face flux computed
-once into a face buffer, then a per-cell pass) against the single-pass tile
-kernel (GRMHD_SINGLE_PASS): the same face routine on the same stage, and the
-same per-cell operations in the same order, so the results are bit-identical.
-Blocks that end inside a tile (ragged) and exactly at a tile boundary (the
-boundary face layers of the last tiles) are both covered, with and without
-constrained transport, and blocks one cell thick along each axis.
+"""The RHS of the cached paths in several passes against the single-pass
+tile kernel (GRMHD_SINGLE_PASS).  FP64: WENO5 in three passes (the face states
+of every cell into a state buffer, every face flux once into a face buffer,
+then a per-cell pass), minmod in two (tiled faces, per-cell pass): the same
+reconstruction, face routine and per-cell operations, so the results are
+bit-identical.  Blocks that end inside a tile (ragged) and exactly at a tile
+boundary are both covered, with and without constrained transport, and blocks
+one cell thick along each axis.  The mixed path keeps the fused single pass.
 """
 import dataclasses
 
@@ -96,3 +97,28 @@ def test_ct_step_bit_identical(G, n):
         out.append((host(gc), host(gp), host(gb)))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rk_steps_multi_pass_against_oracle(G, precision):
+    """SSP-RK3 steps on the cached paths (FP64 in several passes, mixed in
+    the fused pass) against the oracle, ragged block."""
+    from tests.helpers import FP64_TOL, MIXED_TOL, normwise
+    blk, m, prim = state((19, 13, 11))
+    og = O.Grid(blk.n, 3, blk.dx)
+    op = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY)
+    cons = O.prim2con(og, op.gamma, prim, m)
+    dt = 0.25 * blk.dx[0]
+    c, pr = cons, prim
+    for _ in range(2):
+        c, pr, nf = O.rk_step(og, op, O.RK3, dt, c, pr, m)
+        assert nf == 0
+    g = G.Grid(blk.n, 3, blk.dx)
+    p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision)
+    gc, gp, gm = cuda(cons), cuda(prim), cuda(m)
+    ws = G.workspace(g, G.RK3)
+    for _ in range(2):
+        G.rk_step(g, p, G.RK3, dt, gc, gp, gm, ws=ws)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    inner = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
+    assert np.all(normwise(host(gc)[inner], c[inner]) <= tol)
