@@ -920,9 +920,12 @@ __device__ __forceinline__ void div_cell(const DevGrid& g, const DevParams& p, c
   }
 }
 
-// Pass 2 over the interior cells of one block.
+// Pass 2 over the interior cells of one block: 128-thread CTAs, registers
+// fitted to 3 per SM (12 warps; the FP64 curved sources otherwise take 212
+// registers and leave 8 warps per SM).
+constexpr int kDivThreads = 128;
 template <class T, bool CURVED, class S>
-__global__ void __launch_bounds__(256) rhs_div_kernel(DevGrid g, DevParams p, S src, const double* __restrict__ Ff,
+__global__ void __launch_bounds__(kDivThreads, 3) rhs_div_kernel(DevGrid g, DevParams p, S src, const double* __restrict__ Ff,
                                                       StageEpilogue ep) {
   const long long nx = g.n[0], ny = g.n[1], nint = nx * ny * g.n[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
@@ -1134,9 +1137,9 @@ cudaError_t launch_rhs_two_pass(const DevGrid& g, const DevParams& p, const S& s
       ct_ring_kernel<T, RECON, CURVED, S><<<(int)blocks, kRingThreads, 0, s>>>(g, p, src, ep.fb);
   }
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  long long blocks = (nint + 255) / 256;
-  if (blocks > 152LL * 16) blocks = 152LL * 16;
-  rhs_div_kernel<T, CURVED, S><<<(int)blocks, 256, 0, s>>>(g, p, src, ep.faces, ep);
+  long long blocks = (nint + kDivThreads - 1) / kDivThreads;
+  if (blocks > 152LL * 24) blocks = 152LL * 24;
+  rhs_div_kernel<T, CURVED, S><<<(int)blocks, kDivThreads, 0, s>>>(g, p, src, ep.faces, ep);
   return cudaGetLastError();
 }
 

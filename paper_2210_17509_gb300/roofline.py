@@ -50,7 +50,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
 BYTES_PER_CELL_RHS_CURVED = 632 + 384 + 768
-TRAFFIC_PER_CELL_MEASURED = (406.1e6 + 754.4e6 + 770.5e6) / 884736  # 2183 B per cell
+TRAFFIC_PER_CELL_MEASURED = None  # re-measured after the per-cell pass's launch change
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
 HBM_FALLBACK_GBS = 6800.0
