@@ -34,8 +34,8 @@ instead of the cache and has no buffers: 208 B).
 Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
 cells, capture in profiles/rhs_three_pass_fp64_cached_weno5_curved_96cube.md):
-406.1 + 754.4 + 770.5 MB = 1931.0 MB, 2183 B per cell; traffic grows with
-the cell count, so a launch on n^3 cells is 2183 n^3 B.
+405.4 + 754.5 + 786.7 MB = 1946.6 MB, 2200 B per cell; traffic grows with
+the cell count, so a launch on n^3 cells is 2200 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -50,7 +50,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FLOPS_PER_CELL_RHS_CURVED_WENO5 = 5371
 BYTES_PER_CELL_RHS_CURVED = 632 + 384 + 768
-TRAFFIC_PER_CELL_MEASURED = None  # re-measured after the per-cell pass's launch change
+TRAFFIC_PER_CELL_MEASURED = (405.4e6 + 754.5e6 + 786.7e6) / 884736  # 2200 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
 HBM_FALLBACK_GBS = 6800.0
