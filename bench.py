@@ -726,7 +726,7 @@ def main():
 
     # tile shape of the single block from the project's autotuner (per precision)
     from paper_2210_17509_gb300 import autotune
-    # (the FP64 RHS of the cached step runs in two passes on the 8x8x4 tile,
+    # (the FP64 RHS of the cached step runs in three passes, without tiles,
     # whatever the tile parameter says; the mixed RHS takes the tuned shape)
     if args.tile >= 0:
         tiles = {G.FP64: args.tile, G.MIXED: args.tile}

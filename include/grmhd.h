@@ -113,9 +113,11 @@ typedef struct {
  * instead of the Newton iteration (see grmhd_con2prim). */
 #define GRMHD_NEWMAN_HAMLIN 2
 /* flags: the FP64 RHS of the cached paths runs in one pass (each tile
- * computing the faces on its boundaries as well) instead of two (every face
- * flux computed once into the workspace's face buffer, then a per-cell
- * pass).  The results are the same; a switch for comparison. */
+ * computing the faces on its boundaries as well) instead of several (for
+ * WENO5 the face states of every cell into the workspace's state buffer,
+ * every face flux once into its face buffer, then a per-cell pass; for
+ * minmod tiled faces, then the per-cell pass).  The results are the same; a
+ * switch for comparison. */
 #define GRMHD_SINGLE_PASS 4
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
@@ -183,7 +185,7 @@ int grmhd_rhs(const grmhd_grid* grid, const grmhd_params* params, const double* 
 
 /* grmhd_rhs computed from the geometry caches of grmhd_rk_workspace_bytes_cached
  * (and, for GRMHD_MIXED, an FP32 copy of prim; for FP64 with a metric, the
- * two-pass face buffer) held in ws: the same RHS,
+ * multi-pass state and face buffers) held in ws: the same RHS,
  * with the per-face and per-cell metric algebra done once per static metric.
  * ws >= grmhd_rhs_workspace_bytes(grid), 256-byte aligned; the caches are
  * rebuilt unless params->flags has GRMHD_REUSE_GEOMETRY (same grid, metric and
@@ -202,8 +204,9 @@ size_t grmhd_rk_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
  * spacetime with GRMHD_REUSE_GEOMETRY -- stored as FP64 for the FP64 path and
  * as FP32 for the mixed path), an FP64 inverse-metric cache for the recovery,
  * for the mixed path an FP32 copy of the primitives, and for the FP64 path a
- * face buffer of 24 doubles per point (the two-pass RHS: every face flux
- * computed once, see GRMHD_SINGLE_PASS).  With less (but at least
+ * face buffer of 24 and a state buffer of 48 doubles per point (the
+ * multi-pass RHS: every cell's face states and every face flux computed
+ * once, see GRMHD_SINGLE_PASS).  With less (but at least
  * grmhd_rk_workspace_bytes) the kernels read the FP64 inputs directly;
  * results agree to round-off. */
 size_t grmhd_rk_workspace_bytes_cached(const grmhd_grid* grid, int32_t scheme);

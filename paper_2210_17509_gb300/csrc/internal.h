@@ -50,14 +50,16 @@ struct DevParams {
 //                    the d-faces 0 .. n_d with transverse indices -1 .. n
 //                    (the tiles, then a ring kernel; constrained transport)
 //   faces   != NULL: (FP64 with the geometry cache) device scratch of
-//                    24 ncell doubles; the RHS then runs in two passes, every
-//                    face flux computed once into it (rhs.cuh)
+//                    24 ncell doubles; the RHS then runs in several passes,
+//                    every face flux computed once into it (rhs.cuh)
+//   states  != NULL: (with faces, WENO5) 48 ncell doubles for the face states
+//                    of every cell, computed once per cell and direction
 // u0 must be valid whenever u is set.
 struct StageEpilogue {
   double* rhs;
   double* fb;
   double* faces;
-  double* states;  // FP64 WENO5 face states, [3 dir][16][ncell] (nullable; with faces)
+  double* states;
   double* u;
   const double* u0;
   const double* acc_in;
