@@ -208,7 +208,7 @@ def cpu_baseline_sample(G, seconds_target=15.0):
 def batched_bench(G, steps, warmup, nbox=512):
     """512 AMR-like boxes (edges from {8..64}, 3 refinement levels, flat):
     recovery + ghost fill + RHS of every box as one graph of persistent
-    launches (three; four for the two-pass FP64 RHS), against the plain form
+    launches (three; five for the three-pass FP64 WENO5 RHS), against the plain form
     (three launches per box)."""
     import torch
     from paper_2210_17509_gb300 import autotune
@@ -271,8 +271,11 @@ def batched_bench(G, steps, warmup, nbox=512):
             tiles_used[str(autotune.SHAPES[b.tile])] = tiles_used.get(str(autotune.SHAPES[b.tile]), 0) + 1
         out[name] = {"value": ncells / (ms * 1e-3), "unit": "cells/s (recovery+RHS per box, one evaluation)",
                      "ms_per_batch": ms, "plain_per_box_ms": ms_plain, "speedup_vs_plain": ms_plain / ms,
-                     "gpu_launches_per_batch": 4 if batch.c.two_pass and precision == G.FP64 else 3,
-                     "two_pass": bool(batch.c.two_pass and precision == G.FP64), "tile_shapes": tiles_used}
+                     "gpu_launches_per_batch": (3 + (batch.c.two_pass + batch.c.three_pass
+                                                     if precision == G.FP64 else 0)),
+                     "multi_pass": ("three passes" if batch.c.three_pass and precision == G.FP64 else
+                                    "two passes" if batch.c.two_pass and precision == G.FP64 else "one pass"),
+                     "tile_shapes": tiles_used}
         del boxes, batch, graph
         torch.cuda.empty_cache()
     return out

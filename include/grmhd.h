@@ -242,7 +242,10 @@ typedef struct {
   int32_t tile;          /* GRMHD_TILE_* for this box */
   int32_t bc;            /* GRMHD_BC_* for this box's primitive ghosts */
   double* faces;         /* nullable: 24 x ncell doubles of face buffer; when every box has one, the
-                            FP64 RHS runs in two passes (every face flux once), else in one */
+                            FP64 RHS runs in several passes (every face flux once), else in one */
+  double* states;        /* nullable (needs faces): 48 x ncell doubles of WENO5 face states; when every
+                            box has one, the FP64 WENO5 RHS runs in three passes (every cell's face
+                            states once, then every face flux once, then the per-cell pass) */
 } grmhd_box;
 
 /* Prepared batch (filled by grmhd_batch_prepare; plain data, caller-owned). */
@@ -255,7 +258,7 @@ typedef struct {
   int64_t nc2p_items;    /* recovery work items (256 interior cells each) */
   int64_t nghost_items;  /* ghost-fill work items (256 points each) */
   int32_t two_pass;      /* 1 if every box carries a face buffer */
-  int32_t reserved;
+  int32_t three_pass;    /* 1 if every box also carries a state buffer */
 } grmhd_batch;
 
 /* Device workspace (bytes) for a batch of nbox boxes; 0 if nbox is invalid. */
@@ -271,11 +274,12 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
 
 /* For every box: primitive recovery from cons (as grmhd_con2prim), ghost fill
  * (as grmhd_fill_ghosts with the box's bc), then the RHS (as grmhd_rhs with
- * the box's tile shape; the same bits in two passes when batch->two_pass and
- * params->precision is GRMHD_FP64).  Three persistent launches on `stream`
- * (four with two passes; plus one memset of the work counters), no host
+ * the box's tile shape; the same bits in several passes when batch->two_pass
+ * and params->precision is GRMHD_FP64: two, or three for WENO5 with
+ * batch->three_pass).  Three persistent launches on `stream` (four with two
+ * passes, five with three; plus one memset of the work counters), no host
  * synchronisation: the sequence can be captured into a CUDA graph.  nfail as
- * for grmhd_con2prim.  Boxes' face buffers must not overlap. */
+ * for grmhd_con2prim.  Boxes' face and state buffers must not overlap. */
 int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream);
 
 /* ----------------------------------------------------------------------

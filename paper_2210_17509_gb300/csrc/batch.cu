@@ -11,8 +11,8 @@ cudaError_t launch_batch_rhs_fp64(BatchHead* head, const BoxDev* boxes, const De
                                   cudaStream_t s);
 cudaError_t launch_batch_rhs_mixed(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
                                    cudaStream_t s);
-cudaError_t launch_batch_rhs_two_pass(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
-                                      cudaStream_t s);
+cudaError_t launch_batch_rhs_two_pass(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved,
+                                      bool three, int nsm, cudaStream_t s);
 __global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
                                                                     DevParams p, int32_t* nfail) {
   int myfail = 0;
@@ -78,7 +78,7 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   if (ws_bytes < need) return GRMHD_ERR_SIZE;
   const int min_ng = params->recon == GRMHD_WENO5 ? 3 : 2;
   std::vector<BoxDev> host(nbox);
-  int ncurved = 0, nfaces = 0;
+  int ncurved = 0, nfaces = 0, nstates = 0;
   for (int b = 0; b < nbox; ++b) {
     const grmhd_box& x = boxes[b];
     const grmhd_grid& gr = x.grid;
@@ -89,7 +89,9 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
       return GRMHD_ERR_ARG;
     if (x.metric && !aligned8(x.metric)) return GRMHD_ERR_ARG;
     if (x.faces && !aligned8(x.faces)) return GRMHD_ERR_ARG;
+    if (x.states && (!aligned8(x.states) || !x.faces)) return GRMHD_ERR_ARG;
     nfaces += x.faces != nullptr;
+    nstates += x.states != nullptr;
     if (x.tile < 0 || x.tile > 3) return GRMHD_ERR_ARG;
     if (x.bc != GRMHD_BC_PERIODIC && x.bc != GRMHD_BC_COPY) return GRMHD_ERR_ARG;
     ncurved += x.metric != nullptr;
@@ -100,12 +102,14 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
     h.metric = x.metric;
     h.rhs = x.rhs;
     h.faces = x.faces;
+    h.states = x.states;
     h.tile = x.tile;
     h.bc = x.bc;
     for (int d = 0; d < 3; ++d) h.nt[d] = (gr.n[d] + kShape[x.tile][d] - 1) / kShape[x.tile][d];
   }
   if (ncurved != 0 && ncurved != nbox) return GRMHD_ERR_ARG;  // one kernel variant per batch
   if (nfaces != 0 && nfaces != nbox) return GRMHD_ERR_ARG;    // two passes for all boxes or none
+  if (nstates != 0 && nstates != nbox) return GRMHD_ERR_ARG;  // three passes for all boxes or none
   // Largest boxes first (longest-processing-time order) so the dynamic work
   // counter finishes with small items.
   std::vector<int> order(nbox);
@@ -113,13 +117,19 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   auto work = [&](int b) { return (long long)host[b].nt[0] * host[b].nt[1] * host[b].nt[2]; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
   std::vector<BoxDev> sorted(nbox);
-  long long tiles = 0, c2p = 0, gh = 0;
+  long long tiles = 0, c2p = 0, gh = 0, st = 0, fc = 0;
   for (int k = 0; k < nbox; ++k) {
     BoxDev h = host[order[k]];
     h.tile_begin = tiles;
     h.c2p_begin = c2p;
     h.gh_begin = gh;
+    h.st_begin = st;
+    h.fc_begin = fc;
     tiles += work(order[k]);
+    if (h.states) {
+      st += (state_items(h.g) + kBatchItem - 1) / kBatchItem;
+      fc += (face_items(h.g) + kBatchFaces - 1) / kBatchFaces;
+    }
     const long long nint = (long long)h.g.n[0] * h.g.n[1] * h.g.n[2];
     c2p += (nint + kBatchItem - 1) / kBatchItem;
     gh += (h.g.ncell + kBatchItem - 1) / kBatchItem;
@@ -131,7 +141,9 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   head.ntiles = tiles;
   head.nc2p = c2p;
   head.ngh = gh;
-  for (int i = 0; i < 4; ++i) head.counter[i] = 0;
+  head.nst = st;
+  head.nfc = fc;
+  for (int i = 0; i < 6; ++i) head.counter[i] = 0;
   cudaStream_t s = (cudaStream_t)stream;
   // Host sources are pageable: the calls return once the data are staged.
   if (cudaMemcpyAsync(ws, &head, sizeof(head), cudaMemcpyHostToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
@@ -147,7 +159,7 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   batch->nc2p_items = c2p;
   batch->nghost_items = gh;
   batch->two_pass = nfaces == nbox;
-  batch->reserved = 0;
+  batch->three_pass = nstates == nbox;
   return GRMHD_OK;
 }
 
@@ -174,7 +186,7 @@ int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_
   const bool curved = batch->curved != 0;
   cudaError_t e;
   if (p.precision == GRMHD_MIXED) e = launch_batch_rhs_mixed(head, boxes, p, curved, nsm, s);
-  else if (batch->two_pass) e = launch_batch_rhs_two_pass(head, boxes, p, curved, nsm, s);
+  else if (batch->two_pass) e = launch_batch_rhs_two_pass(head, boxes, p, curved, batch->three_pass != 0, nsm, s);
   else e = launch_batch_rhs_fp64(head, boxes, p, curved, nsm, s);
   return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }

@@ -16,22 +16,27 @@ struct BoxDev {
   double* prim;
   const double* metric;
   double* rhs;
-  double* faces;       // two-pass face buffer (24 ncell doubles) or NULL
+  double* faces;       // multi-pass face buffer (24 ncell doubles) or NULL
+  double* states;      // WENO5 state buffer (48 ncell doubles) or NULL
   int tile, bc;
   int nt[3];           // tiles per axis for the box's tile shape
   long long tile_begin;  // first RHS work item of the box
   long long c2p_begin;   // first recovery item (256 interior cells each)
   long long gh_begin;    // first ghost-fill item (256 points each)
+  long long st_begin;    // first state item (kBatchItem state items each)
+  long long fc_begin;    // first face item (kBatchFaces faces each)
 };
 
 struct BatchHead {
   int nbox;
   int pad;
-  long long ntiles, nc2p, ngh;
-  unsigned long long counter[4];  // work counters, zeroed before every run
+  long long ntiles, nc2p, ngh, nst, nfc;
+  // work counters, zeroed before every run: tiles, recovery, ghosts, cells, states, faces
+  unsigned long long counter[6];
 };
 
 constexpr int kBatchItem = 256;
+constexpr int kBatchFaces = kFaceThreads;
 
 // Box holding work item `it` (boxes sorted by ascending begin offsets).
 template <int WHICH>
@@ -39,7 +44,12 @@ __device__ __forceinline__ int find_box(const BoxDev* __restrict__ boxes, int nb
   int lo = 0, hi = nbox - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const long long b = WHICH == 0 ? boxes[mid].tile_begin : (WHICH == 1 ? boxes[mid].c2p_begin : boxes[mid].gh_begin);
+    const BoxDev& x = boxes[mid];
+    const long long b = WHICH == 0   ? x.tile_begin
+                        : WHICH == 1 ? x.c2p_begin
+                        : WHICH == 2 ? x.gh_begin
+                        : WHICH == 3 ? x.st_begin
+                                     : x.fc_begin;
     if (b <= it) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -142,6 +152,49 @@ __global__ void __launch_bounds__(kTileThreads) batch_faces_kernel(BatchHead* he
         break;
     }
     __syncthreads();  // the stage is reused by the next item
+  }
+}
+
+// Three-pass FP64 WENO5 RHS over the table (every box with a state buffer):
+// the state and face items of rhs.cuh, handed out in chunks per box.
+template <int RECON>
+__global__ void __launch_bounds__(kBatchItem) batch_states_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                                  DevParams p) {
+  static_assert(RECON == GRMHD_WENO5, "the state pass is WENO5's");
+  const int nbox = head->nbox;
+  const long long total = head->nst;
+  for (;;) {
+    const long long it = next_item(&head->counter[4]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<3>(boxes, nbox, it)];
+    const long long t = (it - b.st_begin) * kBatchItem + threadIdx.x;
+    if (t < state_items(b.g)) {
+      SrcF64 src;
+      src.prim = b.prim;
+      src.metric = b.metric;
+      src.kij = nullptr;
+      rhs_state_item<SrcF64>(b.g, p, src, b.states, t);
+    }
+  }
+}
+
+template <bool CURVED>
+__global__ void __launch_bounds__(kBatchFaces) batch_face_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
+                                                                 DevParams p) {
+  const int nbox = head->nbox;
+  const long long total = head->nfc;
+  for (;;) {
+    const long long it = next_item(&head->counter[5]);
+    if (it >= total) break;
+    const BoxDev& b = boxes[find_box<4>(boxes, nbox, it)];
+    const long long t = (it - b.fc_begin) * kBatchFaces + threadIdx.x;
+    if (t < face_items(b.g)) {
+      SrcF64 src;
+      src.prim = b.prim;
+      src.metric = b.metric;
+      src.kij = nullptr;
+      rhs_face_item<CURVED, SrcF64, false>(b.g, p, src, b.states, b.faces, nullptr, t);
+    }
   }
 }
 

@@ -1023,74 +1023,95 @@ __host__ __device__ __forceinline__ long long face_count(const DevGrid& g, int d
   return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
 }
 
+// State items of a block: direction, then variable pair, then the cells of
+// the direction's box (x fastest).
+__host__ __device__ __forceinline__ long long state_items(const DevGrid& g) {
+  return 4 * (state_cells(g, 0) + state_cells(g, 1) + state_cells(g, 2));
+}
+__host__ __device__ __forceinline__ long long face_items(const DevGrid& g) {
+  return face_count(g, 0) + face_count(g, 1) + face_count(g, 2);
+}
+
+// State item t (0 <= t < state_items(g)) of pass 1.
+template <class S>
+__device__ __forceinline__ void rhs_state_item(const DevGrid& g, const DevParams& p, const S& src,
+                                               double* __restrict__ St, long long t) {
+  const long long m0 = state_cells(g, 0), m1 = state_cells(g, 1), m2 = state_cells(g, 2);
+  int d = 0;
+  long long r = t;
+  if (r >= 4 * m0) {
+    r -= 4 * m0;
+    d = 1;
+    if (r >= 4 * m1) {
+      r -= 4 * m1;
+      d = 2;
+    }
+  }
+  const long long m = d == 0 ? m0 : (d == 1 ? m1 : m2);
+  const int h = (int)(r / m);
+  const long long l = r - h * m;
+  const int ex = g.n[0] + 2 * (d == 0), ey = g.n[1] + 2 * (d == 1);
+  const long long lxy = l / ex;
+  const int i = (int)(l - lxy * ex) - (d == 0);
+  const int j = (int)(lxy % ey) - (d == 1);
+  const int k = (int)(lxy / ey) - (d == 2);
+  const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
+  const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+  double v[4];
+  weno5_cell_pair_states<S>(src, g.ncell, c, stride, h, p.weno_eps * (12.0 / 13.0), v);
+  double* o = St + (16LL * d + 4 * h) * g.ncell + c;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q * g.ncell] = v[q];
+}
+
+// Face item t (0 <= t < face_items(g)) of pass 2.
+template <bool CURVED, class S, bool POLY>
+__device__ __forceinline__ void rhs_face_item(const DevGrid& g, const DevParams& p, const S& src,
+                                              const double* __restrict__ St, double* __restrict__ Ff,
+                                              double* __restrict__ fb, long long t) {
+  const long long f0 = face_count(g, 0), f1 = face_count(g, 1);
+  const int d = t < f0 ? 0 : (t < f0 + f1 ? 1 : 2);
+  const long long l = t - (d == 0 ? 0 : (d == 1 ? f0 : f0 + f1));
+  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+  const long long lxy = l / ex;
+  const int i = (int)(l - lxy * ex), j = (int)(lxy % ey), k = (int)(lxy / ey);
+  // c: the cell above the face
+  const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
+  const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+  const double* Sd = St + 16LL * d * g.ncell;
+  double pL[8], pR[8], F[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    pL[q] = __ldg(Sd + (2 * q + 1) * g.ncell + c - stride);
+    pR[q] = __ldg(Sd + (2 * q) * g.ncell + c);
+  }
+  face_flux_states<double, CURVED, S, POLY>(g, p, src, c, d, stride, pL, pR, F);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) Ff[(8 * d + q) * g.ncell + c] = F[q];
+  if (fb) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a != d) fb[(3 * d + a) * g.ncell + c] = F[5 + a];
+  }
+}
+
 template <class S>
 __global__ void __launch_bounds__(kStatesThreads) rhs_states_kernel(DevGrid g, DevParams p, S src,
                                                                     double* __restrict__ St) {
-  const long long m0 = state_cells(g, 0), m1 = state_cells(g, 1), m2 = state_cells(g, 2);
-  const long long total = 4 * (m0 + m1 + m2);
-  const double eps13 = p.weno_eps * (12.0 / 13.0);
+  const long long total = state_items(g);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    // direction, then variable pair, then the cells of the direction's box (x fastest)
-    int d = 0;
-    long long r = t;
-    if (r >= 4 * m0) {
-      r -= 4 * m0;
-      d = 1;
-      if (r >= 4 * m1) {
-        r -= 4 * m1;
-        d = 2;
-      }
-    }
-    const long long m = d == 0 ? m0 : (d == 1 ? m1 : m2);
-    const int h = (int)(r / m);
-    const long long l = r - h * m;
-    const int ex = g.n[0] + 2 * (d == 0), ey = g.n[1] + 2 * (d == 1);
-    const long long lxy = l / ex;
-    const int i = (int)(l - lxy * ex) - (d == 0);
-    const int j = (int)(lxy % ey) - (d == 1);
-    const int k = (int)(lxy / ey) - (d == 2);
-    const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
-    const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
-    double v[4];
-    weno5_cell_pair_states<S>(src, g.ncell, c, stride, h, eps13, v);
-    double* o = St + (16LL * d + 4 * h) * g.ncell + c;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) o[q * g.ncell] = v[q];
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    rhs_state_item<S>(g, p, src, St, t);
 }
 
 template <bool CURVED, class S, bool POLY>
 __global__ void __launch_bounds__(kFaceThreads) rhs_face_kernel(DevGrid g, DevParams p, S src,
                                                                 const double* __restrict__ St,
                                                                 double* __restrict__ Ff, double* __restrict__ fb) {
-  const long long f0 = face_count(g, 0), f1 = face_count(g, 1), total = f0 + f1 + face_count(g, 2);
+  const long long total = face_items(g);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int d = t < f0 ? 0 : (t < f0 + f1 ? 1 : 2);
-    const long long l = t - (d == 0 ? 0 : (d == 1 ? f0 : f0 + f1));
-    const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
-    const long long lxy = l / ex;
-    const int i = (int)(l - lxy * ex), j = (int)(lxy % ey), k = (int)(lxy / ey);
-    // c: the cell above the face
-    const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
-    const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
-    const double* Sd = St + 16LL * d * g.ncell;
-    double pL[8], pR[8], F[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      pL[q] = __ldg(Sd + (2 * q + 1) * g.ncell + c - stride);
-      pR[q] = __ldg(Sd + (2 * q) * g.ncell + c);
-    }
-    face_flux_states<double, CURVED, S, POLY>(g, p, src, c, d, stride, pL, pR, F);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) Ff[(8 * d + q) * g.ncell + c] = F[q];
-    if (fb) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (a != d) fb[(3 * d + a) * g.ncell + c] = F[5 + a];
-    }
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    rhs_face_item<CURVED, S, POLY>(g, p, src, St, Ff, fb, t);
 }
 
 // Multi-pass launch (FP64 with the geometry cache and a face buffer in
@@ -1104,11 +1125,11 @@ cudaError_t launch_rhs_two_pass(const DevGrid& g, const DevParams& p, const S& s
   const bool poly = p.eos == GRMHD_EOS_POLYTROPE;
   if (CellRecon<T, RECON>::value && ep.states) {
     // three passes: states, faces (then the ring and the per-cell pass below)
-    const long long ns = 4 * (state_cells(g, 0) + state_cells(g, 1) + state_cells(g, 2));
+    const long long ns = state_items(g);
     long long bs = (ns + kStatesThreads - 1) / kStatesThreads;
     if (bs > 152LL * 32) bs = 152LL * 32;
     rhs_states_kernel<S><<<(int)bs, kStatesThreads, 0, s>>>(g, p, src, ep.states);
-    const long long nf = face_count(g, 0) + face_count(g, 1) + face_count(g, 2);
+    const long long nf = face_items(g);
     long long bf = (nf + kFaceThreads - 1) / kFaceThreads;
     if (bf > 152LL * 32) bf = 152LL * 32;
     if (poly)

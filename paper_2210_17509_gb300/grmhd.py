@@ -294,13 +294,13 @@ def rk_step_static(grid: Grid, params: Params, scheme: int, dt: float, cons, pri
 # ------------------------------------------------------------ batched boxes --
 class CBox(ctypes.Structure):
     _fields_ = [("grid", CGrid), ("cons", _P), ("prim", _P), ("metric", _P), ("rhs", _P), ("tile", _I32),
-                ("bc", _I32), ("faces", _P)]
+                ("bc", _I32), ("faces", _P), ("states", _P)]
 
 
 class CBatch(ctypes.Structure):
     _fields_ = [("ws", _P), ("ws_bytes", ctypes.c_size_t), ("nbox", _I32), ("curved", _I32), ("ntiles", ctypes.c_int64),
                 ("nc2p_items", ctypes.c_int64), ("nghost_items", ctypes.c_int64), ("two_pass", _I32),
-                ("reserved", _I32)]
+                ("three_pass", _I32)]
 
 
 _lib.grmhd_batch_workspace_bytes.argtypes = [_I32]
@@ -322,29 +322,36 @@ class Box:
     metric: "torch.Tensor" = None
     tile: int = 0
     bc: int = BC_PERIODIC
-    faces: "torch.Tensor" = None  # [24][z][y][x] face buffer of the two-pass FP64 RHS
+    faces: "torch.Tensor" = None  # [24][z][y][x] face buffer of the multi-pass FP64 RHS
+    states: "torch.Tensor" = None  # [48][z][y][x] WENO5 state buffer of the three-pass FP64 RHS
 
 
 class Batch:
     """A prepared box table (grmhd_batch_prepare); keeps the tensors alive.
     two_pass (default: FP64): give every box a face buffer (allocated here
-    where a box has none), so that the FP64 RHS runs in two passes."""
+    where a box has none), so that the FP64 RHS runs in several passes; for
+    WENO5 also a state buffer, so that it runs in three (states, faces,
+    cells)."""
 
     def __init__(self, boxes, params: Params, stream=None, two_pass=None):
         self.boxes = list(boxes)
         n = len(self.boxes)
         if two_pass is None:
             two_pass = params.precision == FP64
+        three = bool(two_pass) and params.recon == WENO5
         if two_pass:
             for b in self.boxes:
                 if b.faces is None:
                     b.faces = torch.empty((24,) + b.grid.shape, dtype=torch.float64, device=b.cons.device)
+                if three and b.states is None:
+                    b.states = torch.empty((48,) + b.grid.shape, dtype=torch.float64, device=b.cons.device)
         arr = (CBox * n)()
         for i, b in enumerate(self.boxes):
             arr[i] = CBox(b.grid.c(), _field(b.cons, b.grid, 8, "cons"), _field(b.prim, b.grid, 8, "prim"),
                           _field(b.metric, b.grid, 10, "metric", True), _field(b.rhs, b.grid, 8, "rhs"),
                           int(b.tile), int(b.bc),
-                          _field(b.faces, b.grid, 24, "faces", True) if two_pass else None)
+                          _field(b.faces, b.grid, 24, "faces", True) if two_pass else None,
+                          _field(b.states, b.grid, 48, "states", True) if three else None)
         nbytes = int(_lib.grmhd_batch_workspace_bytes(n))
         if nbytes == 0:
             raise GrmhdError("invalid number of boxes")

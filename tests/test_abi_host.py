@@ -138,6 +138,25 @@ def test_batch_prepare_validation(lib):
     assert rc == -4
 
 
+def test_batch_prepare_rejects_inconsistent_state_buffers(lib):
+    """A state buffer needs a face buffer, and three passes take every box or
+    none: both are rejected while validating, before the box table is copied
+    anywhere (the pointers here are never dereferenced)."""
+    import ctypes as C
+    G = lib
+    p = G.Params().c()
+    nb = G._lib.grmhd_batch_workspace_bytes(2)
+    g = G.Grid((8, 8, 8), 3, (0.1, 0.1, 0.1))
+    out = G.CBatch()
+    boxes = (G.CBox * 1)()
+    boxes[0] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 0, 0, None, FAKE)  # states without faces
+    assert G._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None) == -1
+    boxes = (G.CBox * 2)()
+    boxes[0] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 0, 0, FAKE, FAKE)
+    boxes[1] = G.CBox(g.c(), FAKE, FAKE, None, FAKE, 0, 0, FAKE, None)  # faces only
+    assert G._lib.grmhd_batch_prepare(boxes, 2, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None) == -1
+
+
 def test_autotuner_choice_logic_on_cpu():
     from paper_2210_17509_gb300 import autotune
     costs = {0: 1.0, 1: 1.0, 2: 1.0, 3: 1.0}

@@ -163,15 +163,17 @@ def test_batch_mixed_against_fp64_oracle(G):
 @pytest.mark.parametrize("curved", [False, True])
 @pytest.mark.parametrize("recon", ["weno5", "minmod"])
 def test_batch_two_pass_matches_single_pass(G, curved, recon):
-    """The FP64 batch in two passes (every face flux of every box once into
-    per-box face buffers, then a per-cell pass) against the single-pass batch:
-    the same bits, all four tile shapes present."""
+    """The FP64 batch in several passes against the single-pass batch: the
+    same bits, all four tile shapes present.  WENO5 runs three passes (every
+    box's face states into its state buffer, every face flux into its face
+    buffer, then the per-cell pass), minmod two (tiled faces, per-cell pass)."""
     p = G.Params(recon=G.WENO5 if recon == "weno5" else G.MINMOD, bc=G.BC_PERIODIC)
     out = []
     for two_pass in (True, False):
         boxes, _ = make_boxes(G, p, 12, seed=6, curved=curved)
         batch = G.Batch(boxes, p, two_pass=two_pass)
         assert batch.c.two_pass == (1 if two_pass else 0)
+        assert batch.c.three_pass == (1 if two_pass and recon == "weno5" else 0)
         batch.rhs(p)
         torch.cuda.synchronize()
         out.append([interior(b.rhs.cpu().numpy(), 3) for b in boxes])

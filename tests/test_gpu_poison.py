@@ -114,7 +114,7 @@ def test_ct_step_with_poisoned_workspace(G, precision):
         assert np.array_equal(a[inner], b[inner])
 
 
-def test_batch_with_poisoned_face_buffers(G):
+def test_batch_with_poisoned_face_and_state_buffers(G):
     p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC)
     shapes = I.amr_box_shapes(8, 3)
     out = []
@@ -129,8 +129,10 @@ def test_batch_with_poisoned_face_buffers(G):
             G.fill_ghosts(g, G.BC_PERIODIC, tp)
             tc = G.prim2con(g, p, tp)
             faces = fill(torch.empty((24,) + g.shape, dtype=torch.float64, device="cuda"), poison)
-            boxes.append(G.Box(g, tc, tp.clone(), torch.zeros_like(tp), None, b % 4, G.BC_PERIODIC, faces))
+            states = fill(torch.empty((48,) + g.shape, dtype=torch.float64, device="cuda"), poison)
+            boxes.append(G.Box(g, tc, tp.clone(), torch.zeros_like(tp), None, b % 4, G.BC_PERIODIC, faces, states))
         batch = G.Batch(boxes, p, two_pass=True)
+        assert batch.c.three_pass == 1
         batch.rhs(p)
         out.append([host(b.rhs)[:, 3:-3, 3:-3, 3:-3] for b in boxes])
     for a, b in zip(out[0], out[1]):
