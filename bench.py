@@ -1,8 +1,9 @@
 """Benchmark of the GRMHD method-of-lines hot path on GB300.
 
 One step = one full SSP-RK3 step of the 128^3 + 3-ghost Schwarzschild block
-(WENO5, HLLE, copy boundaries, CFL 0.25): three stages of fused RHS +
-stage update, con2prim and ghost fill.  Metric: zone-cycles/s =
+(WENO5, HLLE, copy boundaries, CFL 0.25): three stages of RHS with the stage
+update (FP64: face states, face fluxes, then the per-cell pass; mixed: one
+fused kernel), con2prim and ghost fill.  Metric: zone-cycles/s =
 steps * interior cells / time (the paper's definition, Sec. 5).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grmhd|reference]
