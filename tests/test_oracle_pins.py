@@ -631,6 +631,70 @@ def test_rk_conserves_totals_periodic():
         assert np.all(np.abs(tot - tot0) <= 1e-14 * scale), scheme
 
 
+def _rk_temporal_errors(schemes, steps):
+    """Max error of U(T) against the semi-discrete solution, on one fixed grid.
+
+    The spatial operator is the same for every run, so the difference from a
+    reference run at a much smaller step is the integrator's own error alone
+    (Sec. 2.3: the method of lines turns the PDE into an ODE system in time).
+    The reference is SSP-RK3 at 2560 steps, whose error (about 1e-11 here) is
+    far below the errors measured.  A wrong stage weight or stage time in any
+    of the three integrators either breaks its order or makes it converge to a
+    different ODE, and both show here."""
+    n = 32
+    g = O.Grid((n, 1, 1), 3, (1.0 / n,) * 3)
+    par = O.make_params(recon=O.REC_WENO5)
+    x = (np.arange(n + 6) - 3 + 0.5) / n
+    prim = np.zeros((8,) + g.shape)
+    prim[0] = 1 + 0.2 * np.sin(2 * np.pi * x)
+    prim[1] = 0.3 + 0.1 * np.cos(2 * np.pi * x)
+    prim[2] = 0.05 * np.sin(4 * np.pi * x)
+    prim[4] = 1.0 + 0.1 * np.cos(2 * np.pi * x)
+    prim[5] = 0.3
+    prim[6] = 0.2 * np.sin(2 * np.pi * x)
+    prim = O.fill_ghosts(g, O.BC_PERIODIC, prim)
+    cons0 = O.prim2con(g, par.gamma, prim)
+    T = 0.25
+
+    def run(scheme, nsteps):
+        c, p = cons0, prim
+        for _ in range(nsteps):
+            c, p, nf = O.rk_step(g, par, scheme, T / nsteps, c, p)
+            assert nf == 0
+        return c[:, 3, 3, 3:n + 3]
+
+    ref = run(O.RK3, 2560)
+    return {s: [np.max(np.abs(run(s, m) - ref)) for m in steps] for s in schemes}
+
+
+def test_rk_integrators_temporal_order():
+    """SSP-RK2 second order, SSP-RK3 third, classical RK4 fourth, all towards the
+    same semi-discrete solution (readings of the paper's RK2/RK4 and of RK3)."""
+    errs = _rk_temporal_errors((O.RK2, O.RK3, O.RK4), (20, 40, 80))
+    expect = {O.RK2: 2.0, O.RK3: 3.0, O.RK4: 4.0}
+    for s, e in errs.items():
+        orders = [math.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)]
+        assert all(abs(o - expect[s]) < 0.15 for o in orders), (s, e, orders)
+    # the error constants order as the schemes do at the same step
+    assert errs[O.RK4][0] < errs[O.RK3][0] < errs[O.RK2][0]
+
+
+@pytest.mark.parametrize("n", [(5, 3, 4), (7, 1, 2), (4, 6, 1)])
+def test_copy_boundary_is_nearest_interior_cell(n):
+    """Sec. 4.1's copy ("von Neumann") condition: every ghost point holds the
+    value of the nearest interior point, i.e. numpy's edge padding, corners
+    and edges included; periodic ghosts are numpy's wrap padding."""
+    ng = 3
+    g = O.Grid(n, ng, (1.0, 1.0, 1.0))
+    rng = np.random.default_rng(7)
+    core = rng.normal(size=(3, n[2], n[1], n[0]))
+    arr = np.full((3,) + g.shape, np.nan)
+    arr[(slice(None),) + g.interior()] = core
+    pad = ((0, 0), (ng, ng), (ng, ng), (ng, ng))
+    np.testing.assert_array_equal(O.fill_ghosts(g, O.BC_COPY, arr), np.pad(core, pad, mode="edge"))
+    np.testing.assert_array_equal(O.fill_ghosts(g, O.BC_PERIODIC, arr), np.pad(core, pad, mode="wrap"))
+
+
 def test_balsara1_peak_lorentz_factor_printed_in_paper():
     """Balsara 1 with the paper's setup at 400 points: peak W ~ 1.458 at t = 0.4."""
     gold = json.load(open(os.path.join(GOLDEN, "balsara_table.json")))
