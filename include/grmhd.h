@@ -363,14 +363,23 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
  * allocating routine (a host code whose device memory belongs to another
  * allocator or pool, a callback context where allocation is forbidden, a
  * binding without a device allocator).  Same arguments and results as
- * grmhd_rk_step minus ws/ws_bytes; the scratch is a file-scope device array
- * of GRMHD_STATIC_SCRATCH_BYTES held by every GPU on which this function is
- * first called, until the process exits.
+ * grmhd_rk_step minus ws/ws_bytes, with that step's workspace laid over a
+ * file-scope device array of GRMHD_STATIC_SCRATCH_BYTES.  The array is held
+ * on every GPU where this library's device code is loaded (under CUDA's
+ * default lazy module loading, from the library's first use there), until
+ * the process exits.
  *   Limit: grmhd_rk_workspace_bytes(grid, scheme) <= GRMHD_STATIC_SCRATCH_BYTES,
  *   i.e. ncell <= 1,048,576 for RK2/RK3 and about half that for RK4 (e.g. a
  *   94^3 interior with 3 ghosts); larger blocks return GRMHD_ERR_SIZE.
+ *   Paths: blocks whose grmhd_rk_workspace_bytes_cached fits in the array
+ *   (ncell <= 54,471 for RK2/RK3, 51,780 for RK4, e.g. a 31^3 interior with
+ *   3 ghosts) run the cached paths, larger ones the uncached paths; the
+ *   results are those of grmhd_rk_step given a workspace of that size.
+ *   GRMHD_REUSE_GEOMETRY is ignored: the geometry caches are rebuilt on
+ *   every call, since the array may hold another block's caches.
  *   The first call on a device (that device current) looks up the array's
- *   device address once; make that first call before any stream capture.
+ *   device address once; make that first call before any stream capture,
+ *   and do not use this function across a cudaDeviceReset.
  *   Every call shares the one array: calls that overlap on the GPU race.
  *   Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call. */
 int grmhd_rk_step_static(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,

@@ -10,14 +10,27 @@
 // this entry point supplies the scratch.
 //
 // The scratch is a file-scope __device__ array of GRMHD_STATIC_SCRATCH_BYTES
-// (64 MiB).  Every GPU on which this entry point is first used holds it until
-// the process exits.  Host code cannot use the array's name as a device
-// address, so on the first call on each device (that device current) the
-// address is looked up once with cudaGetSymbolAddress and cached; that first
-// call should therefore come before any stream capture.  The array is shared
-// by every call: overlapping calls on the GPU (different streams, no ordering
-// between them) race on it.  Nothing in it has to start at zero: the step
-// overwrites the U^n copy and the RK4 accumulator before reading them.
+// (64 MiB).  Every GPU on which this library's device code is loaded holds
+// it until the process exits (under CUDA's default lazy module loading, from
+// the first use of the library on that GPU).  Host code cannot use the
+// array's name as a device address, so on the first call on each device
+// (that device current) the address is looked up once with
+// cudaGetSymbolAddress and cached; that first call should therefore come
+// before any stream capture, and the cached address does not survive a
+// cudaDeviceReset (do not call this entry point across one).  The array is
+// shared by every call: overlapping calls on the GPU (different streams, no
+// ordering between them) race on it.
+//
+// The step lays the grmhd_rk_step workspace over the array, so blocks whose
+// cached workspace (grmhd_rk_workspace_bytes_cached) fits -- ncell <= 54,471
+// points for RK2/RK3, 51,780 for RK4, e.g. a 31^3 interior with 3 ghosts --
+// take the cached paths, and larger blocks up to the plain workspace size the
+// uncached ones, as grmhd_rk_step does with workspaces of those sizes.
+// Nothing in the array has to start at zero: the step overwrites the U^n
+// copy, the RK4 accumulator, the geometry caches and the RHS buffers before
+// reading them.  The caches are rebuilt on every call: GRMHD_REUSE_GEOMETRY
+// is cleared, because the array may hold another block's caches from the
+// previous call.
 #include <mutex>
 
 #include "internal.h"
@@ -52,8 +65,11 @@ extern "C" int grmhd_rk_step_static(const grmhd_grid* grid, const grmhd_params* 
   const size_t need = grmhd_rk_workspace_bytes(grid, scheme);
   if (need == 0) return GRMHD_ERR_ARG;
   if (need > kScratchBytes) return GRMHD_ERR_SIZE;
+  if (!params) return GRMHD_ERR_ARG;
   void* ws = nullptr;
   const int e = scratch_for_current_device(&ws);
   if (e != GRMHD_OK) return e;
-  return grmhd_rk_step(grid, params, scheme, dt, cons, prim, metric, kij, ws, kScratchBytes, nfail, stream);
+  grmhd_params p = *params;
+  p.flags &= ~GRMHD_REUSE_GEOMETRY;
+  return grmhd_rk_step(grid, &p, scheme, dt, cons, prim, metric, kij, ws, kScratchBytes, nfail, stream);
 }
