@@ -209,6 +209,19 @@ def riemann_schwarzschild(n=256, seed=4, ng=NG):
     return blk, riemann_prims(blk, seed), metric
 
 
+def window(blk: Block, arr, lo, m):
+    """The m^3 sub-block of blk whose interior starts at interior cell lo
+    (x, y, z), with ng ghost layers taken from arr's neighbouring points: its
+    Block (same spacing, shifted origin) and a copy of arr's values there."""
+    g = blk.ng
+    for d in range(3):
+        if not (0 <= lo[d] and lo[d] + m <= blk.n[d]):
+            raise ValueError("window outside the block interior")
+    wblk = Block((m, m, m), g, blk.dx, tuple(blk.origin[d] + lo[d] * blk.dx[d] for d in range(3)))
+    sl = (slice(None),) + tuple(slice(lo[d], lo[d] + m + 2 * g) for d in (2, 1, 0))
+    return wblk, np.ascontiguousarray(arr[sl])
+
+
 EDGES = (8, 16, 24, 32, 48, 64)
 
 

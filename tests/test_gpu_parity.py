@@ -329,8 +329,15 @@ def test_rk3_full_size_schwarzschild_step(G, precision, tol):
     CFL 0.25): one full step compared element by element with the oracle.'''
     blk, prim, met = I.smooth_schwarzschild(128, seed=1)
     c, p, co, po = _evolve_both(G, blk, prim, met, 1, 1, 3, 1, 0.25, precision=precision)
-    err = normwise(interior(c, 3), interior(co, 3))
+    c, co = interior(c, 3), interior(co, 3)
+    err = normwise(c, co)
     assert np.all(err < tol), err
+    # rho spans [1e-3, 1]: D and tau also cell by cell, relative to each cell's
+    # own value (floored at 1e-6 of the field's maximum)
+    for q in (0, 4):
+        s = np.maximum(np.abs(co[q]), 1e-6 * np.max(np.abs(co[q])))
+        cell = np.max(np.abs(c[q] - co[q]) / s)
+        assert cell < tol, (q, cell)
 
 
 def test_rk3_periodic_conserves_totals(G):
