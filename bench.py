@@ -1,10 +1,15 @@
 """Benchmark of the GRMHD method-of-lines hot path on GB300.
 
-One step = one full SSP-RK3 step of the 128^3 + 3-ghost Schwarzschild block
-(WENO5, HLLE, copy boundaries, CFL 0.25): three stages of RHS with the stage
-update (FP64: face states, face fluxes, then the per-cell pass; mixed: one
-fused kernel), con2prim and ghost fill.  Metric: zone-cycles/s =
-steps * interior cells / time (the paper's definition, Sec. 5).
+One step = one full SSP-RK3 step of the 256^3 + 3-ghost block on the
+Schwarzschild background (isotropic coordinates, M = 1, block [4, 12]^3)
+with a planar jump along x ((rho, P) = (1, 1) | (0.125, 0.1), B^x = 0.5,
+B^y flipping sign, 1% seeded perturbation), WENO5, HLLE, copy boundaries,
+CFL 0.25: three stages of RHS with the stage update (FP64: face states, face
+fluxes, then the per-cell pass; mixed: one fused kernel), con2prim and ghost
+fill.  Metric: zone-cycles/s = steps * interior cells / time (the paper's
+definition, Sec. 5).  The FP64 step is the headline `value`; the mixed step,
+the adjoint/forward cost ratio, the 128^3 smooth Schwarzschild block and the
+other sections are secondary keys.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grmhd|reference]
 
@@ -36,19 +41,27 @@ from paper_2210_17509_gb300 import inputs as I  # noqa: E402
 
 METRIC = "GRMHD zone-cycles/s (RHS+con2prim) FP64 vs mixed; adjoint/forward cost ratio"
 UNIT = "zone-cycles/s"
-N_CELLS_SIDE = 128
+N_HEADLINE = 256      # Riemann jump on the Schwarzschild background
+N_SMOOTH = 128        # smooth state on the Schwarzschild background
 CFL = 0.25
 PAPER_V100_SETUPA = 0.47e8   # zone-cycles/s, 240^3, RK2, one V100 (Sec. 5.1) -- context only
+WINDOW_LO = (104, 104, 104)  # a 48^3 window of the 256^3 block straddling the jump
 
 
-def workload_config(n=N_CELLS_SIDE):
+def workload_config(n=N_HEADLINE):
     return {
-        "workload": f"schwarzschild-block-{n}^3+3ghost-weno5-hlle-ssprk3",
+        "workload": f"riemann-schwarzschild-{n}^3+3ghost-weno5-hlle-ssprk3",
         "block": [n, n, n], "ghosts": 3, "spacetime": "Schwarzschild isotropic M=1, block [4,12]^3",
+        "initial_data": "planar jump along x: (rho, P) = (1, 1) | (0.125, 0.1), B^x = 0.5, B^y = +1 | -1, "
+                        "1% seeded perturbation of rho and P",
         "recon": "WENO5", "riemann": "HLLE", "integrator": "SSP-RK3", "cfl": CFL, "bc": "copy",
-        "gamma": I.GAMMA, "l2": "inputs larger than L2 (prim+cons+metric ~ 500 MB per block)",
+        "gamma": I.GAMMA, "l2": f"inputs larger than L2 (prim+cons+metric ~ {26 * 8 * (n + 6) ** 3 / 1e9:.1f} GB)",
         "geometry_cache": "static metric: geometry caches built once (first step), reused (GRMHD_REUSE_GEOMETRY)",
     }
+
+
+def headline_state(n=N_HEADLINE, seed=4):
+    return I.riemann_schwarzschild(n, seed=seed)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -121,14 +134,14 @@ def run_reference(args):
     O.build()
     nthreads = os.cpu_count() or 1
     O.set_threads(nthreads)
-    blk, prim, met = I.smooth_schwarzschild(N_CELLS_SIDE, seed=1)
-    # bounded sample: a 24^3 sub-block (cells [52, 76)^3 of the full block, with ghosts)
+    blk, prim, met = headline_state(args.n)
+    # bounded sample: a 24^3 window of the block straddling the jump, its
+    # ghosts by the copy condition
     sub = 24
-    lo = 52
-    sl = (slice(None),) + tuple(slice(lo, lo + sub + 6) for _ in range(3))
-    sblk = I.Block((sub,) * 3, 3, blk.dx, tuple(blk.origin[d] + (lo - 3 + 3) * blk.dx[d] for d in range(3)))
-    sprim = np.ascontiguousarray(prim[sl])
-    smet = np.ascontiguousarray(met[sl])
+    lo = tuple(v // 2 - sub // 2 for v in blk.n)
+    sblk, sprim = I.window(blk, prim, lo, sub)
+    smet = I.window(blk, met, lo, sub)[1]
+    del prim, met
     g = O.Grid(sblk.n, 3, sblk.dx)
     par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY)
     sprim = O.fill_ghosts(g, O.BC_COPY, sprim)
@@ -141,56 +154,92 @@ def run_reference(args):
         cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)
     t = time.perf_counter() - t0
     value = args.steps * sblk.ncells / t
-    sample = (f"{args.steps} SSP-RK3 steps of a {sub}^3 sub-block of the {N_CELLS_SIDE}^3 Schwarzschild "
-              f"workload (same cells, metric, WENO5/HLLE/copy BC), oracle with {nthreads} OpenMP threads")
+    sample = (f"{args.steps} SSP-RK3 steps of a {sub}^3 window (interior cells {lo} ..) of the {args.n}^3 "
+              f"Riemann-on-Schwarzschild workload straddling the jump (same cells, metric, WENO5/HLLE/copy BC), "
+              f"oracle with {nthreads} OpenMP threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(),
+        "data": "synthetic", "config": workload_config(args.n),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(G, seconds_target=15.0):
-    """Oracle throughput on a bounded sample (about 10-30 s of CPU work).
-    Its first step also gives the accuracy report: the max relative error of
-    every conserved field of the FP64 and the mixed GPU paths against the
-    FP64 oracle after one SSP-RK3 step of the same sample."""
+FIELDS = ["D", "S_x", "S_y", "S_z", "tau", "B^x", "B^y", "B^z"]
+
+
+def _errors(c, ref):
+    """Per-field max |c - ref| / max |ref| (normwise), the same with vector
+    components against their vector's largest length, and the cell-wise
+    relative error of D and tau (floored at 1e-6 of the field's maximum)."""
+    norm = [float(np.abs(c[q] - ref[q]).max() / np.abs(ref[q]).max()) for q in range(8)]
+    vl = [np.sqrt((ref[sl] ** 2).sum(axis=0)).max() for sl in (slice(1, 4), slice(5, 8))]
+    scale = [np.abs(ref[0]).max()] + [vl[0]] * 3 + [np.abs(ref[4]).max()] + [vl[1]] * 3
+    vec = [float(np.abs(c[q] - ref[q]).max() / scale[q]) for q in range(8)]
+    cell = {}
+    for q in (0, 4):
+        fl = np.maximum(np.abs(ref[q]), 1e-6 * np.abs(ref[q]).max())
+        cell[FIELDS[q]] = float((np.abs(c[q] - ref[q]) / fl).max())
+    return {"max_rel_err_per_field": norm, "max": max(norm), "vector_scaled_per_field": vec,
+            "vector_scaled_max": max(vec), "cellwise_rel_D_tau": cell}
+
+
+def _accuracy(G, O, blk, prim, met, lo, sub, steps=1):
+    """One window of a workload stepped by the oracle and by the GPU's FP64
+    and mixed paths; returns the oracle's (grid, params, cons, prim, metric,
+    dt) for timing and the error report."""
     import torch
-    import oracle as O
-    O.build()
-    nthreads = os.cpu_count() or 1
-    O.set_threads(nthreads)
-    blk, prim, met = I.smooth_schwarzschild(N_CELLS_SIDE, seed=1)
-    sub, lo = 48, 40
-    sl = (slice(None),) + tuple(slice(lo, lo + sub + 6) for _ in range(3))
-    sblk = I.Block((sub,) * 3, 3, blk.dx, blk.origin)
-    sprim = np.ascontiguousarray(prim[sl])
-    smet = np.ascontiguousarray(met[sl])
+    sblk, sprim = I.window(blk, prim, lo, sub)
+    smet = I.window(blk, met, lo, sub)[1]
     g = O.Grid(sblk.n, 3, sblk.dx)
     gp = G.Params(recon=G.WENO5, bc=G.BC_COPY)
     par = O.make_params(recon=O.REC_WENO5, bc=O.BC_COPY, rho_atm=gp.rho_atm, p_atm=gp.p_atm, weno_eps=gp.weno_eps)
     sprim = O.fill_ghosts(g, O.BC_COPY, sprim)
     cons = O.prim2con(g, par.gamma, sprim, smet)
     dt = CFL * min(sblk.dx)
-    cons0, prim0 = cons, sprim
-    cons, sprim, _ = O.rk_step(g, par, O.RK3, dt, cons, sprim, smet)     # warm-up, and the reference step
+    c1, p1, nf = cons, sprim, 0
+    for _ in range(steps):
+        c1, p1, k = O.rk_step(g, par, O.RK3, dt, c1, p1, smet)
+        nf += k
     gg = G.Grid(sblk.n, 3, sblk.dx)
     inner = (slice(None),) + tuple(slice(3, -3) for _ in range(3))
-    accuracy = {"sample": f"one SSP-RK3 step of the {sub}^3 sub-block",
-                "fields": ["D", "S_x", "S_y", "S_z", "tau", "B^x", "B^y", "B^z"]}
+    acc = {"sample": f"{steps} SSP-RK3 step(s) of the {sub}^3 window at interior cells {tuple(lo)}",
+           "fields": FIELDS, "oracle_failed_cells": nf}
     for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
-        tc = torch.from_numpy(cons0).cuda()
-        tp = torch.from_numpy(prim0).cuda()
-        G.rk_step(gg, dataclasses.replace(gp, precision=prec), G.RK3, dt, tc, tp, torch.from_numpy(smet).cuda(),
-                  None, G.workspace(gg, G.RK3))
-        c = tc.cpu().numpy()[inner]
-        ref = cons[inner]
-        err = [float(np.abs(c[q] - ref[q]).max() / np.abs(ref[q]).max()) for q in range(8)]
-        accuracy[name] = {"max_rel_err_per_field": err, "max": max(err)}
+        tc = torch.from_numpy(cons).cuda()
+        tp = torch.from_numpy(sprim).cuda()
+        tm = torch.from_numpy(smet).cuda()
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ws = G.workspace(gg, G.RK3)
+        for _ in range(steps):
+            G.rk_step(gg, dataclasses.replace(gp, precision=prec), G.RK3, dt, tc, tp, tm, None, ws, nfail)
+        acc[name] = _errors(tc.cpu().numpy()[inner], c1[inner])
+        acc[name]["failed_cells"] = int(nfail.item())
+    return (g, par, c1, p1, smet, dt, sblk), acc
+
+
+def cpu_baseline_sample(G, n=N_HEADLINE, seconds_target=15.0):
+    """Oracle throughput on a bounded sample (about 10-30 s of CPU work): a
+    48^3 window of the headline block straddling the jump.  The same window
+    gives the accuracy report: the errors of every conserved field of the
+    FP64 and the mixed GPU paths against the FP64 oracle after two SSP-RK3
+    steps; a 48^3 window of the smooth 128^3 Schwarzschild block (densities
+    1e-3 .. 1) gives the same report for that workload."""
+    import oracle as O
+    O.build()
+    nthreads = os.cpu_count() or 1
+    O.set_threads(nthreads)
+    blk, prim, met = headline_state(n)
+    og = O.Grid(blk.n, 3, blk.dx)
+    lo = tuple(v // 2 - 24 for v in blk.n)
+    (g, par, cons, sprim, smet, dt, sblk), acc = _accuracy(G, O, blk, prim, met, lo, 48, steps=2)
+    del prim, met, og
+    sblk2, prim2, met2 = I.smooth_schwarzschild(N_SMOOTH, seed=1)
+    _, acc128 = _accuracy(G, O, sblk2, prim2, met2, (40, 40, 40), 48, steps=2)
+    del prim2, met2
     steps, t = 0, 0.0
     t0 = time.perf_counter()
     while t < seconds_target and steps < 400:
@@ -199,9 +248,10 @@ def cpu_baseline_sample(G, seconds_target=15.0):
         t = time.perf_counter() - t0
     return {
         "value": steps * sblk.ncells / t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-        "sample": f"{steps} SSP-RK3 steps of a {sub}^3 sub-block of the same Schwarzschild workload "
-                  f"({t:.1f} s of CPU work, {nthreads} OpenMP threads)",
-        "accuracy_vs_oracle": accuracy,
+        "sample": f"{steps} SSP-RK3 steps of a 48^3 window of the {n}^3 Riemann-on-Schwarzschild workload "
+                  f"straddling the jump ({t:.1f} s of CPU work, {nthreads} OpenMP threads)",
+        "accuracy_vs_oracle": acc,
+        "accuracy_vs_oracle_smooth_128": acc128,
     }
 
 
@@ -507,12 +557,12 @@ def amr_bench(G, steps=5, warmup=2, nc=96, nfine=48):
 
 
 # ------------------------------------------------- constrained transport --
-def ct_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE):
+def ct_bench(G, steps=5, warmup=2, n=N_SMOOTH):
     """Constrained transport (Sec. 3: the field on staggered grids): the
-    headline 128^3 Schwarzschild block with a divergence-free face field (the
+    smooth 128^3 Schwarzschild block with a divergence-free face field (the
     discrete curl of a random edge potential, |sqrt(gamma) B| <= 0.03, so
     b^2/rho <= 0.2 on the density floor of 1e-3; cell field = mean of the
-    faces), WENO5+HLLE, SSP-RK3 at the headline dt, FP64 and mixed.  Timed
+    faces), WENO5+HLLE, SSP-RK3 at CFL 0.25, FP64 and mixed.  Timed
     against plain steps of the same state; the largest |div B| after the
     timed steps is reported relative to max |B| / dx.  (At |B| <= 0.1 the
     cells with plasma beta ~ 2e-3 fall to the atmosphere under CT, in the
@@ -527,7 +577,7 @@ def ct_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE):
     g = G.Grid(blk.n, blk.ng, blk.dx)
     met = torch.from_numpy(met_h).cuda()
     dt = CFL * min(blk.dx)
-    out = {"workload": f"{n}^3 Schwarzschild block (headline state) with a divergence-free face field "
+    out = {"workload": f"{n}^3 smooth Schwarzschild block with a divergence-free face field "
                        f"(|sqrt(gamma) B| <= 0.03), "
                        f"WENO5+HLLE, SSP-RK3, dt = {CFL} dx, copy boundaries"}
     for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
@@ -571,12 +621,12 @@ def ct_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE):
 
 
 # ------------------------------------------------------ polytropic EOS --
-def poly_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE, K=100.0, gamma=2.0):
+def poly_bench(G, steps=5, warmup=2, n=N_SMOOTH, K=100.0, gamma=2.0):
     """Polytropic EOS (Sec. 2.3; K = 100, Gamma = 2 as the paper's TOV star,
-    Sec. 4.4): the headline 128^3 Schwarzschild block with a smooth state of
+    Sec. 4.4): the 128^3 Schwarzschild block with a smooth state of
     density 1e-4 .. 1.28e-3 (the TOV central density), P = K rho^Gamma,
     |v| <= 0.5 and a weak field (|B| <= 1e-3), WENO5+HLLE, SSP-RK3 at the
-    headline dt, copy boundaries; FP64 and mixed."""
+    CFL 0.25, copy boundaries; FP64 and mixed."""
     import torch
     blk = I.Block((n,) * 3, 3, (8.0 / n,) * 3, (4.0,) * 3)
     met_h = I.schwarzschild_metric(blk)
@@ -611,88 +661,202 @@ def poly_bench(G, steps=5, warmup=2, n=N_CELLS_SIDE, K=100.0, gamma=2.0):
     return out
 
 
-# ------------------------------------------------------------ 256^3 block --
-def large_block_bench(G, steps=3, warmup=1, n=256):
-    """256^3 + 3 ghosts on the Schwarzschild background, planar Riemann jump
-    along x with 1% perturbation, WENO5+HLLE, SSP-RK3: FP64, mixed and the
-    adjoint step, each with its HBM fraction against the per-kernel
-    algorithmic byte floor (512 B per cell per stage)."""
+# ------------------------------------------------------------------- GPU --
+def _timer():
     import torch
-    blk, prim_h, met_h = I.riemann_schwarzschild(n, seed=4)
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def block_state(G, blk, prim_h, met, precision, tile=0):
+    import torch
     g = G.Grid(blk.n, blk.ng, blk.dx)
+    p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision, tile=tile)
+    prim = torch.from_numpy(prim_h).cuda()
+    G.fill_ghosts(g, G.BC_COPY, prim)
+    cons = G.prim2con(g, p, prim, met)
+    ws = G.workspace(g, G.RK3)
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return g, p, prim, cons, ws, nfail
+
+
+def time_steps(G, REP, blk, prim_h, met, precision, steps, warmup, tile=0, clocks=None):
+    """warmup + steps SSP-RK3 steps of one block; the timed ones bracketed by a
+    barrier and a synchronize on both sides, on the stream they run on.
+    Returns (ms over the timed steps, max over ranks; failed cells; state)."""
+    import torch
+    g, p, prim, cons, ws, nfail = block_state(G, blk, prim_h, met, precision, tile)
     dt = CFL * min(blk.dx)
-    met = torch.from_numpy(met_h).cuda()
-    from paper_2210_17509_gb300 import roofline as R
-    hbm, _ = R.hbm_peak_gbs()
-    out = {"workload": f"Riemann jump on Schwarzschild, {n}^3+3 ghosts, WENO5+HLLE, SSP-RK3, copy BC"}
+    for _ in range(warmup):
+        G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+        # static metric: the geometry cache built by the first step is kept
+        p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
+    torch.cuda.synchronize()
+    REP.barrier()
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = _timer()
+    e0.record(stream)
+    for _ in range(steps):
+        G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    REP.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    ms = REP.max_over_ranks(e0.elapsed_time(e1))
+    return ms, int(nfail.item()), clk, (g, p, prim, cons, ws, nfail, dt)
+
+
+def adjoint_step_ratio(G, g, p, prim, cons, met, ws, dt, ms_step):
+    """Reverse of one SSP-RK3 step from recorded stages (the checkpointed
+    backward's unit of work) against the forward FP64 step."""
+    import torch
+    stages = torch.empty((3, 8) + g.shape, dtype=torch.float64, device="cuda")
+    c0, p0 = cons.clone(), prim.clone()
+    G.rk_step_record(g, p, G.RK3, dt, cons, prim, stages, met, None, ws)
+    wsa = G.adjoint_workspace(g, G.RK3)
+    ub = torch.zeros_like(cons)
+    pb = torch.zeros_like(prim)
+    pb[0] = 1.0
+    gb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
+    torch.cuda.synchronize()
+    e0, e1 = _timer()
+    e0.record()
+    G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
+    e1.record()
+    torch.cuda.synchronize()
+    ams = e0.elapsed_time(e1)
+    return {"ms": ams, "ratio_to_fp64_step": ams / ms_step,
+            "value": blk_cells(g) / (ams * 1e-3),
+            "unit": "zone-cycles/s (reverse step, recorded stages)"}
+
+
+def blk_cells(g):
+    return g.n[0] * g.n[1] * g.n[2]
+
+
+def e2e_bench(G, REP, blk, prim_h, met, steps_e):
+    """End to end through the public API with host buffers: every step uploads
+    its inputs (U, primitives, metric) from pinned host memory, runs
+    grmhd_rk_step and downloads its result (U, primitives).  Two device
+    buffer sets let step k + 1's upload and step k - 1's download run on
+    copy streams while step k computes (a user streaming steps would do the
+    same); the serial figure (copies, then compute, then copies) is kept too."""
+    import torch
+    g, p, prim_d, cons_d, ws_e, nfail_e = block_state(G, blk, prim_h, met, G.FP64)
+    dt = CFL * min(blk.dx)
+    cons_h = cons_d.cpu().pin_memory()
+    prim_h2 = prim_d.cpu().pin_memory()
+    met_hp = met.cpu().pin_memory()
+    del prim_d, cons_d
+    bufs = []
+    for _ in range(2):
+        bufs.append({"cons": torch.empty_like(cons_h, device="cuda"), "prim": torch.empty_like(prim_h2, device="cuda"),
+                     "met": torch.empty_like(met), "out_c": torch.empty_like(cons_h).pin_memory(),
+                     "out_p": torch.empty_like(prim_h2).pin_memory()})
+    s_comp = torch.cuda.current_stream()
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("up", "done", "down")}
+
+    def serial_step(b):
+        b["cons"].copy_(cons_h, non_blocking=True)
+        b["prim"].copy_(prim_h2, non_blocking=True)
+        b["met"].copy_(met_hp, non_blocking=True)
+        G.rk_step(g, p, G.RK3, dt, b["cons"], b["prim"], b["met"], None, ws_e, nfail_e)
+        b["out_c"].copy_(b["cons"], non_blocking=True)
+        b["out_p"].copy_(b["prim"], non_blocking=True)
+
+    def pipelined(n):
+        # uploads and downloads on streams of their own, so that step k + 1's
+        # upload is not queued behind step k's download
+        for k in range(n):
+            i = k % 2
+            b = bufs[i]
+            with torch.cuda.stream(s_up):
+                if k >= 2:
+                    s_up.wait_event(ev["down"][i])
+                b["cons"].copy_(cons_h, non_blocking=True)
+                b["prim"].copy_(prim_h2, non_blocking=True)
+                b["met"].copy_(met_hp, non_blocking=True)
+                ev["up"][i].record(s_up)
+            s_comp.wait_event(ev["up"][i])
+            G.rk_step(g, p, G.RK3, dt, b["cons"], b["prim"], b["met"], None, ws_e, nfail_e, stream=s_comp)
+            ev["done"][i].record(s_comp)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(ev["done"][i])
+                b["out_c"].copy_(b["cons"], non_blocking=True)
+                b["out_p"].copy_(b["prim"], non_blocking=True)
+                ev["down"][i].record(s_down)
+        s_comp.wait_stream(s_up)
+        s_comp.wait_stream(s_down)
+
+    def timed_e2e(fn):
+        torch.cuda.synchronize()
+        REP.barrier()
+        q0, q1 = _timer()
+        q0.record(s_comp)
+        fn()
+        q1.record(s_comp)
+        torch.cuda.synchronize()
+        REP.barrier()
+        return REP.max_over_ranks(q0.elapsed_time(q1))
+
+    serial_step(bufs[0])
+    pipelined(2)
+    ems_serial = timed_e2e(lambda: [serial_step(bufs[0]) for _ in range(steps_e)])
+    ems = timed_e2e(lambda: pipelined(steps_e))
+    h2d = cons_h.numel() * 8 + prim_h2.numel() * 8 + met_hp.numel() * 8
+    d2h = bufs[0]["out_c"].numel() * 8 + bufs[0]["out_p"].numel() * 8
     ncells = blk.ncells
-    for precision, name in ((G.FP64, "fp64"), (G.MIXED, "mixed")):
-        p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision)
-        prim = torch.from_numpy(prim_h).cuda()
-        G.fill_ghosts(g, G.BC_COPY, prim)
-        cons = G.prim2con(g, p, prim, met)
-        ws = G.workspace(g, G.RK3)
-        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
-        for _ in range(warmup):
-            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
-            p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        zc = ncells / (ms * 1e-3)
-        out[name] = {"value": zc, "unit": UNIT, "ms_per_step": ms, "failed_cells": int(nfail.item()),
-                     "hbm_frac_512B_floor": 512.0 * 3 * zc / (hbm * 1e9)}
-        if precision == G.FP64:
-            # adjoint of one step from recorded stages (the checkpointed backward's unit of work)
-            stages = torch.empty((3, 8) + g.shape, dtype=torch.float64, device="cuda")
-            c0, p0 = cons.clone(), prim.clone()
-            G.rk_step_record(g, p, G.RK3, dt, cons, prim, stages, met, None, ws)
-            wsa = G.adjoint_workspace(g, G.RK3)
-            ub = torch.zeros_like(cons)
-            pb = torch.zeros_like(prim)
-            pb[0] = 1.0
-            gb = torch.zeros(1, dtype=torch.float64, device="cuda")
-            G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
-            torch.cuda.synchronize()
-            e0.record()
-            G.rk_step_adjoint(g, p, G.RK3, dt, c0, p0, ub, pb, gb, met, None, wsa, stage_prims=stages)
-            e1.record()
-            torch.cuda.synchronize()
-            ams = e0.elapsed_time(e1)
-            out["adjoint_step"] = {"ms": ams, "ratio_to_fp64_step": ams / ms, "value": ncells / (ams * 1e-3),
-                                   "unit": "zone-cycles/s (reverse step, recorded stages)"}
-            del stages, wsa, ub, pb, c0, p0
-        del prim, cons, ws
+    return {"value": REP.job_rate(ncells * steps_e, ems), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "dtype": "f64", "steps": steps_e,
+            "copies": "overlapped with the neighbouring steps' compute (two device buffer sets, upload and "
+                      "download streams)",
+            "serial_value": REP.job_rate(ncells * steps_e, ems_serial)}
+
+
+def smooth_block_bench(G, REP, steps, warmup, n=N_SMOOTH):
+    """The smooth 128^3 Schwarzschild block (densities 1e-3 .. 1, |v| <= 0.5,
+    |B| <= 0.1, WENO5+HLLE, SSP-RK3, CFL 0.25, copy BC), FP64 and mixed."""
+    import torch
+    from paper_2210_17509_gb300 import autotune
+    blk, prim_h, met_h = I.smooth_schwarzschild(n, seed=1)
+    met = torch.from_numpy(met_h).cuda()
+    tile = autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n, curved=True)
+    out = {"workload": f"schwarzschild-block-{n}^3+3ghost-weno5-hlle-ssprk3 (smooth, rho 1e-3..1)"}
+    for precision, name, t in ((G.FP64, "fp64", 0), (G.MIXED, "mixed", tile)):
+        ms, nf, _, st = time_steps(G, REP, blk, prim_h, met, precision, steps, warmup, tile=t)
+        out[name] = {"value": REP.job_rate(blk.ncells * steps, ms), "unit": UNIT, "ms_per_step": ms / steps,
+                     "failed_cells": nf}
+        del st
         torch.cuda.empty_cache()
+    out["mixed"]["tile"] = autotune.BLOCK_SHAPES[tile]
+    out["mixed_speedup"] = out["mixed"]["value"] / out["fp64"]["value"]
     return out
 
 
-# ------------------------------------------------------------------- GPU --
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
-    ap.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    ap.add_argument("--n", type=int, default=N_HEADLINE)
+    ap.add_argument("--smooth-n", type=int, default=N_SMOOTH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-smooth", action="store_true")
     ap.add_argument("--no-shocktube", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-ct", action="store_true")
     ap.add_argument("--no-poly", action="store_true")
-    ap.add_argument("--section", default=None, choices=["ct", "poly", "amr", "shocktube", "batched", "adjoint", "large"],
+    ap.add_argument("--section", default=None,
+                    choices=["ct", "poly", "amr", "shocktube", "batched", "adjoint", "smooth"],
                     help="run only this section and print its JSON (profiling runs)")
-    ap.add_argument("--tile", type=int, default=-1, help="RHS tile shape (default: autotuned)")
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-dirs", type=int, default=50)
     args = ap.parse_args()
@@ -708,64 +872,24 @@ def main():
     world, rank = REP.world, REP.rank
 
     from paper_2210_17509_gb300 import grmhd as G
+    from paper_2210_17509_gb300 import roofline as R
 
     if args.section:
-        fns = {"ct": lambda: ct_bench(G, n=args.n), "poly": lambda: poly_bench(G, n=args.n), "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
+        fns = {"ct": lambda: ct_bench(G, n=args.smooth_n), "poly": lambda: poly_bench(G, n=args.smooth_n),
+               "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
                "batched": lambda: batched_bench(G, args.steps, args.warmup),
                "adjoint": lambda: adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs),
-               "large": lambda: large_block_bench(G)}
+               "smooth": lambda: smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n)}
         out = fns[args.section]()
         if rank == 0:
             print(json.dumps({"section": args.section, args.section: out}), flush=True)
         return
 
-    def barrier():
-        REP.barrier()
-
-    blk, prim_h, met_h = I.smooth_schwarzschild(args.n, seed=1 + rank)
-    g = G.Grid(blk.n, blk.ng, blk.dx)
-    dt = CFL * min(blk.dx)
+    blk, prim_h, met_h = headline_state(args.n, seed=4 + rank)
     met = torch.from_numpy(met_h).cuda()
-    stream = torch.cuda.current_stream()
-
-    # tile shape of the single block from the project's autotuner (per precision)
-    from paper_2210_17509_gb300 import autotune
-    # (the FP64 RHS of the cached step runs in three passes, without tiles,
-    # whatever the tile parameter says; the mixed RHS takes the tuned shape)
-    if args.tile >= 0:
-        tiles = {G.FP64: args.tile, G.MIXED: args.tile}
-    else:
-        tiles = {G.FP64: 0,
-                 G.MIXED: autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n,
-                                                    curved=True)}
-
-    def setup(precision):
-        p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision, tile=tiles[precision])
-        prim = torch.from_numpy(prim_h).cuda()
-        G.fill_ghosts(g, G.BC_COPY, prim)
-        cons = G.prim2con(g, p, prim, met)
-        ws = G.workspace(g, G.RK3)
-        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
-        return p, prim, cons, ws, nfail
-
-    def timed(precision, steps, warmup):
-        p, prim, cons, ws, nfail = setup(precision)
-        for i in range(warmup):
-            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
-            # static metric: the geometry cache built by the first step is kept
-            p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
-        torch.cuda.synchronize()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            G.rk_step(g, p, G.RK3, dt, cons, prim, met, None, ws, nfail)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms = REP.max_over_ranks(e0.elapsed_time(e1))
-        return ms, int(nfail.item())
+    del met_h
+    ncells = blk.ncells
+    hbm, hbm_src = R.hbm_peak_gbs()
 
     uuid = None
     try:
@@ -774,143 +898,66 @@ def main():
             uuid = "GPU-" + uuid
     except Exception:
         uuid = None
-    clocks = ClockSampler(uuid)
     # FP64 (headline) -- clocks sampled during this timed region
-    p64, prim, cons, ws, nfail = setup(G.FP64)
-    for _ in range(args.warmup):
-        G.rk_step(g, p64, G.RK3, dt, cons, prim, met, None, ws, nfail)
-        p64 = dataclasses.replace(p64, flags=G.REUSE_GEOMETRY)
-    torch.cuda.synchronize()
-    barrier()
-    clocks.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        G.rk_step(g, p64, G.RK3, dt, cons, prim, met, None, ws, nfail)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms64 = REP.max_over_ranks(e0.elapsed_time(e1))
-    nfail64 = int(nfail.item())
-    ncells = blk.ncells
+    ms64, nfail64, clk, st = time_steps(G, REP, blk, prim_h, met, G.FP64, args.steps, args.warmup,
+                                        clocks=ClockSampler(uuid))
     value64 = REP.job_rate(ncells * args.steps, ms64)
+    # adjoint of one step against the forward step, on the same state
+    g, p64, prim, cons, ws, _, dt = st
+    adj_step = None
+    if not args.no_adjoint:
+        adj_step = adjoint_step_ratio(G, g, p64, prim, cons, met, ws, dt, ms64 / args.steps)
+    del st, prim, cons, ws
+    torch.cuda.empty_cache()
 
-    # mixed precision path
-    msmx, nfailmx = timed(G.MIXED, args.steps, args.warmup)
+    # mixed precision path, on the RHS tile shape the project's autotuner picks
+    from paper_2210_17509_gb300 import autotune
+    tile_mx = autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n,
+                                        curved=True)
+    msmx, nfailmx, _, st = time_steps(G, REP, blk, prim_h, met, G.MIXED, args.steps, args.warmup, tile=tile_mx)
     value_mx = REP.job_rate(ncells * args.steps, msmx)
+    del st
+    torch.cuda.empty_cache()
 
-    # dominant kernel: the fused FP64 RHS, timed live with events on its stream
-    # (the RK step's RHS reads the FP64 geometry cache of the static metric,
-    # so the same kernel is timed here through grmhd_rhs_cached)
-    p, prim_k, cons_k, _, _ = setup(G.FP64)
+    # dominant kernel: the FP64 RHS (states, faces, cells), timed live with
+    # events on its stream through grmhd_rhs_cached, which runs the same
+    # kernels on the same FP64 geometry cache as the step
+    g, p, prim_k, _, _, _ = block_state(G, blk, prim_h, met, G.FP64)
     rhs_out = torch.empty_like(prim_k)
     rws = G.rhs_workspace(g)
     G.rhs_cached(g, p, prim_k, met, None, rhs_out, rws)
     p = dataclasses.replace(p, flags=G.REUSE_GEOMETRY)
     for _ in range(3):
         G.rhs_cached(g, p, prim_k, met, None, rhs_out, rws)
+    stream = torch.cuda.current_stream()
     nk = max(5, args.steps)
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
+    k0, k1 = _timer()
     k0.record(stream)
     for _ in range(nk):
         G.rhs_cached(g, p, prim_k, met, None, rhs_out, rws)
     k1.record(stream)
     torch.cuda.synchronize()
     rhs_ms = k0.elapsed_time(k1) / nk
-    from paper_2210_17509_gb300 import roofline as R
     roof = R.rhs_fp64_roofline(ncells, rhs_ms)
+    del prim_k, rhs_out, rws
+    torch.cuda.empty_cache()
 
-    # end to end through the public API with host buffers: every step uploads
-    # its inputs (U, primitives, metric) from pinned host memory, runs
-    # grmhd_rk_step and downloads its result (U, primitives).  Two device
-    # buffer sets let step k + 1's upload and step k - 1's download run on
-    # copy streams while step k computes (a user streaming steps would do the
-    # same); the serial figure (copies, then compute, then copies) is kept too.
     e2e = None
     if not args.no_e2e:
-        p, prim_d, cons_d, ws_e, nfail_e = setup(G.FP64)
-        cons_h = cons_d.cpu().pin_memory()
-        prim_h2 = prim_d.cpu().pin_memory()
-        met_hp = met.cpu().pin_memory()
-        steps_e = max(3, args.steps // 2)
-        bufs = []
-        for _ in range(2):
-            bufs.append({"cons": torch.empty_like(cons_d), "prim": torch.empty_like(prim_d),
-                         "met": torch.empty_like(met), "out_c": torch.empty_like(cons_h).pin_memory(),
-                         "out_p": torch.empty_like(prim_h2).pin_memory()})
-        s_comp = stream
-        s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
-        ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("up", "done", "down")}
+        e2e = e2e_bench(G, REP, blk, prim_h, met, max(3, args.steps // 2))
+        torch.cuda.empty_cache()
+    del met, prim_h
+    torch.cuda.empty_cache()
 
-        def serial_step(b):
-            b["cons"].copy_(cons_h, non_blocking=True)
-            b["prim"].copy_(prim_h2, non_blocking=True)
-            b["met"].copy_(met_hp, non_blocking=True)
-            G.rk_step(g, p, G.RK3, dt, b["cons"], b["prim"], b["met"], None, ws_e, nfail_e)
-            b["out_c"].copy_(b["cons"], non_blocking=True)
-            b["out_p"].copy_(b["prim"], non_blocking=True)
-
-        def pipelined(n):
-            # uploads and downloads on streams of their own, so that step
-            # k + 1's upload is not queued behind step k's download
-            for k in range(n):
-                i = k % 2
-                b = bufs[i]
-                with torch.cuda.stream(s_up):
-                    if k >= 2:
-                        s_up.wait_event(ev["down"][i])
-                    b["cons"].copy_(cons_h, non_blocking=True)
-                    b["prim"].copy_(prim_h2, non_blocking=True)
-                    b["met"].copy_(met_hp, non_blocking=True)
-                    ev["up"][i].record(s_up)
-                s_comp.wait_event(ev["up"][i])
-                G.rk_step(g, p, G.RK3, dt, b["cons"], b["prim"], b["met"], None, ws_e, nfail_e, stream=s_comp)
-                ev["done"][i].record(s_comp)
-                with torch.cuda.stream(s_down):
-                    s_down.wait_event(ev["done"][i])
-                    b["out_c"].copy_(b["cons"], non_blocking=True)
-                    b["out_p"].copy_(b["prim"], non_blocking=True)
-                    ev["down"][i].record(s_down)
-            s_comp.wait_stream(s_up)
-            s_comp.wait_stream(s_down)
-
-        def timed_e2e(fn):
-            torch.cuda.synchronize()
-            barrier()
-            q0 = torch.cuda.Event(enable_timing=True)
-            q1 = torch.cuda.Event(enable_timing=True)
-            q0.record(s_comp)
-            fn()
-            q1.record(s_comp)
-            torch.cuda.synchronize()
-            barrier()
-            return REP.max_over_ranks(q0.elapsed_time(q1))
-
-        serial_step(bufs[0])
-        pipelined(2)
-        ems_serial = timed_e2e(lambda: [serial_step(bufs[0]) for _ in range(steps_e)])
-        ems = timed_e2e(lambda: pipelined(steps_e))
-        h2d = cons_h.numel() * 8 + prim_h2.numel() * 8 + met_hp.numel() * 8
-        d2h = bufs[0]["out_c"].numel() * 8 + bufs[0]["out_p"].numel() * 8
-        e2e = {"value": REP.job_rate(ncells * steps_e, ems), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "dtype": "f64", "steps": steps_e,
-               "copies": "overlapped with the neighbouring steps' compute (two device buffer sets, upload and "
-                         "download streams)",
-               "serial_value": REP.job_rate(ncells * steps_e, ems_serial)}
-
+    smooth = None
+    if not args.no_smooth:
+        smooth = smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n)
     batched = None
     if not args.no_batched:
         batched = batched_bench(G, args.steps, args.warmup)
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs)
-    large = None
-    if not args.no_large:
-        large = large_block_bench(G)
     tube = None
     if not args.no_shocktube:
         tube = shocktube_bench(G)
@@ -919,41 +966,58 @@ def main():
         amr = amr_bench(G)
     ct = None
     if not args.no_ct:
-        ct = ct_bench(G, n=args.n)
+        ct = ct_bench(G, n=args.smooth_n)
     poly = None
     if not args.no_poly:
-        poly = poly_bench(G, n=args.n)
+        poly = poly_bench(G, n=args.smooth_n)
 
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_sample(G)
+        cpu = cpu_baseline_sample(G, args.n)
+    floor = 512.0 * 3     # per-kernel byte floor per cell per SSP-RK3 step (three stages)
+    zc_mx = value_mx / world
+    mixed = {"value": value_mx, "unit": UNIT, "ms_per_step": msmx / args.steps,
+             "dtype": "f32 reconstruct/HLLE/divergence + f64 con2prim/metric",
+             "speedup_vs_fp64": value_mx / value64, "failed_cells": nfailmx,
+             "tile": autotune.BLOCK_SHAPES[tile_mx],
+             "hbm_frac_512B_floor": floor * zc_mx / (hbm * 1e9)}
+    summary = {
+        "fp64_zc_per_s": value64, "mixed_zc_per_s": value_mx, "fp64_failed_cells": nfail64,
+        "mixed_failed_cells": nfailmx,
+        "fp64_hbm_frac_512B_floor": floor * value64 / world / (hbm * 1e9),
+        "mixed_hbm_frac_512B_floor": mixed["hbm_frac_512B_floor"],
+        "adjoint_step_ratio_256": adj_step["ratio_to_fp64_step"] if adj_step else None,
+        "adjoint_forward_ratio_64cube_20steps": adjoint["adjoint_forward_ratio"] if adjoint else None,
+        "roofline_frac": roof["frac"],
+        "mixed_max_err_vs_oracle": (cpu["accuracy_vs_oracle"]["mixed"]["vector_scaled_max"] if cpu else None),
+        "fp64_max_err_vs_oracle": (cpu["accuracy_vs_oracle"]["fp64"]["max"] if cpu else None),
+    }
     line = {
         "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.n),
-        "mixed": {"value": value_mx, "unit": UNIT, "ms_per_step": msmx / args.steps,
-                  "dtype": "f32 reconstruct/HLLE/divergence + f64 con2prim/metric",
-                  "speedup_vs_fp64": value_mx / value64, "failed_cells": nfailmx},
-        "failed_cells": nfail64,
-        "tile_shapes": {"fp64": "none (three-pass RHS: states, faces, cells)",
-                        "mixed": autotune.BLOCK_SHAPES[tiles[G.MIXED]]},
         # per SSP-RK3 stage: the three RHS passes, the recovery and the ghost fill
         "gpu_launches": args.steps * 15,
         "roofline": roof,
         "clocks": clk,
         "e2e": e2e,
+        "cpu_baseline": cpu,
+        "mixed": mixed,
+        "failed_cells": nfail64,
+        "hbm_peak_gbs": {"value": hbm, "source": hbm_src},
+        "adjoint_step": adj_step,
+        "smooth_128": smooth,
         "batched": batched,
         "adjoint": adjoint,
-        "block_256": large,
         "shocktube": tube,
         "amr2": amr,
         "ct": ct,
         "polytrope": poly,
-        "cpu_baseline": cpu,
         "context": {"paper_v100_setupA_zc_per_s": PAPER_V100_SETUPA,
                     "note": "paper: 240^3, RK2, FP64, V100 (Sec. 5.1); different hardware and setup"},
+        "summary": summary,
     }
     print(json.dumps(line), flush=True)
 
