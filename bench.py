@@ -573,7 +573,6 @@ def ct_bench(G, steps=5, warmup=2, n=N_SMOOTH):
     bf_h = I.face_curl(blk, I.edge_potential(blk, 101))
     inner = (slice(None),) + tuple(slice(blk.ng, s - blk.ng) for s in blk.shape)
     bf_h *= 0.03 / np.abs(bf_h[inner]).max()
-    prim_h = I.ct_state(blk, prim_h, bf_h, met_h)
     g = G.Grid(blk.n, blk.ng, blk.dx)
     met = torch.from_numpy(met_h).cuda()
     dt = CFL * min(blk.dx)
@@ -585,9 +584,10 @@ def ct_bench(G, steps=5, warmup=2, n=N_SMOOTH):
         for mode in ("plain", "ct"):
             p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=prec)
             prim = torch.from_numpy(prim_h).cuda()
+            b = torch.from_numpy(bf_h).cuda()
+            G.ct_cell_field(g, b, prim, met)        # cell field = face mean / sqrt(gamma)
             G.fill_ghosts(g, G.BC_COPY, prim)
             cons = G.prim2con(g, p, prim, met)
-            b = torch.from_numpy(bf_h).cuda()
             ws = G.ct_workspace(g, G.RK3) if mode == "ct" else G.workspace(g, G.RK3)
             nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
 

@@ -503,6 +503,15 @@ int grmhd_ct_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t
                      double* prim, double* bface, const double* metric, const double* kij, void* ws,
                      size_t ws_bytes, int32_t* nfail, void* stream);
 
+/* Cell-centred primitive field from the face field (the cell-centred
+ * densitised field is the mean of a cell's two faces, as above): on every
+ * interior cell prim[5 + a] := (bface[a] of the cell + bface[a] of the cell
+ * above along a) / 2 / sqrt(gamma), sqrt(gamma) from the cell's metric (NULL:
+ * 1).  Nothing else of prim is touched (fill the ghosts afterwards).  For
+ * setting up a state whose cell field matches a given face field. */
+int grmhd_ct_cell_field(const grmhd_grid* grid, const double* bface, const double* metric, double* prim,
+                        void* stream);
+
 /* Discrete divergence of the face field: div [ncell] (nullable) gets
  * sum_a (B^a[+e_a] - B^a)/dx_a on the interior cells and 0 elsewhere;
  * maxabs (nullable, one device double) the largest |div| (a NaN shows as

@@ -375,3 +375,25 @@ def ct_rk_step(grid: Grid, params: OParams, scheme: int, dt: float, cons, prim, 
                                       _ptr(cons), _ptr(prim), _ptr(bface), _ptr(_f64(metric)))
     return cons, prim, bface, nfail
 
+
+
+def ct_cell_field(prim, bface, metric=None):
+    """Primitives whose field is the cell mean of the face field divided by
+    sqrt(gamma) of the cell (reading R19: the cell-centred densitised field is
+    the mean of a cell's two faces), for every cell, ghosts included, that has
+    both of its faces in the array; the other entries keep ``prim``."""
+    prim = np.array(prim, dtype=np.float64, copy=True)
+    sg = np.ones(prim.shape[1:])
+    if metric is not None:
+        g = metric
+        det = (g[4] * (g[7] * g[9] - g[8] * g[8]) - g[5] * (g[5] * g[9] - g[8] * g[6])
+               + g[6] * (g[5] * g[8] - g[7] * g[6]))
+        sg = np.sqrt(det)
+    for a in range(3):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[2 - a] = slice(0, -1)
+        hi[2 - a] = slice(1, None)
+        cell = 0.5 * (bface[a][tuple(lo)] + bface[a][tuple(hi)])
+        prim[5 + a][tuple(lo)] = cell / sg[tuple(lo)]
+    return prim

@@ -411,6 +411,14 @@ int grmhd_ct_rk_step(const grmhd_grid* grid, const grmhd_params* params, int32_t
                       nullptr, &ct);
 }
 
+int grmhd_ct_cell_field(const grmhd_grid* grid, const double* bface, const double* metric, double* prim,
+                        void* stream) {
+  const int e = check_grid(grid, 1);
+  if (e) return e;
+  if (!bface || !prim || !aligned8(bface) || !aligned8(prim) || (metric && !aligned8(metric))) return GRMHD_ERR_ARG;
+  return cuda_status(launch_ct_cell_field(make_grid(*grid), bface, metric, prim, (cudaStream_t)stream));
+}
+
 int grmhd_ct_divergence(const grmhd_grid* grid, const double* bface, double* div, double* maxabs, void* stream) {
   const int e = check_grid(grid, 1);
   if (e) return e;

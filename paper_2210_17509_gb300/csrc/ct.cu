@@ -109,6 +109,27 @@ __global__ void ct_face_to_cell_kernel(DevGrid g, const double* __restrict__ bf,
   }
 }
 
+// Primitive field of every interior cell from the face field: B^a = (mean of
+// the cell's two a-faces) / sqrt(gamma) of the cell (flat: sqrt(gamma) = 1).
+__global__ void ct_cell_field_kernel(DevGrid g, const double* __restrict__ bf, const double* __restrict__ metric,
+                                     double* __restrict__ prim) {
+  const long long nx = g.n[0], ny = g.n[1], total = nx * ny * g.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long x = cell_at(g, (int)(t % nx), (int)((t / nx) % ny), (int)(t / (nx * ny)));
+    double isg = 1.0;
+    if (metric) {
+      const double xx = metric[4 * g.ncell + x], xy = metric[5 * g.ncell + x], xz = metric[6 * g.ncell + x];
+      const double yy = metric[7 * g.ncell + x], yz = metric[8 * g.ncell + x], zz = metric[9 * g.ncell + x];
+      const double det = xx * (yy * zz - yz * yz) - xy * (xy * zz - yz * xz) + xz * (xy * yz - yy * xz);
+      isg = 1.0 / sqrt(det);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      prim[(5 + a) * g.ncell + x] = 0.5 * (bf[a * g.ncell + x] + bf[a * g.ncell + x + axis_stride(g, a)]) * isg;
+  }
+}
+
 // Discrete divergence of every cell (0 outside the interior); the largest
 // |div| into *maxabs (as the bit pattern of a non-negative double, whose
 // integer order is its numeric order).
@@ -153,6 +174,13 @@ cudaError_t launch_ct_faces(const DevGrid& g, const double* fb, double* E, doubl
 cudaError_t launch_ct_face_to_cell(const DevGrid& g, const double* b, double* cons, cudaStream_t s) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
   ct_face_to_cell_kernel<<<ct_blocks(total, 256), 256, 0, s>>>(g, b, cons);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_cell_field(const DevGrid& g, const double* b, const double* metric, double* prim,
+                                 cudaStream_t s) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  ct_cell_field_kernel<<<ct_blocks(total, 256), 256, 0, s>>>(g, b, metric, prim);
   return cudaGetLastError();
 }
 

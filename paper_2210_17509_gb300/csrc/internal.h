@@ -200,6 +200,8 @@ cudaError_t launch_ct_faces(const DevGrid& g, const double* fb, double* E, doubl
                             double wa, double wr, cudaStream_t s);
 cudaError_t launch_ct_face_to_cell(const DevGrid& g, const double* b, double* cons, cudaStream_t s);
 cudaError_t launch_ct_divergence(const DevGrid& g, const double* b, double* div, double* maxabs, cudaStream_t s);
+cudaError_t launch_ct_cell_field(const DevGrid& g, const double* b, const double* metric, double* prim,
+                                 cudaStream_t s);
 
 // Two-level AMR transfer (amr.cu).
 cudaError_t launch_restrict(const DevGrid& c, double* coarse, const DevGrid& f, const double* fine, const int lo[3],

@@ -582,8 +582,9 @@ _lib.grmhd_ct_workspace_bytes_cached.restype = ctypes.c_size_t
 _lib.grmhd_ct_rate.argtypes = [_pg, _pp, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
 _lib.grmhd_ct_rk_step.argtypes = [_pg, _pp, _I32, ctypes.c_double, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]
 _lib.grmhd_ct_divergence.argtypes = [_pg, _P, _P, _P, _P]
+_lib.grmhd_ct_cell_field.argtypes = [_pg, _P, _P, _P, _P]
 C_SYMBOLS = C_SYMBOLS + ("grmhd_ct_flux_bytes", "grmhd_ct_workspace_bytes", "grmhd_ct_workspace_bytes_cached",
-                         "grmhd_ct_rate", "grmhd_ct_rk_step", "grmhd_ct_divergence")
+                         "grmhd_ct_rate", "grmhd_ct_rk_step", "grmhd_ct_divergence", "grmhd_ct_cell_field")
 
 
 def ct_workspace(grid: Grid, scheme: int, device=None, cached: bool = True):
@@ -641,3 +642,13 @@ def ct_divergence(grid: Grid, bface, div=None, maxabs=None, stream=None):
                                   None if maxabs is None else ctypes.c_void_p(maxabs.data_ptr()), _stream(stream))
     _check(rc, "grmhd_ct_divergence")
     return div, maxabs
+
+
+def ct_cell_field(grid: Grid, bface, prim, metric=None, stream=None):
+    """grmhd_ct_cell_field: the primitive field of every interior cell from
+    the face field (face mean over sqrt(gamma)), in place on prim."""
+    rc = _lib.grmhd_ct_cell_field(ctypes.byref(grid.c()), _field(bface, grid, 3, "bface"),
+                                  _field(metric, grid, 10, "metric", True), _field(prim, grid, 8, "prim"),
+                                  _stream(stream))
+    _check(rc, "grmhd_ct_cell_field")
+    return prim

@@ -348,27 +348,6 @@ def face_curl(blk: Block, A):
     return B
 
 
-def ct_state(blk: Block, prim, bface, metric=None):
-    """Primitives whose field is the cell mean of the face field (divided by
-    sqrt(gamma) of the cell), for the interior and ghost cells that have both
-    faces; the other entries keep `prim`."""
-    prim = prim.copy()
-    sg = np.ones(blk.shape)
-    if metric is not None:
-        g = metric
-        det = (g[4] * (g[7] * g[9] - g[8] * g[8]) - g[5] * (g[5] * g[9] - g[8] * g[6])
-               + g[6] * (g[5] * g[8] - g[7] * g[6]))
-        sg = np.sqrt(det)
-    for a in range(3):
-        lo = [slice(None)] * 3
-        hi = [slice(None)] * 3
-        lo[2 - a] = slice(0, -1)
-        hi[2 - a] = slice(1, None)
-        cell = 0.5 * (bface[a][tuple(lo)] + bface[a][tuple(hi)])
-        prim[5 + a][tuple(lo)] = cell / sg[tuple(lo)]
-    return prim
-
-
 def polytrope_prims(blk: Block, seed: int, K: float, gamma: float, metric=None, vmax=0.9, log_rho=(-4.0, -2.5),
                     b_scale=1.0):
     """Random magnetised states on the polytrope P = K rho^gamma: log10 rho

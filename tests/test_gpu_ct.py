@@ -62,7 +62,7 @@ def ct_case(n, seed=1, curved=False, bmax=0.1, ng=3):
     bf = I.face_curl(blk, I.edge_potential(blk, seed + 100))
     inner = (slice(None),) + tuple(slice(ng, s - ng) for s in blk.shape)
     bf *= bmax / np.abs(bf[inner]).max()
-    prim = I.ct_state(blk, prim, bf, metric)
+    prim = O.ct_cell_field(prim, bf, metric)
     og = O.Grid(blk.n, ng, blk.dx)
     prim = O.fill_ghosts(og, bc, prim)
     return blk, og, metric, prim, bf, bc
@@ -215,3 +215,24 @@ def test_ct_without_field_is_the_plain_step(G):
     assert np.array_equal(host(c1), host(c2))
     assert np.array_equal(host(p1), host(p2))
     assert np.all(host(b1) == 0.0)
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_cell_field_from_faces_matches_oracle(G, curved):
+    """grmhd_ct_cell_field: the primitive field of every interior cell is the
+    mean of its two faces over sqrt(gamma), as the oracle forms it; nothing
+    else of prim changes."""
+    blk, og, metric, prim, bf, bc = ct_case((13, 7, 5), seed=4, curved=curved)
+    rng = np.random.default_rng(3)
+    start = prim + rng.normal(size=prim.shape) * 0.01      # a field not yet matching the faces
+    g = G.Grid(blk.n, blk.ng, blk.dx)
+    tp = cuda(start)
+    G.ct_cell_field(g, cuda(bf), tp, None if metric is None else cuda(metric))
+    got = host(tp)
+    ref = O.ct_cell_field(start, bf, metric)
+    inner = (slice(None),) + tuple(slice(blk.ng, s - blk.ng) for s in blk.shape)
+    np.testing.assert_allclose(got[inner][5:], ref[inner][5:], rtol=4e-16, atol=0)
+    np.testing.assert_array_equal(got[inner][:5], start[inner][:5])
+    outer = np.ones(got.shape[1:], bool)
+    outer[inner[1:]] = False
+    np.testing.assert_array_equal(got[:, outer], start[:, outer])

@@ -98,7 +98,7 @@ def test_ct_step_with_poisoned_workspace(G, precision):
     bf = I.face_curl(blk, I.edge_potential(blk, 7))
     inner = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
     bf *= 0.05 / np.abs(bf[inner]).max()
-    prim = O.fill_ghosts(O.Grid(blk.n, 3, blk.dx), O.BC_COPY, I.ct_state(blk, prim, bf, m))
+    prim = O.fill_ghosts(O.Grid(blk.n, 3, blk.dx), O.BC_COPY, O.ct_cell_field(prim, bf, m))
     g = G.Grid(blk.n, 3, blk.dx)
     p = G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=precision)
     gm = cuda(m)

@@ -160,7 +160,7 @@ def test_ct_step(G):
     prim = I.polytrope_prims(blk, 9, K, GAM, vmax=0.4, b_scale=0.0, log_rho=(-3.5, -3.0))
     bf = I.face_curl(blk, I.edge_potential(blk, 109))
     bf *= 0.3 * np.sqrt(10 ** -3.5) / np.abs(interior(bf)).max()
-    prim = O.fill_ghosts(og, O.BC_PERIODIC, I.ct_state(blk, prim, bf))
+    prim = O.fill_ghosts(og, O.BC_PERIODIC, O.ct_cell_field(prim, bf))
     op = oparams()
     cons = O.prim2con(og, GAM, prim, None, params=op)
     dt = 0.25 * min(blk.dx)

@@ -101,7 +101,9 @@ def test_shocktube_parity_with_oracle(G, test):
     print(f"Balsara {test}: {nsteps} steps, cons {errc:.2e}, prim {errp:.2e}, failures {nf // 16} per column")
     # Balsara 4's streams have W = 22.4 (|v| = 0.999): forming W from 1 - v^2 = 2e-3 amplifies the
     # round-off difference of the two formulations (3+1 here, covariant in the oracle) by about
-    # W^2 = 500 per evaluation, so its bound is 1e-11 instead of 1e-12.
+    # W^2 = 500 per evaluation, so its bound is 1e-11 instead of 1e-12.  The oracle alone moves by
+    # about 2e-11 over these 25 steps when its input changes by one ulp
+    # (tests/test_oracle_pins.py: test_balsara_round_off_amplification).
     tol = 1e-11 if test == 4 else FP64_TOL
     assert errc <= tol and errp <= tol, (errc, errp)
 

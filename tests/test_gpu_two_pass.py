@@ -84,7 +84,7 @@ def test_ct_step_bit_identical(G, n):
     bf = I.face_curl(blk, I.edge_potential(blk, 5))
     inner = (slice(None),) + tuple(slice(3, s - 3) for s in blk.shape)
     bf *= 0.05 / np.abs(bf[inner]).max()
-    prim = O.fill_ghosts(O.Grid(blk.n, 3, blk.dx), O.BC_COPY, I.ct_state(blk, prim, bf, m))
+    prim = O.fill_ghosts(O.Grid(blk.n, 3, blk.dx), O.BC_COPY, O.ct_cell_field(prim, bf, m))
     g = G.Grid(blk.n, 3, blk.dx)
     p = G.Params(recon=G.WENO5, bc=G.BC_COPY)
     gm = cuda(m)

@@ -29,7 +29,7 @@ def ct_setup(blk, seed=1, bmax=0.1, prim=None):
     A = I.edge_potential(blk, seed + 100)
     bf = I.face_curl(blk, A)
     bf *= bmax / np.abs(bf[:, 3:-3, 3:-3, 3:-3]).max()
-    prim = I.ct_state(blk, prim, bf)
+    prim = O.ct_cell_field(prim, bf)
     prim = O.fill_ghosts(g, O.BC_PERIODIC, prim)
     return g, prim, bf
 
@@ -118,7 +118,7 @@ def test_weak_field_advection_converges():
         A = I.edge_potential(blk, 9, nmodes=2)
         scale = 1e-4 / np.abs(I.face_curl(blk, A)).max()
         bf = scale * I.face_curl(blk, A)
-        prim = I.ct_state(blk, prim, bf)
+        prim = O.ct_cell_field(prim, bf)
         prim = O.fill_ghosts(g, O.BC_PERIODIC, prim)
         par = O.make_params(recon=O.REC_WENO5, bc=O.BC_PERIODIC)
         cons = O.prim2con(g, par.gamma, prim)

@@ -695,6 +695,37 @@ def test_copy_boundary_is_nearest_interior_cell(n):
     np.testing.assert_array_equal(O.fill_ghosts(g, O.BC_PERIODIC, arr), np.pad(core, pad, mode="wrap"))
 
 
+def _tube_after(test, prim, blk, gamma, n=200, nsteps=25):
+    og = O.Grid(blk.n, blk.ng, blk.dx)
+    op = O.make_params(gamma=gamma, recon=O.REC_MINMOD, bc=O.BC_COPY, rho_atm=1e-10, p_atm=1e-20)
+    cons = O.prim2con(og, gamma, prim)
+    for _ in range(nsteps):
+        cons, prim, _ = O.rk_step(og, op, O.RK4, 0.8 / n, cons, prim)
+    return cons[:, 3, 3, 3:n + 3]
+
+
+@pytest.mark.parametrize("test,lo,hi", [(1, 0.0, 1e-13), (4, 1e-12, 1e-10)])
+def test_balsara_round_off_amplification(test, lo, hi):
+    """How far 25 RK4 steps of a Balsara tube (Sec. 4.1 setup, 200 points)
+    carry a one-ulp change of every initial primitive, in the oracle alone.
+    Balsara 4's W = 22.4 streams (1 - v^2 = 2e-3) amplify it to about 2e-11
+    normwise, so no FP64 implementation that differs from the oracle by
+    round-off can be held to 1e-12 there; Balsara 1 stays at round-off."""
+    from paper_2210_17509_gb300 import inputs as I
+    blk, prim, gamma, _ = I.shocktube(test, 200, 0, 1)
+    base = _tube_after(test, prim, blk, gamma)
+    for seed in range(2):
+        rng = np.random.default_rng(seed)
+        pert = prim * (1 + rng.choice([-1.0, 1.0], size=prim.shape) * 2.0 ** -52)
+        d = _tube_after(test, pert, blk, gamma)
+        # vector components against their vector's largest component (Balsara 1
+        # keeps S_z and B^z at zero)
+        scale = [np.abs(base[g]).max() for g in ([0], [1, 2, 3], [1, 2, 3], [1, 2, 3], [4], [5, 6, 7], [5, 6, 7],
+                                               [5, 6, 7])]
+        err = max(np.abs(d[q] - base[q]).max() / scale[q] for q in range(8))
+        assert lo <= err < hi, (test, err)
+
+
 def test_balsara1_peak_lorentz_factor_printed_in_paper():
     """Balsara 1 with the paper's setup at 400 points: peak W ~ 1.458 at t = 0.4."""
     gold = json.load(open(os.path.join(GOLDEN, "balsara_table.json")))
