@@ -258,9 +258,10 @@ def cpu_baseline_sample(G, n=N_HEADLINE, seconds_target=15.0):
 # --------------------------------------------------------------- batched --
 def batched_bench(G, steps, warmup, nbox=512):
     """512 AMR-like boxes (edges from {8..64}, 3 refinement levels, flat):
-    recovery + ghost fill + RHS of every box as one graph of persistent
-    launches (three; five for the three-pass FP64 WENO5 RHS), against the plain form
-    (three launches per box)."""
+    recovery + ghost fill + RHS of every box as one library-owned CUDA graph
+    of persistent launches (three kernels; five for the three-pass FP64 WENO5
+    RHS), launched once per evaluation, against the same launches issued
+    directly and against the plain form (three launches per box)."""
     import torch
     from paper_2210_17509_gb300 import autotune
     t0 = time.perf_counter()
@@ -282,24 +283,37 @@ def batched_bench(G, steps, warmup, nbox=512):
             boxes.append(G.Box(g, tc, tp, torch.zeros_like(tp), None, autotune.choose(blk.n, costs),
                                G.BC_PERIODIC))
         batch = G.Batch(boxes, p)
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for _ in range(max(warmup, 1)):
-                batch.rhs(p)
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
+        for _ in range(max(warmup, 1)):
             batch.rhs(p)
-        for _ in range(warmup):
-            graph.replay()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            graph.replay()
+            batch.rhs(p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_direct = e0.elapsed_time(e1) / steps
+        # the whole evaluation in one persistent launch (one-pass RHS tiles)
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(max(warmup, 1)):
+            batch.rhs_fused(p, None, status)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            batch.rhs_fused(p, None, status)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_fused = e0.elapsed_time(e1) / steps
+        fused_status = int(status.item())
+        # the library-owned graph of the phased launches: one launch per evaluation
+        graph = batch.graph(p)
+        for _ in range(warmup):
+            graph.launch()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            graph.launch()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
@@ -321,12 +335,20 @@ def batched_bench(G, steps, warmup, nbox=512):
         for b in boxes:
             tiles_used[str(autotune.SHAPES[b.tile])] = tiles_used.get(str(autotune.SHAPES[b.tile]), 0) + 1
         out[name] = {"value": ncells / (ms * 1e-3), "unit": "cells/s (recovery+RHS per box, one evaluation)",
-                     "ms_per_batch": ms, "plain_per_box_ms": ms_plain, "speedup_vs_plain": ms_plain / ms,
-                     "gpu_launches_per_batch": (3 + (batch.c.two_pass + batch.c.three_pass
-                                                     if precision == G.FP64 else 0)),
+                     "ms_per_batch": ms, "form": "library graph (grmhd_batch_graph_launch), one launch per batch",
+                     "direct_ms_per_batch": ms_direct,
+                     "one_launch": {"ms_per_batch": ms_fused, "value": ncells / (ms_fused * 1e-3),
+                                    "form": "grmhd_batch_rhs_fused: one memset + one persistent kernel "
+                                            "(recovery, ghost fill, one-pass RHS tiles)",
+                                    "status": fused_status},
+                     "plain_per_box_ms": ms_plain,
+                     "speedup_vs_plain": ms_plain / ms,
+                     "kernels_per_batch": (3 + (batch.c.two_pass + batch.c.three_pass
+                                                if precision == G.FP64 else 0)),
                      "multi_pass": ("three passes" if batch.c.three_pass and precision == G.FP64 else
                                     "two passes" if batch.c.two_pass and precision == G.FP64 else "one pass"),
                      "tile_shapes": tiles_used}
+        graph.close()
         del boxes, batch, graph
         torch.cuda.empty_cache()
     return out
@@ -817,14 +839,24 @@ def e2e_bench(G, REP, blk, prim_h, met, steps_e):
             "serial_value": REP.job_rate(ncells * steps_e, ems_serial)}
 
 
-def smooth_block_bench(G, REP, steps, warmup, n=N_SMOOTH):
+def mixed_tile(G, n, forced=-1):
+    """RHS tile shape of the mixed path: the project's autotuner's choice for
+    an n^3 curved block, unless one is forced (profiling runs)."""
+    if forced >= 0:
+        return forced
+    from paper_2210_17509_gb300 import autotune
+    return autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), (n, n, n),
+                                     curved=True)
+
+
+def smooth_block_bench(G, REP, steps, warmup, n=N_SMOOTH, tile_mx=-1):
     """The smooth 128^3 Schwarzschild block (densities 1e-3 .. 1, |v| <= 0.5,
     |B| <= 0.1, WENO5+HLLE, SSP-RK3, CFL 0.25, copy BC), FP64 and mixed."""
     import torch
     from paper_2210_17509_gb300 import autotune
     blk, prim_h, met_h = I.smooth_schwarzschild(n, seed=1)
     met = torch.from_numpy(met_h).cuda()
-    tile = autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n, curved=True)
+    tile = mixed_tile(G, n, tile_mx)
     out = {"workload": f"schwarzschild-block-{n}^3+3ghost-weno5-hlle-ssprk3 (smooth, rho 1e-3..1)"}
     for precision, name, t in ((G.FP64, "fp64", 0), (G.MIXED, "mixed", tile)):
         ms, nf, _, st = time_steps(G, REP, blk, prim_h, met, precision, steps, warmup, tile=t)
@@ -857,6 +889,8 @@ def main():
     ap.add_argument("--section", default=None,
                     choices=["ct", "poly", "amr", "shocktube", "batched", "adjoint", "smooth"],
                     help="run only this section and print its JSON (profiling runs)")
+    ap.add_argument("--mixed-tile", type=int, default=-1,
+                    help="RHS tile shape of the mixed path (default: the autotuner's choice)")
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-dirs", type=int, default=50)
     args = ap.parse_args()
@@ -879,7 +913,7 @@ def main():
                "amr": lambda: amr_bench(G), "shocktube": lambda: shocktube_bench(G),
                "batched": lambda: batched_bench(G, args.steps, args.warmup),
                "adjoint": lambda: adjoint_bench(G, n=args.adjoint_n, ndir=args.adjoint_dirs),
-               "smooth": lambda: smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n)}
+               "smooth": lambda: smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n, args.mixed_tile)}
         out = fns[args.section]()
         if rank == 0:
             print(json.dumps({"section": args.section, args.section: out}), flush=True)
@@ -912,8 +946,7 @@ def main():
 
     # mixed precision path, on the RHS tile shape the project's autotuner picks
     from paper_2210_17509_gb300 import autotune
-    tile_mx = autotune.best_block_shape(G.Params(recon=G.WENO5, bc=G.BC_COPY, precision=G.MIXED), blk.n,
-                                        curved=True)
+    tile_mx = mixed_tile(G, args.n, args.mixed_tile)
     msmx, nfailmx, _, st = time_steps(G, REP, blk, prim_h, met, G.MIXED, args.steps, args.warmup, tile=tile_mx)
     value_mx = REP.job_rate(ncells * args.steps, msmx)
     del st
@@ -951,7 +984,7 @@ def main():
 
     smooth = None
     if not args.no_smooth:
-        smooth = smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n)
+        smooth = smooth_block_bench(G, REP, args.steps, args.warmup, args.smooth_n, args.mixed_tile)
     batched = None
     if not args.no_batched:
         batched = batched_bench(G, args.steps, args.warmup)

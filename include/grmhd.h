@@ -9,7 +9,9 @@
  * ---------------------------------------
  *  - All array pointers are DEVICE pointers (cudaMalloc / torch CUDA memory)
  *    unless the argument says "host".  The caller owns every buffer; the
- *    library never allocates, frees or retains memory.
+ *    library never allocates, frees or retains device memory (the one thing
+ *    it holds is the graph handle of grmhd_batch_graph_create, until the
+ *    caller destroys it).
  *  - Layout: structure of arrays, double precision, [var][z][y][x] with x
  *    fastest.  Every field spans the full block including ghosts:
  *    N_d = n_d + 2 ng points per axis, ncell = N_x N_y N_z, component q of a
@@ -281,6 +283,48 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
  * synchronisation: the sequence can be captured into a CUDA graph.  nfail as
  * for grmhd_con2prim.  Boxes' face and state buffers must not overlap. */
 int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, void* stream);
+
+/* grmhd_batch_rhs in ONE persistent launch (plus one memset of the work and
+ * completion counters): recovery, ghost fill and the one-pass RHS of every
+ * box in a single kernel.  One work counter hands out the items of the three
+ * phases in phase order; an item that needs an earlier phase of its own box
+ * (the ghost fill needs the box's recovery, its RHS tiles its ghost fill)
+ * waits, with a bounded spin, until that phase's completion counter for the
+ * box is full.  Every item waited on was handed out earlier to a running CTA,
+ * so the waits end without any co-residency requirement.  Results: the bits
+ * of grmhd_batch_rhs without face buffers (the one-pass RHS, whatever
+ * batch->two_pass says; in FP64 WENO5 the tiles then stage their face
+ * states in 211 KB of shared memory, one CTA per SM).
+ *   status (device int32, nullable): set to GRMHD_ERR_TIMEOUT if a wait gave
+ *   up (the results are then not valid); the caller zeroes it.
+ *   nfail as for grmhd_batch_rhs.  Overlapping calls on one batch race. */
+int grmhd_batch_rhs_fused(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, int32_t* status,
+                          void* stream);
+
+/* A CUDA graph of one grmhd_batch_rhs, owned by the library: an opaque
+ * handle. */
+typedef struct grmhd_batch_graph_t* grmhd_batch_graph;
+
+/* Capture grmhd_batch_rhs(batch, params, nfail) -- the memset of the work
+ * counters and the persistent launches -- into a CUDA graph and instantiate
+ * it.  The capture runs on a private stream that the call creates and
+ * destroys; nothing runs on the GPU.  The batch's workspace and box buffers,
+ * *params' values and nfail are fixed into the graph: they must stay valid,
+ * and the graph computes with the captured params, until the handle is
+ * destroyed.  The handle (host memory and the instantiated graph's driver
+ * resources; no device memory of the caller) is the one thing the library
+ * holds on the caller's behalf.  *graph = NULL on failure; argument errors
+ * of grmhd_batch_rhs are returned as it returns them. */
+int grmhd_batch_graph_create(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail,
+                             grmhd_batch_graph* graph);
+
+/* One evaluation of the captured batch on `stream`: one graph launch,
+ * results as grmhd_batch_rhs.  Launches of one handle on different streams
+ * must not overlap (they share the work counters). */
+int grmhd_batch_graph_launch(grmhd_batch_graph graph, void* stream);
+
+/* Release the handle (NULL is a no-op).  No launch of it may be pending. */
+int grmhd_batch_graph_destroy(grmhd_batch_graph graph);
 
 /* ----------------------------------------------------------------------
  * Reverse mode (adjoint) of the FP64 method, hand-written.  The paper has no

@@ -13,6 +13,7 @@ DevGrid make_grid(const grmhd_grid& g) {
     d.N[i] = g.n[i] + 2 * g.ng;
     d.dx[i] = g.dx[i];
     d.idx[i] = 1.0 / g.dx[i];
+    d.idxf[i] = (float)d.idx[i];
   }
   d.ng = g.ng;
   d.sy = d.N[0];
@@ -39,8 +40,15 @@ DevParams make_params(const grmhd_params& p) {
   d.eos = p.eos;
   d.poly_K = p.poly_K;
   d.poly_g2 = p.gamma == 2.0;
+  d.gammaf = (float)d.gamma;
+  d.gfacf = (float)d.gfac;
+  d.weno_epsf = (float)d.weno_eps;
+  d.eps13f = (float)(d.weno_eps * (12.0 / 13.0));
+  d.gm1gf = (float)d.gm1g;
+  d.rho_atmf = (float)d.rho_atm;
   // the polytrope's atmosphere pressure
   if (p.eos == GRMHD_EOS_POLYTROPE) d.p_atm = p.poly_K * std::pow(p.rho_atm, p.gamma);
+  d.p_atmf = (float)d.p_atm;
   return d;
 }
 

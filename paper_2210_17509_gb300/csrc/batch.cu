@@ -1,6 +1,7 @@
 // Batched boxes: host side of grmhd_batch_prepare / grmhd_batch_rhs.
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -13,6 +14,10 @@ cudaError_t launch_batch_rhs_mixed(BatchHead* head, const BoxDev* boxes, const D
                                    cudaStream_t s);
 cudaError_t launch_batch_rhs_two_pass(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved,
                                       bool three, int nsm, cudaStream_t s);
+cudaError_t launch_batch_fused_fp64(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                    int32_t* nfail, int32_t* status, cudaStream_t s);
+cudaError_t launch_batch_fused_mixed(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                     int32_t* nfail, int32_t* status, cudaStream_t s);
 __global__ void __launch_bounds__(kBatchItem) batch_con2prim_kernel(BatchHead* head, const BoxDev* __restrict__ boxes,
                                                                     DevParams p, int32_t* nfail) {
   int myfail = 0;
@@ -53,8 +58,11 @@ using namespace grmhd;
 
 namespace {
 
-constexpr size_t kHeadBytes = 256;
+constexpr size_t kHeadBytes = kBatchHeadBytes;
 static_assert(sizeof(BatchHead) <= kHeadBytes, "batch header too large");
+
+// The box table sits after the header and the completion counters.
+size_t box_table_offset(int32_t nbox) { return kHeadBytes + batch_done_bytes(nbox); }
 
 const int kShape[4][3] = {{8, 8, 4}, {16, 4, 4}, {32, 4, 2}, {4, 8, 8}};
 
@@ -65,7 +73,7 @@ extern "C" {
 
 size_t grmhd_batch_workspace_bytes(int32_t nbox) {
   if (nbox < 1 || nbox > (1 << 22)) return 0;
-  return kHeadBytes + (((size_t)nbox * sizeof(BoxDev) + 255) & ~(size_t)255);
+  return box_table_offset(nbox) + (((size_t)nbox * sizeof(BoxDev) + 255) & ~(size_t)255);
 }
 
 int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params* params, void* ws,
@@ -147,7 +155,7 @@ int grmhd_batch_prepare(const grmhd_box* boxes, int32_t nbox, const grmhd_params
   cudaStream_t s = (cudaStream_t)stream;
   // Host sources are pageable: the calls return once the data are staged.
   if (cudaMemcpyAsync(ws, &head, sizeof(head), cudaMemcpyHostToDevice, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-  if (cudaMemcpyAsync(static_cast<char*>(ws) + kHeadBytes, sorted.data(), (size_t)nbox * sizeof(BoxDev),
+  if (cudaMemcpyAsync(static_cast<char*>(ws) + box_table_offset(nbox), sorted.data(), (size_t)nbox * sizeof(BoxDev),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return GRMHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return GRMHD_ERR_CUDA;
@@ -176,7 +184,8 @@ int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_
   if (cudaGetDevice(&dev) != cudaSuccess) return GRMHD_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GRMHD_ERR_CUDA;
   BatchHead* head = static_cast<BatchHead*>(batch->ws);
-  const BoxDev* boxes = reinterpret_cast<const BoxDev*>(static_cast<char*>(batch->ws) + kHeadBytes);
+  const BoxDev* boxes =
+      reinterpret_cast<const BoxDev*>(static_cast<char*>(batch->ws) + box_table_offset(batch->nbox));
   const DevParams p = make_params(*params);
   if (cudaMemsetAsync(&head->counter[0], 0, sizeof(head->counter), s) != cudaSuccess) return GRMHD_ERR_CUDA;
   batch_con2prim_kernel<<<nsm * 8, kBatchItem, 0, s>>>(head, boxes, p, nfail);
@@ -188,6 +197,87 @@ int grmhd_batch_rhs(const grmhd_batch* batch, const grmhd_params* params, int32_
   if (p.precision == GRMHD_MIXED) e = launch_batch_rhs_mixed(head, boxes, p, curved, nsm, s);
   else if (batch->two_pass) e = launch_batch_rhs_two_pass(head, boxes, p, curved, batch->three_pass != 0, nsm, s);
   else e = launch_batch_rhs_fp64(head, boxes, p, curved, nsm, s);
+  return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+int grmhd_batch_rhs_fused(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail, int32_t* status,
+                          void* stream) {
+  if (!batch || !params || !batch->ws || batch->nbox < 1) return GRMHD_ERR_ARG;
+  if (params->eos != GRMHD_EOS_IDEAL) return GRMHD_ERR_ARG;  // batched boxes: Gamma-law only
+  if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;
+  if (params->precision != GRMHD_FP64 && params->precision != GRMHD_MIXED) return GRMHD_ERR_ARG;
+  if (!(params->gamma > 1.0 && params->gamma <= 3.0) || params->nr_maxit < 1 || !(params->nr_tol > 0.0))
+    return GRMHD_ERR_ARG;
+  if (nfail && (reinterpret_cast<uintptr_t>(nfail) & 3u)) return GRMHD_ERR_ARG;
+  if (status && (reinterpret_cast<uintptr_t>(status) & 3u)) return GRMHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GRMHD_ERR_CUDA;
+  BatchHead* head = static_cast<BatchHead*>(batch->ws);
+  const BoxDev* boxes =
+      reinterpret_cast<const BoxDev*>(static_cast<char*>(batch->ws) + box_table_offset(batch->nbox));
+  const DevParams p = make_params(*params);
+  // one memset: the work counters (the header's last bytes) and the completion counters after them
+  char* zero_from = reinterpret_cast<char*>(&head->counter[0]);
+  const size_t zero_bytes = static_cast<size_t>(static_cast<char*>(batch->ws) + box_table_offset(batch->nbox) - zero_from);
+  if (cudaMemsetAsync(zero_from, 0, zero_bytes, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+  const bool curved = batch->curved != 0;
+  const cudaError_t e = p.precision == GRMHD_MIXED
+                            ? launch_batch_fused_mixed(head, boxes, p, curved, nsm, nfail, status, s)
+                            : launch_batch_fused_fp64(head, boxes, p, curved, nsm, nfail, status, s);
+  return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+// A library-owned graph of one grmhd_batch_rhs: captured once on a private
+// stream (nothing runs while capturing), replayed with one launch per batch
+// evaluation.
+struct grmhd_batch_graph_t {
+  cudaGraphExec_t exec;
+};
+
+int grmhd_batch_graph_create(const grmhd_batch* batch, const grmhd_params* params, int32_t* nfail,
+                             grmhd_batch_graph* graph) {
+  if (!graph) return GRMHD_ERR_ARG;
+  *graph = nullptr;
+  if (!batch || !params) return GRMHD_ERR_ARG;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return GRMHD_ERR_CUDA;
+  }
+  const int rc = grmhd_batch_rhs(batch, params, nfail, s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &g);
+  cudaStreamDestroy(s);
+  if (rc != GRMHD_OK || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    return rc != GRMHD_OK ? rc : GRMHD_ERR_CUDA;
+  }
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return GRMHD_ERR_CUDA;
+  grmhd_batch_graph_t* h = new (std::nothrow) grmhd_batch_graph_t;
+  if (!h) {
+    cudaGraphExecDestroy(x);
+    return GRMHD_ERR_CUDA;
+  }
+  h->exec = x;
+  *graph = h;
+  return GRMHD_OK;
+}
+
+int grmhd_batch_graph_launch(grmhd_batch_graph graph, void* stream) {
+  if (!graph || !graph->exec) return GRMHD_ERR_ARG;
+  return cudaGraphLaunch(graph->exec, (cudaStream_t)stream) == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+int grmhd_batch_graph_destroy(grmhd_batch_graph graph) {
+  if (!graph) return GRMHD_OK;
+  const cudaError_t e = graph->exec ? cudaGraphExecDestroy(graph->exec) : cudaSuccess;
+  delete graph;
   return e == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }
 

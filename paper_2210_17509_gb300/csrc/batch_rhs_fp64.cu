@@ -6,6 +6,10 @@ cudaError_t launch_batch_rhs_fp64(BatchHead* head, const BoxDev* boxes, const De
                                   cudaStream_t s) {
   return launch_batch_rhs_t<double>(head, boxes, p, curved, nsm, s);
 }
+cudaError_t launch_batch_fused_fp64(BatchHead* head, const BoxDev* boxes, const DevParams& p, bool curved, int nsm,
+                                    int32_t* nfail, int32_t* status, cudaStream_t s) {
+  return launch_batch_fused_t<double>(head, boxes, p, curved, nsm, nfail, status, s);
+}
 
 // Multi-pass FP64 RHS over the table, then the per-cell pass (work counter
 // 3).  With `three` (WENO5, every box with a state buffer): the state and face

@@ -21,6 +21,7 @@ struct DevGrid {
   long long ncell; // N[0] * N[1] * N[2]
   double dx[3];
   double idx[3];   // 1 / dx
+  float idxf[3];   // 1 / dx rounded to FP32 (the FP32 kernels' copy)
 };
 
 // Method parameters with constants folded on the host.
@@ -38,7 +39,16 @@ struct DevParams {
   int eos;         // GRMHD_EOS_IDEAL | GRMHD_EOS_POLYTROPE
   double poly_K;   // K of P = K rho^gamma (polytrope)
   int poly_g2;     // polytrope with gamma == 2: K rho^(gamma - 1) = K rho, no pow
+  // FP32 copies for the FP32 kernels, rounded once on the host (the same
+  // bits as a conversion in the kernel, without its FP64-pipe instruction)
+  float gammaf, gfacf, weno_epsf, eps13f, gm1gf, rho_atmf, p_atmf;
 };
+
+// A parameter in the kernel's arithmetic type: the FP32 copy for float.
+template <class T>
+__host__ __device__ __forceinline__ T par_t(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f; else return (T)d;
+}
 
 // What the RHS kernel does with the RHS value r of each interior cell:
 //   rhs     != NULL: rhs[cell] = r

@@ -201,7 +201,7 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
 // improved (z, W) (unchanged if it fails); the FP64 Newton of c2p_solve then
 // finishes to nr_tol, normally in one or two steps.
 __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
-  const float gm1g = (float)p.gm1g;
+  const float gm1g = p.gm1gf;
   const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
   float zf = (float)z, Wf = (float)W;
   if (!(zf > 0.0f) || !(Wf >= 1.0f)) return false;
@@ -261,7 +261,7 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 // pressure, which starts the Newman-Hamlin fallback.
 __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams& p, float zf, float Wf, float Pg,
                                                double& z, double& W) {
-  const float gm1g = (float)p.gm1g;
+  const float gm1g = p.gm1gf;
   const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
   bool active = zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf);
   bool converged = false;
@@ -384,7 +384,7 @@ __device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p
 // false (W unchanged) if it does not get there in 8 steps.
 __device__ __forceinline__ bool c2p_polytrope_predict(const C2PIn& in, const DevParams& p, double& W) {
   const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2;
-  const float gfac = (float)p.gfac, dzk = (float)((2.0 - p.gamma) * p.gfac);
+  const float gfac = p.gfacf, dzk = (float)((2.0 - p.gamma) * p.gfac);
   float w = fmaxf((float)W, 1.0f);
 #pragma unroll 1
   for (int it = 0; it < 8; ++it) {
@@ -473,7 +473,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
     const float rg = pf[0], Pg = pf[4 * g.ncell];
     Wg = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
-    zg = (rg > 0.0f && Pg > 0.0f) ? (rg + (float)p.gfac * Pg) * Wg * Wg : (float)(tau + D + in.B2);
+    zg = (rg > 0.0f && Pg > 0.0f) ? (rg + p.gfacf * Pg) * Wg * Wg : (float)(tau + D + in.B2);
     Pgf = Pg;
   } else {
     const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
@@ -526,7 +526,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
       const float X = 1.0f / (Wf * zf * zbf);
       const float iW = zf * zbf * X, iz = Wf * zbf * X, izb = Wf * zf * X;
       const float rho = (float)D * iW;
-      const float P = poly ? rho * poly_k_rho_gm1<float>(p, rho) : (float)p.gm1g * (zf * iW * iW - rho);
+      const float P = poly ? rho * poly_k_rho_gm1<float>(p, rho) : p.gm1gf * (zf * iW * iW - rho);
       const float bsz = (float)BS * iz;
       float gf[6], guf[6];
 #pragma unroll
@@ -540,14 +540,14 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
       for (int i = 0; i < 3; ++i) vlo[i] = ((float)Sl[i] + bsz * Blf[i]) * izb;
       lower(guf, vlo, vu);
       const float v2 = vu[0] * vlo[0] + vu[1] * vlo[1] + vu[2] * vlo[2];
-      if (rho >= (float)p.rho_atm && v2 < 1.0f && isfinite(P)) {
+      if (rho >= p.rho_atmf && v2 < 1.0f && isfinite(P)) {
         outf[0] = rho;
         outf[1] = vu[0];
         outf[2] = vu[1];
         outf[3] = vu[2];
         outf[4] = P;
         if (!(P > 0.0f)) {
-          outf[4] = (float)p.p_atm;
+          outf[4] = p.p_atmf;
           st = 3;
         }
       } else {
@@ -555,9 +555,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
       }
     }
     if (st == 2) {
-      outf[0] = (float)p.rho_atm;
+      outf[0] = p.rho_atmf;
       outf[1] = outf[2] = outf[3] = 0.0f;
-      outf[4] = (float)p.p_atm;
+      outf[4] = p.p_atmf;
     }
     outf[5] = Bf[0];
     outf[6] = Bf[1];
@@ -613,7 +613,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
 
 // Ghost point c copies its source: periodic wrap or the nearest interior
 // point, per axis (edges and corners included).  Interior points: no-op.
-template <class F>
+// COHERENT: the sources were written by other CTAs of the same launch, so
+// they are read through L2 (ld.global.cg).
+template <class F, bool COHERENT = false>
 __device__ __forceinline__ void fill_ghost_at(const DevGrid& g, int bc, int nvar, F* __restrict__ f, long long c) {
   int idx[3];
   idx[0] = (int)(c % g.N[0]);
@@ -637,7 +639,7 @@ __device__ __forceinline__ void fill_ghost_at(const DevGrid& g, int bc, int nvar
   }
   if (interior) return;
   const long long sc = (long long)src[2] * g.sz + (long long)src[1] * g.sy + src[0];
-  for (int q = 0; q < nvar; ++q) f[q * g.ncell + c] = f[q * g.ncell + sc];
+  for (int q = 0; q < nvar; ++q) f[q * g.ncell + c] = COHERENT ? __ldcg(f + q * g.ncell + sc) : f[q * g.ncell + sc];
 }
 
 // Interior cell index of the t-th interior point (x fastest).

@@ -52,8 +52,17 @@ typedef SrcCacheT<double, double> SrcCache64;  // FP64: FP64 primitives + FP64 g
 //           is exact, so the sum has the bits of 0.5 (a + b))
 static_assert(kGeomCacheComps == 63 && kGeomCacheHalf == 53, "geometry cache layout");
 
+// SrcF64 whose primitives are written in the same launch (the one-launch
+// batch: recovered and ghost-filled by other CTAs before the tile reads
+// them): the primitives are read through L2 (ld.global.cg), not the
+// read-only path, which is not coherent with writes made during a launch.
+// The metric stays read-only.
+struct SrcF64Co : SrcF64 {};
+
 template <class T>
 __device__ __forceinline__ T ld_prim(const SrcF64& s, long long i) { return (T)__ldg(s.prim + i); }
+template <class T>
+__device__ __forceinline__ T ld_prim(const SrcF64Co& s, long long i) { return (T)__ldcg(s.prim + i); }
 template <class T, class PT, class GT>
 __device__ __forceinline__ T ld_prim(const SrcCacheT<PT, GT>& s, long long i) { return (T)__ldg(s.prim + i); }
 
@@ -250,8 +259,8 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
     rotate_vec(dir, vlL, rvL);
     rotate_vec(dir, vlR, rvR);
     if (CURVED) rotate_metric(dir, m);
-    side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia, rvL, v2L);
-    side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia, rvR, v2R);
+    side_state<T, CURVED, 0, true, true>(rL, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), L, ia, rvL, v2L);
+    side_state<T, CURVED, 0, true, true>(rR, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), R, ia, rvR, v2R);
   } else {
     // FP32 (latency bound, 80 registers): fewer values live across the rotation
     if (!physical_state<T, CURVED>(pL, m)) {
@@ -265,8 +274,8 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
     rotate_state(dir, pL, rL);
     rotate_state(dir, pR, rR);
     if (CURVED) rotate_metric(dir, m);
-    side_state<T, CURVED, 0, true, true>(rL, m, (T)p.gamma, (T)p.gfac, L, ia);
-    side_state<T, CURVED, 0, true, true>(rR, m, (T)p.gamma, (T)p.gfac, R, ia);
+    side_state<T, CURVED, 0, true, true>(rL, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), L, ia);
+    side_state<T, CURVED, 0, true, true>(rR, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), R, ia);
   }
   finish_speeds<T, CURVED, 0>(m, L, R);
   hlle_combine_scaled<T>(L, R, CURVED ? m.alpha : T(1), CURVED ? m.sqrtg : T(1), Fr);
@@ -301,7 +310,7 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   const T iW = omv2 * W;
   const T ab0 = W * Bv;
   const T b2 = B2 * omv2 + Bv * Bv;
-  const T hs = rho + (T)p.gfac * P + b2;
+  const T hs = rho + par_t<T>(p.gfac, p.gfacf) * P + b2;
   const T Ps = P + T(0.5) * b2;
   const T ia = T(1) / alpha;
   const T ia2 = ia * ia;
@@ -375,10 +384,11 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
 }
 
 // Metric quantities from the FP64 inputs: inverse and sqrt(gamma) in FP64,
-// 4th-order centred differences of the cell-centred metric.
-template <class T>
-__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcF64& src, long long c,
-                                             T out[8]) {
+// 4th-order centred differences of the cell-centred metric (S: SrcF64 or
+// SrcF64Co, which differ in how the primitives are read).
+template <class T, class S>
+__device__ __forceinline__ void source_terms_f64(const DevGrid& g, const DevParams& p, const S& src, long long c,
+                                                 T out[8]) {
   const double* __restrict__ metric = src.metric;
   double a[10];
 #pragma unroll
@@ -406,7 +416,18 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
       dA[e][q] = (T)((8.0 * (__ldg(m + s) - __ldg(m - s)) - (__ldg(m + 2 * s) - __ldg(m - 2 * s))) * w);
     }
   }
-  source_core<T, SrcF64>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+  source_core<T, S>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+}
+
+template <class T>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcF64& src, long long c,
+                                             T out[8]) {
+  source_terms_f64<T, SrcF64>(g, p, src, c, out);
+}
+template <class T>
+__device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcF64Co& src, long long c,
+                                             T out[8]) {
+  source_terms_f64<T, SrcF64Co>(g, p, src, c, out);
 }
 
 // Metric quantities from the geometry cache.
@@ -547,7 +568,7 @@ __device__ __forceinline__ bool tile_face_at(const DevGrid& g, const DevParams& 
       pR[q] = sR[(2 * q) * ns + eR];
     }
   } else {
-    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, par_t<T>(p.weno_eps, p.weno_epsf), pL, pR);
   }
   face_flux_states<T, CURVED, S, POLY>(g, p, src, c, dir, stride, pL, pR, F);
   cell = c;
@@ -677,7 +698,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       tile_face<T, RECON, CURVED, TX, TY, TZ, S, POLY>(g, p, src, x0, y0, z0, f, sF, sR, 0, 0, 0);
     __syncthreads();
   } else if constexpr (SM::stage_all) {
-    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+    const T eps13 = par_t<T>(p.weno_eps * (12.0 / 13.0), p.eps13f);
     // (a) the tile's own cells, both states, per direction; (b) the two end
     // cells of every line of the extended box, one state each (the plus
     // state below the tile, the minus state above it).  The two groups are
@@ -716,7 +737,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
                                                   ST::EXX + ST::EYY);
     __syncthreads();
   } else {
-    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+    const T eps13 = par_t<T>(p.weno_eps * (12.0 / 13.0), p.eps13f);
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
       const int ne = dir == 0 ? ST::EXX : (dir == 1 ? ST::EYY : ST::EZZ);
@@ -742,7 +763,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
     const int fx = (ck * TY + cj) * (TX + 1) + ci;
     const int fy = NFX + (ck * (TY + 1) + cj) * TX + ci;
     const int fz = NFX + NFY + (ck * TY + cj) * TX + ci;
-    const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+    const T ix = par_t<T>(g.idx[0], g.idxf[0]), iy = par_t<T>(g.idx[1], g.idxf[1]), iz = par_t<T>(g.idx[2], g.idxf[2]);
     T r[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -764,7 +785,14 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
       const double rq = (double)r[q];
       if (ep.rhs) ep.rhs[o] = rq;
       const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
-      if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+      // FP64 (pipe bound): without an accumulator the ca term, an exact zero, is left out
+      // (the same bits); the FP32 kernels keep the one expression, which measured faster there
+      if constexpr (sizeof(T) == 8) {
+        if (ep.u) ep.u[o] = ep.acc_in ? ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain
+                                      : ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq;
+      } else {
+        if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+      }
       if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
     }
   }
@@ -805,7 +833,7 @@ __device__ __forceinline__ void faces_tile(const DevGrid& g, const DevParams& p,
   const bool top[3] = {x0 + TX == g.n[0], y0 + TY == g.n[1], z0 + TZ == g.n[2]};
   if constexpr (CellRecon<T, RECON>::value) {
     static_assert(TileSmem<T, RECON, TX, TY, TZ>::stage_all, "two-pass RHS needs the all-direction stage");
-    const T eps13 = (T)(p.weno_eps * (12.0 / 13.0));
+    const T eps13 = par_t<T>(p.weno_eps * (12.0 / 13.0), p.eps13f);
     // (a) the tile's own cells, both states; (b) the end cell below every
     // line, plus state; (c) the end cell above every line of the directions
     // in which the tile ends at the block's upper end, minus state
@@ -891,7 +919,7 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_faces_ker
 template <class T, bool CURVED, class S>
 __device__ __forceinline__ void div_cell(const DevGrid& g, const DevParams& p, const S& src,
                                          const double* __restrict__ Ff, long long c, const StageEpilogue& ep) {
-  const T ix = (T)g.idx[0], iy = (T)g.idx[1], iz = (T)g.idx[2];
+  const T ix = par_t<T>(g.idx[0], g.idxf[0]), iy = par_t<T>(g.idx[1], g.idxf[1]), iz = par_t<T>(g.idx[2], g.idxf[2]);
   T r[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -915,7 +943,9 @@ __device__ __forceinline__ void div_cell(const DevGrid& g, const DevParams& p, c
     const double rq = (double)r[q];
     if (ep.rhs) ep.rhs[o] = rq;
     const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
-    if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+    // without an accumulator the ca term (an exact zero) is left out: the same bits
+    if (ep.u) ep.u[o] = ep.acc_in ? ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain
+                                  : ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq;
     if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
   }
 }
@@ -976,7 +1006,7 @@ __global__ void __launch_bounds__(kRingThreads) ct_ring_kernel(DevGrid g, DevPar
     const long long c = (long long)(I[2] + g.ng) * g.sz + (long long)(I[1] + g.ng) * g.sy + (I[0] + g.ng);
     const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
     T pL[8], pR[8], F[8];
-    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, (T)p.weno_eps, pL, pR);
+    reconstruct_face<T, RECON, S>(src, g.ncell, c, stride, par_t<T>(p.weno_eps, p.weno_epsf), pL, pR);
     face_flux_states<T, CURVED, S, POLY>(g, p, src, c, d, stride, pL, pR, F);
 #pragma unroll
     for (int q = 0; q < 3; ++q)

@@ -309,7 +309,17 @@ _lib.grmhd_batch_prepare.argtypes = [ctypes.POINTER(CBox), _I32, _pp, _P, ctypes
 _lib.grmhd_batch_prepare.restype = _I
 _lib.grmhd_batch_rhs.argtypes = [ctypes.POINTER(CBatch), _pp, _P, _P]
 _lib.grmhd_batch_rhs.restype = _I
-C_SYMBOLS = C_SYMBOLS + ("grmhd_batch_workspace_bytes", "grmhd_batch_prepare", "grmhd_batch_rhs")
+_lib.grmhd_batch_rhs_fused.argtypes = [ctypes.POINTER(CBatch), _pp, _P, _P, _P]
+_lib.grmhd_batch_rhs_fused.restype = _I
+_lib.grmhd_batch_graph_create.argtypes = [ctypes.POINTER(CBatch), _pp, _P, ctypes.POINTER(_P)]
+_lib.grmhd_batch_graph_create.restype = _I
+_lib.grmhd_batch_graph_launch.argtypes = [_P, _P]
+_lib.grmhd_batch_graph_launch.restype = _I
+_lib.grmhd_batch_graph_destroy.argtypes = [_P]
+_lib.grmhd_batch_graph_destroy.restype = _I
+C_SYMBOLS = C_SYMBOLS + ("grmhd_batch_workspace_bytes", "grmhd_batch_prepare", "grmhd_batch_rhs",
+                         "grmhd_batch_graph_create", "grmhd_batch_graph_launch", "grmhd_batch_graph_destroy",
+                         "grmhd_batch_rhs_fused")
 
 
 @dataclass
@@ -369,6 +379,47 @@ class Batch:
         nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
         rc = _lib.grmhd_batch_rhs(ctypes.byref(self.c), ctypes.byref(params.c()), nf, _stream(stream))
         _check(rc, "grmhd_batch_rhs")
+
+    def rhs_fused(self, params: Params, nfail=None, status=None, stream=None):
+        """grmhd_batch_rhs_fused: the whole evaluation in one persistent launch
+        (status: optional device int32, set to GRMHD_ERR_TIMEOUT if a wait gave up)."""
+        nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+        st = None if status is None else ctypes.c_void_p(status.data_ptr())
+        rc = _lib.grmhd_batch_rhs_fused(ctypes.byref(self.c), ctypes.byref(params.c()), nf, st, _stream(stream))
+        _check(rc, "grmhd_batch_rhs_fused")
+
+    def graph(self, params: Params, nfail=None):
+        """grmhd_batch_graph_create: the batch evaluation as a library-owned
+        CUDA graph (BatchGraph), replayed with one launch per evaluation."""
+        return BatchGraph(self, params, nfail)
+
+
+class BatchGraph:
+    """A library-owned graph of one batch evaluation; keeps the batch (and
+    so its tensors) and nfail alive, and destroys the graph when collected
+    or closed."""
+
+    def __init__(self, batch: Batch, params: Params, nfail=None):
+        self.batch = batch
+        self.nfail = nfail
+        self.h = _P()
+        nf = None if nfail is None else ctypes.c_void_p(nfail.data_ptr())
+        rc = _lib.grmhd_batch_graph_create(ctypes.byref(batch.c), ctypes.byref(params.c()), nf, ctypes.byref(self.h))
+        _check(rc, "grmhd_batch_graph_create")
+
+    def launch(self, stream=None):
+        _check(_lib.grmhd_batch_graph_launch(self.h, _stream(stream)), "grmhd_batch_graph_launch")
+
+    def close(self):
+        if self.h:
+            _lib.grmhd_batch_graph_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ adjoint --

@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 from paper_2210_17509_gb300 import inputs as I
-from tests.helpers import FP64_TOL, interior, normwise
+from tests.helpers import FP64_TOL, MIXED_TOL, interior, normwise
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -143,7 +143,7 @@ def test_autotuner_choices_are_valid(G):
 
 def test_batch_mixed_against_fp64_oracle(G):
     """Mixed-precision batch (FP32-predicted recovery, FP32 fluxes): RHS of
-    every box within 1e-4 of the FP64 oracle, recovery exact to round-off."""
+    every box within 1e-5 of the FP64 oracle, recovery exact to round-off."""
     p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=G.MIXED)
     boxes, host = make_boxes(G, p, 6, seed=11)
     batch = G.Batch(boxes, p)
@@ -155,7 +155,8 @@ def test_batch_mixed_against_fp64_oracle(G):
         pf = O.fill_ghosts(og, 0, prim)
         ro = O.rhs(og, op, pf, met)
         err = normwise(interior(b.rhs.cpu().numpy(), 3), interior(ro, 3))
-        assert np.all(err < 1e-4), err
+        print("mixed batch RHS vs oracle, normwise", err)
+        assert np.all(err < MIXED_TOL), err
         perr = normwise(interior(b.prim.cpu().numpy(), 3), interior(pf, 3))
         assert np.all(perr < 1e-12), perr
 
@@ -178,4 +179,148 @@ def test_batch_two_pass_matches_single_pass(G, curved, recon):
         torch.cuda.synchronize()
         out.append([interior(b.rhs.cpu().numpy(), 3) for b in boxes])
     for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_library_graph_matches_direct_call(G, precision):
+    """grmhd_batch_graph_create / _launch: the batch evaluation captured by the
+    library and replayed with one launch gives the bits of grmhd_batch_rhs,
+    launch after launch."""
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=precision)
+    boxes, _ = make_boxes(G, p, 16, seed=7)
+    batch = G.Batch(boxes, p)
+    start = [b.prim.clone() for b in boxes]
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.rhs(p, nfail)
+    torch.cuda.synchronize()
+    ref = [b.rhs.clone() for b in boxes]
+    ref_prim = [b.prim.clone() for b in boxes]
+    graph = batch.graph(p, nfail)
+    for _ in range(3):
+        for b, s0 in zip(boxes, start):
+            b.prim.copy_(s0)
+            b.rhs.zero_()
+        graph.launch()
+        torch.cuda.synchronize()
+        for b, r, rp in zip(boxes, ref, ref_prim):
+            np.testing.assert_array_equal(b.rhs.cpu().numpy(), r.cpu().numpy())
+            np.testing.assert_array_equal(b.prim.cpu().numpy(), rp.cpu().numpy())
+    assert int(nfail.item()) == 0
+    graph.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_512_box_batch_sampled_against_oracle(G, precision):
+    """The benchmark's batched workload (512 flat periodic boxes, edges from
+    {8 .. 64}, three levels, WENO5) in the benchmark's form (a library graph
+    of the multi-pass FP64 or the one-pass mixed launches): recovery, ghost
+    fill and RHS of a sample of boxes -- the largest, the smallest and ten
+    others -- against the oracle box by box (FP64 1e-12; mixed: the recovery
+    to 1e-10, as the mixed-recovery test holds it, and the FP32 right-hand
+    side to 1e-5)."""
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=precision)
+    data = I.amr_boxes(512, seed=2)
+    boxes, states = [], []
+    for blk, prim in data:
+        # both sides start from the oracle's conserved variables
+        og = O.Grid(blk.n, 3, blk.dx)
+        pf = O.fill_ghosts(og, O.BC_PERIODIC, prim)
+        cons = O.prim2con(og, p.gamma, pf)
+        states.append((og, pf, cons))
+        g = G.Grid(blk.n, blk.ng, blk.dx)
+        tp = torch.from_numpy(pf).cuda()
+        boxes.append(G.Box(g, torch.from_numpy(cons).cuda(), tp, torch.zeros_like(tp), None, 0, G.BC_PERIODIC))
+    batch = G.Batch(boxes, p)
+    nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+    graph = batch.graph(p, nfail)
+    graph.launch()
+    torch.cuda.synchronize()
+    assert int(nfail.item()) == 0
+    sizes = np.array([b.grid.ncell for b in boxes])
+    rng = np.random.default_rng(17)
+    pick = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} | set(rng.choice(len(boxes), 10, replace=False).tolist()))
+    op = O.make_params(recon=O.REC_WENO5, bc=O.BC_PERIODIC, rho_atm=p.rho_atm, p_atm=p.p_atm, weno_eps=p.weno_eps)
+    for k in pick:
+        b = boxes[k]
+        og, pf, cons = states[k]
+        po, _, nf = O.con2prim(og, op, cons, None, pf)
+        assert nf == 0
+        po = O.fill_ghosts(og, O.BC_PERIODIC, po)
+        ro = O.rhs(og, op, po)
+        perr = normwise(interior(b.prim.cpu().numpy(), 3), interior(po, 3))
+        # the mixed recovery's one refinement step leaves about 1e-13 in (z, W); the pressure,
+        # a difference of two terms of (z, W), carries it amplified (1.1e-12 measured on one box)
+        assert np.all(perr < (FP64_TOL if precision == 0 else 1e-10)), (k, perr)
+        err = normwise(interior(b.rhs.cpu().numpy(), 3), interior(ro, 3))
+        print("512-box batch RHS vs oracle, box", k, "normwise", err)
+        assert np.all(err < (FP64_TOL if precision == 0 else MIXED_TOL)), (k, err)
+    graph.close()
+
+
+@pytest.mark.parametrize("curved", [False, True])
+@pytest.mark.parametrize("recon", ["weno5", "minmod"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_launch_batch_matches_phased_launches(G, precision, recon, curved):
+    """grmhd_batch_rhs_fused: recovery, ghost fill and RHS of every box in one
+    persistent launch, each phase of a box waiting on its earlier phase's
+    completion counter, gives the bits of the phased one-pass launches of
+    grmhd_batch_rhs (all four tile shapes present), call after call, and no
+    wait gives up."""
+    p = G.Params(recon=G.WENO5 if recon == "weno5" else G.MINMOD, bc=G.BC_PERIODIC, precision=precision)
+    out = []
+    for fused in (False, True):
+        boxes, _ = make_boxes(G, p, 20, seed=13, curved=curved)
+        batch = G.Batch(boxes, p, two_pass=False)
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        start = [b.prim.clone() for b in boxes]
+        runs = []
+        for _ in range(2):
+            for b, s0 in zip(boxes, start):
+                b.prim.copy_(s0)
+                b.rhs.zero_()
+            if fused:
+                batch.rhs_fused(p, nfail, status)
+            else:
+                batch.rhs(p, nfail)
+            torch.cuda.synchronize()
+            runs.append([(b.prim.cpu().numpy(), b.rhs.cpu().numpy()) for b in boxes])
+        assert int(status.item()) == 0
+        assert int(nfail.item()) == 0
+        for (p0, r0), (p1, r1) in zip(runs[0], runs[1]):
+            np.testing.assert_array_equal(p0, p1)
+            np.testing.assert_array_equal(r0, r1)
+        out.append(runs[1])
+    for (pa, ra), (pb, rb) in zip(out[0], out[1]):
+        np.testing.assert_array_equal(pa, pb)
+        np.testing.assert_array_equal(ra, rb)
+
+
+def test_one_launch_batch_full_workload(G):
+    """The 512-box workload in one launch (mixed precision) against the phased
+    launches, bit for bit."""
+    p = G.Params(recon=G.WENO5, bc=G.BC_PERIODIC, precision=G.MIXED)
+    data = I.amr_boxes(512, seed=2)
+    res = []
+    for fused in (False, True):
+        boxes = []
+        for blk, prim in data:
+            g = G.Grid(blk.n, blk.ng, blk.dx)
+            tp = torch.from_numpy(prim).cuda()
+            G.fill_ghosts(g, G.BC_PERIODIC, tp)
+            tc = G.prim2con(g, p, tp)
+            boxes.append(G.Box(g, tc, tp, torch.zeros_like(tp), None, 0, G.BC_PERIODIC))
+        batch = G.Batch(boxes, p, two_pass=False)
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        if fused:
+            batch.rhs_fused(p, None, status)
+        else:
+            batch.rhs(p)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        res.append([b.rhs.cpu().numpy() for b in boxes[::17]])
+        del boxes, batch
+        torch.cuda.empty_cache()
+    for a, b in zip(res[0], res[1]):
         np.testing.assert_array_equal(a, b)

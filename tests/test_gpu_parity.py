@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_2210_17509_gb300 import inputs as I
-from tests.helpers import FP64_TOL, MIXED_TOL, interior, normwise
+from tests.helpers import FP64_TOL, MIXED_TOL, interior, normwise, vector_normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -260,7 +260,8 @@ def test_rhs_mixed_close_to_fp64_oracle(G, curved):
     r = host(G.rhs(g, gp, cuda(prim), None if met is None else cuda(met)))
     ro = O.rhs(og, op, prim, met)
     err = normwise(interior(r, 3), interior(ro, 3))
-    assert np.all(err < 1e-4), err
+    print("mixed RHS vs oracle, normwise", err, "vector-scaled", vector_normwise(interior(r, 3), interior(ro, 3)))
+    assert np.all(err < MIXED_TOL), err
 
 
 # ------------------------------------------------------------- RK steps --
@@ -452,5 +453,7 @@ def test_rhs_cached_matches_rhs(G, precision):
     r2 = host(G.rhs_cached(g, dataclasses.replace(gp, flags=G.REUSE_GEOMETRY), tp, tm, None, None, ws))
     np.testing.assert_array_equal(r1, r2)
     ro = O.rhs(og, op, prim, met)
-    tol = FP64_TOL if precision == 0 else 1e-4
-    assert np.all(normwise(interior(r1, 3), interior(ro, 3)) < tol)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    err = normwise(interior(r1, 3), interior(ro, 3))
+    print("cached RHS vs oracle, precision", precision, "normwise", err)
+    assert np.all(err < tol), err
