@@ -112,34 +112,68 @@ __device__ __forceinline__ void weno5_pair<double>(double um3, double um2, doubl
 // candidate values are kept as 6 q_k, the factor 6 moving into the
 // denominator.
 //
-// FP64: product form.  The weights d_k / e_k^2 times (e_0 e_1 e_2)^2 are
-// plus (P12, 6 P02, 3 P01) and minus (P01, 6 P02, 3 P12) up to a common
-// factor, with Pjk = (e_j e_k)^2; the caller divides num / (6 den).  The
-// denominators' sums are written as rounded adds, so that no kernel that
-// inlines this fuses them differently: every FP64 path forms the same bits.
+// FP64 (the FP64 pipe is what bounds the RHS): everything is formed from the
+// four first differences of the stencil, dA = u[i-1] - u[i-2], dB = u[i] -
+// u[i-1], dC = u[i+1] - u[i], dD = u[i+2] - u[i+1].  The second differences
+// are t0 = dB - dA, t1 = dC - dB, t2 = dD - dC; the one-sided ones s0 = 3 dB
+// - dA, s1 = dB + dC (a sign that the square drops), s2 = dD - 3 dC; and
+// each candidate is 6 q_k = 6 u[i] + (a two-term combination of differences):
+// plus (5 dB - 2 dA, 2 dC + dB, 4 dC - dD), minus (2 dD - 5 dC, -2 dB - dC,
+// dA - 4 dB).  As the weights sum to one, a state is u[i] + num / (6 den):
+// 46 FP64 operations for both states of a value instead of 52 in terms of
+// the values themselves.
+// Product form of the weights: d_k / e_k^2 times (e_0 e_1 e_2)^2 are plus
+// (P12, 6 P02, 3 P01) and minus (P01, 6 P02, 3 P12) up to a common factor,
+// with Pjk = (e_j e_k)^2; the caller forms u[i] + num / (6 den).  Every
+// product and sum is written explicitly (rounded products and sums, fused
+// multiply-adds), so that every kernel that inlines this forms the same bits.
+struct Weno5Cell {
+  double dA, dB, dC, dD;   // first differences
+  double P01, P12, A, B, C;  // weights (plus: P12, A, B; minus: P01, A, C)
+};
+
+__device__ __forceinline__ void weno5_cell_weights(double um2, double um1, double u0, double up1, double up2,
+                                                   double eps13, Weno5Cell& w) {
+  const double k313 = 3.0 / 13.0;
+  w.dA = __dsub_rn(um1, um2);
+  w.dB = __dsub_rn(u0, um1);
+  w.dC = __dsub_rn(up1, u0);
+  w.dD = __dsub_rn(up2, up1);
+  const double t0 = __dsub_rn(w.dB, w.dA), t1 = __dsub_rn(w.dC, w.dB), t2 = __dsub_rn(w.dD, w.dC);
+  const double s0 = fma(3.0, w.dB, -w.dA), s1 = __dadd_rn(w.dB, w.dC), s2 = fma(-3.0, w.dC, w.dD);
+  const double e0 = fma(t0, t0, fma(__dmul_rn(k313, s0), s0, eps13));
+  const double e1 = fma(t1, t1, fma(__dmul_rn(k313, s1), s1, eps13));
+  const double e2 = fma(t2, t2, fma(__dmul_rn(k313, s2), s2, eps13));
+  const double p01 = __dmul_rn(e0, e1), p02 = __dmul_rn(e0, e2), p12 = __dmul_rn(e1, e2);
+  w.P01 = __dmul_rn(p01, p01);
+  w.P12 = __dmul_rn(p12, p12);
+  w.A = __dmul_rn(6.0, __dmul_rn(p02, p02));
+  w.B = __dmul_rn(3.0, w.P01);
+  w.C = __dmul_rn(3.0, w.P12);
+}
+
+__device__ __forceinline__ double weno5_cell_num_plus(const Weno5Cell& w) {
+  const double q0 = fma(5.0, w.dB, __dmul_rn(-2.0, w.dA));
+  const double q1 = fma(2.0, w.dC, w.dB);
+  const double q2 = fma(4.0, w.dC, -w.dD);
+  return fma(w.P12, q0, fma(w.A, q1, __dmul_rn(w.B, q2)));
+}
+
+__device__ __forceinline__ double weno5_cell_num_minus(const Weno5Cell& w) {
+  const double q0 = fma(2.0, w.dD, __dmul_rn(-5.0, w.dC));
+  const double q1 = fma(-2.0, w.dB, -w.dC);
+  const double q2 = fma(-4.0, w.dB, w.dA);
+  return fma(w.P01, q0, fma(w.A, q1, __dmul_rn(w.C, q2)));
+}
+
 __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double u0, double up1, double up2,
                                                  double eps13, double& nm, double& dm, double& np, double& dp) {
-  const double k313 = 3.0 / 13.0;
-  const double t0 = fma(-2.0, um1, um2 + u0), s0 = fma(3.0, u0, fma(-4.0, um1, um2));
-  const double t1 = fma(-2.0, u0, um1 + up1), s1 = um1 - up1;
-  const double t2 = fma(-2.0, up1, u0 + up2), s2 = fma(3.0, u0, fma(-4.0, up1, up2));
-  const double e0 = fma(t0, t0, fma(k313 * s0, s0, eps13));
-  const double e1 = fma(t1, t1, fma(k313 * s1, s1, eps13));
-  const double e2 = fma(t2, t2, fma(k313 * s2, s2, eps13));
-  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
-  const double P01 = p01 * p01, P12 = p12 * p12;
-  const double A = 6.0 * (p02 * p02), B = 3.0 * P01, C = 3.0 * P12;
-  const double u11 = 11.0 * u0;
-  const double qp0 = fma(2.0, um2, fma(-7.0, um1, u11));
-  const double qp1 = fma(2.0, up1, fma(5.0, u0, -um1));
-  const double qp2 = fma(5.0, up1, fma(2.0, u0, -up2));
-  const double qm0 = fma(2.0, up2, fma(-7.0, up1, u11));
-  const double qm1 = fma(2.0, um1, fma(5.0, u0, -up1));
-  const double qm2 = fma(5.0, um1, fma(2.0, u0, -um2));
-  np = fma(P12, qp0, fma(A, qp1, B * qp2));
-  dp = __dadd_rn(__dadd_rn(P12, A), B);
-  nm = fma(P01, qm0, fma(A, qm1, C * qm2));
-  dm = __dadd_rn(__dadd_rn(P01, A), C);
+  Weno5Cell w;
+  weno5_cell_weights(um2, um1, u0, up1, up2, eps13, w);
+  np = weno5_cell_num_plus(w);
+  dp = __dadd_rn(__dadd_rn(w.P12, w.A), w.B);
+  nm = weno5_cell_num_minus(w);
+  dm = __dadd_rn(__dadd_rn(w.P01, w.A), w.C);
 }
 
 // The numerator of one of the two states of weno5_cell_parts (plus: the
@@ -148,30 +182,17 @@ __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double 
 __device__ __forceinline__ void weno5_cell_parts_one(double um2, double um1, double u0, double up1, double up2,
                                                      double eps13, bool plus, double& num, double& dm,
                                                      double& dp) {
-  const double k313 = 3.0 / 13.0;
-  const double t0 = fma(-2.0, um1, um2 + u0), s0 = fma(3.0, u0, fma(-4.0, um1, um2));
-  const double t1 = fma(-2.0, u0, um1 + up1), s1 = um1 - up1;
-  const double t2 = fma(-2.0, up1, u0 + up2), s2 = fma(3.0, u0, fma(-4.0, up1, up2));
-  const double e0 = fma(t0, t0, fma(k313 * s0, s0, eps13));
-  const double e1 = fma(t1, t1, fma(k313 * s1, s1, eps13));
-  const double e2 = fma(t2, t2, fma(k313 * s2, s2, eps13));
-  const double p01 = e0 * e1, p02 = e0 * e2, p12 = e1 * e2;
-  const double P01 = p01 * p01, P12 = p12 * p12;
-  const double A = 6.0 * (p02 * p02), B = 3.0 * P01, C = 3.0 * P12;
-  const double u11 = 11.0 * u0;
-  dp = __dadd_rn(__dadd_rn(P12, A), B);
-  dm = __dadd_rn(__dadd_rn(P01, A), C);
-  if (plus) {
-    const double qp0 = fma(2.0, um2, fma(-7.0, um1, u11));
-    const double qp1 = fma(2.0, up1, fma(5.0, u0, -um1));
-    const double qp2 = fma(5.0, up1, fma(2.0, u0, -up2));
-    num = fma(P12, qp0, fma(A, qp1, B * qp2));
-  } else {
-    const double qm0 = fma(2.0, up2, fma(-7.0, up1, u11));
-    const double qm1 = fma(2.0, um1, fma(5.0, u0, -up1));
-    const double qm2 = fma(5.0, um1, fma(2.0, u0, -um2));
-    num = fma(P01, qm0, fma(A, qm1, C * qm2));
-  }
+  Weno5Cell w;
+  weno5_cell_weights(um2, um1, u0, up1, up2, eps13, w);
+  dp = __dadd_rn(__dadd_rn(w.P12, w.A), w.B);
+  dm = __dadd_rn(__dadd_rn(w.P01, w.A), w.C);
+  num = plus ? weno5_cell_num_plus(w) : weno5_cell_num_minus(w);
+}
+
+// A state from its parts: u[i] + num * (the other denominator's share of the
+// one division), the division giving 1 / (6 den_this den_other ...).
+__device__ __forceinline__ double weno5_cell_state(double u0, double num, double other_den_times_x) {
+  return fma(num, other_den_times_x, u0);
 }
 
 // FP32: reciprocal form (the squared products could overflow in single

@@ -128,21 +128,22 @@ __device__ __forceinline__ void reconstruct_face(const double* __restrict__ prim
 template <class S>
 __device__ __forceinline__ void weno5_cell_pair_states(const S& src, long long ncell, long long c, long long stride,
                                                        int h, double eps13, double v[4]) {
-  double nm[2], dm[2], np[2], dp[2];
+  double nm[2], dm[2], np[2], dp[2], u0[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const long long a = (2 * h + k) * ncell + c;
-    weno5_cell_parts(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride), ld_prim<double>(src, a),
+    u0[k] = ld_prim<double>(src, a);
+    weno5_cell_parts(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride), u0[k],
                      ld_prim<double>(src, a + stride), ld_prim<double>(src, a + 2 * stride), eps13, nm[k], dm[k],
                      np[k], dp[k]);
   }
-  const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
-  const double X = 1.0 / (6.0 * a0 * a1);
-  const double x0 = a1 * X, x1 = a0 * X;
-  v[0] = nm[0] * (dp[0] * x0);
-  v[1] = np[0] * (dm[0] * x0);
-  v[2] = nm[1] * (dp[1] * x1);
-  v[3] = np[1] * (dm[1] * x1);
+  const double a0 = __dmul_rn(dm[0], dp[0]), a1 = __dmul_rn(dm[1], dp[1]);
+  const double X = 1.0 / __dmul_rn(__dmul_rn(6.0, a0), a1);
+  const double x0 = __dmul_rn(a1, X), x1 = __dmul_rn(a0, X);
+  v[0] = weno5_cell_state(u0[0], nm[0], __dmul_rn(dp[0], x0));
+  v[1] = weno5_cell_state(u0[0], np[0], __dmul_rn(dm[0], x0));
+  v[2] = weno5_cell_state(u0[1], nm[1], __dmul_rn(dp[1], x1));
+  v[3] = weno5_cell_state(u0[1], np[1], __dmul_rn(dm[1], x1));
 }
 
 // Both reconstructed states of cell c (value at its lower face, "minus", and
@@ -159,23 +160,24 @@ __device__ __forceinline__ void reconstruct_cell_pair(const S& src, long long nc
     if (which != 0) {
       // one state of each of the two variables; the division as below, so
       // the value is the same to the bit as when both states are formed
-      double n[2], dm[2], dp[2];
+      double n[2], dm[2], dp[2], u0[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const long long a = (2 * h + k) * ncell + c;
-        weno5_cell_parts_one(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride),
-                             ld_prim<double>(src, a), ld_prim<double>(src, a + stride),
-                             ld_prim<double>(src, a + 2 * stride), (double)eps13, which == 2, n[k], dm[k], dp[k]);
+        u0[k] = ld_prim<double>(src, a);
+        weno5_cell_parts_one(ld_prim<double>(src, a - 2 * stride), ld_prim<double>(src, a - stride), u0[k],
+                             ld_prim<double>(src, a + stride), ld_prim<double>(src, a + 2 * stride), (double)eps13,
+                             which == 2, n[k], dm[k], dp[k]);
       }
-      const double a0 = dm[0] * dp[0], a1 = dm[1] * dp[1];
-      const double X = 1.0 / (6.0 * a0 * a1);
-      const double x0 = a1 * X, x1 = a0 * X;
+      const double a0 = __dmul_rn(dm[0], dp[0]), a1 = __dmul_rn(dm[1], dp[1]);
+      const double X = 1.0 / __dmul_rn(__dmul_rn(6.0, a0), a1);
+      const double x0 = __dmul_rn(a1, X), x1 = __dmul_rn(a0, X);
       if (which == 2) {
-        sR[(4 * h + 1) * ne + e] = (T)(n[0] * (dm[0] * x0));
-        sR[(4 * h + 3) * ne + e] = (T)(n[1] * (dm[1] * x1));
+        sR[(4 * h + 1) * ne + e] = (T)weno5_cell_state(u0[0], n[0], __dmul_rn(dm[0], x0));
+        sR[(4 * h + 3) * ne + e] = (T)weno5_cell_state(u0[1], n[1], __dmul_rn(dm[1], x1));
       } else {
-        sR[(4 * h + 0) * ne + e] = (T)(n[0] * (dp[0] * x0));
-        sR[(4 * h + 2) * ne + e] = (T)(n[1] * (dp[1] * x1));
+        sR[(4 * h + 0) * ne + e] = (T)weno5_cell_state(u0[0], n[0], __dmul_rn(dp[0], x0));
+        sR[(4 * h + 2) * ne + e] = (T)weno5_cell_state(u0[1], n[1], __dmul_rn(dp[1], x1));
       }
       return;
     }
