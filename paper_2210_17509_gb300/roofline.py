@@ -33,8 +33,8 @@ instead of the cache and has no buffers: 208 B).
 
 Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
-cells): 405.6 + 754.1 + 778.1 MB = 1937.8 MB, 2190 B per cell; traffic grows
-with the cell count, so a launch on n^3 cells is about 2190 n^3 B.
+cells): 406.2 + 754.9 + 778.4 MB = 1939.5 MB, 2192 B per cell; traffic grows
+with the cell count, so a launch on n^3 cells is about 2192 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -52,12 +52,12 @@ with open(os.path.join(HERE, "flop_counts.json")) as _f:
     FLOPS_PER_CELL_RHS_CURVED_WENO5 = int(json.load(_f)["rhs_curved_weno5_per_cell"])
 
 # ncu thread-instruction counts per interior cell at 96^3 (DADD, DMUL, DFMA)
-EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (196, 540, 772), "rhs_face_kernel": (106, 294, 427),
+EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (294, 516, 551), "rhs_face_kernel": (106, 294, 427),
                           "rhs_div_kernel": (37, 81, 155)}
 EXECUTED_FLOPS_PER_CELL = sum(a + m + 2 * f for a, m, f in EXECUTED_FP64_PER_CELL.values())
-FP64_PIPE_BUSY = {"rhs_states_kernel": 0.855, "rhs_face_kernel": 0.891, "rhs_div_kernel": 0.863}
+FP64_PIPE_BUSY = {"rhs_states_kernel": 0.860, "rhs_face_kernel": 0.891, "rhs_div_kernel": 0.864}
 BYTES_PER_CELL_RHS_CURVED = 632 + 384 + 768
-TRAFFIC_PER_CELL_MEASURED = (405.6e6 + 754.1e6 + 778.1e6) / 884736  # 2190 B per cell
+TRAFFIC_PER_CELL_MEASURED = (406.2e6 + 754.9e6 + 778.4e6) / 884736  # 2192 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
 HBM_FALLBACK_GBS = 6800.0
