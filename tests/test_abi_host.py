@@ -283,3 +283,34 @@ def test_batch_rejects_the_polytrope(lib):
     out = lib.CBatch()
     nb = lib._lib.grmhd_batch_workspace_bytes(1)
     assert lib._lib.grmhd_batch_prepare(boxes, 1, C.byref(p), C.c_void_p(0x100000), nb, C.byref(out), None) == -1
+
+
+def test_one_launch_graph_and_cell_field_validation(lib):
+    """The one-launch batch, the library graph and the cell-field set-up
+    reject bad arguments before any CUDA call; the batch workspace holds the
+    completion counters of the one-launch form ahead of the box table."""
+    import ctypes as C
+    G = lib
+    p = G.Params().c()
+    b = G.CBatch()                                    # ws NULL, nbox 0
+    assert G._lib.grmhd_batch_rhs_fused(C.byref(b), C.byref(p), None, None, None) == -1
+    assert G._lib.grmhd_batch_rhs_fused(None, C.byref(p), None, None, None) == -1
+    b.ws, b.nbox = C.c_void_p(0x100000), 4
+    bad = G.Params(recon=7).c()
+    assert G._lib.grmhd_batch_rhs_fused(C.byref(b), C.byref(bad), None, None, None) == -1
+    poly = G.Params(eos=G.EOS_POLYTROPE, poly_K=1.0).c()
+    assert G._lib.grmhd_batch_rhs_fused(C.byref(b), C.byref(poly), None, None, None) == -1
+    assert G._lib.grmhd_batch_rhs_fused(C.byref(b), C.byref(p), None, C.c_void_p(0x1002), None) == -1  # misaligned
+    h = C.c_void_p()
+    assert G._lib.grmhd_batch_graph_create(None, C.byref(p), None, C.byref(h)) == -1 and not h.value
+    assert G._lib.grmhd_batch_graph_create(C.byref(b), C.byref(p), None, None) == -1
+    assert G._lib.grmhd_batch_graph_launch(None, None) == -1
+    assert G._lib.grmhd_batch_graph_destroy(None) == 0
+    # 4 boxes: header 256 B, 2 x 4 counters rounded to 256 B, then the table
+    nb = G._lib.grmhd_batch_workspace_bytes(4)
+    assert nb >= 512 + 4 * C.sizeof(G.CBox) and nb % 256 == 0
+    g = _grid(lib)
+    G._lib.grmhd_ct_cell_field.restype = C.c_int
+    assert G._lib.grmhd_ct_cell_field(C.byref(g.c()), None, None, FAKE, None) == -1
+    assert G._lib.grmhd_ct_cell_field(C.byref(g.c()), FAKE, None, None, None) == -1
+    assert G._lib.grmhd_ct_cell_field(C.byref(g.c()), C.c_void_p(0x1001), None, FAKE, None) == -1
