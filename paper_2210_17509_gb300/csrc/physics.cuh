@@ -236,6 +236,7 @@ struct Geom {
   T g[6];      // gamma_xx, gamma_xy, gamma_xz, gamma_yy, gamma_yz, gamma_zz
   T sqrtg;     // sqrt(det gamma)
   T gup_dd;    // gamma^{dd} of the face normal
+  T ia;        // 1 / alpha (set by the run-time-normal face routines)
 };
 
 // Face metric = mean of the two adjacent cell-centre values; sqrt(gamma) and
@@ -281,6 +282,7 @@ __device__ __forceinline__ void face_geom_rt(const double* __restrict__ metric, 
   for (int i = 0; i < 6; ++i) m.g[i] = (T)a[4 + i];
   m.sqrtg = (T)sqrt(det);
   m.gup_dd = (T)(cdd / det);
+  m.ia = T(1) / m.alpha;
 }
 
 template <class T>

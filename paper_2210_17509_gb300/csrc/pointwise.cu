@@ -103,12 +103,29 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
     for (int q = 0; q < 10; ++q) {
       a[q] = __ldg(metric + q * n + c);
       geom[q * n + c] = (GT)a[q];
-      geom[(kGeomCacheHalf + q) * n + c] = (GT)(0.5 * a[q]);
+      // FP32 cache: half the metric values; a face's metric is the sum of its
+      // two cells' halves (the FP64 cache holds the face metric itself)
+      if constexpr (sizeof(GT) == 4) geom[(kGeomCacheHalf32 + q) * n + c] = (GT)(0.5 * a[q]);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long s = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
       GT sgf = GT(1), gupf = GT(1);
+      if constexpr (sizeof(GT) == 8) {
+        // FP64 cache: the face metric (the two halvings are exact and the sum
+        // is rounded once, the bits of the mean of the two cells) and its
+        // 1/alpha; points without a lower neighbour have no face that any
+        // kernel computes
+        double fa0 = 1.0;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+          double fq = q == 0 ? 1.0 : 0.0;
+          if (idx[d] >= 1) fq = __dadd_rn(__dmul_rn(0.5, __ldg(metric + q * n + c - s)), __dmul_rn(0.5, a[q]));
+          if (q == 0) fa0 = fq;
+          geom[(kGeomCacheFace + 10 * d + q) * n + c] = (GT)fq;
+        }
+        geom[(kGeomCacheFaceIa + d) * n + c] = (GT)(1.0 / fa0);
+      }
       if (idx[d] >= 1) {
         double m[6];
 #pragma unroll

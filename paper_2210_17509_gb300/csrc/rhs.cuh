@@ -47,10 +47,18 @@ typedef SrcCacheT<double, double> SrcCache64;  // FP64: FP64 primitives + FP64 g
 //   13..15  gamma^{dd} on the lower x / y / z face
 //   16      sqrt(gamma) at the point;  17..22 gamma^{ij} at the point
 //   23..52  4th-order derivatives d_e of the 10 metric entries (index 23 + 10 e + q)
+//   FP64 cache (the FP64 RHS is bound by its FP64 instructions: the face
+//   metric read whole saves ten additions and a division per face):
+//   53..82  the metric on the lower d-face of the point, 0.5 a_below + 0.5 a
+//           (index 53 + 10 d + q; the two halvings are exact, so the value
+//           has the bits of the mean of the two cells)
+//   83..85  1 / alpha on the lower d-face
+//   FP32 cache (the FP32 RHS is latency bound: ten arrays that all three
+//   face directions share stay in L1 better than thirty):
 //   53..62  half the metric values, 0.5 (alpha, beta^i, gamma_ij): a face's
-//           metric is then the sum of its two cells' entries (scaling by 0.5
-//           is exact, so the sum has the bits of 0.5 (a + b))
-static_assert(kGeomCacheComps == 63 && kGeomCacheHalf == 53, "geometry cache layout");
+//           metric is the sum of its two cells' entries
+static_assert(kGeomCacheComps == 86 && kGeomCacheFace == 53 && kGeomCacheFaceIa == 83 && kGeomCacheHalf32 == 53,
+              "geometry cache layout");
 
 // SrcF64 whose primitives are written in the same launch (the one-launch
 // batch: recovered and ghost-filled by other CTAs before the tile reads
@@ -213,10 +221,15 @@ __device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, lon
                                                  long long stride, int dir, Geom<T>& m) {
   const GT* gm = s.geom;
   T a[10];
+  if constexpr (sizeof(GT) == 8) {
 #pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    const GT* h = gm + (kGeomCacheHalf + q) * ncell + c;
-    a[q] = (T)__ldg(h - stride) + (T)__ldg(h);
+    for (int q = 0; q < 10; ++q) a[q] = (T)__ldg(gm + (kGeomCacheFace + 10 * dir + q) * ncell + c);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const GT* h = gm + (kGeomCacheHalf32 + q) * ncell + c;
+      a[q] = (T)__ldg(h - stride) + (T)__ldg(h);
+    }
   }
   m.alpha = a[0];
 #pragma unroll
@@ -225,6 +238,8 @@ __device__ __forceinline__ void face_geometry_rt(const SrcCacheT<PT, GT>& s, lon
   for (int i = 0; i < 6; ++i) m.g[i] = a[4 + i];
   m.sqrtg = (T)__ldg(gm + (10 + dir) * ncell + c);
   m.gup_dd = (T)__ldg(gm + (13 + dir) * ncell + c);
+  if constexpr (sizeof(GT) == 8) m.ia = (T)__ldg(gm + (kGeomCacheFaceIa + dir) * ncell + c);
+  else m.ia = T(1) / m.alpha;
 }
 
 // Flux through a face whose normal dir is known only at run time, from its
@@ -242,7 +257,7 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
   if (CURVED) face_geometry_rt<T>(src, g.ncell, c, stride, dir, m);
   T rL[8], rR[8], Fr[8];
   Side<T> L, R;
-  const T ia = CURVED ? T(1) / m.alpha : T(1);  // shared by both sides
+  const T ia = CURVED ? m.ia : T(1);  // 1/alpha of the face, shared by both sides
   if constexpr (sizeof(T) == 8) {
     // FP64 (pipe bound): the check's lowered velocity and v^2 feed the side states
     T vlL[3], vlR[3], v2L, v2R, rvL[3], rvR[3];

@@ -24,12 +24,14 @@ sources, epilogue).  The unit the benchmark times is that triple (one
 grmhd_rhs_cached call).
 
 Algorithmic HBM bytes per interior cell of the triple (FP64, static metric,
-geometry cache): prim 8 x 8 B + geometry cache 63 x 8 B read (the face pass
-reads the half-metric and face entries, the per-cell pass the rest), rhs
-8 x 8 B written = 632 B, plus the face buffer, 24 x 8 B written and read
-back = 384 B, and the state buffer, 48 x 8 B written and read back = 768 B:
-1784 B (the uncached single-pass grmhd_rhs reads the 10 metric entries
-instead of the cache and has no buffers: 208 B).
+geometry cache): prim 8 x 8 B + geometry cache 86 x 8 B read (the face pass
+reads the face metric, 1/alpha, sqrt(gamma) and gamma^dd of the three lower
+faces, 39 values; the per-cell pass the cell metric, sqrt(gamma), gamma^ij
+and the 30 derivatives, 47 values), rhs 8 x 8 B written = 816 B, plus the
+face buffer, 24 x 8 B written and read back = 384 B, and the state buffer,
+48 x 8 B written and read back = 768 B: 1968 B (the uncached single-pass
+grmhd_rhs reads the 10 metric entries instead of the cache and has no
+buffers: 208 B).
 
 Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
@@ -56,7 +58,7 @@ EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (294, 516, 551), "rhs_face_kernel
                           "rhs_div_kernel": (37, 81, 155)}
 EXECUTED_FLOPS_PER_CELL = sum(a + m + 2 * f for a, m, f in EXECUTED_FP64_PER_CELL.values())
 FP64_PIPE_BUSY = {"rhs_states_kernel": 0.860, "rhs_face_kernel": 0.891, "rhs_div_kernel": 0.864}
-BYTES_PER_CELL_RHS_CURVED = 632 + 384 + 768
+BYTES_PER_CELL_RHS_CURVED = 816 + 384 + 768
 TRAFFIC_PER_CELL_MEASURED = (406.2e6 + 754.9e6 + 778.4e6) / 884736  # 2192 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
