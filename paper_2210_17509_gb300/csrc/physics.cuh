@@ -63,6 +63,40 @@ __device__ __forceinline__ float weno5<float>(float um2, float um1, float u0, fl
   return __fdividef(fmaf(a0, q0, fmaf(a1, q1, __fmul_rn(a2, q2))), __fadd_rn(__fadd_rn(a0, a1), a2));
 }
 
+// weno5<float> of two variables at once, one per lane of a float2, in the
+// paired FP32 instructions of this GPU (one fma / add / mul instruction for
+// both lanes, half the issue slots of the scalar form).  The operations are
+// weno5<float>'s in the same order; every negated operand is moved into a
+// constant (round-to-nearest is symmetric in sign: fl(-x) = -fl(x)), and the
+// divisions stay per lane, so each lane has the bits of weno5<float>.
+__device__ __forceinline__ float2 f2c(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 weno5_x2(float2 um2, float2 um1, float2 u0, float2 up1, float2 up2, float2 eps) {
+  const float c6 = 1.0f / 6.0f, c1312 = 13.0f / 12.0f;
+  // q0 = (2 um2 - 7 um1 + 11 u0) / 6
+  const float2 q0 = __fmul2_rn(__ffma2_rn(f2c(2.0f), um2, __ffma2_rn(f2c(-7.0f), um1, __fmul2_rn(f2c(11.0f), u0))),
+                               f2c(c6));
+  // q1 = (2 up1 + (5 u0 - um1)) / 6 = (-2 up1 + (um1 - 5 u0)) * (-1/6)
+  const float2 q1 = __fmul2_rn(__ffma2_rn(f2c(-2.0f), up1, __ffma2_rn(f2c(-5.0f), u0, um1)), f2c(-c6));
+  // q2 = (5 up1 + (2 u0 - up2)) / 6 = (-5 up1 + (up2 - 2 u0)) * (-1/6)
+  const float2 q2 = __fmul2_rn(__ffma2_rn(f2c(-5.0f), up1, __ffma2_rn(f2c(-2.0f), u0, up2)), f2c(-c6));
+  const float2 t0 = __ffma2_rn(f2c(-2.0f), um1, __fadd2_rn(um2, u0));
+  const float2 s0 = __ffma2_rn(f2c(3.0f), u0, __ffma2_rn(f2c(-4.0f), um1, um2));
+  const float2 t1 = __ffma2_rn(f2c(-2.0f), u0, __fadd2_rn(um1, up1));
+  const float2 s1 = __ffma2_rn(f2c(-1.0f), up1, um1);  // um1 - up1, rounded once
+  const float2 t2 = __ffma2_rn(f2c(-2.0f), up1, __fadd2_rn(u0, up2));
+  const float2 s2 = __ffma2_rn(f2c(3.0f), u0, __ffma2_rn(f2c(-4.0f), up1, up2));
+  const float2 e0 = __fadd2_rn(eps, __ffma2_rn(__fmul2_rn(f2c(c1312), t0), t0, __fmul2_rn(__fmul2_rn(f2c(0.25f), s0), s0)));
+  const float2 e1 = __fadd2_rn(eps, __ffma2_rn(__fmul2_rn(f2c(c1312), t1), t1, __fmul2_rn(__fmul2_rn(f2c(0.25f), s1), s1)));
+  const float2 e2 = __fadd2_rn(eps, __ffma2_rn(__fmul2_rn(f2c(c1312), t2), t2, __fmul2_rn(__fmul2_rn(f2c(0.25f), s2), s2)));
+  const float2 w0 = __fmul2_rn(e0, e0), w1 = __fmul2_rn(e1, e1), w2 = __fmul2_rn(e2, e2);
+  const float2 a0 = make_float2(__fdividef(0.1f, w0.x), __fdividef(0.1f, w0.y));
+  const float2 a1 = make_float2(__fdividef(0.6f, w1.x), __fdividef(0.6f, w1.y));
+  const float2 a2 = make_float2(__fdividef(0.3f, w2.x), __fdividef(0.3f, w2.y));
+  const float2 num = __ffma2_rn(a0, q0, __ffma2_rn(a1, q1, __fmul2_rn(a2, q2)));
+  const float2 den = __fadd2_rn(__fadd2_rn(a0, a1), a2);
+  return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
 // Both WENO5 states of the face between cells c-1 and c from the six values
 // u[c-3 .. c+2]: the left state from cell c-1, the right state (mirrored
 // stencil) from cell c.  In FP64 the two normalisations share one division:

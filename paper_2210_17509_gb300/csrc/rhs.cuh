@@ -101,6 +101,25 @@ __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, 
       pL[q + 1] = (T)(n[2] * (d[3] * x23));
       pR[q + 1] = (T)(n[3] * (d[2] * x23));
     }
+  } else if constexpr (RECON == GRMHD_WENO5 && sizeof(T) == 4) {
+    // FP32: two variables per paired instruction (weno5_x2, the bits of weno5<float>)
+    const float2 e2 = make_float2(eps, eps);
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const long long a = q * ncell + c, b = a + ncell;
+      const float2 um3 = make_float2(ld_prim<T>(src, a - 3 * stride), ld_prim<T>(src, b - 3 * stride));
+      const float2 um2 = make_float2(ld_prim<T>(src, a - 2 * stride), ld_prim<T>(src, b - 2 * stride));
+      const float2 um1 = make_float2(ld_prim<T>(src, a - stride), ld_prim<T>(src, b - stride));
+      const float2 u0 = make_float2(ld_prim<T>(src, a), ld_prim<T>(src, b));
+      const float2 up1 = make_float2(ld_prim<T>(src, a + stride), ld_prim<T>(src, b + stride));
+      const float2 up2 = make_float2(ld_prim<T>(src, a + 2 * stride), ld_prim<T>(src, b + 2 * stride));
+      const float2 vL = weno5_x2(um3, um2, um1, u0, up1, e2);
+      const float2 vR = weno5_x2(up2, up1, u0, um1, um2, e2);
+      pL[q] = vL.x;
+      pL[q + 1] = vL.y;
+      pR[q] = vR.x;
+      pR[q + 1] = vR.y;
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
