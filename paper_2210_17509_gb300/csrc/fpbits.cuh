@@ -1,0 +1,84 @@
+// FP64 <-> FP32 conversions on the integer pipe.
+//
+// On this GPU a conversion instruction between FP64 and FP32 occupies the
+// FP64 pipe for as long as an FP64 FMA (about two per SM per clock), and the
+// mixed recovery, which hands values back and forth between its FP32
+// predictor and its FP64 refinement, is bound by that pipe.  These functions
+// do the same conversions on the IEEE-754 bit fields with integer
+// instructions, about a dozen each on a pipe with 32 times the rate.
+//
+// Within the normal FP32 range they give the bits of the hardware
+// conversions (round to nearest, ties to even, for FP64 -> FP32; exact for
+// FP32 -> FP64).  Outside it: an FP32 result below 2^-126 in magnitude
+// flushes to a signed zero (the hardware conversion gives a subnormal), an
+// FP32 input below 2^-126 converts to a signed zero, overflow gives an
+// infinity and a NaN stays a NaN.
+#pragma once
+
+#include <stdint.h>
+
+namespace grmhd {
+
+// FP32 bits of x * 2^k rounded to nearest (ties to even), for the FP64 bits
+// (hi, lo) of x; k shifts the exponent (0 for a plain conversion) so that a
+// value whose FP32 image would underflow can be carried at a scale where it
+// does not, at no extra cost.  The arithmetic is on the two 32-bit words: a
+// mask of the sign bit of the 64-bit pattern of a computed FP64 value is
+// recognised by the compiler as an FP64 absolute value, which takes an FP64
+// instruction.
+__host__ __device__ __forceinline__ uint32_t f64_words_to_f32_bits(uint32_t hi, uint32_t lo, int k = 0) {
+  const uint32_t sign = hi & 0x80000000u, ha = hi & 0x7fffffffu;
+  // round the 52-bit fraction to 23 bits at bit 29 (a carry moves into the exponent)
+  const uint32_t l = lo + 0x0fffffffu + ((lo >> 29) & 1u);
+  const uint32_t h = ha + (l < lo ? 1u : 0u);
+  const int eb = (int)(h >> 20);  // biased FP64 exponent of the rounded value
+  const int e = eb + k;
+  uint32_t f = ((l >> 29) | (h << 3)) - ((uint32_t)(896 - k) << 23);
+  if (e < 897) f = 0u;  // below the normal FP32 range (zero included)
+  if (e > 1150 || eb >= 2047) f = (ha > 0x7ff00000u || (ha == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  return sign | f;
+}
+__host__ __device__ __forceinline__ uint32_t f64_bits_to_f32_bits(uint64_t b, int k = 0) {
+  return f64_words_to_f32_bits((uint32_t)(b >> 32), (uint32_t)b, k);
+}
+
+// FP64 bits (hi, lo) of the FP32 value with bits u (exact).
+__host__ __device__ __forceinline__ void f32_bits_to_f64_words(uint32_t u, uint32_t& hi, uint32_t& lo) {
+  const uint32_t a = u & 0x7fffffffu;
+  hi = (a >> 3) + (896u << 20);
+  lo = a << 29;
+  if (a < 0x00800000u) hi = lo = 0u;  // zero and subnormals
+  if (a >= 0x7f800000u) hi = 0x7ff00000u | ((a >> 3) & 0x000fffffu);
+  hi |= u & 0x80000000u;
+}
+__host__ __device__ __forceinline__ uint64_t f32_bits_to_f64_bits(uint32_t u) {
+  uint32_t hi, lo;
+  f32_bits_to_f64_words(u, hi, lo);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+#ifdef __CUDACC__
+// The FP64 value is split into, and assembled from, its two words by PTX
+// moves, which keep the bit arithmetic out of the compiler's FP64 pattern
+// matching.
+__device__ __forceinline__ float f64_to_f32i(double x, int k = 0) {
+  uint32_t lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+  return __uint_as_float(f64_words_to_f32_bits(hi, lo, k));
+}
+__device__ __forceinline__ double f32_to_f64i(float x) {
+  uint32_t hi, lo;
+  f32_bits_to_f64_words(__float_as_uint(x), hi, lo);
+  double r;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+// Unbiased exponent of a positive normal FP32 value, and the value with its
+// exponent replaced by 0 (its significand in [1, 2)).
+__device__ __forceinline__ int f32_exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127; }
+__device__ __forceinline__ float f32_significand(float x) {
+  return __uint_as_float((__float_as_uint(x) & 0x807fffffu) | 0x3f800000u);
+}
+#endif
+
+}  // namespace grmhd

@@ -2,6 +2,7 @@
 // the single-block kernels and the persistent batched kernels.
 #pragma once
 
+#include "fpbits.cuh"
 #include "physics.cuh"
 
 namespace grmhd {
@@ -202,8 +203,10 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
 // finishes to nr_tol, normally in one or two steps.
 __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParams& p, double& z, double& W) {
   const float gm1g = p.gm1gf;
-  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
-  float zf = (float)z, Wf = (float)W;
+  // conversions on the integer pipe (fpbits.cuh; the bits of the hardware conversions)
+  const float D = f64_to_f32i(in.D), B2 = f64_to_f32i(in.B2), BS2 = f64_to_f32i(in.BS2), S2 = f64_to_f32i(in.S2),
+              tau = f64_to_f32i(in.tau);
+  float zf = f64_to_f32i(z), Wf = f64_to_f32i(W);
   if (!(zf > 0.0f) || !(Wf >= 1.0f)) return false;
   bool converged = false;
   for (int it = 0; it < 30; ++it) {
@@ -229,8 +232,8 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
     if (conv) { converged = true; break; }
   }
   if (zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf)) {
-    z = (double)zf;
-    W = (double)Wf;
+    z = f32_to_f64i(zf);
+    W = f32_to_f64i(Wf);
     return converged;
   }
   return false;
@@ -262,7 +265,9 @@ __device__ __forceinline__ bool c2p_predict_fp32(const C2PIn& in, const DevParam
 __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams& p, float zf, float Wf, float Pg,
                                                double& z, double& W) {
   const float gm1g = p.gm1gf;
-  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2, tau = (float)in.tau;
+  // conversions between the FP32 and FP64 parts on the integer pipe (fpbits.cuh)
+  const float D = f64_to_f32i(in.D), B2 = f64_to_f32i(in.B2), BS2 = f64_to_f32i(in.BS2), S2 = f64_to_f32i(in.S2),
+              tau = f64_to_f32i(in.tau);
   bool active = zf > 0.0f && Wf >= 1.0f && isfinite(zf) && isfinite(Wf);
   bool converged = false;
   const unsigned mask = __activemask();
@@ -297,8 +302,8 @@ __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams&
       }
     }
   }
-  z = (double)zf;
-  W = (double)Wf;
+  z = f32_to_f64i(zf);
+  W = f32_to_f64i(Wf);
   if (converged) {
     // z and W are FP32 values: z^2, W^2 and W^2 - 1 are exact in FP64
     const double W2 = W * W, z2 = z * z, W2z2 = W2 * z2, u2 = W2 - 1.0;
@@ -309,7 +314,7 @@ __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams&
     const float r = __fdividef(1.0f, zf * Wf);
     const float iz = Wf * r, iW = zf * r;
     const float iW2 = iW * iW, iW3 = iW2 * iW, iz3 = iz * iz * iz;
-    const float v2 = (float)u2 * iW2;
+    const float v2 = f64_to_f32i(u2) * iW2;
     const float zb32 = zf + B2;
     const float J11 = 2.0f * zb32 * v2 + 2.0f * BS2 * zb32 * iz3;
     const float J12 = 2.0f * zb32 * zb32 * iW3;
@@ -317,11 +322,18 @@ __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams&
     const float J22 = -B2 * iW3 + gm1g * (D * iW2 - 2.0f * zf * iW3);
     const float idet = 1.0f / (J11 * J22 - J12 * J21);
     const float s = iz * iz * iW2;  // 1 / (W^2 z^2)
-    const float f1 = (float)F1 * s, f2 = (float)F2 * s;
+    // F1 and F2 are of order W^2 z^2 times the predictor's error and would
+    // underflow FP32 for small z: they are converted at the scale 2^k of s
+    // and multiplied by s's significand, an exact power-of-two shift that
+    // leaves f1 and f2 unchanged wherever FP32 F1 and F2 are normal
+    const bool sn = s > 0.0f && s <= 3.4028235e38f && s >= 1.17549435e-38f;
+    const int ks = sn ? f32_exponent(s) : 0;
+    const float sm = sn ? f32_significand(s) : s;
+    const float f1 = f64_to_f32i(F1, ks) * sm, f2 = f64_to_f32i(F2, ks) * sm;
     const float dz = (f1 * J22 - f2 * J12) * idet;
     const float dW = (J11 * f2 - J21 * f1) * idet;
     if (fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf) {
-      const double zn = z - (double)dz, Wn = W - (double)dW;
+      const double zn = z - f32_to_f64i(dz), Wn = W - f32_to_f64i(dW);
       if (zn > 0.0 && c2p_root_physical(in, p, zn, Wn)) {
         z = zn;
         W = Wn;
@@ -383,9 +395,9 @@ __device__ __forceinline__ int c2p_polytrope(const C2PIn& in, const DevParams& p
 // about 1e-6 from the guess, for the one FP64 step that follows.  Returns
 // false (W unchanged) if it does not get there in 8 steps.
 __device__ __forceinline__ bool c2p_polytrope_predict(const C2PIn& in, const DevParams& p, double& W) {
-  const float D = (float)in.D, B2 = (float)in.B2, BS2 = (float)in.BS2, S2 = (float)in.S2;
+  const float D = f64_to_f32i(in.D), B2 = f64_to_f32i(in.B2), BS2 = f64_to_f32i(in.BS2), S2 = f64_to_f32i(in.S2);
   const float gfac = p.gfacf, dzk = (float)((2.0 - p.gamma) * p.gfac);
-  float w = fmaxf((float)W, 1.0f);
+  float w = fmaxf(f64_to_f32i(W), 1.0f);
 #pragma unroll 1
   for (int it = 0; it < 8; ++it) {
     const float iw = 1.0f / w;
@@ -399,7 +411,7 @@ __device__ __forceinline__ bool c2p_polytrope_predict(const C2PIn& in, const Dev
     const float wn = fmaxf(w - f / df, 1.0f);
     if (!isfinite(wn)) return false;
     if (fabsf(wn - w) <= 1e-6f * wn) {
-      W = (double)wn;
+      W = f32_to_f64i(wn);
       return true;
     }
     w = wn;
@@ -467,13 +479,13 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
     float gf[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : (float)m.g[i];
+    for (int i = 0; i < 6; ++i) gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : f64_to_f32i(m.g[i]);
     float vl[3];
     lower(gf, v, vl);
     const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
     const float rg = pf[0], Pg = pf[4 * g.ncell];
     Wg = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
-    zg = (rg > 0.0f && Pg > 0.0f) ? (rg + p.gfacf * Pg) * Wg * Wg : (float)(tau + D + in.B2);
+    zg = (rg > 0.0f && Pg > 0.0f) ? (rg + p.gfacf * Pg) * Wg * Wg : f64_to_f32i(tau + D + in.B2);
     Pgf = Pg;
   } else {
     const double v[3] = {pc[g.ncell], pc[2 * g.ncell], pc[3 * g.ncell]};
@@ -489,7 +501,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   constexpr bool poly = POLY;
   if constexpr (POLY) {
     if (D > 0.0) {
-      if (F32IO) W = (double)Wg;
+      if (F32IO) W = f32_to_f64i(Wg);
       double tol_first = p.nr_tol;
       if (PREDICT && c2p_polytrope_predict(in, p, W)) tol_first = 1e-6;
       st = c2p_polytrope(in, p, z, W, tol_first);
@@ -501,16 +513,16 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     // of a cell whose pressure is round-off) is unchanged
     if (PREDICT && p.precision == GRMHD_MIXED && !(p.flags & GRMHD_NEWMAN_HAMLIN)) {
       if (!F32IO) {
-        zg = (float)z;
-        Wg = (float)W;
-        Pgf = (float)P0;
+        zg = f64_to_f32i(z);
+        Wg = f64_to_f32i(W);
+        Pgf = f64_to_f32i(P0);
       }
       st = c2p_solve_mixed(in, p, zg, Wg, Pgf, z, W);
     } else {
       if (F32IO) {
-        z = (double)zg;
-        W = (double)Wg;
-        P0 = (double)Pgf;
+        z = f32_to_f64i(zg);
+        W = f32_to_f64i(Wg);
+        P0 = f32_to_f64i(Pgf);
       }
       if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
       if (PREDICT) c2p_predict_fp32(in, p, z, W);
@@ -520,24 +532,25 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   if constexpr (!RESULT64) {
     // FP32 primitives from the FP64 root: 1/W, 1/z, 1/(z + B^2) from one division
     float outf[8];
-    const float Bf[3] = {(float)B[0], (float)B[1], (float)B[2]};
+    // (the conversions on the integer pipe, fpbits.cuh)
+    const float Bf[3] = {f64_to_f32i(B[0]), f64_to_f32i(B[1]), f64_to_f32i(B[2])};
     if (st != 2) {
-      const float zf = (float)z, Wf = (float)W, zbf = (float)(z + in.B2);
+      const float zf = f64_to_f32i(z), Wf = f64_to_f32i(W), zbf = f64_to_f32i(z + in.B2);
       const float X = 1.0f / (Wf * zf * zbf);
       const float iW = zf * zbf * X, iz = Wf * zbf * X, izb = Wf * zf * X;
-      const float rho = (float)D * iW;
+      const float rho = f64_to_f32i(D) * iW;
       const float P = poly ? rho * poly_k_rho_gm1<float>(p, rho) : p.gm1gf * (zf * iW * iW - rho);
-      const float bsz = (float)BS * iz;
+      const float bsz = f64_to_f32i(BS) * iz;
       float gf[6], guf[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : (float)m.g[i];
-        guf[i] = geom32 ? __ldg(geom32 + (17 + i) * g.ncell + c) : (float)m.gu[i];
+        gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : f64_to_f32i(m.g[i]);
+        guf[i] = geom32 ? __ldg(geom32 + (17 + i) * g.ncell + c) : f64_to_f32i(m.gu[i]);
       }
       float Blf[3], vlo[3], vu[3];
       lower(gf, Bf, Blf);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) vlo[i] = ((float)Sl[i] + bsz * Blf[i]) * izb;
+      for (int i = 0; i < 3; ++i) vlo[i] = (f64_to_f32i(Sl[i]) + bsz * Blf[i]) * izb;
       lower(guf, vlo, vu);
       const float v2 = vu[0] * vlo[0] + vu[1] * vlo[1] + vu[2] * vlo[2];
       if (rho >= p.rho_atmf && v2 < 1.0f && isfinite(P)) {
@@ -606,7 +619,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   for (int q = 0; q < 8; ++q) pc[q * g.ncell] = out[q];
   if (F32IO) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = (float)out[q];
+    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = f64_to_f32i(out[q]);
   }
   return st;
 }
