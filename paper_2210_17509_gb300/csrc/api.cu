@@ -165,7 +165,7 @@ int grmhd_rhs_cached(const grmhd_grid* grid, const grmhd_params* params, const d
   const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
   if (metric && !reuse && launch_geom_cache(g, metric, geom, !mixed, mcache, s) != cudaSuccess) return GRMHD_ERR_CUDA;
   if (mixed) {
-    if (launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (launch_prim_to_f32_pairs(g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     return cuda_status(launch_rhs_mixed_cached(g, p, prim32, static_cast<const float*>(geom), kij, metric != nullptr,
                                                ep, s));
   }
@@ -246,7 +246,7 @@ int rk_step_impl(const grmhd_grid* grid, const grmhd_params* params, int32_t sch
     const bool reuse = (p.flags & GRMHD_REUSE_GEOMETRY) != 0;
     if (metric && !reuse && launch_geom_cache(g, metric, geom, fast_fp64, mcache, s) != cudaSuccess)
       return GRMHD_ERR_CUDA;
-    if (fast_mixed && launch_to_f32(8 * g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (fast_mixed && launch_prim_to_f32_pairs(g.ncell, prim, prim32, s) != cudaSuccess) return GRMHD_ERR_CUDA;
   }
 
   RkStage st[4];

@@ -95,8 +95,11 @@ cudaError_t launch_fill_ghosts(const DevGrid& g, int bc, int nvar, double* field
 cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,
                                   double* prim, float* prim32, const double* mcache, const float* geom32,
                                   bool result64, int32_t* nfail, cudaStream_t s);
+// Ghost fill of the FP32 primitive pairs (nvar variables, nvar even, in the
+// [q/2][ncell] float2 layout of launch_prim_to_f32_pairs).
 cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s);
-cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s);
+// FP32 copy of the primitives [8][ncell] in pairs: [q/2][ncell] float2.
+cudaError_t launch_prim_to_f32_pairs(long long ncell, const double* prim, float* prim32, cudaStream_t s);
 cudaError_t launch_geom_cache(const DevGrid& g, const double* metric, void* geom, bool fp64, double* mcache,
                               cudaStream_t s);
 cudaError_t launch_con2prim_cached(const DevGrid& g, const DevParams& p, const double* cons, const double* metric,

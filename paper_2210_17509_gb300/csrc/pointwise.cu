@@ -74,15 +74,23 @@ __global__ void con2prim_mixed_kernel(DevGrid g, DevParams p, const double* __re
   if (nfail && myfail) atomicAdd(nfail, myfail);
 }
 
-__global__ void fill_ghosts_f32_kernel(DevGrid g, int bc, int nvar, float* __restrict__ f) {
+// The FP32 primitive copy of the mixed path holds the primitives in pairs,
+// [q/2][ncell] float2 (q even in .x, q odd in .y): its ghost fill copies
+// npair float2 components.
+__global__ void fill_ghosts_f32_kernel(DevGrid g, int bc, int npair, float2* __restrict__ f) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
        c += (long long)gridDim.x * blockDim.x)
-    fill_ghost_at(g, bc, nvar, f, c);
+    fill_ghost_at(g, bc, npair, f, c);
 }
 
-__global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* __restrict__ b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// FP32 pair copy of the FP64 primitives [8][n] (conversions on the integer
+// pipe, fpbits.cuh).
+__global__ void prim_to_f32_pairs_kernel(long long n, const double* __restrict__ a, float2* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      b[h * n + i] = make_float2(f64_to_f32i(__ldg(a + 2 * h * n + i)), f64_to_f32i(__ldg(a + (2 * h + 1) * n + i)));
+  }
 }
 
 // Geometry cache of a static metric (layout in rhs.cuh, kGeomCacheComps values per
@@ -230,12 +238,12 @@ cudaError_t launch_con2prim_mixed(const DevGrid& g, const DevParams& p, const do
 }
 
 cudaError_t launch_fill_ghosts_f32(const DevGrid& g, int bc, int nvar, float* field, cudaStream_t s) {
-  fill_ghosts_f32_kernel<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, bc, nvar, field);
+  fill_ghosts_f32_kernel<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, bc, nvar / 2, reinterpret_cast<float2*>(field));
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t s) {
-  to_f32_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);
+cudaError_t launch_prim_to_f32_pairs(long long ncell, const double* prim, float* prim32, cudaStream_t s) {
+  prim_to_f32_pairs_kernel<<<grid_blocks(ncell, 256), 256, 0, s>>>(ncell, prim, reinterpret_cast<float2*>(prim32));
   return cudaGetLastError();
 }
 

@@ -422,9 +422,9 @@ __device__ __forceinline__ bool c2p_polytrope_predict(const C2PIn& in, const Dev
 // Recovery of the interior cell c (Sec. 2.3).  The incoming primitives of
 // the cell are the Newton initial guess and are overwritten with the result.
 // Returns the status: 0 Newton, 1 bisection, 2 atmosphere, 3 pressure floor.
-// With PREDICT (mixed path) the guess comes from the FP32 primitives prim32,
-// an FP32 Newton predictor runs before the FP64 Newton, and the result is
-// also stored in prim32.  mcache (nullable) holds, per point, 1/sqrt(gamma)
+// With PREDICT (mixed path) the guess comes from the FP32 primitives prim32
+// (in pairs, [q/2][ncell] float2, q even in .x), an FP32 Newton predictor
+// runs before the FP64 Newton, and the result is also stored in prim32.  mcache (nullable) holds, per point, 1/sqrt(gamma)
 // and gamma^ij in FP64 (7 components), saving the per-call inverse.
 // F32IO (with PREDICT) takes the guess from and writes the result to prim32;
 // without it the guess is read from the FP64 primitives.  geom32 (nullable,
@@ -475,15 +475,17 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
   double W = 1.0, z = 0.0, P0 = 0.0;
   float Wg = 1.0f, zg = 0.0f, Pgf = 0.0f;  // the FP32 guess (F32IO)
   if (F32IO) {
-    const float* pf = prim32 + c;
-    const float v[3] = {pf[g.ncell], pf[2 * g.ncell], pf[3 * g.ncell]};
+    // the FP32 primitives in pairs, [q/2][ncell] float2 (q even in .x)
+    const float2* pf = reinterpret_cast<const float2*>(prim32) + c;
+    const float2 p01 = pf[0], p23 = pf[g.ncell], p45 = pf[2 * g.ncell];
+    const float v[3] = {p01.y, p23.x, p23.y};
     float gf[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) gf[i] = geom32 ? __ldg(geom32 + (4 + i) * g.ncell + c) : f64_to_f32i(m.g[i]);
     float vl[3];
     lower(gf, v, vl);
     const float v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
-    const float rg = pf[0], Pg = pf[4 * g.ncell];
+    const float rg = p01.x, Pg = p45.x;
     Wg = (v2g >= 0.0f && v2g < 1.0f) ? rsqrtf(1.0f - v2g) : 1.0f;
     zg = (rg > 0.0f && Pg > 0.0f) ? (rg + p.gfacf * Pg) * Wg * Wg : f64_to_f32i(tau + D + in.B2);
     Pgf = Pg;
@@ -575,8 +577,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     outf[5] = Bf[0];
     outf[6] = Bf[1];
     outf[7] = Bf[2];
+    float2* po = reinterpret_cast<float2*>(prim32) + c;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = outf[q];
+    for (int h = 0; h < 4; ++h) po[h * g.ncell] = make_float2(outf[2 * h], outf[2 * h + 1]);
     return st;
   }
   double out[8];
@@ -618,8 +621,9 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
 #pragma unroll
   for (int q = 0; q < 8; ++q) pc[q * g.ncell] = out[q];
   if (F32IO) {
+    float2* po = reinterpret_cast<float2*>(prim32) + c;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) prim32[q * g.ncell + c] = f64_to_f32i(out[q]);
+    for (int h = 0; h < 4; ++h) po[h * g.ncell] = make_float2(f64_to_f32i(out[2 * h]), f64_to_f32i(out[2 * h + 1]));
   }
   return st;
 }

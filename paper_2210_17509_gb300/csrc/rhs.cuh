@@ -71,8 +71,31 @@ template <class T>
 __device__ __forceinline__ T ld_prim(const SrcF64& s, long long i) { return (T)__ldg(s.prim + i); }
 template <class T>
 __device__ __forceinline__ T ld_prim(const SrcF64Co& s, long long i) { return (T)__ldcg(s.prim + i); }
-template <class T, class PT, class GT>
-__device__ __forceinline__ T ld_prim(const SrcCacheT<PT, GT>& s, long long i) { return (T)__ldg(s.prim + i); }
+template <class T, class GT>
+__device__ __forceinline__ T ld_prim(const SrcCacheT<double, GT>& s, long long i) { return (T)__ldg(s.prim + i); }
+
+// Primitive q of point i.  The FP64 sources hold the primitives as
+// [q][ncell]; the FP32 copy of the mixed path (SrcCacheT<float, GT>) holds
+// them in pairs, [q/2][ncell] float2 (q even in .x, q odd in .y), so that
+// the two variables of a paired FP32 instruction (weno5_x2) arrive in one
+// 8-byte load.
+template <class T, class S>
+__device__ __forceinline__ T ld_pq(const S& s, long long ncell, int q, long long i) {
+  return ld_prim<T>(s, q * ncell + i);
+}
+template <class T, class GT>
+__device__ __forceinline__ T ld_pq(const SrcCacheT<float, GT>& s, long long ncell, int q, long long i) {
+  return (T)__ldg(s.prim + 2 * ((q >> 1) * ncell + i) + (q & 1));
+}
+// Primitives 2h and 2h+1 of point i.
+template <class S>
+__device__ __forceinline__ float2 ld_pair(const S& s, long long ncell, int h, long long i) {
+  return make_float2(ld_pq<float>(s, ncell, 2 * h, i), ld_pq<float>(s, ncell, 2 * h + 1, i));
+}
+template <class GT>
+__device__ __forceinline__ float2 ld_pair(const SrcCacheT<float, GT>& s, long long ncell, int h, long long i) {
+  return __ldg(reinterpret_cast<const float2*>(s.prim) + h * ncell + i);
+}
 
 // Load the 8 primitives at the six-point stencil of the face between cell
 // c - stride and c, reconstruct both states.
@@ -106,13 +129,10 @@ __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, 
     const float2 e2 = make_float2(eps, eps);
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
-      const long long a = q * ncell + c, b = a + ncell;
-      const float2 um3 = make_float2(ld_prim<T>(src, a - 3 * stride), ld_prim<T>(src, b - 3 * stride));
-      const float2 um2 = make_float2(ld_prim<T>(src, a - 2 * stride), ld_prim<T>(src, b - 2 * stride));
-      const float2 um1 = make_float2(ld_prim<T>(src, a - stride), ld_prim<T>(src, b - stride));
-      const float2 u0 = make_float2(ld_prim<T>(src, a), ld_prim<T>(src, b));
-      const float2 up1 = make_float2(ld_prim<T>(src, a + stride), ld_prim<T>(src, b + stride));
-      const float2 up2 = make_float2(ld_prim<T>(src, a + 2 * stride), ld_prim<T>(src, b + 2 * stride));
+      const int h = q >> 1;
+      const float2 um3 = ld_pair(src, ncell, h, c - 3 * stride), um2 = ld_pair(src, ncell, h, c - 2 * stride);
+      const float2 um1 = ld_pair(src, ncell, h, c - stride), u0 = ld_pair(src, ncell, h, c);
+      const float2 up1 = ld_pair(src, ncell, h, c + stride), up2 = ld_pair(src, ncell, h, c + 2 * stride);
       const float2 vL = weno5_x2(um3, um2, um1, u0, up1, e2);
       const float2 vR = weno5_x2(up2, up1, u0, um1, um2, e2);
       pL[q] = vL.x;
@@ -123,15 +143,14 @@ __device__ __forceinline__ void reconstruct_face(const S& src, long long ncell, 
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const long long a = q * ncell + c;
       if constexpr (RECON == GRMHD_WENO5) {
-        const T um3 = ld_prim<T>(src, a - 3 * stride), um2 = ld_prim<T>(src, a - 2 * stride);
-        const T um1 = ld_prim<T>(src, a - stride), u0 = ld_prim<T>(src, a);
-        const T up1 = ld_prim<T>(src, a + stride), up2 = ld_prim<T>(src, a + 2 * stride);
+        const T um3 = ld_pq<T>(src, ncell, q, c - 3 * stride), um2 = ld_pq<T>(src, ncell, q, c - 2 * stride);
+        const T um1 = ld_pq<T>(src, ncell, q, c - stride), u0 = ld_pq<T>(src, ncell, q, c);
+        const T up1 = ld_pq<T>(src, ncell, q, c + stride), up2 = ld_pq<T>(src, ncell, q, c + 2 * stride);
         weno5_pair<T>(um3, um2, um1, u0, up1, up2, eps, pL[q], pR[q]);
       } else {
-        const T um2 = ld_prim<T>(src, a - 2 * stride), um1 = ld_prim<T>(src, a - stride);
-        const T u0 = ld_prim<T>(src, a), up1 = ld_prim<T>(src, a + stride);
+        const T um2 = ld_pq<T>(src, ncell, q, c - 2 * stride), um1 = ld_pq<T>(src, ncell, q, c - stride);
+        const T u0 = ld_pq<T>(src, ncell, q, c), up1 = ld_pq<T>(src, ncell, q, c + stride);
         pL[q] = um1 + T(0.5) * minmod<T>(um1 - um2, u0 - um1);
         pR[q] = u0 - T(0.5) * minmod<T>(u0 - um1, up1 - u0);
       }
@@ -215,13 +234,15 @@ __device__ __forceinline__ void reconstruct_cell_pair(const S& src, long long nc
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const long long a = (2 * h + k) * ncell + c;
+      const int q = 2 * h + k;
       T vm, vp;
       if constexpr (RECON == GRMHD_WENO5) {
-        weno5_cell((float)ld_prim<T>(src, a - 2 * stride), (float)ld_prim<T>(src, a - stride), (float)ld_prim<T>(src, a),
-                   (float)ld_prim<T>(src, a + stride), (float)ld_prim<T>(src, a + 2 * stride), (float)eps13, vm, vp);
+        weno5_cell((float)ld_pq<T>(src, ncell, q, c - 2 * stride), (float)ld_pq<T>(src, ncell, q, c - stride),
+                   (float)ld_pq<T>(src, ncell, q, c), (float)ld_pq<T>(src, ncell, q, c + stride),
+                   (float)ld_pq<T>(src, ncell, q, c + 2 * stride), (float)eps13, vm, vp);
       } else {
-        minmod_cell<T>(ld_prim<T>(src, a - stride), ld_prim<T>(src, a), ld_prim<T>(src, a + stride), vm, vp);
+        minmod_cell<T>(ld_pq<T>(src, ncell, q, c - stride), ld_pq<T>(src, ncell, q, c),
+                       ld_pq<T>(src, ncell, q, c + stride), vm, vp);
       }
       sR[(4 * h + 2 * k) * ne + e] = vm;
       sR[(4 * h + 2 * k + 1) * ne + e] = vp;
@@ -282,12 +303,12 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
     T vlL[3], vlR[3], v2L, v2R, rvL[3], rvR[3];
     if (!physical_state_v<T, CURVED>(pL, m, vlL, v2L)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+      for (int q = 0; q < 8; ++q) pL[q] = ld_pq<T>(src, g.ncell, q, c - stride);
       physical_state_v<T, CURVED>(pL, m, vlL, v2L);
     }
     if (!physical_state_v<T, CURVED>(pR, m, vlR, v2R)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+      for (int q = 0; q < 8; ++q) pR[q] = ld_pq<T>(src, g.ncell, q, c);
       physical_state_v<T, CURVED>(pR, m, vlR, v2R);
     }
     rotate_state(dir, pL, rL);
@@ -301,11 +322,11 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
     // FP32 (latency bound, 80 registers): fewer values live across the rotation
     if (!physical_state<T, CURVED>(pL, m)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) pL[q] = ld_prim<T>(src, q * g.ncell + c - stride);
+      for (int q = 0; q < 8; ++q) pL[q] = ld_pq<T>(src, g.ncell, q, c - stride);
     }
     if (!physical_state<T, CURVED>(pR, m)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) pR[q] = ld_prim<T>(src, q * g.ncell + c);
+      for (int q = 0; q < 8; ++q) pR[q] = ld_pq<T>(src, g.ncell, q, c);
     }
     rotate_state(dir, pL, rL);
     rotate_state(dir, pR, rR);
@@ -330,10 +351,10 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
                                             const T alpha, const T beta[3], const T gm[6], const T sg, const T gu[6],
                                             const T dA[3][10], T out[8]) {
   // fluid at the cell centre
-  const T rho = ld_prim<T>(src, c), P = ld_prim<T>(src, c + 4 * g.ncell);
-  const T v[3] = {ld_prim<T>(src, c + g.ncell), ld_prim<T>(src, c + 2 * g.ncell), ld_prim<T>(src, c + 3 * g.ncell)};
-  const T B[3] = {ld_prim<T>(src, c + 5 * g.ncell), ld_prim<T>(src, c + 6 * g.ncell),
-                  ld_prim<T>(src, c + 7 * g.ncell)};
+  const long long n = g.ncell;
+  const T rho = ld_pq<T>(src, n, 0, c), P = ld_pq<T>(src, n, 4, c);
+  const T v[3] = {ld_pq<T>(src, n, 1, c), ld_pq<T>(src, n, 2, c), ld_pq<T>(src, n, 3, c)};
+  const T B[3] = {ld_pq<T>(src, n, 5, c), ld_pq<T>(src, n, 6, c), ld_pq<T>(src, n, 7, c)};
   T vl[3], Bl[3], bl_[3];
   lower(gm, v, vl);
   lower(gm, B, Bl);
