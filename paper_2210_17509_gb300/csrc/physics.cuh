@@ -166,14 +166,15 @@ struct Weno5Cell {
   double P01, P12, A, B, C;  // weights (plus: P12, A, B; minus: P01, A, C)
 };
 
-__device__ __forceinline__ void weno5_cell_weights(double um2, double um1, double u0, double up1, double up2,
-                                                   double eps13, Weno5Cell& w) {
+// The weights from the first differences (dA .. dD) and the second
+// differences t0 = dB - dA, t1 = dC - dB, t2 = dD - dC of the stencil.
+__device__ __forceinline__ void weno5_cell_weights_dt(double dA, double dB, double dC, double dD, double t0,
+                                                      double t1, double t2, double eps13, Weno5Cell& w) {
   const double k313 = 3.0 / 13.0;
-  w.dA = __dsub_rn(um1, um2);
-  w.dB = __dsub_rn(u0, um1);
-  w.dC = __dsub_rn(up1, u0);
-  w.dD = __dsub_rn(up2, up1);
-  const double t0 = __dsub_rn(w.dB, w.dA), t1 = __dsub_rn(w.dC, w.dB), t2 = __dsub_rn(w.dD, w.dC);
+  w.dA = dA;
+  w.dB = dB;
+  w.dC = dC;
+  w.dD = dD;
   const double s0 = fma(3.0, w.dB, -w.dA), s1 = __dadd_rn(w.dB, w.dC), s2 = fma(-3.0, w.dC, w.dD);
   const double e0 = fma(t0, t0, fma(__dmul_rn(k313, s0), s0, eps13));
   const double e1 = fma(t1, t1, fma(__dmul_rn(k313, s1), s1, eps13));
@@ -184,6 +185,12 @@ __device__ __forceinline__ void weno5_cell_weights(double um2, double um1, doubl
   w.A = __dmul_rn(6.0, __dmul_rn(p02, p02));
   w.B = __dmul_rn(3.0, w.P01);
   w.C = __dmul_rn(3.0, w.P12);
+}
+
+__device__ __forceinline__ void weno5_cell_weights(double um2, double um1, double u0, double up1, double up2,
+                                                   double eps13, Weno5Cell& w) {
+  const double dA = __dsub_rn(um1, um2), dB = __dsub_rn(u0, um1), dC = __dsub_rn(up1, u0), dD = __dsub_rn(up2, up1);
+  weno5_cell_weights_dt(dA, dB, dC, dD, __dsub_rn(dB, dA), __dsub_rn(dC, dB), __dsub_rn(dD, dC), eps13, w);
 }
 
 __device__ __forceinline__ double weno5_cell_num_plus(const Weno5Cell& w) {
@@ -208,6 +215,33 @@ __device__ __forceinline__ void weno5_cell_parts(double um2, double um1, double 
   dp = __dadd_rn(__dadd_rn(w.P12, w.A), w.B);
   nm = weno5_cell_num_minus(w);
   dm = __dadd_rn(__dadd_rn(w.P01, w.A), w.C);
+}
+
+// weno5_cell_parts of two neighbouring cells i and i+1 of a line from the
+// six values u[i-2 .. i+3]: the two stencils share four values, and with
+// them three first differences and two second differences, which are formed
+// once (the same operations on the same operands, so each cell has the bits
+// of weno5_cell_parts).  Part 1 is skipped (outputs untouched) when !two.
+__device__ __forceinline__ void weno5_two_cell_parts(const double u[6], double eps13, bool two, double& nm0,
+                                                     double& dm0, double& np0, double& dp0, double& nm1, double& dm1,
+                                                     double& np1, double& dp1) {
+  const double d0 = __dsub_rn(u[1], u[0]), d1 = __dsub_rn(u[2], u[1]), d2 = __dsub_rn(u[3], u[2]),
+               d3 = __dsub_rn(u[4], u[3]);
+  const double t0 = __dsub_rn(d1, d0), t1 = __dsub_rn(d2, d1), t2 = __dsub_rn(d3, d2);
+  Weno5Cell w;
+  weno5_cell_weights_dt(d0, d1, d2, d3, t0, t1, t2, eps13, w);
+  np0 = weno5_cell_num_plus(w);
+  dp0 = __dadd_rn(__dadd_rn(w.P12, w.A), w.B);
+  nm0 = weno5_cell_num_minus(w);
+  dm0 = __dadd_rn(__dadd_rn(w.P01, w.A), w.C);
+  if (two) {
+    const double d4 = __dsub_rn(u[5], u[4]);
+    weno5_cell_weights_dt(d1, d2, d3, d4, t1, t2, __dsub_rn(d4, d3), eps13, w);
+    np1 = weno5_cell_num_plus(w);
+    dp1 = __dadd_rn(__dadd_rn(w.P12, w.A), w.B);
+    nm1 = weno5_cell_num_minus(w);
+    dm1 = __dadd_rn(__dadd_rn(w.P01, w.A), w.C);
+  }
 }
 
 // The numerator of one of the two states of weno5_cell_parts (plus: the

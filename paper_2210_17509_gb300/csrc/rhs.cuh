@@ -1101,29 +1101,76 @@ __global__ void __launch_bounds__(kTileThreads, MinCtas<T>::value) rhs_kernel(De
 // once, read once), against an FP64-pipe-bound pass.
 constexpr int kStatesThreads = 256, kFaceThreads = 128;
 
-// Cells of direction d's state box: n_d + 2 along d, interior across.
-__host__ __device__ __forceinline__ long long state_cells(const DevGrid& g, int d) {
-  return (long long)(g.n[0] + 2 * (d == 0)) * (g.n[1] + 2 * (d == 1)) * (g.n[2] + 2 * (d == 2));
+// State units of direction d: the cells -1 .. n_d of each line along d in
+// pairs ((n_d + 3) / 2 pairs, the last one a single cell when n_d is odd),
+// interior across.
+__host__ __device__ __forceinline__ long long state_units(const DevGrid& g, int d) {
+  return (long long)(d == 0 ? (g.n[0] + 3) / 2 : g.n[0]) * (d == 1 ? (g.n[1] + 3) / 2 : g.n[1]) *
+         (d == 2 ? (g.n[2] + 3) / 2 : g.n[2]);
 }
 // Faces of direction d: n_d + 1 along d, interior across.
 __host__ __device__ __forceinline__ long long face_count(const DevGrid& g, int d) {
   return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
 }
 
-// State items of a block: direction, then variable pair, then the cells of
-// the direction's box (x fastest).
+// State items of a block: direction, then variable pair, then the cell
+// pairs of the direction's lines (x fastest).
 __host__ __device__ __forceinline__ long long state_items(const DevGrid& g) {
-  return 4 * (state_cells(g, 0) + state_cells(g, 1) + state_cells(g, 2));
+  return 4 * (state_units(g, 0) + state_units(g, 1) + state_units(g, 2));
 }
 __host__ __device__ __forceinline__ long long face_items(const DevGrid& g) {
   return face_count(g, 0) + face_count(g, 1) + face_count(g, 2);
 }
 
-// State item t (0 <= t < state_items(g)) of pass 1.
+// The four states of weno5_cell_pair_states from the parts of its two
+// variables (one shared division).
+__device__ __forceinline__ void weno5_pair_states_from_parts(const double u0[2], const double nm[2],
+                                                             const double dm[2], const double np[2],
+                                                             const double dp[2], double v[4]) {
+  const double a0 = __dmul_rn(dm[0], dp[0]), a1 = __dmul_rn(dm[1], dp[1]);
+  const double X = 1.0 / __dmul_rn(__dmul_rn(6.0, a0), a1);
+  const double x0 = __dmul_rn(a1, X), x1 = __dmul_rn(a0, X);
+  v[0] = weno5_cell_state(u0[0], nm[0], __dmul_rn(dp[0], x0));
+  v[1] = weno5_cell_state(u0[0], np[0], __dmul_rn(dm[0], x0));
+  v[2] = weno5_cell_state(u0[1], nm[1], __dmul_rn(dp[1], x1));
+  v[3] = weno5_cell_state(u0[1], np[1], __dmul_rn(dm[1], x1));
+}
+
+// FP64 WENO5 of the two neighbouring cells c and c + stride of a line (the
+// second one only if two): both states of each for the primitives 2h and
+// 2h+1 into v0 and v1, as weno5_cell_pair_states forms them (the same bits),
+// from the six values of each variable that the two stencils cover.
+template <class S>
+__device__ __forceinline__ void weno5_two_cell_pair_states(const S& src, long long ncell, long long c,
+                                                           long long stride, int h, double eps13, bool two,
+                                                           double v0[4], double v1[4]) {
+  // parts of cell 0 (A) and cell 1 (B) for the two variables
+  double nmA[2], dmA[2], npA[2], dpA[2], uA[2], nmB[2], dmB[2], npB[2], dpB[2], uB[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long a = (2 * h + k) * ncell + c;
+    double u[6];
+    u[0] = ld_prim<double>(src, a - 2 * stride);
+    u[1] = ld_prim<double>(src, a - stride);
+    u[2] = ld_prim<double>(src, a);
+    u[3] = ld_prim<double>(src, a + stride);
+    u[4] = ld_prim<double>(src, a + 2 * stride);
+    u[5] = two ? ld_prim<double>(src, a + 3 * stride) : u[4];
+    weno5_two_cell_parts(u, eps13, two, nmA[k], dmA[k], npA[k], dpA[k], nmB[k], dmB[k], npB[k], dpB[k]);
+    uA[k] = u[2];
+    uB[k] = u[3];
+  }
+  weno5_pair_states_from_parts(uA, nmA, dmA, npA, dpA, v0);
+  if (two) weno5_pair_states_from_parts(uB, nmB, dmB, npB, dpB, v1);
+}
+
+// State item t (0 <= t < state_items(g)) of pass 1: one cell pair of a line
+// along d, one variable pair.  The two cells share four of their six stencil
+// values (and three first and two second differences of them).
 template <class S>
 __device__ __forceinline__ void rhs_state_item(const DevGrid& g, const DevParams& p, const S& src,
                                                double* __restrict__ St, long long t) {
-  const long long m0 = state_cells(g, 0), m1 = state_cells(g, 1), m2 = state_cells(g, 2);
+  const long long m0 = state_units(g, 0), m1 = state_units(g, 1), m2 = state_units(g, 2);
   int d = 0;
   long long r = t;
   if (r >= 4 * m0) {
@@ -1137,18 +1184,25 @@ __device__ __forceinline__ void rhs_state_item(const DevGrid& g, const DevParams
   const long long m = d == 0 ? m0 : (d == 1 ? m1 : m2);
   const int h = (int)(r / m);
   const long long l = r - h * m;
-  const int ex = g.n[0] + 2 * (d == 0), ey = g.n[1] + 2 * (d == 1);
+  const int ex = d == 0 ? (g.n[0] + 3) / 2 : g.n[0], ey = d == 1 ? (g.n[1] + 3) / 2 : g.n[1];
   const long long lxy = l / ex;
-  const int i = (int)(l - lxy * ex) - (d == 0);
-  const int j = (int)(lxy % ey) - (d == 1);
-  const int k = (int)(lxy / ey) - (d == 2);
+  int i = (int)(l - lxy * ex), j = (int)(lxy % ey), k = (int)(lxy / ey);
+  // the first cell of the pair along d: -1, 1, 3, ...
+  if (d == 0) i = 2 * i - 1;
+  else if (d == 1) j = 2 * j - 1;
+  else k = 2 * k - 1;
+  const bool two = (d == 0 ? i : (d == 1 ? j : k)) + 1 <= g.n[d];
   const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
   const long long stride = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
-  double v[4];
-  weno5_cell_pair_states<S>(src, g.ncell, c, stride, h, p.weno_eps * (12.0 / 13.0), v);
+  double v0[4], v1[4];
+  weno5_two_cell_pair_states<S>(src, g.ncell, c, stride, h, p.weno_eps * (12.0 / 13.0), two, v0, v1);
   double* o = St + (16LL * d + 4 * h) * g.ncell + c;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) o[q * g.ncell] = v[q];
+  for (int q = 0; q < 4; ++q) o[q * g.ncell] = v0[q];
+  if (two) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q * g.ncell + stride] = v1[q];
+  }
 }
 
 // Face item t (0 <= t < face_items(g)) of pass 2.
