@@ -73,6 +73,75 @@ __device__ __forceinline__ double f32_to_f64i(float x) {
   asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
   return r;
 }
+// FP64 comparisons and clamps on the integer pipe.  On this GPU an FP64
+// compare or min / max also takes an FP64-pipe slot, so the FP64-bound face
+// code makes these decisions on the bit patterns; the results are the IEEE
+// ones, NaN operands included.
+__device__ __forceinline__ void dwords(double x, uint32_t& hi, uint32_t& lo) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+__device__ __forceinline__ double dfromwords(uint32_t hi, uint32_t lo) {
+  double r;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+// x >= +0 and not a NaN (+0 and +inf included; -0 excluded)
+__device__ __forceinline__ bool dwords_nonneg(uint32_t hi, uint32_t lo) {
+  return hi < 0x7ff00000u || (hi == 0x7ff00000u && lo == 0u);
+}
+// x > 0 (IEEE)
+__device__ __forceinline__ bool dgt0i(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  return dwords_nonneg(hi, lo) && (hi | lo) != 0u;
+}
+// x < 1 (IEEE)
+__device__ __forceinline__ bool dlt1i(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  const uint32_t ha = hi & 0x7fffffffu;
+  const bool nan = ha > 0x7ff00000u || (ha == 0x7ff00000u && lo != 0u);
+  return hi < 0x3ff00000u || (hi >= 0x80000000u && !nan);
+}
+// 0 <= x < c for a positive constant c, i.e. x < c for x >= 0 (IEEE)
+__device__ __forceinline__ bool dltposi(double x, double c) {
+  uint32_t hi, lo, ch, cl;
+  dwords(x, hi, lo);
+  dwords(c, ch, cl);
+  return hi < ch || (hi == ch && lo < cl);
+}
+// fmax(x, 0) (+0 for x <= 0 or a NaN)
+__device__ __forceinline__ double dmax0i(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  const bool keep = dwords_nonneg(hi, lo);
+  return dfromwords(keep ? hi : 0u, keep ? lo : 0u);
+}
+// fmax(0, fmax(a, b)): the bit patterns of non-negative values order like
+// the values; a negative value or a NaN counts as +0.
+__device__ __forceinline__ double dmax0_2i(double a, double b) {
+  uint32_t ha, la, hb, lb;
+  dwords(a, ha, la);
+  dwords(b, hb, lb);
+  if (!dwords_nonneg(ha, la)) ha = la = 0u;
+  if (!dwords_nonneg(hb, lb)) hb = lb = 0u;
+  const bool tb = hb > ha || (hb == ha && lb > la);
+  return dfromwords(tb ? hb : ha, tb ? lb : la);
+}
+// fmin(0, fmin(a, b)) = -fmax(0, fmax(-a, -b)), +0 when neither is negative
+__device__ __forceinline__ double dmin0_2i(double a, double b) {
+  uint32_t ha, la, hb, lb;
+  dwords(a, ha, la);
+  dwords(b, hb, lb);
+  ha ^= 0x80000000u;
+  hb ^= 0x80000000u;
+  if (!dwords_nonneg(ha, la)) ha = la = 0u;
+  if (!dwords_nonneg(hb, lb)) hb = lb = 0u;
+  const bool tb = hb > ha || (hb == ha && lb > la);
+  const uint32_t h = tb ? hb : ha, l = tb ? lb : la;
+  return dfromwords((h | l) != 0u ? h ^ 0x80000000u : 0u, l);
+}
+
 // Unbiased exponent of a positive normal FP32 value, and the value with its
 // exponent replaced by 0 (its significand in [1, 2)).
 __device__ __forceinline__ int f32_exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127; }

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include "fpbits.cuh"
 #include "internal.h"
 
 namespace grmhd {
@@ -443,7 +444,9 @@ __device__ __forceinline__ bool physical_state_v(const T pr[8], const Geom<T>& m
     for (int i = 0; i < 3; ++i) vl[i] = v[i];
   }
   v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
-  return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
+  // FP64: the comparisons on the integer pipe (fpbits.cuh)
+  if constexpr (sizeof(T) == 8) return dgt0i(pr[0]) && dgt0i(pr[4]) && dlt1i(v2);
+  else return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
 }
 
 template <class T, bool CURVED>
@@ -559,7 +562,9 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   const T hmn = hs - Na;       // (1 - a^2) hs
   const T gdd = CURVED ? m.gup_dd : T(1);
   const T vd = v[DIR];
-  const T Q = xmax(gdd * dsp - vd * vd * hmn, T(0));
+  T Q = gdd * dsp - vd * vd * hmn;
+  if constexpr (sizeof(T) == 8) Q = dmax0i(Q);  // the clamp on the integer pipe (fpbits.cuh)
+  else Q = xmax(Q, T(0));
   const T sq = xsqrt(Na * omv2 * Q);
   const T c0 = vd * hmn;
   if (SHARED) {
@@ -594,11 +599,21 @@ __device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side
 // with the mean physical flux.
 template <class T>
 __device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side<T>& R, T alpha, T sg, T F[8]) {
-  const T xm = xmin(T(0), xmin(L.lm, R.lm));
-  const T xp = xmax(T(0), xmax(L.lp, R.lp));
+  T xm, xp;
+  if constexpr (sizeof(T) == 8) {
+    // FP64: the bounds and the test on the integer pipe (fpbits.cuh)
+    xm = dmin0_2i(L.lm, R.lm);
+    xp = dmax0_2i(L.lp, R.lp);
+  } else {
+    xm = xmin(T(0), xmin(L.lm, R.lm));
+    xp = xmax(T(0), xmax(L.lp, R.lp));
+  }
   const T den = xp - xm;
   const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
-  if (den < tiny) {
+  bool degenerate;
+  if constexpr (sizeof(T) == 8) degenerate = dltposi(den, tiny);
+  else degenerate = den < tiny;
+  if (degenerate) {
     const T h = T(0.5) * alpha * sg;
 #pragma unroll
     for (int q = 0; q < 8; ++q) F[q] = h * (L.F[q] + R.F[q]);
