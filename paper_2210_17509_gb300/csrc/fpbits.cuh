@@ -110,6 +110,46 @@ __device__ __forceinline__ bool dltposi(double x, double c) {
   dwords(c, ch, cl);
   return hi < ch || (hi == ch && lo < cl);
 }
+// x finite (IEEE)
+__device__ __forceinline__ bool dfinitei(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  return (hi & 0x7ff00000u) != 0x7ff00000u;
+}
+// x >= 1 (IEEE)
+__device__ __forceinline__ bool dge1i(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  return dwords_nonneg(hi, lo) && hi >= 0x3ff00000u;
+}
+// x >= 0 (IEEE: -0 included)
+__device__ __forceinline__ bool dge0i(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  return dwords_nonneg(hi, lo) || (hi == 0x80000000u && lo == 0u);
+}
+// x > c and x >= c (IEEE) for a bound c >= +0 that is not a NaN
+__device__ __forceinline__ bool dgtci(double x, double c) {
+  uint32_t hi, lo, ch, cl;
+  dwords(x, hi, lo);
+  dwords(c, ch, cl);
+  return dwords_nonneg(hi, lo) && (hi > ch || (hi == ch && lo > cl));
+}
+__device__ __forceinline__ bool dgeci(double x, double c) {
+  uint32_t hi, lo, ch, cl;
+  dwords(x, hi, lo);
+  dwords(c, ch, cl);
+  return (dwords_nonneg(hi, lo) && (hi > ch || (hi == ch && lo >= cl))) ||
+         (hi == 0x80000000u && lo == 0u && (ch | cl) == 0u);
+}
+// |a| <= c (IEEE) for a bound c >= +0 that is not a NaN
+__device__ __forceinline__ bool dabsleci(double a, double c) {
+  uint32_t hi, lo, ch, cl;
+  dwords(a, hi, lo);
+  dwords(c, ch, cl);
+  hi &= 0x7fffffffu;
+  return dwords_nonneg(hi, lo) && (hi < ch || (hi == ch && lo <= cl));
+}
 // fmax(x, 0) (+0 for x <= 0 or a NaN)
 __device__ __forceinline__ double dmax0i(double x) {
   uint32_t hi, lo;

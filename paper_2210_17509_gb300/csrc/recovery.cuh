@@ -105,7 +105,8 @@ static __device__ int c2p_bisect(const C2PIn& in, const DevParams& p, double& z,
 // Otherwise (the iteration can settle on a spurious root from a poor guess,
 // e.g. next to an atmosphere cell) the bracketed bisection decides.
 __device__ __forceinline__ bool c2p_root_physical(const C2PIn& in, const DevParams& p, double z, double W) {
-  return W >= 1.0 && isfinite(W) && z > in.D * W && in.D >= p.rho_atm * W;
+  // (the comparisons on the integer pipe, fpbits.cuh; D W and rho_atm W are >= 0)
+  return dge1i(W) && dfinitei(W) && dgtci(z, in.D * W) && dgeci(in.D, p.rho_atm * W);
 }
 
 // Newman-Hamlin iteration over the pressure (Sec. 2.3, the paper's fallback
@@ -167,7 +168,8 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
   const double D = in.D, B2 = in.B2, BS2 = in.BS2, S2 = in.S2, tau = in.tau;
   bool ok = false;
   const bool newman_first = (p.flags & GRMHD_NEWMAN_HAMLIN) != 0;
-  if (!newman_first && z > 0.0 && W >= 1.0 && isfinite(z) && isfinite(W)) {
+  // (the comparisons on the integer pipe, fpbits.cuh)
+  if (!newman_first && dgt0i(z) && dge1i(W) && dfinitei(z) && dfinitei(W)) {
     for (int it = 0; it < p.nr_maxit; ++it) {
       const double izW = 1.0 / (z * W);  // 1/z and 1/W from one division
       const double iz = W * izW, iW = z * izW;
@@ -182,11 +184,11 @@ static __device__ int c2p_solve(const C2PIn& in, const DevParams& p, double& z, 
       const double idet = 1.0 / (J11 * J22 - J12 * J21);
       const double dz = (f1 * J22 - f2 * J12) * idet;
       const double dW = (J11 * f2 - J21 * f1) * idet;
-      if (!isfinite(dz) || !isfinite(dW)) break;
-      const bool conv = fabs(dz) <= p.nr_tol * z && fabs(dW) <= p.nr_tol * W;
+      if (!dfinitei(dz) || !dfinitei(dW)) break;
+      const bool conv = dabsleci(dz, p.nr_tol * z) && dabsleci(dW, p.nr_tol * W);  // z > 0, W >= 1
       double zn = z - dz, Wn = W - dW;
-      if (!(zn > 0.0)) zn = 0.5 * z;
-      if (!(Wn >= 1.0)) Wn = 0.5 * (W + 1.0);
+      if (!dgt0i(zn)) zn = 0.5 * z;
+      if (!dge1i(Wn)) Wn = 0.5 * (W + 1.0);
       z = zn;
       W = Wn;
       if (conv) { ok = true; break; }
@@ -334,7 +336,7 @@ __device__ __forceinline__ int c2p_solve_mixed(const C2PIn& in, const DevParams&
     const float dW = (J11 * f2 - J21 * f1) * idet;
     if (fabsf(dz) <= 1e-6f * zf && fabsf(dW) <= 1e-6f * Wf) {
       const double zn = z - f32_to_f64i(dz), Wn = W - f32_to_f64i(dW);
-      if (zn > 0.0 && c2p_root_physical(in, p, zn, Wn)) {
+      if (dgt0i(zn) && c2p_root_physical(in, p, zn, Wn)) {
         z = zn;
         W = Wn;
         return 0;
@@ -495,20 +497,20 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     lower(m.g, v, vl);
     const double v2g = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
     const double rg = pc[0], Pg = pc[4 * g.ncell];
-    W = (v2g >= 0.0 && v2g < 1.0) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
-    z = (rg > 0.0 && Pg > 0.0) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
+    W = (dge0i(v2g) && dlt1i(v2g)) ? 1.0 / sqrt(1.0 - v2g) : 1.0;
+    z = (dgt0i(rg) && dgt0i(Pg)) ? (rg + p.gfac * Pg) * W * W : (tau + D + in.B2);
     P0 = Pg;
   }
   int st = 2;
   constexpr bool poly = POLY;
   if constexpr (POLY) {
-    if (D > 0.0) {
+    if (dgt0i(D)) {
       if (F32IO) W = f32_to_f64i(Wg);
       double tol_first = p.nr_tol;
       if (PREDICT && c2p_polytrope_predict(in, p, W)) tol_first = 1e-6;
       st = c2p_polytrope(in, p, z, W, tol_first);
     }
-  } else if (D > 0.0 && tau + D > 0.0) {
+  } else if (dgt0i(D) && dgt0i(tau + D)) {
     // mixed: the FP32 predictor and one refinement step (c2p_solve_mixed);
     // FP64: the predictor only supplies the starting point, and the FP64
     // Newton still converges to nr_tol, so the root (and the floor decision
@@ -526,7 +528,7 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
         W = f32_to_f64i(Wg);
         P0 = f32_to_f64i(Pgf);
       }
-      if (!(P0 > 0.0) || !isfinite(P0)) P0 = p.gm1g * (tau + D);
+      if (!dgt0i(P0) || !dfinitei(P0)) P0 = p.gm1g * (tau + D);
       if (PREDICT) c2p_predict_fp32(in, p, z, W);
       st = c2p_solve(in, p, z, W, P0);
     }
@@ -596,13 +598,13 @@ __device__ __forceinline__ int con2prim_at(const DevGrid& g, const DevParams& p,
     for (int i = 0; i < 3; ++i) vlo[i] = (Sl[i] + bsz * Bl[i]) * izb;
     lower(m.gu, vlo, vu);
     const double v2 = vu[0] * vlo[0] + vu[1] * vlo[1] + vu[2] * vlo[2];
-    if (rho >= p.rho_atm && v2 < 1.0 && isfinite(P)) {
+    if (dgeci(rho, p.rho_atm) && dlt1i(v2) && dfinitei(P)) {
       out[0] = rho;
       out[1] = vu[0];
       out[2] = vu[1];
       out[3] = vu[2];
       out[4] = P;
-      if (!(P > 0.0)) {  // valid density and velocity, non-positive pressure: floor
+      if (!dgt0i(P)) {  // valid density and velocity, non-positive pressure: floor
         out[4] = p.p_atm;
         st = 3;
       }
