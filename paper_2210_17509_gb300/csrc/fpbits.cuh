@@ -182,6 +182,39 @@ __device__ __forceinline__ double dmin0_2i(double a, double b) {
   return dfromwords((h | l) != 0u ? h ^ 0x80000000u : 0u, l);
 }
 
+// FP64 reciprocal and square root for the FP64-pipe-bound kernels, from the
+// hardware's 20-bit approximations (PTX rcp.approx.ftz.f64 and
+// rsqrt.approx.ftz.f64, no FP64-pipe instructions) and one Newton-Raphson
+// step carried to second order: with e = 1 - x r0 the reciprocal is
+// r0 / (1 - e) = r0 (1 + e + e^2 + ...), and with e = 1 - x y0^2 the square
+// root is x y0 (1 - e)^(-1/2) = x y0 (1 + e/2 + 3 e^2 / 8 + ...).  The
+// neglected terms are of order e^3 ~ 2^-60, so the results are within one
+// ulp of the exact value (faithful rounding, not always the correctly
+// rounded value) for 3 and 5 FP64 operations, against 5 and 8 for the
+// correctly rounded library sequences.  Operands outside the range where the
+// approximation and the result are normal (zero, subnormals, results that
+// would be subnormal, infinities, NaN, negative square-root operands) take
+// the library operation.
+__device__ __forceinline__ double rcp_nr(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  if (((hi >> 20) & 0x7ffu) - 1u >= 2044u) return 1.0 / x;  // |x| < 2^-1022 or >= 2^1022, inf, NaN
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
+  const double e = fma(-x, r0, 1.0);
+  return fma(fma(e, e, e), r0, r0);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  uint32_t hi, lo;
+  dwords(x, hi, lo);
+  if ((hi >> 20) - 1u >= 2046u) return sqrt(x);  // negative, zero, subnormal, inf, NaN
+  double y0;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+  const double t = x * y0;
+  const double e = fma(-t, y0, 1.0);
+  return fma(t, fma(0.375, e, 0.5) * e, t);
+}
+
 // Unbiased exponent of a positive normal FP32 value, and the value with its
 // exponent replaced by 0 (its significand in [1, 2)).
 __device__ __forceinline__ int f32_exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127; }

@@ -565,7 +565,9 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   T Q = gdd * dsp - vd * vd * hmn;
   if constexpr (sizeof(T) == 8) Q = dmax0i(Q);  // the clamp on the integer pipe (fpbits.cuh)
   else Q = xmax(Q, T(0));
-  const T sq = xsqrt(Na * omv2 * Q);
+  T sq;
+  if constexpr (sizeof(T) == 8) sq = sqrt_nr(Na * omv2 * Q);  // fpbits.cuh
+  else sq = xsqrt(Na * omv2 * Q);
   const T c0 = vd * hmn;
   if (SHARED) {
     o.lp = c0 + sq;
@@ -585,7 +587,9 @@ template <class T, bool CURVED, int DIR>
 __device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side<T>& R) {
   const T alpha = CURVED ? m.alpha : T(1);
   const T bd = CURVED ? m.beta[DIR] : T(0);
-  const T X = alpha / (L.sden * R.sden);
+  T X;
+  if constexpr (sizeof(T) == 8) X = alpha * rcp_nr(L.sden * R.sden);  // fpbits.cuh
+  else X = alpha / (L.sden * R.sden);
   const T iL = R.sden * X, iR = L.sden * X;
   L.lp = iL * L.lp - bd;
   L.lm = iL * L.lm - bd;
@@ -619,7 +623,9 @@ __device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side
     for (int q = 0; q < 8; ++q) F[q] = h * (L.F[q] + R.F[q]);
     return;
   }
-  const T s = sg / den;
+  T s;
+  if constexpr (sizeof(T) == 8) s = sg * rcp_nr(den);  // fpbits.cuh
+  else s = sg / den;
   const T axp = alpha * xp, axm = alpha * xm, xpm = xp * xm;
 #pragma unroll
   for (int q = 0; q < 8; ++q) F[q] = (axp * L.F[q] - axm * R.F[q] + xpm * (R.U[q] - L.U[q])) * s;
