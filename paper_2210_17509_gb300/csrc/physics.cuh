@@ -597,8 +597,9 @@ __device__ __forceinline__ void finish_speeds(const Geom<T>& m, Side<T>& L, Side
   R.lm = iR * R.lm - bd;
 }
 
-// HLLE flux (Sec. 2.3) from SCALED side states: F = sqrt(gamma) [alpha (xp F~L
-// - xm F~R) + xp xm (U~R - U~L)] / (xp - xm), the common factors applied once;
+// HLLE flux (Sec. 2.3) from SCALED side states of a face whose normal is the
+// first axis: F = sqrt(gamma) [alpha (xp F~L - xm F~R) + xp xm (U~R - U~L)] /
+// (xp - xm), the common factors applied once;
 // 1e-300 (double) / 1e-30 (float) guards the degenerate fan xi+ = xi- = 0
 // with the mean physical flux.
 template <class T>
@@ -626,9 +627,18 @@ __device__ __forceinline__ void hlle_combine_scaled(const Side<T>& L, const Side
   T s;
   if constexpr (sizeof(T) == 8) s = sg * rcp_nr(den);  // fpbits.cuh
   else s = sg / den;
-  const T axp = alpha * xp, axm = alpha * xm, xpm = xp * xm;
+  // the factor s taken into the three coefficients once
+  const T as = alpha * s;
+  const T axp = as * xp, axm = as * xm, xpm = (xp * xm) * s;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) F[q] = (axp * L.F[q] - axm * R.F[q] + xpm * (R.U[q] - L.U[q])) * s;
+  for (int q = 0; q < 8; ++q) {
+    if (q == 5) {
+      // the normal field component (the first axis of the rotated frame) has no flux on either side
+      F[q] = xpm * (R.U[q] - L.U[q]);
+    } else {
+      F[q] = fma(axp, L.F[q], fma(-axm, R.F[q], xpm * (R.U[q] - L.U[q])));
+    }
+  }
 }
 
 
