@@ -17,6 +17,14 @@ of DADD, DMUL and DFMA thread instructions of the three FP64 RHS kernels
 n_d, so its count per interior cell falls with n as (n + 2) / n; at 256^3 it
 is 0.8% below the 96^3 figure, which is used as it stands.
 
+The algorithmic figure can exceed the FMA peak: the restatement forms every
+face value on its own, where the kernels share work exactly (a cell's two
+WENO5 states share their smoothness indicators and weights, neighbouring
+cells of a line their first and second differences, the two sides of a face
+1/alpha and one division), and it counts an add or a multiply as one flop,
+as the hardware does, but two for each of its FMAs only where it writes one.
+The FP64-pipe busy fractions (ncu) state the bound.
+
 The FP64 RHS of the cached paths runs in three passes: rhs_states_kernel
 (WENO5 states of every cell per direction), rhs_face_kernel (face metric,
 side states and HLLE of every face once) and rhs_div_kernel (divergence,
@@ -35,8 +43,8 @@ buffers: 208 B).
 
 Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
-cells): 406.2 + 754.9 + 778.4 MB = 1939.5 MB, 2192 B per cell; traffic grows
-with the cell count, so a launch on n^3 cells is about 2192 n^3 B.
+cells): 462.9 + 830.2 + 778.6 MB = 2071.7 MB, 2342 B per cell; traffic grows
+with the cell count, so a launch on n^3 cells is about 2342 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -54,12 +62,12 @@ with open(os.path.join(HERE, "flop_counts.json")) as _f:
     FLOPS_PER_CELL_RHS_CURVED_WENO5 = int(json.load(_f)["rhs_curved_weno5_per_cell"])
 
 # ncu thread-instruction counts per interior cell at 96^3 (DADD, DMUL, DFMA)
-EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (294, 516, 551), "rhs_face_kernel": (106, 294, 427),
+EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (233, 516, 551), "rhs_face_kernel": (76, 270, 370),
                           "rhs_div_kernel": (37, 81, 155)}
 EXECUTED_FLOPS_PER_CELL = sum(a + m + 2 * f for a, m, f in EXECUTED_FP64_PER_CELL.values())
-FP64_PIPE_BUSY = {"rhs_states_kernel": 0.860, "rhs_face_kernel": 0.891, "rhs_div_kernel": 0.864}
+FP64_PIPE_BUSY = {"rhs_states_kernel": 0.863, "rhs_face_kernel": 0.896, "rhs_div_kernel": 0.865}
 BYTES_PER_CELL_RHS_CURVED = 816 + 384 + 768
-TRAFFIC_PER_CELL_MEASURED = (406.2e6 + 754.9e6 + 778.4e6) / 884736  # 2192 B per cell
+TRAFFIC_PER_CELL_MEASURED = (462.9e6 + 830.2e6 + 778.6e6) / 884736  # 2342 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
 HBM_FALLBACK_GBS = 6800.0
