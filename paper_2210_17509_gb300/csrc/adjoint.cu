@@ -144,36 +144,72 @@ __device__ __forceinline__ void cons_jacobian(const DevGrid& g, const DevParams&
     for (int j = 0; j < 9; ++j) J[i][j] = U[i].d[j];
 }
 
-// Solve A^T x = b (8x8, partial pivoting) in place: b becomes x.
+// Solve A^T x = b in place (b becomes x) for A = dU/dP (8x8), using its
+// block form: the conserved field is sqrt(gamma) B, so the rows of U^5..7
+// are sqrt(gamma) times the unit rows of B and A = [[A11, A12], [0, sg I]].
+// Then A11^T x1 = b1 (5x5, partial pivoting) and x2 = (b2 - A12^T x1) / sg.
+// Everything is unrolled with compile-time indices (the row exchanges are
+// selects), so the matrix stays in registers; the pivot search compares
+// magnitudes on the integer pipe.
 __device__ __forceinline__ bool solve_transposed8(const double J[8][9], double b[8]) {
-  double a[8][8];
+  constexpr int N = 5;
+  double a[N][N], ip[N];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < N; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) a[r][c] = J[c][r];  // A^T
-  for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < N; ++c) a[r][c] = J[c][r];  // A11^T
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
     int piv = c;
-    double best = fabs(a[c][c]);
-    for (int r = c + 1; r < 8; ++r)
-      if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); piv = r; }
-    if (!(best > 0.0)) return false;
-    if (piv != c) {
-      for (int k = 0; k < 8; ++k) { const double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t; }
-      const double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    uint32_t bh, bl;
+    dwords(a[c][c], bh, bl);
+    bh &= 0x7fffffffu;
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      uint32_t h, l;
+      dwords(a[r][c], h, l);
+      h &= 0x7fffffffu;
+      if (h > bh || (h == bh && l > bl)) { bh = h; bl = l; piv = r; }
     }
-    const double ip = 1.0 / a[c][c];
-    for (int r = c + 1; r < 8; ++r) {
-      const double f = a[r][c] * ip;
-      if (f != 0.0) {
-        for (int k = c; k < 8; ++k) a[r][k] -= f * a[c][k];
-        b[r] -= f * b[c];
+    if ((bh | bl) == 0u || bh >= 0x7ff00000u) return false;  // zero pivot, or not finite
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const bool sw = piv == r;
+#pragma unroll
+      for (int k = c; k < N; ++k) {
+        const double t = a[c][k];
+        a[c][k] = sw ? a[r][k] : t;
+        a[r][k] = sw ? t : a[r][k];
       }
+      const double t = b[c];
+      b[c] = sw ? b[r] : t;
+      b[r] = sw ? t : b[r];
+    }
+    ip[c] = 1.0 / a[c][c];
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const double f = a[r][c] * ip[c];
+#pragma unroll
+      for (int k = c + 1; k < N; ++k) a[r][k] -= f * a[c][k];
+      b[r] -= f * b[c];
     }
   }
-  for (int r = 7; r >= 0; --r) {
+#pragma unroll
+  for (int r = N - 1; r >= 0; --r) {
     double s = b[r];
-    for (int k = r + 1; k < 8; ++k) s -= a[r][k] * b[k];
-    b[r] = s / a[r][r];
+#pragma unroll
+    for (int k = r + 1; k < N; ++k) s -= a[r][k] * b[k];
+    b[r] = s * ip[r];
+  }
+  const double sg = J[5][5];
+  if (!dgt0i(sg) || !dfinitei(sg)) return false;
+  const double isg = 1.0 / sg;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double s = b[5 + k];
+#pragma unroll
+    for (int i = 0; i < N; ++i) s -= J[i][5 + k] * b[i];
+    b[5 + k] = s * isg;
   }
   return true;
 }
@@ -356,7 +392,7 @@ __device__ __forceinline__ void weno5_value_grad2(const double uA[5], const doub
   weno5_vg_parts(uA, eps13, A);
   weno5_vg_parts(uB, eps13, B);
   const double xa = A.ws * A.ee, xb = B.ws * B.ee;
-  const double Z = 1.0 / (xa * xb);
+  const double Z = rcp_nr(xa * xb);
   const double ra = xb * Z, rb = xa * Z;
   vA = weno5_vg_finish(A, A.ee * ra, A.ws * ra, grA);
   vB = weno5_vg_finish(B, B.ee * rb, B.ws * rb, grB);
@@ -383,8 +419,8 @@ __device__ __forceinline__ double minmod_left_adj(double um2, double um1, double
 // sq = sqrt(Na (1 - v^2) Q), c0 = vd hmn.
 template <bool CURVED, int DIR>
 __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<double>& m, double gamma, double gfac,
-                                               double ia, const double Ub[8], const double Fb[8], double lmb,
-                                               double lpb, double prb[8], double& gammab) {
+                                               double dgfac, double ia, const double Ub[8], const double Fb[8],
+                                               double lmb, double lpb, double prb[8], double& gammab) {
   const double rho = pr[0], P = pr[4];
   const double v[3] = {pr[1], pr[2], pr[3]};
   const double B[3] = {pr[5], pr[6], pr[7]};
@@ -430,12 +466,14 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   const double hmn = hs - Na;
   const double vd = v[DIR];
   const double Q0 = gdd * dsp - vd * vd * hmn;
-  const double Q = Q0 > 0.0 ? Q0 : 0.0;
-  const double sq = sqrt(Na * omv2 * Q);
+  // (the clamp, the tests, the square root and the reciprocal as in side_state: fpbits.cuh)
+  const double Q = dmax0i(Q0);
+  const double sq = sqrt_nr(Na * omv2 * Q);
   const double c0 = vd * hmn;
+  const bool sqpos = dgt0i(sq);
   // 1/dsp and 1/sq from one division
-  const double sqs = sq > 0.0 ? sq : 1.0;
-  const double Y = 1.0 / (dsp * sqs);
+  const double sqs = sqpos ? sq : 1.0;
+  const double Y = rcp_nr(dsp * sqs);
   const double idsp = sqs * Y, isq = dsp * Y;
   const double id = alpha * idsp;
 
@@ -456,12 +494,12 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
     const double sqb = id * (lpb - lmb);
     double dspb = -id * idsp * idb;
     double Nab = 0, hmnb = 0, vdb = 0;
-    if (sq > 0.0) {
+    if (sqpos) {
       const double Xb = 0.5 * sqb * isq;
       Nab += omv2 * Q * Xb;
       omv2b += Na * Q * Xb;
       const double Qb = Na * omv2 * Xb;
-      if (Q0 > 0.0) {
+      if (dgt0i(Q0)) {
         dspb += gdd * Qb;
         vdb -= 2.0 * vd * hmn * Qb;
         hmnb -= vd * vd * Qb;
@@ -568,7 +606,7 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) { vb[i] += Gvlb[i]; Bb[i] += GBlb[i]; }
-  gammab += gfacb * (-1.0 / ((gamma - 1.0) * (gamma - 1.0)));
+  gammab += gfacb * dgfac;  // dgfac = d gfac / d Gamma = -1 / (Gamma - 1)^2
   prb[0] += rhob;
   prb[1] += vb[0];
   prb[2] += vb[1];
@@ -627,14 +665,15 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
   finish_speeds<double, CURVED, DIR>(m, L, R);
   // HLLE reverse
   double FLb[8], FRb[8], ULb[8], URb[8], lmLb = 0, lpLb = 0, lmRb = 0, lpRb = 0;
-  const double xm = fmin(0.0, fmin(L.lm, R.lm));
-  const double xp = fmax(0.0, fmax(L.lp, R.lp));
+  // (the bounds, the tests and the reciprocal on the integer pipe / as Newton steps: fpbits.cuh)
+  const double xm = dmin0_2i(L.lm, R.lm);
+  const double xp = dmax0_2i(L.lp, R.lp);
   const double dd = xp - xm;
-  if (dd < 1e-300) {
+  if (dltposi(dd, 1e-300)) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) { FLb[q] = FRb[q] = 0.5 * Fb[q]; ULb[q] = URb[q] = 0.0; }
   } else {
-    const double inv = 1.0 / dd;
+    const double inv = rcp_nr(dd);
     double xpb = 0, xmb = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -648,12 +687,13 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
       xmb += Fb[q] * (-R.F[q] + xp * dU + F) * inv;
     }
     // route through max / min (ties go to the first candidate in the forward order)
-    if (xp > 0.0) { if (L.lp >= R.lp) lpLb += xpb; else lpRb += xpb; }
-    if (xm < 0.0) { if (L.lm <= R.lm) lmLb += xmb; else lmRb += xmb; }
+    if (dgt0i(xp)) { if (L.lp >= R.lp) lpLb += xpb; else lpRb += xpb; }
+    if (!dge0i(xm)) { if (L.lm <= R.lm) lmLb += xmb; else lmRb += xmb; }
   }
   double pLb[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pRb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  side_state_adj<CURVED, DIR>(pL, m, p.gamma, p.gfac, ia, ULb, FLb, lmLb, lpLb, pLb, gammab);
-  side_state_adj<CURVED, DIR>(pR, m, p.gamma, p.gfac, ia, URb, FRb, lmRb, lpRb, pRb, gammab);
+  const double dgfac = -1.0 / ((p.gamma - 1.0) * (p.gamma - 1.0));
+  side_state_adj<CURVED, DIR>(pL, m, p.gamma, p.gfac, dgfac, ia, ULb, FLb, lmLb, lpLb, pLb, gammab);
+  side_state_adj<CURVED, DIR>(pR, m, p.gamma, p.gfac, dgfac, ia, URb, FRb, lmRb, lpRb, pRb, gammab);
   // reconstruction reverse (stencil values reloaded), scatter to the stencil
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {

@@ -460,7 +460,9 @@ __device__ __forceinline__ bool physical_state(const T pr[8], const Geom<T>& m) 
   } else {
     v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   }
-  return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
+  // FP64: the comparisons on the integer pipe (fpbits.cuh)
+  if constexpr (sizeof(T) == 8) return dgt0i(pr[0]) && dgt0i(pr[4]) && dlt1i(v2);
+  else return pr[0] > T(0) && pr[4] > T(0) && v2 < T(1);
 }
 
 // ------------------------------------------------- one side of a Riemann face
