@@ -106,45 +106,47 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
     idx[0] = (int)(c % g.N[0]);
     idx[1] = (int)((c / g.N[0]) % g.N[1]);
     idx[2] = (int)(c / ((long long)g.N[0] * g.N[1]));
+    // the FP32 cache's values are converted on the integer pipe (fpbits.cuh;
+    // the bits of the conversion instruction for normal FP32 values)
+    auto cvt = [](double x) -> GT {
+      if constexpr (sizeof(GT) == 4) return f64_to_f32i(x);
+      else return x;
+    };
     double a[10];
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
       a[q] = __ldg(metric + q * n + c);
-      geom[q * n + c] = (GT)a[q];
+      geom[q * n + c] = cvt(a[q]);
       // FP32 cache: half the metric values; a face's metric is the sum of its
       // two cells' halves (the FP64 cache holds the face metric itself)
-      if constexpr (sizeof(GT) == 4) geom[(kGeomCacheHalf32 + q) * n + c] = (GT)(0.5 * a[q]);
+      if constexpr (sizeof(GT) == 4) geom[(kGeomCacheHalf32 + q) * n + c] = cvt(0.5 * a[q]);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long s = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
       GT sgf = GT(1), gupf = GT(1);
-      if constexpr (sizeof(GT) == 8) {
-        // FP64 cache: the face metric (the two halvings are exact and the sum
-        // is rounded once, the bits of the mean of the two cells) and its
-        // 1/alpha; points without a lower neighbour have no face that any
-        // kernel computes
-        double fa0 = 1.0;
+      // the face metric, the mean of the two cells (0.5 (a_below + a): the
+      // halving is exact, so the value has the bits of 0.5 a_below + 0.5 a)
+      double fm[10];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) {
-          double fq = q == 0 ? 1.0 : 0.0;
-          if (idx[d] >= 1) fq = __dadd_rn(__dmul_rn(0.5, __ldg(metric + q * n + c - s)), __dmul_rn(0.5, a[q]));
-          if (q == 0) fa0 = fq;
-          geom[(kGeomCacheFace + 10 * d + q) * n + c] = (GT)fq;
-        }
-        geom[(kGeomCacheFaceIa + d) * n + c] = (GT)(1.0 / fa0);
+      for (int q = 0; q < 10; ++q)
+        fm[q] = idx[d] >= 1 ? 0.5 * (__ldg(metric + q * n + c - s) + a[q]) : (q == 0 ? 1.0 : 0.0);
+      if constexpr (sizeof(GT) == 8) {
+        // FP64 cache: the face metric and its 1/alpha; points without a lower
+        // neighbour have no face that any kernel computes
+#pragma unroll
+        for (int q = 0; q < 10; ++q) geom[(kGeomCacheFace + 10 * d + q) * n + c] = fm[q];
+        geom[(kGeomCacheFaceIa + d) * n + c] = 1.0 / fm[0];
       }
       if (idx[d] >= 1) {
-        double m[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] = 0.5 * (__ldg(metric + (4 + i) * n + c - s) + a[4 + i]);
+        const double* m = fm + 4;
         const double cxx = m[3] * m[5] - m[4] * m[4];
         const double cyy = m[0] * m[5] - m[2] * m[2];
         const double czz = m[0] * m[3] - m[1] * m[1];
         const double det = m[0] * cxx - m[1] * (m[1] * m[5] - m[4] * m[2]) + m[2] * (m[1] * m[4] - m[3] * m[2]);
         const double cdd = d == 0 ? cxx : (d == 1 ? cyy : czz);
-        sgf = (GT)sqrt(det);
-        gupf = (GT)(cdd / det);
+        sgf = cvt(sqrt(det));
+        gupf = cvt(cdd / det);
       }
       geom[(10 + d) * n + c] = sgf;
       geom[(13 + d) * n + c] = gupf;
@@ -156,7 +158,7 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       const double det = gxx * cxx + gxy * cxy + gxz * cxz;
       const double idet = 1.0 / det;
       const double sgd = sqrt(det);
-      geom[16 * n + c] = (GT)sgd;
+      geom[16 * n + c] = cvt(sgd);
       mcache[c] = 1.0 / sgd;
       mcache[1 * n + c] = cxx * idet;
       mcache[2 * n + c] = cxy * idet;
@@ -164,12 +166,12 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
       mcache[4 * n + c] = cyy * idet;
       mcache[5 * n + c] = cyz * idet;
       mcache[6 * n + c] = czz * idet;
-      geom[17 * n + c] = (GT)(cxx * idet);
-      geom[18 * n + c] = (GT)(cxy * idet);
-      geom[19 * n + c] = (GT)(cxz * idet);
-      geom[20 * n + c] = (GT)(cyy * idet);
-      geom[21 * n + c] = (GT)(cyz * idet);
-      geom[22 * n + c] = (GT)(czz * idet);
+      geom[17 * n + c] = cvt(cxx * idet);
+      geom[18 * n + c] = cvt(cxy * idet);
+      geom[19 * n + c] = cvt(cxz * idet);
+      geom[20 * n + c] = cvt(cyy * idet);
+      geom[21 * n + c] = cvt(cyz * idet);
+      geom[22 * n + c] = cvt(czz * idet);
     }
     const bool inner = idx[0] >= 2 && idx[0] < g.N[0] - 2 && idx[1] >= 2 && idx[1] < g.N[1] - 2 && idx[2] >= 2 &&
                        idx[2] < g.N[2] - 2;
@@ -182,7 +184,7 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
         GT v = GT(0);
         if (inner) {
           const double* mm = metric + q * n + c;
-          v = (GT)((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
+          v = cvt((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
         }
         geom[(23 + 10 * e + q) * n + c] = v;
       }
