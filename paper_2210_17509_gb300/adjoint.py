@@ -5,7 +5,12 @@ library's forward step and its hand-written reverse (grmhd_rk_step_adjoint).
 [8, nz, ny, nx]) and the Gamma-law index to the interior primitives after
 ``nsteps`` steps.  The forward pass keeps a checkpoint (U, P) every
 ``checkpoint_every`` steps; the backward pass recomputes each segment from its
-checkpoint and runs the reverse steps in the library.  ``density_l2`` is the
+checkpoint and runs the reverse steps in the library.  With
+``keep_last_segment`` (the default) the forward pass records the stages of
+the last segment as it runs them, so the backward pass recomputes only the
+earlier segments: the memory of one segment's stages (per step U, P and one
+primitive array per stage) instead of a recomputation the forward pass has
+just done.  ``density_l2`` is the
 functional  L = sum rho^2 sqrt(gamma) dV  with its adjoint.  The gradient with
 respect to Gamma holds the initial primitives (pressure, not eps) fixed.
 Only scheduling and layout (embedding the interior into ghosted arrays)
@@ -34,17 +39,29 @@ def _interior(grid: G.Grid, full: torch.Tensor) -> torch.Tensor:
 
 class _Evolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, prim0, gamma, grid, params, scheme, dt, nsteps, every, metric):
+    def forward(ctx, prim0, gamma, grid, params, scheme, dt, nsteps, every, metric, keep_last):
         p = dataclasses.replace(params, gamma=float(gamma.item()))
         full = _embed(grid, prim0.detach())
         G.fill_ghosts(grid, p.bc, full)
         cons = G.prim2con(grid, p, full, metric)
         ws = G.workspace(grid, scheme, full.device)
         ckpt = {0: (cons.clone(), full.clone())}
+        # the last segment starts at the last checkpoint; with keep_last its
+        # steps are recorded now, for the backward pass
+        last = ((nsteps - 1) // every) * every if nsteps > 0 else 0
+        record = keep_last and any(ctx.needs_input_grad[:2])
+        tail = []
+        ns = G.stage_count(scheme)
         for s in range(nsteps):
-            G.rk_step(grid, p, scheme, dt, cons, full, metric, None, ws)
+            if record and s >= last:
+                stages = torch.empty((ns, 8) + grid.shape, dtype=torch.float64, device=full.device)
+                tail.append((cons.clone(), full.clone(), stages))
+                G.rk_step_record(grid, p, scheme, dt, cons, full, stages, metric, None, ws)
+            else:
+                G.rk_step(grid, p, scheme, dt, cons, full, metric, None, ws)
             if (s + 1) % every == 0 and s + 1 < nsteps:
                 ckpt[s + 1] = (cons.clone(), full.clone())
+        ctx.tail = (last, tail) if record else None
         ctx.grid, ctx.params, ctx.scheme, ctx.dt, ctx.nsteps, ctx.every = grid, p, scheme, dt, nsteps, every
         ctx.metric = metric
         ctx.ckpt = ckpt
@@ -64,13 +81,16 @@ class _Evolve(torch.autograd.Function):
         for k in reversed(range(len(starts))):
             s0 = starts[k]
             s1 = starts[k + 1] if k + 1 < len(starts) else ctx.nsteps
-            cons, prim = (t.clone() for t in ctx.ckpt[s0])
-            states = []
-            ns = G.stage_count(scheme)
-            for s in range(s0, s1):
-                stages = torch.empty((ns, 8) + grid.shape, dtype=torch.float64, device=dev)
-                states.append((cons.clone(), prim.clone(), stages))
-                G.rk_step_record(grid, p, scheme, dt, cons, prim, stages, metric, None, ws)
+            if ctx.tail is not None and s0 == ctx.tail[0] and len(ctx.tail[1]) == s1 - s0:
+                states = ctx.tail[1]  # recorded by the forward pass
+            else:
+                cons, prim = (t.clone() for t in ctx.ckpt[s0])
+                states = []
+                ns = G.stage_count(scheme)
+                for s in range(s0, s1):
+                    stages = torch.empty((ns, 8) + grid.shape, dtype=torch.float64, device=dev)
+                    states.append((cons.clone(), prim.clone(), stages))
+                    G.rk_step_record(grid, p, scheme, dt, cons, prim, stages, metric, None, ws)
             for cons_s, prim_s, stages in reversed(states):
                 G.rk_step_adjoint(grid, p, scheme, dt, cons_s, prim_s, ubar, pbar, gbar, metric, None, wsa,
                                   stage_prims=stages)
@@ -78,7 +98,9 @@ class _Evolve(torch.autograd.Function):
         _, prim_init = ctx.ckpt[0]
         G.fill_ghosts_adjoint(grid, p.bc, pbar)
         G.prim2con_adjoint(grid, p, prim_init, ubar, pbar, gbar, metric)
-        return _interior(grid, pbar).clone(), gbar.reshape(()).clone(), None, None, None, None, None, None, None
+        ctx.tail = None
+        return (_interior(grid, pbar).clone(), gbar.reshape(()).clone(), None, None, None, None, None, None, None,
+                None)
 
 
 class _DensityL2(torch.autograd.Function):
@@ -100,9 +122,12 @@ class _DensityL2(torch.autograd.Function):
 
 
 def evolve(prim0, gamma, grid: G.Grid, params: G.Params, scheme: int, dt: float, nsteps: int,
-           checkpoint_every: int = 5, metric=None):
-    """Interior primitives after nsteps steps (differentiable in prim0 and gamma)."""
-    return _Evolve.apply(prim0, gamma, grid, params, scheme, dt, nsteps, checkpoint_every, metric)
+           checkpoint_every: int = 5, metric=None, keep_last_segment: bool = True):
+    """Interior primitives after nsteps steps (differentiable in prim0 and gamma).
+    keep_last_segment=False recomputes the last segment in the backward pass
+    too (no memory beyond the checkpoints)."""
+    return _Evolve.apply(prim0, gamma, grid, params, scheme, dt, nsteps, checkpoint_every, metric,
+                         keep_last_segment)
 
 
 def density_l2(prim, grid: G.Grid, metric=None):

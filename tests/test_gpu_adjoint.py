@@ -229,6 +229,27 @@ def test_config3_gradient_matches_central_differences(G, A):
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
 
 
+@pytest.mark.parametrize("nsteps,every", [(7, 3), (6, 3), (1, 5)])
+def test_kept_last_segment_gives_the_recomputed_gradient(G, A, nsteps, every):
+    """The forward pass that records its last segment (keep_last_segment, the
+    default) gives the gradient of the one that recomputes it, to round-off
+    (the reverse's atomic scatter varies in the last bits from run to run),
+    and the same end state to the bit."""
+    g, p, prim, met, blk, _ = state(G, 10, True, seed=8)
+    dt = 0.25 * blk.dx[0]
+    res = []
+    for keep in (True, False):
+        x = prim[:, 3:-3, 3:-3, 3:-3].clone().requires_grad_(True)
+        gam = torch.tensor(p.gamma, dtype=torch.float64, requires_grad=True)
+        out = A.evolve(x, gam, g, p, G.RK3, dt, nsteps, checkpoint_every=every, metric=met, keep_last_segment=keep)
+        A.density_l2(out, g, met).backward()
+        res.append((out.detach().cpu().numpy(), x.grad.cpu().numpy(), float(gam.grad.item())))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    scale = np.abs(res[1][1]).max()
+    assert np.abs(res[0][1] - res[1][1]).max() <= 1e-13 * scale
+    assert abs(res[0][2] - res[1][2]) <= 1e-13 * abs(res[1][2])
+
+
 def test_rk_step_adjoint_with_recorded_stages_is_identical(G):
     g, p, prim, met, blk, _ = state(G, 8, True)
     cons = G.prim2con(g, p, prim, met)
