@@ -416,8 +416,8 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
  *   i.e. ncell <= 1,048,576 for RK2/RK3 and about half that for RK4 (e.g. a
  *   94^3 interior with 3 ghosts); larger blocks return GRMHD_ERR_SIZE.
  *   Paths: blocks whose grmhd_rk_workspace_bytes_cached fits in the array
- *   (ncell <= 47,392 for RK2/RK3, 45,343 for RK4, e.g. a 29^3 interior with
- *   3 ghosts) run the cached paths, larger ones the uncached paths; the
+ *   (ncell up to about 42,100 for RK2/RK3 and 40,500 for RK4, e.g. a 28^3
+ *   interior with 3 ghosts) run the cached paths, larger ones the uncached paths; the
  *   results are those of grmhd_rk_step given a workspace of that size.
  *   GRMHD_REUSE_GEOMETRY is ignored: the geometry caches are rebuilt on
  *   every call, since the array may hold another block's caches.

@@ -108,10 +108,11 @@ cudaError_t launch_rhs_fp64_cached(const DevGrid& g, const DevParams& p, const d
                                    const double* kij, const StageEpilogue& ep, cudaStream_t s);
 cudaError_t launch_rhs_mixed_cached(const DevGrid& g, const DevParams& p, const float* prim32, const float* geom,
                                     const double* kij, bool curved, const StageEpilogue& ep, cudaStream_t s);
-constexpr int kGeomCacheComps = 86;  // geometry cache components (layout in rhs.cuh)
+constexpr int kGeomCacheComps = 108; // geometry cache components (layout in rhs.cuh)
 constexpr int kGeomCacheFace = 53;   // FP64 cache: first of the 3 x 10 face-metric components
 constexpr int kGeomCacheFaceIa = 83; // FP64 cache: first of the 3 face 1/alpha components
 constexpr int kGeomCacheHalf32 = 53; // FP32 cache: first of the ten half-metric components
+constexpr int kGeomCacheStat = 86;   // FP64 cache: first of the 22 metric factors of the sources
 constexpr int kMetricCacheComps = 7;
 
 // ---------------------------------------------------------- host helpers

@@ -298,6 +298,43 @@ __device__ __forceinline__ void minmod_cell(T um1, T u0, T up1, T& vm, T& vp) {
 }
 
 // ---------------------------------------------------------------- geometry
+// The factors of the Eq. 13 sources that depend on the metric alone (static
+// for a static metric): formed per cell on the fly from the metric, or read
+// from the FP64 geometry cache, where they are formed once in FP64 with the
+// same operations (source_statics).
+template <class T>
+struct SrcStatics {
+  T ia, ia2;     // 1 / alpha, 1 / alpha^2
+  T bia2[3];     // beta^i / alpha^2
+  T M[6];        // gamma^ij - beta^i beta^j / alpha^2 (packed like gamma)
+  T betal[3];    // beta_i = gamma_ij beta^j
+  T asg;         // alpha sqrt(gamma)
+  T bb[6];       // beta^i beta^j (packed)
+  T bda;         // beta^i d_i alpha
+};
+constexpr int kSrcStaticsComps = 22;
+static_assert(kGeomCacheStat + kSrcStaticsComps == kGeomCacheComps, "geometry cache layout");
+
+template <class T>
+__device__ __forceinline__ void source_statics(const T alpha, const T beta[3], const T gm[6], const T sg,
+                                               const T gu[6], const T da[3], SrcStatics<T>& st) {
+  const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+  st.ia = T(1) / alpha;
+  st.ia2 = st.ia * st.ia;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) st.bia2[i] = beta[i] * st.ia2;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    st.bb[s] = beta[I6[s]] * beta[J6[s]];
+    st.M[s] = gu[s] - st.bb[s] * st.ia2;
+  }
+  st.betal[0] = gm[0] * beta[0] + gm[1] * beta[1] + gm[2] * beta[2];
+  st.betal[1] = gm[1] * beta[0] + gm[3] * beta[1] + gm[4] * beta[2];
+  st.betal[2] = gm[2] * beta[0] + gm[4] * beta[1] + gm[5] * beta[2];
+  st.asg = alpha * sg;
+  st.bda = beta[0] * da[0] + beta[1] * da[1] + beta[2] * da[2];
+}
+
 // Metric at a face (or a cell) converted to the compute type.
 template <class T>
 struct Geom {

@@ -175,19 +175,46 @@ __global__ void geom_cache_kernel(DevGrid g, const double* __restrict__ metric, 
     }
     const bool inner = idx[0] >= 2 && idx[0] < g.N[0] - 2 && idx[1] >= 2 && idx[1] < g.N[1] - 2 && idx[2] >= 2 &&
                        idx[2] < g.N[2] - 2;
+    double da[3];  // d_e alpha
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const long long s = e == 0 ? 1 : (e == 1 ? g.sy : g.sz);
       const double w = g.idx[e] * (1.0 / 12.0);
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
-        GT v = GT(0);
+        double v = 0.0;
         if (inner) {
           const double* mm = metric + q * n + c;
-          v = cvt((8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w);
+          v = (8.0 * (__ldg(mm + s) - __ldg(mm - s)) - (__ldg(mm + 2 * s) - __ldg(mm - 2 * s))) * w;
         }
-        geom[(23 + 10 * e + q) * n + c] = v;
+        if (q == 0) da[e] = v;
+        geom[(23 + 10 * e + q) * n + c] = cvt(v);
       }
+    }
+    if constexpr (sizeof(GT) == 8) {
+      // the metric factors of the sources (SrcStatics, in its order), formed
+      // from the values the RHS reads from this cache
+      const double beta[3] = {a[1], a[2], a[3]};
+      const double gm[6] = {a[4], a[5], a[6], a[7], a[8], a[9]};
+      double gu[6], sgc;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) gu[i] = geom[(17 + i) * n + c];
+      sgc = geom[16 * n + c];
+      SrcStatics<double> st;
+      source_statics<double>(a[0], beta, gm, sgc, gu, da, st);
+      double* q = geom + (long long)kGeomCacheStat * n + c;
+      q[0] = st.ia;
+      q[n] = st.ia2;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) q[(2 + i) * n] = st.bia2[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) q[(5 + k) * n] = st.M[k];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) q[(11 + i) * n] = st.betal[i];
+      q[14 * n] = st.asg;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) q[(15 + k) * n] = st.bb[k];
+      q[21 * n] = st.bda;
     }
   }
 }

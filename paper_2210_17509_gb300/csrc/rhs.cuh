@@ -53,12 +53,38 @@ typedef SrcCacheT<double, double> SrcCache64;  // FP64: FP64 primitives + FP64 g
 //           (index 53 + 10 d + q; the two halvings are exact, so the value
 //           has the bits of the mean of the two cells)
 //   83..85  1 / alpha on the lower d-face
+//   86..107 the metric factors of the sources at the point (SrcStatics:
+//           1/alpha, 1/alpha^2, beta^i / alpha^2, gamma^ij - beta^i beta^j /
+//           alpha^2, beta_i, alpha sqrt(gamma), beta^i beta^j, beta^i d_i alpha)
 //   FP32 cache (the FP32 RHS is latency bound: ten arrays that all three
 //   face directions share stay in L1 better than thirty):
 //   53..62  half the metric values, 0.5 (alpha, beta^i, gamma_ij): a face's
 //           metric is the sum of its two cells' entries
-static_assert(kGeomCacheComps == 86 && kGeomCacheFace == 53 && kGeomCacheFaceIa == 83 && kGeomCacheHalf32 == 53,
+static_assert(kGeomCacheComps == 108 && kGeomCacheFace == 53 && kGeomCacheFaceIa == 83 && kGeomCacheHalf32 == 53 &&
+                  kGeomCacheStat == 86,
               "geometry cache layout");
+
+// (SrcStatics and source_statics, the metric factors of the sources: physics.cuh)
+
+// SrcStatics as stored in the FP64 geometry cache (component k at index
+// kGeomCacheStat + k, in the order of the struct).
+template <class T>
+__device__ __forceinline__ void load_statics(const double* __restrict__ gc, long long n, long long c,
+                                             SrcStatics<T>& st) {
+  const double* q = gc + (long long)kGeomCacheStat * n + c;
+  st.ia = (T)__ldg(q);
+  st.ia2 = (T)__ldg(q + n);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) st.bia2[i] = (T)__ldg(q + (2 + i) * n);
+#pragma unroll
+  for (int s = 0; s < 6; ++s) st.M[s] = (T)__ldg(q + (5 + s) * n);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) st.betal[i] = (T)__ldg(q + (11 + i) * n);
+  st.asg = (T)__ldg(q + 14 * n);
+#pragma unroll
+  for (int s = 0; s < 6; ++s) st.bb[s] = (T)__ldg(q + (15 + s) * n);
+  st.bda = (T)__ldg(q + 21 * n);
+}
 
 // SrcF64 whose primitives are written in the same launch (the one-launch
 // batch: recovered and ghost-filled by other CTAs before the tile reads
@@ -348,8 +374,8 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
 // the metric derivatives dA[e][q].
 template <class T, class S>
 __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p, const S& src, long long c,
-                                            const T alpha, const T beta[3], const T gm[6], const T sg, const T gu[6],
-                                            const T dA[3][10], T out[8]) {
+                                            const T alpha, const T beta[3], const T gm[6], const T dA[3][10],
+                                            const SrcStatics<T>& st, T out[8]) {
   // fluid at the cell centre
   const long long n = g.ncell;
   const T rho = ld_pq<T>(src, n, 0, c), P = ld_pq<T>(src, n, 4, c);
@@ -369,8 +395,7 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   const T b2 = B2 * omv2 + Bv * Bv;
   const T hs = rho + par_t<T>(p.gfac, p.gfacf) * P + b2;
   const T Ps = P + T(0.5) * b2;
-  const T ia = T(1) / alpha;
-  const T ia2 = ia * ia;
+  const T ia = st.ia, ia2 = st.ia2;
   const T b0 = ab0 * ia;
   T vt[3], bu[3];
 #pragma unroll
@@ -382,22 +407,20 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   const T T00 = (hW2 - Ps) * ia2 - b0 * b0;
   T T0[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) T0[i] = hW2 * vt[i] * ia + Ps * beta[i] * ia2 - b0 * bu[i];
+  for (int i = 0; i < 3; ++i) T0[i] = hW2 * vt[i] * ia + Ps * st.bia2[i] - b0 * bu[i];
   // T^{ij}, symmetric, packed like gamma
   const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
   T Tij[6];
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     const int i = I6[s], j = J6[s];
-    Tij[s] = hW2 * vt[i] * vt[j] + Ps * (gu[s] - beta[i] * beta[j] * ia2) - bu[i] * bu[j];
+    Tij[s] = hW2 * vt[i] * vt[j] + Ps * st.M[s] - bu[i] * bu[j];
   }
-  T betal[3];
-  lower(gm, beta, betal);
   T T0l[3];  // T^0_i = beta_i T^00 + gamma_ij T^0j
   lower(gm, T0, T0l);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) T0l[i] += betal[i] * T00;
-  const T asg = alpha * sg;
+  for (int i = 0; i < 3; ++i) T0l[i] += st.betal[i] * T00;
+  const T asg = st.asg;
   // symmetric contraction weights: off-diagonal entries count twice
   const T wsym[6] = {T(1), T(2), T(2), T(1), T(2), T(1)};
   out[0] = T(0);
@@ -409,7 +432,7 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     const int i = I6[s], k = J6[s];
-    Wg[s] = (T(0.5) * wsym[s]) * (T00 * (beta[i] * beta[k]) + (T0[i] * beta[k] + T0[k] * beta[i]) + Tij[s]);
+    Wg[s] = (T(0.5) * wsym[s]) * (T00 * st.bb[s] + (T0[i] * beta[k] + T0[k] * beta[i]) + Tij[s]);
   }
   const T T00a = T00 * alpha;
 #pragma unroll
@@ -421,7 +444,7 @@ __device__ __forceinline__ void source_core(const DevGrid& g, const DevParams& p
   }
   {
     T t = -(T0[0] * dA[0][0] + T0[1] * dA[1][0] + T0[2] * dA[2][0]);
-    t -= T00 * (beta[0] * dA[0][0] + beta[1] * dA[1][0] + beta[2] * dA[2][0]);
+    t -= T00 * st.bda;
     if (src.kij) {
       T K[6];
 #pragma unroll
@@ -473,7 +496,10 @@ __device__ __forceinline__ void source_terms_f64(const DevGrid& g, const DevPara
       dA[e][q] = (T)((8.0 * (__ldg(m + s) - __ldg(m - s)) - (__ldg(m + 2 * s) - __ldg(m - 2 * s))) * w);
     }
   }
-  source_core<T, S>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+  SrcStatics<T> st;
+  const T da[3] = {dA[0][0], dA[1][0], dA[2][0]};
+  source_statics<T>(alpha, beta, gm, sg, gu, da, st);
+  source_core<T, S>(g, p, src, c, alpha, beta, gm, dA, st, out);
 }
 
 template <class T>
@@ -495,19 +521,27 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   const long long n = g.ncell;
   const T alpha = (T)__ldg(gc + c);
   const T beta[3] = {(T)__ldg(gc + n + c), (T)__ldg(gc + 2 * n + c), (T)__ldg(gc + 3 * n + c)};
-  T gm[6], gu[6];
+  T gm[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    gm[i] = (T)__ldg(gc + (4 + i) * n + c);
-    gu[i] = (T)__ldg(gc + (17 + i) * n + c);
-  }
-  const T sg = (T)__ldg(gc + 16 * n + c);
+  for (int i = 0; i < 6; ++i) gm[i] = (T)__ldg(gc + (4 + i) * n + c);
   T dA[3][10];
 #pragma unroll
   for (int e = 0; e < 3; ++e)
 #pragma unroll
     for (int q = 0; q < 10; ++q) dA[e][q] = (T)__ldg(gc + (23 + 10 * e + q) * n + c);
-  source_core<T, SrcCacheT<PT, GT>>(g, p, src, c, alpha, beta, gm, sg, gu, dA, out);
+  SrcStatics<T> st;
+  if constexpr (sizeof(GT) == 8) {
+    // FP64 cache: the metric factors formed once (the FP64 sources are bound by the FP64 pipe)
+    load_statics<T>(gc, n, c, st);
+  } else {
+    T gu[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gu[i] = (T)__ldg(gc + (17 + i) * n + c);
+    const T sg = (T)__ldg(gc + 16 * n + c);
+    const T da[3] = {dA[0][0], dA[1][0], dA[2][0]};
+    source_statics<T>(alpha, beta, gm, sg, gu, da, st);
+  }
+  source_core<T, SrcCacheT<PT, GT>>(g, p, src, c, alpha, beta, gm, dA, st, out);
 }
 
 // Tile shapes the kernels are instantiated for (cells per axis, 256 cells each).

@@ -22,8 +22,9 @@
 // ordering between them) race on it.
 //
 // The step lays the grmhd_rk_step workspace over the array, so blocks whose
-// cached workspace (grmhd_rk_workspace_bytes_cached) fits -- ncell <= 47,392
-// points for RK2/RK3, 45,343 for RK4, e.g. a 29^3 interior with 3 ghosts --
+// cached workspace (grmhd_rk_workspace_bytes_cached) fits -- ncell up to
+// about 42,100 points for RK2/RK3 and 40,500 for RK4, e.g. a 28^3 interior
+// with 3 ghosts --
 // take the cached paths, and larger blocks up to the plain workspace size the
 // uncached ones, as grmhd_rk_step does with workspaces of those sizes.
 // Nothing in the array has to start at zero: the step overwrites the U^n
