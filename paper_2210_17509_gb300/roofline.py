@@ -32,19 +32,20 @@ sources, epilogue).  The unit the benchmark times is that triple (one
 grmhd_rhs_cached call).
 
 Algorithmic HBM bytes per interior cell of the triple (FP64, static metric,
-geometry cache): prim 8 x 8 B + geometry cache 86 x 8 B read (the face pass
-reads the face metric, 1/alpha, sqrt(gamma) and gamma^dd of the three lower
-faces, 39 values; the per-cell pass the cell metric, sqrt(gamma), gamma^ij
-and the 30 derivatives, 47 values), rhs 8 x 8 B written = 816 B, plus the
-face buffer, 24 x 8 B written and read back = 384 B, and the state buffer,
-48 x 8 B written and read back = 768 B: 1968 B (the uncached single-pass
-grmhd_rhs reads the 10 metric entries instead of the cache and has no
-buffers: 208 B).
+geometry cache): prim 8 x 8 B + geometry cache 101 x 8 B read (the face
+pass reads the face metric, 1/alpha, sqrt(gamma) and gamma^dd of the three
+lower faces, 39 values; the per-cell pass the cell metric, the 30
+derivatives and the 22 metric factors of the sources, 62 values), rhs 8 x 8
+B written = 936 B, plus the face buffer, 24 x 8 B written and read back =
+384 B, and the state buffer, 48 x 8 B written and read back = 768 B: 2088 B
+(the uncached single-pass grmhd_rhs reads the 10 metric entries instead of
+the cache and has no buffers: 208 B).
 
 Measured DRAM traffic of the triple (ncu, dram__bytes_read.sum +
 dram__bytes_write.sum, all three kernels) for the 96^3 block (884,736
-cells): 462.9 + 830.2 + 778.6 MB = 2071.7 MB, 2342 B per cell; traffic grows
-with the cell count, so a launch on n^3 cells is about 2342 n^3 B.
+cells): 462.1 + 829.7 + 949.7 MB = 2241.5 MB, 2534 B per cell (the per-cell
+pass adds about 50 MB of register spills); traffic grows with the cell
+count, so a launch on n^3 cells is about 2534 n^3 B.
 
 Peaks: HBM copy bandwidth from the generated MEASURED_PEAKS.json; the
 FP64 FMA peak was measured on this GPU model with ``python -m
@@ -63,11 +64,11 @@ with open(os.path.join(HERE, "flop_counts.json")) as _f:
 
 # ncu thread-instruction counts per interior cell at 96^3 (DADD, DMUL, DFMA)
 EXECUTED_FP64_PER_CELL = {"rhs_states_kernel": (233, 516, 551), "rhs_face_kernel": (76, 270, 370),
-                          "rhs_div_kernel": (37, 81, 155)}
+                          "rhs_div_kernel": (37, 66, 136)}
 EXECUTED_FLOPS_PER_CELL = sum(a + m + 2 * f for a, m, f in EXECUTED_FP64_PER_CELL.values())
-FP64_PIPE_BUSY = {"rhs_states_kernel": 0.863, "rhs_face_kernel": 0.896, "rhs_div_kernel": 0.865}
-BYTES_PER_CELL_RHS_CURVED = 816 + 384 + 768
-TRAFFIC_PER_CELL_MEASURED = (462.9e6 + 830.2e6 + 778.6e6) / 884736  # 2342 B per cell
+FP64_PIPE_BUSY = {"rhs_states_kernel": 0.863, "rhs_face_kernel": 0.896, "rhs_div_kernel": 0.807}
+BYTES_PER_CELL_RHS_CURVED = 936 + 384 + 768
+TRAFFIC_PER_CELL_MEASURED = (462.1e6 + 829.7e6 + 949.7e6) / 884736  # 2534 B per cell
 FP64_PEAK_TFLOPS_MEASURED = 1.256
 FP32_PEAK_TFLOPS_MEASURED = 78.5
 HBM_FALLBACK_GBS = 6800.0
