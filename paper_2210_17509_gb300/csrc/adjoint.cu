@@ -288,6 +288,17 @@ __global__ void fill_ghosts_adjoint_kernel(DevGrid g, int bc, int nvar, double* 
     idx[0] = (int)(t % g.n[0]);
     idx[1] = (int)((t / g.n[0]) % g.n[1]);
     idx[2] = (int)(t / ((long long)g.n[0] * g.n[1]));
+    // only interior points that some ghost copies from have work (copy:
+    // the first and last point of an axis; periodic: the ng points at each
+    // end, all of them on axes shorter than 2 ng); for the others the
+    // gather below would store the point's own value back
+    bool source = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int i = idx[d];
+      source = source || (bc == GRMHD_BC_PERIODIC ? (i < g.ng || i >= g.n[d] - g.ng) : (i == 0 || i == g.n[d] - 1));
+    }
+    if (!source) continue;
     // per axis, every full-array coordinate whose source is this interior coordinate
     int pos[3][1 + 2 * 16];
     int cnt[3];

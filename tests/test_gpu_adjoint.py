@@ -60,7 +60,7 @@ def interior_mask(g):
 def test_ghost_fill_adjoint_is_the_transpose(G):
     gen = torch.Generator(device="cuda").manual_seed(0)
     for bc in (0, 1):
-        for n in ((6, 5, 4), (1, 3, 2)):
+        for n in ((6, 5, 4), (1, 3, 2), (12, 9, 8)):
             g = G.Grid(n, 3, (0.1, 0.1, 0.1))
             v = torch.randn((8,) + g.shape, dtype=torch.float64, device="cuda", generator=gen)
             w = torch.randn((8,) + g.shape, dtype=torch.float64, device="cuda", generator=gen)
