@@ -371,7 +371,10 @@ int grmhd_fill_ghosts_adjoint(const grmhd_grid* grid, int32_t bc, int32_t nvar, 
 int grmhd_density_l2(const grmhd_grid* grid, const double* prim, const double* metric, double lbar,
                      double* loss, double* prim_bar, void* stream);
 
-/* Bytes of workspace for grmhd_rk_step_adjoint (RK2 / RK3; 0 otherwise). */
+/* Bytes of workspace for grmhd_rk_step_adjoint (RK2 / RK3; 0 otherwise):
+ * the stage and adjoint arrays (5 + stages fields of 8 x ncell doubles) and
+ * the cell-state buffer of the WENO5 face adjoint (96 x ncell doubles: both
+ * WENO5 states of every cell of one direction with their derivatives). */
 size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme);
 
 /* grmhd_rk_step that also records the primitives after each stage (ghosts

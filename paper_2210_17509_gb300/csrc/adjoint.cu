@@ -409,6 +409,45 @@ __device__ __forceinline__ void weno5_value_grad2(const double uA[5], const doub
   vB = weno5_vg_finish(B, B.ee * rb, B.ws * rb, grB);
 }
 
+// Both WENO5 states of one cell from its stencil u[0..4] = u_{i-2..i+2},
+// with their partial derivatives: vp / gp (plus: the value at the upper face
+// i+1/2, gp[k] = dvp/du_k) and vm / gm (minus: the value at the lower face,
+// from the mirrored stencil, gm[k] = dvm/du_k).  The mirrored stencil has
+// the same smoothness indicators in reverse order (t, e and p reversed, s
+// reversed with its middle entry negated, which the squares drop), so they
+// are formed once; the three reciprocals 1/ws+, 1/ws- and 1/(e0 e1 e2) come
+// from one division.
+__device__ __forceinline__ void weno5_cell_value_grad(const double u[5], double eps13, double& vm, double gm[5],
+                                                      double& vp, double gp[5]) {
+  Weno5VG A, B;
+  weno5_vg_parts(u, eps13, A);
+  B.q[0] = fma(2.0, u[4], fma(-7.0, u[3], 11.0 * u[2]));
+  B.q[1] = fma(2.0, u[1], fma(5.0, u[2], -u[3]));
+  B.q[2] = fma(5.0, u[1], fma(2.0, u[2], -u[0]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    B.t[k] = A.t[2 - k];
+    B.s[k] = A.s[2 - k];
+    B.e[k] = A.e[2 - k];
+    B.p[k] = A.p[2 - k];
+  }
+  B.s[1] = -A.s[1];
+  B.w[0] = A.p[2] * A.p[2];
+  B.w[1] = A.w[1];
+  B.w[2] = 3.0 * A.w[0];
+  B.ws = B.w[0] + B.w[1] + B.w[2];
+  B.ee = A.ee;
+  const double ab = A.ws * B.ws;
+  const double Z = rcp_nr(ab * A.ee);
+  const double eZ = A.ee * Z;
+  double gr[5];
+  const double iee = ab * Z;
+  vp = weno5_vg_finish(A, B.ws * eZ, iee, gp);
+  vm = weno5_vg_finish(B, A.ws * eZ, iee, gr);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) gm[k] = gr[4 - k];  // derivatives w.r.t. the mirrored stencil's u_{4-k}
+}
+
 // minmod face value um1 + minmod(um1 - um2, u0 - um1) / 2 with its adjoint.
 __device__ __forceinline__ double minmod_left_adj(double um2, double um1, double u0, double vbar, double ub[3]) {
   const double a = um1 - um2, b = u0 - um1;
@@ -629,17 +668,34 @@ __device__ __forceinline__ void side_state_adj(const double pr[8], const Geom<do
 }
 
 // ---------------------------------------------------------------- face adjoint
-template <int RECON, bool CURVED, int DIR>
+// Cell-state buffer of one direction (BUF): Wb[((2 q + s) 6 + j) ncell + cell],
+// s = 0 the minus state (value at the cell's lower face), 1 the plus state,
+// j = 0 the value and 1..5 its derivatives with respect to u_{i-2 .. i+2}.
+constexpr int kAdjStateComps = 96;
+__device__ __forceinline__ long long adj_state_index(int q, int side, int j, long long ncell, long long cell) {
+  return (long long)((2 * q + side) * 6 + j) * ncell + cell;
+}
+
+template <int RECON, bool CURVED, int DIR, bool BUF = false>
 __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& p, const double* __restrict__ prim,
                                              const double* __restrict__ metric, long long c, const double Fb[8],
-                                             double* __restrict__ prim_bar, double& gammab, double* gsm) {
+                                             double* __restrict__ prim_bar, double& gammab, double* gsm,
+                                             const double* __restrict__ Wb = nullptr) {
   const long long stride = (DIR == 0) ? 1 : ((DIR == 1) ? g.sy : g.sz);
   // primal reconstruction; for WENO5 the five partial derivatives of every
   // face value are kept in shared memory (gsm[j * blockDim.x + tid],
-  // j = (2 q + side) * 5 + k) for the reverse sweep below
+  // j = (2 q + side) * 5 + k) for the reverse sweep below, or (BUF) read
+  // from the cell-state buffer: the left state is the plus state of the cell
+  // below, the right state the minus state of the cell above
   double pL[8], pR[8];
   const double eps = p.weno_eps;
-  if (RECON == GRMHD_WENO5) {
+  if constexpr (BUF) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      pL[q] = __ldg(Wb + adj_state_index(q, 1, 0, g.ncell, c - stride));
+      pR[q] = __ldg(Wb + adj_state_index(q, 0, 0, g.ncell, c));
+    }
+  } else if (RECON == GRMHD_WENO5) {
     const double eps13 = eps * (12.0 / 13.0);
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
@@ -711,7 +767,17 @@ __device__ __forceinline__ void face_adjoint(const DevGrid& g, const DevParams& 
     double ub[6] = {0, 0, 0, 0, 0, 0};
     if (fbL) ub[2] += pLb[q];
     if (fbR) ub[3] += pRb[q];
-    if (RECON == GRMHD_WENO5) {
+    if constexpr (BUF) {
+      // plus state of the cell below: u_{c-3 .. c+1}; minus state of the cell above: u_{c-2 .. c+2}
+      if (!fbL) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ub[k] += __ldg(Wb + adj_state_index(q, 1, 1 + k, g.ncell, c - stride)) * pLb[q];
+      }
+      if (!fbR) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ub[k + 1] += __ldg(Wb + adj_state_index(q, 0, 1 + k, g.ncell, c)) * pRb[q];
+      }
+    } else if (RECON == GRMHD_WENO5) {
       if (!fbL) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) ub[k] += gsm[((2 * q) * 5 + k) * blockDim.x + threadIdx.x] * pLb[q];
@@ -794,6 +860,73 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
     if (dir == 0) face_adjoint<RECON, CURVED, 0>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
     else if (dir == 1) face_adjoint<RECON, CURVED, 1>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
     else face_adjoint<RECON, CURVED, 2>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
+  }
+  block_add_gamma(gb, gamma_bar);
+}
+
+// The cell states of direction DIR with their derivatives, for the buffered
+// face adjoint: the cells -1 .. n_DIR of every line along DIR (interior
+// across), one item per (variable, cell).  Each cell's two states share their
+// smoothness indicators (weno5_cell_value_grad).
+template <int DIR>
+__global__ void __launch_bounds__(128) adj_cell_states_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
+                                                              double* __restrict__ Wb) {
+  const int ex = g.n[0] + 2 * (DIR == 0), ey = g.n[1] + 2 * (DIR == 1), ez = g.n[2] + 2 * (DIR == 2);
+  const long long m = (long long)ex * ey * ez;
+  const long long stride = DIR == 0 ? 1 : (DIR == 1 ? g.sy : g.sz);
+  const double eps13 = p.weno_eps * (12.0 / 13.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / m);
+    const long long l = t - q * m;
+    const long long lxy = l / ex;
+    const int i = (int)(l - lxy * ex) - (DIR == 0), j = (int)(lxy % ey) - (DIR == 1), k = (int)(lxy / ey) - (DIR == 2);
+    const long long c = (long long)(k + g.ng) * g.sz + (long long)(j + g.ng) * g.sy + (i + g.ng);
+    double u[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) u[a] = __ldg(prim + q * g.ncell + c + (a - 2) * stride);
+    double vm, gm[5], vp, gp[5];
+    weno5_cell_value_grad(u, eps13, vm, gm, vp, gp);
+    Wb[adj_state_index(q, 0, 0, g.ncell, c)] = vm;
+    Wb[adj_state_index(q, 1, 0, g.ncell, c)] = vp;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      Wb[adj_state_index(q, 0, 1 + a, g.ncell, c)] = gm[a];
+      Wb[adj_state_index(q, 1, 1 + a, g.ncell, c)] = gp[a];
+    }
+  }
+}
+
+// Face adjoint of the DIR-faces from the cell-state buffer (WENO5).
+template <bool CURVED, int DIR>
+__global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, DevParams p,
+                                                                  const double* __restrict__ prim,
+                                                                  const double* __restrict__ metric,
+                                                                  const double* __restrict__ rhs_bar, double scale,
+                                                                  double* __restrict__ prim_bar,
+                                                                  double* __restrict__ gamma_bar,
+                                                                  const double* __restrict__ Wb) {
+  const int fx = g.n[0] + (DIR == 0), fy = g.n[1] + (DIR == 1);
+  const long long total = (long long)fx * fy * (g.n[2] + (DIR == 2));
+  const long long stride = DIR == 0 ? 1 : (DIR == 1 ? g.sy : g.sz);
+  double gb = 0.0;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const long long fxy = f / fx;
+    const int xi = (int)(f - fxy * fx), yi = (int)(fxy % fy), zi = (int)(fxy / fy);
+    const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
+    const int ic = DIR == 0 ? xi : (DIR == 1 ? yi : zi);
+    const bool has_hi = ic < g.n[DIR];  // cell c is interior
+    const bool has_lo = ic > 0;         // cell c - stride is interior
+    double Fb[8];
+    const double w = scale * g.idx[DIR];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double hi = has_hi ? rhs_bar[q * g.ncell + c] : 0.0;
+      const double lo = has_lo ? rhs_bar[q * g.ncell + c - stride] : 0.0;
+      Fb[q] = w * (hi - lo);
+    }
+    face_adjoint<GRMHD_WENO5, CURVED, DIR, true>(g, p, prim, metric, c, Fb, prim_bar, gb, nullptr, Wb);
   }
   block_add_gamma(gb, gamma_bar);
 }
@@ -1035,9 +1168,42 @@ int blocks_for(long long work, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
+template <bool CURVED, int DIR>
+cudaError_t launch_face_adjoint_dir(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
+                                    const double* rhs_bar, double scale, double* prim_bar, double* gamma_bar,
+                                    double* Wb, cudaStream_t s) {
+  const long long cells = 8LL * (g.n[0] + 2 * (DIR == 0)) * (g.n[1] + 2 * (DIR == 1)) * (g.n[2] + 2 * (DIR == 2));
+  adj_cell_states_kernel<DIR><<<blocks_for(cells, 128), 128, 0, s>>>(g, p, prim, Wb);
+  const long long faces = (long long)(g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
+  rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces, 128), 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale,
+                                                                                prim_bar, gamma_bar, Wb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rhs_adjoint(const DevGrid& g, const DevParams& p, const double* prim, const double* metric,
                                const double* kij, const double* rhs_bar, double scale, double* prim_bar,
-                               double* gamma_bar, cudaStream_t s) {
+                               double* gamma_bar, cudaStream_t s, double* Wb = nullptr) {
+  if (Wb && p.recon == GRMHD_WENO5) {
+    // WENO5 with a cell-state buffer: per direction, the cell states with
+    // their derivatives, then the faces
+    cudaError_t e;
+    if (metric) {
+      if ((e = launch_face_adjoint_dir<true, 0>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)) ||
+          (e = launch_face_adjoint_dir<true, 1>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)) ||
+          (e = launch_face_adjoint_dir<true, 2>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)))
+        return e;
+    } else {
+      if ((e = launch_face_adjoint_dir<false, 0>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)) ||
+          (e = launch_face_adjoint_dir<false, 1>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)) ||
+          (e = launch_face_adjoint_dir<false, 2>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, s)))
+        return e;
+      return cudaSuccess;
+    }
+    const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+    source_adjoint_kernel<<<blocks_for(nint, 128), 128, 0, s>>>(g, p, prim, metric, kij, rhs_bar, scale, prim_bar,
+                                                                gamma_bar);
+    return cudaGetLastError();
+  }
   const long long faces = (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
                           (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
   const int nb = blocks_for(faces, 128);
@@ -1170,7 +1336,8 @@ size_t grmhd_rk_adjoint_workspace_bytes(const grmhd_grid* grid, int32_t scheme) 
   const DevGrid g = make_grid(*grid);
   const size_t field = r256((size_t)8 * g.ncell * sizeof(double));
   const int stages = scheme == GRMHD_RK3 ? 3 : 2;
-  return (size_t)(1 + stages + 1 + 1 + 2) * field;
+  // + the cell-state buffer of the WENO5 face adjoint (one direction at a time)
+  return (size_t)(1 + stages + 1 + 1 + 2) * field + r256((size_t)kAdjStateComps * g.ncell * sizeof(double));
 }
 
 int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, int32_t scheme, double dt,
@@ -1200,6 +1367,7 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
   double* Bacc = reinterpret_cast<double*>(base + (size_t)(ns + 2) * field);
   double* Pn = reinterpret_cast<double*>(base + (size_t)(ns + 3) * field);
   double* Pk = reinterpret_cast<double*>(base + (size_t)(ns + 4) * field);
+  double* Wb = reinterpret_cast<double*>(base + (size_t)(ns + 5) * field);
   double c0[3], c1[3], cr[3];
   if (ns == 3) {
     c0[0] = 1.0; c1[0] = 0.0; cr[0] = 1.0;
@@ -1244,7 +1412,7 @@ int grmhd_rk_step_adjoint(const grmhd_grid* grid, const grmhd_params* params, in
     if (c2p_adjoint(g, p, Pst[k + 1], metric, Pn, A, gamma_bar, nullptr, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     if (axpby(g, c0[k], A, 1.0, Bacc, s) != cudaSuccess) return GRMHD_ERR_CUDA;
     if (cudaMemsetAsync(Pk, 0, nbytes, s) != cudaSuccess) return GRMHD_ERR_CUDA;
-    if (launch_rhs_adjoint(g, p, Pst[k], metric, kij, A, cr[k] * dt, Pk, gamma_bar, s) != cudaSuccess)
+    if (launch_rhs_adjoint(g, p, Pst[k], metric, kij, A, cr[k] * dt, Pk, gamma_bar, s, Wb) != cudaSuccess)
       return GRMHD_ERR_CUDA;
     if (k >= 1) {
       if (axpby(g, 0.0, nullptr, c1[k], A, s) != cudaSuccess) return GRMHD_ERR_CUDA;
