@@ -416,7 +416,41 @@ __device__ __forceinline__ void weno5_value_grad2(const double uA[5], const doub
 // the same smoothness indicators in reverse order (t, e and p reversed, s
 // reversed with its middle entry negated, which the squares drop), so they
 // are formed once; the three reciprocals 1/ws+, 1/ws- and 1/(e0 e1 e2) come
-// from one division.
+// from one division.  The derivative of a state is
+//   dv/du_j = sum_k o_k dq_k/du_j + sum_k c_k (2 t_k dt_k/du_j + (6/13) s_k ds_k/du_j),
+//   c_k = -2 o_k (q_k - v) / e_k,  o_k = w_k / ws
+// (the weights sum to one, so the derivative of the normalisation drops
+// out); 2 t_k, (6/13) s_k and -2 p_k / (e0 e1 e2) = -2 / e_k are shared by
+// the two states.
+struct Weno5CellGradShared {
+  double t2[3], s613[3], m2ie[3];  // 2 t_k, (6/13) s_k, -2 p_k / ee (plus-state order)
+};
+
+// Value and gradient of one state from its parts (a: the state's stencil
+// order), the shared factors in that order (t2, s613, m2ie) and 1/ws.
+__device__ __forceinline__ double weno5_state_grad(const Weno5VG& a, const double t2[3], const double s613[3],
+                                                   const double m2ie[3], double iws, double gr[5]) {
+  const double c6 = 1.0 / 6.0;
+  double oc[3], tb[3], sb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) oc[k] = (a.w[k] * iws) * c6;  // o_k / 6
+  // 6 v (a.q holds 6 q_k)
+  const double v6 = 6.0 * fma(oc[0], a.q[0], fma(oc[1], a.q[1], oc[2] * a.q[2]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // c_k = -2 o_k (q_k - v) / e_k = (o_k / 6) (6 q_k - 6 v) (-2 / e_k)
+    const double ck = oc[k] * (a.q[k] - v6) * m2ie[k];
+    tb[k] = t2[k] * ck;
+    sb[k] = s613[k] * ck;
+  }
+  gr[0] = 2.0 * oc[0] + tb[0] + sb[0];
+  gr[1] = -7.0 * oc[0] - oc[1] - 2.0 * tb[0] - 4.0 * sb[0] + tb[1] + sb[1];
+  gr[2] = 11.0 * oc[0] + 5.0 * oc[1] + 2.0 * oc[2] + tb[0] + 3.0 * sb[0] - 2.0 * tb[1] + tb[2] + 3.0 * sb[2];
+  gr[3] = 2.0 * oc[1] + 5.0 * oc[2] + tb[1] - sb[1] - 2.0 * tb[2] - 4.0 * sb[2];
+  gr[4] = -oc[2] + tb[2] + sb[2];
+  return v6 * c6;
+}
+
 __device__ __forceinline__ void weno5_cell_value_grad(const double u[5], double eps13, double& vm, double gm[5],
                                                       double& vp, double gp[5]) {
   Weno5VG A, B;
@@ -424,26 +458,32 @@ __device__ __forceinline__ void weno5_cell_value_grad(const double u[5], double 
   B.q[0] = fma(2.0, u[4], fma(-7.0, u[3], 11.0 * u[2]));
   B.q[1] = fma(2.0, u[1], fma(5.0, u[2], -u[3]));
   B.q[2] = fma(5.0, u[1], fma(2.0, u[2], -u[0]));
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    B.t[k] = A.t[2 - k];
-    B.s[k] = A.s[2 - k];
-    B.e[k] = A.e[2 - k];
-    B.p[k] = A.p[2 - k];
-  }
-  B.s[1] = -A.s[1];
   B.w[0] = A.p[2] * A.p[2];
   B.w[1] = A.w[1];
   B.w[2] = 3.0 * A.w[0];
   B.ws = B.w[0] + B.w[1] + B.w[2];
-  B.ee = A.ee;
   const double ab = A.ws * B.ws;
   const double Z = rcp_nr(ab * A.ee);
   const double eZ = A.ee * Z;
+  const double m2iee = -2.0 * (ab * Z);  // -2 / (e0 e1 e2)
+  // shared factors in the plus state's order and mirrored for the minus state
+  double t2A[3], sA[3], mA[3], t2B[3], sB[3], mB[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    t2A[k] = 2.0 * A.t[k];
+    sA[k] = (6.0 / 13.0) * A.s[k];
+    mA[k] = A.p[k] * m2iee;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    t2B[k] = t2A[2 - k];
+    sB[k] = sA[2 - k];
+    mB[k] = mA[2 - k];
+  }
+  sB[1] = -sA[1];
   double gr[5];
-  const double iee = ab * Z;
-  vp = weno5_vg_finish(A, B.ws * eZ, iee, gp);
-  vm = weno5_vg_finish(B, A.ws * eZ, iee, gr);
+  vp = weno5_state_grad(A, t2A, sA, mA, B.ws * eZ, gp);
+  vm = weno5_state_grad(B, t2B, sB, mB, A.ws * eZ, gr);
 #pragma unroll
   for (int k = 0; k < 5; ++k) gm[k] = gr[4 - k];  // derivatives w.r.t. the mirrored stencil's u_{4-k}
 }
