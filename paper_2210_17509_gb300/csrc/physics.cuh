@@ -620,6 +620,124 @@ __device__ __forceinline__ void side_state(const T pr[8], const Geom<T>& m, T ga
   }
 }
 
+// ------------------------------------- both sides of a face, paired (FP32)
+// The two sides of a face run the same operations on different states, so
+// the FP32 face code forms them together: the left state in the .x lane and
+// the right state in the .y lane of paired FP32 instructions (one fma / add
+// / mul instruction for both sides), the metric of the face broadcast to both
+// lanes.  Square roots, reciprocal square roots and clamps stay per lane.
+// The operations are those of side_state<float, CURVED, 0, true, true> and
+// physical_state, with every sum and product written explicitly; they
+// differ from the scalar forms only in rounding order, and every FP32 kernel
+// forms its face fluxes through these, so the tiles, the batched kernels and
+// the constrained-transport ring faces stay bit-identical to one another.
+// a - b and -a, each rounded once (-1 * b is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(f2c(-1.0f), b, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(f2c(-1.0f), a); }
+// lowered vectors of both sides with the face metric
+template <bool CURVED>
+__device__ __forceinline__ void lower_x2(const Geom<float>& m, const float2 v[3], float2 vl[3]) {
+  if (CURVED) {
+    const float2 g0 = f2c(m.g[0]), g1 = f2c(m.g[1]), g2 = f2c(m.g[2]), g3 = f2c(m.g[3]), g4 = f2c(m.g[4]),
+                 g5 = f2c(m.g[5]);
+    vl[0] = __ffma2_rn(g2, v[2], __ffma2_rn(g1, v[1], __fmul2_rn(g0, v[0])));
+    vl[1] = __ffma2_rn(g4, v[2], __ffma2_rn(g3, v[1], __fmul2_rn(g1, v[0])));
+    vl[2] = __ffma2_rn(g5, v[2], __ffma2_rn(g4, v[1], __fmul2_rn(g2, v[0])));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vl[i] = v[i];
+  }
+}
+__device__ __forceinline__ float2 dot_x2(const float2 a[3], const float2 b[3]) {
+  return __ffma2_rn(a[2], b[2], __ffma2_rn(a[1], b[1], __fmul2_rn(a[0], b[0])));
+}
+// physical_state of both face states (unrotated, with the face metric)
+template <bool CURVED>
+__device__ __forceinline__ void physical_states_x2(const float pL[8], const float pR[8], const Geom<float>& m,
+                                                   bool& okL, bool& okR) {
+  float2 v[3], vl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = make_float2(pL[1 + i], pR[1 + i]);
+  lower_x2<CURVED>(m, v, vl);
+  const float2 v2 = dot_x2(v, vl);
+  okL = pL[0] > 0.0f && pL[4] > 0.0f && v2.x < 1.0f;
+  okR = pR[0] > 0.0f && pR[4] > 0.0f && v2.y < 1.0f;
+}
+// Side states of a face whose normal is the first axis (rotated states rL,
+// rR), SHARED and SCALED as side_state<float, CURVED, 0, true, true> forms
+// them: U and F without sqrt(gamma) and alpha, the speed numerators in lp /
+// lm and the denominator in sden, for finish_speeds and hlle_combine_scaled.
+// ia = 1 / alpha of the face.
+template <bool CURVED>
+__device__ __forceinline__ void side_states_x2(const float rL[8], const float rR[8], const Geom<float>& m,
+                                               float gamma, float gfac, float ia, Side<float>& L, Side<float>& R) {
+  const float2 rho = make_float2(rL[0], rR[0]), P = make_float2(rL[4], rR[4]);
+  float2 v[3], B[3], vl[3], Bl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    v[i] = make_float2(rL[1 + i], rR[1 + i]);
+    B[i] = make_float2(rL[5 + i], rR[5 + i]);
+  }
+  lower_x2<CURVED>(m, v, vl);
+  lower_x2<CURVED>(m, B, Bl);
+  const float2 v2 = dot_x2(v, vl), Bv = dot_x2(B, vl), B2 = dot_x2(B, Bl);
+  const float2 omv2 = sub2(f2c(1.0f), v2);
+  const float2 W = make_float2(rsqrtf(omv2.x), rsqrtf(omv2.y));
+  const float2 iW = __fmul2_rn(omv2, W);
+  const float2 ab0 = __fmul2_rn(W, Bv);
+  const float2 nab0 = neg2(ab0);
+  const float2 b2 = __ffma2_rn(B2, omv2, __fmul2_rn(Bv, Bv));
+  float2 bl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bl[i] = __ffma2_rn(Bl[i], iW, __fmul2_rn(ab0, vl[i]));
+  const float2 hs = __fadd2_rn(__ffma2_rn(f2c(gfac), P, rho), b2);
+  const float2 Ps = __ffma2_rn(f2c(0.5f), b2, P);
+  const float2 hW2 = __fmul2_rn(__fmul2_rn(hs, W), W);
+  const float2 D = __fmul2_rn(rho, W);
+  float2 U[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) U[i] = __ffma2_rn(nab0, bl[i], __fmul2_rn(hW2, vl[i]));
+  const float2 tau = sub2(__ffma2_rn(nab0, ab0, sub2(hW2, Ps)), D);
+  // v^i - beta^i / alpha, the shift term formed once for both sides
+  float2 vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vt[i] = CURVED ? __fadd2_rn(v[i], f2c(-m.beta[i] * ia)) : v[i];
+  const float2 vtd = vt[0];
+  const float2 nBdiW = neg2(__fmul2_rn(B[0], iW));
+  const float2 nB0 = neg2(B[0]);
+  float2 F[8];
+  F[0] = __fmul2_rn(D, vtd);
+  F[1] = __ffma2_rn(nBdiW, bl[0], __ffma2_rn(U[0], vtd, Ps));
+  F[2] = __ffma2_rn(nBdiW, bl[1], __fmul2_rn(U[1], vtd));
+  F[3] = __ffma2_rn(nBdiW, bl[2], __fmul2_rn(U[2], vtd));
+  F[4] = __ffma2_rn(nBdiW, ab0, __ffma2_rn(Ps, v[0], __fmul2_rn(tau, vtd)));
+  F[5] = f2c(0.0f);
+  F[6] = __ffma2_rn(nB0, vt[1], __fmul2_rn(B[1], vtd));
+  F[7] = __ffma2_rn(nB0, vt[2], __fmul2_rn(B[2], vtd));
+  const float2 Na = __ffma2_rn(f2c(gamma), P, b2);
+  const float2 dsp = __ffma2_rn(neg2(v2), Na, hs);
+  const float2 hmn = sub2(hs, Na);
+  const float gdd = CURVED ? m.gup_dd : 1.0f;
+  float2 Q = __ffma2_rn(f2c(gdd), dsp, __fmul2_rn(__fmul2_rn(neg2(v[0]), v[0]), hmn));
+  Q = make_float2(fmaxf(Q.x, 0.0f), fmaxf(Q.y, 0.0f));
+  const float2 a = __fmul2_rn(__fmul2_rn(Na, omv2), Q);
+  const float2 sq = make_float2(sqrtf(a.x), sqrtf(a.y));
+  const float2 c0 = __fmul2_rn(v[0], hmn);
+  const float2 lp = __fadd2_rn(c0, sq), lm = sub2(c0, sq);
+  L.U[0] = D.x; R.U[0] = D.y;
+  L.U[4] = tau.x; R.U[4] = tau.y;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    L.U[1 + i] = U[i].x; R.U[1 + i] = U[i].y;
+    L.U[5 + i] = B[i].x; R.U[5 + i] = B[i].y;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { L.F[q] = F[q].x; R.F[q] = F[q].y; }
+  L.lp = lp.x; R.lp = lp.y;
+  L.lm = lm.x; R.lm = lm.y;
+  L.sden = dsp.x; R.sden = dsp.y;
+}
+
 // Speeds of the two sides of a face from their SHARED side states: one
 // division for both denominators.
 template <class T, bool CURVED, int DIR>

@@ -345,20 +345,21 @@ __device__ __forceinline__ void face_flux_states(const DevGrid& g, const DevPara
     side_state<T, CURVED, 0, true, true>(rL, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), L, ia, rvL, v2L);
     side_state<T, CURVED, 0, true, true>(rR, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), R, ia, rvR, v2R);
   } else {
-    // FP32 (latency bound, 80 registers): fewer values live across the rotation
-    if (!physical_state<T, CURVED>(pL, m)) {
+    // FP32: both sides in paired instructions (one side per lane)
+    bool okL, okR;
+    physical_states_x2<CURVED>(pL, pR, m, okL, okR);
+    if (!okL) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) pL[q] = ld_pq<T>(src, g.ncell, q, c - stride);
     }
-    if (!physical_state<T, CURVED>(pR, m)) {
+    if (!okR) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) pR[q] = ld_pq<T>(src, g.ncell, q, c);
     }
     rotate_state(dir, pL, rL);
     rotate_state(dir, pR, rR);
     if (CURVED) rotate_metric(dir, m);
-    side_state<T, CURVED, 0, true, true>(rL, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), L, ia);
-    side_state<T, CURVED, 0, true, true>(rR, m, par_t<T>(p.gamma, p.gammaf), par_t<T>(p.gfac, p.gfacf), R, ia);
+    side_states_x2<CURVED>(rL, rR, m, p.gammaf, p.gfacf, ia, L, R);
   }
   finish_speeds<T, CURVED, 0>(m, L, R);
   hlle_combine_scaled<T>(L, R, CURVED ? m.alpha : T(1), CURVED ? m.sqrtg : T(1), Fr);
@@ -543,6 +544,13 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   }
   source_core<T, SrcCacheT<PT, GT>>(g, p, src, c, alpha, beta, gm, dA, st, out);
 }
+
+// A compute-type RHS value in FP64 for the stage epilogue: FP32 is widened on
+// the integer pipe (fpbits.cuh), which on this GPU would otherwise take an
+// FP64-pipe slot per value.  The result is the exact FP64 value, except that
+// FP32 subnormals (magnitude below 2^-126) become zero.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64i(x); }
 
 // Tile shapes the kernels are instantiated for (cells per axis, 256 cells each).
 template <int S> struct TileShape;
@@ -873,7 +881,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const long long o = q * g.ncell + c;
-      const double rq = (double)r[q];
+      const double rq = to_f64(r[q]);
       if (ep.rhs) ep.rhs[o] = rq;
       const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
       // FP64 (pipe bound): without an accumulator the ca term, an exact zero, is left out
@@ -1031,7 +1039,7 @@ __device__ __forceinline__ void div_cell(const DevGrid& g, const DevParams& p, c
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const long long o = q * g.ncell + c;
-    const double rq = (double)r[q];
+    const double rq = to_f64(r[q]);
     if (ep.rhs) ep.rhs[o] = rq;
     const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
     // without an accumulator the ca term (an exact zero) is left out: the same bits
