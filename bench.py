@@ -369,10 +369,10 @@ def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
     dt = 0.25 * blk.dx[0]
     prim0 = torch.from_numpy(prim_h[:, 3:-3, 3:-3, 3:-3].copy()).cuda()
 
-    def run(with_grad):
+    def run(with_grad, det=False):
         x = prim0.clone().requires_grad_(with_grad)
         gam = torch.tensor(p.gamma, dtype=torch.float64, requires_grad=with_grad)
-        L = A.density_l2(A.evolve(x, gam, g, p, G.RK3, dt, nsteps, checkpoint_every=every), g)
+        L = A.density_l2(A.evolve(x, gam, g, p, G.RK3, dt, nsteps, checkpoint_every=every, deterministic=det), g)
         return x, gam, L
 
     for _ in range(2):               # warm-up (module load, workspaces, the allocator's pools)
@@ -391,6 +391,25 @@ def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
     # the backward is driven from Python (a few thousand launches); a stall of the
     # shared host's CPU leaves the GPU idle and adds tens of ms to single passes
     t_fwd, t_bwd = min(reps, key=lambda r: r[1])
+    # the fixed-order reverse (GRMHD_DETERMINISTIC): one warm-up, two timed passes;
+    # the two gradients must agree to the bit
+    run(True, True)[2].backward()
+    dreps, dgrads = [], []
+    for _ in range(2):
+        e0.record()
+        xd, gd, Ld = run(True, True)
+        e1.record()
+        Ld.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        dreps.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        dgrads.append((xd.grad.clone(), float(gd.grad)))
+    dfwd, dbwd = min(dreps, key=lambda r: r[1])
+    deterministic = {
+        "passes_ms": dreps, "forward_ms": dfwd, "backward_ms": dbwd, "adjoint_forward_ratio": dbwd / dfwd,
+        "repeats_bitwise": bool(torch.equal(dgrads[0][0], dgrads[1][0]) and dgrads[0][1] == dgrads[1][1]),
+        "max_rel_diff_vs_atomic": float((dgrads[0][0] - x.grad).abs().max() / x.grad.abs().max()),
+    }
     # plain forward without checkpoint copies, for context
     e0.record()
     with torch.no_grad():
@@ -426,6 +445,7 @@ def adjoint_bench(G, n=64, nsteps=20, every=5, ndir=50):
         "passes_ms": reps,
         "forward_ms": t_fwd, "backward_ms": t_bwd, "forward_plain_ms": t_plain,
         "adjoint_forward_ratio": t_bwd / t_fwd, "adjoint_plain_forward_ratio": t_bwd / t_plain,
+        "deterministic": deterministic,
         "fd_check": ({"directions": ndir, "h": h, "max_rel_err": max(errs), "median_rel_err": float(np.median(errs))}
                      if errs else None),
         "loss": float(L.item()),

@@ -87,7 +87,8 @@ typedef struct {
   double nr_tol;     /* Newton stop: |dz|/z and |dW|/W below nr_tol (e.g. 1e-12) */
   double weno_eps;   /* WENO5 epsilon in alpha_k = d_k / (eps + beta_k)^2 (e.g. 1e-6) */
   int32_t tile;      /* RHS tile shape GRMHD_TILE_* (0 = 8x8x4); performance only */
-  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS */
+  int32_t flags;     /* 0, or GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS |
+                        GRMHD_DETERMINISTIC */
   int32_t eos;       /* GRMHD_EOS_IDEAL (Gamma-law, P = (Gamma - 1) rho eps) | GRMHD_EOS_POLYTROPE */
   double poly_K;     /* polytropic constant K of P = K rho^gamma (GRMHD_EOS_POLYTROPE; > 0) */
 } grmhd_params;
@@ -121,6 +122,17 @@ typedef struct {
  * minmod tiled faces, then the per-cell pass).  The results are the same; a
  * switch for comparison. */
 #define GRMHD_SINGLE_PASS 4
+/* flags: the reverse-mode calls (grmhd_rhs_adjoint, grmhd_con2prim_adjoint,
+ * grmhd_prim2con_adjoint, grmhd_rk_step_adjoint) add in a fixed order, so
+ * their results are the same to the bit from run to run.  Each direction's
+ * face adjoint runs in six launches, the faces by their index mod 6 (faces
+ * six apart have disjoint stencils, so no cell receives two adds in one
+ * launch), and the Gamma sums go to per-warp slots that the last block of
+ * each launch adds in slot order.  The slots belong to the library: calls
+ * with this flag must not run concurrently on different streams.  Without
+ * it the adds are atomic, their order varies and so do the last bits.
+ * grmhd_density_l2's loss sum stays atomic; the forward calls ignore it. */
+#define GRMHD_DETERMINISTIC 8
 
 /* RHS tile shapes (cells per CTA along x, y, z; 256 threads per CTA).  The
  * shape changes only how the work is cut, never the result.  8x8x8 (two
@@ -341,7 +353,8 @@ int grmhd_batch_graph_destroy(grmhd_batch_graph graph);
  *   prim_bar  acc  8 x ncell, ghost entries included (they receive the
  *                  adjoint of the stencil reads; see grmhd_fill_ghosts_adjoint)
  *   gamma_bar acc  one device double
- * Contributions are added with atomics; the summation order varies. */
+ * Contributions are added with atomics, in an order that varies, unless
+ * params->flags has GRMHD_DETERMINISTIC. */
 int grmhd_rhs_adjoint(const grmhd_grid* grid, const grmhd_params* params, const double* prim,
                       const double* metric, const double* kij, const double* rhs_bar, double* prim_bar,
                       double* gamma_bar, void* stream);

@@ -122,10 +122,14 @@ class _DensityL2(torch.autograd.Function):
 
 
 def evolve(prim0, gamma, grid: G.Grid, params: G.Params, scheme: int, dt: float, nsteps: int,
-           checkpoint_every: int = 5, metric=None, keep_last_segment: bool = True):
+           checkpoint_every: int = 5, metric=None, keep_last_segment: bool = True, deterministic: bool = False):
     """Interior primitives after nsteps steps (differentiable in prim0 and gamma).
     keep_last_segment=False recomputes the last segment in the backward pass
-    too (no memory beyond the checkpoints)."""
+    too (no memory beyond the checkpoints).  deterministic=True sets
+    GRMHD_DETERMINISTIC for the reverse calls: the gradients are then the
+    same to the bit from run to run."""
+    if deterministic:
+        params = dataclasses.replace(params, flags=params.flags | G.DETERMINISTIC)
     return _Evolve.apply(prim0, gamma, grid, params, scheme, dt, nsteps, checkpoint_every, metric,
                          keep_last_segment)
 

@@ -221,6 +221,53 @@ __device__ __forceinline__ void block_add_gamma(double v, double* gamma_bar) {
   if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gamma_bar, v);
 }
 
+// GRMHD_DETERMINISTIC: the same sum in a fixed order.  Every warp's partial
+// (reduced as above) goes to its slot, blockIdx * warps + warp; the block
+// that finishes last, elected by a ticket counter (no block waits for
+// another), sums the slots in slot order through a fixed tree and adds the
+// total to *gamma_bar once, then resets the ticket for the next launch.
+// The slots are the library's, so deterministic reverse calls on concurrent
+// streams would share them; they are meant for one stream at a time.
+// Grids are at most 152 x 32 blocks (blocks_for) of at most 256 threads.
+constexpr int kDetSlots = 152 * 32 * 8;
+__device__ double g_det_slots[kDetSlots];
+__device__ unsigned int g_det_ticket;
+
+__device__ __noinline__ void block_add_gamma_det(double v, double* gamma_bar) {
+  __shared__ double red[256];
+  __shared__ unsigned int last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int nw = blockDim.x >> 5;
+  const int nslot = min((int)gridDim.x * nw, kDetSlots);
+  const int slot = blockIdx.x * nw + (threadIdx.x >> 5);
+  if ((threadIdx.x & 31) == 0 && slot < kDetSlots) g_det_slots[slot] = v;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&g_det_ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x) s += __ldcg(g_det_slots + i);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (red[0] != 0.0) *gamma_bar += red[0];
+    g_det_ticket = 0u;
+  }
+}
+
+// Called by every thread of the block, once, at the end of the kernel.
+__device__ __forceinline__ void add_gamma(const DevParams& p, double v, double* gamma_bar) {
+  if (p.flags & GRMHD_DETERMINISTIC) block_add_gamma_det(v, gamma_bar);
+  else block_add_gamma(v, gamma_bar);
+}
+
 // ---------------------------------------------------- con2prim / prim2con
 // cons_bar += (dU/dP)^{-T} prim_bar;  gamma_bar -= x . dU/dGamma   (interior)
 __global__ void con2prim_adjoint_kernel(DevGrid g, DevParams p, const double* __restrict__ prim,
@@ -247,7 +294,7 @@ __global__ void con2prim_adjoint_kernel(DevGrid g, DevParams p, const double* __
       gb -= x[q] * J[q][8];
     }
   }
-  block_add_gamma(gb, gamma_bar);
+  add_gamma(p, gb, gamma_bar);
 }
 
 // prim_bar += (dU/dP)^T cons_bar;  gamma_bar += cons_bar . dU/dGamma   (interior)
@@ -274,7 +321,7 @@ __global__ void prim2con_adjoint_kernel(DevGrid g, DevParams p, const double* __
 #pragma unroll
     for (int i = 0; i < 8; ++i) gb += ub[i] * J[i][8];
   }
-  block_add_gamma(gb, gamma_bar);
+  add_gamma(p, gb, gamma_bar);
 }
 
 // ------------------------------------------------------------ ghost fill
@@ -855,10 +902,22 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
                                                               const double* __restrict__ metric,
                                                               const double* __restrict__ rhs_bar, double scale,
                                                               double* __restrict__ prim_bar,
-                                                              double* __restrict__ gamma_bar) {
-  const long long nfx = (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
-  const long long nfy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
-  const long long nfz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+                                                              double* __restrict__ gamma_bar, int dsel, int r0,
+                                                              int rstep) {
+  // dsel < 0: the faces of all three directions; else the dsel-faces at r0,
+  // r0 + rstep, ... along dsel (as rhs_face_adjoint_buf_kernel)
+  long long nfx = (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
+  long long nfy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
+  long long nfz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+  int nd = 0;
+  if (dsel >= 0) {
+    nd = g.n[dsel] + 1 > r0 ? (g.n[dsel] + 1 - r0 + rstep - 1) / rstep : 0;
+    const long long cross = (long long)g.n[0] * g.n[1] * g.n[2] / g.n[dsel];
+    nfx = dsel == 0 ? nd * cross : 0;
+    nfy = dsel == 1 ? nd * cross : 0;
+    nfz = dsel == 2 ? nd * cross : 0;
+  }
+  const int ex = dsel == 0 ? nd : g.n[0] + 1, ey = dsel == 1 ? nd : g.n[1] + 1;
   const long long total = nfx + nfy + nfz;
   extern __shared__ __align__(16) unsigned char adj_smem[];
   double* gsm = reinterpret_cast<double*>(adj_smem);  // WENO5 partials, 80 per thread
@@ -868,21 +927,26 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
     int dir, xi, yi, zi;
     if (f < nfx) {
       dir = 0;
-      xi = (int)(f % (g.n[0] + 1));
-      yi = (int)((f / (g.n[0] + 1)) % g.n[1]);
-      zi = (int)(f / ((long long)(g.n[0] + 1) * g.n[1]));
+      xi = (int)(f % ex);
+      yi = (int)((f / ex) % g.n[1]);
+      zi = (int)(f / ((long long)ex * g.n[1]));
     } else if (f < nfx + nfy) {
       const long long ff = f - nfx;
       dir = 1;
       xi = (int)(ff % g.n[0]);
-      yi = (int)((ff / g.n[0]) % (g.n[1] + 1));
-      zi = (int)(ff / ((long long)g.n[0] * (g.n[1] + 1)));
+      yi = (int)((ff / g.n[0]) % ey);
+      zi = (int)(ff / ((long long)g.n[0] * ey));
     } else {
       const long long ff = f - nfx - nfy;
       dir = 2;
       xi = (int)(ff % g.n[0]);
       yi = (int)((ff / g.n[0]) % g.n[1]);
       zi = (int)(ff / ((long long)g.n[0] * g.n[1]));
+    }
+    if (dsel >= 0) {
+      if (dir == 0) xi = r0 + rstep * xi;
+      else if (dir == 1) yi = r0 + rstep * yi;
+      else zi = r0 + rstep * zi;
     }
     const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
     const long long stride = dir == 0 ? 1 : (dir == 1 ? g.sy : g.sz);
@@ -901,7 +965,7 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_kernel(DevGrid g, DevPar
     else if (dir == 1) face_adjoint<RECON, CURVED, 1>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
     else face_adjoint<RECON, CURVED, 2>(g, p, prim, metric, c, Fb, prim_bar, gb, gsm);
   }
-  block_add_gamma(gb, gamma_bar);
+  add_gamma(p, gb, gamma_bar);
 }
 
 // The cell states of direction DIR with their derivatives, for the buffered
@@ -937,7 +1001,10 @@ __global__ void __launch_bounds__(128) adj_cell_states_kernel(DevGrid g, DevPara
   }
 }
 
-// Face adjoint of the DIR-faces from the cell-state buffer (WENO5).
+// Face adjoint of the DIR-faces from the cell-state buffer (WENO5).  Each
+// face adds into the six cells of its stencil along DIR; the faces r0,
+// r0 + 6, ... have disjoint stencils, so with rstep = 6 no cell receives two
+// adds in one launch (GRMHD_DETERMINISTIC runs r0 = 0 .. 5 in order).
 template <bool CURVED, int DIR>
 __global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, DevParams p,
                                                                   const double* __restrict__ prim,
@@ -945,15 +1012,21 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, De
                                                                   const double* __restrict__ rhs_bar, double scale,
                                                                   double* __restrict__ prim_bar,
                                                                   double* __restrict__ gamma_bar,
-                                                                  const double* __restrict__ Wb) {
-  const int fx = g.n[0] + (DIR == 0), fy = g.n[1] + (DIR == 1);
-  const long long total = (long long)fx * fy * (g.n[2] + (DIR == 2));
+                                                                  const double* __restrict__ Wb, int r0,
+                                                                  int rstep) {
+  // the DIR-faces at r0, r0 + rstep, ... along DIR (all of them: 0, 1)
+  const int nd = g.n[DIR] + 1 > r0 ? (g.n[DIR] + 1 - r0 + rstep - 1) / rstep : 0;
+  const int fx = DIR == 0 ? nd : g.n[0], fy = DIR == 1 ? nd : g.n[1], fz = DIR == 2 ? nd : g.n[2];
+  const long long total = (long long)fx * fy * fz;
   const long long stride = DIR == 0 ? 1 : (DIR == 1 ? g.sy : g.sz);
   double gb = 0.0;
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
        f += (long long)gridDim.x * blockDim.x) {
     const long long fxy = f / fx;
-    const int xi = (int)(f - fxy * fx), yi = (int)(fxy % fy), zi = (int)(fxy / fy);
+    int xi = (int)(f - fxy * fx), yi = (int)(fxy % fy), zi = (int)(fxy / fy);
+    if (DIR == 0) xi = r0 + rstep * xi;
+    else if (DIR == 1) yi = r0 + rstep * yi;
+    else zi = r0 + rstep * zi;
     const long long c = (long long)(zi + g.ng) * g.sz + (long long)(yi + g.ng) * g.sy + (xi + g.ng);
     const int ic = DIR == 0 ? xi : (DIR == 1 ? yi : zi);
     const bool has_hi = ic < g.n[DIR];  // cell c is interior
@@ -968,7 +1041,7 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, De
     }
     face_adjoint<GRMHD_WENO5, CURVED, DIR, true>(g, p, prim, metric, c, Fb, prim_bar, gb, nullptr, Wb);
   }
-  block_add_gamma(gb, gamma_bar);
+  add_gamma(p, gb, gamma_bar);
 }
 
 // ------------------------------------------------------------- source adjoint
@@ -1168,7 +1241,7 @@ __global__ void source_adjoint_kernel(DevGrid g, DevParams p, const double* __re
       if (pb[q] != 0.0) atomicAdd(prim_bar + q * g.ncell + c, pb[q]);
     gb += gfb * dgfac;
   }
-  block_add_gamma(gb, gamma_bar);
+  add_gamma(p, gb, gamma_bar);
 }
 
 // --------------------------------------------------------- elementwise pieces
@@ -1215,8 +1288,15 @@ cudaError_t launch_face_adjoint_dir(const DevGrid& g, const DevParams& p, const 
   const long long cells = 8LL * (g.n[0] + 2 * (DIR == 0)) * (g.n[1] + 2 * (DIR == 1)) * (g.n[2] + 2 * (DIR == 2));
   adj_cell_states_kernel<DIR><<<blocks_for(cells, 128), 128, 0, s>>>(g, p, prim, Wb);
   const long long faces = (long long)(g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-  rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces, 128), 128, 0, s>>>(g, p, prim, metric, rhs_bar, scale,
-                                                                                prim_bar, gamma_bar, Wb);
+  if (p.flags & GRMHD_DETERMINISTIC) {
+    // six launches, the faces of one residue of their index mod 6 each
+    for (int r = 0; r < 6; ++r)
+      rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces / 6 + 1, 128), 128, 0, s>>>(
+          g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, r, 6);
+  } else {
+    rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces, 128), 128, 0, s>>>(
+        g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, 0, 1);
+  }
   return cudaGetLastError();
 }
 
@@ -1249,12 +1329,20 @@ cudaError_t launch_rhs_adjoint(const DevGrid& g, const DevParams& p, const doubl
   const int nb = blocks_for(faces, 128);
   const bool weno = p.recon == GRMHD_WENO5;
   const size_t smem = weno ? (size_t)80 * 128 * sizeof(double) : 0;
-  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, double, double*, double*);
+  void (*k)(DevGrid, DevParams, const double*, const double*, const double*, double, double*, double*, int, int, int);
   if (metric) k = weno ? rhs_face_adjoint_kernel<GRMHD_WENO5, true> : rhs_face_adjoint_kernel<GRMHD_MINMOD, true>;
   else k = weno ? rhs_face_adjoint_kernel<GRMHD_WENO5, false> : rhs_face_adjoint_kernel<GRMHD_MINMOD, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<nb, 128, smem, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar);
+  if (p.flags & GRMHD_DETERMINISTIC) {
+    // per direction, six launches by face index mod 6 (disjoint stencils)
+    for (int d = 0; d < 3; ++d)
+      for (int r = 0; r < 6; ++r)
+        k<<<blocks_for(faces / 18 + 1, 128), 128, smem, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar,
+                                                             d, r, 6);
+  } else {
+    k<<<nb, 128, smem, s>>>(g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, -1, 0, 1);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess || !metric) return e;
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -1275,6 +1363,8 @@ size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
 int check_common(const grmhd_grid* grid, const grmhd_params* params, const double* metric) {
   if (!grid || !params) return GRMHD_ERR_ARG;
   if (params->precision != GRMHD_FP64) return GRMHD_ERR_ARG;  // the adjoint is of the FP64 method
+  if ((params->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS | GRMHD_DETERMINISTIC)) != 0)
+    return GRMHD_ERR_ARG;
   if (params->eos != GRMHD_EOS_IDEAL) return GRMHD_ERR_ARG;    // ... with the Gamma-law
   if (!(params->gamma > 1.0 && params->gamma <= 3.0)) return GRMHD_ERR_ARG;
   if (params->recon != GRMHD_WENO5 && params->recon != GRMHD_MINMOD) return GRMHD_ERR_ARG;

@@ -142,7 +142,8 @@ inline int check_params(const grmhd_params* p) {
   if (!(p->weno_eps > 0.0) || !std::isfinite(p->weno_eps)) return GRMHD_ERR_ARG;
   if (!(p->rho_atm > 0.0) || !(p->p_atm > 0.0)) return GRMHD_ERR_ARG;
   if (p->tile < 0 || p->tile > 4) return GRMHD_ERR_ARG;
-  if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS)) != 0) return GRMHD_ERR_ARG;
+  if ((p->flags & ~(GRMHD_REUSE_GEOMETRY | GRMHD_NEWMAN_HAMLIN | GRMHD_SINGLE_PASS | GRMHD_DETERMINISTIC)) != 0)
+    return GRMHD_ERR_ARG;
   if (p->eos != GRMHD_EOS_IDEAL && p->eos != GRMHD_EOS_POLYTROPE) return GRMHD_ERR_ARG;
   if (p->eos == GRMHD_EOS_POLYTROPE && !(p->poly_K > 0.0 && std::isfinite(p->poly_K))) return GRMHD_ERR_ARG;
   return GRMHD_OK;

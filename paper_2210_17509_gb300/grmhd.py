@@ -25,6 +25,7 @@ RK2, RK3, RK4 = 2, 3, 4
 REUSE_GEOMETRY = 1
 NEWMAN_HAMLIN = 2
 SINGLE_PASS = 4
+DETERMINISTIC = 8
 EOS_IDEAL, EOS_POLYTROPE = 0, 1
 
 

@@ -97,17 +97,22 @@ def test_recovery_flag_validation(lib):
     """Unknown flag bits are rejected; every call here fails validation before any launch."""
     g = _grid(lib).c()
     ws = ctypes.c_void_p(0x100000)
-    known = lib.REUSE_GEOMETRY | lib.NEWMAN_HAMLIN | lib.SINGLE_PASS
-    for flags in (8, 16, lib.NEWMAN_HAMLIN | 32, 1 << 20):
+    known = lib.REUSE_GEOMETRY | lib.NEWMAN_HAMLIN | lib.SINGLE_PASS | lib.DETERMINISTIC
+    for flags in (16, lib.NEWMAN_HAMLIN | 32, 1 << 20):
         assert flags & ~known
         p = lib.Params(flags=flags).c()
         assert lib._lib.grmhd_rhs(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, None) == -1
     # the known flags pass the parameter check and stop at the workspace size
-    for flags in (lib.NEWMAN_HAMLIN, lib.NEWMAN_HAMLIN | lib.REUSE_GEOMETRY, lib.SINGLE_PASS):
+    for flags in (lib.NEWMAN_HAMLIN, lib.NEWMAN_HAMLIN | lib.REUSE_GEOMETRY, lib.SINGLE_PASS, lib.DETERMINISTIC):
         p = lib.Params(flags=flags).c()
         rc = lib._lib.grmhd_rk_step(ctypes.byref(g), ctypes.byref(p), lib.RK3, 0.01, FAKE, FAKE, None, None, ws, 8,
                                     None, None)
         assert rc == -4
+    # the reverse calls check the same bits before any launch
+    for flags in (16, lib.DETERMINISTIC | 32, 1 << 20):
+        p = lib.Params(flags=flags).c()
+        assert lib._lib.grmhd_rhs_adjoint(ctypes.byref(g), ctypes.byref(p), FAKE, None, None, FAKE, FAKE, FAKE,
+                                          None) == -1
 
 
 def test_error_strings(lib):
