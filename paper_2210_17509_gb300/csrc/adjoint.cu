@@ -1004,8 +1004,11 @@ __global__ void __launch_bounds__(128) adj_cell_states_kernel(DevGrid g, DevPara
 // Face adjoint of the DIR-faces from the cell-state buffer (WENO5).  Each
 // face adds into the six cells of its stencil along DIR; the faces r0,
 // r0 + 6, ... have disjoint stencils, so with rstep = 6 no cell receives two
-// adds in one launch (GRMHD_DETERMINISTIC runs r0 = 0 .. 5 in order).
-template <bool CURVED, int DIR>
+// adds in one launch (GRMHD_DETERMINISTIC runs r0 = 0 .. 5 in order).  DET:
+// the fixed-order Gamma sum, a separate instantiation so that the default
+// kernel carries none of it (its reverse was 0.7% slower with a run-time
+// switch).
+template <bool CURVED, int DIR, bool DET>
 __global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, DevParams p,
                                                                   const double* __restrict__ prim,
                                                                   const double* __restrict__ metric,
@@ -1041,7 +1044,8 @@ __global__ void __launch_bounds__(128) rhs_face_adjoint_buf_kernel(DevGrid g, De
     }
     face_adjoint<GRMHD_WENO5, CURVED, DIR, true>(g, p, prim, metric, c, Fb, prim_bar, gb, nullptr, Wb);
   }
-  add_gamma(p, gb, gamma_bar);
+  if constexpr (DET) block_add_gamma_det(gb, gamma_bar);
+  else block_add_gamma(gb, gamma_bar);
 }
 
 // ------------------------------------------------------------- source adjoint
@@ -1291,10 +1295,10 @@ cudaError_t launch_face_adjoint_dir(const DevGrid& g, const DevParams& p, const 
   if (p.flags & GRMHD_DETERMINISTIC) {
     // six launches, the faces of one residue of their index mod 6 each
     for (int r = 0; r < 6; ++r)
-      rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces / 6 + 1, 128), 128, 0, s>>>(
+      rhs_face_adjoint_buf_kernel<CURVED, DIR, true><<<blocks_for(faces / 6 + 1, 128), 128, 0, s>>>(
           g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, r, 6);
   } else {
-    rhs_face_adjoint_buf_kernel<CURVED, DIR><<<blocks_for(faces, 128), 128, 0, s>>>(
+    rhs_face_adjoint_buf_kernel<CURVED, DIR, false><<<blocks_for(faces, 128), 128, 0, s>>>(
         g, p, prim, metric, rhs_bar, scale, prim_bar, gamma_bar, Wb, 0, 1);
   }
   return cudaGetLastError();
