@@ -64,9 +64,10 @@ def close(a, b, rel):
     return float((a - b).abs().max()) <= rel * scale
 
 
-@pytest.mark.parametrize("curved,recon,n", [(True, 1, (12, 10, 9)), (False, 1, (16, 7, 13)), (False, 0, (13, 4, 7))])
-def test_deterministic_step_adjoint_repeats_to_the_bit(G, curved, recon, n):
-    """SSP-RK3 reverse step (WENO5: the buffered face pass; minmod: the
+@pytest.mark.parametrize("curved,recon,n,scheme", [(True, 1, (12, 10, 9), 3), (False, 1, (16, 7, 13), 3),
+                                                  (False, 0, (13, 4, 7), 3), (True, 1, (9, 11, 8), 2)])
+def test_deterministic_step_adjoint_repeats_to_the_bit(G, curved, recon, n, scheme):
+    """SSP-RK3 / RK2 reverse step (WENO5: the buffered face pass; minmod: the
     per-face pass, one direction and one residue per launch) twice with the
     flag: the same bits; against the atomic adds: rounding only."""
     g, p, prim, met, blk = block(G, n, curved, recon)
@@ -77,7 +78,7 @@ def test_deterministic_step_adjoint_repeats_to_the_bit(G, curved, recon, n):
     for pp in (det(G, p), det(G, p), p):
         ub, pb = ub0.clone(), pb0.clone()
         gb = torch.zeros(1, dtype=torch.float64, device="cuda")
-        G.rk_step_adjoint(g, pp, G.RK3, dt, cons, prim, ub, pb, gb, met)
+        G.rk_step_adjoint(g, pp, scheme, dt, cons, prim, ub, pb, gb, met)
         torch.cuda.synchronize()
         out.append((ub, pb, gb))
     for k in range(3):
