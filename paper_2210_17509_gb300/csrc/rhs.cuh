@@ -514,22 +514,34 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   source_terms_f64<T, SrcF64Co>(g, p, src, c, out);
 }
 
+// A value the cell phase reads once (the sources' geometry, the stage
+// update's U0 and U): the FP32 kernels read it through L2 only
+// (ld.global.cg), leaving L1 to the primitive stencils and face metrics that
+// the face pass re-reads (measured: the FP32 RHS is sensitive to L1 space);
+// the FP64 kernels, bound by the FP64 pipe, keep the read-only path.
+template <bool L2ONLY, class V>
+__device__ __forceinline__ V ld_once(const V* p) {
+  if constexpr (L2ONLY) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // Metric quantities from the geometry cache.
 template <class T, class PT, class GT>
 __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& p, const SrcCacheT<PT, GT>& src,
                                              long long c, T out[8]) {
+  constexpr bool F32 = sizeof(GT) == 4;
   const GT* gc = src.geom;
   const long long n = g.ncell;
-  const T alpha = (T)__ldg(gc + c);
-  const T beta[3] = {(T)__ldg(gc + n + c), (T)__ldg(gc + 2 * n + c), (T)__ldg(gc + 3 * n + c)};
+  const T alpha = (T)ld_once<F32>(gc + c);
+  const T beta[3] = {(T)ld_once<F32>(gc + n + c), (T)ld_once<F32>(gc + 2 * n + c), (T)ld_once<F32>(gc + 3 * n + c)};
   T gm[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) gm[i] = (T)__ldg(gc + (4 + i) * n + c);
+  for (int i = 0; i < 6; ++i) gm[i] = (T)ld_once<F32>(gc + (4 + i) * n + c);
   T dA[3][10];
 #pragma unroll
   for (int e = 0; e < 3; ++e)
 #pragma unroll
-    for (int q = 0; q < 10; ++q) dA[e][q] = (T)__ldg(gc + (23 + 10 * e + q) * n + c);
+    for (int q = 0; q < 10; ++q) dA[e][q] = (T)ld_once<F32>(gc + (23 + 10 * e + q) * n + c);
   SrcStatics<T> st;
   if constexpr (sizeof(GT) == 8) {
     // FP64 cache: the metric factors formed once (the FP64 sources are bound by the FP64 pipe)
@@ -537,8 +549,8 @@ __device__ __forceinline__ void source_terms(const DevGrid& g, const DevParams& 
   } else {
     T gu[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) gu[i] = (T)__ldg(gc + (17 + i) * n + c);
-    const T sg = (T)__ldg(gc + 16 * n + c);
+    for (int i = 0; i < 6; ++i) gu[i] = (T)ld_once<F32>(gc + (17 + i) * n + c);
+    const T sg = (T)ld_once<F32>(gc + 16 * n + c);
     const T da[3] = {dA[0][0], dA[1][0], dA[2][0]};
     source_statics<T>(alpha, beta, gm, sg, gu, da, st);
   }
@@ -882,7 +894,10 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
     for (int q = 0; q < 8; ++q) {
       const long long o = q * g.ncell + c;
       const double rq = to_f64(r[q]);
-      if (ep.rhs) ep.rhs[o] = rq;
+      if (ep.rhs) {
+        if constexpr (sizeof(T) == 4) __stcg(ep.rhs + o, rq);
+        else ep.rhs[o] = rq;
+      }
       const double ain = ep.acc_in ? ep.acc_in[o] : 0.0;
       // FP64 (pipe bound): without an accumulator the ca term, an exact zero, is left out
       // (the same bits); the FP32 kernels keep the one expression, which measured faster there
@@ -890,7 +905,7 @@ __device__ __forceinline__ void rhs_tile(const DevGrid& g, const DevParams& p, c
         if (ep.u) ep.u[o] = ep.acc_in ? ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain
                                       : ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq;
       } else {
-        if (ep.u) ep.u[o] = ep.c0 * ep.u0[o] + ep.c1 * ep.u[o] + ep.cr * rq + ep.ca * ain;
+        if (ep.u) __stcg(ep.u + o, ep.c0 * ld_once<true>(ep.u0 + o) + ep.c1 * ld_once<true>(ep.u + o) + ep.cr * rq + ep.ca * ain);
       }
       if (ep.acc_out) ep.acc_out[o] = ep.wa * ain + ep.wr * rq;
     }
